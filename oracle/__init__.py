@@ -1,0 +1,149 @@
+"""CPU oracle of the reconstruction path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (the ``librta`` CUDA library
+and its binding) never loads it and shares no code with it.
+
+``oracle.c`` holds the arithmetic (plain C, FP64 except the one deliberate FP32
+calibration multiply); this module only marshals numpy arrays.  Row layouts:
+
+  hillas row (12 doubles): size, x, y, length, width, psi, r, phi,
+                           time_grad, time_mean, n_pix, flags
+  stereo row (6 doubles):  dir_x, dir_y (deg), core_x, core_y (m), n_valid, flags
+
+``mlp.py`` holds the FP64 deep-sets network, its backward pass and Adam.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+H_FIELDS = ["size", "x", "y", "length", "width", "psi", "r", "phi", "time_grad", "time_mean", "n_pix", "flags"]
+S_FIELDS = ["dir_x", "dir_y", "core_x", "core_y", "n_valid", "flags"]
+H = {k: i for i, k in enumerate(H_FIELDS)}
+S = {k: i for i, k in enumerate(S_FIELDS)}
+FLAG_EMPTY = 1
+FLAG_NO_TIME = 2
+FLAG_STEREO_INVALID = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so in-tree. -ffp-contract=off keeps the FP32 multiply un-fused."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32, i64, f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_float
+        lib.or_integrate.argtypes = [P, i32, i32, P, P, i32, i32, i32, P, P, P, P]
+        lib.or_clean.argtypes = [i32, P, P, i32, f32, f32, i32, P]
+        lib.or_hillas.argtypes = [i32, P, P, P, P, P]
+        lib.or_stereo.argtypes = [i32, P, P, P]
+        lib.or_reconstruct.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, i32, f32, f32, i32, P, P, P, P,
+                                       P, i64, P, P, P, i32]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def integrate(wave, p16, scale, sliding: bool, start: int, W: int):
+    """wave (P, S) uint16 -> (q float32, t float64, window start int32, window sum int64)."""
+    wave = np.ascontiguousarray(wave, np.uint16)
+    P, Sn = wave.shape
+    p16 = np.ascontiguousarray(p16, np.int32)
+    scale = np.ascontiguousarray(scale, np.float32)
+    q = np.zeros(P, np.float32)
+    t = np.zeros(P, np.float64)
+    ws = np.zeros(P, np.int32)
+    wsum = np.zeros(P, np.int64)
+    if _L().or_integrate(_p(wave), P, Sn, _p(p16), _p(scale), int(sliding), int(start), int(W), _p(q), _p(t),
+                         _p(ws), _p(wsum)) != 0:
+        raise ValueError("or_integrate: bad arguments")
+    return q, t, ws, wsum
+
+
+def clean(q, nb, t_hi: float, t_lo: float, core_needs_neighbour: bool):
+    q = np.ascontiguousarray(q, np.float32)
+    nb = np.ascontiguousarray(nb, np.int16)
+    mask = np.zeros(len(q), np.uint8)
+    _L().or_clean(len(q), _p(q), _p(nb), nb.shape[1], float(t_hi), float(t_lo), int(core_needs_neighbour), _p(mask))
+    return mask
+
+
+def hillas(xy, q, t, mask):
+    xy = np.ascontiguousarray(xy, np.float32)
+    q = np.ascontiguousarray(q, np.float32)
+    t = None if t is None else np.ascontiguousarray(t, np.float64)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    out = np.zeros(len(H_FIELDS), np.float64)
+    _L().or_hillas(len(q), _p(xy), _p(q), _p(t), _p(mask), _p(out))
+    return out
+
+
+def stereo(hrows, txy):
+    hrows = np.ascontiguousarray(hrows, np.float64).reshape(-1, len(H_FIELDS))
+    txy = np.ascontiguousarray(txy, np.float64).reshape(-1, 2)
+    out = np.zeros(len(S_FIELDS), np.float64)
+    _L().or_stereo(len(hrows), _p(hrows), _p(txy), _p(out))
+    return out
+
+
+def reconstruct(wl, threads: int | None = None, do_stereo: bool = True, per_pixel: bool = False, wave=None):
+    """Whole chain over a synth.Workload.
+
+    Returns dict(hillas=(n_img,12), stereo=(n_evt,6) or None, q/t/mask per pixel if asked)."""
+    lib = _L()
+    wave = wl.wave if wave is None else wave
+    cam_info = np.zeros((16, 3), np.int32)
+    cam_xy = (ctypes.c_void_p * 16)()
+    cam_nb = (ctypes.c_void_p * 16)()
+    keep = []
+    for c, cam in wl.cams.items():
+        cam_info[c] = (cam.n_pix, cam.n_samples, cam.K)
+        xy = np.ascontiguousarray(cam.xy, np.float32)
+        nb = np.ascontiguousarray(cam.nb, np.int16)
+        keep += [xy, nb]
+        cam_xy[c] = _p(xy).value
+        cam_nb[c] = _p(nb).value
+    n_img, n_evt = wl.n_img, wl.n_evt
+    hil = np.zeros((n_img, len(H_FIELDS)), np.float64)
+    ste = np.zeros((n_evt, len(S_FIELDS)), np.float64) if do_stereo else None
+    npx = int(wl.pix_off[-1])
+    q = np.zeros(npx, np.float32) if per_pixel else None
+    t = np.zeros(npx, np.float64) if per_pixel else None
+    mk = np.zeros(npx, np.uint8) if per_pixel else None
+    pr = wl.proc
+    threads = threads or os.cpu_count() or 1
+    tel_xy = np.ascontiguousarray(wl.tel_xy, np.float32)
+    st = lib.or_reconstruct(n_img, _p(wave), _p(wl.wave_off), _p(wl.img_tel), _p(wl.tel_cam), _p(wl.tel_pix_off),
+                            _p(wl.p16), _p(wl.scale), _p(cam_info), ctypes.cast(cam_xy, ctypes.c_void_p),
+                            ctypes.cast(cam_nb, ctypes.c_void_p), int(pr.sliding), int(pr.start), int(pr.W),
+                            float(pr.t_hi), float(pr.t_lo), int(pr.core_needs_neighbour), _p(hil),
+                            _p(wl.pix_off) if per_pixel else None, _p(q), _p(t), _p(mk), n_evt if do_stereo else 0,
+                            _p(wl.evt_off), _p(tel_xy), _p(ste), int(threads))
+    if st != 0:
+        raise RuntimeError("or_reconstruct failed")
+    return dict(hillas=hil, stereo=ste, q=q, t=t, mask=mk)
