@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark: waveform -> Hillas -> stereo reconstruction of the 69-telescope
+array (three camera types, bundles of 10,000 events of multiplicity 2-40).
+
+One step = one pass of the whole path over one bundle: the fused image kernel
+(calibrate + integrate + clean + Hillas, all images) and the stereo kernel (all
+events), on inputs already resident in HBM. `value` is events/s over all ranks;
+`e2e` is the same metric through the host-buffer call (pinned host bundle in,
+host event list out, copies inside the timed region). The roofline object
+reports the fused image kernel against the measured HBM copy bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--events E] [--impl ours|reference]
+
+Under torchrun each rank reconstructs its own bundle (different seed); the
+bundles are independent, so no collective touches the data path ("weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "waveform→Hillas→stereo events/s and GB/s vs HBM peak; p99 bundle latency"
+WORKLOAD = "69-telescope array bundle (4x1855px/40, 15x1764px/30, 50x2048px/25 samples), 10k gamma events"
+PAPER_RATE = "paper requirement: 0.5-8 GB/s of DL0 input (abstract, Sec. 2.2)"
+HILLAS_BYTES, STEREO_BYTES = 64, 32
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_bundle(n_events: int, seed: int, pinned: bool):
+    import synth
+    import torch
+    wl = synth.make_workload(2, n_events, seed=seed, render=False)
+    total = wl.n_samples_total
+    if pinned:
+        host = torch.empty(total, dtype=torch.int16, pin_memory=True)
+        buf = host.numpy().view(np.uint16)
+    else:
+        host, buf = None, np.empty(total, np.uint16)
+    synth.render_waves(wl, wave_out=buf)
+    return wl, host
+
+
+def cpu_baseline(wl, target_s: float = 15.0):
+    """The oracle, as it stands, on a bounded sample of the same bundle (all host cores)."""
+    import oracle
+    import synth
+    cores = os.cpu_count() or 1
+    n = min(wl.n_evt, 64)
+    while True:
+        sub = synth.subset(wl, np.arange(n))
+        t0 = time.perf_counter()
+        oracle.reconstruct(sub, threads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 4 or n >= wl.n_evt:
+            break
+        n = min(wl.n_evt, max(n * 2, int(n * target_s / 4 / max(dt, 1e-3))))
+    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} events ({sub.n_img} images, {sub.wave_bytes / 1e6:.0f} MB) of the bundle, "
+                      f"{dt:.1f} s on {cores} threads", "gbs": sub.wave_bytes / dt / 1e9}
+
+
+def run_reference(args, ws, rank):
+    """The reference arm of this build is the CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    wl = synth.make_workload(2, args.events, seed=synth.BASE_SEED + 2)
+    cores = os.cpu_count() or 1
+    per_step = max(8, min(wl.n_evt, args.ref_events))
+    rng = np.random.default_rng(0)
+    times = []
+    for k in range(args.warmup + args.steps):
+        ev = np.sort(rng.choice(wl.n_evt, per_step, replace=False))
+        sub = synth.subset(wl, ev)
+        t0 = time.perf_counter()
+        oracle.reconstruct(sub, threads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16->f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f"; each step {per_step} random events of it", "events": args.events,
+                       "preset": 2},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random events per step"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--events", type=int, default=10000)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-events", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1307_6489_gb300 as rta
+    import synth
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    seed = synth.BASE_SEED + 2 + 1000 * rank
+    wl, host = make_bundle(args.events, seed, pinned=True)
+    wave_h = host.numpy().view(np.uint16)
+
+    ctx = rta.Context(local, hbm_budget_bytes=8 << 30)
+    for c, cam in wl.cams.items():
+        ctx.register_camera(c, cam.xy, cam.nb, cam.n_samples)
+    ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
+    p = wl.proc
+    mode = rta.RTA_WINDOW_SLIDING if p.sliding else rta.RTA_WINDOW_FIXED
+    proc = (mode, p.start, p.W, p.t_hi, p.t_lo, p.core_needs_neighbour)
+    dev = torch.device("cuda", local)
+    wave = host.to(dev)
+    wave_off = torch.from_numpy(wl.wave_off).to(dev)
+    img_tel = torch.from_numpy(wl.img_tel).to(dev)
+    evt_off = torch.from_numpy(wl.evt_off).to(dev)
+    hil = torch.zeros(wl.n_img * 16, dtype=torch.float32, device=dev)
+    ste = torch.zeros(wl.n_evt * 8, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    h = ctx.handle
+    nw = wave.numel()
+
+    def step():
+        rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *proc,
+                            hil.data_ptr(), sp)
+        rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(),
+                       sp)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check(sp)
+
+    # ---------------- timed region (device-resident inputs; 5+ GB per bundle >> 129 MB L2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *proc,
+                            hil.data_ptr(), sp)
+        e1.record(stream)
+        rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(),
+                       sp)
+        e2.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.check(sp)
+    total_ms = t_start.elapsed_time(t_end)
+    chain_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    stereo_ms = [b.elapsed_time(c) for _, b, c in ev]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    events_all = wl.n_evt * ws
+    value = events_all / (ms_per_step / 1e3)
+
+    # ---------------- roofline of the dominant kernel (fused image kernel)
+    hbm_peak, peak_kind = peaks()
+    alg_bytes = wl.wave_bytes + wl.n_img * HILLAS_BYTES
+    chain_avg = statistics.mean(chain_ms)
+    achieved = alg_bytes / (chain_avg / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("kernel_hash") == _kernel_hash():
+                traffic = tj["bytes_per_image"] * wl.n_img
+        except Exception:
+            traffic = None
+
+    # ---------------- end to end through the host-buffer call
+    e2e_steps = args.e2e_steps or args.steps
+    hh = np.zeros(wl.n_img * 16, np.float32)
+    hs = np.zeros(wl.n_evt * 8, np.float32)
+    woff = np.ascontiguousarray(wl.wave_off)
+    itel = np.ascontiguousarray(wl.img_tel)
+    eoff = np.ascontiguousarray(wl.evt_off)
+    ctx.reconstruct_host(wave_h, woff, itel, eoff, *proc, hh, hs)   # warm (allocates staging)
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.reconstruct_host(wave_h, woff, itel, eoff, *proc, hh, hs)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.array_equal(hh.view(np.uint32), hil.cpu().numpy().view(np.uint32)), "host path differs"
+    h2d = wl.wave_bytes + wl.n_img * 12 + (wl.n_evt + 1) * 4
+    d2h = wl.n_img * HILLAS_BYTES + wl.n_evt * STEREO_BYTES
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        cfg = ctx.chain_config()
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16->int32/f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_bundle": wl.n_evt, "images_per_bundle": wl.n_img,
+                       "bundle_bytes": wl.wave_bytes, "mean_multiplicity": wl.n_img / wl.n_evt,
+                       "l2": "inputs larger than L2 (bundle >> 129 MB), no flush",
+                       "chain": cfg, "paper_context": PAPER_RATE},
+            "gbs": wl.wave_bytes * ws / (ms_per_step / 1e3) / 1e9,
+            "gbs_vs_hbm_peak": wl.wave_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+            "kernel_ms": {"image_chain": chain_avg, "stereo": statistics.mean(stereo_ms)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_image_chain", "algorithmic_bytes_per_launch": alg_bytes},
+            "e2e": {"value": events_all / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "gbs": wl.wave_bytes * ws / e2e_s / 1e9,
+                    "call": "rta_reconstruct_host (pinned host bundle)"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1307_6489_gb300", "csrc"))):
+        if f.startswith("k_image") or f.endswith(".cuh"):
+            h.update(open(os.path.join(ROOT, "paper_1307_6489_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    main()

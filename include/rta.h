@@ -1,0 +1,238 @@
+/*
+ * librta -- C ABI of the GB300 real-time reconstruction path for Cherenkov
+ * telescope arrays: waveform calibration and charge integration, tailcut
+ * cleaning, Hillas moments and stereo Hillas intersection.
+ *
+ * The paper (Bulgarelli et al., "The Real-Time Analysis of the CTA
+ * Observatory", ICRC 2013) defines the problem these calls solve: the RT-RECO
+ * stage turns the DL0 data of the central event builder (the waveforms of the
+ * telescopes triggered by one event, Sec. 2.2 and Sec. 4.1) into an event
+ * list through calibration with the calibration matrices and direction (and
+ * energy) reconstruction (Sec. 4.1), event by event and with the emphasis on
+ * speed (Sec. 4.2), keeping up with 0.5-8 GB/s of input (abstract, Sec. 2.2);
+ * Sec. 5 names GPU ports of signal-extraction algorithms. The paper prints no
+ * formula; each call below states the definition it computes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Return value: RTA_OK (0) or a negative rta_status. On failure
+ *    rta_last_error() returns a thread-local message. Nothing is launched when
+ *    argument checks fail.
+ *  - "d_" pointers are device pointers owned by the caller; "h_" pointers are
+ *    host pointers owned by the caller. The library owns the context, its copies
+ *    of geometry and calibration, and its scratch memory.
+ *  - Launch calls are asynchronous on the caller's stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream). Kernel-side input faults (an image
+ *    offset that is not 16-byte aligned, a telescope id out of range) never
+ *    fault the GPU: the image is skipped, its output row carries
+ *    RTA_HF_BAD_INPUT, and a bit is set in the context's device status word,
+ *    which rta_check() reports as RTA_E_DEVICE.
+ *  - There is no CPU fallback: every call runs CUDA kernels for sm_103a.
+ *
+ * Data layout (the bundle)
+ * ------------------------
+ *  - Waveforms: uint16 ADC samples, pixel-major and sample-minor: image i
+ *    occupies d_wave[d_wave_off[i] + p*S + k] for pixel p < P and sample k < S of
+ *    its camera. d_wave must be 16-byte aligned and every d_wave_off[i] a
+ *    multiple of 8 samples (16 bytes); each registered camera needs P*S to be a
+ *    multiple of 8.
+ *  - n_wave: number of uint16 samples in d_wave; an image whose samples do not
+ *    lie inside [0, n_wave) is skipped (RTA_HF_BAD_INPUT), never read.
+ *  - d_img_tel[i]: telescope id of image i (0 <= id < n_tel of rta_register_array).
+ *  - d_pix_off[i]: first row of image i in per-pixel arrays (q, t, mask) of
+ *    n_q rows; an image whose rows do not fit is skipped.
+ *  - d_evt_off[e] .. d_evt_off[e+1]: the images of event e (CSR, ascending,
+ *    within [0, n_img)); an event that breaks this is flagged RTA_SF_INVALID.
+ *  - Calibration rows: telescope t's pixel p uses row tel_row[t] + p where the
+ *    rows of all telescopes are concatenated in telescope order.
+ */
+#ifndef RTA_H
+#define RTA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rta_ctx rta_ctx;
+
+typedef enum {
+    RTA_OK = 0,
+    RTA_E_INVALID = -1, /* bad argument (size, range, NULL) */
+    RTA_E_ALIGN = -2,   /* pointer or camera size violates the 16-byte layout rule */
+    RTA_E_NOMEM = -3,   /* device allocation failed or the HBM budget is exceeded */
+    RTA_E_CUDA = -4,    /* a CUDA runtime call failed */
+    RTA_E_BUSY = -5,    /* a resource is in use; retry later */
+    RTA_E_TIMEOUT = -6, /* a bounded device wait ran out */
+    RTA_E_DEVICE = -7   /* the device status word reports a skipped input */
+} rta_status;
+
+/* Window modes of rta_calibrate_integrate / rta_image_chain */
+#define RTA_WINDOW_FIXED 0   /* samples [start, start+W) */
+#define RTA_WINDOW_SLIDING 1 /* the W-window of maximal integer sum, lowest start on ties */
+
+/* Hillas row flags */
+#define RTA_HF_EMPTY 1u     /* no pixel survived cleaning: every field but n_pix is 0 */
+#define RTA_HF_NO_TIME 2u   /* fewer than two pixels: time_grad is 0 */
+#define RTA_HF_BAD_INPUT 4u /* image skipped (misaligned offset or bad telescope id) */
+
+/* Stereo row flags */
+#define RTA_SF_INVALID 1u   /* no usable image pair: direction and core are 0 */
+
+/* Device status word bits (rta_check) */
+#define RTA_DEV_BAD_IMAGE 1u
+#define RTA_DEV_TIMEOUT 2u
+
+/* One image's parameters, 64 bytes. Angles in radians, positions in degrees of
+ * the flat camera (nominal) frame, time in samples (ns at 1 GS/s). */
+typedef struct rta_hillas_t {
+    float size;      /* sum of cleaned charges, photoelectrons */
+    float x, y;      /* charge-weighted centroid */
+    float length;    /* sqrt(lambda1) of the charge-weighted covariance */
+    float width;     /* sqrt(lambda2), computed as sqrt(det / lambda1) */
+    float psi;       /* major-axis angle, atan2(2 sxy, sxx - syy) / 2, in (-pi/2, pi/2] */
+    float r, phi;    /* polar coordinates of the centroid */
+    float time_grad; /* charge-weighted least-squares slope of pixel time along the major axis */
+    float time_mean; /* charge-weighted mean pixel time */
+    int32_t n_pix;   /* pixels that survived cleaning */
+    uint32_t flags;  /* RTA_HF_* */
+    float reserved[4];
+} rta_hillas_t;
+
+/* One event's stereo result, 32 bytes. */
+typedef struct rta_stereo_t {
+    float dir_x, dir_y;   /* reconstructed direction, degrees in the nominal frame */
+    float core_x, core_y; /* reconstructed impact point, metres on the ground */
+    int32_t n_valid;      /* images used (n_pix >= 3) */
+    uint32_t flags;       /* RTA_SF_* */
+    float reserved[2];
+} rta_stereo_t;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Library ABI version (major*100 + minor). */
+int rta_version(void);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* rta_last_error(void);
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes bounds the
+ * device memory the library itself may allocate for staging buffers of the
+ * host-buffer calls (0 = 4 GiB). Allocates the context's device status word
+ * and work counters. Returns RTA_E_CUDA if the device cannot be used. */
+int rta_create(rta_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Release every device and host resource of the context. Synchronises the
+ * device first. NULL is accepted. */
+int rta_destroy(rta_ctx* ctx);
+
+/* Register camera type `cam` (0 <= cam < 16): n_pix pixels (1..4096), n_samples
+ * samples per pixel (1..128, n_pix*n_samples a multiple of 8), pixel centres
+ * h_pix_xy[2*p], h_pix_xy[2*p+1] in degrees, and neighbour lists
+ * h_nb[p*K + j] (pixel ids, -1 padded, 1 <= K <= 8). Host arrays are copied. */
+int rta_register_camera(rta_ctx* ctx, int cam, int n_pix, int n_samples, const float* h_pix_xy,
+                        const int16_t* h_nb, int K);
+
+/* Register the array: n_tel telescopes (1..1024) with camera type h_tel_cam[t]
+ * (already registered), ground position h_tel_xy[2t], h_tel_xy[2t+1] in metres,
+ * and the calibration table (Sec. 4.1 "calibration matrices"): per row the
+ * pedestal in 1/16 ADC fixed point h_p16[row] and the FP32 factor
+ * h_scale[row] = 1 / (16 * gain * window containment) that converts the
+ * 1/16-ADC window numerator into photoelectrons. Rows of telescope t start at
+ * sum of n_pix of telescopes < t. Host arrays are copied. */
+int rta_register_array(rta_ctx* ctx, int n_tel, const int32_t* h_tel_cam, const float* h_tel_xy,
+                       const int32_t* h_p16, const float* h_scale);
+
+/* Synchronise `stream`, then read and clear the device status word.
+ * Returns RTA_OK, RTA_E_DEVICE (bits in *status_bits, may be NULL) or RTA_E_CUDA. */
+int rta_check(rta_ctx* ctx, void* stream, uint32_t* status_bits);
+
+/* Launch configuration of the fused image kernel (rta_image_chain and the
+ * calls built on it): n_stages shared-memory pipeline stages (2..8) and at most
+ * ctas_per_sm resident CTAs per SM (0 = as many as fit). Returns RTA_E_INVALID
+ * if the combination does not fit in shared memory. The autotuner of the
+ * Python binding sweeps these two values. */
+int rta_set_chain_config(rta_ctx* ctx, int n_stages, int ctas_per_sm);
+
+/* The configuration a launch would use now: stages, CTAs per SM, grid size and
+ * dynamic shared memory per CTA in bytes (NULL outputs are skipped). */
+int rta_get_chain_config(rta_ctx* ctx, int* n_stages, int* ctas_per_sm, int* grid, size_t* smem_bytes);
+
+/* ---------------------------------------------------------------------- */
+/* Stage calls (Sec. 4.1 calibration; Sec. 5 signal extraction)            */
+/* ---------------------------------------------------------------------- */
+
+/* Calibration + charge integration of n_img images. Per pixel:
+ *   window start s: `start` (RTA_WINDOW_FIXED) or the first start maximising the
+ *   integer W-sample sum (RTA_WINDOW_SLIDING);
+ *   num = 16 * sum - W * p16 (exact integer);  q = fp32(num) * scale (one FP32
+ *   multiply, round to nearest, never fused);
+ *   t = s + sum_j j * (16 * w[s+j] - p16) / num in FP32, or s + (W-1)/2 if num <= 0.
+ * Writes d_q[d_pix_off[i] + p] (photoelectrons) and, if d_t != NULL, d_t (samples).
+ * 1 <= W <= min(S, 16) for every camera the bundle uses; fixed windows need
+ * start + W <= S. */
+int rta_calibrate_integrate(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                            const int32_t* d_img_tel, const int64_t* d_pix_off, int64_t n_img, int window_mode,
+                            int start, int W, float* d_q, float* d_t, int64_t n_q, void* stream);
+
+/* Two-threshold tailcut cleaning of n_img images (charges d_q as written by
+ * rta_calibrate_integrate):
+ *   core     = q >= t_hi, and (if core_needs_neighbour) a neighbour with q >= t_hi
+ *   boundary = q >= t_lo and a core neighbour;   mask = core | boundary (one pass).
+ * Writes d_mask[d_pix_off[i] + p] in {0, 1}. Requires t_hi >= t_lo > 0. */
+int rta_clean(rta_ctx* ctx, const float* d_q, int64_t n_q, const int32_t* d_img_tel, const int64_t* d_pix_off,
+              int64_t n_img, float t_hi, float t_lo, int core_needs_neighbour, uint8_t* d_mask, void* stream);
+
+/* Hillas moments of n_img cleaned images (FP32, two-pass about the centroid),
+ * plus the time gradient when d_t != NULL. Writes d_out[i]. */
+int rta_hillas(rta_ctx* ctx, const float* d_q, const float* d_t, const uint8_t* d_mask, int64_t n_q,
+               const int32_t* d_img_tel, const int64_t* d_pix_off, int64_t n_img, rta_hillas_t* d_out, void* stream);
+
+/* The fused hot path: calibrate + integrate + clean + Hillas in one persistent
+ * launch over a mixed-camera bundle; per-pixel values stay in shared memory and
+ * only d_out[i] is written. Same definitions and argument rules as the three
+ * calls above. */
+int rta_image_chain(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                    const int32_t* d_img_tel, int64_t n_img, int window_mode, int start, int W, float t_hi,
+                    float t_lo, int core_needs_neighbour, rta_hillas_t* d_out, void* stream);
+
+/* Stereo Hillas intersection of n_evt events (direction reconstruction,
+ * Sec. 4.1). Images with n_pix >= 3 are used. For each used pair i < j with
+ * |sin(psi_j - psi_i)| >= 1e-6, the major axes u = (cos psi, sin psi) through
+ * the centroids meet at p_ij = c_i + u_i * cross(c_j - c_i, u_j) / sin(psi_j - psi_i)
+ * and, drawn through the telescope positions T, at g_ij on the ground; with
+ * w_ij = |sin(psi_i - psi_j)| * s_i s_j / (s_i + s_j) * (1 - W_i/L_i)(1 - W_j/L_j)
+ * the direction is sum w p / sum w and the core sum w g / sum w. Events with no
+ * usable pair get RTA_SF_INVALID. d_evt_off has n_evt + 1 entries; at most 64
+ * images per event are used. */
+int rta_stereo(rta_ctx* ctx, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+               const int32_t* d_evt_off, int64_t n_evt, rta_stereo_t* d_out, void* stream);
+
+/* One pass of the whole path over a device-resident bundle:
+ * rta_image_chain followed by rta_stereo, stream-ordered, no host sync and no
+ * allocation (capturable in a CUDA graph). d_hillas must hold n_img rows. */
+int rta_reconstruct(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                    const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off, int64_t n_evt, int window_mode,
+                    int start, int W, float t_hi, float t_lo, int core_needs_neighbour, rta_hillas_t* d_hillas,
+                    rta_stereo_t* d_stereo, void* stream);
+
+/* The same pass over a bundle in HOST memory (pinned memory gives full copy
+ * speed): the library copies the bundle to its own device staging buffers in
+ * event-aligned chunks, overlapping the copy of chunk k+1 with the work on
+ * chunk k, and copies the results back into h_hillas[n_img] and
+ * h_stereo[n_evt]. Blocks until the results are in host memory. Host offsets
+ * are as on the device. Staging memory is bounded by the context's budget. */
+int rta_reconstruct_host(rta_ctx* ctx, const uint16_t* h_wave, int64_t n_wave, const int64_t* h_wave_off,
+                         const int32_t* h_img_tel, int64_t n_img, const int32_t* h_evt_off, int64_t n_evt,
+                         int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                         rta_hillas_t* h_hillas, rta_stereo_t* h_stereo);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTA_H */

@@ -1,0 +1,326 @@
+"""Python binding of librta, the GB300 real-time reconstruction library.
+
+Argument marshalling only: every step runs in the CUDA kernels of
+``librta.so`` (built in-tree for sm_103a by ``_build.py``).  The functions
+below carry the C-ABI names of ``include/rta.h`` and take device pointers as
+integers (e.g. ``tensor.data_ptr()``) and streams as integers
+(``torch.cuda.current_stream().cuda_stream``).  ``Context`` is a convenience
+wrapper that accepts torch tensors and checks their dtype and device.
+
+There is no CPU fallback: if the library cannot be built or loaded, importing
+works but every call raises ``RtaUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+RTA_OK = 0
+RTA_E_INVALID = -1
+RTA_E_ALIGN = -2
+RTA_E_NOMEM = -3
+RTA_E_CUDA = -4
+RTA_E_BUSY = -5
+RTA_E_TIMEOUT = -6
+RTA_E_DEVICE = -7
+RTA_WINDOW_FIXED = 0
+RTA_WINDOW_SLIDING = 1
+RTA_HF_EMPTY = 1
+RTA_HF_NO_TIME = 2
+RTA_HF_BAD_INPUT = 4
+RTA_SF_INVALID = 1
+RTA_DEV_BAD_IMAGE = 1
+RTA_DEV_TIMEOUT = 2
+
+HILLAS_FIELDS = ["size", "x", "y", "length", "width", "psi", "r", "phi", "time_grad", "time_mean"]
+HILLAS_BYTES = 64
+STEREO_BYTES = 32
+
+_lib = None
+
+
+class RtaUnavailable(RuntimeError):
+    pass
+
+
+class RtaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"librta error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load librta.so (building it first if needed and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    try:
+        if build:
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+    except Exception as e:  # no nvcc, no library: fail loudly, never fall back
+        raise RtaUnavailable(f"librta is not available: {e}") from e
+    P, i32, i64, f32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    sig = {
+        "rta_version": ([], i32),
+        "rta_last_error": ([], ctypes.c_char_p),
+        "rta_create": ([P, i32, sz], i32),
+        "rta_destroy": ([P], i32),
+        "rta_register_camera": ([P, i32, i32, i32, P, P, i32], i32),
+        "rta_register_array": ([P, i32, P, P, P, P], i32),
+        "rta_check": ([P, P, P], i32),
+        "rta_set_chain_config": ([P, i32, i32], i32),
+        "rta_get_chain_config": ([P, P, P, P, P], i32),
+        "rta_calibrate_integrate": ([P, P, i64, P, P, P, i64, i32, i32, i32, P, P, i64, P], i32),
+        "rta_clean": ([P, P, i64, P, P, i64, f32, f32, i32, P, P], i32),
+        "rta_hillas": ([P, P, P, P, i64, P, P, i64, P, P], i32),
+        "rta_image_chain": ([P, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32, P, P], i32),
+        "rta_stereo": ([P, P, P, i64, P, i64, P, P], i32),
+        "rta_reconstruct": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P, P], i32),
+        "rta_reconstruct_host": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [l.split("(")[0].split()[-1].lstrip("*") for l in _header_decls()]
+
+
+def _header_decls():
+    """Function declarations of include/rta.h (one string each)."""
+    path = os.path.join(_build.INCLUDE, "rta.h")
+    text = open(path).read()
+    out, cur = [], ""
+    for line in text.splitlines():
+        s = line.strip()
+        if s.startswith(("int rta_", "const char* rta_", "void rta_")) or cur:
+            cur += " " + s
+            if s.endswith(";"):
+                out.append(cur.strip())
+                cur = ""
+    return out
+
+
+def _check(rc: int):
+    if rc != RTA_OK:
+        raise RtaError(rc, load().rta_last_error().decode())
+
+
+# ----------------------------------------------------------------------------- C-ABI names
+def rta_version() -> int:
+    return load().rta_version()
+
+
+def rta_last_error() -> str:
+    return load().rta_last_error().decode()
+
+
+def rta_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().rta_create(ctypes.byref(h), device, hbm_budget_bytes))
+    return h.value
+
+
+def rta_destroy(ctx: int):
+    _check(load().rta_destroy(ctx))
+
+
+def _np(a, dtype):
+    a = np.ascontiguousarray(a, dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def rta_register_camera(ctx: int, cam: int, n_pix: int, n_samples: int, pix_xy, nb, K: int):
+    xy, pxy = _np(pix_xy, np.float32)
+    nbv, pnb = _np(nb, np.int16)
+    _check(load().rta_register_camera(ctx, cam, n_pix, n_samples, pxy, pnb, K))
+
+
+def rta_register_array(ctx: int, n_tel: int, tel_cam, tel_xy, p16, scale):
+    a, pa = _np(tel_cam, np.int32)
+    b, pb = _np(tel_xy, np.float32)
+    c, pc = _np(p16, np.int32)
+    d, pd = _np(scale, np.float32)
+    _check(load().rta_register_array(ctx, n_tel, pa, pb, pc, pd))
+
+
+def rta_check(ctx: int, stream: int = 0) -> int:
+    """Synchronise and return the device status bits; raises RtaError(RTA_E_DEVICE) when non-zero."""
+    bits = ctypes.c_uint32(0)
+    rc = load().rta_check(ctx, stream, ctypes.byref(bits))
+    if rc not in (RTA_OK, RTA_E_DEVICE):
+        _check(rc)
+    if rc == RTA_E_DEVICE:
+        err = RtaError(rc, rta_last_error())
+        err.bits = bits.value
+        raise err
+    return bits.value
+
+
+def rta_set_chain_config(ctx: int, n_stages: int, ctas_per_sm: int):
+    _check(load().rta_set_chain_config(ctx, n_stages, ctas_per_sm))
+
+
+def rta_get_chain_config(ctx: int):
+    ns, cps, grid, smem = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(load().rta_get_chain_config(ctx, ctypes.byref(ns), ctypes.byref(cps), ctypes.byref(grid),
+                                       ctypes.byref(smem)))
+    return dict(n_stages=ns.value, ctas_per_sm=cps.value, grid=grid.value, smem_bytes=smem.value)
+
+
+def rta_calibrate_integrate(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, window_mode, start, W,
+                            d_q, d_t, n_q, stream=0):
+    _check(load().rta_calibrate_integrate(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, window_mode,
+                                          start, W, d_q, d_t, n_q, stream))
+
+
+def rta_clean(ctx, d_q, n_q, d_img_tel, d_pix_off, n_img, t_hi, t_lo, core_needs_neighbour, d_mask, stream=0):
+    _check(load().rta_clean(ctx, d_q, n_q, d_img_tel, d_pix_off, n_img, t_hi, t_lo, int(core_needs_neighbour),
+                            d_mask, stream))
+
+
+def rta_hillas(ctx, d_q, d_t, d_mask, n_q, d_img_tel, d_pix_off, n_img, d_out, stream=0):
+    _check(load().rta_hillas(ctx, d_q, d_t, d_mask, n_q, d_img_tel, d_pix_off, n_img, d_out, stream))
+
+
+def rta_image_chain(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
+                    core_needs_neighbour, d_out, stream=0):
+    _check(load().rta_image_chain(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi,
+                                  t_lo, int(core_needs_neighbour), d_out, stream))
+
+
+def rta_stereo(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_out, stream=0):
+    _check(load().rta_stereo(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_out, stream))
+
+
+def rta_reconstruct(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, d_evt_off, n_evt, window_mode, start, W, t_hi,
+                    t_lo, core_needs_neighbour, d_hillas, d_stereo, stream=0):
+    _check(load().rta_reconstruct(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, d_evt_off, n_evt, window_mode,
+                                  start, W, t_hi, t_lo, int(core_needs_neighbour), d_hillas, d_stereo, stream))
+
+
+def rta_reconstruct_host(ctx, h_wave, n_wave, h_wave_off, h_img_tel, n_img, h_evt_off, n_evt, window_mode, start, W,
+                         t_hi, t_lo, core_needs_neighbour, h_hillas, h_stereo):
+    _check(load().rta_reconstruct_host(ctx, h_wave, n_wave, h_wave_off, h_img_tel, n_img, h_evt_off, n_evt,
+                                       window_mode, start, W, t_hi, t_lo, int(core_needs_neighbour), h_hillas,
+                                       h_stereo))
+
+
+# ----------------------------------------------------------------------------- row decoding
+def hillas_to_numpy(raw: np.ndarray) -> dict:
+    """Decode rows of rta_hillas_t (a uint8/float32 buffer of n*64 bytes) into named arrays."""
+    raw = np.ascontiguousarray(raw).view(np.uint8).reshape(-1, HILLAS_BYTES)
+    f = raw.view(np.float32).reshape(-1, 16)
+    i = raw.view(np.int32).reshape(-1, 16)
+    out = {k: f[:, j].copy() for j, k in enumerate(HILLAS_FIELDS)}
+    out["n_pix"] = i[:, 10].copy()
+    out["flags"] = i[:, 11].view(np.uint32).copy()
+    return out
+
+
+def stereo_to_numpy(raw: np.ndarray) -> dict:
+    raw = np.ascontiguousarray(raw).view(np.uint8).reshape(-1, STEREO_BYTES)
+    f = raw.view(np.float32).reshape(-1, 8)
+    i = raw.view(np.int32).reshape(-1, 8)
+    return dict(dir_x=f[:, 0].copy(), dir_y=f[:, 1].copy(), core_x=f[:, 2].copy(), core_y=f[:, 3].copy(),
+                n_valid=i[:, 4].copy(), flags=i[:, 5].view(np.uint32).copy())
+
+
+# ----------------------------------------------------------------------------- convenience wrapper
+class Context:
+    """Owns an rta_ctx; methods take torch tensors (device pointers are read from them)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.handle = rta_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            rta_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register_camera(self, cam: int, pix_xy, nb, n_samples: int):
+        nb = np.asarray(nb)
+        rta_register_camera(self.handle, cam, nb.shape[0], n_samples, pix_xy, nb, nb.shape[1])
+
+    def register_array(self, tel_cam, tel_xy, p16, scale):
+        rta_register_array(self.handle, len(tel_cam), tel_cam, tel_xy, p16, scale)
+
+    def check(self, stream: int = 0) -> int:
+        return rta_check(self.handle, stream)
+
+    def set_chain_config(self, n_stages: int, ctas_per_sm: int):
+        rta_set_chain_config(self.handle, n_stages, ctas_per_sm)
+
+    def chain_config(self) -> dict:
+        return rta_get_chain_config(self.handle)
+
+    @staticmethod
+    def _stream(stream):
+        if stream is None:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        return int(stream)
+
+    def calibrate_integrate(self, wave, wave_off, img_tel, pix_off, window_mode, start, W, q, t=None, stream=None):
+        if t is not None:
+            assert t.numel() == q.numel()
+        rta_calibrate_integrate(self.handle, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(),
+                                pix_off.data_ptr(), img_tel.numel(), window_mode, start, W, q.data_ptr(),
+                                0 if t is None else t.data_ptr(), q.numel(), self._stream(stream))
+
+    def clean(self, q, img_tel, pix_off, t_hi, t_lo, core_needs_neighbour, mask, stream=None):
+        assert mask.numel() == q.numel()
+        rta_clean(self.handle, q.data_ptr(), q.numel(), img_tel.data_ptr(), pix_off.data_ptr(), img_tel.numel(),
+                  t_hi, t_lo, core_needs_neighbour, mask.data_ptr(), self._stream(stream))
+
+    def hillas(self, q, t, mask, img_tel, pix_off, out, stream=None):
+        assert mask.numel() == q.numel() and (t is None or t.numel() == q.numel())
+        rta_hillas(self.handle, q.data_ptr(), 0 if t is None else t.data_ptr(), mask.data_ptr(), q.numel(),
+                   img_tel.data_ptr(), pix_off.data_ptr(), img_tel.numel(), out.data_ptr(), self._stream(stream))
+
+    def image_chain(self, wave, wave_off, img_tel, window_mode, start, W, t_hi, t_lo, core_needs_neighbour, out,
+                    stream=None):
+        rta_image_chain(self.handle, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(),
+                        img_tel.numel(), window_mode, start, W, t_hi, t_lo, core_needs_neighbour, out.data_ptr(),
+                        self._stream(stream))
+
+    def stereo(self, hillas, evt_off, img_tel, out, stream=None):
+        rta_stereo(self.handle, hillas.data_ptr(), img_tel.data_ptr(), img_tel.numel(), evt_off.data_ptr(),
+                   evt_off.numel() - 1, out.data_ptr(), self._stream(stream))
+
+    def reconstruct(self, wave, wave_off, img_tel, evt_off, window_mode, start, W, t_hi, t_lo, core_needs_neighbour,
+                    hillas, stereo, stream=None):
+        rta_reconstruct(self.handle, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(),
+                        img_tel.numel(), evt_off.data_ptr(), evt_off.numel() - 1, window_mode, start, W, t_hi, t_lo,
+                        core_needs_neighbour, hillas.data_ptr(), stereo.data_ptr(), self._stream(stream))
+
+    def reconstruct_host(self, wave: np.ndarray, wave_off: np.ndarray, img_tel: np.ndarray, evt_off: np.ndarray,
+                         window_mode, start, W, t_hi, t_lo, core_needs_neighbour, hillas: np.ndarray,
+                         stereo: np.ndarray):
+        """Host buffers in, host rows out (hillas: n_img*64 bytes, stereo: n_evt*32 bytes)."""
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        for a in (wave, wave_off, img_tel, evt_off, hillas, stereo):
+            assert a.flags["C_CONTIGUOUS"]
+        rta_reconstruct_host(self.handle, ptr(wave), wave.size, ptr(wave_off), ptr(img_tel), len(img_tel), ptr(evt_off),
+                             len(evt_off) - 1, window_mode, start, W, t_hi, t_lo, core_needs_neighbour, ptr(hillas),
+                             ptr(stereo))

@@ -1,0 +1,588 @@
+// Image kernels: calibration + charge integration, tailcut cleaning and Hillas
+// moments (the per-telescope part of RT-RECO, Sec. 4.1; signal extraction,
+// Sec. 5).
+//
+// k_image_chain is the hot path. It is a persistent, warp-specialised kernel:
+//   warp 0      producer: takes the next image from a global work counter and
+//               streams it, chunk by chunk, into a ring of shared-memory stages
+//               with bulk copies on the TMA engine (cp.async.bulk, one mbarrier
+//               per stage, transaction-count completion); the calibration rows
+//               of the chunk's pixels travel with it;
+//   warps 1..8  consumers: one thread per pixel of the chunk computes the
+//               integer window sum, the single FP32 calibration multiply and the
+//               peak time, keeping q and t in shared memory; after the image's
+//               last chunk they clean it and reduce the Hillas moments with warp
+//               shuffles, while the producer already streams the next image.
+// Waveform bytes are read from HBM exactly once; per-pixel values never leave
+// the SM. Every mbarrier wait is bounded by the global timer; a wait that runs
+// out sets RTA_DEV_TIMEOUT, raises a CTA-wide abort flag and the CTA drains its
+// copies in flight before it returns.
+#include "rta_launch.cuh"
+
+namespace rta {
+
+constexpr int NCW = 8;             // consumer warps
+constexpr int NCT = NCW * 32;      // consumer threads = largest chunk in pixels
+constexpr int CHAIN_THREADS = NCT + 32;
+constexpr int MAX_STAGES = 8;
+
+enum { HDR_LAST = 1, HDR_BAD = 2, HDR_END = 4 };
+
+struct StageHdr {
+    int img;
+    int base;      // first pixel of the chunk
+    int npix;      // pixels in the chunk
+    int flags;     // HDR_*
+    int P, S, cam, pad;
+    int64_t pix_off;
+    int64_t pad2;
+};
+
+
+// ------------------------------------------------------------------ per-pixel integration
+template <int S>
+__device__ __forceinline__ void load_row(const uint16_t* row, uint32_t (&w)[(S + 1) / 2]) {
+    if constexpr ((2 * S) % 16 == 0) {
+        const uint4* v = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+        for (int k = 0; k < S / 8; ++k) {
+            uint4 a = v[k];
+            w[4 * k] = a.x; w[4 * k + 1] = a.y; w[4 * k + 2] = a.z; w[4 * k + 3] = a.w;
+        }
+    } else if constexpr (S % 2 == 0) {
+        const uint32_t* v = reinterpret_cast<const uint32_t*>(row);
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k) w[k] = v[k];
+    } else {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(row);
+        const uint32_t* v = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+        const uint32_t sh = (a & 2) ? 16u : 0u;
+        uint32_t tmp[(S + 1) / 2 + 1];
+#pragma unroll
+        for (int k = 0; k < (S + 1) / 2 + 1; ++k) tmp[k] = v[k];
+#pragma unroll
+        for (int k = 0; k < (S + 1) / 2; ++k) w[k] = __funnelshift_r(tmp[k], tmp[k + 1], sh);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ int sample(const uint32_t (&w)[(S + 1) / 2], int k) {
+    return (k & 1) ? int(w[k >> 1] >> 16) : int(w[k >> 1] & 0xFFFFu);
+}
+
+// Window of maximal integer sum, lowest start on ties: the key sum*128 + (127-k)
+// orders by sum first and, among equal sums, prefers the smaller start k.
+template <int S, int W>
+__device__ __forceinline__ void sliding_best_T(const uint16_t* row, int& best_sum, int& best_start) {
+    uint32_t w[(S + 1) / 2];
+    load_row<S>(row, w);
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) s += sample<S>(w, k);
+    int key = s * 128 + 127;
+#pragma unroll
+    for (int k = 1; k + W <= S; ++k) {
+        s += sample<S>(w, k + W - 1) - sample<S>(w, k - 1);
+        key = max(key, s * 128 + (127 - k));
+    }
+    best_sum = key >> 7;
+    best_start = 127 - (key & 127);
+}
+
+__device__ __forceinline__ void sliding_best_generic(const uint16_t* row, int S, int W, int& best_sum,
+                                                     int& best_start) {
+    int s = 0;
+    for (int k = 0; k < W; ++k) s += row[k];
+    int key = s * 128 + 127;
+    for (int k = 1; k + W <= S; ++k) {
+        s += int(row[k + W - 1]) - int(row[k - 1]);
+        key = max(key, s * 128 + (127 - k));
+    }
+    best_sum = key >> 7;
+    best_start = 127 - (key & 127);
+}
+
+// q and t of one pixel whose S samples start at `row` (shared memory).
+__device__ __forceinline__ void integrate_pixel(const uint16_t* row, int S, const ProcParams& pp, int p16,
+                                                float scale, float& q, float& t) {
+    const int W = pp.W;
+    int sum, st;
+    if (pp.sliding) {
+        if (S == 40 && W == 6) sliding_best_T<40, 6>(row, sum, st);
+        else if (S == 30 && W == 6) sliding_best_T<30, 6>(row, sum, st);
+        else if (S == 25 && W == 6) sliding_best_T<25, 6>(row, sum, st);
+        else if (S == 16 && W == 5) sliding_best_T<16, 5>(row, sum, st);
+        else sliding_best_generic(row, S, W, sum, st);
+    } else {
+        st = pp.start;
+        sum = 0;
+        for (int k = 0; k < W; ++k) sum += row[st + k];
+    }
+    int sj = 0;
+    for (int j = 1; j < W; ++j) sj += j * int(row[st + j]);
+    const int num = 16 * sum - W * p16;
+    const int numt = 16 * sj - p16 * (W * (W - 1) / 2);
+    q = __fmul_rn(__int2float_rn(num), scale);
+    t = num > 0 ? __fadd_rn(float(st), __fdiv_rn(__int2float_rn(numt), __int2float_rn(num)))
+                : float(st) + 0.5f * float(W - 1);
+}
+
+// ------------------------------------------------------------------ cleaning + Hillas
+struct NamedBar {
+    __device__ __forceinline__ void operator()() const { named_bar_sync(1, NCT); }
+};
+struct BlockBar {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Reduce N floats over `nthr` threads (nthr/32 warps): warp shuffle tree, then a
+// fixed-order sum over warps. The order never depends on the data or the batch.
+template <int N, class Bar>
+__device__ __forceinline__ void block_reduce(float (&v)[N], float* red, int tid, int nthr, Bar bar) {
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) red[warp * 8 + k] = v[k];
+    }
+    bar();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        float s = 0.f;
+        for (int w = 0; w < nthr / 32; ++w) s += red[w * 8 + k];
+        v[k] = s;
+    }
+}
+
+__device__ __forceinline__ bool any_neighbour(const int4 nbr, int K, const uint8_t* fl, uint8_t bit) {
+    const int16_t* n = reinterpret_cast<const int16_t*>(&nbr);
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < RTA_NB_PAD; ++j) {
+        const int id = n[j];
+        if (j < K && id >= 0 && (fl[id] & bit)) any = true;
+    }
+    return any;
+}
+
+// Tailcut flags in fl[p]: bit0 q >= t_hi, bit1 core, bit2 in the cleaned mask.
+// Returns via acc (per thread): n, sum q, sum q x, sum q y over masked pixels.
+template <class Bar>
+__device__ __forceinline__ void clean_image(const float* q, uint8_t* fl, const DevCam& C, const ProcParams& pp,
+                                            int tid, int nthr, Bar bar, float (&acc)[4]) {
+    const int P = C.P;
+    for (int p = tid; p < P; p += nthr) fl[p] = q[p] >= pp.t_hi ? 1 : 0;
+    bar();
+    for (int p = tid; p < P; p += nthr) {
+        const uint8_t f = fl[p];
+        if (f & 1) {
+            const bool ok = pp.core_nb ? any_neighbour(__ldg(C.nb + p), C.K, fl, 1) : true;
+            if (ok) fl[p] = f | 2;
+        }
+    }
+    bar();
+    acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+    for (int p = tid; p < P; p += nthr) {
+        const uint8_t f = fl[p];
+        const float qp = q[p];
+        bool m = (f & 2) != 0;
+        if (!m && qp >= pp.t_lo) m = any_neighbour(__ldg(C.nb + p), C.K, fl, 2);
+        if (m) {
+            fl[p] = f | 4;
+            const float2 xy = __ldg(C.xy + p);
+            acc[0] += 1.f;
+            acc[1] += qp;
+            acc[2] += qp * xy.x;
+            acc[3] += qp * xy.y;
+        }
+    }
+}
+
+// Hillas parameters from the masked pixels (fl bit2). acc holds the per-thread
+// first-moment partials of clean_image. Thread 0 writes the row.
+template <class Bar>
+__device__ __forceinline__ void hillas_image(const float* q, const float* t, const uint8_t* fl, const DevCam& C,
+                                             float (&acc)[4], float* red, int tid, int nthr, Bar bar,
+                                             rta_hillas_t* out) {
+    const int P = C.P;
+    block_reduce<4>(acc, red, tid, nthr, bar);
+    const int n = int(acc[0]);
+    const float size = acc[1];
+    if (n == 0 || !(size > 0.f)) {
+        if (tid == 0) {
+            rta_hillas_t h = {};
+            h.n_pix = n;
+            h.flags = RTA_HF_EMPTY | RTA_HF_NO_TIME;
+            *out = h;
+        }
+        return;
+    }
+    const float cx = __fdiv_rn(acc[2], size), cy = __fdiv_rn(acc[3], size);
+    float b[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p = tid; p < P; p += nthr) {
+        if (fl[p] & 4) {
+            const float qp = q[p];
+            const float2 xy = __ldg(C.xy + p);
+            const float dx = xy.x - cx, dy = xy.y - cy;
+            b[0] += qp * dx * dx;
+            b[1] += qp * dy * dy;
+            b[2] += qp * dx * dy;
+            if (t) b[3] += qp * t[p];
+        }
+    }
+    block_reduce<4>(b, red + NCW * 8 * 2, tid, nthr, bar);
+    const float sxx = __fdiv_rn(b[0], size), syy = __fdiv_rn(b[1], size), sxy = __fdiv_rn(b[2], size);
+    const float hd = 0.5f * (sxx - syy);
+    const float lam1 = 0.5f * (sxx + syy) + sqrtf(hd * hd + sxy * sxy);
+    const float det = diff_of_products(sxx, syy, sxy, sxy);
+    const float length = lam1 > 0.f ? sqrtf(lam1) : 0.f;
+    const float width = lam1 > 0.f ? sqrtf(fmaxf(det, 0.f) / lam1) : 0.f;
+    const float psi = 0.5f * atan2f(2.f * sxy, sxx - syy);
+    const float tmean = t ? __fdiv_rn(b[3], size) : 0.f;
+    float grad = 0.f;
+    uint32_t flags = 0;
+    if (t && n >= 2) {
+        float sp, cp;
+        sincosf(psi, &sp, &cp);
+        float c[2] = {0.f, 0.f};
+        for (int p = tid; p < P; p += nthr) {
+            if (fl[p] & 4) {
+                const float qp = q[p];
+                const float2 xy = __ldg(C.xy + p);
+                const float l = (xy.x - cx) * cp + (xy.y - cy) * sp;
+                c[0] += qp * l * l;
+                c[1] += qp * l * (t[p] - tmean);
+            }
+        }
+        block_reduce<2>(c, red + NCW * 8 * 1, tid, nthr, bar);
+        grad = c[0] > 0.f ? __fdiv_rn(c[1], c[0]) : 0.f;
+    } else {
+        flags |= RTA_HF_NO_TIME;
+    }
+    if (tid == 0) {
+        rta_hillas_t h;
+        h.size = size;
+        h.x = cx;
+        h.y = cy;
+        h.length = length;
+        h.width = width;
+        h.psi = psi;
+        h.r = sqrtf(cx * cx + cy * cy);
+        h.phi = atan2f(cy, cx);
+        h.time_grad = grad;
+        h.time_mean = tmean;
+        h.n_pix = n;
+        h.flags = flags;
+        h.reserved[0] = h.reserved[1] = h.reserved[2] = h.reserved[3] = 0.f;
+        *out = h;
+    }
+}
+
+__device__ __forceinline__ void write_bad_row(rta_hillas_t* out) {
+    rta_hillas_t h = {};
+    h.flags = RTA_HF_BAD_INPUT | RTA_HF_EMPTY | RTA_HF_NO_TIME;
+    *out = h;
+}
+
+// ------------------------------------------------------------------ the fused persistent kernel
+struct ChainSmem {
+    uint64_t full[MAX_STAGES];
+    uint64_t empty[MAX_STAGES];
+    StageHdr hdr[MAX_STAGES];
+    int abort;
+    int pad[31];
+    float red[3 * NCW * 8];
+};
+
+__global__ void __launch_bounds__(CHAIN_THREADS) k_image_chain(const ChainArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ChainSmem& sm = *reinterpret_cast<ChainSmem*>(smem_raw);
+    const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
+    const int NST = a.nstage;
+    const int calib_bytes = NCT * 4;
+    const int stage_bytes = a.stage_wave_bytes + 2 * calib_bytes;
+    unsigned char* stages = smem_raw + head;
+    float* sq = reinterpret_cast<float*>(stages + size_t(NST) * stage_bytes);
+    float* st = sq + a.arr.max_P;
+    uint8_t* fl = reinterpret_cast<uint8_t*>(st + a.arr.max_P);
+    volatile int* abort_flag = &sm.abort;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NCW);
+        }
+        sm.abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid < 32) {
+        // ---------------- producer warp: lane 0 issues everything
+        if (tid != 0) return;
+        const uint64_t pol_stream = l2_policy_evict_first();
+        const uint64_t pol_keep = l2_policy_evict_last();
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t pending = 0;          // stages whose copy is issued and not yet seen free again
+        uint32_t pend_par[MAX_STAGES];
+        bool ok = true;
+        auto acquire = [&](int s, uint32_t ph) -> bool {
+            if (!mbar_wait(&sm.empty[s], ph ^ 1u, abort_flag)) return false;
+            pending &= ~(1u << s);
+            return true;
+        };
+        for (;;) {
+            const unsigned int img_u = atomicAdd(a.counter, 1u);
+            const int64_t img = img_u;
+            if (img >= a.n_img) {
+                if (!acquire(stage, phase)) { ok = false; break; }
+                StageHdr h = {};
+                h.img = -1;
+                h.flags = HDR_END;
+                sm.hdr[stage] = h;
+                mbar_arrive(&sm.full[stage]);
+                break;
+            }
+            const int tel = a.img_tel[img];
+            const int64_t woff = a.wave_off[img];
+            bool bad = tel < 0 || tel >= a.arr.n_tel || woff < 0 || (woff & 7) != 0;
+            DevCam C = {};
+            int64_t poff = 0;
+            if (!bad) {
+                C = a.arr.cams[a.arr.tel_cam[tel]];
+                bad = woff + int64_t(C.P) * C.S > a.n_wave;       // never read past the waveform buffer
+                if (a.integrate_only) {
+                    poff = a.pix_off[img];
+                    bad = bad || poff < 0 || poff + C.P > a.n_q;    // never write past q / t
+                }
+            }
+            if (bad) {
+                if (!acquire(stage, phase)) { ok = false; break; }
+                StageHdr h = {};
+                h.img = int(img);
+                h.flags = HDR_BAD | HDR_LAST;
+                sm.hdr[stage] = h;
+                mbar_arrive(&sm.full[stage]);
+                if (++stage == NST) { stage = 0; phase ^= 1u; }
+                continue;
+            }
+            const int cam = a.arr.tel_cam[tel];
+            const int P = C.P, S = C.S, CP = C.chunk_pix;
+            const int64_t row = a.arr.tel_row[tel];
+            const uint16_t* src = a.wave + woff;
+            for (int base = 0; base < P; base += CP) {
+                if (!acquire(stage, phase)) { ok = false; break; }
+                const int npix = min(CP, P - base);
+                StageHdr h;
+                h.img = int(img);
+                h.base = base;
+                h.npix = npix;
+                h.flags = (base + CP >= P) ? HDR_LAST : 0;
+                h.P = P;
+                h.S = S;
+                h.cam = cam;
+                h.pad = 0;
+                h.pix_off = poff;
+                h.pad2 = 0;
+                sm.hdr[stage] = h;
+                const uint32_t wbytes = uint32_t(npix) * uint32_t(S) * 2u;     // multiple of 16 (P*S % 8 == 0)
+                const uint32_t cbytes = (uint32_t(npix) * 4u + 15u) & ~15u;
+                unsigned char* buf = stages + size_t(stage) * stage_bytes;
+                mbar_arrive_expect_tx(&sm.full[stage], wbytes + 2u * cbytes);
+                bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], pol_stream);
+                bulk_g2s(buf + a.stage_wave_bytes, a.arr.p16 + row + base, cbytes, &sm.full[stage], pol_keep);
+                bulk_g2s(buf + a.stage_wave_bytes + calib_bytes, a.arr.scale + row + base, cbytes, &sm.full[stage],
+                         pol_keep);
+                pending |= 1u << stage;
+                pend_par[stage] = phase;
+                if (++stage == NST) { stage = 0; phase ^= 1u; }
+            }
+            if (!ok) break;
+        }
+        if (!ok) {
+            atomicOr(a.status, RTA_DEV_TIMEOUT);
+            *abort_flag = 1;
+            // drain: every copy still in flight must land before the CTA exits
+            for (int s = 0; s < NST; ++s)
+                if (pending & (1u << s)) {
+                    const uint64_t t0 = global_ns();
+                    while (!mbar_try_wait(&sm.full[s], pend_par[s]))
+                        if (global_ns() - t0 > RTA_WAIT_TIMEOUT_NS) break;
+                }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
+    const int ct = tid - 32;          // 0 .. NCT-1
+    const int lane = tid & 31;
+    int stage = 0;
+    uint32_t phase = 0;
+    const ProcParams pp = a.pp;
+    for (;;) {
+        if (!mbar_wait(&sm.full[stage], phase, abort_flag)) {
+            if (!*abort_flag) atomicOr(a.status, RTA_DEV_TIMEOUT);
+            *abort_flag = 1;
+            break;
+        }
+        const StageHdr h = sm.hdr[stage];
+        if (h.flags & HDR_END) break;
+        if (h.flags & HDR_BAD) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            if (ct == 0) {
+                atomicOr(a.status, RTA_DEV_BAD_IMAGE);
+                if (!a.integrate_only) write_bad_row(a.out + h.img);
+            }
+            if (++stage == NST) { stage = 0; phase ^= 1u; }
+            continue;
+        }
+        const unsigned char* buf = stages + size_t(stage) * stage_bytes;
+        if (ct < h.npix) {
+            const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(ct) * h.S;
+            const int p16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes)[ct];
+            const float sc = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes)[ct];
+            float q, t;
+            integrate_pixel(row, h.S, pp, p16, sc, q, t);
+            const int p = h.base + ct;
+            if (a.integrate_only) {
+                a.q_out[h.pix_off + p] = q;
+                if (a.t_out) a.t_out[h.pix_off + p] = t;
+            } else {
+                sq[p] = q;
+                st[p] = t;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[stage]);
+        if (++stage == NST) { stage = 0; phase ^= 1u; }
+        if ((h.flags & HDR_LAST) && !a.integrate_only) {
+            named_bar_sync(1, NCT);
+            const DevCam C = a.arr.cams[h.cam];
+            float acc[4];
+            clean_image(sq, fl, C, pp, ct, NCT, NamedBar(), acc);
+            hillas_image(sq, st, fl, C, acc, sm.red, ct, NCT, NamedBar(), a.out + h.img);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ unfused stage kernels
+
+__global__ void __launch_bounds__(256) k_clean(const CleanArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* sq = reinterpret_cast<float*>(smem_raw);
+    uint8_t* fl = reinterpret_cast<uint8_t*>(sq + a.arr.max_P);
+    for (int64_t img = blockIdx.x; img < a.n_img; img += gridDim.x) {
+        const int tel = a.img_tel[img];
+        if (tel < 0 || tel >= a.arr.n_tel) {
+            if (threadIdx.x == 0) atomicOr(a.status, RTA_DEV_BAD_IMAGE);
+            continue;
+        }
+        const DevCam C = a.arr.cams[a.arr.tel_cam[tel]];
+        const int64_t off = a.pix_off[img];
+        if (off < 0 || off + C.P > a.n_q) {
+            if (threadIdx.x == 0) atomicOr(a.status, RTA_DEV_BAD_IMAGE);
+            continue;
+        }
+        for (int p = threadIdx.x; p < C.P; p += blockDim.x) sq[p] = a.q[off + p];
+        __syncthreads();
+        float acc[4];
+        clean_image(sq, fl, C, a.pp, threadIdx.x, blockDim.x, BlockBar(), acc);
+        __syncthreads();
+        for (int p = threadIdx.x; p < C.P; p += blockDim.x) a.mask[off + p] = (fl[p] >> 2) & 1;
+        __syncthreads();
+    }
+}
+
+
+__global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ float red[3 * NCW * 8];
+    float* sq = reinterpret_cast<float*>(smem_raw);
+    float* st = sq + a.arr.max_P;
+    uint8_t* fl = reinterpret_cast<uint8_t*>(st + a.arr.max_P);
+    for (int64_t img = blockIdx.x; img < a.n_img; img += gridDim.x) {
+        const int tel = a.img_tel[img];
+        if (tel < 0 || tel >= a.arr.n_tel) {
+            if (threadIdx.x == 0) {
+                atomicOr(a.status, RTA_DEV_BAD_IMAGE);
+                write_bad_row(a.out + img);
+            }
+            continue;
+        }
+        const DevCam C = a.arr.cams[a.arr.tel_cam[tel]];
+        const int64_t off = a.pix_off[img];
+        if (off < 0 || off + C.P > a.n_q) {
+            if (threadIdx.x == 0) {
+                atomicOr(a.status, RTA_DEV_BAD_IMAGE);
+                write_bad_row(a.out + img);
+            }
+            continue;
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int p = threadIdx.x; p < C.P; p += blockDim.x) {
+            const float qp = a.q[off + p];
+            const uint8_t m = a.mask[off + p] ? 4 : 0;
+            sq[p] = qp;
+            if (a.t) st[p] = a.t[off + p];
+            fl[p] = m;
+            if (m) {
+                const float2 xy = __ldg(C.xy + p);
+                acc[0] += 1.f;
+                acc[1] += qp;
+                acc[2] += qp * xy.x;
+                acc[3] += qp * xy.y;
+            }
+        }
+        __syncthreads();
+        hillas_image(sq, a.t ? st : nullptr, fl, C, acc, red, threadIdx.x, blockDim.x, BlockBar(), a.out + img);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host-side launchers
+size_t chain_smem_bytes(int nstage, int stage_wave_bytes, int max_P) {
+    const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
+    return head + size_t(nstage) * (stage_wave_bytes + 2 * NCT * 4) + size_t(max_P) * 9 + 16;
+}
+
+int chain_threads() { return CHAIN_THREADS; }
+int chain_max_chunk_pix() { return NCT; }
+
+cudaError_t launch_image_chain(const ChainArgs& a, int grid, size_t smem, cudaStream_t s) {
+    // the dynamic shared-memory opt-in is per device; remember the largest size set
+    static size_t attr_bytes[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || attr_bytes[dev] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_image_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_bytes[dev] = smem;
+    }
+    k_image_chain<<<grid, CHAIN_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int chain_occupancy(size_t smem) {
+    cudaFuncSetAttribute(k_image_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_image_chain, CHAIN_THREADS, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s) {
+    const size_t smem = size_t(a.arr.max_P) * 5 + 16;
+    k_clean<<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s) {
+    const size_t smem = size_t(a.arr.max_P) * 9 + 16;
+    k_hillas<<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace rta

@@ -1,0 +1,615 @@
+// Host side of librta: the C ABI declared in include/rta.h. Argument checks,
+// the context (registered cameras, array, calibration table, device status
+// word, work counters), launch configuration and its autotuner, and the
+// host-buffer path with double-buffered staging.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "rta.h"
+#include "rta_launch.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(RTA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int N_COUNTERS = 1024;
+
+struct HostCam {
+    bool valid = false;
+    int P = 0, S = 0, K = 0;
+    float2* d_xy = nullptr;
+    int4* d_nb = nullptr;
+};
+
+struct Slot {  // one half of the host-path double buffer
+    cudaStream_t stream = nullptr;
+    cudaEvent_t meta_done = nullptr;
+    uint16_t* d_wave = nullptr;
+    size_t wave_cap = 0;
+    int64_t* d_off = nullptr;
+    int32_t* d_tel = nullptr;
+    int32_t* d_evt = nullptr;
+    rta_hillas_t* d_h = nullptr;
+    rta_stereo_t* d_s = nullptr;
+    size_t img_cap = 0, evt_cap = 0;
+    int64_t* h_off = nullptr;   // pinned
+    int32_t* h_evt = nullptr;   // pinned
+};
+
+}  // namespace
+
+struct rta_ctx {
+    int device = 0;
+    int n_sm = 0;
+    size_t budget = 0;
+    size_t staged_bytes = 0;
+    HostCam cams[RTA_MAX_CAMS];
+    rta::DevCam* d_cams = nullptr;
+    int n_tel = 0;
+    std::vector<int32_t> tel_cam;
+    int32_t* d_tel_cam = nullptr;
+    float2* d_tel_xy = nullptr;
+    int64_t* d_tel_row = nullptr;
+    int32_t* d_p16 = nullptr;
+    float* d_scale = nullptr;
+    unsigned int* d_status = nullptr;
+    unsigned int* d_counters = nullptr;
+    std::atomic<unsigned> next_counter{0};
+    // launch configuration of the fused image kernel
+    int nstage = 4;
+    int ctas_per_sm = 0;  // 0 = as many as fit
+    int stage_wave_bytes = 0;
+    int max_P = 0, max_S = 0;
+    Slot slot[2];
+    std::mutex host_mu;
+};
+
+namespace {
+
+int check_ctx(rta_ctx* c) {
+    if (!c) return fail(RTA_E_INVALID, "context is NULL");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(RTA_E_CUDA, "cudaSetDevice(%d) failed", c->device);
+    return RTA_OK;
+}
+
+int check_array(rta_ctx* c) {
+    if (c->n_tel <= 0) return fail(RTA_E_INVALID, "no array registered (rta_register_array)");
+    return RTA_OK;
+}
+
+// Work counters for device-resident calls: a ring, so that calls in flight on
+// different streams use different counters. The last two belong to the
+// host-buffer path.
+unsigned int* take_counter(rta_ctx* c) {
+    unsigned i = c->next_counter.fetch_add(1) % (N_COUNTERS - 2);
+    return c->d_counters + i;
+}
+
+// Recompute the per-stage buffer size and every camera's chunk size.
+int refresh_cams(rta_ctx* c) {
+    int maxS = 1, maxP = 1;
+    for (auto& h : c->cams)
+        if (h.valid) { maxS = std::max(maxS, h.S); maxP = std::max(maxP, h.P); }
+    const int nct = rta::chain_max_chunk_pix();
+    int swb = ((nct * 2 * maxS + 16) + 127) & ~127;
+    swb = std::min(swb, 24576);
+    c->stage_wave_bytes = swb;
+    c->max_P = maxP;
+    c->max_S = maxS;
+    rta::DevCam dc[RTA_MAX_CAMS];
+    memset(dc, 0, sizeof dc);
+    for (int i = 0; i < RTA_MAX_CAMS; ++i) {
+        const HostCam& h = c->cams[i];
+        if (!h.valid) continue;
+        int cp = ((swb - 16) / (2 * h.S)) & ~7;
+        cp = std::min(cp, nct);
+        dc[i].P = h.P;
+        dc[i].S = h.S;
+        dc[i].K = h.K;
+        dc[i].chunk_pix = cp;
+        dc[i].xy = h.d_xy;
+        dc[i].nb = h.d_nb;
+    }
+    CUDA_TRY(cudaMemcpy(c->d_cams, dc, sizeof dc, cudaMemcpyHostToDevice));
+    return RTA_OK;
+}
+
+rta::DevArray dev_array(rta_ctx* c) {
+    rta::DevArray a;
+    a.cams = c->d_cams;
+    a.tel_cam = c->d_tel_cam;
+    a.tel_xy = c->d_tel_xy;
+    a.tel_row = c->d_tel_row;
+    a.p16 = c->d_p16;
+    a.scale = c->d_scale;
+    a.n_tel = c->n_tel;
+    a.max_P = c->max_P;
+    return a;
+}
+
+// Window and tailcut rules against every camera the array uses.
+int check_proc(rta_ctx* c, int mode, int start, int W, bool need_clean, float t_hi, float t_lo) {
+    if (mode != RTA_WINDOW_FIXED && mode != RTA_WINDOW_SLIDING) return fail(RTA_E_INVALID, "bad window mode %d", mode);
+    if (W < 1 || W > RTA_MAX_W) return fail(RTA_E_INVALID, "window width %d outside 1..%d", W, RTA_MAX_W);
+    for (int t = 0; t < c->n_tel; ++t) {
+        const HostCam& h = c->cams[c->tel_cam[t]];
+        if (W > h.S) return fail(RTA_E_INVALID, "window width %d exceeds %d samples of camera %d", W, h.S, c->tel_cam[t]);
+        if (mode == RTA_WINDOW_FIXED && (start < 0 || start + W > h.S))
+            return fail(RTA_E_INVALID, "fixed window [%d, %d) outside %d samples", start, start + W, h.S);
+    }
+    if (need_clean && !(t_hi >= t_lo && t_lo > 0.f))
+        return fail(RTA_E_INVALID, "tailcut thresholds need t_hi >= t_lo > 0 (got %g, %g)", t_hi, t_lo);
+    return RTA_OK;
+}
+
+int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem) {
+    const int nst = std::max(2, std::min(c->nstage, 8));
+    *smem = rta::chain_smem_bytes(nst, c->stage_wave_bytes, c->max_P);
+    int occ = rta::chain_occupancy(*smem);
+    if (occ < 1) return fail(RTA_E_INVALID, "image kernel does not fit: %zu bytes of shared memory", *smem);
+    if (c->ctas_per_sm > 0) occ = std::min(occ, c->ctas_per_sm);
+    int64_t g = int64_t(c->n_sm) * occ;
+    g = std::min<int64_t>(g, std::max<int64_t>(n_img, 1));
+    *grid = int(g);
+    return RTA_OK;
+}
+
+int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
+              const int64_t* d_pix_off, int64_t n_img, const rta::ProcParams& pp, float* d_q, float* d_t,
+              int64_t n_q, rta_hillas_t* d_out, int integrate_only, cudaStream_t s, unsigned int* counter) {
+    int grid;
+    size_t smem;
+    int rc = chain_launch_config(c, n_img, &grid, &smem);
+    if (rc) return rc;
+    rta::ChainArgs a;
+    a.arr = dev_array(c);
+    a.pp = pp;
+    a.wave = d_wave;
+    a.n_wave = n_wave;
+    a.wave_off = d_wave_off;
+    a.img_tel = d_img_tel;
+    a.pix_off = d_pix_off;
+    a.n_q = n_q;
+    a.n_img = n_img;
+    a.q_out = d_q;
+    a.t_out = d_t;
+    a.out = d_out;
+    a.counter = counter ? counter : take_counter(c);
+    a.status = c->d_status;
+    a.stage_wave_bytes = c->stage_wave_bytes;
+    a.nstage = std::max(2, std::min(c->nstage, 8));
+    a.integrate_only = integrate_only;
+    CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
+    CUDA_TRY(rta::launch_image_chain(a, grid, smem, s));
+    return RTA_OK;
+}
+
+int run_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off,
+               int64_t n_evt, rta_stereo_t* d_out, cudaStream_t s) {
+    rta::StereoArgs a;
+    a.arr = dev_array(c);
+    a.h = d_h;
+    a.img_tel = d_img_tel;
+    a.n_img = n_img;
+    a.evt_off = d_evt_off;
+    a.n_evt = n_evt;
+    a.out = d_out;
+    a.status = c->d_status;
+    const int epb = rta::stereo_events_per_block();
+    int64_t g = (n_evt + epb - 1) / epb;
+    g = std::min<int64_t>(g, int64_t(c->n_sm) * 16);
+    CUDA_TRY(rta::launch_stereo(a, int(std::max<int64_t>(g, 1)), s));
+    return RTA_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_n(int64_t n, const char* what) {
+    if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(RTA_E_INVALID, "%s = %lld outside 0..2^31-1", what, (long long)n);
+    return RTA_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+int rta_version(void) { return 100; }
+
+const char* rta_last_error(void) { return g_err; }
+
+int rta_create(rta_ctx** out, int device, size_t hbm_budget_bytes) {
+    if (!out) return fail(RTA_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RTA_E_CUDA, "no CUDA device available");
+    if (device < 0 || device >= ndev) return fail(RTA_E_INVALID, "device %d outside 0..%d", device, ndev - 1);
+    CUDA_TRY(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) return fail(RTA_E_CUDA, "device %d is sm_%d%d; librta is built for sm_103a", device, prop.major, prop.minor);
+    rta_ctx* c = new rta_ctx();
+    c->device = device;
+    c->n_sm = prop.multiProcessorCount;
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t(4) << 30);
+    if (cudaMalloc(&c->d_cams, sizeof(rta::DevCam) * RTA_MAX_CAMS) != cudaSuccess ||
+        cudaMalloc(&c->d_status, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&c->d_counters, sizeof(unsigned int) * N_COUNTERS) != cudaSuccess) {
+        rta_destroy(c);
+        return fail(RTA_E_NOMEM, "context allocation failed");
+    }
+    cudaMemset(c->d_cams, 0, sizeof(rta::DevCam) * RTA_MAX_CAMS);
+    cudaMemset(c->d_status, 0, sizeof(unsigned int));
+    cudaMemset(c->d_counters, 0, sizeof(unsigned int) * N_COUNTERS);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        rta_destroy(c);
+        return fail(RTA_E_CUDA, "device initialisation failed");
+    }
+    *out = c;
+    return RTA_OK;
+}
+
+int rta_destroy(rta_ctx* c) {
+    if (!c) return RTA_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& h : c->cams) {
+        cudaFree(h.d_xy);
+        cudaFree(h.d_nb);
+    }
+    for (auto& s : c->slot) {
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.meta_done) cudaEventDestroy(s.meta_done);
+        cudaFree(s.d_wave); cudaFree(s.d_off); cudaFree(s.d_tel); cudaFree(s.d_evt); cudaFree(s.d_h); cudaFree(s.d_s);
+        cudaFreeHost(s.h_off); cudaFreeHost(s.h_evt);
+    }
+    cudaFree(c->d_cams); cudaFree(c->d_tel_cam); cudaFree(c->d_tel_xy); cudaFree(c->d_tel_row);
+    cudaFree(c->d_p16); cudaFree(c->d_scale); cudaFree(c->d_status); cudaFree(c->d_counters);
+    delete c;
+    return RTA_OK;
+}
+
+int rta_register_camera(rta_ctx* c, int cam, int n_pix, int n_samples, const float* h_pix_xy, const int16_t* h_nb,
+                        int K) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (cam < 0 || cam >= RTA_MAX_CAMS) return fail(RTA_E_INVALID, "camera id %d outside 0..%d", cam, RTA_MAX_CAMS - 1);
+    if (n_pix < 1 || n_pix > RTA_MAX_PIX) return fail(RTA_E_INVALID, "n_pix %d outside 1..%d", n_pix, RTA_MAX_PIX);
+    if (n_samples < 1 || n_samples > RTA_MAX_SAMPLES)
+        return fail(RTA_E_INVALID, "n_samples %d outside 1..%d", n_samples, RTA_MAX_SAMPLES);
+    if ((int64_t(n_pix) * n_samples) % 8 != 0)
+        return fail(RTA_E_ALIGN, "n_pix*n_samples = %d is not a multiple of 8 (16-byte image rule)", n_pix * n_samples);
+    if (K < 1 || K > RTA_NB_PAD) return fail(RTA_E_INVALID, "K = %d outside 1..%d", K, RTA_NB_PAD);
+    if (!h_pix_xy || !h_nb) return fail(RTA_E_INVALID, "pixel table is NULL");
+    std::vector<int16_t> nb(size_t(n_pix) * RTA_NB_PAD, int16_t(-1));
+    for (int p = 0; p < n_pix; ++p)
+        for (int j = 0; j < K; ++j) {
+            int v = h_nb[size_t(p) * K + j];
+            if (v < -1 || v >= n_pix || v == p) return fail(RTA_E_INVALID, "neighbour %d of pixel %d is invalid", v, p);
+            nb[size_t(p) * RTA_NB_PAD + j] = int16_t(v);
+        }
+    HostCam& h = c->cams[cam];
+    cudaFree(h.d_xy);
+    cudaFree(h.d_nb);
+    h = HostCam();
+    CUDA_TRY(cudaMalloc(&h.d_xy, sizeof(float2) * n_pix));
+    CUDA_TRY(cudaMalloc(&h.d_nb, sizeof(int4) * n_pix));
+    CUDA_TRY(cudaMemcpy(h.d_xy, h_pix_xy, sizeof(float2) * n_pix, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h.d_nb, nb.data(), sizeof(int4) * n_pix, cudaMemcpyHostToDevice));
+    h.P = n_pix;
+    h.S = n_samples;
+    h.K = K;
+    h.valid = true;
+    return refresh_cams(c);
+}
+
+int rta_register_array(rta_ctx* c, int n_tel, const int32_t* h_tel_cam, const float* h_tel_xy, const int32_t* h_p16,
+                       const float* h_scale) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n_tel < 1 || n_tel > RTA_MAX_TEL) return fail(RTA_E_INVALID, "n_tel %d outside 1..%d", n_tel, RTA_MAX_TEL);
+    if (!h_tel_cam || !h_tel_xy || !h_p16 || !h_scale) return fail(RTA_E_INVALID, "array table is NULL");
+    std::vector<int64_t> row(n_tel);
+    int64_t rows = 0, src_rows = 0;
+    for (int t = 0; t < n_tel; ++t) {
+        int cam = h_tel_cam[t];
+        if (cam < 0 || cam >= RTA_MAX_CAMS || !c->cams[cam].valid)
+            return fail(RTA_E_INVALID, "telescope %d uses unregistered camera %d", t, cam);
+        row[t] = rows;
+        rows += (c->cams[cam].P + RTA_CALIB_ALIGN - 1) / RTA_CALIB_ALIGN * RTA_CALIB_ALIGN;
+        src_rows += c->cams[cam].P;
+    }
+    rows += RTA_CALIB_ALIGN;  // slack for the 16-byte rounded tail copy
+    std::vector<int32_t> p16(rows, 0);
+    std::vector<float> scale(rows, 0.f);
+    int64_t s = 0;
+    for (int t = 0; t < n_tel; ++t) {
+        int P = c->cams[h_tel_cam[t]].P;
+        for (int p = 0; p < P; ++p) {
+            p16[row[t] + p] = h_p16[s + p];
+            scale[row[t] + p] = h_scale[s + p];
+        }
+        s += P;
+    }
+    cudaFree(c->d_tel_cam); cudaFree(c->d_tel_xy); cudaFree(c->d_tel_row); cudaFree(c->d_p16); cudaFree(c->d_scale);
+    c->d_tel_cam = nullptr; c->d_tel_xy = nullptr; c->d_tel_row = nullptr; c->d_p16 = nullptr; c->d_scale = nullptr;
+    c->n_tel = 0;
+    CUDA_TRY(cudaMalloc(&c->d_tel_cam, sizeof(int32_t) * n_tel));
+    CUDA_TRY(cudaMalloc(&c->d_tel_xy, sizeof(float2) * n_tel));
+    CUDA_TRY(cudaMalloc(&c->d_tel_row, sizeof(int64_t) * n_tel));
+    CUDA_TRY(cudaMalloc(&c->d_p16, sizeof(int32_t) * rows));
+    CUDA_TRY(cudaMalloc(&c->d_scale, sizeof(float) * rows));
+    CUDA_TRY(cudaMemcpy(c->d_tel_cam, h_tel_cam, sizeof(int32_t) * n_tel, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_tel_xy, h_tel_xy, sizeof(float2) * n_tel, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_tel_row, row.data(), sizeof(int64_t) * n_tel, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_p16, p16.data(), sizeof(int32_t) * rows, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_scale, scale.data(), sizeof(float) * rows, cudaMemcpyHostToDevice));
+    c->tel_cam.assign(h_tel_cam, h_tel_cam + n_tel);
+    c->n_tel = n_tel;
+    (void)src_rows;
+    return RTA_OK;
+}
+
+int rta_check(rta_ctx* c, void* stream, uint32_t* status_bits) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(c->d_status, 0, sizeof st));
+    if (status_bits) *status_bits = st;
+    if (st) return fail(RTA_E_DEVICE, "device status 0x%x (bit0 skipped image, bit1 wait timeout)", st);
+    return RTA_OK;
+}
+
+int rta_set_chain_config(rta_ctx* c, int n_stages, int ctas_per_sm) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n_stages < 2 || n_stages > 8) return fail(RTA_E_INVALID, "n_stages %d outside 2..8", n_stages);
+    if (ctas_per_sm < 0 || ctas_per_sm > 8) return fail(RTA_E_INVALID, "ctas_per_sm %d outside 0..8", ctas_per_sm);
+    size_t smem = rta::chain_smem_bytes(n_stages, c->stage_wave_bytes, c->max_P);
+    if (rta::chain_occupancy(smem) < std::max(1, ctas_per_sm))
+        return fail(RTA_E_INVALID, "%d stages x %d CTAs/SM does not fit in shared memory", n_stages, ctas_per_sm);
+    c->nstage = n_stages;
+    c->ctas_per_sm = ctas_per_sm;
+    return RTA_OK;
+}
+
+int rta_get_chain_config(rta_ctx* c, int* n_stages, int* ctas_per_sm, int* grid, size_t* smem_bytes) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    int g;
+    size_t sm;
+    rc = chain_launch_config(c, int64_t(1) << 30, &g, &sm);
+    if (rc) return rc;
+    if (n_stages) *n_stages = c->nstage;
+    if (ctas_per_sm) *ctas_per_sm = g / c->n_sm;
+    if (grid) *grid = g;
+    if (smem_bytes) *smem_bytes = sm;
+    return RTA_OK;
+}
+
+int rta_calibrate_integrate(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                            const int32_t* d_img_tel, const int64_t* d_pix_off, int64_t n_img, int window_mode,
+                            int start, int W, float* d_q, float* d_t, int64_t n_q, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, false, 0.f, 0.f))) return rc;
+    if (n_img == 0) return RTA_OK;
+    if (!d_wave || !d_wave_off || !d_img_tel || !d_pix_off || !d_q) return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, 0, 0.f, 0.f};
+    if (n_wave < 0 || n_q < 0) return fail(RTA_E_INVALID, "negative buffer length");
+    return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, pp, d_q, d_t, n_q, nullptr, 1,
+                     (cudaStream_t)stream, nullptr);
+}
+
+int rta_clean(rta_ctx* c, const float* d_q, int64_t n_q, const int32_t* d_img_tel, const int64_t* d_pix_off,
+              int64_t n_img, float t_hi, float t_lo, int core_needs_neighbour, uint8_t* d_mask, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img"))) return rc;
+    if (!(t_hi >= t_lo && t_lo > 0.f)) return fail(RTA_E_INVALID, "tailcut thresholds need t_hi >= t_lo > 0");
+    if (n_img == 0) return RTA_OK;
+    if (!d_q || !d_img_tel || !d_pix_off || !d_mask) return fail(RTA_E_INVALID, "NULL device pointer");
+    rta::CleanArgs a;
+    a.arr = dev_array(c);
+    a.pp = rta::ProcParams{0, 0, 1, core_needs_neighbour ? 1 : 0, t_hi, t_lo};
+    a.q = d_q;
+    a.n_q = n_q;
+    a.img_tel = d_img_tel;
+    a.pix_off = d_pix_off;
+    a.n_img = n_img;
+    a.mask = d_mask;
+    a.status = c->d_status;
+    int grid = int(std::min<int64_t>(n_img, int64_t(c->n_sm) * 8));
+    CUDA_TRY(rta::launch_clean(a, grid, (cudaStream_t)stream));
+    return RTA_OK;
+}
+
+int rta_hillas(rta_ctx* c, const float* d_q, const float* d_t, const uint8_t* d_mask, int64_t n_q,
+               const int32_t* d_img_tel, const int64_t* d_pix_off, int64_t n_img, rta_hillas_t* d_out, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img"))) return rc;
+    if (n_img == 0) return RTA_OK;
+    if (!d_q || !d_mask || !d_img_tel || !d_pix_off || !d_out) return fail(RTA_E_INVALID, "NULL device pointer");
+    rta::HillasArgs a;
+    a.arr = dev_array(c);
+    a.q = d_q;
+    a.t = d_t;
+    a.mask = d_mask;
+    a.n_q = n_q;
+    a.img_tel = d_img_tel;
+    a.pix_off = d_pix_off;
+    a.n_img = n_img;
+    a.out = d_out;
+    a.status = c->d_status;
+    int grid = int(std::min<int64_t>(n_img, int64_t(c->n_sm) * 8));
+    CUDA_TRY(rta::launch_hillas(a, grid, (cudaStream_t)stream));
+    return RTA_OK;
+}
+
+int rta_image_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                    const int32_t* d_img_tel, int64_t n_img, int window_mode, int start, int W, float t_hi,
+                    float t_lo, int core_needs_neighbour, rta_hillas_t* d_out, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (n_img == 0) return RTA_OK;
+    if (!d_wave || !d_wave_off || !d_img_tel || !d_out) return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo};
+    if (n_wave < 0) return fail(RTA_E_INVALID, "negative buffer length");
+    return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out, 0,
+                     (cudaStream_t)stream, nullptr);
+}
+
+int rta_stereo(rta_ctx* c, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+               const int32_t* d_evt_off, int64_t n_evt, rta_stereo_t* d_out, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_evt, "n_evt")) || (rc = check_n(n_img, "n_img"))) return rc;
+    if (n_evt == 0) return RTA_OK;
+    if (!d_evt_off || !d_out || (n_img > 0 && (!d_hillas || !d_img_tel))) return fail(RTA_E_INVALID, "NULL device pointer");
+    return run_stereo(c, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_out, (cudaStream_t)stream);
+}
+
+int rta_reconstruct(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                    const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off, int64_t n_evt, int window_mode,
+                    int start, int W, float t_hi, float t_lo, int core_needs_neighbour, rta_hillas_t* d_hillas,
+                    rta_stereo_t* d_stereo, void* stream) {
+    int rc = rta_image_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
+                             core_needs_neighbour, d_hillas, stream);
+    if (rc) return rc;
+    return rta_stereo(c, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_stereo, stream);
+}
+
+int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, const int64_t* h_wave_off,
+                         const int32_t* h_img_tel, int64_t n_img, const int32_t* h_evt_off, int64_t n_evt,
+                         int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                         rta_hillas_t* h_hillas, rta_stereo_t* h_stereo) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img")) || (rc = check_n(n_evt, "n_evt"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (n_evt == 0) return RTA_OK;
+    if (!h_wave || !h_wave_off || !h_img_tel || !h_evt_off || !h_hillas || !h_stereo)
+        return fail(RTA_E_INVALID, "NULL host pointer");
+    if (h_evt_off[0] != 0 || h_evt_off[n_evt] != n_img) return fail(RTA_E_INVALID, "evt_off must run from 0 to n_img");
+    // image byte extents from the host tables
+    std::vector<int64_t> img_end(static_cast<size_t>(n_img));
+    for (int64_t i = 0; i < n_img; ++i) {
+        const int tel = h_img_tel[i];
+        if (tel < 0 || tel >= c->n_tel) return fail(RTA_E_INVALID, "image %lld has telescope id %d", (long long)i, tel);
+        const HostCam& h = c->cams[c->tel_cam[tel]];
+        if (h_wave_off[i] < 0 || (h_wave_off[i] & 7)) return fail(RTA_E_ALIGN, "image %lld offset not a multiple of 8", (long long)i);
+        if (i && h_wave_off[i] < img_end[i - 1]) return fail(RTA_E_INVALID, "image offsets must be increasing and non-overlapping");
+        img_end[i] = h_wave_off[i] + int64_t(h.P) * h.S;
+        if (img_end[i] > n_wave) return fail(RTA_E_INVALID, "image %lld ends past n_wave", (long long)i);
+    }
+    for (int64_t e = 0; e < n_evt; ++e)
+        if (h_evt_off[e + 1] < h_evt_off[e]) return fail(RTA_E_INVALID, "evt_off must be non-decreasing");
+    std::lock_guard<std::mutex> lock(c->host_mu);
+    // chunk plan: whole events, at most `cap` waveform samples per chunk
+    const size_t cap_bytes = std::max<size_t>(size_t(64) << 20, std::min<size_t>(c->budget / 2, size_t(512) << 20));
+    const int64_t cap = int64_t(cap_bytes / 2);
+    struct Chunk { int64_t e0, e1; };
+    std::vector<Chunk> chunks;
+    int64_t max_img = 0, max_evt = 0;
+    for (int64_t e = 0; e < n_evt;) {
+        int64_t e1 = e;
+        const int64_t i0 = h_evt_off[e];
+        while (e1 < n_evt) {
+            const int64_t i1 = h_evt_off[e1 + 1];
+            if (i1 > i0 && img_end[i1 - 1] - h_wave_off[i0] > cap && e1 > e) break;
+            ++e1;
+        }
+        const int64_t i1 = h_evt_off[e1];
+        if (i1 > i0 && img_end[i1 - 1] - h_wave_off[i0] > cap)
+            return fail(RTA_E_NOMEM, "one event needs more than the %zu-byte staging buffer", cap_bytes);
+        chunks.push_back({e, e1});
+        max_img = std::max(max_img, i1 - i0);
+        max_evt = std::max(max_evt, e1 - e);
+        e = e1;
+    }
+    // staging buffers (grown on demand, bounded by the budget)
+    for (auto& s : c->slot) {
+        if (!s.stream) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&s.meta_done, cudaEventDisableTiming));
+        }
+        if (s.wave_cap < size_t(cap) * 2) {
+            if (c->staged_bytes + size_t(cap) * 2 > c->budget) return fail(RTA_E_NOMEM, "staging exceeds the HBM budget");
+            cudaFree(s.d_wave);
+            s.d_wave = nullptr;
+            CUDA_TRY(cudaMalloc(&s.d_wave, size_t(cap) * 2));
+            s.wave_cap = size_t(cap) * 2;
+            c->staged_bytes += s.wave_cap;
+        }
+        if (s.img_cap < size_t(max_img) || s.evt_cap < size_t(max_evt) + 1) {
+            cudaFree(s.d_off); cudaFree(s.d_tel); cudaFree(s.d_evt); cudaFree(s.d_h); cudaFree(s.d_s);
+            cudaFreeHost(s.h_off); cudaFreeHost(s.h_evt);
+            s.img_cap = size_t(max_img) + 1024;
+            s.evt_cap = size_t(max_evt) + 1024;
+            CUDA_TRY(cudaMalloc(&s.d_off, sizeof(int64_t) * s.img_cap));
+            CUDA_TRY(cudaMalloc(&s.d_tel, sizeof(int32_t) * s.img_cap));
+            CUDA_TRY(cudaMalloc(&s.d_evt, sizeof(int32_t) * s.evt_cap));
+            CUDA_TRY(cudaMalloc(&s.d_h, sizeof(rta_hillas_t) * s.img_cap));
+            CUDA_TRY(cudaMalloc(&s.d_s, sizeof(rta_stereo_t) * s.evt_cap));
+            CUDA_TRY(cudaMallocHost(&s.h_off, sizeof(int64_t) * s.img_cap));
+            CUDA_TRY(cudaMallocHost(&s.h_evt, sizeof(int32_t) * s.evt_cap));
+        }
+    }
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo};
+    for (size_t k = 0; k < chunks.size(); ++k) {
+        Slot& s = c->slot[k & 1];
+        const int64_t e0 = chunks[k].e0, e1 = chunks[k].e1;
+        const int64_t i0 = h_evt_off[e0], i1 = h_evt_off[e1];
+        const int64_t ni = i1 - i0, ne = e1 - e0;
+        // the pinned metadata of this slot may still feed the copy issued two chunks ago
+        CUDA_TRY(cudaEventSynchronize(s.meta_done));
+        const int64_t base = ni ? h_wave_off[i0] : 0;
+        for (int64_t i = 0; i < ni; ++i) s.h_off[i] = h_wave_off[i0 + i] - base;
+        for (int64_t e = 0; e <= ne; ++e) s.h_evt[e] = int32_t(h_evt_off[e0 + e] - i0);
+        if (ni) {
+            const size_t bytes = size_t(img_end[i1 - 1] - base) * 2;
+            CUDA_TRY(cudaMemcpyAsync(s.d_wave, h_wave + base, bytes, cudaMemcpyHostToDevice, s.stream));
+            CUDA_TRY(cudaMemcpyAsync(s.d_off, s.h_off, sizeof(int64_t) * ni, cudaMemcpyHostToDevice, s.stream));
+            CUDA_TRY(cudaMemcpyAsync(s.d_tel, h_img_tel + i0, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s.stream));
+        }
+        CUDA_TRY(cudaMemcpyAsync(s.d_evt, s.h_evt, sizeof(int32_t) * (ne + 1), cudaMemcpyHostToDevice, s.stream));
+        CUDA_TRY(cudaEventRecord(s.meta_done, s.stream));
+        if (ni) {
+            rc = run_chain(c, s.d_wave, int64_t(s.wave_cap / 2), s.d_off, s.d_tel, nullptr, ni, pp, nullptr, nullptr,
+                           0, s.d_h, 0, s.stream, c->d_counters + N_COUNTERS - 1 - (k & 1));
+            if (rc) return rc;
+            CUDA_TRY(cudaMemcpyAsync(h_hillas + i0, s.d_h, sizeof(rta_hillas_t) * ni, cudaMemcpyDeviceToHost, s.stream));
+        }
+        rc = run_stereo(c, s.d_h, s.d_tel, ni, s.d_evt, ne, s.d_s, s.stream);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemcpyAsync(h_stereo + e0, s.d_s, sizeof(rta_stereo_t) * ne, cudaMemcpyDeviceToHost, s.stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->slot[0].stream));
+    CUDA_TRY(cudaStreamSynchronize(c->slot[1].stream));
+    return RTA_OK;
+}
+
+}  // extern "C"

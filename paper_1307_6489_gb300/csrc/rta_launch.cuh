@@ -1,0 +1,74 @@
+// Launch-argument blocks of the librta kernels and their host-side launchers.
+#pragma once
+
+#include "rta_device.cuh"
+
+namespace rta {
+
+struct ChainArgs {
+    DevArray arr;
+    ProcParams pp;
+    const uint16_t* wave;
+    int64_t n_wave;          // samples in wave
+    const int64_t* wave_off;
+    const int32_t* img_tel;
+    const int64_t* pix_off;  // integrate-only mode
+    int64_t n_q;             // rows of q_out / t_out
+    int64_t n_img;
+    float* q_out;            // integrate-only mode
+    float* t_out;
+    rta_hillas_t* out;       // full mode
+    unsigned int* counter;   // zeroed before the launch
+    unsigned int* status;
+    int stage_wave_bytes;    // multiple of 128
+    int nstage;
+    int integrate_only;
+};
+
+struct CleanArgs {
+    DevArray arr;
+    ProcParams pp;
+    const float* q;
+    int64_t n_q;
+    const int32_t* img_tel;
+    const int64_t* pix_off;
+    int64_t n_img;
+    uint8_t* mask;
+    unsigned int* status;
+};
+
+struct HillasArgs {
+    DevArray arr;
+    const float* q;
+    const float* t;
+    const uint8_t* mask;
+    int64_t n_q;
+    const int32_t* img_tel;
+    const int64_t* pix_off;
+    int64_t n_img;
+    rta_hillas_t* out;
+    unsigned int* status;
+};
+
+struct StereoArgs {
+    DevArray arr;
+    const rta_hillas_t* h;
+    const int32_t* img_tel;
+    int64_t n_img;
+    const int32_t* evt_off;
+    int64_t n_evt;
+    rta_stereo_t* out;
+    unsigned int* status;
+};
+
+size_t chain_smem_bytes(int nstage, int stage_wave_bytes, int max_P);
+int chain_threads();
+int chain_max_chunk_pix();
+int chain_occupancy(size_t smem);
+int stereo_events_per_block();
+cudaError_t launch_image_chain(const ChainArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_stereo(const StereoArgs& a, int grid, cudaStream_t s);
+
+}  // namespace rta
