@@ -200,7 +200,12 @@ __device__ __forceinline__ void clean_image(const float* q, uint8_t* fl, const D
 }
 
 // Hillas parameters from the masked pixels (fl bit2). acc holds the per-thread
-// first-moment partials of clean_image. Thread 0 writes the row.
+// first-moment partials of clean_image. Pass 2 gives the central second moments
+// and psi; pass 3 projects every pixel on the principal axes, so that
+// length^2 = sum q l^2 / size and width^2 = sum q w^2 / size. These equal lambda1
+// and det/lambda1 of the covariance, but stay well conditioned in FP32 for
+// nearly collinear images, where det is a small difference of large products.
+// Thread 0 writes the row.
 template <class Bar>
 __device__ __forceinline__ void hillas_image(const float* q, const float* t, const uint8_t* fl, const DevCam& C,
                                              float (&acc)[4], float* red, int tid, int nthr, Bar bar,
@@ -232,41 +237,35 @@ __device__ __forceinline__ void hillas_image(const float* q, const float* t, con
         }
     }
     block_reduce<4>(b, red + NCW * 8 * 2, tid, nthr, bar);
-    const float sxx = __fdiv_rn(b[0], size), syy = __fdiv_rn(b[1], size), sxy = __fdiv_rn(b[2], size);
-    const float hd = 0.5f * (sxx - syy);
-    const float lam1 = 0.5f * (sxx + syy) + sqrtf(hd * hd + sxy * sxy);
-    const float det = diff_of_products(sxx, syy, sxy, sxy);
-    const float length = lam1 > 0.f ? sqrtf(lam1) : 0.f;
-    const float width = lam1 > 0.f ? sqrtf(fmaxf(det, 0.f) / lam1) : 0.f;
-    const float psi = 0.5f * atan2f(2.f * sxy, sxx - syy);
+    const float psi = 0.5f * atan2f(2.f * b[2], b[0] - b[1]);
     const float tmean = t ? __fdiv_rn(b[3], size) : 0.f;
-    float grad = 0.f;
-    uint32_t flags = 0;
-    if (t && n >= 2) {
-        float sp, cp;
-        sincosf(psi, &sp, &cp);
-        float c[2] = {0.f, 0.f};
-        for (int p = tid; p < P; p += nthr) {
-            if (fl[p] & 4) {
-                const float qp = q[p];
-                const float2 xy = __ldg(C.xy + p);
-                const float l = (xy.x - cx) * cp + (xy.y - cy) * sp;
-                c[0] += qp * l * l;
-                c[1] += qp * l * (t[p] - tmean);
-            }
+    float sp, cp;
+    sincosf(psi, &sp, &cp);
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p = tid; p < P; p += nthr) {
+        if (fl[p] & 4) {
+            const float qp = q[p];
+            const float2 xy = __ldg(C.xy + p);
+            const float dx = xy.x - cx, dy = xy.y - cy;
+            const float l = dx * cp + dy * sp;
+            const float w = dy * cp - dx * sp;
+            c[0] += qp * l * l;
+            c[1] += qp * w * w;
+            if (t) c[2] += qp * l * (t[p] - tmean);
         }
-        block_reduce<2>(c, red + NCW * 8 * 1, tid, nthr, bar);
-        grad = c[0] > 0.f ? __fdiv_rn(c[1], c[0]) : 0.f;
-    } else {
-        flags |= RTA_HF_NO_TIME;
     }
+    block_reduce<4>(c, red + NCW * 8 * 1, tid, nthr, bar);
+    uint32_t flags = 0;
+    float grad = 0.f;
+    if (t && n >= 2) grad = c[0] > 0.f ? __fdiv_rn(c[2], c[0]) : 0.f;
+    else flags |= RTA_HF_NO_TIME;
     if (tid == 0) {
         rta_hillas_t h;
         h.size = size;
         h.x = cx;
         h.y = cy;
-        h.length = length;
-        h.width = width;
+        h.length = sqrtf(__fdiv_rn(c[0], size));
+        h.width = sqrtf(__fdiv_rn(c[1], size));
         h.psi = psi;
         h.r = sqrtf(cx * cx + cy * cy);
         h.phi = atan2f(cy, cx);

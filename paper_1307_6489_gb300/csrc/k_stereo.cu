@@ -7,7 +7,11 @@
 //   w * p = F * (|s| * c_i + sign(s) * cross(c_j - c_i, u_j) * u_i),
 // with F = s_i s_j / (s_i + s_j) (1 - W_i/L_i)(1 - W_j/L_j) and s = cross(u_i, u_j),
 // which is the same quantity as |s| F * (c_i + u_i cross / s) but stays well
-// conditioned for nearly parallel axes.
+// conditioned for nearly parallel axes. The pair arithmetic is FP64: when every
+// pair of an event is nearly parallel, the result is a ratio of two small sums
+// and FP32 rounding of the axis directions alone would move it by far more
+// than the rounding of the inputs. The work is a few hundred pairs per event,
+// far below the image kernel's cost.
 #include "rta_launch.cuh"
 
 namespace rta {
@@ -16,16 +20,15 @@ constexpr int ST_WARPS = 8;
 
 
 struct StereoImg {
-    float x, y, c, s, f, tx, ty;  // f = size factor * shape factor, 0 if unused
+    double x, y, c, s, f, tx, ty, size;  // f = 1 - W/L, 0 if unused
     int used;
+    int pad;
 };
 
 __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
     __shared__ StereoImg sh[ST_WARPS][RTA_STEREO_MAX_M];
-    __shared__ float ssize[ST_WARPS][RTA_STEREO_MAX_M];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     StereoImg* im = sh[warp];
-    float* sz = ssize[warp];
     for (int64_t e = int64_t(blockIdx.x) * ST_WARPS + warp; e < a.n_evt; e += int64_t(gridDim.x) * ST_WARPS) {
         const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
         if (i0 < 0 || i1 < i0 || i1 > a.n_img) {            // malformed CSR: flag, never index
@@ -46,39 +49,38 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
             const bool used = tel_ok && hh.n_pix >= 3 && !(hh.flags & (RTA_HF_EMPTY | RTA_HF_BAD_INPUT));
             if (!tel_ok) atomicOr(a.status, RTA_DEV_BAD_IMAGE);
             StereoImg v;
-            float sp, cp;
-            sincosf(hh.psi, &sp, &cp);
+            double sp = 0.0, cp = 1.0;
+            if (used) sincos(double(hh.psi), &sp, &cp);
             v.x = hh.x;
             v.y = hh.y;
             v.c = cp;
             v.s = sp;
-            v.f = used ? (1.f - __fdiv_rn(hh.width, hh.length)) : 0.f;
+            v.f = used ? 1.0 - double(hh.width) / double(hh.length) : 0.0;
             const float2 t = tel_ok ? a.arr.tel_xy[tel] : make_float2(0.f, 0.f);
             v.tx = t.x;
             v.ty = t.y;
+            v.size = hh.size;
             v.used = used;
+            v.pad = 0;
             im[k] = v;
-            sz[k] = hh.size;
             nvalid_lane += used;
         }
         __syncwarp();
-        float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         int npair = 0;
         for (int i = 0; i < m; ++i) {
+            if (!im[i].used) continue;
             const StereoImg A = im[i];
-            if (!A.used) continue;
-            const float sa = sz[i];
             for (int j = i + 1 + lane; j < m; j += 32) {
                 const StereoImg B = im[j];
                 if (!B.used) continue;
-                const float s = A.c * B.s - A.s * B.c;   // sin(psi_j - psi_i)
-                if (fabsf(s) < 1e-6f) continue;
-                const float sb = sz[j];
-                const float F = __fdiv_rn(sa * sb, sa + sb) * A.f * B.f;
-                const float as = fabsf(s);
-                const float sg = s > 0.f ? 1.f : -1.f;
-                const float cr = (B.x - A.x) * B.s - (B.y - A.y) * B.c;      // cross(c_j - c_i, u_j)
-                const float crg = (B.tx - A.tx) * B.s - (B.ty - A.ty) * B.c;
+                const double s = A.c * B.s - A.s * B.c;   // sin(psi_j - psi_i)
+                if (fabs(s) < 1e-6) continue;
+                const double F = A.size * B.size / (A.size + B.size) * A.f * B.f;
+                const double as = fabs(s);
+                const double sg = s > 0.0 ? 1.0 : -1.0;
+                const double cr = (B.x - A.x) * B.s - (B.y - A.y) * B.c;      // cross(c_j - c_i, u_j)
+                const double crg = (B.tx - A.tx) * B.s - (B.ty - A.ty) * B.c;
                 acc[0] += F * as;
                 acc[1] += F * (as * A.x + sg * cr * A.c);
                 acc[2] += F * (as * A.y + sg * cr * A.s);
@@ -88,7 +90,9 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
             }
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) acc[k] = warp_sum(acc[k]);
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             npair += __shfl_xor_sync(0xffffffffu, npair, o);
@@ -97,11 +101,11 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
         if (lane == 0) {
             rta_stereo_t r = {};
             r.n_valid = nvalid_lane;
-            if (npair > 0 && acc[0] > 0.f) {
-                r.dir_x = __fdiv_rn(acc[1], acc[0]);
-                r.dir_y = __fdiv_rn(acc[2], acc[0]);
-                r.core_x = __fdiv_rn(acc[3], acc[0]);
-                r.core_y = __fdiv_rn(acc[4], acc[0]);
+            if (npair > 0 && acc[0] > 0.0) {
+                r.dir_x = float(acc[1] / acc[0]);
+                r.dir_y = float(acc[2] / acc[0]);
+                r.core_x = float(acc[3] / acc[0]);
+                r.core_y = float(acc[4] / acc[0]);
             } else {
                 r.flags = RTA_SF_INVALID;
             }
