@@ -70,27 +70,42 @@ __device__ __forceinline__ int sample(const uint32_t (&w)[(S + 1) / 2], int k) {
     return (k & 1) ? int(w[k >> 1] >> 16) : int(w[k >> 1] & 0xFFFFu);
 }
 
-// Window of maximal integer sum, lowest start on ties: the key sum*128 + (127-k)
-// orders by sum first and, among equal sums, prefers the smaller start k.
-template <int S, int W>
-__device__ __forceinline__ void sliding_best_T(const uint16_t* row, int& best_sum, int& best_start) {
-    uint32_t w[(S + 1) / 2];
-    load_row<S>(row, w);
-    int s = 0;
+// Pairwise maximum over a compile-time array (a tree: no serial dependency chain).
+template <int N>
+__device__ __forceinline__ int tree_max(int (&v)[N]) {
 #pragma unroll
-    for (int k = 0; k < W; ++k) s += sample<S>(w, k);
-    int key = s * 128 + 127;
+    for (int step = 1; step < N; step *= 2)
 #pragma unroll
-    for (int k = 1; k + W <= S; ++k) {
-        s += sample<S>(w, k + W - 1) - sample<S>(w, k - 1);
-        key = max(key, s * 128 + (127 - k));
-    }
-    best_sum = key >> 7;
-    best_start = 127 - (key & 127);
+        for (int i = 0; i + step < N; i += 2 * step) v[i] = max(v[i], v[i + step]);
+    return v[0];
 }
 
-__device__ __forceinline__ void sliding_best_generic(const uint16_t* row, int S, int W, int& best_sum,
-                                                     int& best_start) {
+// Window of maximal integer sum, lowest start on ties. Every window start k gets
+// the key sum*128 + (127 - k): keys order by sum first and, among equal sums,
+// prefer the smaller start. All window sums are independent of each other (built
+// from pair sums), so the search has no serial dependency chain.
+template <int S, int W>
+__device__ __forceinline__ int best_key_T(const uint16_t* row) {
+    static_assert(W == 5 || W == 6, "specialised widths");
+    constexpr int NK = S - W + 1;
+    uint32_t w[(S + 1) / 2];
+    load_row<S>(row, w);
+    int x[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) x[k] = sample<S>(w, k);
+    int p2[S - 1];
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) p2[k] = x[k] + x[k + 1];
+    int key[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int sum = (W == 6) ? p2[k] + p2[k + 2] + p2[k + 4] : p2[k] + p2[k + 2] + x[k + 4];
+        key[k] = sum * 128 + (127 - k);
+    }
+    return tree_max(key);
+}
+
+__device__ __forceinline__ int best_key_generic(const uint16_t* row, int S, int W) {
     int s = 0;
     for (int k = 0; k < W; ++k) s += row[k];
     int key = s * 128 + 127;
@@ -98,36 +113,50 @@ __device__ __forceinline__ void sliding_best_generic(const uint16_t* row, int S,
         s += int(row[k + W - 1]) - int(row[k - 1]);
         key = max(key, s * 128 + (127 - k));
     }
-    best_sum = key >> 7;
-    best_start = 127 - (key & 127);
+    return key;
 }
 
-// q and t of one pixel whose S samples start at `row` (shared memory).
-__device__ __forceinline__ void integrate_pixel(const uint16_t* row, int S, const ProcParams& pp, int p16,
-                                                float scale, float& q, float& t) {
+// Window start and integer sum of one pixel whose S samples start at `row` (shared memory).
+__device__ __forceinline__ void window_sum(const uint16_t* row, int S, const ProcParams& pp, int& sum, int& st) {
     const int W = pp.W;
-    int sum, st;
     if (pp.sliding) {
-        if (S == 40 && W == 6) sliding_best_T<40, 6>(row, sum, st);
-        else if (S == 30 && W == 6) sliding_best_T<30, 6>(row, sum, st);
-        else if (S == 25 && W == 6) sliding_best_T<25, 6>(row, sum, st);
-        else if (S == 16 && W == 5) sliding_best_T<16, 5>(row, sum, st);
-        else sliding_best_generic(row, S, W, sum, st);
+        int key;
+        if (S == 40 && W == 6) key = best_key_T<40, 6>(row);
+        else if (S == 30 && W == 6) key = best_key_T<30, 6>(row);
+        else if (S == 25 && W == 6) key = best_key_T<25, 6>(row);
+        else if (S == 16 && W == 5) key = best_key_T<16, 5>(row);
+        else key = best_key_generic(row, S, W);
+        sum = key >> 7;
+        st = 127 - (key & 127);
     } else {
         st = pp.start;
         sum = 0;
         for (int k = 0; k < W; ++k) sum += row[st + k];
     }
+}
+
+// The calibrated charge: exact integer numerator, one FP32 multiply (never fused).
+__device__ __forceinline__ float charge(int sum, int W, int p16, float scale, int& num) {
+    num = 16 * sum - W * p16;
+    return __fmul_rn(__int2float_rn(num), scale);
+}
+
+// Pedestal-subtracted sample centroid of the chosen window.
+__device__ __forceinline__ float peak_time(const uint16_t* row, int st, int W, int p16, int num) {
     int sj = 0;
     for (int j = 1; j < W; ++j) sj += j * int(row[st + j]);
-    const int num = 16 * sum - W * p16;
     const int numt = 16 * sj - p16 * (W * (W - 1) / 2);
-    q = __fmul_rn(__int2float_rn(num), scale);
-    t = num > 0 ? __fadd_rn(float(st), __fdiv_rn(__int2float_rn(numt), __int2float_rn(num)))
-                : float(st) + 0.5f * float(W - 1);
+    return num > 0 ? __fadd_rn(float(st), __fdiv_rn(__int2float_rn(numt), __int2float_rn(num)))
+                   : float(st) + 0.5f * float(W - 1);
 }
 
 // ------------------------------------------------------------------ cleaning + Hillas
+// Per-image pixel sets are bitmaps of 32-pixel words (word w holds pixels
+// 32w..32w+31): hi = {q >= t_hi}, lo = {q >= t_lo}, core, mask. Cleaning and the
+// moment sums visit only the set bits, so pixels below t_lo cost nothing after
+// integration. Thread w owns word w and visits its bits in increasing order, and
+// partial sums are combined by a fixed tree: the summation order depends only on
+// the camera, never on the data or on the rest of the batch.
 struct NamedBar {
     __device__ __forceinline__ void operator()() const { named_bar_sync(1, NCT); }
 };
@@ -135,8 +164,17 @@ struct BlockBar {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
+struct ImgBits {
+    uint32_t* hi;
+    uint32_t* lo;
+    uint32_t* core;
+    uint32_t* mask;
+};
+
+__device__ __forceinline__ int words_of(int P) { return (P + 31) >> 5; }
+
 // Reduce N floats over `nthr` threads (nthr/32 warps): warp shuffle tree, then a
-// fixed-order sum over warps. The order never depends on the data or the batch.
+// fixed-order sum over warps.
 template <int N, class Bar>
 __device__ __forceinline__ void block_reduce(float (&v)[N], float* red, int tid, int nthr, Bar bar) {
     const int lane = tid & 31, warp = tid >> 5;
@@ -155,65 +193,74 @@ __device__ __forceinline__ void block_reduce(float (&v)[N], float* red, int tid,
     }
 }
 
-__device__ __forceinline__ bool any_neighbour(const int4 nbr, int K, const uint8_t* fl, uint8_t bit) {
+__device__ __forceinline__ bool bit_of(const uint32_t* bits, int id) { return (bits[id >> 5] >> (id & 31)) & 1u; }
+
+__device__ __forceinline__ bool any_neighbour(const int4 nbr, int K, const uint32_t* bits) {
     const int16_t* n = reinterpret_cast<const int16_t*>(&nbr);
     bool any = false;
 #pragma unroll
     for (int j = 0; j < RTA_NB_PAD; ++j) {
         const int id = n[j];
-        if (j < K && id >= 0 && (fl[id] & bit)) any = true;
+        if (j < K && id >= 0 && bit_of(bits, id)) any = true;
     }
     return any;
 }
 
-// Tailcut flags in fl[p]: bit0 q >= t_hi, bit1 core, bit2 in the cleaned mask.
-// Returns via acc (per thread): n, sum q, sum q x, sum q y over masked pixels.
+// Tailcut cleaning on the bitmaps: core = hi (with a hi neighbour if asked),
+// mask = core | (lo with a core neighbour). Needs hi and lo filled.
 template <class Bar>
-__device__ __forceinline__ void clean_image(const float* q, uint8_t* fl, const DevCam& C, const ProcParams& pp,
-                                            int tid, int nthr, Bar bar, float (&acc)[4]) {
-    const int P = C.P;
-    for (int p = tid; p < P; p += nthr) fl[p] = q[p] >= pp.t_hi ? 1 : 0;
-    bar();
-    for (int p = tid; p < P; p += nthr) {
-        const uint8_t f = fl[p];
-        if (f & 1) {
-            const bool ok = pp.core_nb ? any_neighbour(__ldg(C.nb + p), C.K, fl, 1) : true;
-            if (ok) fl[p] = f | 2;
+__device__ __forceinline__ void clean_bits(const DevCam& C, const ProcParams& pp, const ImgBits& b, int tid,
+                                           int nthr, Bar bar) {
+    const int nw = words_of(C.P);
+    for (int w = tid; w < nw; w += nthr) {
+        const uint32_t hb = b.hi[w];
+        uint32_t cb = hb;
+        if (pp.core_nb) {
+            cb = 0;
+            for (uint32_t m = hb; m; m &= m - 1) {
+                const int bit = __ffs(m) - 1;
+                if (any_neighbour(__ldg(C.nb + (w * 32 + bit)), C.K, b.hi)) cb |= 1u << bit;
+            }
         }
+        b.core[w] = cb;
     }
     bar();
-    acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
-    for (int p = tid; p < P; p += nthr) {
-        const uint8_t f = fl[p];
-        const float qp = q[p];
-        bool m = (f & 2) != 0;
-        if (!m && qp >= pp.t_lo) m = any_neighbour(__ldg(C.nb + p), C.K, fl, 2);
-        if (m) {
-            fl[p] = f | 4;
-            const float2 xy = __ldg(C.xy + p);
-            acc[0] += 1.f;
-            acc[1] += qp;
-            acc[2] += qp * xy.x;
-            acc[3] += qp * xy.y;
+    for (int w = tid; w < nw; w += nthr) {
+        const uint32_t cb = b.core[w];
+        uint32_t mb = cb;
+        for (uint32_t m = b.lo[w] & ~cb; m; m &= m - 1) {
+            const int bit = __ffs(m) - 1;
+            if (any_neighbour(__ldg(C.nb + (w * 32 + bit)), C.K, b.core)) mb |= 1u << bit;
         }
+        b.mask[w] = mb;
     }
+    bar();
 }
 
-// Hillas parameters from the masked pixels (fl bit2). acc holds the per-thread
-// first-moment partials of clean_image. Pass 2 gives the central second moments
-// and psi; pass 3 projects every pixel on the principal axes, so that
-// length^2 = sum q l^2 / size and width^2 = sum q w^2 / size. These equal lambda1
-// and det/lambda1 of the covariance, but stay well conditioned in FP32 for
-// nearly collinear images, where det is a small difference of large products.
-// Thread 0 writes the row.
+// Hillas parameters of the pixels in b.mask. Pass 1: size and centroid; pass 2:
+// central second moments and psi; pass 3: projections on the principal axes,
+// length^2 = sum q l^2 / size and width^2 = sum q w^2 / size, and the time
+// gradient. These equal lambda1 and det/lambda1 of the covariance, but stay well
+// conditioned in FP32 for nearly collinear images, where det is a small
+// difference of large products. Thread 0 writes the row.
 template <class Bar>
-__device__ __forceinline__ void hillas_image(const float* q, const float* t, const uint8_t* fl, const DevCam& C,
-                                             float (&acc)[4], float* red, int tid, int nthr, Bar bar,
-                                             rta_hillas_t* out) {
-    const int P = C.P;
-    block_reduce<4>(acc, red, tid, nthr, bar);
-    const int n = int(acc[0]);
-    const float size = acc[1];
+__device__ __forceinline__ void hillas_bits(const float* q, const float* t, const DevCam& C, const uint32_t* mask,
+                                            float* red, int tid, int nthr, Bar bar, rta_hillas_t* out) {
+    const int nw = words_of(C.P);
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int w = tid; w < nw; w += nthr)
+        for (uint32_t m = mask[w]; m; m &= m - 1) {
+            const int p = w * 32 + __ffs(m) - 1;
+            const float qp = q[p];
+            const float2 xy = __ldg(C.xy + p);
+            a[0] += 1.f;
+            a[1] += qp;
+            a[2] += qp * xy.x;
+            a[3] += qp * xy.y;
+        }
+    block_reduce<4>(a, red, tid, nthr, bar);
+    const int n = int(a[0]);
+    const float size = a[1];
     if (n == 0 || !(size > 0.f)) {
         if (tid == 0) {
             rta_hillas_t h = {};
@@ -223,10 +270,11 @@ __device__ __forceinline__ void hillas_image(const float* q, const float* t, con
         }
         return;
     }
-    const float cx = __fdiv_rn(acc[2], size), cy = __fdiv_rn(acc[3], size);
+    const float cx = __fdiv_rn(a[2], size), cy = __fdiv_rn(a[3], size);
     float b[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int p = tid; p < P; p += nthr) {
-        if (fl[p] & 4) {
+    for (int w = tid; w < nw; w += nthr)
+        for (uint32_t m = mask[w]; m; m &= m - 1) {
+            const int p = w * 32 + __ffs(m) - 1;
             const float qp = q[p];
             const float2 xy = __ldg(C.xy + p);
             const float dx = xy.x - cx, dy = xy.y - cy;
@@ -235,25 +283,24 @@ __device__ __forceinline__ void hillas_image(const float* q, const float* t, con
             b[2] += qp * dx * dy;
             if (t) b[3] += qp * t[p];
         }
-    }
     block_reduce<4>(b, red + NCW * 8 * 2, tid, nthr, bar);
     const float psi = 0.5f * atan2f(2.f * b[2], b[0] - b[1]);
     const float tmean = t ? __fdiv_rn(b[3], size) : 0.f;
     float sp, cp;
     sincosf(psi, &sp, &cp);
     float c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int p = tid; p < P; p += nthr) {
-        if (fl[p] & 4) {
+    for (int w = tid; w < nw; w += nthr)
+        for (uint32_t m = mask[w]; m; m &= m - 1) {
+            const int p = w * 32 + __ffs(m) - 1;
             const float qp = q[p];
             const float2 xy = __ldg(C.xy + p);
             const float dx = xy.x - cx, dy = xy.y - cy;
             const float l = dx * cp + dy * sp;
-            const float w = dy * cp - dx * sp;
+            const float wd = dy * cp - dx * sp;
             c[0] += qp * l * l;
-            c[1] += qp * w * w;
+            c[1] += qp * wd * wd;
             if (t) c[2] += qp * l * (t[p] - tmean);
         }
-    }
     block_reduce<4>(c, red + NCW * 8 * 1, tid, nthr, bar);
     uint32_t flags = 0;
     float grad = 0.f;
@@ -294,7 +341,7 @@ struct ChainSmem {
     float red[3 * NCW * 8];
 };
 
-__global__ void __launch_bounds__(CHAIN_THREADS) k_image_chain(const ChainArgs a) {
+__global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ChainSmem& sm = *reinterpret_cast<ChainSmem*>(smem_raw);
     const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
@@ -304,7 +351,9 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_image_chain(const ChainArgs a
     unsigned char* stages = smem_raw + head;
     float* sq = reinterpret_cast<float*>(stages + size_t(NST) * stage_bytes);
     float* st = sq + a.arr.max_P;
-    uint8_t* fl = reinterpret_cast<uint8_t*>(st + a.arr.max_P);
+    const int maxw = words_of(a.arr.max_P);
+    uint32_t* bits0 = reinterpret_cast<uint32_t*>(st + a.arr.max_P);
+    const ImgBits ib = {bits0, bits0 + maxw, bits0 + 2 * maxw, bits0 + 3 * maxw};
     volatile int* abort_flag = &sm.abort;
 
     const int tid = threadIdx.x;
@@ -440,19 +489,32 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_image_chain(const ChainArgs a
             continue;
         }
         const unsigned char* buf = stages + size_t(stage) * stage_bytes;
+        bool hi = false, lo = false;
         if (ct < h.npix) {
             const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(ct) * h.S;
             const int p16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes)[ct];
             const float sc = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes)[ct];
-            float q, t;
-            integrate_pixel(row, h.S, pp, p16, sc, q, t);
+            int sum, wst, num;
+            window_sum(row, h.S, pp, sum, wst);
+            const float q = charge(sum, pp.W, p16, sc, num);
             const int p = h.base + ct;
             if (a.integrate_only) {
                 a.q_out[h.pix_off + p] = q;
-                if (a.t_out) a.t_out[h.pix_off + p] = t;
+                if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, pp.W, p16, num);
             } else {
                 sq[p] = q;
-                st[p] = t;
+                hi = q >= pp.t_hi;
+                lo = q >= pp.t_lo;
+                // only pixels that can survive cleaning need their time
+                if (lo) st[p] = peak_time(row, wst, pp.W, p16, num);
+            }
+        }
+        if (!a.integrate_only) {
+            const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
+            const int word = (h.base >> 5) + (ct >> 5);
+            if (lane == 0 && word < words_of(h.P)) {
+                ib.hi[word] = bh;
+                ib.lo[word] = bl;
             }
         }
         __syncwarp();
@@ -461,19 +523,36 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_image_chain(const ChainArgs a
         if ((h.flags & HDR_LAST) && !a.integrate_only) {
             named_bar_sync(1, NCT);
             const DevCam C = a.arr.cams[h.cam];
-            float acc[4];
-            clean_image(sq, fl, C, pp, ct, NCT, NamedBar(), acc);
-            hillas_image(sq, st, fl, C, acc, sm.red, ct, NCT, NamedBar(), a.out + h.img);
+            clean_bits(C, pp, ib, ct, NCT, NamedBar());
+            hillas_bits(sq, st, C, ib.mask, sm.red, ct, NCT, NamedBar(), a.out + h.img);
         }
     }
 }
 
 // ------------------------------------------------------------------ unfused stage kernels
 
+// Bitmaps of one image from per-pixel values in global memory: the warp that
+// covers 32 consecutive pixels writes their word.
+__device__ __forceinline__ void ballot_words(int P, int tid, int nthr, uint32_t* w0, uint32_t* w1, const float* q,
+                                             float t0, float t1) {
+    for (int base = 0; base < P; base += nthr) {
+        const int p = base + tid;
+        const float v = p < P ? q[p] : 0.f;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, p < P && v >= t0);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, p < P && v >= t1);
+        if ((tid & 31) == 0 && (p >> 5) < words_of(P)) {
+            w0[p >> 5] = b0;
+            if (w1) w1[p >> 5] = b1;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_clean(const CleanArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* sq = reinterpret_cast<float*>(smem_raw);
-    uint8_t* fl = reinterpret_cast<uint8_t*>(sq + a.arr.max_P);
+    const int maxw = words_of(a.arr.max_P);
+    uint32_t* bits0 = reinterpret_cast<uint32_t*>(sq + a.arr.max_P);
+    const ImgBits ib = {bits0, bits0 + maxw, bits0 + 2 * maxw, bits0 + 3 * maxw};
     for (int64_t img = blockIdx.x; img < a.n_img; img += gridDim.x) {
         const int tel = a.img_tel[img];
         if (tel < 0 || tel >= a.arr.n_tel) {
@@ -488,21 +567,21 @@ __global__ void __launch_bounds__(256) k_clean(const CleanArgs a) {
         }
         for (int p = threadIdx.x; p < C.P; p += blockDim.x) sq[p] = a.q[off + p];
         __syncthreads();
-        float acc[4];
-        clean_image(sq, fl, C, a.pp, threadIdx.x, blockDim.x, BlockBar(), acc);
+        ballot_words(C.P, threadIdx.x, blockDim.x, ib.hi, ib.lo, sq, a.pp.t_hi, a.pp.t_lo);
         __syncthreads();
-        for (int p = threadIdx.x; p < C.P; p += blockDim.x) a.mask[off + p] = (fl[p] >> 2) & 1;
+        clean_bits(C, a.pp, ib, threadIdx.x, blockDim.x, BlockBar());
+        for (int p = threadIdx.x; p < C.P; p += blockDim.x) a.mask[off + p] = bit_of(ib.mask, p) ? 1 : 0;
         __syncthreads();
     }
 }
-
 
 __global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ float red[3 * NCW * 8];
     float* sq = reinterpret_cast<float*>(smem_raw);
     float* st = sq + a.arr.max_P;
-    uint8_t* fl = reinterpret_cast<uint8_t*>(st + a.arr.max_P);
+    float* sm = st + a.arr.max_P;
+    uint32_t* mask = reinterpret_cast<uint32_t*>(sm + a.arr.max_P);
     for (int64_t img = blockIdx.x; img < a.n_img; img += gridDim.x) {
         const int tel = a.img_tel[img];
         if (tel < 0 || tel >= a.arr.n_tel) {
@@ -521,23 +600,15 @@ __global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
             }
             continue;
         }
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int p = threadIdx.x; p < C.P; p += blockDim.x) {
-            const float qp = a.q[off + p];
-            const uint8_t m = a.mask[off + p] ? 4 : 0;
-            sq[p] = qp;
+            sq[p] = a.q[off + p];
             if (a.t) st[p] = a.t[off + p];
-            fl[p] = m;
-            if (m) {
-                const float2 xy = __ldg(C.xy + p);
-                acc[0] += 1.f;
-                acc[1] += qp;
-                acc[2] += qp * xy.x;
-                acc[3] += qp * xy.y;
-            }
+            sm[p] = a.mask[off + p] ? 1.f : 0.f;
         }
         __syncthreads();
-        hillas_image(sq, a.t ? st : nullptr, fl, C, acc, red, threadIdx.x, blockDim.x, BlockBar(), a.out + img);
+        ballot_words(C.P, threadIdx.x, blockDim.x, mask, nullptr, sm, 0.5f, 0.5f);
+        __syncthreads();
+        hillas_bits(sq, a.t ? st : nullptr, C, mask, red, threadIdx.x, blockDim.x, BlockBar(), a.out + img);
         __syncthreads();
     }
 }
@@ -545,7 +616,8 @@ __global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
 // ------------------------------------------------------------------ host-side launchers
 size_t chain_smem_bytes(int nstage, int stage_wave_bytes, int max_P) {
     const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
-    return head + size_t(nstage) * (stage_wave_bytes + 2 * NCT * 4) + size_t(max_P) * 9 + 16;
+    return head + size_t(nstage) * (stage_wave_bytes + 2 * NCT * 4) + size_t(max_P) * 8 +
+           size_t(16) * ((max_P + 31) / 32) + 16;
 }
 
 int chain_threads() { return CHAIN_THREADS; }
@@ -573,13 +645,13 @@ int chain_occupancy(size_t smem) {
 }
 
 cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s) {
-    const size_t smem = size_t(a.arr.max_P) * 5 + 16;
+    const size_t smem = size_t(a.arr.max_P) * 4 + size_t(16) * ((a.arr.max_P + 31) / 32) + 16;
     k_clean<<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s) {
-    const size_t smem = size_t(a.arr.max_P) * 9 + 16;
+    const size_t smem = size_t(a.arr.max_P) * 12 + size_t(4) * ((a.arr.max_P + 31) / 32) + 16;
     k_hillas<<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -122,7 +122,7 @@ int refresh_cams(rta_ctx* c) {
     for (int i = 0; i < RTA_MAX_CAMS; ++i) {
         const HostCam& h = c->cams[i];
         if (!h.valid) continue;
-        int cp = ((swb - 16) / (2 * h.S)) & ~7;
+        int cp = ((swb - 16) / (2 * h.S)) & ~31;   // a multiple of 32: chunks start on bitmap words
         cp = std::min(cp, nct);
         dc[i].P = h.P;
         dc[i].S = h.S;
