@@ -23,7 +23,7 @@ namespace rta {
 
 constexpr int NCW = 8;             // consumer warps
 constexpr int NCT = NCW * 32;      // consumer threads = largest chunk in pixels
-constexpr int CHAIN_THREADS = NCT + 32;
+constexpr int CHAIN_THREADS = NCT + 64;   // producer warp + integrators + tail warp
 constexpr int MAX_STAGES = 8;
 
 enum { HDR_LAST = 1, HDR_BAD = 2, HDR_END = 4 };
@@ -163,6 +163,9 @@ struct NamedBar {
 struct BlockBar {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
+struct WarpBar {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
 
 struct ImgBits {
     uint32_t* hi;
@@ -180,6 +183,7 @@ __device__ __forceinline__ void block_reduce(float (&v)[N], float* red, int tid,
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+    if (nthr == 32) return;   // one warp: every lane already holds the totals
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < N; ++k) red[warp * 8 + k] = v[k];
@@ -332,14 +336,38 @@ __device__ __forceinline__ void write_bad_row(rta_hillas_t* out) {
 }
 
 // ------------------------------------------------------------------ the fused persistent kernel
+// Warp roles: warp 0 producer, warps 1..NCW integrators, warp NCW+1 the tail
+// warp. Integrated images go through two shared-memory slots (q, t and the hi/lo
+// bitmaps of one image each): the integrators fill one slot while the tail warp
+// cleans and parameterises the other, so cleaning and moments never stall the
+// integration of the next image.
+constexpr int NSLOT = 2;
+enum { SLOT_END = 1 };
+
+struct SlotHdr {
+    int img, cam, flags, pad;
+};
+
 struct ChainSmem {
     uint64_t full[MAX_STAGES];
     uint64_t empty[MAX_STAGES];
+    uint64_t slot_full[NSLOT];
+    uint64_t slot_free[NSLOT];
     StageHdr hdr[MAX_STAGES];
+    SlotHdr shdr[NSLOT];
     int abort;
     int pad[31];
     float red[3 * NCW * 8];
 };
+
+struct SlotView {
+    float* q;
+    float* t;
+    uint32_t* hi;
+    uint32_t* lo;
+};
+
+__device__ __forceinline__ size_t slot_bytes(int max_P) { return size_t(max_P) * 8 + size_t(8) * words_of(max_P); }
 
 __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -349,11 +377,20 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
     const int calib_bytes = NCT * 4;
     const int stage_bytes = a.stage_wave_bytes + 2 * calib_bytes;
     unsigned char* stages = smem_raw + head;
-    float* sq = reinterpret_cast<float*>(stages + size_t(NST) * stage_bytes);
-    float* st = sq + a.arr.max_P;
-    const int maxw = words_of(a.arr.max_P);
-    uint32_t* bits0 = reinterpret_cast<uint32_t*>(st + a.arr.max_P);
-    const ImgBits ib = {bits0, bits0 + maxw, bits0 + 2 * maxw, bits0 + 3 * maxw};
+    const int maxP = a.arr.max_P;
+    const int maxw = words_of(maxP);
+    unsigned char* slots = stages + size_t(NST) * stage_bytes;
+    auto slot_view = [&](int s) {
+        unsigned char* b = slots + size_t(s) * slot_bytes(maxP);
+        SlotView v;
+        v.q = reinterpret_cast<float*>(b);
+        v.t = v.q + maxP;
+        v.hi = reinterpret_cast<uint32_t*>(v.t + maxP);
+        v.lo = v.hi + maxw;
+        return v;
+    };
+    uint32_t* core = reinterpret_cast<uint32_t*>(slots + NSLOT * slot_bytes(maxP));
+    uint32_t* maskb = core + maxw;
     volatile int* abort_flag = &sm.abort;
 
     const int tid = threadIdx.x;
@@ -361,6 +398,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
         for (int s = 0; s < NST; ++s) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], NCW);
+        }
+        for (int s = 0; s < NSLOT; ++s) {
+            mbar_init(&sm.slot_full[s], NCW);
+            mbar_init(&sm.slot_free[s], 1);
         }
         sm.abort = 0;
         fence_mbar_init();
@@ -464,20 +505,48 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
         return;
     }
 
-    // ---------------- consumer warps
-    const int ct = tid - 32;          // 0 .. NCT-1
     const int lane = tid & 31;
-    int stage = 0;
-    uint32_t phase = 0;
     const ProcParams pp = a.pp;
+    auto give_up = [&]() {
+        if (!*abort_flag) atomicOr(a.status, RTA_DEV_TIMEOUT);
+        *abort_flag = 1;
+    };
+
+    if (tid >= 32 + NCT) {
+        // ---------------- tail warp: cleaning + Hillas of integrated images
+        int slot = 0;
+        uint32_t ph = 0;
+        for (;;) {
+            if (!mbar_wait(&sm.slot_full[slot], ph, abort_flag)) { give_up(); break; }
+            const SlotHdr sh = sm.shdr[slot];
+            if (sh.flags & SLOT_END) break;
+            const SlotView v = slot_view(slot);
+            const DevCam C = a.arr.cams[sh.cam];
+            const ImgBits ib = {v.hi, v.lo, core, maskb};
+            clean_bits(C, pp, ib, lane, 32, WarpBar());
+            hillas_bits(v.q, v.t, C, maskb, sm.red, lane, 32, WarpBar(), a.out + sh.img);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.slot_free[slot]);
+            if (++slot == NSLOT) { slot = 0; ph ^= 1u; }
+        }
+        return;
+    }
+
+    // ---------------- integrator warps
+    const int ct = tid - 32;          // 0 .. NCT-1
+    int stage = 0, slot = 0;
+    uint32_t phase = 0, sphase = 0;
     for (;;) {
-        if (!mbar_wait(&sm.full[stage], phase, abort_flag)) {
-            if (!*abort_flag) atomicOr(a.status, RTA_DEV_TIMEOUT);
-            *abort_flag = 1;
+        if (!mbar_wait(&sm.full[stage], phase, abort_flag)) { give_up(); break; }
+        const StageHdr h = sm.hdr[stage];
+        if (h.flags & HDR_END) {
+            // tell the tail warp there is nothing more
+            if (!mbar_wait(&sm.slot_free[slot], sphase ^ 1u, abort_flag)) { give_up(); break; }
+            if (ct == 0) sm.shdr[slot].flags = SLOT_END;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.slot_full[slot]);
             break;
         }
-        const StageHdr h = sm.hdr[stage];
-        if (h.flags & HDR_END) break;
         if (h.flags & HDR_BAD) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[stage]);
@@ -488,6 +557,11 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
             if (++stage == NST) { stage = 0; phase ^= 1u; }
             continue;
         }
+        if (h.base == 0 && !a.integrate_only) {
+            // the slot must be free: the tail warp is done with the image two back
+            if (!mbar_wait(&sm.slot_free[slot], sphase ^ 1u, abort_flag)) { give_up(); break; }
+        }
+        const SlotView v = slot_view(slot);
         const unsigned char* buf = stages + size_t(stage) * stage_bytes;
         bool hi = false, lo = false;
         if (ct < h.npix) {
@@ -502,29 +576,36 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
                 a.q_out[h.pix_off + p] = q;
                 if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, pp.W, p16, num);
             } else {
-                sq[p] = q;
+                v.q[p] = q;
                 hi = q >= pp.t_hi;
                 lo = q >= pp.t_lo;
                 // only pixels that can survive cleaning need their time
-                if (lo) st[p] = peak_time(row, wst, pp.W, p16, num);
+                if (lo) v.t[p] = peak_time(row, wst, pp.W, p16, num);
             }
         }
         if (!a.integrate_only) {
             const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
             const int word = (h.base >> 5) + (ct >> 5);
             if (lane == 0 && word < words_of(h.P)) {
-                ib.hi[word] = bh;
-                ib.lo[word] = bl;
+                v.hi[word] = bh;
+                v.lo[word] = bl;
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == NST) { stage = 0; phase ^= 1u; }
         if ((h.flags & HDR_LAST) && !a.integrate_only) {
-            named_bar_sync(1, NCT);
-            const DevCam C = a.arr.cams[h.cam];
-            clean_bits(C, pp, ib, ct, NCT, NamedBar());
-            hillas_bits(sq, st, C, ib.mask, sm.red, ct, NCT, NamedBar(), a.out + h.img);
+            if (ct == 0) {
+                SlotHdr sh;
+                sh.img = h.img;
+                sh.cam = h.cam;
+                sh.flags = 0;
+                sh.pad = 0;
+                sm.shdr[slot] = sh;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.slot_full[slot]);
+            if (++slot == NSLOT) { slot = 0; sphase ^= 1u; }
         }
     }
 }
@@ -616,8 +697,9 @@ __global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
 // ------------------------------------------------------------------ host-side launchers
 size_t chain_smem_bytes(int nstage, int stage_wave_bytes, int max_P) {
     const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
-    return head + size_t(nstage) * (stage_wave_bytes + 2 * NCT * 4) + size_t(max_P) * 8 +
-           size_t(16) * ((max_P + 31) / 32) + 16;
+    const size_t words = (max_P + 31) / 32;
+    return head + size_t(nstage) * (stage_wave_bytes + 2 * NCT * 4) + NSLOT * (size_t(max_P) * 8 + 8 * words) +
+           8 * words + 16;
 }
 
 int chain_threads() { return CHAIN_THREADS; }

@@ -77,7 +77,7 @@ struct rta_ctx {
     unsigned int* d_counters = nullptr;
     std::atomic<unsigned> next_counter{0};
     // launch configuration of the fused image kernel
-    int nstage = 4;
+    int nstage = 3;
     int ctas_per_sm = 0;  // 0 = as many as fit
     int stage_wave_bytes = 0;
     int max_P = 0, max_S = 0;

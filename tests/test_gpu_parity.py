@@ -85,21 +85,23 @@ def test_image_chain_fused(setup):
     assert (g["n_pix"] > 0).mean() > 0.5
 
 
-@pytest.mark.parametrize("n_stages,ctas", [(2, 1), (3, 0), (4, 2), (6, 1), (8, 1)])
+@pytest.mark.parametrize("n_stages,ctas", [(2, 1), (2, 2), (3, 0), (4, 1), (6, 1), (8, 1)])
 def test_image_chain_every_pipeline_depth_is_identical(setup, n_stages, ctas):
     name, wl, ref, ctx, dev = setup
     mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    default = ctx.chain_config()
     base = dev.hillas_buf()
-    ctx.set_chain_config(4, 0)
     ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, base)
     try:
         ctx.set_chain_config(n_stages, ctas)
     except Exception as e:
         pytest.skip(f"configuration does not fit: {e}")
     out = dev.hillas_buf()
-    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, out)
-    assert ctx.check() == 0
-    ctx.set_chain_config(4, 0)
+    try:
+        ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, out)
+        assert ctx.check() == 0
+    finally:
+        ctx.set_chain_config(default["n_stages"], 0)
     assert torch.equal(out, base)
 
 
