@@ -85,7 +85,7 @@ __device__ __forceinline__ int tree_max(int (&v)[N]) {
 // prefer the smaller start. All window sums are independent of each other (built
 // from pair sums), so the search has no serial dependency chain.
 template <int S, int W>
-__device__ __forceinline__ int best_key_T(const uint16_t* row) {
+__device__ __forceinline__ int best_key_T(const uint16_t* row, int one, int k128) {
     static_assert(W == 5 || W == 6, "specialised widths");
     constexpr int NK = S - W + 1;
     uint32_t w[(S + 1) / 2];
@@ -95,12 +95,12 @@ __device__ __forceinline__ int best_key_T(const uint16_t* row) {
     for (int k = 0; k < S; ++k) x[k] = sample<S>(w, k);
     int p2[S - 1];
 #pragma unroll
-    for (int k = 0; k < S - 1; ++k) p2[k] = x[k] + x[k + 1];
+    for (int k = 0; k < S - 1; ++k) p2[k] = x[k] * one + x[k + 1];          // IMAD: FMA pipe
     int key[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         const int sum = (W == 6) ? p2[k] + p2[k + 2] + p2[k + 4] : p2[k] + p2[k + 2] + x[k + 4];
-        key[k] = sum * 128 + (127 - k);
+        key[k] = sum * k128 + (127 - k);                                     // IMAD: FMA pipe
     }
     return tree_max(key);
 }
@@ -121,10 +121,10 @@ __device__ __forceinline__ void window_sum(const uint16_t* row, int S, const Pro
     const int W = pp.W;
     if (pp.sliding) {
         int key;
-        if (S == 40 && W == 6) key = best_key_T<40, 6>(row);
-        else if (S == 30 && W == 6) key = best_key_T<30, 6>(row);
-        else if (S == 25 && W == 6) key = best_key_T<25, 6>(row);
-        else if (S == 16 && W == 5) key = best_key_T<16, 5>(row);
+        if (S == 40 && W == 6) key = best_key_T<40, 6>(row, pp.one, pp.k128);
+        else if (S == 30 && W == 6) key = best_key_T<30, 6>(row, pp.one, pp.k128);
+        else if (S == 25 && W == 6) key = best_key_T<25, 6>(row, pp.one, pp.k128);
+        else if (S == 16 && W == 5) key = best_key_T<16, 5>(row, pp.one, pp.k128);
         else key = best_key_generic(row, S, W);
         sum = key >> 7;
         st = 127 - (key & 127);

@@ -419,7 +419,7 @@ int rta_calibrate_integrate(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, 
     if (n_img == 0) return RTA_OK;
     if (!d_wave || !d_wave_off || !d_img_tel || !d_pix_off || !d_q) return fail(RTA_E_INVALID, "NULL device pointer");
     if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, 0, 0.f, 0.f};
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, 0, 0.f, 0.f, 1, 128};
     if (n_wave < 0 || n_q < 0) return fail(RTA_E_INVALID, "negative buffer length");
     return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, pp, d_q, d_t, n_q, nullptr, 1,
                      (cudaStream_t)stream, nullptr);
@@ -434,7 +434,7 @@ int rta_clean(rta_ctx* c, const float* d_q, int64_t n_q, const int32_t* d_img_te
     if (!d_q || !d_img_tel || !d_pix_off || !d_mask) return fail(RTA_E_INVALID, "NULL device pointer");
     rta::CleanArgs a;
     a.arr = dev_array(c);
-    a.pp = rta::ProcParams{0, 0, 1, core_needs_neighbour ? 1 : 0, t_hi, t_lo};
+    a.pp = rta::ProcParams{0, 0, 1, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
     a.q = d_q;
     a.n_q = n_q;
     a.img_tel = d_img_tel;
@@ -478,7 +478,7 @@ int rta_image_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const in
     if (n_img == 0) return RTA_OK;
     if (!d_wave || !d_wave_off || !d_img_tel || !d_out) return fail(RTA_E_INVALID, "NULL device pointer");
     if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo};
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
     if (n_wave < 0) return fail(RTA_E_INVALID, "negative buffer length");
     return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out, 0,
                      (cudaStream_t)stream, nullptr);
@@ -578,7 +578,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
             CUDA_TRY(cudaMallocHost(&s.h_evt, sizeof(int32_t) * s.evt_cap));
         }
     }
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo};
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
     for (size_t k = 0; k < chunks.size(); ++k) {
         Slot& s = c->slot[k & 1];
         const int64_t e0 = chunks[k].e0, e1 = chunks[k].e1;

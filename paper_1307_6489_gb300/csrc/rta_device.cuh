@@ -41,6 +41,10 @@ struct DevArray {
 struct ProcParams {
     int sliding, start, W, core_nb;
     float t_hi, t_lo;
+    // Runtime copies of the constants 1 and 128. Integer multiply-adds by a value
+    // the compiler cannot see run on the FMA pipe, so part of the window search
+    // leaves the integer ALU pipe, which it would otherwise saturate.
+    int one, k128;
 };
 
 // ------------------------------------------------------------------ PTX helpers
