@@ -152,15 +152,38 @@ int rta_register_array(rta_ctx* ctx, int n_tel, const int32_t* h_tel_cam, const 
 int rta_check(rta_ctx* ctx, void* stream, uint32_t* status_bits);
 
 /* Launch configuration of the fused image kernel (rta_image_chain and the
- * calls built on it): n_stages shared-memory pipeline stages (2..8) and at most
- * ctas_per_sm resident CTAs per SM (0 = as many as fit). Returns RTA_E_INVALID
- * if the combination does not fit in shared memory. The autotuner of the
- * Python binding sweeps these two values. */
-int rta_set_chain_config(rta_ctx* ctx, int n_stages, int ctas_per_sm);
+ * calls built on it). variant selects the tile shape (rta_chain_variant_info:
+ * integrator warps per CTA and pixels per thread), n_stages the shared-memory
+ * pipeline depth (2..8), ctas_per_sm the resident CTAs per SM (0 = as many as
+ * fit). Returns RTA_E_INVALID if the combination does not fit in shared memory
+ * for the registered cameras. Results do not depend on the configuration. */
+int rta_set_chain_config(rta_ctx* ctx, int variant, int n_stages, int ctas_per_sm);
 
-/* The configuration a launch would use now: stages, CTAs per SM, grid size and
- * dynamic shared memory per CTA in bytes (NULL outputs are skipped). */
-int rta_get_chain_config(rta_ctx* ctx, int* n_stages, int* ctas_per_sm, int* grid, size_t* smem_bytes);
+/* The configuration a launch would use now: variant, stages, CTAs per SM, grid
+ * size and dynamic shared memory per CTA in bytes (NULL outputs are skipped). */
+int rta_get_chain_config(rta_ctx* ctx, int* variant, int* n_stages, int* ctas_per_sm, int* grid,
+                         size_t* smem_bytes);
+
+/* Tile shape of a variant (0 .. RTA_CHAIN_VARIANTS-1). */
+#define RTA_CHAIN_VARIANTS 4
+int rta_chain_variant_info(int variant, int* integrator_warps, int* pixels_per_thread);
+
+/* One measured configuration of rta_autotune. */
+typedef struct rta_tune_entry_t {
+    int variant, n_stages, ctas_per_sm, grid;
+    float ms; /* mean duration of one rta_image_chain launch */
+} rta_tune_entry_t;
+
+/* The autotuner: runs rta_image_chain on the given device-resident bundle for
+ * every configuration that fits (variant x 2..6 stages x 1..4 CTAs/SM), `reps`
+ * timed launches each (CUDA events on `stream`), keeps the fastest in the
+ * context and reports every measurement in h_entries (up to max_entries;
+ * *n_entries = number measured). d_out receives the (configuration-independent)
+ * Hillas rows. Synchronises `stream`. */
+int rta_autotune(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                 const int32_t* d_img_tel, int64_t n_img, int window_mode, int start, int W, float t_hi,
+                 float t_lo, int core_needs_neighbour, rta_hillas_t* d_out, int reps, rta_tune_entry_t* h_entries,
+                 int max_entries, int* n_entries, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Stage calls (Sec. 4.1 calibration; Sec. 5 signal extraction)            */

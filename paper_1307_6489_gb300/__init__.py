@@ -77,8 +77,10 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_register_camera": ([P, i32, i32, i32, P, P, i32], i32),
         "rta_register_array": ([P, i32, P, P, P, P], i32),
         "rta_check": ([P, P, P], i32),
-        "rta_set_chain_config": ([P, i32, i32], i32),
-        "rta_get_chain_config": ([P, P, P, P, P], i32),
+        "rta_set_chain_config": ([P, i32, i32, i32], i32),
+        "rta_get_chain_config": ([P, P, P, P, P, P], i32),
+        "rta_chain_variant_info": ([i32, P, P], i32),
+        "rta_autotune": ([P, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32, P, i32, P, i32, P, P], i32),
         "rta_calibrate_integrate": ([P, P, i64, P, P, P, i64, i32, i32, i32, P, P, i64, P], i32),
         "rta_clean": ([P, P, i64, P, P, i64, f32, f32, i32, P, P], i32),
         "rta_hillas": ([P, P, P, P, i64, P, P, i64, P, P], i32),
@@ -170,15 +172,41 @@ def rta_check(ctx: int, stream: int = 0) -> int:
     return bits.value
 
 
-def rta_set_chain_config(ctx: int, n_stages: int, ctas_per_sm: int):
-    _check(load().rta_set_chain_config(ctx, n_stages, ctas_per_sm))
+RTA_CHAIN_VARIANTS = 4
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("n_stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("grid", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+def rta_set_chain_config(ctx: int, variant: int, n_stages: int, ctas_per_sm: int):
+    _check(load().rta_set_chain_config(ctx, variant, n_stages, ctas_per_sm))
 
 
 def rta_get_chain_config(ctx: int):
-    ns, cps, grid, smem = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
-    _check(load().rta_get_chain_config(ctx, ctypes.byref(ns), ctypes.byref(cps), ctypes.byref(grid),
+    v, ns, cps, grid, smem = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(load().rta_get_chain_config(ctx, ctypes.byref(v), ctypes.byref(ns), ctypes.byref(cps), ctypes.byref(grid),
                                        ctypes.byref(smem)))
-    return dict(n_stages=ns.value, ctas_per_sm=cps.value, grid=grid.value, smem_bytes=smem.value)
+    return dict(variant=v.value, n_stages=ns.value, ctas_per_sm=cps.value, grid=grid.value, smem_bytes=smem.value)
+
+
+def rta_chain_variant_info(variant: int):
+    w, p = ctypes.c_int(), ctypes.c_int()
+    _check(load().rta_chain_variant_info(variant, ctypes.byref(w), ctypes.byref(p)))
+    return dict(integrator_warps=w.value, pixels_per_thread=p.value)
+
+
+def rta_autotune(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
+                 core_needs_neighbour, d_out, reps=3, stream=0):
+    """Sweep the fused kernel's launch configurations on a bundle; keeps the fastest. Returns all measurements."""
+    cap = 256
+    entries = (TuneEntry * cap)()
+    n = ctypes.c_int()
+    _check(load().rta_autotune(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
+                               int(core_needs_neighbour), d_out, reps, entries, cap, ctypes.byref(n), stream))
+    return [dict(variant=e.variant, n_stages=e.n_stages, ctas_per_sm=e.ctas_per_sm, grid=e.grid, ms=e.ms)
+            for e in entries[: min(n.value, cap)]]
 
 
 def rta_calibrate_integrate(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, window_mode, start, W,
@@ -268,8 +296,14 @@ class Context:
     def check(self, stream: int = 0) -> int:
         return rta_check(self.handle, stream)
 
-    def set_chain_config(self, n_stages: int, ctas_per_sm: int):
-        rta_set_chain_config(self.handle, n_stages, ctas_per_sm)
+    def set_chain_config(self, variant: int, n_stages: int, ctas_per_sm: int):
+        rta_set_chain_config(self.handle, variant, n_stages, ctas_per_sm)
+
+    def autotune(self, wave, wave_off, img_tel, window_mode, start, W, t_hi, t_lo, core_needs_neighbour, out, reps=3,
+                 stream=None):
+        return rta_autotune(self.handle, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(),
+                            img_tel.numel(), window_mode, start, W, t_hi, t_lo, core_needs_neighbour, out.data_ptr(),
+                            reps, self._stream(stream))
 
     def chain_config(self) -> dict:
         return rta_get_chain_config(self.handle)

@@ -21,9 +21,8 @@
 
 namespace rta {
 
-constexpr int NCW = 8;             // consumer warps
-constexpr int NCT = NCW * 32;      // consumer threads = largest chunk in pixels
-constexpr int CHAIN_THREADS = NCT + 64;   // producer warp + integrators + tail warp
+constexpr int NCW = 8;             // warps of the block-wide (unfused) kernels
+constexpr int NCT = NCW * 32;
 constexpr int MAX_STAGES = 8;
 
 enum { HDR_LAST = 1, HDR_BAD = 2, HDR_END = 4 };
@@ -70,13 +69,15 @@ __device__ __forceinline__ int sample(const uint32_t (&w)[(S + 1) / 2], int k) {
     return (k & 1) ? int(w[k >> 1] >> 16) : int(w[k >> 1] & 0xFFFFu);
 }
 
-// Pairwise maximum over a compile-time array (a tree: no serial dependency chain).
+// Maximum over a compile-time array as a tree of three-input maxima (no serial
+// dependency chain, half the instructions of a pairwise tree).
 template <int N>
 __device__ __forceinline__ int tree_max(int (&v)[N]) {
 #pragma unroll
-    for (int step = 1; step < N; step *= 2)
+    for (int step = 1; step < N; step *= 3)
 #pragma unroll
-        for (int i = 0; i + step < N; i += 2 * step) v[i] = max(v[i], v[i + step]);
+        for (int i = 0; i + step < N; i += 3 * step)
+            v[i] = (i + 2 * step < N) ? __vimax3_s32(v[i], v[i + step], v[i + 2 * step]) : max(v[i], v[i + step]);
     return v[0];
 }
 
@@ -336,11 +337,13 @@ __device__ __forceinline__ void write_bad_row(rta_hillas_t* out) {
 }
 
 // ------------------------------------------------------------------ the fused persistent kernel
-// Warp roles: warp 0 producer, warps 1..NCW integrators, warp NCW+1 the tail
-// warp. Integrated images go through two shared-memory slots (q, t and the hi/lo
-// bitmaps of one image each): the integrators fill one slot while the tail warp
-// cleans and parameterises the other, so cleaning and moments never stall the
-// integration of the next image.
+// Warp roles: warp 0 producer, warps 1..IW integrators, warp IW+1 the tail warp.
+// Tile shape: IW integrator warps, each thread integrating PPT pixels of a chunk
+// of IW*32*PPT pixels (thread i takes pixels i, i + IW*32, ...), so the per-chunk
+// bookkeeping is shared by PPT pixels and each thread has PPT independent window
+// searches in flight. Integrated images go through two shared-memory slots (q, t
+// and the hi/lo bitmaps of one image each): the integrators fill one slot while
+// the tail warp cleans and parameterises the other.
 constexpr int NSLOT = 2;
 enum { SLOT_END = 1 };
 
@@ -357,7 +360,7 @@ struct ChainSmem {
     SlotHdr shdr[NSLOT];
     int abort;
     int pad[31];
-    float red[3 * NCW * 8];
+    float red[8];
 };
 
 struct SlotView {
@@ -367,14 +370,27 @@ struct SlotView {
     uint32_t* lo;
 };
 
-__device__ __forceinline__ size_t slot_bytes(int max_P) { return size_t(max_P) * 8 + size_t(8) * words_of(max_P); }
+__host__ __device__ __forceinline__ size_t slot_bytes(int max_P) {
+    return size_t(max_P) * 8 + size_t(8) * ((max_P + 31) / 32);
+}
 
-__global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArgs a) {
+// Pixels of camera S per stage: a multiple of 32 (chunks start on bitmap words)
+// that fits the stage's waveform area with 16 bytes of slack for the unaligned
+// row loads of odd sample counts.
+__host__ __device__ __forceinline__ int chunk_pixels(int chunk, int stage_wave_bytes, int S) {
+    const int cp = ((stage_wave_bytes - 16) / (2 * S)) & ~31;
+    return cp < chunk ? cp : chunk;
+}
+
+template <int IW, int PPT>
+__global__ void __launch_bounds__(IW * 32 + 64, 1) k_image_chain(const ChainArgs a) {
+    constexpr int IT = IW * 32;          // integrator threads
+    constexpr int CHUNK = IT * PPT;      // largest chunk in pixels
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ChainSmem& sm = *reinterpret_cast<ChainSmem*>(smem_raw);
     const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
     const int NST = a.nstage;
-    const int calib_bytes = NCT * 4;
+    const int calib_bytes = CHUNK * 4;
     const int stage_bytes = a.stage_wave_bytes + 2 * calib_bytes;
     unsigned char* stages = smem_raw + head;
     const int maxP = a.arr.max_P;
@@ -397,10 +413,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NCW);
+            mbar_init(&sm.empty[s], IW);
         }
         for (int s = 0; s < NSLOT; ++s) {
-            mbar_init(&sm.slot_full[s], NCW);
+            mbar_init(&sm.slot_full[s], IW);
             mbar_init(&sm.slot_free[s], 1);
         }
         sm.abort = 0;
@@ -459,7 +475,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
                 continue;
             }
             const int cam = a.arr.tel_cam[tel];
-            const int P = C.P, S = C.S, CP = C.chunk_pix;
+            const int P = C.P, S = C.S, CP = chunk_pixels(CHUNK, a.stage_wave_bytes, S);
             const int64_t row = a.arr.tel_row[tel];
             const uint16_t* src = a.wave + woff;
             for (int base = 0; base < P; base += CP) {
@@ -512,7 +528,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
         *abort_flag = 1;
     };
 
-    if (tid >= 32 + NCT) {
+    if (tid >= 32 + IT) {
         // ---------------- tail warp: cleaning + Hillas of integrated images
         int slot = 0;
         uint32_t ph = 0;
@@ -533,9 +549,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
     }
 
     // ---------------- integrator warps
-    const int ct = tid - 32;          // 0 .. NCT-1
+    const int ct = tid - 32;          // 0 .. IT-1
     int stage = 0, slot = 0;
     uint32_t phase = 0, sphase = 0;
+    SlotView v = slot_view(0);
     for (;;) {
         if (!mbar_wait(&sm.full[stage], phase, abort_flag)) { give_up(); break; }
         const StageHdr h = sm.hdr[stage];
@@ -561,34 +578,38 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
             // the slot must be free: the tail warp is done with the image two back
             if (!mbar_wait(&sm.slot_free[slot], sphase ^ 1u, abort_flag)) { give_up(); break; }
         }
-        const SlotView v = slot_view(slot);
         const unsigned char* buf = stages + size_t(stage) * stage_bytes;
-        bool hi = false, lo = false;
-        if (ct < h.npix) {
-            const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(ct) * h.S;
-            const int p16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes)[ct];
-            const float sc = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes)[ct];
-            int sum, wst, num;
-            window_sum(row, h.S, pp, sum, wst);
-            const float q = charge(sum, pp.W, p16, sc, num);
-            const int p = h.base + ct;
-            if (a.integrate_only) {
-                a.q_out[h.pix_off + p] = q;
-                if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, pp.W, p16, num);
-            } else {
-                v.q[p] = q;
-                hi = q >= pp.t_hi;
-                lo = q >= pp.t_lo;
-                // only pixels that can survive cleaning need their time
-                if (lo) v.t[p] = peak_time(row, wst, pp.W, p16, num);
+        const int32_t* cp16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes);
+        const float* cscale = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int c = ct + k * IT;    // pixel within the chunk
+            bool hi = false, lo = false;
+            if (c < h.npix) {
+                const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * h.S;
+                const int p16 = cp16[c];
+                int sum, wst, num;
+                window_sum(row, h.S, pp, sum, wst);
+                const float q = charge(sum, pp.W, p16, cscale[c], num);
+                const int p = h.base + c;
+                if (a.integrate_only) {
+                    a.q_out[h.pix_off + p] = q;
+                    if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, pp.W, p16, num);
+                } else {
+                    v.q[p] = q;
+                    hi = q >= pp.t_hi;
+                    lo = q >= pp.t_lo;
+                    // only pixels that can survive cleaning need their time
+                    if (lo) v.t[p] = peak_time(row, wst, pp.W, p16, num);
+                }
             }
-        }
-        if (!a.integrate_only) {
-            const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
-            const int word = (h.base >> 5) + (ct >> 5);
-            if (lane == 0 && word < words_of(h.P)) {
-                v.hi[word] = bh;
-                v.lo[word] = bl;
+            if (!a.integrate_only) {
+                const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
+                const int word = (h.base + c) >> 5;
+                if (lane == 0 && word < words_of(h.P)) {
+                    v.hi[word] = bh;
+                    v.lo[word] = bl;
+                }
             }
         }
         __syncwarp();
@@ -606,6 +627,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 2) k_image_chain(const ChainArg
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.slot_full[slot]);
             if (++slot == NSLOT) { slot = 0; sphase ^= 1u; }
+            v = slot_view(slot);
         }
     }
 }
@@ -695,34 +717,77 @@ __global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
 }
 
 // ------------------------------------------------------------------ host-side launchers
-size_t chain_smem_bytes(int nstage, int stage_wave_bytes, int max_P) {
-    const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
-    const size_t words = (max_P + 31) / 32;
-    return head + size_t(nstage) * (stage_wave_bytes + 2 * NCT * 4) + NSLOT * (size_t(max_P) * 8 + 8 * words) +
-           8 * words + 16;
+// Tile-shape variants of the fused kernel: (integrator warps, pixels per thread).
+struct ChainVariant {
+    int iw, ppt;
+};
+static const ChainVariant kVariants[RTA_CHAIN_VARIANTS] = {{8, 1}, {4, 2}, {8, 2}, {4, 1}};
+
+int chain_variant_warps(int v) { return kVariants[v].iw; }
+int chain_variant_ppt(int v) { return kVariants[v].ppt; }
+int chain_threads(int v) { return kVariants[v].iw * 32 + 64; }
+
+int chain_stage_wave_bytes(int v, int max_S) {
+    const int chunk = kVariants[v].iw * 32 * kVariants[v].ppt;
+    int swb = ((chunk * 2 * max_S + 16) + 127) & ~127;
+    const int cap = 48 * 1024;
+    return swb < cap ? swb : cap;
 }
 
-int chain_threads() { return CHAIN_THREADS; }
-int chain_max_chunk_pix() { return NCT; }
+size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P) {
+    const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
+    const size_t words = (max_P + 31) / 32;
+    const size_t chunk = size_t(kVariants[v].iw) * 32 * kVariants[v].ppt;
+    return head + size_t(nstage) * (stage_wave_bytes + 2 * chunk * 4) + NSLOT * slot_bytes(max_P) + 8 * words + 16;
+}
 
-cudaError_t launch_image_chain(const ChainArgs& a, int grid, size_t smem, cudaStream_t s) {
+int chain_chunk_pixels(int v, int stage_wave_bytes, int S) {
+    return chunk_pixels(kVariants[v].iw * 32 * kVariants[v].ppt, stage_wave_bytes, S);
+}
+
+template <int IW, int PPT>
+static cudaError_t launch_t(const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occupancy_only,
+                            int* occ) {
+    auto kern = k_image_chain<IW, PPT>;
     // the dynamic shared-memory opt-in is per device; remember the largest size set
     static size_t attr_bytes[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || attr_bytes[dev] < smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_image_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_bytes[dev] = smem;
     }
-    k_image_chain<<<grid, CHAIN_THREADS, smem, s>>>(a);
+    if (occupancy_only) {
+        *occ = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, IW * 32 + 64, smem);
+    }
+    kern<<<grid, IW * 32 + 64, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-int chain_occupancy(size_t smem) {
-    cudaFuncSetAttribute(k_image_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+static cudaError_t dispatch(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
+                            int* occ) {
+    switch (v) {
+    case 0: return launch_t<8, 1>(a, grid, smem, s, occ_only, occ);
+    case 1: return launch_t<4, 2>(a, grid, smem, s, occ_only, occ);
+    case 2: return launch_t<8, 2>(a, grid, smem, s, occ_only, occ);
+    case 3: return launch_t<4, 1>(a, grid, smem, s, occ_only, occ);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s) {
+    return dispatch(v, a, grid, smem, s, false, nullptr);
+}
+
+int chain_occupancy(int v, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_image_chain, CHAIN_THREADS, smem) != cudaSuccess) return 0;
+    ChainArgs dummy = {};
+    if (dispatch(v, dummy, 0, smem, nullptr, true, &n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return n;
 }
 

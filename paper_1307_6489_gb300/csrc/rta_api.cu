@@ -77,9 +77,9 @@ struct rta_ctx {
     unsigned int* d_counters = nullptr;
     std::atomic<unsigned> next_counter{0};
     // launch configuration of the fused image kernel
+    int variant = 0;      // tile shape, see chain_variant_*
     int nstage = 3;
     int ctas_per_sm = 0;  // 0 = as many as fit
-    int stage_wave_bytes = 0;
     int max_P = 0, max_S = 0;
     Slot slot[2];
     std::mutex host_mu;
@@ -106,15 +106,11 @@ unsigned int* take_counter(rta_ctx* c) {
     return c->d_counters + i;
 }
 
-// Recompute the per-stage buffer size and every camera's chunk size.
+// Upload the device camera table; the largest P and S size the kernel's buffers.
 int refresh_cams(rta_ctx* c) {
     int maxS = 1, maxP = 1;
     for (auto& h : c->cams)
         if (h.valid) { maxS = std::max(maxS, h.S); maxP = std::max(maxP, h.P); }
-    const int nct = rta::chain_max_chunk_pix();
-    int swb = ((nct * 2 * maxS + 16) + 127) & ~127;
-    swb = std::min(swb, 24576);
-    c->stage_wave_bytes = swb;
     c->max_P = maxP;
     c->max_S = maxS;
     rta::DevCam dc[RTA_MAX_CAMS];
@@ -122,12 +118,9 @@ int refresh_cams(rta_ctx* c) {
     for (int i = 0; i < RTA_MAX_CAMS; ++i) {
         const HostCam& h = c->cams[i];
         if (!h.valid) continue;
-        int cp = ((swb - 16) / (2 * h.S)) & ~31;   // a multiple of 32: chunks start on bitmap words
-        cp = std::min(cp, nct);
         dc[i].P = h.P;
         dc[i].S = h.S;
         dc[i].K = h.K;
-        dc[i].chunk_pix = cp;
         dc[i].xy = h.d_xy;
         dc[i].nb = h.d_nb;
     }
@@ -163,24 +156,39 @@ int check_proc(rta_ctx* c, int mode, int start, int W, bool need_clean, float t_
     return RTA_OK;
 }
 
-int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem) {
-    const int nst = std::max(2, std::min(c->nstage, 8));
-    *smem = rta::chain_smem_bytes(nst, c->stage_wave_bytes, c->max_P);
-    int occ = rta::chain_occupancy(*smem);
+struct ChainCfg {
+    int variant, nstage, ctas_per_sm;
+};
+
+int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_t* smem, int* swb) {
+    if (k.variant < 0 || k.variant >= RTA_CHAIN_VARIANTS) return fail(RTA_E_INVALID, "variant %d", k.variant);
+    const int nst = std::max(2, std::min(k.nstage, 8));
+    *swb = rta::chain_stage_wave_bytes(k.variant, c->max_S);
+    if (rta::chain_chunk_pixels(k.variant, *swb, c->max_S) < 32)
+        return fail(RTA_E_INVALID, "tile variant %d has no room for %d samples", k.variant, c->max_S);
+    *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P);
+    int occ = rta::chain_occupancy(k.variant, *smem);
     if (occ < 1) return fail(RTA_E_INVALID, "image kernel does not fit: %zu bytes of shared memory", *smem);
-    if (c->ctas_per_sm > 0) occ = std::min(occ, c->ctas_per_sm);
+    if (k.ctas_per_sm > 0) {
+        if (occ < k.ctas_per_sm) return fail(RTA_E_INVALID, "%d CTAs/SM do not fit (%d do)", k.ctas_per_sm, occ);
+        occ = k.ctas_per_sm;
+    }
     int64_t g = int64_t(c->n_sm) * occ;
     g = std::min<int64_t>(g, std::max<int64_t>(n_img, 1));
     *grid = int(g);
     return RTA_OK;
 }
 
+int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int* swb) {
+    return config_launch(c, ChainCfg{c->variant, c->nstage, c->ctas_per_sm}, n_img, grid, smem, swb);
+}
+
 int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
               const int64_t* d_pix_off, int64_t n_img, const rta::ProcParams& pp, float* d_q, float* d_t,
               int64_t n_q, rta_hillas_t* d_out, int integrate_only, cudaStream_t s, unsigned int* counter) {
-    int grid;
+    int grid, swb;
     size_t smem;
-    int rc = chain_launch_config(c, n_img, &grid, &smem);
+    int rc = chain_launch_config(c, n_img, &grid, &smem, &swb);
     if (rc) return rc;
     rta::ChainArgs a;
     a.arr = dev_array(c);
@@ -197,11 +205,11 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.out = d_out;
     a.counter = counter ? counter : take_counter(c);
     a.status = c->d_status;
-    a.stage_wave_bytes = c->stage_wave_bytes;
+    a.stage_wave_bytes = swb;
     a.nstage = std::max(2, std::min(c->nstage, 8));
     a.integrate_only = integrate_only;
     CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
-    CUDA_TRY(rta::launch_image_chain(a, grid, smem, s));
+    CUDA_TRY(rta::launch_image_chain(c->variant, a, grid, smem, s));
     return RTA_OK;
 }
 
@@ -383,31 +391,94 @@ int rta_check(rta_ctx* c, void* stream, uint32_t* status_bits) {
     return RTA_OK;
 }
 
-int rta_set_chain_config(rta_ctx* c, int n_stages, int ctas_per_sm) {
+int rta_set_chain_config(rta_ctx* c, int variant, int n_stages, int ctas_per_sm) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (n_stages < 2 || n_stages > 8) return fail(RTA_E_INVALID, "n_stages %d outside 2..8", n_stages);
     if (ctas_per_sm < 0 || ctas_per_sm > 8) return fail(RTA_E_INVALID, "ctas_per_sm %d outside 0..8", ctas_per_sm);
-    size_t smem = rta::chain_smem_bytes(n_stages, c->stage_wave_bytes, c->max_P);
-    if (rta::chain_occupancy(smem) < std::max(1, ctas_per_sm))
-        return fail(RTA_E_INVALID, "%d stages x %d CTAs/SM does not fit in shared memory", n_stages, ctas_per_sm);
+    int g, swb;
+    size_t sm;
+    if ((rc = config_launch(c, ChainCfg{variant, n_stages, ctas_per_sm}, int64_t(1) << 30, &g, &sm, &swb))) return rc;
+    c->variant = variant;
     c->nstage = n_stages;
     c->ctas_per_sm = ctas_per_sm;
     return RTA_OK;
 }
 
-int rta_get_chain_config(rta_ctx* c, int* n_stages, int* ctas_per_sm, int* grid, size_t* smem_bytes) {
+int rta_get_chain_config(rta_ctx* c, int* variant, int* n_stages, int* ctas_per_sm, int* grid, size_t* smem_bytes) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    int g;
+    int g, swb;
     size_t sm;
-    rc = chain_launch_config(c, int64_t(1) << 30, &g, &sm);
+    rc = chain_launch_config(c, int64_t(1) << 30, &g, &sm, &swb);
     if (rc) return rc;
+    if (variant) *variant = c->variant;
     if (n_stages) *n_stages = c->nstage;
     if (ctas_per_sm) *ctas_per_sm = g / c->n_sm;
     if (grid) *grid = g;
     if (smem_bytes) *smem_bytes = sm;
     return RTA_OK;
+}
+
+int rta_chain_variant_info(int variant, int* integrator_warps, int* pixels_per_thread) {
+    if (variant < 0 || variant >= RTA_CHAIN_VARIANTS) return fail(RTA_E_INVALID, "variant %d", variant);
+    if (integrator_warps) *integrator_warps = rta::chain_variant_warps(variant);
+    if (pixels_per_thread) *pixels_per_thread = rta::chain_variant_ppt(variant);
+    return RTA_OK;
+}
+
+int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
+                 int64_t n_img, int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                 rta_hillas_t* d_out, int reps, rta_tune_entry_t* h_entries, int max_entries, int* n_entries,
+                 void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (n_img == 0 || !d_wave || !d_wave_off || !d_img_tel || !d_out) return fail(RTA_E_INVALID, "empty or NULL bundle");
+    if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
+    if (reps < 1) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    const ChainCfg saved{c->variant, c->nstage, c->ctas_per_sm};
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    ChainCfg best = saved;
+    float best_ms = 1e30f;
+    int n = 0;
+    for (int v = 0; v < RTA_CHAIN_VARIANTS; ++v)
+        for (int nst = 2; nst <= 6; ++nst)
+            for (int cps = 1; cps <= 4; ++cps) {
+                int g, swb;
+                size_t sm;
+                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb) != RTA_OK) continue;
+                c->variant = v;
+                c->nstage = nst;
+                c->ctas_per_sm = cps;
+                rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out,
+                               0, s, nullptr);
+                if (rc) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && !rc; ++r)
+                    rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0,
+                                   d_out, 0, s, nullptr);
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(RTA_E_CUDA, "autotune run failed"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                if (h_entries && n < max_entries) h_entries[n] = rta_tune_entry_t{v, nst, cps, g, ms};
+                ++n;
+                if (ms < best_ms) { best_ms = ms; best = ChainCfg{v, nst, cps}; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->variant = rc ? saved.variant : best.variant;
+    c->nstage = rc ? saved.nstage : best.nstage;
+    c->ctas_per_sm = rc ? saved.ctas_per_sm : best.ctas_per_sm;
+    if (n_entries) *n_entries = n;
+    return rc;
 }
 
 int rta_calibrate_integrate(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,

@@ -22,7 +22,7 @@
 namespace rta {
 
 struct DevCam {
-    int P, S, K, chunk_pix;  // chunk_pix: pixels per pipeline stage for this camera
+    int P, S, K, pad;
     const float2* xy;        // P pixel centres (deg)
     const int4* nb;          // P rows of 8 int16 neighbour ids (-1 = none)
 };

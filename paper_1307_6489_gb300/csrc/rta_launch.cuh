@@ -61,12 +61,15 @@ struct StereoArgs {
     unsigned int* status;
 };
 
-size_t chain_smem_bytes(int nstage, int stage_wave_bytes, int max_P);
-int chain_threads();
-int chain_max_chunk_pix();
-int chain_occupancy(size_t smem);
+int chain_variant_warps(int v);
+int chain_variant_ppt(int v);
+int chain_threads(int v);
+int chain_stage_wave_bytes(int v, int max_S);
+size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P);
+int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
+int chain_occupancy(int v, size_t smem);
 int stereo_events_per_block();
-cudaError_t launch_image_chain(const ChainArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_stereo(const StereoArgs& a, int grid, cudaStream_t s);

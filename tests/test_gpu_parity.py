@@ -85,15 +85,16 @@ def test_image_chain_fused(setup):
     assert (g["n_pix"] > 0).mean() > 0.5
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("n_stages,ctas", [(2, 1), (2, 2), (3, 0), (4, 1), (6, 1), (8, 1)])
-def test_image_chain_every_pipeline_depth_is_identical(setup, n_stages, ctas):
+def test_image_chain_every_tile_and_pipeline_depth_is_identical(setup, variant, n_stages, ctas):
     name, wl, ref, ctx, dev = setup
     mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
     default = ctx.chain_config()
     base = dev.hillas_buf()
     ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, base)
     try:
-        ctx.set_chain_config(n_stages, ctas)
+        ctx.set_chain_config(variant, n_stages, ctas)
     except Exception as e:
         pytest.skip(f"configuration does not fit: {e}")
     out = dev.hillas_buf()
@@ -101,8 +102,20 @@ def test_image_chain_every_pipeline_depth_is_identical(setup, n_stages, ctas):
         ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, out)
         assert ctx.check() == 0
     finally:
-        ctx.set_chain_config(default["n_stages"], 0)
+        ctx.set_chain_config(default["variant"], default["n_stages"], 0)
     assert torch.equal(out, base)
+
+
+def test_autotuner_picks_a_measured_configuration(setup):
+    name, wl, ref, ctx, dev = setup
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    out = dev.hillas_buf()
+    table = ctx.autotune(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, out, reps=1)
+    assert len(table) >= 4 and all(e["ms"] > 0 for e in table)
+    best = min(table, key=lambda e: e["ms"])
+    cfg = ctx.chain_config()
+    assert (cfg["variant"], cfg["n_stages"]) == (best["variant"], best["n_stages"])
+    compare_hillas(hillas_rows(out, wl.n_img), ref["hillas"], name)
 
 
 def test_stereo_stage_isolated(setup):
