@@ -289,7 +289,7 @@ def main():
     chain_avg = statistics.mean(chain_ms)
     achieved = alg_bytes / (chain_avg / 1e3) / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    prof = os.path.join(ROOT, "profiles", "image_chain_traffic.json")
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
@@ -360,7 +360,7 @@ def _kernel_hash():
     import hashlib
     h = hashlib.sha1()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_1307_6489_gb300", "csrc"))):
-        if f.startswith("k_image") or f.endswith(".cuh"):
+        if f in ("k_image.cu", "rta_device.cuh"):
             h.update(open(os.path.join(ROOT, "paper_1307_6489_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
