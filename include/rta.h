@@ -254,6 +254,58 @@ int rta_reconstruct_host(rta_ctx* ctx, const uint16_t* h_wave, int64_t n_wave, c
                          int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
                          rta_hillas_t* h_hillas, rta_stereo_t* h_stereo);
 
+/* ---------------------------------------------------------------------- */
+/* Entry point that allocates nothing                                      */
+/* ---------------------------------------------------------------------- */
+/* The paper has no counterpart of this call; it exists for callers that may
+ * not allocate device memory: real-time processes that must not stall
+ * (cudaMalloc and cudaFree can synchronise the whole device), frameworks that
+ * own all device memory through their own pool, and code running where new
+ * allocations are not allowed. Such callers cannot use an rta_ctx, because
+ * creating and filling one allocates. */
+
+#define RTA_NOALLOC_MAX_CAMS 16   /* camera descriptors per call */
+#define RTA_NOALLOC_MAX_TEL 1024  /* telescopes per call */
+
+/* One camera type, tables in caller-owned device memory. */
+typedef struct rta_camera_desc_t {
+    int n_pix, n_samples, K;  /* as rta_register_camera; n_pix*n_samples a multiple of 8 */
+    const float* d_pix_xy;    /* 2*n_pix floats (deg), 8-byte aligned */
+    const int16_t* d_nb8;     /* n_pix rows of 8 int16 neighbour ids, -1 padded, 16-byte aligned */
+} rta_camera_desc_t;
+
+/* rta_image_chain without a context and without any allocation: the same
+ * fused kernel (calibrate + integrate + clean + Hillas, same definitions and
+ * same rows) on the current device, in its default launch configuration.
+ * The caller passes every buffer:
+ *   h_cams[n_cams]          camera descriptors; telescopes refer to them by index;
+ *   h_tel_cam[n_tel]        camera index of each telescope (host);
+ *   h_tel_row[n_tel]        first calibration row of each telescope (host): a
+ *                           multiple of 8, with at least 8 rows after its last
+ *                           pixel inside the n_calib_rows of d_p16 / d_scale;
+ *   d_p16, d_scale          the calibration table (as rta_register_array),
+ *                           16-byte aligned;
+ *   d_wave ... d_out        the bundle and the Hillas rows, as rta_image_chain;
+ *   d_status                optional (NULL = none): receives the device status
+ *                           word (RTA_DEV_* bits) when the kernel has finished.
+ * Limits: n_cams <= RTA_NOALLOC_MAX_CAMS and n_tel <= RTA_NOALLOC_MAX_TEL;
+ * larger values return RTA_E_INVALID before anything is launched.
+ * Scratch: the per-call tables, the work counter and the status word live in a
+ * fixed ~13 KiB file-scope __device__ array that every GPU which loads this
+ * library keeps until the process exits. All calls share it and it keeps the
+ * last call's contents (each call resets what must start at zero), so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. This call makes no
+ * cudaMalloc, cudaFree or other allocating call. Asynchronous on `stream`. */
+int rta_image_chain_noalloc(const rta_camera_desc_t* h_cams, int n_cams, const int32_t* h_tel_cam,
+                            const int64_t* h_tel_row, int n_tel, const int32_t* d_p16, const float* d_scale,
+                            int64_t n_calib_rows, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                            const int32_t* d_img_tel, int64_t n_img, int window_mode, int start, int W, float t_hi,
+                            float t_lo, int core_needs_neighbour, rta_hillas_t* d_out, uint32_t* d_status,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_stereo": ([P, P, P, i64, P, i64, P, P], i32),
         "rta_reconstruct": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P, P], i32),
         "rta_reconstruct_host": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P], i32),
+        "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
+                                     P, P, P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +247,32 @@ def rta_reconstruct_host(ctx, h_wave, n_wave, h_wave_off, h_img_tel, n_img, h_ev
     _check(load().rta_reconstruct_host(ctx, h_wave, n_wave, h_wave_off, h_img_tel, n_img, h_evt_off, n_evt,
                                        window_mode, start, W, t_hi, t_lo, int(core_needs_neighbour), h_hillas,
                                        h_stereo))
+
+
+RTA_NOALLOC_MAX_CAMS = 16
+RTA_NOALLOC_MAX_TEL = 1024
+
+
+class CameraDesc(ctypes.Structure):
+    """rta_camera_desc_t: one camera type whose tables live in caller-owned device memory."""
+    _fields_ = [("n_pix", ctypes.c_int), ("n_samples", ctypes.c_int), ("K", ctypes.c_int),
+                ("d_pix_xy", ctypes.c_void_p), ("d_nb8", ctypes.c_void_p)]
+
+
+def rta_image_chain_noalloc(cams, tel_cam, tel_row, d_p16, d_scale, n_calib_rows, d_wave, n_wave, d_wave_off,
+                            d_img_tel, n_img, window_mode, start, W, t_hi, t_lo, core_needs_neighbour, d_out,
+                            d_status=0, stream=0):
+    """For callers that cannot allocate device memory: the fused image kernel with
+    caller-owned buffers only (see include/rta.h). `cams` is a sequence of
+    CameraDesc (or (n_pix, n_samples, K, d_pix_xy, d_nb8) tuples)."""
+    arr = (CameraDesc * max(1, len(cams)))()
+    for i, c in enumerate(cams):
+        arr[i] = c if isinstance(c, CameraDesc) else CameraDesc(*c)
+    tc, ptc = _np(tel_cam, np.int32)
+    tr, ptr = _np(tel_row, np.int64)
+    _check(load().rta_image_chain_noalloc(arr, len(cams), ptc, ptr, len(tc), d_p16, d_scale, n_calib_rows, d_wave,
+                                          n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
+                                          int(core_needs_neighbour), d_out, d_status, stream))
 
 
 # ----------------------------------------------------------------------------- row decoding

@@ -59,6 +59,10 @@ struct Slot {  // one half of the host-path double buffer
 
 }  // namespace
 
+void rta::set_last_error(const char* msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg);
+}
+
 struct rta_ctx {
     int device = 0;
     int n_sm = 0;

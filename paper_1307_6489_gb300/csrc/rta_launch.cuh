@@ -73,5 +73,7 @@ cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem,
 cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_stereo(const StereoArgs& a, int grid, cudaStream_t s);
+// stores a message for rta_last_error() on the calling thread
+void set_last_error(const char* msg);
 
 }  // namespace rta
