@@ -283,6 +283,25 @@ def main():
     events_all = wl.n_evt * ws
     value = events_all / (ms_per_step / 1e3)
 
+    # ---------------- the same step launched as one CUDA graph (captured at capacity)
+    n_img_d = torch.tensor([wl.n_img], dtype=torch.int64, device=dev)
+    n_evt_d = torch.tensor([wl.n_evt], dtype=torch.int64, device=dev)
+    graph = rta.rta_graph_create(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), n_img_d.data_ptr(),
+                                 wl.n_img, evt_off.data_ptr(), n_evt_d.data_ptr(), wl.n_evt, *proc, hil.data_ptr(),
+                                 ste.data_ptr())
+    for _ in range(3):
+        rta.rta_graph_launch(graph, sp)
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        rta.rta_graph_launch(graph, sp)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = g0.elapsed_time(g1) / args.steps
+    rta.rta_graph_destroy(graph)
+    ctx.check(sp)
+
     # ---------------- roofline of the dominant kernel (fused image kernel)
     hbm_peak, peak_kind = peaks()
     alg_bytes = wl.wave_bytes + wl.n_img * HILLAS_BYTES
@@ -340,13 +359,14 @@ def main():
             "gbs": wl.wave_bytes * ws / (ms_per_step / 1e3) / 1e9,
             "gbs_vs_hbm_peak": wl.wave_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
             "kernel_ms": {"image_chain": chain_avg, "stereo": statistics.mean(stereo_ms)},
+            "graph": {"ms_per_step": graph_ms, "events_per_s": events_all / (graph_ms / 1e3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_image_chain", "algorithmic_bytes_per_launch": alg_bytes},
             "e2e": {"value": events_all / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "gbs": wl.wave_bytes * ws / e2e_s / 1e9,
                     "call": "rta_reconstruct_host (pinned host bundle)"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 2 * args.steps,   # timed region: k_image_chain + k_stereo per step
             "clocks": clk,
             "cpu_baseline": cpu,
         }

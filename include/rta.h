@@ -243,6 +243,24 @@ int rta_reconstruct(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const 
                     int start, int W, float t_hi, float t_lo, int core_needs_neighbour, rta_hillas_t* d_hillas,
                     rta_stereo_t* d_stereo, void* stream);
 
+/* The pass of rta_reconstruct captured once into a CUDA graph (one memset and
+ * two kernel launches) for repeated launches on fixed buffers. The graph is
+ * captured at capacity (max_img images, max_evt events); the actual counts are
+ * read at run time from the device-resident int64 values *d_n_img (<= max_img)
+ * and *d_n_evt (<= max_evt), so one graph serves bundles of any size up to its
+ * capacity: write the counts (and the bundle) on the launch stream, then
+ * rta_graph_launch. All buffers must stay valid for the graph's lifetime; the
+ * launch configuration is the context's at capture time. Launches of one graph
+ * must not overlap on the GPU (they share a work counter). */
+typedef struct rta_graph rta_graph;
+int rta_graph_create(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                     const int32_t* d_img_tel, const int64_t* d_n_img, int64_t max_img, const int32_t* d_evt_off,
+                     const int64_t* d_n_evt, int64_t max_evt, int window_mode, int start, int W, float t_hi,
+                     float t_lo, int core_needs_neighbour, rta_hillas_t* d_hillas, rta_stereo_t* d_stereo,
+                     rta_graph** out);
+int rta_graph_launch(rta_graph* graph, void* stream);
+int rta_graph_destroy(rta_graph* graph);
+
 /* The same pass over a bundle in HOST memory (pinned memory gives full copy
  * speed): the library copies the bundle to its own device staging buffers in
  * event-aligned chunks, overlapping the copy of chunk k+1 with the work on

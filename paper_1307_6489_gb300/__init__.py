@@ -88,6 +88,9 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_stereo": ([P, P, P, i64, P, i64, P, P], i32),
         "rta_reconstruct": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P, P], i32),
         "rta_reconstruct_host": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P], i32),
+        "rta_graph_create": ([P, P, i64, P, P, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32, P, P, P], i32),
+        "rta_graph_launch": ([P, P], i32),
+        "rta_graph_destroy": ([P], i32),
         "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
                                      P, P, P], i32),
     }
@@ -247,6 +250,23 @@ def rta_reconstruct_host(ctx, h_wave, n_wave, h_wave_off, h_img_tel, n_img, h_ev
     _check(load().rta_reconstruct_host(ctx, h_wave, n_wave, h_wave_off, h_img_tel, n_img, h_evt_off, n_evt,
                                        window_mode, start, W, t_hi, t_lo, int(core_needs_neighbour), h_hillas,
                                        h_stereo))
+
+
+def rta_graph_create(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_n_img, max_img, d_evt_off, d_n_evt, max_evt,
+                     window_mode, start, W, t_hi, t_lo, core_needs_neighbour, d_hillas, d_stereo) -> int:
+    g = ctypes.c_void_p()
+    _check(load().rta_graph_create(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_n_img, max_img, d_evt_off, d_n_evt,
+                                   max_evt, window_mode, start, W, t_hi, t_lo, int(core_needs_neighbour), d_hillas,
+                                   d_stereo, ctypes.byref(g)))
+    return g.value
+
+
+def rta_graph_launch(graph: int, stream: int = 0):
+    _check(load().rta_graph_launch(graph, stream))
+
+
+def rta_graph_destroy(graph: int):
+    _check(load().rta_graph_destroy(graph))
 
 
 RTA_NOALLOC_MAX_CAMS = 16

@@ -427,6 +427,8 @@ __global__ void __launch_bounds__(IW * 32 + 64, 1) k_image_chain(const ChainArgs
     if (tid < 32) {
         // ---------------- producer warp: lane 0 issues everything
         if (tid != 0) return;
+        // a graph captured at capacity reads the bundle's image count at run time
+        const int64_t n_img = a.n_img_dev ? min(*a.n_img_dev, a.n_img) : a.n_img;
         const uint64_t pol_stream = l2_policy_evict_first();
         const uint64_t pol_keep = l2_policy_evict_last();
         int stage = 0;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, 1) k_image_chain(const ChainArgs
         for (;;) {
             const unsigned int img_u = atomicAdd(a.counter, 1u);
             const int64_t img = img_u;
-            if (img >= a.n_img) {
+            if (img >= n_img) {
                 if (!acquire(stage, phase)) { ok = false; break; }
                 StageHdr h = {};
                 h.img = -1;

@@ -1,37 +1,58 @@
 // Stereo Hillas intersection (direction and core reconstruction, Sec. 4.1).
 //
 // One warp per event. The event's images (at most 64) are staged in shared
-// memory; lanes then take the pairs (i, j > i) and accumulate the weighted
-// intersections, and a shuffle tree sums the five partial sums. The weighted
-// intersection is accumulated without dividing by sin(psi_j - psi_i):
+// memory; the lanes then share out the m*m index pairs (i, j), keep those with
+// i < j, and accumulate the weighted intersections; a shuffle tree sums the five
+// partial sums. The weighted intersection is accumulated without dividing by
+// s = sin(psi_j - psi_i):
 //   w * p = F * (|s| * c_i + sign(s) * cross(c_j - c_i, u_j) * u_i),
-// with F = s_i s_j / (s_i + s_j) (1 - W_i/L_i)(1 - W_j/L_j) and s = cross(u_i, u_j),
-// which is the same quantity as |s| F * (c_i + u_i cross / s) but stays well
-// conditioned for nearly parallel axes. The pair arithmetic is FP64: when every
-// pair of an event is nearly parallel, the result is a ratio of two small sums
-// and FP32 rounding of the axis directions alone would move it by far more
-// than the rounding of the inputs. The work is a few hundred pairs per event,
-// far below the image kernel's cost.
+// with F = s_i s_j / (s_i + s_j) (1 - W_i/L_i)(1 - W_j/L_j), the same quantity as
+// |s| F * (c_i + u_i cross / s) but well conditioned for nearly parallel axes.
+// Precision: when every pair of an event is nearly parallel the result is a
+// ratio of small sums, so s must be accurate relative to itself. It is taken as
+// sinf of the angle difference computed exactly in FP64 and reduced to
+// (-pi/2, pi/2] (sin(d - pi) = -sin d), never as a difference of products of
+// rounded cosines; everything else is FP32, each lane's sums are compensated
+// (Kahan-Babuska) and the lanes are combined in FP64.
 #include "rta_launch.cuh"
 
 namespace rta {
 
 constexpr int ST_WARPS = 8;
 
-
 struct StereoImg {
-    double x, y, c, s, f, tx, ty, size;  // f = 1 - W/L, 0 if unused
+    float x, y, c, s, psi, f, tx, ty, size;  // f = 1 - W/L
     int used;
-    int pad;
 };
+
+// Compensated running sum (Neumaier's variant of Kahan summation).
+struct CSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
     __shared__ StereoImg sh[ST_WARPS][RTA_STEREO_MAX_M];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     StereoImg* im = sh[warp];
-    for (int64_t e = int64_t(blockIdx.x) * ST_WARPS + warp; e < a.n_evt; e += int64_t(gridDim.x) * ST_WARPS) {
+    const double kPi = 3.141592653589793;
+    // a graph captured at capacity reads the bundle's counts at run time
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    const int64_t n_img = a.n_img_dev ? min(*a.n_img_dev, a.n_img) : a.n_img;
+    for (int64_t e = int64_t(blockIdx.x) * ST_WARPS + warp; e < n_evt; e += int64_t(gridDim.x) * ST_WARPS) {
         const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
-        if (i0 < 0 || i1 < i0 || i1 > a.n_img) {            // malformed CSR: flag, never index
+        if (i0 < 0 || i1 < i0 || i1 > n_img) {            // malformed CSR: flag, never index
             if (lane == 0) {
                 atomicOr(a.status, RTA_DEV_BAD_IMAGE);
                 rta_stereo_t r = {};
@@ -49,50 +70,51 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
             const bool used = tel_ok && hh.n_pix >= 3 && !(hh.flags & (RTA_HF_EMPTY | RTA_HF_BAD_INPUT));
             if (!tel_ok) atomicOr(a.status, RTA_DEV_BAD_IMAGE);
             StereoImg v;
-            double sp = 0.0, cp = 1.0;
-            if (used) sincos(double(hh.psi), &sp, &cp);
+            float sp, cp;
+            sincosf(hh.psi, &sp, &cp);
             v.x = hh.x;
             v.y = hh.y;
             v.c = cp;
             v.s = sp;
-            v.f = used ? 1.0 - double(hh.width) / double(hh.length) : 0.0;
+            v.psi = hh.psi;
+            v.f = used ? 1.f - __fdiv_rn(hh.width, hh.length) : 0.f;
             const float2 t = tel_ok ? a.arr.tel_xy[tel] : make_float2(0.f, 0.f);
             v.tx = t.x;
             v.ty = t.y;
             v.size = hh.size;
             v.used = used;
-            v.pad = 0;
             im[k] = v;
             nvalid_lane += used;
         }
         __syncwarp();
-        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        CSum acc[5];
         int npair = 0;
-        for (int i = 0; i < m; ++i) {
-            if (!im[i].used) continue;
-            const StereoImg A = im[i];
-            for (int j = i + 1 + lane; j < m; j += 32) {
-                const StereoImg B = im[j];
-                if (!B.used) continue;
-                const double s = A.c * B.s - A.s * B.c;   // sin(psi_j - psi_i)
-                if (fabs(s) < 1e-6) continue;
-                const double F = A.size * B.size / (A.size + B.size) * A.f * B.f;
-                const double as = fabs(s);
-                const double sg = s > 0.0 ? 1.0 : -1.0;
-                const double cr = (B.x - A.x) * B.s - (B.y - A.y) * B.c;      // cross(c_j - c_i, u_j)
-                const double crg = (B.tx - A.tx) * B.s - (B.ty - A.ty) * B.c;
-                acc[0] += F * as;
-                acc[1] += F * (as * A.x + sg * cr * A.c);
-                acc[2] += F * (as * A.y + sg * cr * A.s);
-                acc[3] += F * (as * A.tx + sg * crg * A.c);
-                acc[4] += F * (as * A.ty + sg * crg * A.s);
-                ++npair;
-            }
+        for (int p = lane; p < m * m; p += 32) {
+            const int i = p / m, j = p - i * m;
+            if (j <= i) continue;
+            const StereoImg A = im[i], B = im[j];
+            if (!A.used || !B.used) continue;
+            double d = double(B.psi) - double(A.psi);     // exact: both are FP32 values
+            float sgn = 1.f;
+            if (d > 0.5 * kPi) { d -= kPi; sgn = -1.f; }
+            else if (d <= -0.5 * kPi) { d += kPi; sgn = -1.f; }
+            const float s = sgn * sinf(float(d));         // sin(psi_j - psi_i), relatively accurate
+            if (fabsf(s) < 1e-6f) continue;
+            const float F = __fdiv_rn(A.size * B.size, A.size + B.size) * A.f * B.f;
+            const float as = fabsf(s);
+            const float sg = s > 0.f ? 1.f : -1.f;
+            const float cr = (B.x - A.x) * B.s - (B.y - A.y) * B.c;      // cross(c_j - c_i, u_j)
+            const float crg = (B.tx - A.tx) * B.s - (B.ty - A.ty) * B.c;
+            acc[0].add(F * as);
+            acc[1].add(F * (as * A.x + sg * cr * A.c));
+            acc[2].add(F * (as * A.y + sg * cr * A.s));
+            acc[3].add(F * (as * A.tx + sg * crg * A.c));
+            acc[4].add(F * (as * A.ty + sg * crg * A.s));
+            ++npair;
         }
+        double tot[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        for (int k = 0; k < 5; ++k) tot[k] = warp_sum_d(acc[k].value());
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             npair += __shfl_xor_sync(0xffffffffu, npair, o);
@@ -101,11 +123,11 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
         if (lane == 0) {
             rta_stereo_t r = {};
             r.n_valid = nvalid_lane;
-            if (npair > 0 && acc[0] > 0.0) {
-                r.dir_x = float(acc[1] / acc[0]);
-                r.dir_y = float(acc[2] / acc[0]);
-                r.core_x = float(acc[3] / acc[0]);
-                r.core_y = float(acc[4] / acc[0]);
+            if (npair > 0 && tot[0] > 0.0) {
+                r.dir_x = float(tot[1] / tot[0]);
+                r.dir_y = float(tot[2] / tot[0]);
+                r.core_x = float(tot[3] / tot[0]);
+                r.core_y = float(tot[4] / tot[0]);
             } else {
                 r.flags = RTA_SF_INVALID;
             }

@@ -189,7 +189,8 @@ int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int*
 
 int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
               const int64_t* d_pix_off, int64_t n_img, const rta::ProcParams& pp, float* d_q, float* d_t,
-              int64_t n_q, rta_hillas_t* d_out, int integrate_only, cudaStream_t s, unsigned int* counter) {
+              int64_t n_q, rta_hillas_t* d_out, int integrate_only, cudaStream_t s, unsigned int* counter,
+              const int64_t* d_n_img = nullptr) {
     int grid, swb;
     size_t smem;
     int rc = chain_launch_config(c, n_img, &grid, &smem, &swb);
@@ -204,6 +205,7 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.pix_off = d_pix_off;
     a.n_q = n_q;
     a.n_img = n_img;
+    a.n_img_dev = nullptr;
     a.q_out = d_q;
     a.t_out = d_t;
     a.out = d_out;
@@ -212,13 +214,15 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.stage_wave_bytes = swb;
     a.nstage = std::max(2, std::min(c->nstage, 8));
     a.integrate_only = integrate_only;
+    a.n_img_dev = d_n_img;
     CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
     CUDA_TRY(rta::launch_image_chain(c->variant, a, grid, smem, s));
     return RTA_OK;
 }
 
 int run_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off,
-               int64_t n_evt, rta_stereo_t* d_out, cudaStream_t s) {
+               int64_t n_evt, rta_stereo_t* d_out, cudaStream_t s, const int64_t* d_n_img = nullptr,
+               const int64_t* d_n_evt = nullptr) {
     rta::StereoArgs a;
     a.arr = dev_array(c);
     a.h = d_h;
@@ -226,6 +230,8 @@ int run_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     a.n_img = n_img;
     a.evt_off = d_evt_off;
     a.n_evt = n_evt;
+    a.n_img_dev = d_n_img;
+    a.n_evt_dev = d_n_evt;
     a.out = d_out;
     a.status = c->d_status;
     const int epb = rta::stereo_events_per_block();
@@ -684,6 +690,73 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
     }
     CUDA_TRY(cudaStreamSynchronize(c->slot[0].stream));
     CUDA_TRY(cudaStreamSynchronize(c->slot[1].stream));
+    return RTA_OK;
+}
+
+struct rta_graph {
+    rta_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned int* counter = nullptr;
+};
+
+int rta_graph_create(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                     const int32_t* d_img_tel, const int64_t* d_n_img, int64_t max_img, const int32_t* d_evt_off,
+                     const int64_t* d_n_evt, int64_t max_evt, int window_mode, int start, int W, float t_hi,
+                     float t_lo, int core_needs_neighbour, rta_hillas_t* d_hillas, rta_stereo_t* d_stereo,
+                     rta_graph** out) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(max_img, "max_img")) || (rc = check_n(max_evt, "max_evt")))
+        return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (!out || !d_wave || !d_wave_off || !d_img_tel || !d_n_img || !d_evt_off || !d_n_evt || !d_hillas || !d_stereo ||
+        max_img < 1 || max_evt < 1)
+        return fail(RTA_E_INVALID, "NULL pointer or empty capacity");
+    if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
+    rta_graph* g = new rta_graph();
+    g->ctx = c;
+    g->counter = take_counter(c);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        delete g;
+        return fail(RTA_E_CUDA, "stream creation failed");
+    }
+    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, max_img, pp, nullptr, nullptr, 0, d_hillas, 0,
+                       s, g->counter, d_n_img);
+        if (!rc) rc = run_stereo(c, d_hillas, d_img_tel, max_img, d_evt_off, max_evt, d_stereo, s, d_n_img, d_n_evt);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
+        if (!rc && e2 != cudaSuccess) rc = fail(RTA_E_CUDA, "capture failed: %s", cudaGetErrorString(e2));
+    } else {
+        rc = fail(RTA_E_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    if (!rc && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = fail(RTA_E_CUDA, "graph instantiation failed");
+    cudaStreamDestroy(s);
+    if (rc) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return RTA_OK;
+}
+
+int rta_graph_launch(rta_graph* g, void* stream) {
+    if (!g) return fail(RTA_E_INVALID, "graph is NULL");
+    int rc = check_ctx(g->ctx);
+    if (rc) return rc;
+    CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return RTA_OK;
+}
+
+int rta_graph_destroy(rta_graph* g) {
+    if (!g) return RTA_OK;
+    cudaSetDevice(g->ctx->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
     return RTA_OK;
 }
 

@@ -14,7 +14,8 @@ struct ChainArgs {
     const int32_t* img_tel;
     const int64_t* pix_off;  // integrate-only mode
     int64_t n_q;             // rows of q_out / t_out
-    int64_t n_img;
+    int64_t n_img;           // images (capacity when n_img_dev is set)
+    const int64_t* n_img_dev;  // optional device-resident image count (<= n_img), read at run time
     float* q_out;            // integrate-only mode
     float* t_out;
     rta_hillas_t* out;       // full mode
@@ -56,7 +57,9 @@ struct StereoArgs {
     const int32_t* img_tel;
     int64_t n_img;
     const int32_t* evt_off;
-    int64_t n_evt;
+    int64_t n_evt;             // events (capacity when n_evt_dev is set)
+    const int64_t* n_img_dev;  // optional device-resident counts, read at run time
+    const int64_t* n_evt_dev;
     rta_stereo_t* out;
     unsigned int* status;
 };
