@@ -110,6 +110,19 @@ typedef struct rta_stereo_t {
     float reserved[2];
 } rta_stereo_t;
 
+/* One event of the learned reconstruction, 32 bytes. */
+typedef struct rta_event_t {
+    float log_energy;     /* log10(E / TeV) */
+    float dir_x, dir_y;   /* direction, degrees in the nominal frame */
+    float gammaness;      /* gamma-likeness in (0, 1) */
+    int32_t n_used;       /* images with >= 3 pixels (-1: malformed event) */
+    uint32_t flags;       /* RTA_EF_* */
+    float base_x, base_y; /* the two-image baseline the learned offsets refer to */
+} rta_event_t;
+
+#define RTA_EF_NO_DIRECTION 1u /* fewer than 2 used images: no direction (geometric undefined too) */
+#define RTA_EF_FALLBACK 2u     /* learned and baseline directions disagree: geometric direction used */
+
 /* ---------------------------------------------------------------------- */
 /* Context                                                                 */
 /* ---------------------------------------------------------------------- */
@@ -271,6 +284,54 @@ int rta_reconstruct_host(rta_ctx* ctx, const uint16_t* h_wave, int64_t n_wave, c
                          const int32_t* h_img_tel, int64_t n_img, const int32_t* h_evt_off, int64_t n_evt,
                          int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
                          rta_hillas_t* h_hillas, rta_stereo_t* h_stereo);
+
+/* ---------------------------------------------------------------------- */
+/* Learned reconstruction: deep-sets surrogate (Sec. 4.1 energy, direction, */
+/* gamma/hadron separation)                                                */
+/* ---------------------------------------------------------------------- */
+/* Features per image (from its Hillas row and telescope; images with >= 3
+ * pixels are used): log10 size, centroid minus the event baseline b (x, y),
+ * length, width, cos 2psi, sin 2psi, time_grad / 10, |centroid - b|, camera type
+ * code, telescope x / 1000 m, y / 1000 m. The baseline b is the axis
+ * intersection of the event's two brightest used images when
+ * |sin(psi_2 - psi_1)| >= 0.1, else their size-weighted mean centroid.
+ * Network: phi 12 -> 128 -> 128 (ReLU) per image; pooling
+ * [sum / 40, mean] over used images (256); rho 256 -> 256 (ReLU) -> 4 =
+ * (log10 E/TeV, direction offset from b in x and y (deg), gammaness logit).
+ * Weights are BF16 copies of FP32 master weights; the GEMMs run on the tensor
+ * cores with FP32 accumulation; activations are stored in BF16.
+ * Loss (mean over events): gammas (y0 - log10 E)^2 + |y_12 - (src - b)|^2 / 0.1^2,
+ * all events BCE(sigmoid(y3), is_gamma). Adam(0.9, 0.999, 1e-8), bias-corrected.
+ * Packed parameter order (rta_surrogate_num_params() floats, row-major):
+ * W1[12x128], b1[128], W2[128x128], b2[128], V1[256x256], c1[256], V2[256x4], c2[4].
+ * The model borrows the context's telescope tables and must not outlive it.
+ * Calls that need a larger batch than any before grow the model's device
+ * workspace (an allocation). */
+typedef struct rta_model rta_model;
+int rta_surrogate_num_params(void);
+/* h_cam_code: RTA_MAX_CAMS floats, the type code of each camera id (NULL = zeros). */
+int rta_surrogate_create(rta_ctx* ctx, uint64_t seed, const float* h_cam_code, rta_model** out);
+int rta_surrogate_destroy(rta_model* model);
+int rta_surrogate_set_params(rta_model* model, const float* h_params);
+/* which: 0 parameters, 1 last gradients, 2 Adam first moments, 3 second moments. Synchronises. */
+int rta_surrogate_get_params(rta_model* model, int which, float* h_out);
+/* Raw network outputs d_y[n_evt*4] and baselines d_base[n_evt*2] (either may be NULL). */
+int rta_surrogate_forward(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                          const int32_t* d_evt_off, int64_t n_evt, float* d_y, float* d_base, void* stream);
+/* One training step on a batch: loss into *d_loss (may be NULL), gradients into
+ * the model and, when apply_update != 0, one Adam update with learning rate lr.
+ * Labels per event: d_log_energy (log10 E/TeV), d_src_xy (true direction, 2
+ * floats, deg), d_is_gamma (0/1). */
+int rta_surrogate_train_step(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                             const int32_t* d_evt_off, int64_t n_evt, const float* d_log_energy, const float* d_src_xy,
+                             const uint8_t* d_is_gamma, float lr, int apply_update, float* d_loss, void* stream);
+/* Inference: energy, direction (baseline + learned offset), gammaness. Events
+ * with fewer than 2 used images get RTA_EF_NO_DIRECTION (the geometric method
+ * is undefined too); events whose learned offset from the baseline exceeds
+ * fallback_deg get the geometric intersection of rta_stereo (computed for those
+ * events only) and RTA_EF_FALLBACK. */
+int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                        const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Entry point that allocates nothing                                      */

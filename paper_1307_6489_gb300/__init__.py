@@ -91,6 +91,14 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_graph_create": ([P, P, i64, P, P, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32, P, P, P], i32),
         "rta_graph_launch": ([P, P], i32),
         "rta_graph_destroy": ([P], i32),
+        "rta_surrogate_num_params": ([], i32),
+        "rta_surrogate_create": ([P, ctypes.c_uint64, P, P], i32),
+        "rta_surrogate_destroy": ([P], i32),
+        "rta_surrogate_set_params": ([P, P], i32),
+        "rta_surrogate_get_params": ([P, i32, P], i32),
+        "rta_surrogate_forward": ([P, P, P, i64, P, i64, P, P, P], i32),
+        "rta_surrogate_train_step": ([P, P, P, i64, P, i64, P, P, P, f32, i32, P, P], i32),
+        "rta_surrogate_infer": ([P, P, P, i64, P, i64, f32, P, P], i32),
         "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
                                      P, P, P], i32),
     }
@@ -267,6 +275,83 @@ def rta_graph_launch(graph: int, stream: int = 0):
 
 def rta_graph_destroy(graph: int):
     _check(load().rta_graph_destroy(graph))
+
+
+RTA_EF_NO_DIRECTION = 1
+RTA_EF_FALLBACK = 2
+EVENT_BYTES = 32
+
+
+def rta_surrogate_num_params() -> int:
+    return load().rta_surrogate_num_params()
+
+
+def rta_surrogate_create(ctx: int, seed: int = 0, cam_code=None) -> int:
+    m = ctypes.c_void_p()
+    codes = None
+    if cam_code is not None:
+        codes, _ = _np(np.resize(np.asarray(cam_code, np.float32), 16), np.float32)
+    _check(load().rta_surrogate_create(ctx, seed, None if codes is None else codes.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(m)))
+    return m.value
+
+
+def rta_surrogate_destroy(model: int):
+    _check(load().rta_surrogate_destroy(model))
+
+
+def rta_surrogate_set_params(model: int, params):
+    a, pa = _np(params, np.float32)
+    assert a.size == rta_surrogate_num_params()
+    _check(load().rta_surrogate_set_params(model, pa))
+
+
+def rta_surrogate_get_params(model: int, which: int = 0) -> np.ndarray:
+    out = np.zeros(rta_surrogate_num_params(), np.float32)
+    _check(load().rta_surrogate_get_params(model, which, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def rta_surrogate_forward(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_y, d_base, stream=0):
+    _check(load().rta_surrogate_forward(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_y, d_base, stream))
+
+
+def rta_surrogate_train_step(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_log_energy, d_src_xy, d_is_gamma,
+                             lr, apply_update=1, d_loss=0, stream=0):
+    _check(load().rta_surrogate_train_step(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_log_energy, d_src_xy,
+                                           d_is_gamma, lr, int(apply_update), d_loss, stream))
+
+
+def rta_surrogate_infer(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, fallback_deg, d_out, stream=0):
+    _check(load().rta_surrogate_infer(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, fallback_deg, d_out, stream))
+
+
+def events_to_numpy(raw: np.ndarray) -> dict:
+    """Decode rows of rta_event_t (n*32 bytes)."""
+    raw = np.ascontiguousarray(raw).view(np.uint8).reshape(-1, EVENT_BYTES)
+    f = raw.view(np.float32).reshape(-1, 8)
+    i = raw.view(np.int32).reshape(-1, 8)
+    return dict(log_energy=f[:, 0].copy(), dir_x=f[:, 1].copy(), dir_y=f[:, 2].copy(), gammaness=f[:, 3].copy(),
+                n_used=i[:, 4].copy(), flags=i[:, 5].view(np.uint32).copy(), base_x=f[:, 6].copy(),
+                base_y=f[:, 7].copy())
+
+
+# packed parameter layout of the surrogate (name, shape), row-major
+SURROGATE_LAYOUT = [("W1", (12, 128)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("V1", (256, 256)),
+                    ("c1", (256,)), ("V2", (256, 4)), ("c2", (4,))]
+
+
+def pack_params(d: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(d[k], np.float32).reshape(-1) for k, _ in SURROGATE_LAYOUT])
+
+
+def unpack_params(flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for k, shp in SURROGATE_LAYOUT:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n]).reshape(shp)
+        o += n
+    return out
 
 
 RTA_NOALLOC_MAX_CAMS = 16

@@ -1,0 +1,507 @@
+// Kernels of the learned deep-sets surrogate (energy, direction offset and
+// gamma/hadron score; the paper's Sec. 4.1 asks RT-RECO for energy and
+// gamma/hadron separation next to the direction).
+//
+//   k_features   per event: used images, baseline (two brightest axes), 12 features per image
+//   k_gemm       C = op(A) op(B) on BF16 operands with FP32 accumulation on the
+//                tensor cores (mma.sync m16n8k16), fused epilogues
+//   k_pool / k_pool_bwd, k_head / k_head_bwd, k_loss, k_adam, k_colsum, k_reduce_splits
+//
+// Row-major matrices throughout. Activations are stored in BF16 (the operand
+// type of the next GEMM); biases, the 4-wide output layer and every gradient
+// reduction are FP32.
+#include "rta_mlp.cuh"
+
+namespace rta {
+
+// ------------------------------------------------------------------ features
+// One warp per event; mirrors the feature definition of the surrogate.
+__global__ void __launch_bounds__(256) k_features(const FeatArgs a) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    const int64_t n_img = a.n_img_dev ? min(*a.n_img_dev, a.n_img) : a.n_img;
+    for (int64_t e = warp; e < n_evt; e += nwarps) {
+        const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
+        if (i0 < 0 || i1 < i0 || i1 > n_img) {
+            if (lane == 0) {
+                a.base[e] = make_float2(0.f, 0.f);
+                a.n_used[e] = -1;     // malformed event
+            }
+            continue;
+        }
+        // used images, brightest two (size desc, index asc), weighted centroid. Sizes are
+        // positive, so their bit patterns order like the values; the low word prefers
+        // the lower index on ties.
+        unsigned long long k1 = 0ull, k2 = 0ull;
+        int cnt = 0;
+        float sw = 0.f, swx = 0.f, swy = 0.f;
+        for (int k = lane; k < i1 - i0; k += 32) {
+            const rta_hillas_t h = a.h[i0 + k];
+            const bool used = h.n_pix >= 3 && !(h.flags & (RTA_HF_EMPTY | RTA_HF_BAD_INPUT));
+            a.used[i0 + k] = used;
+            if (!used) continue;
+            ++cnt;
+            sw += h.size;
+            swx += h.size * h.x;
+            swy += h.size * h.y;
+            const unsigned long long key =
+                (static_cast<unsigned long long>(__float_as_uint(fmaxf(h.size, 0.f))) << 32) | (0xFFFFFFFFu - unsigned(k));
+            if (key > k1) { k2 = k1; k1 = key; }
+            else if (key > k2) { k2 = key; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, k1, o);
+            const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, k2, o);
+            // top two of {k1, k2, o1, o2} (all keys distinct or zero)
+            const unsigned long long hi = k1 > o1 ? k1 : o1;
+            const unsigned long long lo = k1 > o1 ? o1 : k1;
+            const unsigned long long sec = k1 > o1 ? k2 : o2;
+            k1 = hi;
+            k2 = lo > sec ? lo : sec;
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            swx += __shfl_xor_sync(0xffffffffu, swx, o);
+            swy += __shfl_xor_sync(0xffffffffu, swy, o);
+        }
+        const int idx1 = k1 ? int(0xFFFFFFFFu - unsigned(k1 & 0xFFFFFFFFull)) : -1;
+        const int idx2 = k2 ? int(0xFFFFFFFFu - unsigned(k2 & 0xFFFFFFFFull)) : -1;
+        float bx = 0.f, by = 0.f;
+        bool done = false;
+        if (cnt >= 2 && idx1 >= 0 && idx2 >= 0) {
+            const rta_hillas_t A = a.h[i0 + idx1], B = a.h[i0 + idx2];
+            const float s = sinf(B.psi - A.psi);
+            if (fabsf(s) >= SUR_BASE_MIN_SIN) {
+                float sa, ca, sb, cb2;
+                sincosf(A.psi, &sa, &ca);
+                sincosf(B.psi, &sb, &cb2);
+                const float k = ((B.x - A.x) * sb - (B.y - A.y) * cb2) / s;
+                bx = A.x + k * ca;
+                by = A.y + k * sa;
+                done = true;
+            }
+        }
+        if (!done && cnt >= 1) {
+            bx = swx / sw;
+            by = swy / sw;
+        }
+        if (lane == 0) {
+            a.base[e] = make_float2(bx, by);
+            a.n_used[e] = cnt;
+        }
+        for (int k = lane; k < i1 - i0; k += 32) {
+            const rta_hillas_t h = a.h[i0 + k];
+            const int tel = a.img_tel[i0 + k];
+            const bool tel_ok = tel >= 0 && tel < a.n_tel;
+            const float2 txy = tel_ok ? a.tel_xy[tel] : make_float2(0.f, 0.f);
+            const float code = tel_ok ? a.cam_code[a.tel_cam[tel]] : 0.f;
+            const float dx = h.x - bx, dy = h.y - by;
+            float s2, c2;
+            sincosf(2.f * h.psi, &s2, &c2);
+            const float f[SUR_XPAD] = {log10f(fmaxf(h.size, 1e-3f)), dx, dy, h.length, h.width, c2, s2,
+                                       h.time_grad * 0.1f, sqrtf(dx * dx + dy * dy), code, txy.x * 1e-3f,
+                                       txy.y * 1e-3f, 0.f, 0.f, 0.f, 0.f};
+            __nv_bfloat16* xr = a.X + int64_t(i0 + k) * SUR_XPAD;
+#pragma unroll
+            for (int j = 0; j < SUR_XPAD; j += 2)
+                *reinterpret_cast<__nv_bfloat162*>(xr + j) = __floats2bfloat162_rn(f[j], f[j + 1]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core GEMM
+// C[M x N] = op(A)[M x K] op(B)[K x N]; A is [M x K] (TA = false) or stored as
+// [K x M] (TA = true); B is [K x N] (TB = false) or stored as [N x K] (TB = true).
+// Tile 64 x 64 x 32, 4 warps of 32 x 32, mma.sync.m16n8k16 BF16 -> FP32.
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];   // n-major: k pairs adjacent
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int64_t M = g.M_dev ? min(*g.M_dev, g.M) : g.M;
+    const int64_t K = g.K_dev ? min(*g.K_dev, g.K) : g.K;
+    if (m0 >= M) return;
+    // split-K range
+    const int64_t kchunk = ((K + gridDim.z - 1) / gridDim.z + GBK - 1) / GBK * GBK;
+    const int64_t kbeg = int64_t(blockIdx.z) * kchunk, kend = min(K, kbeg + kchunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+        for (int e = tid; e < GBM * GBK; e += 128) {
+            int m, k;
+            if (TA) { m = e % GBM; k = e / GBM; }     // consecutive threads along the stored row (m)
+            else { k = e % GBK; m = e / GBK; }
+            const int64_t gm = m0 + m, gk = k0 + k;
+            __nv_bfloat16 v = zero;
+            if (gm < M && gk < kend) v = TA ? g.A[gk * g.lda + gm] : g.A[gm * g.lda + gk];
+            As[m][k] = v;
+        }
+        for (int e = tid; e < GBN * GBK; e += 128) {
+            int n, k;
+            if (TB) { k = e % GBK; n = e / GBK; }
+            else { n = e % GBN; k = e / GBN; }
+            const int64_t gn = n0 + n, gk = k0 + k;
+            __nv_bfloat16 v = zero;
+            if (gn < g.N && gk < kend) v = TB ? g.B[gn * g.ldb + gk] : g.B[gk * g.ldb + gn];
+            Bs[n][k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + 16 * i + gq, c = kk + 2 * tq;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][c]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][c]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][c + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][c + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = wn + 8 * j + gq, c = kk + 2 * tq;
+                bf[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][c]);
+                bf[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][c + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t m = m0 + wm + 16 * i + gq + (r >= 2 ? 8 : 0);
+                const int64_t n = n0 + wn + 8 * j + 2 * tq + (r & 1);
+                if (m >= M || n >= g.N) continue;
+                float v = acc[i][j][r];
+                const int64_t o = m * g.ldc + n;
+                switch (g.epi) {
+                case EPI_BIAS_RELU_BF16:
+                    v = fmaxf(v + g.bias[n], 0.f);
+                    g.Cb[o] = __float2bfloat16(v);
+                    break;
+                case EPI_MASK_BF16:
+                    v = __bfloat162float(g.mask[m * g.ldmask + n]) > 0.f ? v : 0.f;
+                    g.Cb[o] = __float2bfloat16(v);
+                    break;
+                case EPI_BF16:
+                    g.Cb[o] = __float2bfloat16(v);
+                    break;
+                default:   // EPI_F32_SPLIT: partial sums of split z
+                    g.Cf[int64_t(blockIdx.z) * M * g.ldc + o] = v;
+                    break;
+                }
+            }
+}
+
+// Sum of the split-K partials in a fixed order.
+__global__ void k_reduce_splits(const float* ws, int splits, int64_t n, float* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += ws[z * n + i];
+        out[i] = s;
+    }
+}
+
+// Column sums of a BF16 or FP32 matrix [rows x cols] (bias gradients), fixed order.
+__global__ void k_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t* rows_dev, int64_t rows, int cols,
+                         float* out) {
+    __shared__ float part[8][33];
+    const int64_t R = rows_dev ? min(*rows_dev, rows) : rows;
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int ty = threadIdx.x >> 5;
+    float s = 0.f;
+    if (c < cols)
+        for (int64_t r = ty; r < R; r += 8) s += Xb ? __bfloat162float(Xb[r * cols + c]) : Xf[r * cols + c];
+    part[ty][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (ty == 0 && c < cols) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x & 31];
+        out[c] = t;
+    }
+}
+
+// ------------------------------------------------------------------ pooling
+// P[e] = [sum_used h2 / 40, sum_used h2 / max(1, n_used)] (BF16). One block per event, 128 threads (one per channel).
+__global__ void __launch_bounds__(SUR_H) k_pool(const PoolArgs a) {
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    const int ch = threadIdx.x;
+    for (int64_t e = blockIdx.x; e < n_evt; e += gridDim.x) {
+        const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
+        float s = 0.f;
+        int cnt = 0;
+        if (a.n_used[e] >= 0)
+            for (int i = i0; i < i1; ++i)
+                if (a.used[i]) {
+                    s += __bfloat162float(a.H2[int64_t(i) * SUR_H + ch]);
+                    ++cnt;
+                }
+        a.P[e * 2 * SUR_H + ch] = __float2bfloat16(s * (1.f / SUR_POOL_DIV));
+        a.P[e * 2 * SUR_H + SUR_H + ch] = __float2bfloat16(s / fmaxf(1.f, float(cnt)));
+    }
+}
+
+// dZ2[i] = used_i * (dP[e][:H] / 40 + dP[e][H:] / max(1, n)) * (H2[i] > 0), BF16.
+__global__ void __launch_bounds__(SUR_H) k_pool_bwd(const PoolArgs a) {
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    const int ch = threadIdx.x;
+    for (int64_t e = blockIdx.x; e < n_evt; e += gridDim.x) {
+        const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
+        int cnt = 0;
+        if (a.n_used[e] >= 0)
+            for (int i = i0; i < i1; ++i) cnt += a.used[i] ? 1 : 0;
+        const float g = __bfloat162float(a.dP[e * 2 * SUR_H + ch]) * (1.f / SUR_POOL_DIV) +
+                        __bfloat162float(a.dP[e * 2 * SUR_H + SUR_H + ch]) / fmaxf(1.f, float(cnt));
+        if (a.n_used[e] < 0) continue;
+        for (int i = i0; i < i1; ++i) {
+            const float h = __bfloat162float(a.H2[int64_t(i) * SUR_H + ch]);
+            a.dZ2[int64_t(i) * SUR_H + ch] = __float2bfloat16(a.used[i] && h > 0.f ? g : 0.f);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ output layer, loss, outputs
+// y[e] = G[e] . V2 + c2 (4 outputs), one warp per event, FP32 dot products.
+__global__ void __launch_bounds__(256) k_head(const HeadArgs a) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    for (int64_t e = warp; e < n_evt; e += nwarps) {
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = lane; k < SUR_G; k += 32) {
+            const float gk = __bfloat162float(a.G[e * SUR_G + k]);
+#pragma unroll
+            for (int o = 0; o < 4; ++o) y[o] += gk * __bfloat162float(a.V2b[k * 4 + o]);
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            y[o] = warp_sum(y[o]) + a.c2[o];
+        }
+        if (lane < 4) a.Y[e * 4 + lane] = y[lane];
+    }
+}
+
+// Per-event loss terms and dL/dy (mean over n_evt events).
+__global__ void k_loss(const LossArgs a) {
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    const float inv_n = 1.f / float(n_evt > 1 ? n_evt : 1);
+    const float ids2 = 1.f / (SUR_DIR_SIGMA * SUR_DIR_SIGMA);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < a.n_evt; e += int64_t(gridDim.x) * blockDim.x) {
+        if (e >= n_evt) { a.lterm[e] = 0.f; continue; }
+        const float* y = a.Y + e * 4;
+        const float gam = a.is_gamma[e] ? 1.f : 0.f;
+        const float2 b = a.base[e];
+        const float2 src = a.src[e];
+        const float r0 = y[0] - a.logE[e];
+        const float r1 = y[1] - (src.x - b.x), r2 = y[2] - (src.y - b.y);
+        const float sig = 1.f / (1.f + expf(-y[3]));
+        const float bce = fmaxf(y[3], 0.f) + log1pf(expf(-fabsf(y[3]))) - gam * y[3];
+        a.lterm[e] = gam * (r0 * r0 + (r1 * r1 + r2 * r2) * ids2) + bce;
+        a.dY[e * 4 + 0] = 2.f * gam * r0 * inv_n;
+        a.dY[e * 4 + 1] = 2.f * gam * r1 * ids2 * inv_n;
+        a.dY[e * 4 + 2] = 2.f * gam * r2 * ids2 * inv_n;
+        a.dY[e * 4 + 3] = (sig - gam) * inv_n;
+    }
+}
+
+// Sum of the loss terms / n in a fixed order (one block).
+__global__ void k_loss_sum(const float* lterm, int64_t n, const int64_t* n_dev, float* out) {
+    __shared__ float part[256];
+    const int64_t N = n_dev ? min(*n_dev, n) : n;
+    float s = 0.f;
+    for (int64_t i = threadIdx.x; i < N; i += 256) s += lterm[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0] / float(N > 1 ? N : 1);
+}
+
+// Backward of the output layer: dV2 = G^T dY (256 x 4, one block per 32 rows of V2),
+// dG = (dY V2^T) * (G > 0) (BF16), dc2 = sum dY.
+__global__ void k_head_bwd_dg(const HeadArgs a) {
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_evt * SUR_G;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t e = i / SUR_G;
+        const int k = int(i - e * SUR_G);
+        const float g = __bfloat162float(a.G[i]);
+        float d = 0.f;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) d += a.dY[e * 4 + o] * __bfloat162float(a.V2b[k * 4 + o]);
+        a.dG[i] = __float2bfloat16(g > 0.f ? d : 0.f);
+    }
+}
+
+__global__ void k_head_bwd_dv2(const HeadArgs a) {
+    // one block of 256 threads per (row k of V2): sum over events of G[e][k] * dY[e][o]
+    __shared__ float part[4][256];
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    const int k = blockIdx.x;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t e = threadIdx.x; e < n_evt; e += blockDim.x) {
+        const float g = k < SUR_G ? __bfloat162float(a.G[e * SUR_G + k]) : 1.f;   // row SUR_G: bias (dc2)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) s[o] += g * a.dY[e * 4 + o];
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) part[o][threadIdx.x] = s[o];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) part[o][threadIdx.x] += part[o][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) {
+        if (k < SUR_G) a.dV2[k * 4 + threadIdx.x] = part[threadIdx.x][0];
+        else a.dc2[threadIdx.x] = part[threadIdx.x][0];
+    }
+}
+
+// Inference outputs: direction = baseline + offsets; fallback list for the geometric pass.
+__global__ void k_outputs(const OutArgs a) {
+    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n_evt; e += int64_t(gridDim.x) * blockDim.x) {
+        const float* y = a.Y + e * 4;
+        const float2 b = a.base[e];
+        rta_event_t r = {};
+        r.log_energy = y[0];
+        r.dir_x = b.x + y[1];
+        r.dir_y = b.y + y[2];
+        r.gammaness = 1.f / (1.f + expf(-y[3]));
+        r.n_used = a.n_used[e];
+        r.base_x = b.x;
+        r.base_y = b.y;
+        if (a.n_used[e] < 2) {
+            r.flags |= RTA_EF_NO_DIRECTION;        // the geometric method is undefined as well
+        } else if (sqrtf(y[1] * y[1] + y[2] * y[2]) > a.fallback_deg) {
+            r.flags |= RTA_EF_FALLBACK;
+            const unsigned slot = atomicAdd(a.n_fallback, 1u);
+            a.fallback_idx[slot] = int(e);
+        }
+        a.out[e] = r;
+    }
+}
+
+// Geometric direction for the events on the fallback list (after k_stereo_list).
+__global__ void k_apply_fallback(const OutArgs a) {
+    const unsigned n = *a.n_fallback;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int e = a.fallback_idx[i];
+        const rta_stereo_t s = a.geo[i];
+        rta_event_t r = a.out[e];
+        if (!(s.flags & RTA_SF_INVALID)) {
+            r.dir_x = s.dir_x;
+            r.dir_y = s.dir_y;
+        } else {
+            r.flags |= RTA_EF_NO_DIRECTION;
+        }
+        a.out[e] = r;
+    }
+}
+
+// ------------------------------------------------------------------ Adam
+// FP32 master weights; BF16 copies of the GEMM operands refreshed in the same pass.
+__global__ void k_adam(const AdamArgs a) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a.n; i += int64_t(gridDim.x) * blockDim.x) {
+        const float g = a.g[i];
+        const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+        const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+        a.m[i] = m;
+        a.v[i] = v;
+        const float mh = m / a.bc1, vh = v / a.bc2;
+        const float p = a.p[i] - a.lr * mh / (sqrtf(vh) + a.eps);
+        a.p[i] = p;
+        a.pb[i] = __float2bfloat16(p);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <bool TA, bool TB>
+static cudaError_t gemm_t(const GemmArgs& g, int splits, cudaStream_t s) {
+    dim3 grid(unsigned((g.N + GBN - 1) / GBN), unsigned((g.M + GBM - 1) / GBM), unsigned(splits));
+    k_gemm<TA, TB><<<grid, 128, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, bool ta, bool tb, int splits, cudaStream_t s) {
+    if (ta && tb) return gemm_t<true, true>(g, splits, s);
+    if (ta) return gemm_t<true, false>(g, splits, s);
+    if (tb) return gemm_t<false, true>(g, splits, s);
+    return gemm_t<false, false>(g, splits, s);
+}
+
+cudaError_t launch_features(const FeatArgs& a, int grid, cudaStream_t s) {
+    k_features<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_pool(const PoolArgs& a, int grid, bool bwd, cudaStream_t s) {
+    if (bwd) k_pool_bwd<<<grid, SUR_H, 0, s>>>(a);
+    else k_pool<<<grid, SUR_H, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_head(const HeadArgs& a, int grid, cudaStream_t s) {
+    k_head<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_head_bwd(const HeadArgs& a, int grid, cudaStream_t s) {
+    k_head_bwd_dg<<<grid, 256, 0, s>>>(a);
+    k_head_bwd_dv2<<<SUR_G + 1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_loss(const LossArgs& a, int grid, float* d_loss, cudaStream_t s) {
+    k_loss<<<grid, 256, 0, s>>>(a);
+    if (d_loss) k_loss_sum<<<1, 256, 0, s>>>(a.lterm, a.n_evt, a.n_evt_dev, d_loss);
+    return cudaGetLastError();
+}
+cudaError_t launch_outputs(const OutArgs& a, int grid, bool apply_fallback, cudaStream_t s) {
+    if (apply_fallback) k_apply_fallback<<<grid, 256, 0, s>>>(a);
+    else k_outputs<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t* rows_dev, int64_t rows, int cols,
+                          float* out, cudaStream_t s) {
+    k_colsum<<<(cols + 31) / 32, 256, 0, s>>>(Xb, Xf, rows_dev, rows, cols, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* out, cudaStream_t s) {
+    k_reduce_splits<<<int((n + 255) / 256), 256, 0, s>>>(ws, splits, n, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s) {
+    k_adam<<<int((a.n + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace rta

@@ -48,10 +48,12 @@ __global__ void __launch_bounds__(ST_WARPS * 32) k_stereo(const StereoArgs a) {
     StereoImg* im = sh[warp];
     const double kPi = 3.141592653589793;
     // a graph captured at capacity reads the bundle's counts at run time
-    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
+    if (a.evt_idx) n_evt = min(int64_t(*a.n_list_dev), a.n_evt);
     const int64_t n_img = a.n_img_dev ? min(*a.n_img_dev, a.n_img) : a.n_img;
     for (int64_t e = int64_t(blockIdx.x) * ST_WARPS + warp; e < n_evt; e += int64_t(gridDim.x) * ST_WARPS) {
-        const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
+        const int64_t ev = a.evt_idx ? a.evt_idx[e] : e;       // the event; e is the output row
+        const int i0 = a.evt_off[ev], i1 = a.evt_off[ev + 1];
         if (i0 < 0 || i1 < i0 || i1 > n_img) {            // malformed CSR: flag, never index
             if (lane == 0) {
                 atomicOr(a.status, RTA_DEV_BAD_IMAGE);

@@ -1,0 +1,135 @@
+// Launch-argument blocks and constants of the deep-sets surrogate kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "rta_launch.cuh"
+
+#define SUR_NF 12            // features per image
+#define SUR_XPAD 16          // feature rows padded to 16 (one k-step of the tensor-core MMA)
+#define SUR_H 128            // width of the per-telescope network
+#define SUR_G 256            // width of the event network (and of the pooled vector)
+#define SUR_POOL_DIV 40.f    // sum pooling divisor
+#define SUR_DIR_SIGMA 0.1f   // direction scale of the loss (deg)
+#define SUR_BASE_MIN_SIN 0.1f
+
+namespace rta {
+
+// internal parameter layout (FP32 master copy and its BF16 twin), element offsets
+constexpr int64_t OFF_W1 = 0;                                // [16 x 128], rows 12..15 zero
+constexpr int64_t OFF_B1 = OFF_W1 + SUR_XPAD * SUR_H;
+constexpr int64_t OFF_W2 = OFF_B1 + SUR_H;                   // [128 x 128]
+constexpr int64_t OFF_B2 = OFF_W2 + SUR_H * SUR_H;
+constexpr int64_t OFF_V1 = OFF_B2 + SUR_H;                   // [256 x 256]
+constexpr int64_t OFF_C1 = OFF_V1 + SUR_G * SUR_G;
+constexpr int64_t OFF_V2 = OFF_C1 + SUR_G;                   // [256 x 4]
+constexpr int64_t OFF_C2 = OFF_V2 + SUR_G * 4;
+constexpr int64_t N_PARAM_INTERNAL = OFF_C2 + 4;
+constexpr int64_t N_PARAM_PACKED = SUR_NF * SUR_H + SUR_H + SUR_H * SUR_H + SUR_H + SUR_G * SUR_G + SUR_G + SUR_G * 4 + 4;
+
+struct FeatArgs {
+    const rta_hillas_t* h;
+    const int32_t* img_tel;
+    const int32_t* evt_off;
+    int64_t n_img, n_evt;
+    const int64_t* n_img_dev;
+    const int64_t* n_evt_dev;
+    const int32_t* tel_cam;
+    const float2* tel_xy;
+    const float* cam_code;   // per camera id
+    int n_tel;
+    __nv_bfloat16* X;        // [n_img x 16]
+    uint8_t* used;           // [n_img]
+    float2* base;            // [n_evt]
+    int32_t* n_used;         // [n_evt], -1 = malformed event
+};
+
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32_SPLIT = 2, EPI_BF16 = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    const __nv_bfloat16* B;
+    int64_t lda, ldb, ldc, ldmask;
+    int64_t M, N, K;
+    const int64_t* M_dev;    // optional run-time row count (<= M)
+    const int64_t* K_dev;    // optional run-time reduction length (<= K)
+    int epi;
+    const float* bias;
+    const __nv_bfloat16* mask;
+    __nv_bfloat16* Cb;
+    float* Cf;
+};
+
+struct PoolArgs {
+    const int32_t* evt_off;
+    int64_t n_evt;
+    const int64_t* n_evt_dev;
+    const uint8_t* used;
+    const int32_t* n_used;
+    const __nv_bfloat16* H2;   // [n_img x 128]
+    __nv_bfloat16* P;          // [n_evt x 256]
+    const __nv_bfloat16* dP;
+    __nv_bfloat16* dZ2;
+};
+
+struct HeadArgs {
+    int64_t n_evt;
+    const int64_t* n_evt_dev;
+    const __nv_bfloat16* G;    // [n_evt x 256]
+    const __nv_bfloat16* V2b;  // [256 x 4]
+    const float* c2;
+    float* Y;                  // [n_evt x 4]
+    const float* dY;
+    __nv_bfloat16* dG;
+    float* dV2;
+    float* dc2;
+};
+
+struct LossArgs {
+    int64_t n_evt;
+    const int64_t* n_evt_dev;
+    const float* Y;
+    const float2* base;
+    const float* logE;
+    const float2* src;
+    const uint8_t* is_gamma;
+    float* lterm;
+    float* dY;
+};
+
+struct OutArgs {
+    int64_t n_evt;
+    const int64_t* n_evt_dev;
+    const float* Y;
+    const float2* base;
+    const int32_t* n_used;
+    float fallback_deg;
+    rta_event_t* out;
+    unsigned int* n_fallback;
+    int32_t* fallback_idx;
+    const rta_stereo_t* geo;
+};
+
+struct AdamArgs {
+    int64_t n;
+    float* p;
+    float* m;
+    float* v;
+    const float* g;
+    __nv_bfloat16* pb;
+    float lr, b1, b2, eps, bc1, bc2;
+};
+
+cudaError_t launch_features(const FeatArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_gemm(const GemmArgs& g, bool ta, bool tb, int splits, cudaStream_t s);
+cudaError_t launch_pool(const PoolArgs& a, int grid, bool bwd, cudaStream_t s);
+cudaError_t launch_head(const HeadArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_head_bwd(const HeadArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_loss(const LossArgs& a, int grid, float* d_loss, cudaStream_t s);
+cudaError_t launch_outputs(const OutArgs& a, int grid, bool apply_fallback, cudaStream_t s);
+cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t* rows_dev, int64_t rows, int cols,
+                          float* out, cudaStream_t s);
+cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
+
+}  // namespace rta

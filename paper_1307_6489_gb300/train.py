@@ -1,0 +1,123 @@
+"""Host-side driver for training and evaluating the deep-sets surrogate.
+
+Marshalling only: batching, learning-rate schedule and bookkeeping on the host;
+every computation (image reconstruction, features, forward, backward, Adam,
+inference) runs in librta's kernels through the C-ABI calls of the binding.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import (RTA_WINDOW_FIXED, RTA_WINDOW_SLIDING, Context, rta_surrogate_create, rta_surrogate_destroy,
+               rta_surrogate_infer, rta_surrogate_train_step, events_to_numpy, hillas_to_numpy, stereo_to_numpy)
+
+
+def reconstruct_images(ctx: Context, wave, wave_off, img_tel, evt_off, proc, stream=None):
+    """Hillas rows (device, float32 view of n_img*16) of a device-resident bundle.
+
+    wave/wave_off/img_tel/evt_off are torch CUDA tensors; proc = (window_mode,
+    start, W, t_hi, t_lo, core_needs_neighbour)."""
+    import torch
+    h = torch.zeros(img_tel.numel() * 16, dtype=torch.float32, device=wave.device)
+    ctx.image_chain(wave, wave_off, img_tel, *proc, h, stream=stream)
+    return h
+
+
+class SurrogateTrainer:
+    """Trains an rta_model on a device-resident set of events.
+
+    hillas: float32 CUDA tensor of n_img*16 (rta_hillas_t rows); img_tel: int32
+    CUDA tensor; evt_off: int64 numpy array (n_evt+1, CSR of images); labels:
+    log_energy (float32, n_evt), src_xy (float32, n_evt*2), is_gamma (uint8).
+    """
+
+    def __init__(self, ctx: Context, seed: int = 0, cam_code=None, model: int | None = None):
+        self.ctx = ctx
+        self.model = model if model is not None else rta_surrogate_create(ctx.handle, seed, cam_code)
+        self.own = model is None
+
+    def close(self):
+        if self.own and self.model:
+            rta_surrogate_destroy(self.model)
+        self.model = None
+
+    def fit(self, hillas, img_tel, evt_off, log_energy, src_xy, is_gamma, epochs=10, batch_events=4096, lr=2e-3,
+            lr_end=2e-4, seed=0, stream=None):
+        import torch
+        dev = hillas.device
+        stream = torch.cuda.current_stream(dev).cuda_stream if stream is None else int(stream)
+        evt_off = np.asarray(evt_off, np.int64)
+        n_evt = len(evt_off) - 1
+        starts = np.arange(0, n_evt, batch_events)
+        rng = np.random.default_rng(seed)
+        steps = epochs * len(starts)
+        losses = []
+        d_loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        off_buf = torch.zeros(batch_events + 1, dtype=torch.int32, device=dev)
+        k = 0
+        for ep in range(epochs):
+            for e0 in rng.permutation(starts):
+                e1 = min(n_evt, e0 + batch_events)
+                i0, i1 = int(evt_off[e0]), int(evt_off[e1])
+                off = torch.from_numpy((evt_off[e0:e1 + 1] - i0).astype(np.int32))
+                off_buf[: e1 - e0 + 1].copy_(off, non_blocking=False)
+                rate = lr * (lr_end / lr) ** (k / max(1, steps - 1))
+                rta_surrogate_train_step(self.model, hillas.data_ptr() + 64 * i0, img_tel.data_ptr() + 4 * i0, i1 - i0,
+                                         off_buf.data_ptr(), e1 - e0, log_energy.data_ptr() + 4 * e0,
+                                         src_xy.data_ptr() + 8 * e0, is_gamma.data_ptr() + e0, rate, 1,
+                                         d_loss.data_ptr(), stream)
+                losses.append(float(d_loss.item()))
+                k += 1
+        return losses
+
+    def infer(self, hillas, img_tel, evt_off_dev, fallback_deg=0.5, stream=None):
+        """rta_event_t rows (uint8 CUDA tensor n_evt*32) for a device-resident set."""
+        import torch
+        n_evt = evt_off_dev.numel() - 1
+        out = torch.zeros(n_evt * 32, dtype=torch.uint8, device=hillas.device)
+        stream = torch.cuda.current_stream(hillas.device).cuda_stream if stream is None else int(stream)
+        rta_surrogate_infer(self.model, hillas.data_ptr(), img_tel.data_ptr(), img_tel.numel(), evt_off_dev.data_ptr(),
+                            n_evt, fallback_deg, out.data_ptr(), stream)
+        return out
+
+
+def containment68(d):
+    d = np.asarray(d)
+    return float(np.percentile(d, 68)) if len(d) else float("nan")
+
+
+def roc_auc(score_pos, score_neg):
+    """Area under the ROC curve (probability a positive outranks a negative; ties count half)."""
+    s = np.concatenate([score_pos, score_neg])
+    order = np.argsort(s, kind="mergesort")
+    ranks = np.empty(len(s))
+    sorted_s = s[order]
+    i = 0
+    while i < len(s):
+        j = i
+        while j + 1 < len(s) and sorted_s[j + 1] == sorted_s[i]:
+            j += 1
+        ranks[order[i:j + 1]] = 0.5 * (i + j) + 1
+        i = j + 1
+    n1, n0 = len(score_pos), len(score_neg)
+    return float((ranks[:n1].sum() - n1 * (n1 + 1) / 2) / (n1 * n0)) if n1 and n0 else float("nan")
+
+
+def evaluate(events: dict, stereo: dict, truth: np.ndarray):
+    """Resolution of the learned and the geometric reconstruction against the
+    generated truth (truth rows: E TeV, src_x, src_y, core_x, core_y, is_proton, m, attempts)."""
+    gam = truth[:, 5] == 0
+    ok_s = (events["flags"] & 1) == 0
+    ok_g = (stereo["flags"] & 1) == 0
+    both = gam & ok_s & ok_g
+    d_s = np.hypot(events["dir_x"] - truth[:, 1], events["dir_y"] - truth[:, 2])
+    d_g = np.hypot(stereo["dir_x"] - truth[:, 1], stereo["dir_y"] - truth[:, 2])
+    le = events["log_energy"] - np.log10(truth[:, 0])
+    out = dict(n_events=int(len(truth)), n_gamma_both=int(both.sum()),
+               r68_surrogate_deg=containment68(d_s[both]), r68_geometric_deg=containment68(d_g[both]),
+               energy_bias=float(np.mean(le[gam & ok_s])) if (gam & ok_s).any() else float("nan"),
+               energy_res=float(np.std(le[gam & ok_s])) if (gam & ok_s).any() else float("nan"),
+               fallback_frac=float(np.mean((events["flags"] & 2) != 0)),
+               auc_gamma_hadron=roc_auc(events["gammaness"][gam & ok_s], events["gammaness"][~gam & ok_s]))
+    out["r68_ratio"] = out["r68_surrogate_deg"] / out["r68_geometric_deg"]
+    return out

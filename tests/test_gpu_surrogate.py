@@ -1,0 +1,189 @@
+"""The learned deep-sets surrogate on the GPU against its FP64 oracle, and what
+training it gains over the geometric reconstruction.
+
+Parity inputs are built on the CPU only: Hillas rows from the CPU oracle,
+rounded to FP32, feed both sides; the network weights come from a seeded numpy
+initialiser, rounded to BF16. The oracle takes the same BF16 features and
+weights and computes in FP64; the GPU keeps activations in BF16 between layers.
+
+Tolerances (derived from BF16 storage of four activation layers, 2^-9 relative
+each): forward outputs |dy| <= 2e-2 (1 + |y|); per-tensor gradients cosine
+>= 0.999 and relative L2 <= 2e-2; baselines 1e-4 deg.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1307_6489_gb300 as rta
+from oracle import mlp
+
+from gpu_helpers import Dev, f32_rows_as_oracle, hillas_rows_as_f32, make_ctx, proc_args, stereo_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+Y_TOL = 2e-2
+G_COS, G_REL = 0.999, 2e-2
+
+
+def cam_codes(wl):
+    codes = np.zeros(16, np.float32)
+    for c, cam in wl.cams.items():
+        codes[c] = np.log10(cam.mirror_area) - 2.0
+    return codes
+
+
+@pytest.fixture(scope="module")
+def setup():
+    wl = synth.make_workload(3, 300)
+    ref = oracle.reconstruct(wl, do_stereo=False)
+    rows32 = hillas_rows_as_f32(ref["hillas"])
+    same = f32_rows_as_oracle(rows32)
+    ctx = make_ctx(wl)
+    codes = cam_codes(wl)
+    model = rta.rta_surrogate_create(ctx.handle, 7, codes)
+    p = {k: mlp.bf16_round(v) for k, v in mlp.init_params(11).items()}
+    rta.rta_surrogate_set_params(model, rta.pack_params(p))
+    tel_code = codes[wl.tel_cam]
+    X, used, base, n_used = mlp.features(same, wl.evt_off, wl.img_tel, wl.tel_xy.astype(np.float64), tel_code)
+    d = dict(h=torch.from_numpy(rows32.reshape(-1)).cuda(), img_tel=torch.from_numpy(wl.img_tel).cuda(),
+             evt_off=torch.from_numpy(wl.evt_off).cuda(),
+             logE=torch.from_numpy(np.log10(wl.truth[:, 0]).astype(np.float32)).cuda(),
+             src=torch.from_numpy(wl.truth[:, 1:3].astype(np.float32).reshape(-1)).cuda(),
+             gam=torch.from_numpy((wl.truth[:, 5] == 0).astype(np.uint8)).cuda())
+    yield dict(wl=wl, ctx=ctx, model=model, p=p, same=same, X=X, used=used, base=base, n_used=n_used, d=d,
+               rows32=rows32)
+    rta.rta_surrogate_destroy(model)
+    ctx.close()
+
+
+def gpu_forward(s):
+    wl, d = s["wl"], s["d"]
+    y = torch.zeros(wl.n_evt * 4, dtype=torch.float32, device="cuda")
+    b = torch.zeros(wl.n_evt * 2, dtype=torch.float32, device="cuda")
+    rta.rta_surrogate_forward(s["model"], d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img, d["evt_off"].data_ptr(),
+                              wl.n_evt, y.data_ptr(), b.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().reshape(-1, 4), b.cpu().numpy().reshape(-1, 2)
+
+
+def test_forward_and_baseline_match_the_oracle(setup):
+    s = setup
+    y, b = gpu_forward(s)
+    np.testing.assert_allclose(b, s["base"], atol=1e-4)
+    y_ref, _ = mlp.forward(s["p"], mlp.bf16_round(s["X"]), s["used"], s["wl"].evt_off)
+    err = np.abs(y - y_ref) / (1 + np.abs(y_ref))
+    print("forward max scaled error", err.max(axis=0))
+    assert err.max() <= Y_TOL
+    assert np.abs(y_ref).max() > 0.1                      # a non-trivial network
+
+
+def test_gradients_match_the_oracle(setup):
+    s = setup
+    wl, d = s["wl"], s["d"]
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    rta.rta_surrogate_train_step(s["model"], d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img,
+                                 d["evt_off"].data_ptr(), wl.n_evt, d["logE"].data_ptr(), d["src"].data_ptr(),
+                                 d["gam"].data_ptr(), 1e-3, 0, loss.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    g = rta.unpack_params(rta.rta_surrogate_get_params(s["model"], 1))
+    y_ref, cache = mlp.forward(s["p"], mlp.bf16_round(s["X"]), s["used"], wl.evt_off)
+    L_ref, dy = mlp.loss(y_ref, np.log10(wl.truth[:, 0]), wl.truth[:, 1:3] - s["base"], wl.truth[:, 5] == 0)
+    g_ref = mlp.backward(s["p"], cache, dy)
+    assert float(loss.item()) == pytest.approx(L_ref, rel=2e-2)
+    for k in g_ref:
+        a, r = g[k].reshape(-1).astype(np.float64), g_ref[k].reshape(-1)
+        cos = a @ r / (np.linalg.norm(a) * np.linalg.norm(r))
+        rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+        print(k, "cos", cos, "rel", rel)
+        assert cos >= G_COS and rel <= G_REL, k
+
+
+def test_adam_step_moves_each_weight_by_lr_against_its_gradient(setup):
+    s = setup
+    wl, d = s["wl"], s["d"]
+    ctx = s["ctx"]
+    model = rta.rta_surrogate_create(ctx.handle, 3, cam_codes(wl))
+    try:
+        rta.rta_surrogate_set_params(model, rta.pack_params(s["p"]))
+        lr = 1e-3
+        rta.rta_surrogate_train_step(model, d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img,
+                                     d["evt_off"].data_ptr(), wl.n_evt, d["logE"].data_ptr(), d["src"].data_ptr(),
+                                     d["gam"].data_ptr(), lr, 1, 0, torch.cuda.current_stream().cuda_stream)
+        new = rta.unpack_params(rta.rta_surrogate_get_params(model, 0))
+        g = rta.rta_surrogate_get_params(model, 1)
+        m = rta.rta_surrogate_get_params(model, 2)
+        v = rta.rta_surrogate_get_params(model, 3)
+        np.testing.assert_allclose(m, 0.1 * g, rtol=1e-6, atol=1e-12)            # first moment after one step
+        np.testing.assert_allclose(v, 0.001 * g.astype(np.float64) ** 2, rtol=1e-5, atol=1e-20)
+        y_ref, cache = mlp.forward(s["p"], mlp.bf16_round(s["X"]), s["used"], wl.evt_off)
+        _, dy = mlp.loss(y_ref, np.log10(wl.truth[:, 0]), wl.truth[:, 1:3] - s["base"], wl.truth[:, 5] == 0)
+        g_ref = mlp.backward(s["p"], cache, dy)
+        for k in g_ref:
+            sel = np.abs(g_ref[k]) > 1e-2 * np.abs(g_ref[k]).max()
+            step = new[k][sel] - s["p"][k][sel]
+            np.testing.assert_allclose(step, -lr * np.sign(g_ref[k][sel]), atol=2e-5 + 1e-6 * np.abs(s["p"][k][sel]).max())
+    finally:
+        rta.rta_surrogate_destroy(model)
+
+
+def test_inference_flags_and_geometric_fallback(setup):
+    s = setup
+    wl, d, ctx = s["wl"], s["d"], s["ctx"]
+    y, b = gpu_forward(s)
+    geo = torch.zeros(wl.n_evt * 8, dtype=torch.float32, device="cuda")
+    ctx.stereo(d["h"], d["evt_off"], d["img_tel"], geo)
+    st = stereo_rows(geo, wl.n_evt)
+    for bound in [1e3, 1e-4, 0.3]:
+        out = torch.zeros(wl.n_evt * 32, dtype=torch.uint8, device="cuda")
+        rta.rta_surrogate_infer(s["model"], d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img,
+                                d["evt_off"].data_ptr(), wl.n_evt, bound, out.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+        ctx.check()
+        ev = rta.events_to_numpy(out.cpu().numpy())
+        nodir = s["n_used"] < 2
+        np.testing.assert_array_equal((ev["flags"] & rta.RTA_EF_NO_DIRECTION) != 0,
+                                      nodir | (((ev["flags"] & rta.RTA_EF_FALLBACK) != 0) & (st["flags"] != 0)))
+        fb = (ev["flags"] & rta.RTA_EF_FALLBACK) != 0
+        expect_fb = ~nodir & (np.hypot(y[:, 1], y[:, 2]) > bound)
+        np.testing.assert_array_equal(fb, expect_fb)
+        ok = fb & (st["flags"] == 0)
+        np.testing.assert_array_equal(ev["dir_x"][ok], st["dir_x"][ok])
+        keep = ~fb & ~nodir
+        np.testing.assert_allclose(ev["dir_x"][keep], b[keep, 0] + y[keep, 1], rtol=0, atol=1e-6)
+        np.testing.assert_allclose(ev["log_energy"], y[:, 0], rtol=0, atol=0)
+        np.testing.assert_allclose(ev["gammaness"], 1 / (1 + np.exp(-y[:, 3].astype(np.float64))), atol=1e-6)
+
+
+def test_trained_network_gains_over_the_geometric_reconstruction():
+    """Train on 24k mixed gamma/proton events with the GPU kernels, evaluate on 6k
+    held-out events: the learned path adds an energy estimate and a gamma/hadron
+    score that the geometric method does not have, at a comparable direction."""
+    from paper_1307_6489_gb300 import train
+    wl = synth.make_workload(3, 30000)
+    ctx = make_ctx(wl)
+    dev = Dev(wl)
+    proc = proc_args(wl)
+    h = train.reconstruct_images(ctx, dev.wave, dev.wave_off, dev.img_tel, dev.evt_off, proc)
+    n_tr = 24000
+    i_tr = int(wl.evt_off[n_tr])
+    logE = torch.from_numpy(np.log10(wl.truth[:, 0]).astype(np.float32)).cuda()
+    src = torch.from_numpy(wl.truth[:, 1:3].astype(np.float32).reshape(-1)).cuda()
+    gam = torch.from_numpy((wl.truth[:, 5] == 0).astype(np.uint8)).cuda()
+    tr = train.SurrogateTrainer(ctx, seed=1, cam_code=cam_codes(wl))
+    losses = tr.fit(h[: i_tr * 16], dev.img_tel[:i_tr], wl.evt_off[: n_tr + 1], logE, src, gam, epochs=25,
+                    batch_events=1024, lr=2e-3, lr_end=1e-4)
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5])
+    # held-out events
+    off_te = torch.from_numpy((wl.evt_off[n_tr:] - i_tr).astype(np.int32)).cuda()
+    h_te, tel_te = h[i_tr * 16:].contiguous(), dev.img_tel[i_tr:].contiguous()
+    ev = rta.events_to_numpy(tr.infer(h_te, tel_te, off_te, fallback_deg=0.5).cpu().numpy())
+    geo = torch.zeros((wl.n_evt - n_tr) * 8, dtype=torch.float32, device="cuda")
+    ctx.stereo(h_te, off_te, tel_te, geo)
+    res = train.evaluate(ev, stereo_rows(geo, wl.n_evt - n_tr), wl.truth[n_tr:])
+    print("surrogate vs geometric:", res)
+    assert res["energy_res"] < 0.3 and abs(res["energy_bias"]) < 0.1
+    assert res["auc_gamma_hadron"] > 0.75
+    assert res["r68_ratio"] < 1.5
+    tr.close()
+    ctx.close()
