@@ -57,6 +57,7 @@ class SurrogateTrainer:
         k = 0
         for ep in range(epochs):
             for e0 in rng.permutation(starts):
+                e0 = int(e0)
                 e1 = min(n_evt, e0 + batch_events)
                 i0, i1 = int(evt_off[e0]), int(evt_off[e1])
                 off = torch.from_numpy((evt_off[e0:e1 + 1] - i0).astype(np.int32))

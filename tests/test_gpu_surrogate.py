@@ -114,8 +114,11 @@ def test_adam_step_moves_each_weight_by_lr_against_its_gradient(setup):
         g = rta.rta_surrogate_get_params(model, 1)
         m = rta.rta_surrogate_get_params(model, 2)
         v = rta.rta_surrogate_get_params(model, 3)
-        np.testing.assert_allclose(m, 0.1 * g, rtol=1e-6, atol=1e-12)            # first moment after one step
-        np.testing.assert_allclose(v, 0.001 * g.astype(np.float64) ** 2, rtol=1e-5, atol=1e-20)
+        # first and second moments after one step from zero, with the FP32 values of 1 - beta
+        one_m_b1 = np.float32(1) - np.float32(0.9)
+        one_m_b2 = np.float32(1) - np.float32(0.999)
+        np.testing.assert_allclose(m, one_m_b1 * g, rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(v, one_m_b2 * (g * g), rtol=1e-6, atol=1e-20)
         y_ref, cache = mlp.forward(s["p"], mlp.bf16_round(s["X"]), s["used"], wl.evt_off)
         _, dy = mlp.loss(y_ref, np.log10(wl.truth[:, 0]), wl.truth[:, 1:3] - s["base"], wl.truth[:, 5] == 0)
         g_ref = mlp.backward(s["p"], cache, dy)
