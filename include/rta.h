@@ -334,6 +334,67 @@ int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const in
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: a stream of bundles with continuous batching, and the sky map   */
+/* (Sec. 4.2 event-by-event RTA; Sec. 2.1 30 s alert latency and           */
+/* transient search on several timescales)                                 */
+/* ---------------------------------------------------------------------- */
+#define RTA_SKY_N 256      /* sky-map bins per axis, 0.02 deg each, [-2.56, 2.56) deg */
+#define RTA_SKY_SLABS 30   /* one-second slabs; a map is the sum of the last 30 */
+
+/* One bundle of events in HOST memory (pinned memory gives full copy speed).
+ * Layout as the device calls (offsets from h_wave, CSR from 0). Every buffer
+ * must stay valid until rta_stream_poll reports the bundle done; h_events
+ * (n_evt rows) then holds its event list. */
+typedef struct rta_bundle_t {
+    const uint16_t* h_wave;
+    int64_t n_wave;
+    const int64_t* h_wave_off;
+    const int32_t* h_img_tel;
+    int64_t n_img;
+    const int32_t* h_evt_off;
+    int64_t n_evt;
+    int64_t arrival_ns;      /* steady clock (CLOCK_MONOTONIC) nanoseconds of arrival */
+    rta_event_t* h_events;   /* out */
+} rta_bundle_t;
+
+typedef struct rta_stream rta_stream;
+
+/* Create the serving engine. hbm_budget_bytes is allocated once and
+ * sub-allocated per bundle (its waveforms, tables, Hillas rows and event
+ * list): a bundle is admitted when one of max_inflight slots (CUDA streams) is
+ * free and the budget has room, in arrival order; bundles of several slots run
+ * concurrently. Each bundle: copies in, rta_image_chain, then
+ * rta_surrogate_infer with the given model (events with a learned direction,
+ * geometric fallback) or, with model = NULL, rta_stereo (geometric direction,
+ * no energy or gammaness), the sky-map fill of the one-second slab of its
+ * arrival, and the copy of its event list out. max_img / max_evt bound one
+ * bundle. A scheduler thread owned by the stream does the device work. */
+int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, int max_inflight, int64_t max_img,
+                      int64_t max_evt, int window_mode, int start, int W, float t_hi, float t_lo,
+                      int core_needs_neighbour, float fallback_deg, rta_stream** out);
+/* Queue a bundle; returns at once with its ticket. RTA_E_NOMEM if it can never
+ * fit the budget, RTA_E_BUSY if 4096 bundles are already waiting. */
+int rta_stream_submit(rta_stream* stream, const rta_bundle_t* bundle, uint64_t* ticket);
+/* Non-blocking: RTA_OK once the bundle's event list is in host memory (its
+ * completion time in *done_ns, same clock as arrival_ns; the ticket is then
+ * released), RTA_E_BUSY while it is queued or running. */
+int rta_stream_poll(rta_stream* stream, uint64_t ticket, int64_t* done_ns);
+/* Wait until every submitted bundle has finished (RTA_E_TIMEOUT after timeout_ms). */
+int rta_stream_drain(rta_stream* stream, int timeout_ms);
+/* The sky-count map at time now_ns: per bin (row y, column x, RTA_SKY_N each)
+ * the events of the slabs of the last 30 seconds, into h_map. Bin of a
+ * direction: floor((v + 2.56f) * 50.0f) in FP32 (round to nearest, no
+ * contraction), kept when in [0, 256); events without direction are not
+ * counted. Synchronises the map's stream. */
+int rta_skymap_read(rta_stream* stream, int64_t now_ns, uint32_t* h_map);
+/* Count externally reconstructed events (device rows) into the sky map as if
+ * they had arrived at arrival_ns; ordered after the work already queued on
+ * `stream` and before later work on it that reuses d_events. */
+int rta_stream_add_events(rta_stream* stream, const rta_event_t* d_events, int64_t n_evt, int64_t arrival_ns,
+                          void* cuda_stream);
+int rta_stream_destroy(rta_stream* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Entry point that allocates nothing                                      */
 /* ---------------------------------------------------------------------- */
 /* The paper has no counterpart of this call; it exists for callers that may

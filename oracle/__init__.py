@@ -111,6 +111,34 @@ def stereo(hrows, txy):
     return out
 
 
+SKY_N = 256
+SKY_WINDOW_S = 30
+
+
+def sky_bin(v):
+    """Sky-map bin of a nominal-frame coordinate (deg): floor((v + 2.56) * 50) with
+    both operations in FP32, round to nearest (the quantisation is decided in the
+    precision of the device, as the reading of the binning states); -1 outside
+    [0, 256) or for NaN."""
+    v = np.asarray(v, np.float32)
+    with np.errstate(invalid="ignore"):
+        u = (v + np.float32(2.56)).astype(np.float32) * np.float32(50.0)
+        u = u.astype(np.float32)
+        ok = (u >= 0) & (u < SKY_N)
+    return np.where(ok, np.floor(np.where(ok, u, 0)), -1).astype(np.int64)
+
+
+def skymap(dir_x, dir_y, has_dir, arrival_s, now_s):
+    """Counts of events with a direction whose arrival second lies in
+    (now_s - 30, now_s], per bin [iy, ix]."""
+    ix, iy = sky_bin(dir_x), sky_bin(dir_y)
+    sec = np.asarray(arrival_s, np.int64)
+    sel = np.asarray(has_dir, bool) & (ix >= 0) & (iy >= 0) & (sec > now_s - SKY_WINDOW_S) & (sec <= now_s)
+    m = np.zeros((SKY_N, SKY_N), np.int64)
+    np.add.at(m, (iy[sel], ix[sel]), 1)
+    return m
+
+
 def reconstruct(wl, threads: int | None = None, do_stereo: bool = True, per_pixel: bool = False, wave=None):
     """Whole chain over a synth.Workload.
 

@@ -99,6 +99,13 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_surrogate_forward": ([P, P, P, i64, P, i64, P, P, P], i32),
         "rta_surrogate_train_step": ([P, P, P, i64, P, i64, P, P, P, f32, i32, P, P], i32),
         "rta_surrogate_infer": ([P, P, P, i64, P, i64, f32, P, P], i32),
+        "rta_stream_create": ([P, P, sz, i32, i64, i64, i32, i32, i32, f32, f32, i32, f32, P], i32),
+        "rta_stream_submit": ([P, P, P], i32),
+        "rta_stream_poll": ([P, ctypes.c_uint64, P], i32),
+        "rta_stream_drain": ([P, i32], i32),
+        "rta_skymap_read": ([P, i64, P], i32),
+        "rta_stream_add_events": ([P, P, i64, i64, P], i32),
+        "rta_stream_destroy": ([P], i32),
         "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
                                      P, P, P], i32),
     }
@@ -352,6 +359,59 @@ def unpack_params(flat: np.ndarray) -> dict:
         out[k] = np.asarray(flat[o:o + n]).reshape(shp)
         o += n
     return out
+
+
+RTA_SKY_N = 256
+RTA_SKY_SLABS = 30
+
+
+class Bundle(ctypes.Structure):
+    """rta_bundle_t: one bundle in host memory for the serving stream."""
+    _fields_ = [("h_wave", ctypes.c_void_p), ("n_wave", ctypes.c_int64), ("h_wave_off", ctypes.c_void_p),
+                ("h_img_tel", ctypes.c_void_p), ("n_img", ctypes.c_int64), ("h_evt_off", ctypes.c_void_p),
+                ("n_evt", ctypes.c_int64), ("arrival_ns", ctypes.c_int64), ("h_events", ctypes.c_void_p)]
+
+
+def rta_stream_create(ctx, model, hbm_budget_bytes, max_inflight, max_img, max_evt, window_mode, start, W, t_hi, t_lo,
+                      core_needs_neighbour, fallback_deg=0.5) -> int:
+    h = ctypes.c_void_p()
+    _check(load().rta_stream_create(ctx, model or None, hbm_budget_bytes, max_inflight, max_img, max_evt, window_mode,
+                                    start, W, t_hi, t_lo, int(core_needs_neighbour), fallback_deg, ctypes.byref(h)))
+    return h.value
+
+
+def rta_stream_submit(stream: int, bundle: Bundle) -> int:
+    t = ctypes.c_uint64()
+    _check(load().rta_stream_submit(stream, ctypes.byref(bundle), ctypes.byref(t)))
+    return t.value
+
+
+def rta_stream_poll(stream: int, ticket: int):
+    """Completion time (ns) once done, else None."""
+    done = ctypes.c_int64()
+    rc = load().rta_stream_poll(stream, ticket, ctypes.byref(done))
+    if rc == RTA_E_BUSY:
+        return None
+    _check(rc)
+    return done.value
+
+
+def rta_stream_drain(stream: int, timeout_ms: int = 60000):
+    _check(load().rta_stream_drain(stream, timeout_ms))
+
+
+def rta_skymap_read(stream: int, now_ns: int) -> np.ndarray:
+    out = np.zeros((RTA_SKY_N, RTA_SKY_N), np.uint32)
+    _check(load().rta_skymap_read(stream, now_ns, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def rta_stream_add_events(stream: int, d_events: int, n_evt: int, arrival_ns: int, cuda_stream: int = 0):
+    _check(load().rta_stream_add_events(stream, d_events, n_evt, arrival_ns, cuda_stream))
+
+
+def rta_stream_destroy(stream: int):
+    _check(load().rta_stream_destroy(stream))
 
 
 RTA_NOALLOC_MAX_CAMS = 16

@@ -80,6 +80,12 @@ cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_stereo(const StereoArgs& a, int grid, cudaStream_t s);
 // stores a message for rta_last_error() on the calling thread
 void set_last_error(const char* msg);
+// sky map and geometric event rows (k_skymap.cu)
+cudaError_t launch_skymap_fill(const rta_event_t* ev, int64_t n_evt, unsigned int* slab, cudaStream_t s);
+cudaError_t launch_skymap_sum(const unsigned int* slabs, unsigned long long use, unsigned int* out, cudaStream_t s);
+cudaError_t launch_stereo_to_events(const rta_stereo_t* st, int64_t n_evt, rta_event_t* ev, cudaStream_t s);
+// grow a model's workspace ahead of use (rta_surrogate.cu)
+int surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt);
 // context access for the surrogate (rta_api.cu)
 int surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2** tel_xy, int* n_tel, int* device);
 int surrogate_stereo_list(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,

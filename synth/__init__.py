@@ -233,12 +233,14 @@ def _calibration(seed, tel_cam, proc: Processing, cams):
 
 def make_workload(preset: int, n_events: int, seed: int | None = None, *, render: bool = True,
                   threads: int | None = None, wave_out: np.ndarray | None = None, flags: int = 0,
-                  proton_frac: float | None = None) -> Workload:
+                  proton_frac: float | None = None, telescopes=None) -> Workload:
     """Plan (and optionally render) ``n_events`` events of a preset.
 
     ``wave_out`` may supply the destination buffer (e.g. a pinned host array) of
     at least the workload's sample count; ``flags`` bit0 turns off electronic
-    noise and bit1 turns off night-sky background (used by tests)."""
+    noise and bit1 turns off night-sky background (used by tests);
+    ``telescopes`` (array presets) restricts triggering to a sub-array of
+    telescope ids (the calibration table still covers the whole array)."""
     if preset not in PRESET_PROCESSING:
         raise ValueError(f"unknown preset {preset}")
     seed = BASE_SEED + preset if seed is None else int(seed)
@@ -267,11 +269,14 @@ def make_workload(preset: int, n_events: int, seed: int | None = None, *, render
         ell = np.zeros((max_img, 3, 6), np.float32)
         n_ell = np.zeros(max_img, np.int32)
         truth = np.zeros((n_events, 8), np.float64)
-        n_img = lib.synth_plan_array(seed, n_events, pf, len(tel_cam), _p(tel_cam), _p(tel_xy), max_img,
+        sub = np.arange(len(tel_cam)) if telescopes is None else np.asarray(sorted(set(int(t) for t in telescopes)))
+        sub_cam = np.ascontiguousarray(tel_cam[sub], np.int32)
+        sub_xy = np.ascontiguousarray(tel_xy[sub], np.float32)
+        n_img = lib.synth_plan_array(seed, n_events, pf, len(sub), _p(sub_cam), _p(sub_xy), max_img,
                                      _p(evt_off), _p(img_tel), _p(ell), _p(n_ell), _p(truth))
         if n_img < 0:
             raise RuntimeError("synth_plan_array failed")
-        img_tel = img_tel[:n_img].copy()
+        img_tel = sub[img_tel[:n_img]].astype(np.int32)
         ell = ell[:n_img].copy()
         n_ell = n_ell[:n_img].copy()
     tel_pix_off, ped, gain, p16, scale = _calibration(seed, tel_cam, proc, cams)

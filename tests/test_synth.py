@@ -77,3 +77,10 @@ def test_pedestal_only_pixels_statistics():
     assert (wl.p16 == np.round(16 * wl.ped)).all()
     f = synth.window_fraction(False, 4, 5)
     np.testing.assert_array_equal(wl.scale, (1.0 / (16 * wl.gain * f)).astype(np.float32))
+
+
+def test_sub_array_workload():
+    sub = [0, 1, 2, 3, 4, 5, 6, 20, 21, 22]
+    wl = synth.make_workload(2, 50, telescopes=sub)
+    assert set(np.unique(wl.img_tel)) <= set(sub)
+    assert len(wl.tel_cam) == 69 and np.diff(wl.evt_off).min() >= 2
