@@ -115,7 +115,7 @@ def test_admission_waits_for_the_budget(env):
     bundles = make_bundles(wl, [600, 600, 600])
     need = max(b.wave_bytes for b in bundles)
     # room for one bundle at a time: the others are admitted as memory frees up
-    st = rta.rta_stream_create(ctx.handle, 0, int(need * 1.3) + (8 << 20), 4, 20000, 2000, mode, start, W, t_hi,
+    st = rta.rta_stream_create(ctx.handle, 0, int(need * 1.3) + (8 << 20), 4, 20000, 3000, mode, start, W, t_hi,
                                t_lo, core_nb, 0.5)
     try:
         res = serve(st, bundles, time.monotonic_ns())
