@@ -121,8 +121,9 @@ def make_bundle(n_events: int, seed: int, pinned: bool):
     return wl, host
 
 
-def cpu_baseline(wl, target_s: float = 15.0):
-    """The oracle, as it stands, on a bounded sample of the same bundle (all host cores)."""
+def cpu_baseline(wl, target_s: float = 10.0):
+    """The oracle, as it stands, on a bounded sample of the same bundle (all host
+    cores): whole passes over the bundle's first events until about target_s of work."""
     import oracle
     import synth
     cores = os.cpu_count() or 1
@@ -135,9 +136,167 @@ def cpu_baseline(wl, target_s: float = 15.0):
         if dt >= target_s / 4 or n >= wl.n_evt:
             break
         n = min(wl.n_evt, max(n * 2, int(n * target_s / 4 / max(dt, 1e-3))))
-    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {n} events ({sub.n_img} images, {sub.wave_bytes / 1e6:.0f} MB) of the bundle, "
-                      f"{dt:.1f} s on {cores} threads", "gbs": sub.wave_bytes / dt / 1e9}
+    reps, total = 1, dt
+    while total < target_s:
+        t0 = time.perf_counter()
+        oracle.reconstruct(sub, threads=cores)
+        total += time.perf_counter() - t0
+        reps += 1
+    return {"value": reps * n / total, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} passes over the first {n} events ({sub.n_img} images, {sub.wave_bytes / 1e6:.0f} MB) "
+                      f"of the bundle, {total:.1f} s on {cores} threads",
+            "gbs": reps * sub.wave_bytes / total / 1e9}
+
+
+def cam_codes(wl):
+    codes = np.zeros(16, np.float32)
+    for c, cam in wl.cams.items():
+        codes[c] = np.log10(cam.mirror_area) - 2.0
+    return codes
+
+
+def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
+    """Train the deep-sets surrogate with the library's kernels on mixed gamma/proton
+    events (setup), then time the learned path on the benchmark bundle
+    (image kernel + surrogate with geometric fallback) against the geometric
+    path, and compare both with the generated truth."""
+    import torch
+    import paper_1307_6489_gb300 as rta
+    import synth
+    from paper_1307_6489_gb300 import train
+    wave, wave_off, img_tel, evt_off, hil, ste = dev_b
+    sp = stream.cuda_stream
+    t_setup = time.perf_counter()
+    tw = synth.make_workload(3, n_train)
+    dwave = torch.from_numpy(tw.wave.view(np.int16)).cuda()
+    doff = torch.from_numpy(tw.wave_off).cuda()
+    dtel = torch.from_numpy(tw.img_tel).cuda()
+    devt = torch.from_numpy(tw.evt_off).cuda()
+    h_tr = train.reconstruct_images(ctx, dwave, doff, dtel, devt, proc)
+    logE = torch.from_numpy(np.log10(tw.truth[:, 0]).astype(np.float32)).cuda()
+    src = torch.from_numpy(tw.truth[:, 1:3].astype(np.float32).reshape(-1)).cuda()
+    gam = torch.from_numpy((tw.truth[:, 5] == 0).astype(np.uint8)).cuda()
+    tr = train.SurrogateTrainer(ctx, seed=1, cam_code=cam_codes(tw))
+    t_fit = time.perf_counter()
+    losses = tr.fit(h_tr, dtel, tw.evt_off, logE, src, gam, epochs=25, batch_events=1024, lr=2e-3, lr_end=1e-4)
+    fit_s = time.perf_counter() - t_fit
+    del dwave, h_tr
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    # timed: image kernel + learned reconstruction on the bundle
+    ev = torch.zeros(wl.n_evt * 32, dtype=torch.uint8, device=wave.device)
+    h = ctx.handle
+
+    def sur_step():
+        rta.rta_image_chain(h, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img,
+                            *proc, hil.data_ptr(), sp)
+        rta.rta_surrogate_infer(tr.model, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt,
+                                0.5, ev.data_ptr(), sp)
+
+    for _ in range(3):
+        sur_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sur_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sur_ms = e0.elapsed_time(e1) / steps
+    ctx.check(sp)
+    # accuracy on the bundle (gamma showers) against the geometric result of the same images
+    rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), sp)
+    torch.cuda.synchronize()
+    res = train.evaluate(rta.events_to_numpy(ev.cpu().numpy()), rta.stereo_to_numpy(ste.cpu().numpy()), wl.truth)
+    out = {"ms_per_step": sur_ms, "events_per_s": wl.n_evt / (sur_ms / 1e3), "train_events": n_train,
+           "train_steps": len(losses), "train_s": fit_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
+           "accuracy_on_bundle": res}
+    return out, tr
+
+
+def build_serving_pool(wl, wave_h, n_bundles, rng, max_events):
+    """Bundles of sub-array events cut from the benchmark bundle into their own
+    pinned host buffers: each takes a random event range and a random subset of
+    20-69 telescopes and keeps the events with at least two images left."""
+    import torch
+    pool = []
+    P = np.array([wl.cams[int(c)].n_pix * wl.cams[int(c)].n_samples for c in wl.tel_cam], np.int64)
+    for _ in range(n_bundles):
+        n = int(rng.integers(1000, min(max_events, wl.n_evt) + 1))
+        e0 = int(rng.integers(0, wl.n_evt - n + 1))
+        keep_tel = np.zeros(len(wl.tel_cam), bool)
+        keep_tel[rng.choice(len(wl.tel_cam), size=int(rng.integers(20, len(wl.tel_cam) + 1)), replace=False)] = True
+        imgs, evt_off = [], [0]
+        for e in range(e0, e0 + n):
+            ii = [i for i in range(wl.evt_off[e], wl.evt_off[e + 1]) if keep_tel[wl.img_tel[i]]]
+            if len(ii) >= 2:
+                imgs += ii
+                evt_off.append(len(imgs))
+        imgs = np.asarray(imgs, np.int64)
+        sizes = P[wl.img_tel[imgs]]
+        off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        total = int(sizes.sum())
+        t_wave = torch.empty(total, dtype=torch.int16, pin_memory=True)
+        w = t_wave.numpy().view(np.uint16)
+        for k, i in enumerate(imgs):
+            w[off[k]:off[k] + sizes[k]] = wave_h[wl.wave_off[i]:wl.wave_off[i] + sizes[k]]
+        pool.append(dict(t_wave=t_wave, wave=w, off=off, tel=wl.img_tel[imgs].astype(np.int32),
+                         evt=np.asarray(evt_off, np.int32), n_img=len(imgs), n_evt=len(evt_off) - 1,
+                         bytes=2 * total))
+    return pool
+
+
+def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894):
+    """Poisson arrivals of sub-array bundles at fixed aggregate rates through the
+    serving stream (continuous batching under an HBM budget); per rate the
+    sustained GB/s and the arrival-to-event-list latency percentiles."""
+    import torch
+    import paper_1307_6489_gb300 as rta
+    rng = np.random.default_rng(seed)
+    pool = build_serving_pool(wl, wave_h, 6, rng, 10000)
+    max_img = max(b["n_img"] for b in pool)
+    max_evt = max(b["n_evt"] for b in pool)
+    st = rta.rta_stream_create(ctx.handle, model or 0, 24 << 30, 4, max_img, max_evt, *proc, 0.5)
+    out = []
+    try:
+        for rate in rates:
+            sched, total, t = [], 0, time.monotonic_ns() + 50_000_000
+            while total < rate * 1e9 * duration_s:
+                b = pool[int(rng.integers(len(pool)))]
+                t += int(rng.exponential(b["bytes"] / (rate * 1e9)) * 1e9)
+                sched.append((t, b))
+                total += b["bytes"]
+            ev_all = torch.empty(sum(b["n_evt"] for _, b in sched) * 32, dtype=torch.uint8, pin_memory=True)
+            ev_np = ev_all.numpy()
+            pos, structs, tickets, arr = 0, [], [], []
+            for t_arr, b in sched:
+                bs = rta.Bundle(b["wave"].ctypes.data, b["wave"].size, b["off"].ctypes.data, b["tel"].ctypes.data,
+                                b["n_img"], b["evt"].ctypes.data, b["n_evt"], t_arr, ev_np[pos:].ctypes.data)
+                pos += b["n_evt"] * 32
+                structs.append(bs)
+            done = {}
+            k = 0
+            while len(done) < len(sched):
+                now = time.monotonic_ns()
+                while k < len(sched) and sched[k][0] <= now:
+                    tickets.append(rta.rta_stream_submit(st, structs[k]))
+                    arr.append(sched[k][0])
+                    k += 1
+                for j, tk in enumerate(tickets):
+                    if j not in done:
+                        d = rta.rta_stream_poll(st, tk)
+                        if d is not None:
+                            done[j] = d
+                time.sleep(0.0002)
+            lat = np.array([(done[j] - arr[j]) / 1e6 for j in range(len(sched))])
+            span = (max(done.values()) - arr[0]) / 1e9
+            out.append({"rate_gbs": rate, "bundles": len(sched), "bytes": int(total),
+                        "sustained_gbs": total / span / 1e9, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())})
+    finally:
+        rta.rta_stream_destroy(st)
+    return out, {"pool_bundles": len(pool), "pool_events": [b["n_evt"] for b in pool],
+                 "pool_gb": sum(b["bytes"] for b in pool) / 1e9}
 
 
 def run_reference(args, ws, rank):
@@ -182,6 +341,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--train-events", type=int, default=24000)
+    ap.add_argument("--serve-rates", default="0.5,2,8", help="aggregate arrival rates, GB/s")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--chain", default="", help="fixed image-kernel config 'variant,stages,ctas_per_sm'")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -339,6 +503,18 @@ def main():
     h2d = wl.wave_bytes + wl.n_img * 12 + (wl.n_evt + 1) * 4
     d2h = wl.n_img * HILLAS_BYTES + wl.n_evt * STEREO_BYTES
 
+    # ---------------- the learned path (setup: training) and the serving loop
+    sur, trainer, serving, pool_info = None, None, None, None
+    if not args.no_surrogate:
+        sur, trainer = surrogate_leg(ctx, wl, (wave, wave_off, img_tel, evt_off, hil, ste), proc, stream, args.steps,
+                                     args.train_events)
+    if not args.no_serving:
+        rates = [float(r) for r in args.serve_rates.split(",")]
+        serving, pool_info = serving_leg(ctx, trainer.model if trainer else None, wl, wave_h, proc, rates,
+                                         args.serve_seconds)
+    if trainer:
+        trainer.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
@@ -366,6 +542,11 @@ def main():
             "e2e": {"value": events_all / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "gbs": wl.wave_bytes * ws / e2e_s / 1e9,
                     "call": "rta_reconstruct_host (pinned host bundle)"},
+            "paths": {"geometric": {"ms_per_step": ms_per_step, "events_per_s": wl.n_evt / (ms_per_step / 1e3)},
+                      "surrogate": sur},
+            "serving": {"rates": serving, "pool": pool_info, "budget_gb": 24 * 1.073741824, "slots": 4,
+                        "model": "surrogate" if trainer else "geometric"} if serving else None,
+            "p99_bundle_latency_ms": serving[-1]["p99_ms"] if serving else None,
             "gpu_launches": 2 * args.steps,   # timed region: k_image_chain + k_stereo per step
             "clocks": clk,
             "cpu_baseline": cpu,
