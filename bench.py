@@ -167,7 +167,7 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
     wave, wave_off, img_tel, evt_off, hil, ste = dev_b
     sp = stream.cuda_stream
     t_setup = time.perf_counter()
-    tw = synth.make_workload(3, n_train)
+    tw = synth.make_workload(3, n_train, calib_seed=wl.seed)      # same array, same calibration
     dwave = torch.from_numpy(tw.wave.view(np.int16)).cuda()
     doff = torch.from_numpy(tw.wave_off).cuda()
     dtel = torch.from_numpy(tw.img_tel).cuda()
@@ -261,7 +261,12 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
     try:
         for rate in rates:
             sched, total, t = [], 0, time.monotonic_ns() + 50_000_000
-            while total < rate * 1e9 * duration_s:
+            if rate == float("inf"):      # capacity: a burst of 24 bundles arriving together
+                for _ in range(24):
+                    b = pool[int(rng.integers(len(pool)))]
+                    sched.append((t, b))
+                    total += b["bytes"]
+            while rate != float("inf") and total < rate * 1e9 * duration_s:
                 b = pool[int(rng.integers(len(pool)))]
                 t += int(rng.exponential(b["bytes"] / (rate * 1e9)) * 1e9)
                 sched.append((t, b))
@@ -290,7 +295,9 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
                 time.sleep(0.0002)
             lat = np.array([(done[j] - arr[j]) / 1e6 for j in range(len(sched))])
             span = (max(done.values()) - arr[0]) / 1e9
-            out.append({"rate_gbs": rate, "bundles": len(sched), "bytes": int(total),
+            out.append({"rate_gbs": rate if rate != float("inf") else "burst", "bundles": len(sched),
+                        "bytes": int(total),
+                        "offered_gbs": (total / ((arr[-1] - arr[0]) / 1e9) / 1e9) if arr[-1] > arr[0] else None,
                         "sustained_gbs": total / span / 1e9, "p50_ms": float(np.percentile(lat, 50)),
                         "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())})
     finally:
@@ -344,8 +351,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--train-events", type=int, default=24000)
-    ap.add_argument("--serve-rates", default="0.5,2,8", help="aggregate arrival rates, GB/s")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rates", default="0.5,2,8,inf", help="aggregate arrival rates, GB/s (inf: a burst)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--chain", default="", help="fixed image-kernel config 'variant,stages,ctas_per_sm'")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -546,15 +553,27 @@ def main():
                       "surrogate": sur},
             "serving": {"rates": serving, "pool": pool_info, "budget_gb": 24 * 1.073741824, "slots": 4,
                         "model": "surrogate" if trainer else "geometric"} if serving else None,
-            "p99_bundle_latency_ms": serving[-1]["p99_ms"] if serving else None,
+            "p99_bundle_latency_ms": next((r["p99_ms"] for r in serving if r["rate_gbs"] == 8.0), None)
+            if serving else None,
             "gpu_launches": 2 * args.steps,   # timed region: k_image_chain + k_stereo per step
             "clocks": clk,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_finite(line)), flush=True)
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _finite(x):
+    """NaN and infinities become null (strict JSON)."""
+    if isinstance(x, float):
+        return x if np.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: _finite(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_finite(v) for v in x]
+    return x
 
 
 def _kernel_hash():

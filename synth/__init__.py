@@ -233,14 +233,16 @@ def _calibration(seed, tel_cam, proc: Processing, cams):
 
 def make_workload(preset: int, n_events: int, seed: int | None = None, *, render: bool = True,
                   threads: int | None = None, wave_out: np.ndarray | None = None, flags: int = 0,
-                  proton_frac: float | None = None, telescopes=None) -> Workload:
+                  proton_frac: float | None = None, telescopes=None, calib_seed: int | None = None) -> Workload:
     """Plan (and optionally render) ``n_events`` events of a preset.
 
     ``wave_out`` may supply the destination buffer (e.g. a pinned host array) of
     at least the workload's sample count; ``flags`` bit0 turns off electronic
     noise and bit1 turns off night-sky background (used by tests);
     ``telescopes`` (array presets) restricts triggering to a sub-array of
-    telescope ids (the calibration table still covers the whole array)."""
+    telescope ids (the calibration table still covers the whole array);
+    ``calib_seed`` draws pedestals and gains from another seed, e.g. to make
+    more events for the same physical array as an earlier workload."""
     if preset not in PRESET_PROCESSING:
         raise ValueError(f"unknown preset {preset}")
     seed = BASE_SEED + preset if seed is None else int(seed)
@@ -279,7 +281,8 @@ def make_workload(preset: int, n_events: int, seed: int | None = None, *, render
         img_tel = sub[img_tel[:n_img]].astype(np.int32)
         ell = ell[:n_img].copy()
         n_ell = n_ell[:n_img].copy()
-    tel_pix_off, ped, gain, p16, scale = _calibration(seed, tel_cam, proc, cams)
+    tel_pix_off, ped, gain, p16, scale = _calibration(seed if calib_seed is None else int(calib_seed), tel_cam, proc,
+                                                      cams)
     img_evt = np.repeat(np.arange(len(evt_off) - 1, dtype=np.int32), np.diff(evt_off)).astype(np.int32)
     P = np.array([cams[int(tel_cam[t])].n_pix for t in img_tel], np.int64)
     S = np.array([cams[int(tel_cam[t])].n_samples for t in img_tel], np.int64)
