@@ -204,11 +204,28 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
     torch.cuda.synchronize()
     sur_ms = e0.elapsed_time(e1) / steps
     ctx.check(sp)
+
+    def infer_ms(bound):
+        # the learned reconstruction alone on the Hillas rows of the bundle
+        for _ in range(3):
+            rta.rta_surrogate_infer(tr.model, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(),
+                                    wl.n_evt, bound, ev.data_ptr(), sp)
+        e0.record(stream)
+        for _ in range(steps):
+            rta.rta_surrogate_infer(tr.model, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(),
+                                    wl.n_evt, bound, ev.data_ptr(), sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    infer_nofb_ms = infer_ms(1e30)
+    infer_full_ms = infer_ms(0.5)
     # accuracy on the bundle (gamma showers) against the geometric result of the same images
     rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), sp)
     torch.cuda.synchronize()
     res = train.evaluate(rta.events_to_numpy(ev.cpu().numpy()), rta.stereo_to_numpy(ste.cpu().numpy()), wl.truth)
-    out = {"ms_per_step": sur_ms, "events_per_s": wl.n_evt / (sur_ms / 1e3), "train_events": n_train,
+    out = {"ms_per_step": sur_ms, "events_per_s": wl.n_evt / (sur_ms / 1e3),
+           "infer_ms": infer_full_ms, "infer_without_fallback_ms": infer_nofb_ms, "train_events": n_train,
            "train_steps": len(losses), "train_s": fit_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
            "accuracy_on_bundle": res}
     return out, tr

@@ -164,6 +164,14 @@ int rta_register_array(rta_ctx* ctx, int n_tel, const int32_t* h_tel_cam, const 
  * Returns RTA_OK, RTA_E_DEVICE (bits in *status_bits, may be NULL) or RTA_E_CUDA. */
 int rta_check(rta_ctx* ctx, void* stream, uint32_t* status_bits);
 
+/* Failure-detection self-test (availability > 98 %, Sec. 2.1): a one-thread
+ * kernel waits, through the same bounded mbarrier wait as the image kernel, on a
+ * barrier nothing completes. After timeout_ms (1..10000) the wait gives up, the
+ * device status word gets RTA_DEV_TIMEOUT (read it with rta_check) and the
+ * kernel returns normally; the context stays usable. *waited_ns (may be NULL)
+ * receives the device-measured wait. Synchronises `stream`. */
+int rta_selftest_wait_timeout(rta_ctx* ctx, int timeout_ms, uint64_t* waited_ns, void* stream);
+
 /* Launch configuration of the fused image kernel (rta_image_chain and the
  * calls built on it). variant selects the tile shape (rta_chain_variant_info:
  * integrator warps per CTA and pixels per thread), n_stages the shared-memory

@@ -106,6 +106,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_skymap_read": ([P, i64, P], i32),
         "rta_stream_add_events": ([P, P, i64, i64, P], i32),
         "rta_stream_destroy": ([P], i32),
+        "rta_selftest_wait_timeout": ([P, i32, P, P], i32),
         "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
                                      P, P, P], i32),
     }
@@ -198,6 +199,13 @@ RTA_CHAIN_VARIANTS = 4
 class TuneEntry(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("n_stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("grid", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+def rta_selftest_wait_timeout(ctx: int, timeout_ms: int, stream: int = 0) -> int:
+    """Run the bounded-wait self-test; returns the device-measured wait in ns."""
+    w = ctypes.c_uint64()
+    _check(load().rta_selftest_wait_timeout(ctx, timeout_ms, ctypes.byref(w), stream))
+    return w.value
 
 
 def rta_set_chain_config(ctx: int, variant: int, n_stages: int, ctas_per_sm: int):

@@ -10,102 +10,44 @@
 // Row-major matrices throughout. Activations are stored in BF16 (the operand
 // type of the next GEMM); biases, the 4-wide output layer and every gradient
 // reduction are FP32.
-#include "rta_mlp.cuh"
+#include "rta_mlp_dev.cuh"
 
 namespace rta {
 
 // ------------------------------------------------------------------ features
-// One warp per event; mirrors the feature definition of the surrogate.
+// Eight lanes per event (four events per warp); also the first stage of inference.
 __global__ void __launch_bounds__(256) k_features(const FeatArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int sub = lane % SUR_EVT_LANES;
+    constexpr int GROUPS = 32 / SUR_EVT_LANES;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
     const int64_t n_img = a.n_img_dev ? min(*a.n_img_dev, a.n_img) : a.n_img;
-    for (int64_t e = warp; e < n_evt; e += nwarps) {
-        const int i0 = a.evt_off[e], i1 = a.evt_off[e + 1];
-        if (i0 < 0 || i1 < i0 || i1 > n_img) {
-            if (lane == 0) {
-                a.base[e] = make_float2(0.f, 0.f);
-                a.n_used[e] = -1;     // malformed event
-            }
-            continue;
+    // the whole warp iterates together (the group reductions shuffle across it)
+    for (int64_t e0 = int64_t(gwarp) * GROUPS; e0 < n_evt; e0 += nwarps * GROUPS) {
+        const int64_t e = e0 + lane / SUR_EVT_LANES;
+        int i0 = 0, n = 0;
+        bool ok = false;
+        if (e < n_evt) {
+            i0 = a.evt_off[e];
+            const int i1 = a.evt_off[e + 1];
+            ok = !(i0 < 0 || i1 < i0 || i1 > n_img);
+            n = ok ? i1 - i0 : 0;
         }
-        // used images, brightest two (size desc, index asc), weighted centroid. Sizes are
-        // positive, so their bit patterns order like the values; the low word prefers
-        // the lower index on ties.
-        unsigned long long k1 = 0ull, k2 = 0ull;
-        int cnt = 0;
-        float sw = 0.f, swx = 0.f, swy = 0.f;
-        for (int k = lane; k < i1 - i0; k += 32) {
-            const rta_hillas_t h = a.h[i0 + k];
-            const bool used = h.n_pix >= 3 && !(h.flags & (RTA_HF_EMPTY | RTA_HF_BAD_INPUT));
-            a.used[i0 + k] = used;
-            if (!used) continue;
-            ++cnt;
-            sw += h.size;
-            swx += h.size * h.x;
-            swy += h.size * h.y;
-            const unsigned long long key =
-                (static_cast<unsigned long long>(__float_as_uint(fmaxf(h.size, 0.f))) << 32) | (0xFFFFFFFFu - unsigned(k));
-            if (key > k1) { k2 = k1; k1 = key; }
-            else if (key > k2) { k2 = key; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, k1, o);
-            const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, k2, o);
-            // top two of {k1, k2, o1, o2} (all keys distinct or zero)
-            const unsigned long long hi = k1 > o1 ? k1 : o1;
-            const unsigned long long lo = k1 > o1 ? o1 : k1;
-            const unsigned long long sec = k1 > o1 ? k2 : o2;
-            k1 = hi;
-            k2 = lo > sec ? lo : sec;
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            sw += __shfl_xor_sync(0xffffffffu, sw, o);
-            swx += __shfl_xor_sync(0xffffffffu, swx, o);
-            swy += __shfl_xor_sync(0xffffffffu, swy, o);
-        }
-        const int idx1 = k1 ? int(0xFFFFFFFFu - unsigned(k1 & 0xFFFFFFFFull)) : -1;
-        const int idx2 = k2 ? int(0xFFFFFFFFu - unsigned(k2 & 0xFFFFFFFFull)) : -1;
-        float bx = 0.f, by = 0.f;
-        bool done = false;
-        if (cnt >= 2 && idx1 >= 0 && idx2 >= 0) {
-            const rta_hillas_t A = a.h[i0 + idx1], B = a.h[i0 + idx2];
-            const float s = sinf(B.psi - A.psi);
-            if (fabsf(s) >= SUR_BASE_MIN_SIN) {
-                float sa, ca, sb, cb2;
-                sincosf(A.psi, &sa, &ca);
-                sincosf(B.psi, &sb, &cb2);
-                const float k = ((B.x - A.x) * sb - (B.y - A.y) * cb2) / s;
-                bx = A.x + k * ca;
-                by = A.y + k * sa;
-                done = true;
-            }
-        }
-        if (!done && cnt >= 1) {
-            bx = swx / sw;
-            by = swy / sw;
-        }
-        if (lane == 0) {
+        float bx, by;
+        int cnt;
+        sur_event_baseline(a.h, i0, n, sub, a.used, bx, by, cnt);
+        if (e < n_evt && sub == 0) {
             a.base[e] = make_float2(bx, by);
-            a.n_used[e] = cnt;
+            a.n_used[e] = ok ? cnt : -1;      // -1: malformed event
         }
-        for (int k = lane; k < i1 - i0; k += 32) {
+        for (int k = sub; k < n; k += SUR_EVT_LANES) {
             const rta_hillas_t h = a.h[i0 + k];
-            const int tel = a.img_tel[i0 + k];
-            const bool tel_ok = tel >= 0 && tel < a.n_tel;
-            const float2 txy = tel_ok ? a.tel_xy[tel] : make_float2(0.f, 0.f);
-            const float code = tel_ok ? a.cam_code[a.tel_cam[tel]] : 0.f;
-            const float dx = h.x - bx, dy = h.y - by;
-            float s2, c2;
-            sincosf(2.f * h.psi, &s2, &c2);
-            const float f[SUR_XPAD] = {log10f(fmaxf(h.size, 1e-3f)), dx, dy, h.length, h.width, c2, s2,
-                                       h.time_grad * 0.1f, sqrtf(dx * dx + dy * dy), code, txy.x * 1e-3f,
-                                       txy.y * 1e-3f, 0.f, 0.f, 0.f, 0.f};
-            __nv_bfloat16* xr = a.X + int64_t(i0 + k) * SUR_XPAD;
-#pragma unroll
-            for (int j = 0; j < SUR_XPAD; j += 2)
-                *reinterpret_cast<__nv_bfloat162*>(xr + j) = __floats2bfloat162_rn(f[j], f[j + 1]);
+            __nv_bfloat162 x[SUR_XPAD / 2];
+            sur_image_features(h, a.img_tel[i0 + k], a.tel_cam, a.tel_xy, a.cam_code, a.n_tel, bx, by, x);
+            uint4* xr = reinterpret_cast<uint4*>(a.X + int64_t(i0 + k) * SUR_XPAD);
+            xr[0] = make_uint4(bf2_bits(x[0]), bf2_bits(x[1]), bf2_bits(x[2]), bf2_bits(x[3]));
+            xr[1] = make_uint4(bf2_bits(x[4]), bf2_bits(x[5]), bf2_bits(x[6]), bf2_bits(x[7]));
         }
     }
 }
@@ -115,14 +57,6 @@ __global__ void __launch_bounds__(256) k_features(const FeatArgs a) {
 // [K x M] (TA = true); B is [K x N] (TB = false) or stored as [N x K] (TB = true).
 // Tile 64 x 64 x 32, 4 warps of 32 x 32, mma.sync.m16n8k16 BF16 -> FP32.
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
@@ -289,23 +223,38 @@ __global__ void __launch_bounds__(SUR_H) k_pool_bwd(const PoolArgs a) {
 }
 
 // ------------------------------------------------------------------ output layer, loss, outputs
-// y[e] = G[e] . V2 + c2 (4 outputs), one warp per event, FP32 dot products.
+// y[e] = G[e] . V2 + c2 (4 outputs) on the tensor cores: one warp per 16
+// events, 16 k-steps in ascending order, V2 widened to 8 zero-padded columns.
 __global__ void __launch_bounds__(256) k_head(const HeadArgs a) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
-    for (int64_t e = warp; e < n_evt; e += nwarps) {
-        float y[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k = lane; k < SUR_G; k += 32) {
-            const float gk = __bfloat162float(a.G[e * SUR_G + k]);
-#pragma unroll
-            for (int o = 0; o < 4; ++o) y[o] += gk * __bfloat162float(a.V2b[k * 4 + o]);
+    for (int64_t r0 = int64_t(warp) * 16; r0 < n_evt; r0 += nwarps * 16) {
+        const int64_t ra = r0 + gq, rb = r0 + gq + 8;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+        for (int ks = 0; ks < SUR_G / 16; ++ks) {
+            const int k = 16 * ks + 2 * tq;
+            uint32_t af[4], bf[2];
+            af[0] = ra < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + ra * SUR_G + k) : 0u;
+            af[1] = rb < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + rb * SUR_G + k) : 0u;
+            af[2] = ra < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + ra * SUR_G + k + 8) : 0u;
+            af[3] = rb < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + rb * SUR_G + k + 8) : 0u;
+            head_b_fragment(a.V2b, ks, gq, tq, bf);
+            mma_bf16(acc, af, bf);
         }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            y[o] = warp_sum(y[o]) + a.c2[o];
+        if (tq < 2) {
+            const int c = 2 * tq;
+            if (ra < n_evt) {
+                a.Y[ra * 4 + c] = acc[0] + a.c2[c];
+                a.Y[ra * 4 + c + 1] = acc[1] + a.c2[c + 1];
+            }
+            if (rb < n_evt) {
+                a.Y[rb * 4 + c] = acc[2] + a.c2[c];
+                a.Y[rb * 4 + c + 1] = acc[3] + a.c2[c + 1];
+            }
         }
-        if (lane < 4) a.Y[e * 4 + lane] = y[lane];
     }
 }
 
@@ -393,24 +342,8 @@ __global__ void k_head_bwd_dv2(const HeadArgs a) {
 __global__ void k_outputs(const OutArgs a) {
     const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n_evt; e += int64_t(gridDim.x) * blockDim.x) {
-        const float* y = a.Y + e * 4;
-        const float2 b = a.base[e];
-        rta_event_t r = {};
-        r.log_energy = y[0];
-        r.dir_x = b.x + y[1];
-        r.dir_y = b.y + y[2];
-        r.gammaness = 1.f / (1.f + expf(-y[3]));
-        r.n_used = a.n_used[e];
-        r.base_x = b.x;
-        r.base_y = b.y;
-        if (a.n_used[e] < 2) {
-            r.flags |= RTA_EF_NO_DIRECTION;        // the geometric method is undefined as well
-        } else if (sqrtf(y[1] * y[1] + y[2] * y[2]) > a.fallback_deg) {
-            r.flags |= RTA_EF_FALLBACK;
-            const unsigned slot = atomicAdd(a.n_fallback, 1u);
-            a.fallback_idx[slot] = int(e);
-        }
-        a.out[e] = r;
+        const float y[4] = {a.Y[e * 4 + 0], a.Y[e * 4 + 1], a.Y[e * 4 + 2], a.Y[e * 4 + 3]};
+        sur_emit_event(a, e, y, a.base[e], a.n_used[e]);
     }
 }
 

@@ -728,6 +728,22 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
     return RTA_OK;
 }
 
+int rta_selftest_wait_timeout(rta_ctx* c, int timeout_ms, uint64_t* waited_ns, void* stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (timeout_ms < 1 || timeout_ms > 10000) return fail(RTA_E_INVALID, "timeout_ms %d outside 1..10000", timeout_ms);
+    unsigned long long* d_w = nullptr;
+    CUDA_TRY(cudaMalloc(&d_w, sizeof(unsigned long long)));
+    cudaError_t e = rta::launch_wait_selftest(c->d_status, uint64_t(timeout_ms) * 1000000ull, d_w, (cudaStream_t)stream);
+    unsigned long long w = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&w, d_w, sizeof w, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(d_w);
+    if (e != cudaSuccess) return fail(RTA_E_CUDA, "self-test: %s", cudaGetErrorString(e));
+    if (waited_ns) *waited_ns = w;
+    return RTA_OK;
+}
+
 struct rta_graph {
     rta_ctx* ctx = nullptr;
     cudaGraph_t graph = nullptr;

@@ -87,16 +87,20 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the phase of `parity` to complete. Gives up after the timeout or as
+// Wait for the phase of `parity` to complete. Gives up after timeout_ns or as
 // soon as *abort becomes non-zero; returns false then.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
-        if (global_ns() - t0 > RTA_WAIT_TIMEOUT_NS) return false;
+        if (global_ns() - t0 > timeout_ns) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    return mbar_wait_ns(bar, parity, abort, RTA_WAIT_TIMEOUT_NS);
 }
 
 // One bulk copy global -> shared through the TMA engine, completing `bytes` of

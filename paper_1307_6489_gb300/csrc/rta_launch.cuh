@@ -78,6 +78,8 @@ cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem,
 cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_hillas(const HillasArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_stereo(const StereoArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned int* status, uint64_t timeout_ns, unsigned long long* waited_ns,
+                                 cudaStream_t s);
 // stores a message for rta_last_error() on the calling thread
 void set_last_error(const char* msg);
 // sky map and geometric event rows (k_skymap.cu)

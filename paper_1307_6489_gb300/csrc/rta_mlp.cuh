@@ -110,6 +110,19 @@ struct OutArgs {
     const rta_stereo_t* geo;
 };
 
+// Fused inference after k_features: f carries the event offsets and the
+// features, used flags, baselines and used counts that k_features wrote; the
+// output block's Y/base are not read.
+struct InferArgs {
+    FeatArgs f;
+    const __nv_bfloat16* pb;   // BF16 parameter twin (internal layout)
+    const float* p;            // FP32 master (biases)
+    __nv_bfloat16* H2;         // [n_img x 128] per-telescope network output (workspace)
+    int tile_events;           // events per tile of k_event, 1..32
+    int64_t n_tiles;
+    OutArgs o;
+};
+
 struct AdamArgs {
     int64_t n;
     float* p;
@@ -131,5 +144,8 @@ cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_
                           float* out, cudaStream_t s);
 cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
+// k_phi then k_event (one CTA per SM, n_sm of them at most)
+cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s);
+constexpr int INFER_MAX_TILE_EVENTS = 32;
 
 }  // namespace rta

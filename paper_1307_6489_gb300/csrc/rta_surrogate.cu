@@ -46,6 +46,7 @@ struct rta_model {
     float* cam_code = nullptr;       // per camera id
     float* split_ws = nullptr;
     int64_t step = 0;
+    int n_sm = 1;
     // workspace
     int64_t cap_img = 0, cap_evt = 0;
     __nv_bfloat16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dZ1 = nullptr, *dZ2 = nullptr;
@@ -173,7 +174,7 @@ int forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     f.base = md->base;
     f.n_used = md->n_used;
     if (n_img > 0) S_TRY(cudaMemsetAsync(md->X, 0, sizeof(__nv_bfloat16) * n_img * SUR_XPAD, s));
-    S_TRY(rta::launch_features(f, blocks_for(n_evt, 8), s));
+    S_TRY(rta::launch_features(f, blocks_for(n_evt, 32), s));
     const __nv_bfloat16* pb = md->pb;
     if (n_img > 0) {
         if ((rc = gemm(md->X, SUR_XPAD, false, pb + rta::OFF_W1, SUR_H, false, n_img, SUR_H, SUR_XPAD,
@@ -200,7 +201,7 @@ int forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     ha.V2b = pb + rta::OFF_V2;
     ha.c2 = md->p + rta::OFF_C2;
     ha.Y = md->Y;
-    S_TRY(rta::launch_head(ha, blocks_for(n_evt, 8), s));
+    S_TRY(rta::launch_head(ha, blocks_for(n_evt, 128), s));
     return RTA_OK;
 }
 
@@ -263,6 +264,8 @@ int rta_surrogate_create(rta_ctx* ctx, uint64_t seed, const float* h_cam_code, r
     rta_model* md = new rta_model();
     md->ctx = ctx;
     md->device = dev;
+    if (cudaDeviceGetAttribute(&md->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || md->n_sm < 1)
+        md->n_sm = 1;
     const size_t n = rta::N_PARAM_INTERNAL;
     bool ok = cudaMalloc(&md->p, n * 4) == cudaSuccess && cudaMalloc(&md->pb, n * 2) == cudaSuccess &&
               cudaMalloc(&md->m, n * 4) == cudaSuccess && cudaMalloc(&md->v, n * 4) == cudaSuccess &&
@@ -447,19 +450,37 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     if (!d_out) return sfail(RTA_E_INVALID, "NULL output");
     if (!(fallback_deg > 0.f)) return sfail(RTA_E_INVALID, "fallback bound must be > 0");
     cudaStream_t s = (cudaStream_t)stream;
-    if ((rc = forward(md, d_h, d_img_tel, n_img, d_evt_off, n_evt, s))) return rc;
-    S_TRY(cudaMemsetAsync(md->n_fallback, 0, sizeof(unsigned int), s));
-    rta::OutArgs oa = {};
+    rta::InferArgs ia = {};
+    ia.f.h = d_h;
+    ia.f.img_tel = d_img_tel;
+    ia.f.evt_off = d_evt_off;
+    ia.f.n_img = n_img;
+    ia.f.n_evt = n_evt;
+    if ((rc = rta::surrogate_ctx_tables(md->ctx, &ia.f.tel_cam, &ia.f.tel_xy, &ia.f.n_tel, nullptr))) return rc;
+    ia.f.cam_code = md->cam_code;
+    ia.f.X = md->X;
+    ia.f.used = md->used;
+    ia.f.base = md->base;
+    ia.f.n_used = md->n_used;
+    ia.pb = md->pb;
+    ia.p = md->p;
+    ia.H2 = md->H2;
+    // one persistent CTA per SM; tiles of up to 32 events, sized so that every
+    // CTA gets the same number of tiles
+    const int64_t per_round = int64_t(md->n_sm) * rta::INFER_MAX_TILE_EVENTS;
+    const int64_t rounds = (n_evt + per_round - 1) / per_round;
+    ia.tile_events = int((n_evt + md->n_sm * rounds - 1) / (md->n_sm * rounds));
+    ia.n_tiles = (n_evt + ia.tile_events - 1) / ia.tile_events;
+    rta::OutArgs& oa = ia.o;
     oa.n_evt = n_evt;
-    oa.Y = md->Y;
-    oa.base = md->base;
-    oa.n_used = md->n_used;
     oa.fallback_deg = fallback_deg;
     oa.out = d_out;
     oa.n_fallback = md->n_fallback;
     oa.fallback_idx = md->fallback_idx;
     oa.geo = md->geo;
-    S_TRY(rta::launch_outputs(oa, blocks_for(n_evt, 256), false, s));
+    S_TRY(cudaMemsetAsync(md->n_fallback, 0, sizeof(unsigned int), s));
+    S_TRY(rta::launch_features(ia.f, blocks_for(n_evt, 32), s));
+    S_TRY(rta::launch_infer(ia, md->n_sm, s));
     // the geometric intersection only for the events that need it
     if ((rc = rta::surrogate_stereo_list(md->ctx, d_h, d_img_tel, n_img, d_evt_off, n_evt, md->fallback_idx,
                                          md->n_fallback, md->geo, s)))

@@ -2,6 +2,8 @@
 degenerate images, saturated samples, the generic (non-specialised) integration
 paths at the maximum camera size, argument checks, and the full-size bundle on
 sampled outputs."""
+import time
+
 import numpy as np
 import pytest
 
@@ -237,3 +239,22 @@ def test_full_size_bundle_sampled():
                  st["dir_y"][events][ok] - ref["stereo"][ok, S["dir_y"]])
     assert np.percentile(d, 99) <= DIR_DEG
     ctx.close()
+
+
+def test_bounded_device_wait_times_out_and_the_context_survives(arr):
+    """Failure detection without a GPU fault: a wait that nothing completes gives
+    up after its limit, reports RTA_DEV_TIMEOUT, and the next launch works."""
+    wl, ctx = arr
+    t0 = time.perf_counter()
+    waited = rta.rta_selftest_wait_timeout(ctx.handle, 200)
+    dt = time.perf_counter() - t0
+    assert 0.2e9 <= waited < 2.0e9 and dt < 5.0
+    with pytest.raises(rta.RtaError) as e:
+        ctx.check()
+    assert e.value.code == rta.RTA_E_DEVICE and e.value.bits == rta.RTA_DEV_TIMEOUT
+    dev = Dev(wl)
+    out = dev.hillas_buf()
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, out)
+    assert ctx.check() == 0
+    assert (hillas_rows(out, wl.n_img)["n_pix"] > 0).any()

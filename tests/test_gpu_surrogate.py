@@ -190,3 +190,58 @@ def test_trained_network_gains_over_the_geometric_reconstruction():
     assert res["r68_ratio"] < 1.5
     tr.close()
     ctx.close()
+
+
+def _infer_and_forward(s, a, b, merge=1, break_offsets=False):
+    """Events [a, b) of the parity workload through the fused inference kernel and
+    through the layer-by-layer forward pass; merge > 1 joins that many consecutive
+    events into one (events of hundreds of images), break_offsets plants
+    malformed offsets."""
+    wl, d = s["wl"], s["d"]
+    off = wl.evt_off[a:b + 1:merge].astype(np.int64)
+    if off[-1] != wl.evt_off[b]:
+        off = np.append(off, wl.evt_off[b])
+    i0 = int(off[0])
+    off = (off - i0).astype(np.int32)
+    n_img, n_evt = int(off[-1]), len(off) - 1
+    if break_offsets:
+        off[min(3, n_evt)] = -5                    # events 2 and 3 malformed
+        off[min(10, n_evt)] = n_img + 100          # events 9 and 10 malformed
+    h = d["h"][i0 * 16:].contiguous()
+    tel = d["img_tel"][i0:].contiguous()
+    doff = torch.from_numpy(off).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    y = torch.zeros(n_evt * 4, dtype=torch.float32, device="cuda")
+    bb = torch.zeros(n_evt * 2, dtype=torch.float32, device="cuda")
+    rta.rta_surrogate_forward(s["model"], h.data_ptr(), tel.data_ptr(), n_img, doff.data_ptr(), n_evt, y.data_ptr(),
+                              bb.data_ptr(), stream)
+    out = torch.zeros(n_evt * 32, dtype=torch.uint8, device="cuda")
+    rta.rta_surrogate_infer(s["model"], h.data_ptr(), tel.data_ptr(), n_img, doff.data_ptr(), n_evt, 1e3,
+                            out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    return rta.events_to_numpy(out.cpu().numpy()), y.cpu().numpy().reshape(-1, 4), bb.cpu().numpy().reshape(-1, 2)
+
+
+@pytest.mark.parametrize("case", ["all", "one", "ragged", "hundreds_of_images", "malformed"])
+def test_fused_inference_equals_the_layer_by_layer_forward(setup, case):
+    """The fused kernel keeps every expression and summation order of the
+    training-path kernels, so its outputs equal theirs bit for bit."""
+    s = setup
+    n = s["wl"].n_evt
+    a, b, merge, brk = {"all": (0, n, 1, False), "one": (7, 8, 1, False), "ragged": (5, 5 + 211, 1, False),
+                        "hundreds_of_images": (0, n, 25, False), "malformed": (0, 64, 1, True)}[case]
+    ev, y, base = _infer_and_forward(s, a, b, merge, brk)
+    np.testing.assert_array_equal(ev["log_energy"].view(np.uint32), y[:, 0].view(np.uint32))
+    np.testing.assert_array_equal(ev["base_x"].view(np.uint32), base[:, 0].view(np.uint32))
+    np.testing.assert_array_equal(ev["base_y"].view(np.uint32), base[:, 1].view(np.uint32))
+    np.testing.assert_array_equal(ev["dir_x"], base[:, 0] + y[:, 1])
+    np.testing.assert_array_equal(ev["dir_y"], base[:, 1] + y[:, 2])
+    np.testing.assert_allclose(ev["gammaness"], 1 / (1 + np.exp(-y[:, 3].astype(np.float64))), rtol=0, atol=1e-6)
+    assert ((ev["flags"] & rta.RTA_EF_FALLBACK) == 0).all()
+    np.testing.assert_array_equal((ev["flags"] & rta.RTA_EF_NO_DIRECTION) != 0, ev["n_used"] < 2)
+    if case == "malformed":
+        assert (ev["n_used"][[2, 3, 9, 10]] == -1).all() and (ev["n_used"] >= 0).sum() == len(ev["n_used"]) - 4
+    elif merge == 1:
+        np.testing.assert_array_equal(ev["n_used"], s["n_used"][a:b])
+    else:
+        assert ev["n_used"].max() > 64
