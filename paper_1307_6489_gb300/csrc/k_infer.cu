@@ -1,27 +1,28 @@
 // Inference of the deep-sets surrogate (energy, direction offset and
-// gamma/hadron score next to the geometric direction, Sec. 4.1), after
-// k_features (per-event baseline, per-image BF16 features and used flags,
-// shared with training):
+// gamma/hadron score next to the geometric direction, Sec. 4.1), in two kernels:
 //
-//   k_phi    image-parallel per-telescope network, 16 -> 128 -> 128 (ReLU) on
-//            the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
-//            accumulators). One warp owns 16 image rows: the first layer's
-//            accumulators become the second layer's A fragments in registers;
-//            the weights sit in shared memory and reach the MMA by
-//            ldmatrix.trans. No block barrier after the weights are staged.
-//            Unused images get +0 rows.
-//   k_event  one persistent CTA per SM walks tiles of up to 32 consecutive
-//            events: it stages the tile's rows of the per-telescope output in
-//            shared memory, pools them (sum / 40 and mean), runs the event
-//            network 256 -> 256 (ReLU, weights staged once per CTA) and
-//            256 -> 4 on the tensor cores, and writes the outputs and the
-//            fallback list for the geometric intersection.
+//   k_tel    one warp per four events, no block barrier after the weights are
+//            staged: per-event baseline and used images (eight lanes per
+//            event), per-image features, the per-telescope network
+//            16 -> 128 -> 128 (ReLU) on the tensor cores (mma.sync m16n8k16,
+//            BF16 operands, FP32 accumulators) sixteen image rows at a time --
+//            the first layer's accumulators become the second layer's A
+//            fragments in registers, the weights reach the MMA from shared
+//            memory by ldmatrix.trans -- and the sum / mean pooling in
+//            registers. Writes the pooled vectors, baselines and used counts.
+//   k_event  one persistent CTA per SM walks tiles of up to 32 events: the
+//            event network 256 -> 256 (ReLU, weights staged once per CTA) and
+//            256 -> 4 on the tensor cores, then the outputs and the fallback
+//            list for the geometric intersection. The next tile's pooled rows
+//            arrive by cp.async while the current one computes.
 //
 // Every stage evaluates the same expressions in the same order as the
-// layer-by-layer kernels of the training path (k_mlp.cu): the k-order of each
-// MMA accumulation, the image order of the pooling sums (a +0 row leaves a sum
-// unchanged where the pooling kernel skips the image), the output head. The
-// outputs therefore equal those of the training-path forward bit for bit.
+// layer-by-layer kernels of the training path (k_features, k_gemm, k_pool,
+// k_head in k_mlp.cu): the features and the eight-lane event reductions, the
+// k-order of each MMA accumulation, the image order of the pooling sums (an
+// unused image adds +0 here where the pooling kernel skips it, which leaves a
+// sum unchanged). The outputs therefore equal those of the training-path
+// forward bit for bit.
 #include <algorithm>
 
 #include "rta_mlp_dev.cuh"
@@ -29,23 +30,32 @@
 namespace rta {
 namespace {
 
-constexpr int FE = 32;              // events per tile at most (one warp-wide scan)
-constexpr int RT = 128;             // staged per-telescope rows per pass
-constexpr int NT = 256;             // threads per k_event CTA
-constexpr int PHI_WARPS = 4;        // warps per k_phi CTA
+constexpr int FE = 32;              // events per k_event tile at most
+constexpr int NT = 256;             // threads per CTA (both kernels)
+constexpr int EPW = 32 / SUR_EVT_LANES;   // events per k_tel warp iteration
+constexpr int LDX = 24;             // feature row stride (16 + 8: conflict-free fragment loads)
 constexpr int LDH = SUR_H + 8;      // hidden row stride (conflict-free ldmatrix / fragment loads)
 constexpr int LDV = SUR_G + 8;      // pooled / event-network row stride
 
+// k_tel shared memory: weights, then per warp a 16-row feature tile and a
+// 16-row hidden tile
+constexpr size_t TS_W1 = 0;                                      // bf16 [16][LDH]
+constexpr size_t TS_W2 = TS_W1 + size_t(SUR_XPAD) * LDH * 2;     // bf16 [128][LDH]
+constexpr size_t TS_B = TS_W2 + size_t(SUR_H) * LDH * 2;         // f32 b1[128], b2[128]
+constexpr size_t TS_WARP = TS_B + 2 * SUR_H * 4;
+constexpr size_t TS_X_BYTES = 16 * LDX * 2;
+constexpr size_t TS_H_BYTES = 16 * LDH * 2;
+constexpr size_t TS_TOTAL = TS_WARP + (NT / 32) * (TS_X_BYTES + TS_H_BYTES);
+static_assert(2 * TS_TOTAL <= 227 * 1024, "two k_tel CTAs per SM");
+static_assert(EPW == 4, "k_tel assigns rows to four events per warp");
+
+// k_event shared memory
 constexpr size_t SM_V1 = 0;                                      // bf16 [256 k][LDV]: V1 as stored
-constexpr size_t SM_H = SM_V1 + size_t(SUR_G) * LDV * 2;         // bf16 [RT][LDH] staged rows; P, G later
-constexpr size_t SM_PACC = SM_H + size_t(RT) * LDH * 2;          // f32 [32][128] pooling sums
-constexpr size_t SM_V2 = SM_PACC + size_t(FE) * SUR_H * 4;       // bf16 [256][4]
+constexpr size_t SM_P = SM_V1 + size_t(SUR_G) * LDV * 2;         // bf16 [2][32][LDV] pooled rows, double-buffered
+constexpr size_t SM_G = SM_P + 2 * size_t(FE) * LDV * 2;         // bf16 [32][LDV]
+constexpr size_t SM_V2 = SM_G + size_t(FE) * LDV * 2;            // bf16 [256][4]
 constexpr size_t SM_Y = SM_V2 + size_t(SUR_G) * 4 * 2;           // f32 [32][4]
-constexpr size_t SM_ROWB = SM_Y + size_t(FE) * 4 * 4;            // int64 [33] first row of each event
-constexpr size_t SM_LO = SM_ROWB + size_t(FE + 1) * 8;           // int [32] first image
-constexpr size_t SM_TOTAL = SM_LO + size_t(FE) * 4;
-constexpr size_t SM_G_OFF = size_t(FE) * LDV * 2;                // G follows P inside the staged-row buffer
-static_assert(2 * size_t(FE) * LDV * 2 <= size_t(RT) * LDH * 2, "P and G must fit the staged-row buffer");
+constexpr size_t SM_TOTAL = SM_Y + size_t(FE) * 4 * 4;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
@@ -90,6 +100,18 @@ __device__ __forceinline__ void ldsm_b_trans(uint32_t (&b)[4], const __nv_bfloat
                  : "r"(addr));
 }
 
+template <typename T>
+__device__ __forceinline__ T sel4(int g, T v0, T v1, T v2, T v3) {
+    return g == 0 ? v0 : g == 1 ? v1 : g == 2 ? v2 : v3;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void zero_acc(float (&acc)[2][4][4]) {
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -101,113 +123,215 @@ __device__ __forceinline__ void zero_acc(float (&acc)[2][4][4]) {
 
 }  // namespace
 
-// ------------------------------------------------------------------ k_phi
-__global__ void __launch_bounds__(PHI_WARPS * 32, 3) k_phi(const InferArgs a) {
-    __shared__ __align__(16) __nv_bfloat16 W1s[SUR_XPAD][LDH];
-    __shared__ __align__(16) __nv_bfloat16 W2s[SUR_H][LDH];
-    __shared__ float b1s[SUR_H], b2s[SUR_H];
+
+// ------------------------------------------------------------------ k_tel
+__global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(sm + TS_W1);
+    __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(sm + TS_W2);
+    float* b1s = reinterpret_cast<float*>(sm + TS_B);
+    float* b2s = b1s + SUR_H;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+    __nv_bfloat16* Xw = reinterpret_cast<__nv_bfloat16*>(sm + TS_WARP + warp * (TS_X_BYTES + TS_H_BYTES));
+    __nv_bfloat16* Hw = reinterpret_cast<__nv_bfloat16*>(sm + TS_WARP + warp * (TS_X_BYTES + TS_H_BYTES) + TS_X_BYTES);
     {
         const uint4* w1 = reinterpret_cast<const uint4*>(a.pb + OFF_W1);
         const uint4* w2 = reinterpret_cast<const uint4*>(a.pb + OFF_W2);
-        for (int i = tid; i < SUR_XPAD * SUR_H / 8; i += PHI_WARPS * 32)
-            *reinterpret_cast<uint4*>(&W1s[i / (SUR_H / 8)][8 * (i % (SUR_H / 8))]) = w1[i];
-        for (int i = tid; i < SUR_H * SUR_H / 8; i += PHI_WARPS * 32)
-            *reinterpret_cast<uint4*>(&W2s[i / (SUR_H / 8)][8 * (i % (SUR_H / 8))]) = w2[i];
-        for (int i = tid; i < SUR_H; i += PHI_WARPS * 32) {
+        for (int i = tid; i < SUR_XPAD * SUR_H / 8; i += NT)
+            *reinterpret_cast<uint4*>(W1s + (i / (SUR_H / 8)) * LDH + 8 * (i % (SUR_H / 8))) = w1[i];
+        for (int i = tid; i < SUR_H * SUR_H / 8; i += NT)
+            *reinterpret_cast<uint4*>(W2s + (i / (SUR_H / 8)) * LDH + 8 * (i % (SUR_H / 8))) = w2[i];
+        for (int i = tid; i < SUR_H; i += NT) {
             b1s[i] = a.p[OFF_B1 + i];
             b2s[i] = a.p[OFF_B2 + i];
         }
     }
     __syncthreads();
-    const int64_t n_img = a.f.n_img;
-    const int64_t n_units = (n_img + 15) / 16;
-    for (int64_t u = int64_t(blockIdx.x) * PHI_WARPS + warp; u < n_units; u += int64_t(gridDim.x) * PHI_WARPS) {
-        const int64_t ra = u * 16 + gq, rb = ra + 8;
-        const bool va = ra < n_img, vb = rb < n_img;
-        // A fragment of the features (one k-step)
-        uint32_t ax[4];
-        {
-            const uint32_t* xa = reinterpret_cast<const uint32_t*>(a.f.X + ra * SUR_XPAD) + tq;
-            const uint32_t* xb = reinterpret_cast<const uint32_t*>(a.f.X + rb * SUR_XPAD) + tq;
-            ax[0] = va ? xa[0] : 0u;
-            ax[1] = vb ? xb[0] : 0u;
-            ax[2] = va ? xa[4] : 0u;
-            ax[3] = vb ? xb[4] : 0u;
+    const FeatArgs& f = a.f;
+    const int64_t n_evt = f.n_evt, n_img = f.n_img;
+    const int sub = lane % SUR_EVT_LANES, grp = lane / SUR_EVT_LANES;
+    const int64_t nwarps = (int64_t(gridDim.x) * NT) >> 5;
+    for (int64_t e0 = (int64_t(blockIdx.x) * (NT / 32) + warp) * EPW; e0 < n_evt; e0 += nwarps * EPW) {
+        // ---- per-event prologue, eight lanes per event (as k_features)
+        const int64_t e = e0 + grp;
+        int i0 = 0, n = 0;
+        bool ok = false;
+        if (e < n_evt) {
+            i0 = f.evt_off[e];
+            const int i1 = f.evt_off[e + 1];
+            ok = !(i0 < 0 || i1 < i0 || i1 > n_img);
+            n = ok ? i1 - i0 : 0;
         }
-        const bool ua = va && a.f.used[ra], ub = vb && a.f.used[rb];
-        // layer 1: 16 n8 tiles
-        float acc1[16][4];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
-#pragma unroll
-        for (int jp = 0; jp < 8; ++jp) {
-            uint32_t b[4];
-            ldsm_b_trans(b, &W1s[0][0], LDH, 0, 16 * jp, lane);
-            const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
-            mma_bf16(acc1[2 * jp], ax, b0);
-            mma_bf16(acc1[2 * jp + 1], ax, b1);
+        float bx, by;
+        int cnt;
+        sur_event_baseline(f.h, i0, n, sub, nullptr, bx, by, cnt);
+        if (e < n_evt && sub == 0) {
+            f.base[e] = make_float2(bx, by);
+            f.n_used[e] = ok ? cnt : -1;
         }
-        // ReLU(acc + b1) in BF16, rearranged as the A fragments of layer 2
-        uint32_t ah[8][4];
+        // the four events' rows, in order
+        int off[EPW + 1], ig[EPW], cg[EPW];
+        float bxg[EPW], byg[EPW];
+        off[0] = 0;
 #pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-            const int n0 = 16 * ks + 2 * tq, n1 = n0 + 8;
-            const float* c0 = acc1[2 * ks];
-            const float* c1 = acc1[2 * ks + 1];
-            ah[ks][0] = bf2_bits(__floats2bfloat162_rn(fmaxf(c0[0] + b1s[n0], 0.f), fmaxf(c0[1] + b1s[n0 + 1], 0.f)));
-            ah[ks][1] = bf2_bits(__floats2bfloat162_rn(fmaxf(c0[2] + b1s[n0], 0.f), fmaxf(c0[3] + b1s[n0 + 1], 0.f)));
-            ah[ks][2] = bf2_bits(__floats2bfloat162_rn(fmaxf(c1[0] + b1s[n1], 0.f), fmaxf(c1[1] + b1s[n1 + 1], 0.f)));
-            ah[ks][3] = bf2_bits(__floats2bfloat162_rn(fmaxf(c1[2] + b1s[n1], 0.f), fmaxf(c1[3] + b1s[n1 + 1], 0.f)));
+        for (int g = 0; g < EPW; ++g) {
+            off[g + 1] = off[g] + __shfl_sync(0xffffffffu, n, SUR_EVT_LANES * g);
+            ig[g] = __shfl_sync(0xffffffffu, i0, SUR_EVT_LANES * g);
+            cg[g] = __shfl_sync(0xffffffffu, ok ? cnt : 0, SUR_EVT_LANES * g);
+            bxg[g] = __shfl_sync(0xffffffffu, bx, SUR_EVT_LANES * g);
+            byg[g] = __shfl_sync(0xffffffffu, by, SUR_EVT_LANES * g);
         }
-        // layer 2: 8 k-steps in ascending order for every n8 tile
-        float acc2[16][4];
+        const int R = off[EPW];
+        float pacc[EPW][4];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
+        for (int g = 0; g < EPW; ++g) pacc[g][0] = pacc[g][1] = pacc[g][2] = pacc[g][3] = 0.f;
+
+        for (int rb = 0; rb < R; rb += 16) {
+            // ---- features of rows rb .. rb + 15 (lanes 0..15)
+            bool urow = false;
+            if (lane < 16) {
+                const int r = rb + lane;
+                __nv_bfloat162 x[SUR_XPAD / 2];
+                if (r < R) {
+                    const int g = (r >= off[1]) + (r >= off[2]) + (r >= off[3]);
+                    const int img = sel4(g, ig[0], ig[1], ig[2], ig[3]) + (r - sel4(g, off[0], off[1], off[2], off[3]));
+                    const rta_hillas_t h = f.h[img];
+                    urow = sur_used(h);
+                    sur_image_features(h, f.img_tel[img], f.tel_cam, f.tel_xy, f.cam_code, f.n_tel,
+                                       sel4(g, bxg[0], bxg[1], bxg[2], bxg[3]),
+                                       sel4(g, byg[0], byg[1], byg[2], byg[3]), x);
+                } else {
 #pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-#pragma unroll
-            for (int jp = 0; jp < 8; ++jp) {
-                uint32_t b[4];
-                ldsm_b_trans(b, &W2s[0][0], LDH, 16 * ks, 16 * jp, lane);
-                const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
-                mma_bf16(acc2[2 * jp], ah[ks], b0);
-                mma_bf16(acc2[2 * jp + 1], ah[ks], b1);
+                    for (int j = 0; j < SUR_XPAD / 2; ++j) x[j] = __floats2bfloat162_rn(0.f, 0.f);
+                }
+                uint4* xr = reinterpret_cast<uint4*>(Xw + lane * LDX);
+                xr[0] = make_uint4(bf2_bits(x[0]), bf2_bits(x[1]), bf2_bits(x[2]), bf2_bits(x[3]));
+                xr[1] = make_uint4(bf2_bits(x[4]), bf2_bits(x[5]), bf2_bits(x[6]), bf2_bits(x[7]));
             }
-        }
-        // ReLU(acc + b2) in BF16; an unused image gets a +0 row
-        __nv_bfloat16* ha = a.H2 + ra * SUR_H + 2 * tq;
-        __nv_bfloat16* hb = a.H2 + rb * SUR_H + 2 * tq;
+            const unsigned umask = __ballot_sync(0xffffffffu, urow);
+            __syncwarp();
+            const bool ua = (umask >> gq) & 1u, ub = (umask >> (gq + 8)) & 1u;
+            // ---- layer 1: 16 n8 tiles, one k-step
+            uint32_t ax[4];
+            {
+                const __nv_bfloat16* p = Xw + gq * LDX + 2 * tq;
+                ax[0] = lds32(p);
+                ax[1] = lds32(p + 8 * LDX);
+                ax[2] = lds32(p + 8);
+                ax[3] = lds32(p + 8 * LDX + 8);
+            }
+            uint32_t ah[8][4];
+            {
+                float acc1[16][4];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int n = 8 * j + 2 * tq;
-            if (va)
-                *reinterpret_cast<__nv_bfloat162*>(ha + 8 * j) = __floats2bfloat162_rn(
-                    ua ? fmaxf(acc2[j][0] + b2s[n], 0.f) : 0.f, ua ? fmaxf(acc2[j][1] + b2s[n + 1], 0.f) : 0.f);
-            if (vb)
-                *reinterpret_cast<__nv_bfloat162*>(hb + 8 * j) = __floats2bfloat162_rn(
-                    ub ? fmaxf(acc2[j][2] + b2s[n], 0.f) : 0.f, ub ? fmaxf(acc2[j][3] + b2s[n + 1], 0.f) : 0.f);
+                for (int j = 0; j < 16; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
+#pragma unroll
+                for (int jp = 0; jp < 8; ++jp) {
+                    uint32_t b[4];
+                    ldsm_b_trans(b, W1s, LDH, 0, 16 * jp, lane);
+                    const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
+                    mma_bf16(acc1[2 * jp], ax, b0);
+                    mma_bf16(acc1[2 * jp + 1], ax, b1);
+                }
+                // ReLU(acc + b1) in BF16, rearranged as the A fragments of layer 2
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks) {
+                    const int n0 = 16 * ks + 2 * tq, n1 = n0 + 8;
+                    const float* c0 = acc1[2 * ks];
+                    const float* c1 = acc1[2 * ks + 1];
+                    ah[ks][0] = bf2_bits(__floats2bfloat162_rn(fmaxf(c0[0] + b1s[n0], 0.f), fmaxf(c0[1] + b1s[n0 + 1], 0.f)));
+                    ah[ks][1] = bf2_bits(__floats2bfloat162_rn(fmaxf(c0[2] + b1s[n0], 0.f), fmaxf(c0[3] + b1s[n0 + 1], 0.f)));
+                    ah[ks][2] = bf2_bits(__floats2bfloat162_rn(fmaxf(c1[0] + b1s[n1], 0.f), fmaxf(c1[1] + b1s[n1 + 1], 0.f)));
+                    ah[ks][3] = bf2_bits(__floats2bfloat162_rn(fmaxf(c1[2] + b1s[n1], 0.f), fmaxf(c1[3] + b1s[n1 + 1], 0.f)));
+                }
+            }
+            // ---- layer 2 in two halves of 64 columns; 8 k-steps in ascending order per tile
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float acc2[8][4];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks) {
+#pragma unroll
+                    for (int jp = 0; jp < 4; ++jp) {
+                        uint32_t b[4];
+                        ldsm_b_trans(b, W2s, LDH, 16 * ks, 64 * half + 16 * jp, lane);
+                        const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
+                        mma_bf16(acc2[2 * jp], ah[ks], b0);
+                        mma_bf16(acc2[2 * jp + 1], ah[ks], b1);
+                    }
+                }
+                // ReLU(acc + b2) in BF16; an unused image gets a +0 row
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = 64 * half + 8 * j + 2 * tq;
+                    *reinterpret_cast<__nv_bfloat162*>(Hw + gq * LDH + n) = __floats2bfloat162_rn(
+                        ua ? fmaxf(acc2[j][0] + b2s[n], 0.f) : 0.f, ua ? fmaxf(acc2[j][1] + b2s[n + 1], 0.f) : 0.f);
+                    *reinterpret_cast<__nv_bfloat162*>(Hw + (gq + 8) * LDH + n) = __floats2bfloat162_rn(
+                        ub ? fmaxf(acc2[j][2] + b2s[n], 0.f) : 0.f, ub ? fmaxf(acc2[j][3] + b2s[n + 1], 0.f) : 0.f);
+                }
+            }
+            __syncwarp();
+            // ---- pooling: lane = 4 channels; rows in image order, each into its event
+            const int rend = min(R, rb + 16);
+            for (int r = rb; r < rend; ++r) {
+                const int g = (r >= off[1]) + (r >= off[2]) + (r >= off[3]);
+                const uint2 v = *reinterpret_cast<const uint2*>(Hw + (r - rb) * LDH + 4 * lane);
+                const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+                const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+#pragma unroll
+                for (int gg = 0; gg < EPW; ++gg)
+                    if (g == gg) {
+                        pacc[gg][0] += lo.x;
+                        pacc[gg][1] += lo.y;
+                        pacc[gg][2] += hi.x;
+                        pacc[gg][3] += hi.y;
+                    }
+            }
+            __syncwarp();
+        }
+        // ---- pooled vectors [sum / 40, sum / max(1, n_used)] in BF16
+#pragma unroll
+        for (int g = 0; g < EPW; ++g) {
+            const int64_t eg = e0 + g;
+            if (eg >= n_evt) break;
+            const float d = fmaxf(1.f, float(cg[g]));
+            __nv_bfloat16* pr = a.P + eg * SUR_G + 4 * lane;
+            const __nv_bfloat162 s0 = __floats2bfloat162_rn(pacc[g][0] * (1.f / SUR_POOL_DIV), pacc[g][1] * (1.f / SUR_POOL_DIV));
+            const __nv_bfloat162 s1 = __floats2bfloat162_rn(pacc[g][2] * (1.f / SUR_POOL_DIV), pacc[g][3] * (1.f / SUR_POOL_DIV));
+            const __nv_bfloat162 m0 = __floats2bfloat162_rn(pacc[g][0] / d, pacc[g][1] / d);
+            const __nv_bfloat162 m1 = __floats2bfloat162_rn(pacc[g][2] / d, pacc[g][3] / d);
+            *reinterpret_cast<uint2*>(pr) = make_uint2(bf2_bits(s0), bf2_bits(s1));
+            *reinterpret_cast<uint2*>(pr + SUR_H) = make_uint2(bf2_bits(m0), bf2_bits(m1));
         }
     }
 }
 
 // ------------------------------------------------------------------ k_event
+// Pooled rows of events [e0, e0 + ne) into a shared-memory tile (zeros past ne).
+__device__ __forceinline__ void stage_pooled(__nv_bfloat16* Pt, const __nv_bfloat16* P, int64_t e0, int ne, int tid) {
+    for (int i = tid; i < FE * (SUR_G / 8); i += NT) {
+        const int el = i / (SUR_G / 8), c = i % (SUR_G / 8);
+        __nv_bfloat16* dst = Pt + el * LDV + 8 * c;
+        if (el < ne) cp_async16(dst, P + (e0 + el) * SUR_G + 8 * c);
+        else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_commit();
+}
+
 __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
     extern __shared__ __align__(128) unsigned char sm[];
     __nv_bfloat16* V1s = reinterpret_cast<__nv_bfloat16*>(sm + SM_V1);
-    __nv_bfloat16* Hs = reinterpret_cast<__nv_bfloat16*>(sm + SM_H);
-    __nv_bfloat16* Ps = Hs;
-    __nv_bfloat16* Gs = reinterpret_cast<__nv_bfloat16*>(sm + SM_H + SM_G_OFF);
-    float* Pacc = reinterpret_cast<float*>(sm + SM_PACC);
+    __nv_bfloat16* Pbuf = reinterpret_cast<__nv_bfloat16*>(sm + SM_P);
+    __nv_bfloat16* Gs = reinterpret_cast<__nv_bfloat16*>(sm + SM_G);
     __nv_bfloat16* V2s = reinterpret_cast<__nv_bfloat16*>(sm + SM_V2);
     float* Ys = reinterpret_cast<float*>(sm + SM_Y);
-    int64_t* rowb = reinterpret_cast<int64_t*>(sm + SM_ROWB);
-    int* lo_s = reinterpret_cast<int*>(sm + SM_LO);
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    const FeatArgs& f = a.f;
-    const int64_t n_evt = f.n_evt;
+    const int64_t n_evt = a.f.n_evt;
     const int TE = a.tile_events;
+    int64_t t = blockIdx.x;
+    if (t < a.n_tiles) stage_pooled(Pbuf, a.P, t * TE, int(TE < n_evt - t * TE ? TE : n_evt - t * TE), tid);
     // weights: V1 copied as stored (k-major rows, padded), V2 as stored
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.pb + OFF_V1);
@@ -221,81 +345,16 @@ __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int c = 0; c < 2; ++c) c1r[j][c] = a.p[OFF_C1 + wn2 + 8 * j + 2 * tq + c];
-    __syncthreads();
 
-    for (int64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    for (int buf = 0; t < a.n_tiles; t += gridDim.x, buf ^= 1) {
         const int64_t e0 = t * TE;
         const int ne = int(TE < n_evt - e0 ? TE : n_evt - e0);
-        // rows of the tile: the images of its well-formed events, in order
-        if (warp == 0) {
-            int64_t v = 0;
-            if (lane < ne) {
-                const int64_t e = e0 + lane;
-                const int i0 = f.evt_off[e];
-                lo_s[lane] = i0;
-                v = f.n_used[e] >= 0 ? int64_t(f.evt_off[e + 1]) - i0 : 0;
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            rowb[lane + 1] = v;
-            if (lane == 0) rowb[0] = 0;
-        }
-        for (int i = tid; i < FE * SUR_H; i += NT) Pacc[i] = 0.f;
+        __nv_bfloat16* Ps = Pbuf + buf * (FE * LDV);
+        cp_async_wait_all();
         __syncthreads();
-        const int64_t R = rowb[ne];
-
-        // ---- pooling over the staged rows, RT rows at a time
-        for (int64_t c0 = 0; c0 < R; c0 += RT) {
-            const int64_t c1 = min(R, c0 + RT);
-            for (int i = tid; i < RT * (SUR_H / 8); i += NT) {
-                const int row = i / (SUR_H / 8), part = i % (SUR_H / 8);
-                const int64_t r = c0 + row;
-                if (r >= c1) break;
-                int lo = 0, hi = ne - 1;                // last event whose first row is <= r
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (rowb[mid] <= r) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int64_t img = int64_t(lo_s[lo]) + (r - rowb[lo]);
-                *reinterpret_cast<uint4*>(Hs + row * LDH + 8 * part) =
-                    reinterpret_cast<const uint4*>(a.H2 + img * SUR_H)[part];
-            }
-            __syncthreads();
-            // thread = (channel pair, event group); image order within each event
-            const int cp = tid & 63;
-            for (int el = tid >> 6; el < ne; el += NT / 64) {
-                const int64_t lo = max(rowb[el], c0), hi = min(rowb[el + 1], c1);
-                if (lo >= hi) continue;
-                float2 s = reinterpret_cast<float2*>(Pacc + el * SUR_H)[cp];
-                for (int64_t r = lo; r < hi; ++r) {
-                    const float2 h =
-                        __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(Hs + (r - c0) * LDH)[cp]);
-                    s.x += h.x;
-                    s.y += h.y;
-                }
-                reinterpret_cast<float2*>(Pacc + el * SUR_H)[cp] = s;
-            }
-            __syncthreads();
-        }
-
-        // ---- pooled vector [sum / 40, sum / max(1, n_used)] in BF16
-        for (int idx = tid; idx < FE * (SUR_H / 4); idx += NT) {
-            const int el = idx / (SUR_H / 4), c4 = idx % (SUR_H / 4);
-            const float4 s = reinterpret_cast<const float4*>(Pacc + el * SUR_H)[c4];
-            const int nu = el < ne ? f.n_used[e0 + el] : 0;
-            const float d = fmaxf(1.f, float(nu > 0 ? nu : 0));
-            __nv_bfloat162* pr = reinterpret_cast<__nv_bfloat162*>(Ps + el * LDV + 4 * c4);
-            pr[0] = __floats2bfloat162_rn(s.x * (1.f / SUR_POOL_DIV), s.y * (1.f / SUR_POOL_DIV));
-            pr[1] = __floats2bfloat162_rn(s.z * (1.f / SUR_POOL_DIV), s.w * (1.f / SUR_POOL_DIV));
-            pr[SUR_H / 2] = __floats2bfloat162_rn(s.x / d, s.y / d);
-            pr[SUR_H / 2 + 1] = __floats2bfloat162_rn(s.z / d, s.w / d);
-        }
-        __syncthreads();
-
+        const int64_t tn = t + gridDim.x;
+        if (tn < a.n_tiles)
+            stage_pooled(Pbuf + (buf ^ 1) * (FE * LDV), a.P, tn * TE, int(TE < n_evt - tn * TE ? TE : n_evt - tn * TE), tid);
         // ---- event network 256 -> 256 (columns wn2..wn2+31 per warp)
         {
             float acc[2][4][4];
@@ -343,23 +402,23 @@ __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
         if (tid < ne) {
             const int64_t e = e0 + tid;
             const float y[4] = {Ys[tid * 4 + 0], Ys[tid * 4 + 1], Ys[tid * 4 + 2], Ys[tid * 4 + 3]};
-            sur_emit_event(a.o, e, y, f.base[e], f.n_used[e]);
+            sur_emit_event(a.o, e, y, a.f.base[e], a.f.n_used[e]);
         }
-        __syncthreads();
     }
+    cp_async_wait_all();
 }
 
 cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s) {
     if (a.tile_events < 1 || a.tile_events > FE) return cudaErrorInvalidValue;
-    const int64_t units = (a.f.n_img + 15) / 16;
-    if (units > 0) {
-        const int64_t g = std::min<int64_t>((units + PHI_WARPS - 1) / PHI_WARPS, int64_t(n_sm) * 3);
-        k_phi<<<int(g), PHI_WARPS * 32, 0, s>>>(a);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = cudaFuncSetAttribute(k_event, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SM_TOTAL));
+    if (a.f.n_evt <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_tel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TS_TOTAL));
     if (e != cudaSuccess) return e;
+    const int64_t warps = (a.f.n_evt + EPW - 1) / EPW;
+    const int64_t g = std::min<int64_t>((warps + NT / 32 - 1) / (NT / 32), int64_t(n_sm) * 2);
+    k_tel<<<int(g), NT, TS_TOTAL, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_event, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SM_TOTAL))) != cudaSuccess)
+        return e;
     k_event<<<int(std::min<int64_t>(a.n_tiles, n_sm)), NT, SM_TOTAL, s>>>(a);
     return cudaGetLastError();
 }

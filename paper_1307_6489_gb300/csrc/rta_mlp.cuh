@@ -110,14 +110,14 @@ struct OutArgs {
     const rta_stereo_t* geo;
 };
 
-// Fused inference after k_features: f carries the event offsets and the
-// features, used flags, baselines and used counts that k_features wrote; the
-// output block's Y/base are not read.
+// Inference: f carries the inputs and tables, and receives the baselines and
+// used counts (its X/used are not touched); the output block's Y/base are not
+// read.
 struct InferArgs {
     FeatArgs f;
     const __nv_bfloat16* pb;   // BF16 parameter twin (internal layout)
     const float* p;            // FP32 master (biases)
-    __nv_bfloat16* H2;         // [n_img x 128] per-telescope network output (workspace)
+    __nv_bfloat16* P;          // [n_evt x 256] pooled vectors (workspace)
     int tile_events;           // events per tile of k_event, 1..32
     int64_t n_tiles;
     OutArgs o;
@@ -144,7 +144,7 @@ cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_
                           float* out, cudaStream_t s);
 cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
-// k_phi then k_event (one CTA per SM, n_sm of them at most)
+// k_tel then k_event (one CTA per SM, n_sm of them at most)
 cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s);
 constexpr int INFER_MAX_TILE_EVENTS = 32;
 

@@ -458,13 +458,11 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     ia.f.n_evt = n_evt;
     if ((rc = rta::surrogate_ctx_tables(md->ctx, &ia.f.tel_cam, &ia.f.tel_xy, &ia.f.n_tel, nullptr))) return rc;
     ia.f.cam_code = md->cam_code;
-    ia.f.X = md->X;
-    ia.f.used = md->used;
     ia.f.base = md->base;
     ia.f.n_used = md->n_used;
     ia.pb = md->pb;
     ia.p = md->p;
-    ia.H2 = md->H2;
+    ia.P = md->P;
     // one persistent CTA per SM; tiles of up to 32 events, sized so that every
     // CTA gets the same number of tiles
     const int64_t per_round = int64_t(md->n_sm) * rta::INFER_MAX_TILE_EVENTS;
@@ -479,7 +477,6 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     oa.fallback_idx = md->fallback_idx;
     oa.geo = md->geo;
     S_TRY(cudaMemsetAsync(md->n_fallback, 0, sizeof(unsigned int), s));
-    S_TRY(rta::launch_features(ia.f, blocks_for(n_evt, 32), s));
     S_TRY(rta::launch_infer(ia, md->n_sm, s));
     // the geometric intersection only for the events that need it
     if ((rc = rta::surrogate_stereo_list(md->ctx, d_h, d_img_tel, n_img, d_evt_off, n_evt, md->fallback_idx,
