@@ -1,425 +1,457 @@
 // Inference of the deep-sets surrogate (energy, direction offset and
-// gamma/hadron score next to the geometric direction, Sec. 4.1), in two kernels:
+// gamma/hadron score next to the geometric direction, Sec. 4.1), in two
+// kernels, both on the fifth-generation tensor cores (tcgen05: operands in
+// shared memory as canonical K-major core matrices, FP32 accumulators in
+// tensor memory, one thread issuing the MMAs and committing them to an
+// mbarrier that the CTA waits on with a time limit):
 //
-//   k_tel    one warp per four events, no block barrier after the weights are
-//            staged: per-event baseline and used images (eight lanes per
-//            event), per-image features, the per-telescope network
-//            16 -> 128 -> 128 (ReLU) on the tensor cores (mma.sync m16n8k16,
-//            BF16 operands, FP32 accumulators) sixteen image rows at a time --
-//            the first layer's accumulators become the second layer's A
-//            fragments in registers, the weights reach the MMA from shared
-//            memory by ldmatrix.trans -- and the sum / mean pooling in
-//            registers. Writes the pooled vectors, baselines and used counts.
-//   k_event  one persistent CTA per SM walks tiles of up to 32 events: the
-//            event network 256 -> 256 (ReLU, weights staged once per CTA) and
-//            256 -> 4 on the tensor cores, then the outputs and the fallback
-//            list for the geometric intersection. The next tile's pooled rows
-//            arrive by cp.async while the current one computes.
+//   k_tel    tiles of up to 32 events: per-event baseline and used images (eight
+//            lanes per event), then, 128 image rows at a time, the features,
+//            the per-telescope network 16 -> 128 -> 128 (ReLU; BF16
+//            activations re-staged as the next layer's operand) and the sum /
+//            mean pooling in image order. Writes the pooled vectors, baselines
+//            and used counts.
+//   k_event  tiles of 128 events: the event network 256 -> 256 (ReLU), then
+//            the 256 -> 4 output layer in FP32 from the BF16-rounded
+//            activations, the outputs, and the fallback list for the
+//            geometric intersection.
 //
-// Every stage evaluates the same expressions in the same order as the
-// layer-by-layer kernels of the training path (k_features, k_gemm, k_pool,
-// k_head in k_mlp.cu): the features and the eight-lane event reductions, the
-// k-order of each MMA accumulation, the image order of the pooling sums (an
-// unused image adds +0 here where the pooling kernel skips it, which leaves a
-// sum unchanged). The outputs therefore equal those of the training-path
-// forward bit for bit.
+// The features and the eight-lane event reductions are the training path's
+// own expressions (rta_mlp_dev.cuh), so the baselines and used counts equal
+// those of k_features bit for bit. The network layers sum their exact BF16
+// products in FP32 in the tensor core's order rather than mma.sync's, so the
+// outputs agree with the training-path forward to accumulation-order effects.
 #include <algorithm>
 
 #include "rta_mlp_dev.cuh"
+#include "rta_tc.cuh"
 
 namespace rta {
 namespace {
 
-constexpr int FE = 32;              // events per k_event tile at most
 constexpr int NT = 256;             // threads per CTA (both kernels)
-constexpr int EPW = 32 / SUR_EVT_LANES;   // events per k_tel warp iteration
-constexpr int LDX = 24;             // feature row stride (16 + 8: conflict-free fragment loads)
-constexpr int LDH = SUR_H + 8;      // hidden row stride (conflict-free ldmatrix / fragment loads)
-constexpr int LDV = SUR_G + 8;      // pooled / event-network row stride
+constexpr int TM = 128;             // MMA M: image rows per k_tel block, events per k_event tile
+constexpr int TE = 32;              // events per k_tel tile at most
+constexpr int LDH = SUR_H + 8;      // row stride of the row-major hidden tile used for pooling
 
-// k_tel shared memory: weights, then per warp a 16-row feature tile and a
-// 16-row hidden tile
-constexpr size_t TS_W1 = 0;                                      // bf16 [16][LDH]
-constexpr size_t TS_W2 = TS_W1 + size_t(SUR_XPAD) * LDH * 2;     // bf16 [128][LDH]
-constexpr size_t TS_B = TS_W2 + size_t(SUR_H) * LDH * 2;         // f32 b1[128], b2[128]
-constexpr size_t TS_WARP = TS_B + 2 * SUR_H * 4;
-constexpr size_t TS_X_BYTES = 16 * LDX * 2;
-constexpr size_t TS_H_BYTES = 16 * LDH * 2;
-constexpr size_t TS_TOTAL = TS_WARP + (NT / 32) * (TS_X_BYTES + TS_H_BYTES);
+// k_tel shared memory (two CTAs per SM)
+constexpr size_t TS_W1 = 0;                                      // bf16 W1^T canonical [128 n][16 k]
+constexpr size_t TS_W2 = TS_W1 + size_t(SUR_H) * SUR_XPAD * 2;   // bf16 W2^T canonical [128 n][128 k]
+constexpr size_t TS_X = TS_W2 + size_t(SUR_H) * SUR_H * 2;       // bf16 features, canonical [128][16]
+constexpr size_t TS_H = TS_X + size_t(TM) * SUR_XPAD * 2;        // bf16 H1 canonical [128][128]; then H2 row-major [128][LDH]
+constexpr size_t TS_PACC = TS_H + size_t(TM) * LDH * 2;          // f32 [32][128] pooling sums
+constexpr size_t TS_B = TS_PACC + size_t(TE) * SUR_H * 4;        // f32 b1[128], b2[128]
+constexpr size_t TS_ROWB = TS_B + 2 * SUR_H * 4;                 // int64 [33] first row of each event
+constexpr size_t TS_BASE = TS_ROWB + size_t(TE + 1) * 8;         // float2 [32]
+constexpr size_t TS_LO = TS_BASE + size_t(TE) * 8;               // int [32] first image
+constexpr size_t TS_CNT = TS_LO + size_t(TE) * 4;                // int [32] rows
+constexpr size_t TS_NU = TS_CNT + size_t(TE) * 4;                // int [32] used images (0 if malformed)
+constexpr size_t TS_USED = TS_NU + size_t(TE) * 4;               // u8 [128]
+constexpr size_t TS_BAR = TS_USED + TM;                          // mbarrier, TMEM address, abort flag
+constexpr size_t TS_TOTAL = TS_BAR + 32;
+static_assert(TS_H % 16 == 0 && TS_X % 16 == 0 && TS_W2 % 16 == 0, "16-byte aligned operand tiles");
+static_assert(TS_BAR % 8 == 0 && TS_ROWB % 8 == 0, "aligned barrier and row table");
 static_assert(2 * TS_TOTAL <= 227 * 1024, "two k_tel CTAs per SM");
-static_assert(EPW == 4, "k_tel assigns rows to four events per warp");
 
 // k_event shared memory
-constexpr size_t SM_V1 = 0;                                      // bf16 [256 k][LDV]: V1 as stored
-constexpr size_t SM_P = SM_V1 + size_t(SUR_G) * LDV * 2;         // bf16 [2][32][LDV] pooled rows, double-buffered
-constexpr size_t SM_G = SM_P + 2 * size_t(FE) * LDV * 2;         // bf16 [32][LDV]
-constexpr size_t SM_V2 = SM_G + size_t(FE) * LDV * 2;            // bf16 [256][4]
-constexpr size_t SM_Y = SM_V2 + size_t(SUR_G) * 4 * 2;           // f32 [32][4]
-constexpr size_t SM_TOTAL = SM_Y + size_t(FE) * 4 * 4;
+constexpr size_t SM_V1 = 0;                                      // bf16 V1^T, canonical K-major [256 n][256 k]
+constexpr size_t SM_P = SM_V1 + size_t(SUR_G) * SUR_G * 2;       // bf16 pooled tile, canonical [128][256]
+constexpr size_t SM_V2 = SM_P + size_t(TM) * SUR_G * 2;          // f32 [256][4]
+constexpr size_t SM_C1 = SM_V2 + size_t(SUR_G) * 4 * 4;          // f32 [256]
+constexpr size_t SM_YP = SM_C1 + size_t(SUR_G) * 4;              // f32 [128][4] second-half partial outputs
+constexpr size_t SM_BAR = SM_YP + size_t(TM) * 4 * 4;            // mbarrier, TMEM address, abort flag
+constexpr size_t SM_TOTAL = SM_BAR + 32;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory per CTA");
 
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// A fragments of two m16 row blocks at rows r0.., k-columns k0..k0+15 of a row-major BF16 tile.
-__device__ __forceinline__ void load_a(uint32_t (&af)[2][4], const __nv_bfloat16* base, int ld, int r0, int k0,
-                                       int gq, int tq) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const __nv_bfloat16* p = base + (r0 + 16 * i + gq) * ld + k0 + 2 * tq;
-        af[i][0] = lds32(p);
-        af[i][1] = lds32(p + 8 * ld);
-        af[i][2] = lds32(p + 8);
-        af[i][3] = lds32(p + 8 * ld + 8);
+// Wait for the MMAs committed to bar (phase `phase`); on a timeout flag the
+// status word and the CTA's abort flag. Every thread calls it; returns false
+// for every thread once any thread gave up.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase, volatile int* abort_s, unsigned int* status) {
+    if (!mbar_wait(bar, phase, abort_s)) {
+        *abort_s = 1;
+        atomicOr(status, RTA_DEV_TIMEOUT);
     }
+    __syncthreads();
+    if (*abort_s) return false;
+    tc_fence_after();
+    return true;
 }
 
-// ReLU(acc + bias) rounded to BF16 into a row-major tile (rows r0.., columns c0..).
-__device__ __forceinline__ void store_relu(const float (&acc)[2][4][4], const float (&bias)[4][2], __nv_bfloat16* dst,
-                                           int ld, int r0, int c0, int gq, int tq) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = r0 + 16 * i + gq + 8 * h, n = c0 + 8 * j + 2 * tq;
-                const float v0 = fmaxf(acc[i][j][2 * h] + bias[j][0], 0.f);
-                const float v1 = fmaxf(acc[i][j][2 * h + 1] + bias[j][1], 0.f);
-                *reinterpret_cast<__nv_bfloat162*>(dst + m * ld + n) = __floats2bfloat162_rn(v0, v1);
-            }
-}
-
-// B fragments of two n8 tiles (columns n0..n0+15) at k-rows k0..k0+15 of a
-// k-major BF16 matrix in shared memory: b[0..1] for n0, b[2..3] for n0 + 8.
-__device__ __forceinline__ void ldsm_b_trans(uint32_t (&b)[4], const __nv_bfloat16* base, int ld, int k0, int n0,
-                                             int lane) {
-    const __nv_bfloat16* p = base + (k0 + (lane & 15)) * ld + n0 + (lane >> 4) * 8;
-    const uint32_t addr = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
-                 : "r"(addr));
-}
-
-template <typename T>
-__device__ __forceinline__ T sel4(int g, T v0, T v1, T v2, T v3) {
-    return g == 0 ? v0 : g == 1 ? v1 : g == 2 ? v2 : v3;
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-__device__ __forceinline__ void zero_acc(float (&acc)[2][4][4]) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+// Release the CTA's tensor memory. After an abort, one more bounded wait lets
+// MMAs still in flight finish first.
+__device__ __forceinline__ void tc_teardown(uint64_t* bar, uint32_t phase, volatile int* abort_s, uint32_t tmem,
+                                            uint32_t ncols) {
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_s && threadIdx.x == 0) {
+        volatile int none = 0;
+        mbar_wait(bar, phase ^ 1u, &none);
+    }
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc_dealloc(tmem, ncols);
 }
 
 }  // namespace
 
-
 // ------------------------------------------------------------------ k_tel
 __global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
-    extern __shared__ __align__(128) unsigned char sm[];
+    extern __shared__ __align__(1024) unsigned char sm[];
     __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(sm + TS_W1);
     __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(sm + TS_W2);
+    __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(sm + TS_X);
+    __nv_bfloat16* Hs = reinterpret_cast<__nv_bfloat16*>(sm + TS_H);
+    float* Pacc = reinterpret_cast<float*>(sm + TS_PACC);
     float* b1s = reinterpret_cast<float*>(sm + TS_B);
     float* b2s = b1s + SUR_H;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    __nv_bfloat16* Xw = reinterpret_cast<__nv_bfloat16*>(sm + TS_WARP + warp * (TS_X_BYTES + TS_H_BYTES));
-    __nv_bfloat16* Hw = reinterpret_cast<__nv_bfloat16*>(sm + TS_WARP + warp * (TS_X_BYTES + TS_H_BYTES) + TS_X_BYTES);
+    int64_t* rowb = reinterpret_cast<int64_t*>(sm + TS_ROWB);
+    float2* base_s = reinterpret_cast<float2*>(sm + TS_BASE);
+    int* lo_s = reinterpret_cast<int*>(sm + TS_LO);
+    int* cnt_s = reinterpret_cast<int*>(sm + TS_CNT);
+    int* nu_s = reinterpret_cast<int*>(sm + TS_NU);
+    uint8_t* used_s = sm + TS_USED;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TS_BAR);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + TS_BAR + 8);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(sm + TS_BAR + 12);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const FeatArgs& f = a.f;
+    const int64_t n_evt = f.n_evt, n_img = f.n_img;
+
+    if (warp == 0) {
+        tc_alloc(tmem_s, 256);               // columns 0-127: layer 1, 128-255: layer 2
+        tc_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        *abort_s = 0;
+    }
     {
-        const uint4* w1 = reinterpret_cast<const uint4*>(a.pb + OFF_W1);
-        const uint4* w2 = reinterpret_cast<const uint4*>(a.pb + OFF_W2);
-        for (int i = tid; i < SUR_XPAD * SUR_H / 8; i += NT)
-            *reinterpret_cast<uint4*>(W1s + (i / (SUR_H / 8)) * LDH + 8 * (i % (SUR_H / 8))) = w1[i];
-        for (int i = tid; i < SUR_H * SUR_H / 8; i += NT)
-            *reinterpret_cast<uint4*>(W2s + (i / (SUR_H / 8)) * LDH + 8 * (i % (SUR_H / 8))) = w2[i];
+        const uint4* w1 = reinterpret_cast<const uint4*>(a.pk + PK_W1T);
+        const uint4* w2 = reinterpret_cast<const uint4*>(a.pk + PK_W2T);
+        for (int i = tid; i < SUR_H * SUR_XPAD / 8; i += NT) reinterpret_cast<uint4*>(W1s)[i] = w1[i];
+        for (int i = tid; i < SUR_H * SUR_H / 8; i += NT) reinterpret_cast<uint4*>(W2s)[i] = w2[i];
         for (int i = tid; i < SUR_H; i += NT) {
             b1s[i] = a.p[OFF_B1 + i];
             b2s[i] = a.p[OFF_B2 + i];
         }
     }
+    fence_proxy_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const FeatArgs& f = a.f;
-    const int64_t n_evt = f.n_evt, n_img = f.n_img;
+    tc_fence_after();
+    const uint32_t tmem = *tmem_s;
+    const uint32_t idesc = tc_idesc_bf16(TM, SUR_H);
+    const uint32_t x_addr = smem_addr(Xs), h_addr = smem_addr(Hs), w1_addr = smem_addr(W1s), w2_addr = smem_addr(W2s);
+    const int q = warp & 3, c_half = (warp >> 2) * (SUR_H / 2), row = 32 * q + lane;
+    const uint32_t t_lane = uint32_t(32 * q) << 16;
     const int sub = lane % SUR_EVT_LANES, grp = lane / SUR_EVT_LANES;
-    const int64_t nwarps = (int64_t(gridDim.x) * NT) >> 5;
-    for (int64_t e0 = (int64_t(blockIdx.x) * (NT / 32) + warp) * EPW; e0 < n_evt; e0 += nwarps * EPW) {
-        // ---- per-event prologue, eight lanes per event (as k_features)
-        const int64_t e = e0 + grp;
-        int i0 = 0, n = 0;
-        bool ok = false;
-        if (e < n_evt) {
-            i0 = f.evt_off[e];
-            const int i1 = f.evt_off[e + 1];
-            ok = !(i0 < 0 || i1 < i0 || i1 > n_img);
-            n = ok ? i1 - i0 : 0;
-        }
-        float bx, by;
-        int cnt;
-        sur_event_baseline(f.h, i0, n, sub, nullptr, bx, by, cnt);
-        if (e < n_evt && sub == 0) {
-            f.base[e] = make_float2(bx, by);
-            f.n_used[e] = ok ? cnt : -1;
-        }
-        // the four events' rows, in order
-        int off[EPW + 1], ig[EPW], cg[EPW];
-        float bxg[EPW], byg[EPW];
-        off[0] = 0;
-#pragma unroll
-        for (int g = 0; g < EPW; ++g) {
-            off[g + 1] = off[g] + __shfl_sync(0xffffffffu, n, SUR_EVT_LANES * g);
-            ig[g] = __shfl_sync(0xffffffffu, i0, SUR_EVT_LANES * g);
-            cg[g] = __shfl_sync(0xffffffffu, ok ? cnt : 0, SUR_EVT_LANES * g);
-            bxg[g] = __shfl_sync(0xffffffffu, bx, SUR_EVT_LANES * g);
-            byg[g] = __shfl_sync(0xffffffffu, by, SUR_EVT_LANES * g);
-        }
-        const int R = off[EPW];
-        float pacc[EPW][4];
-#pragma unroll
-        for (int g = 0; g < EPW; ++g) pacc[g][0] = pacc[g][1] = pacc[g][2] = pacc[g][3] = 0.f;
+    uint32_t phase = 0;
+    bool alive = true;
+    const int te = a.tel_tile_events;
+    const int64_t n_tiles = (n_evt + te - 1) / te;
 
-        for (int rb = 0; rb < R; rb += 16) {
-            // ---- features of rows rb .. rb + 15 (lanes 0..15)
-            bool urow = false;
-            if (lane < 16) {
-                const int r = rb + lane;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t e0 = t * te;
+        const int ne = int(te < n_evt - e0 ? te : n_evt - e0);
+        // ---- per-event prologue, eight lanes per event (as k_features)
+        {
+            const int el = (32 / SUR_EVT_LANES) * warp + grp;
+            const int64_t e = e0 + el;
+            int i0 = 0, n = 0;
+            bool ok = false;
+            if (el < ne) {
+                i0 = f.evt_off[e];
+                const int i1 = f.evt_off[e + 1];
+                ok = !(i0 < 0 || i1 < i0 || i1 > n_img);
+                n = ok ? i1 - i0 : 0;
+            }
+            float bx, by;
+            int cnt;
+            sur_event_baseline(f.h, i0, n, sub, nullptr, bx, by, cnt);
+            if (sub == 0) {
+                if (el < ne) {
+                    f.base[e] = make_float2(bx, by);
+                    f.n_used[e] = ok ? cnt : -1;
+                }
+                base_s[el] = make_float2(bx, by);
+                lo_s[el] = i0;
+                cnt_s[el] = n;
+                nu_s[el] = ok ? cnt : 0;
+            }
+        }
+        for (int i = tid; i < TE * SUR_H; i += NT) Pacc[i] = 0.f;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t v = cnt_s[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            rowb[lane + 1] = v;
+            if (lane == 0) rowb[0] = 0;
+        }
+        __syncthreads();
+        const int64_t R = rowb[TE];
+
+        for (int64_t rb = 0; rb < R; rb += TM) {
+            // ---- features of rows rb .. rb + 127, one thread per row
+            if (tid < TM) {
+                const int64_t r = rb + tid;
                 __nv_bfloat162 x[SUR_XPAD / 2];
+                bool used = false;
                 if (r < R) {
-                    const int g = (r >= off[1]) + (r >= off[2]) + (r >= off[3]);
-                    const int img = sel4(g, ig[0], ig[1], ig[2], ig[3]) + (r - sel4(g, off[0], off[1], off[2], off[3]));
+                    int lo = 0, hi = TE - 1;              // last event whose first row is <= r
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (rowb[mid] <= r) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int64_t img = int64_t(lo_s[lo]) + (r - rowb[lo]);
                     const rta_hillas_t h = f.h[img];
-                    urow = sur_used(h);
-                    sur_image_features(h, f.img_tel[img], f.tel_cam, f.tel_xy, f.cam_code, f.n_tel,
-                                       sel4(g, bxg[0], bxg[1], bxg[2], bxg[3]),
-                                       sel4(g, byg[0], byg[1], byg[2], byg[3]), x);
+                    used = sur_used(h);
+                    const float2 b = base_s[lo];
+                    sur_image_features(h, f.img_tel[img], f.tel_cam, f.tel_xy, f.cam_code, f.n_tel, b.x, b.y, x);
                 } else {
 #pragma unroll
                     for (int j = 0; j < SUR_XPAD / 2; ++j) x[j] = __floats2bfloat162_rn(0.f, 0.f);
                 }
-                uint4* xr = reinterpret_cast<uint4*>(Xw + lane * LDX);
-                xr[0] = make_uint4(bf2_bits(x[0]), bf2_bits(x[1]), bf2_bits(x[2]), bf2_bits(x[3]));
-                xr[1] = make_uint4(bf2_bits(x[4]), bf2_bits(x[5]), bf2_bits(x[6]), bf2_bits(x[7]));
+                *reinterpret_cast<uint4*>(Xs + canon_off(tid, 0, SUR_XPAD)) =
+                    make_uint4(bf2_bits(x[0]), bf2_bits(x[1]), bf2_bits(x[2]), bf2_bits(x[3]));
+                *reinterpret_cast<uint4*>(Xs + canon_off(tid, 8, SUR_XPAD)) =
+                    make_uint4(bf2_bits(x[4]), bf2_bits(x[5]), bf2_bits(x[6]), bf2_bits(x[7]));
+                used_s[tid] = used;
             }
-            const unsigned umask = __ballot_sync(0xffffffffu, urow);
-            __syncwarp();
-            const bool ua = (umask >> gq) & 1u, ub = (umask >> (gq + 8)) & 1u;
-            // ---- layer 1: 16 n8 tiles, one k-step
-            uint32_t ax[4];
+            fence_proxy_async_smem();
+            __syncthreads();
+            // ---- layer 1: D1 = X W1 (one K-step)
+            if (tid == 0) {
+                tc_fence_after();
+                tc_mma(tmem, tc_desc(x_addr, 128u, 16u * SUR_XPAD), tc_desc(w1_addr, 128u, 16u * SUR_XPAD), idesc, false);
+                tc_commit(bar);
+            }
+            alive = tc_wait(bar, phase, abort_s, a.o.status);
+            phase ^= 1u;
+            if (!alive) break;
+            // ReLU(D1 + b1) in BF16 -> canonical operand of layer 2 (this thread: one row, 64 columns)
+#pragma unroll 1
+            for (int cb = 0; cb < SUR_H / 2; cb += 16) {
+                const int c0 = c_half + cb;
+                uint32_t v[16];
+                tc_ld16(tmem + t_lane + uint32_t(c0), v);
+                uint32_t w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    w[i] = bf2_bits(__floats2bfloat162_rn(fmaxf(__uint_as_float(v[2 * i]) + b1s[c0 + 2 * i], 0.f),
+                                                          fmaxf(__uint_as_float(v[2 * i + 1]) + b1s[c0 + 2 * i + 1], 0.f)));
+                *reinterpret_cast<uint4*>(Hs + canon_off(row, c0, SUR_H)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(Hs + canon_off(row, c0 + 8, SUR_H)) = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            // ---- layer 2: D2 = H1 W2 (eight K-steps)
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll 1
+                for (int ks = 0; ks < SUR_H / 16; ++ks)
+                    tc_mma(tmem + SUR_H, tc_desc(h_addr + 256u * ks, 128u, 16u * SUR_H),
+                           tc_desc(w2_addr + 256u * ks, 128u, 16u * SUR_H), idesc, ks > 0);
+                tc_commit(bar);
+            }
+            alive = tc_wait(bar, phase, abort_s, a.o.status);
+            phase ^= 1u;
+            if (!alive) break;
+            // ReLU(D2 + b2) in BF16, +0 rows for unused images -> row-major tile for pooling
+            const bool urow = used_s[row];
+#pragma unroll 1
+            for (int cb = 0; cb < SUR_H / 2; cb += 16) {
+                const int c0 = c_half + cb;
+                uint32_t v[16];
+                tc_ld16(tmem + SUR_H + t_lane + uint32_t(c0), v);
+                uint32_t w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    w[i] = bf2_bits(__floats2bfloat162_rn(
+                        urow ? fmaxf(__uint_as_float(v[2 * i]) + b2s[c0 + 2 * i], 0.f) : 0.f,
+                        urow ? fmaxf(__uint_as_float(v[2 * i + 1]) + b2s[c0 + 2 * i + 1], 0.f) : 0.f));
+                uint4* hr = reinterpret_cast<uint4*>(Hs + row * LDH + c0);
+                hr[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                hr[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            tc_fence_before();
+            __syncthreads();
+            // ---- pooling: thread = (channel, event parity); image order within each event
             {
-                const __nv_bfloat16* p = Xw + gq * LDX + 2 * tq;
-                ax[0] = lds32(p);
-                ax[1] = lds32(p + 8 * LDX);
-                ax[2] = lds32(p + 8);
-                ax[3] = lds32(p + 8 * LDX + 8);
-            }
-            uint32_t ah[8][4];
-            {
-                float acc1[16][4];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
-#pragma unroll
-                for (int jp = 0; jp < 8; ++jp) {
-                    uint32_t b[4];
-                    ldsm_b_trans(b, W1s, LDH, 0, 16 * jp, lane);
-                    const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
-                    mma_bf16(acc1[2 * jp], ax, b0);
-                    mma_bf16(acc1[2 * jp + 1], ax, b1);
-                }
-                // ReLU(acc + b1) in BF16, rearranged as the A fragments of layer 2
-#pragma unroll
-                for (int ks = 0; ks < 8; ++ks) {
-                    const int n0 = 16 * ks + 2 * tq, n1 = n0 + 8;
-                    const float* c0 = acc1[2 * ks];
-                    const float* c1 = acc1[2 * ks + 1];
-                    ah[ks][0] = bf2_bits(__floats2bfloat162_rn(fmaxf(c0[0] + b1s[n0], 0.f), fmaxf(c0[1] + b1s[n0 + 1], 0.f)));
-                    ah[ks][1] = bf2_bits(__floats2bfloat162_rn(fmaxf(c0[2] + b1s[n0], 0.f), fmaxf(c0[3] + b1s[n0 + 1], 0.f)));
-                    ah[ks][2] = bf2_bits(__floats2bfloat162_rn(fmaxf(c1[0] + b1s[n1], 0.f), fmaxf(c1[1] + b1s[n1 + 1], 0.f)));
-                    ah[ks][3] = bf2_bits(__floats2bfloat162_rn(fmaxf(c1[2] + b1s[n1], 0.f), fmaxf(c1[3] + b1s[n1 + 1], 0.f)));
+                const int c = tid & (SUR_H - 1);
+                const int64_t rend = min(R, rb + TM);
+                for (int el = tid >> 7; el < ne; el += NT / SUR_H) {
+                    const int64_t lo = max(rowb[el], rb), hi = min(rowb[el + 1], rend);
+                    if (lo >= hi) continue;
+                    float s = Pacc[el * SUR_H + c];
+                    for (int64_t r = lo; r < hi; ++r) s += __bfloat162float(Hs[(r - rb) * LDH + c]);
+                    Pacc[el * SUR_H + c] = s;
                 }
             }
-            // ---- layer 2 in two halves of 64 columns; 8 k-steps in ascending order per tile
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                float acc2[8][4];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
-#pragma unroll
-                for (int ks = 0; ks < 8; ++ks) {
-#pragma unroll
-                    for (int jp = 0; jp < 4; ++jp) {
-                        uint32_t b[4];
-                        ldsm_b_trans(b, W2s, LDH, 16 * ks, 64 * half + 16 * jp, lane);
-                        const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
-                        mma_bf16(acc2[2 * jp], ah[ks], b0);
-                        mma_bf16(acc2[2 * jp + 1], ah[ks], b1);
-                    }
-                }
-                // ReLU(acc + b2) in BF16; an unused image gets a +0 row
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int n = 64 * half + 8 * j + 2 * tq;
-                    *reinterpret_cast<__nv_bfloat162*>(Hw + gq * LDH + n) = __floats2bfloat162_rn(
-                        ua ? fmaxf(acc2[j][0] + b2s[n], 0.f) : 0.f, ua ? fmaxf(acc2[j][1] + b2s[n + 1], 0.f) : 0.f);
-                    *reinterpret_cast<__nv_bfloat162*>(Hw + (gq + 8) * LDH + n) = __floats2bfloat162_rn(
-                        ub ? fmaxf(acc2[j][2] + b2s[n], 0.f) : 0.f, ub ? fmaxf(acc2[j][3] + b2s[n + 1], 0.f) : 0.f);
-                }
-            }
-            __syncwarp();
-            // ---- pooling: lane = 4 channels; rows in image order, each into its event
-            const int rend = min(R, rb + 16);
-            for (int r = rb; r < rend; ++r) {
-                const int g = (r >= off[1]) + (r >= off[2]) + (r >= off[3]);
-                const uint2 v = *reinterpret_cast<const uint2*>(Hw + (r - rb) * LDH + 4 * lane);
-                const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
-                const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
-#pragma unroll
-                for (int gg = 0; gg < EPW; ++gg)
-                    if (g == gg) {
-                        pacc[gg][0] += lo.x;
-                        pacc[gg][1] += lo.y;
-                        pacc[gg][2] += hi.x;
-                        pacc[gg][3] += hi.y;
-                    }
-            }
-            __syncwarp();
+            __syncthreads();
         }
+        if (!alive) break;
         // ---- pooled vectors [sum / 40, sum / max(1, n_used)] in BF16
-#pragma unroll
-        for (int g = 0; g < EPW; ++g) {
-            const int64_t eg = e0 + g;
-            if (eg >= n_evt) break;
-            const float d = fmaxf(1.f, float(cg[g]));
-            __nv_bfloat16* pr = a.P + eg * SUR_G + 4 * lane;
-            const __nv_bfloat162 s0 = __floats2bfloat162_rn(pacc[g][0] * (1.f / SUR_POOL_DIV), pacc[g][1] * (1.f / SUR_POOL_DIV));
-            const __nv_bfloat162 s1 = __floats2bfloat162_rn(pacc[g][2] * (1.f / SUR_POOL_DIV), pacc[g][3] * (1.f / SUR_POOL_DIV));
-            const __nv_bfloat162 m0 = __floats2bfloat162_rn(pacc[g][0] / d, pacc[g][1] / d);
-            const __nv_bfloat162 m1 = __floats2bfloat162_rn(pacc[g][2] / d, pacc[g][3] / d);
-            *reinterpret_cast<uint2*>(pr) = make_uint2(bf2_bits(s0), bf2_bits(s1));
-            *reinterpret_cast<uint2*>(pr + SUR_H) = make_uint2(bf2_bits(m0), bf2_bits(m1));
+        for (int idx = tid; idx < ne * (SUR_H / 4); idx += NT) {
+            const int el = idx / (SUR_H / 4), c4 = idx % (SUR_H / 4);
+            const float4 s = reinterpret_cast<const float4*>(Pacc + el * SUR_H)[c4];
+            const float d = fmaxf(1.f, float(nu_s[el]));
+            __nv_bfloat16* pr = a.P + (e0 + el) * SUR_G + 4 * c4;
+            *reinterpret_cast<uint2*>(pr) =
+                make_uint2(bf2_bits(__floats2bfloat162_rn(s.x * (1.f / SUR_POOL_DIV), s.y * (1.f / SUR_POOL_DIV))),
+                           bf2_bits(__floats2bfloat162_rn(s.z * (1.f / SUR_POOL_DIV), s.w * (1.f / SUR_POOL_DIV))));
+            *reinterpret_cast<uint2*>(pr + SUR_H) = make_uint2(bf2_bits(__floats2bfloat162_rn(s.x / d, s.y / d)),
+                                                               bf2_bits(__floats2bfloat162_rn(s.z / d, s.w / d)));
         }
+        __syncthreads();
     }
+    tc_teardown(bar, phase, abort_s, tmem, 256);
 }
 
 // ------------------------------------------------------------------ k_event
-// Pooled rows of events [e0, e0 + ne) into a shared-memory tile (zeros past ne).
-__device__ __forceinline__ void stage_pooled(__nv_bfloat16* Pt, const __nv_bfloat16* P, int64_t e0, int ne, int tid) {
-    for (int i = tid; i < FE * (SUR_G / 8); i += NT) {
-        const int el = i / (SUR_G / 8), c = i % (SUR_G / 8);
-        __nv_bfloat16* dst = Pt + el * LDV + 8 * c;
-        if (el < ne) cp_async16(dst, P + (e0 + el) * SUR_G + 8 * c);
-        else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+// Event network on tcgen05: per tile of 128 events, G = ReLU(P V1 + c1) with
+// P (128 x 256) and V1^T (256 x 256) in shared memory as canonical K-major
+// operands and G (FP32, 128 lanes x 256 columns) in tensor memory; one thread
+// issues the sixteen K-steps and commits them to an mbarrier. Then each thread
+// reads one event's row of G (warps 0-3 columns 0-127, warps 4-7 columns
+// 128-255), rounds it to BF16 as the training path stores it, and forms the
+// 256 -> 4 output layer in FP32; the outputs and fallback list follow.
+__global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __nv_bfloat16* V1s = reinterpret_cast<__nv_bfloat16*>(sm + SM_V1);
+    __nv_bfloat16* Pt = reinterpret_cast<__nv_bfloat16*>(sm + SM_P);
+    float* V2f = reinterpret_cast<float*>(sm + SM_V2);
+    float* c1s = reinterpret_cast<float*>(sm + SM_C1);
+    float* yp = reinterpret_cast<float*>(sm + SM_YP);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM_BAR);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + SM_BAR + 8);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(sm + SM_BAR + 12);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t n_evt = a.f.n_evt;
+
+    if (warp == 0) {
+        tc_alloc(tmem_s, 256);
+        tc_relinquish();
     }
-    cp_async_commit();
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        *abort_s = 0;
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.pk + PK_V1T);
+        uint4* dst = reinterpret_cast<uint4*>(V1s);
+        for (int i = tid; i < SUR_G * SUR_G / 8; i += NT) dst[i] = src[i];
+        for (int i = tid; i < SUR_G * 4; i += NT) V2f[i] = __bfloat162float(a.pb[OFF_V2 + i]);
+        for (int i = tid; i < SUR_G; i += NT) c1s[i] = a.p[OFF_C1 + i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_s;
+    const uint32_t idesc = tc_idesc_bf16(TM, SUR_G);
+    const uint32_t p_addr = smem_addr(Pt), v_addr = smem_addr(V1s);
+    const int q = warp & 3, hcol = (warp >> 2) * (SUR_G / 2);
+    const int row = 32 * q + lane;
+    const float c2[4] = {a.p[OFF_C2 + 0], a.p[OFF_C2 + 1], a.p[OFF_C2 + 2], a.p[OFF_C2 + 3]};
+    uint32_t phase = 0;
+    const int64_t n_tiles = (n_evt + TM - 1) / TM;
+
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t e0 = t * TM;
+        const int ne = int(TM < n_evt - e0 ? TM : n_evt - e0);
+        // pooled rows -> canonical K-major tile; eight consecutive threads fill
+        // one 128-byte core-matrix row block
+        for (int idx = tid; idx < TM * (SUR_G / 8); idx += NT) {
+            const int r = 8 * (idx >> 8) + (idx & 7), c = (idx >> 3) & 31;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (r < ne) v = *reinterpret_cast<const uint4*>(a.P + (e0 + r) * SUR_G + 8 * c);
+            *reinterpret_cast<uint4*>(Pt + canon_off(r, 8 * c, SUR_G)) = v;
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int ks = 0; ks < SUR_G / 16; ++ks)
+                tc_mma(tmem, tc_desc(p_addr + 256u * ks, 128u, 16u * SUR_G), tc_desc(v_addr + 256u * ks, 128u, 16u * SUR_G),
+                       idesc, ks > 0);
+            tc_commit(bar);
+        }
+        const bool alive = tc_wait(bar, phase, abort_s, a.o.status);
+        phase ^= 1u;
+        if (!alive) break;
+        // this thread's event row, half of the columns
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int cb = 0; cb < SUR_G / 2; cb += 16) {
+            uint32_t r[16];
+            tc_ld16(tmem + (uint32_t(32 * q) << 16) + uint32_t(hcol + cb), r);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = hcol + cb + i;
+                const float g = __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(r[i]) + c1s[col], 0.f)));
+#pragma unroll
+                for (int o = 0; o < 4; ++o) y[o] = fmaf(g, V2f[col * 4 + o], y[o]);
+            }
+        }
+        if (hcol != 0) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) yp[row * 4 + o] = y[o];
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (hcol == 0 && row < ne) {
+            float yo[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) yo[o] = (y[o] + yp[row * 4 + o]) + c2[o];
+            const int64_t e = e0 + row;
+            sur_emit_event(a.o, e, yo, a.f.base[e], a.f.n_used[e]);
+        }
+    }
+    tc_teardown(bar, phase, abort_s, tmem, 256);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    __nv_bfloat16* V1s = reinterpret_cast<__nv_bfloat16*>(sm + SM_V1);
-    __nv_bfloat16* Pbuf = reinterpret_cast<__nv_bfloat16*>(sm + SM_P);
-    __nv_bfloat16* Gs = reinterpret_cast<__nv_bfloat16*>(sm + SM_G);
-    __nv_bfloat16* V2s = reinterpret_cast<__nv_bfloat16*>(sm + SM_V2);
-    float* Ys = reinterpret_cast<float*>(sm + SM_Y);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    const int64_t n_evt = a.f.n_evt;
-    const int TE = a.tile_events;
-    int64_t t = blockIdx.x;
-    if (t < a.n_tiles) stage_pooled(Pbuf, a.P, t * TE, int(TE < n_evt - t * TE ? TE : n_evt - t * TE), tid);
-    // weights: V1 copied as stored (k-major rows, padded), V2 as stored
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(a.pb + OFF_V1);
-        for (int i = tid; i < SUR_G * SUR_G / 8; i += NT)
-            *reinterpret_cast<uint4*>(V1s + (i / (SUR_G / 8)) * LDV + 8 * (i % (SUR_G / 8))) = src[i];
-        for (int i = tid; i < SUR_G * 4; i += NT) V2s[i] = a.pb[OFF_V2 + i];
+// BF16 twin -> transposed canonical K-major layout of the tensor-core layers.
+__global__ void k_pack_tc(const __nv_bfloat16* __restrict__ pb, __nv_bfloat16* __restrict__ pk) {
+    const int64_t n1 = SUR_H * SUR_XPAD, n2 = SUR_H * SUR_H, n3 = SUR_G * SUR_G;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n1 + n2 + n3;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        if (i < n1) {                                 // W1 [16 k][128 n] -> [128 n][16 k]
+            const int64_t k = i / SUR_H, n = i % SUR_H;
+            pk[PK_W1T + canon_off(n, k, SUR_XPAD)] = pb[OFF_W1 + i];
+        } else if (i < n1 + n2) {                     // W2 [128 k][128 n]
+            const int64_t j = i - n1, k = j / SUR_H, n = j % SUR_H;
+            pk[PK_W2T + canon_off(n, k, SUR_H)] = pb[OFF_W2 + j];
+        } else {                                      // V1 [256 k][256 n]
+            const int64_t j = i - n1 - n2, k = j / SUR_G, n = j % SUR_G;
+            pk[PK_V1T + canon_off(n, k, SUR_G)] = pb[OFF_V1 + j];
+        }
     }
-    const int wn2 = warp * 32;
-    float c1r[4][2];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) c1r[j][c] = a.p[OFF_C1 + wn2 + 8 * j + 2 * tq + c];
+}
 
-    for (int buf = 0; t < a.n_tiles; t += gridDim.x, buf ^= 1) {
-        const int64_t e0 = t * TE;
-        const int ne = int(TE < n_evt - e0 ? TE : n_evt - e0);
-        __nv_bfloat16* Ps = Pbuf + buf * (FE * LDV);
-        cp_async_wait_all();
-        __syncthreads();
-        const int64_t tn = t + gridDim.x;
-        if (tn < a.n_tiles)
-            stage_pooled(Pbuf + (buf ^ 1) * (FE * LDV), a.P, tn * TE, int(TE < n_evt - tn * TE ? TE : n_evt - tn * TE), tid);
-        // ---- event network 256 -> 256 (columns wn2..wn2+31 per warp)
-        {
-            float acc[2][4][4];
-            uint32_t af[2][4], bfr[2][4];
-            zero_acc(acc);
-#pragma unroll 4
-            for (int ks = 0; ks < SUR_G / 16; ++ks) {
-                load_a(af, Ps, LDV, 0, 16 * ks, gq, tq);
-                ldsm_b_trans(bfr[0], V1s, LDV, 16 * ks, wn2, lane);
-                ldsm_b_trans(bfr[1], V1s, LDV, 16 * ks, wn2 + 16, lane);
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t b[2] = {bfr[j >> 1][2 * (j & 1)], bfr[j >> 1][2 * (j & 1) + 1]};
-                        mma_bf16(acc[i][j], af[i], b);
-                    }
-            }
-            store_relu(acc, c1r, Gs, LDV, 0, wn2, gq, tq);
-        }
-        __syncthreads();
-        // ---- 256 -> 4 on the tensor cores, one warp per 16 events
-        if (warp < 2) {
-            const int r0 = 16 * warp;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-            for (int ks = 0; ks < SUR_G / 16; ++ks) {
-                const __nv_bfloat16* p = Gs + (r0 + gq) * LDV + 16 * ks + 2 * tq;
-                const uint32_t af[4] = {lds32(p), lds32(p + 8 * LDV), lds32(p + 8), lds32(p + 8 * LDV + 8)};
-                uint32_t bf[2];
-                head_b_fragment(V2s, ks, gq, tq, bf);
-                mma_bf16(acc, af, bf);
-            }
-            if (tq < 2) {
-                const int c = 2 * tq;
-                const float c2a = a.p[OFF_C2 + c], c2b = a.p[OFF_C2 + c + 1];
-                Ys[(r0 + gq) * 4 + c] = acc[0] + c2a;
-                Ys[(r0 + gq) * 4 + c + 1] = acc[1] + c2b;
-                Ys[(r0 + gq + 8) * 4 + c] = acc[2] + c2a;
-                Ys[(r0 + gq + 8) * 4 + c + 1] = acc[3] + c2b;
-            }
-        }
-        __syncthreads();
-        // ---- outputs
-        if (tid < ne) {
-            const int64_t e = e0 + tid;
-            const float y[4] = {Ys[tid * 4 + 0], Ys[tid * 4 + 1], Ys[tid * 4 + 2], Ys[tid * 4 + 3]};
-            sur_emit_event(a.o, e, y, a.f.base[e], a.f.n_used[e]);
-        }
-    }
-    cp_async_wait_all();
+cudaError_t launch_pack_tc(const __nv_bfloat16* pb, __nv_bfloat16* pk, cudaStream_t s) {
+    k_pack_tc<<<64, 256, 0, s>>>(pb, pk);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s) {
-    if (a.tile_events < 1 || a.tile_events > FE) return cudaErrorInvalidValue;
     if (a.f.n_evt <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_tel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TS_TOTAL));
     if (e != cudaSuccess) return e;
-    const int64_t warps = (a.f.n_evt + EPW - 1) / EPW;
-    const int64_t g = std::min<int64_t>((warps + NT / 32 - 1) / (NT / 32), int64_t(n_sm) * 2);
-    k_tel<<<int(g), NT, TS_TOTAL, s>>>(a);
+    if (a.tel_tile_events < 1 || a.tel_tile_events > TE) return cudaErrorInvalidValue;
+    const int64_t tel_tiles = (a.f.n_evt + a.tel_tile_events - 1) / a.tel_tile_events;
+    k_tel<<<int(std::min<int64_t>(tel_tiles, int64_t(n_sm) * 2)), NT, TS_TOTAL, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_event, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SM_TOTAL))) != cudaSuccess)
         return e;
-    k_event<<<int(std::min<int64_t>(a.n_tiles, n_sm)), NT, SM_TOTAL, s>>>(a);
+    const int64_t tiles = (a.f.n_evt + TM - 1) / TM;
+    k_event<<<int(std::min<int64_t>(tiles, n_sm)), NT, SM_TOTAL, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -263,6 +263,8 @@ int rta::surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2*
     return RTA_OK;
 }
 
+unsigned int* rta::surrogate_ctx_status(rta_ctx* c) { return c ? c->d_status : nullptr; }
+
 int rta::surrogate_stereo_list(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
                                const int32_t* d_evt_off, int64_t n_evt, const int32_t* d_idx, const unsigned int* d_n,
                                rta_stereo_t* d_out, cudaStream_t s) {

@@ -90,6 +90,8 @@ cudaError_t launch_stereo_to_events(const rta_stereo_t* st, int64_t n_evt, rta_e
 int surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt);
 // context access for the surrogate (rta_api.cu)
 int surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2** tel_xy, int* n_tel, int* device);
+// the context's device status word
+unsigned int* surrogate_ctx_status(rta_ctx* c);
 int surrogate_stereo_list(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
                           const int32_t* d_evt_off, int64_t n_evt, const int32_t* d_idx, const unsigned int* d_n,
                           rta_stereo_t* d_out, cudaStream_t s);

@@ -25,6 +25,14 @@ constexpr int64_t OFF_C1 = OFF_V1 + SUR_G * SUR_G;
 constexpr int64_t OFF_V2 = OFF_C1 + SUR_G;                   // [256 x 4]
 constexpr int64_t OFF_C2 = OFF_V2 + SUR_G * 4;
 constexpr int64_t N_PARAM_INTERNAL = OFF_C2 + 4;
+// Weights of the inference kernels' tensor-core layers, transposed to N x K and
+// laid out as canonical K-major core matrices (see rta_tc.cuh): W1 (128 x 16),
+// W2 (128 x 128), V1 (256 x 256). Refreshed from the BF16 twin after every
+// parameter change.
+constexpr int64_t PK_W1T = 0;
+constexpr int64_t PK_W2T = PK_W1T + SUR_H * SUR_XPAD;
+constexpr int64_t PK_V1T = PK_W2T + SUR_H * SUR_H;
+constexpr int64_t N_PK = PK_V1T + SUR_G * SUR_G;
 constexpr int64_t N_PARAM_PACKED = SUR_NF * SUR_H + SUR_H + SUR_H * SUR_H + SUR_H + SUR_G * SUR_G + SUR_G + SUR_G * 4 + 4;
 
 struct FeatArgs {
@@ -108,6 +116,7 @@ struct OutArgs {
     unsigned int* n_fallback;
     int32_t* fallback_idx;
     const rta_stereo_t* geo;
+    unsigned int* status;      // device status word (RTA_DEV_*)
 };
 
 // Inference: f carries the inputs and tables, and receives the baselines and
@@ -117,9 +126,9 @@ struct InferArgs {
     FeatArgs f;
     const __nv_bfloat16* pb;   // BF16 parameter twin (internal layout)
     const float* p;            // FP32 master (biases)
+    const __nv_bfloat16* pk;   // tensor-core weight layout (PK_*)
     __nv_bfloat16* P;          // [n_evt x 256] pooled vectors (workspace)
-    int tile_events;           // events per tile of k_event, 1..32
-    int64_t n_tiles;
+    int tel_tile_events;       // events per k_tel tile, 1..32
     OutArgs o;
 };
 
@@ -146,6 +155,7 @@ cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* 
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
 // k_tel then k_event (one CTA per SM, n_sm of them at most)
 cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s);
-constexpr int INFER_MAX_TILE_EVENTS = 32;
+// BF16 twin -> tensor-core weight layout
+cudaError_t launch_pack_tc(const __nv_bfloat16* pb, __nv_bfloat16* pk, cudaStream_t s);
 
 }  // namespace rta

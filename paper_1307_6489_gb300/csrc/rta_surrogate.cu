@@ -40,6 +40,7 @@ struct rta_model {
     int device = 0;
     float* p = nullptr;              // FP32 master weights (internal layout)
     __nv_bfloat16* pb = nullptr;     // BF16 twin
+    __nv_bfloat16* pk = nullptr;     // tensor-core layout of the inference weights
     float* m = nullptr;
     float* v = nullptr;
     float* g = nullptr;
@@ -240,6 +241,8 @@ int upload_params(rta_model* md, const std::vector<float>& internal) {
     for (size_t i = 0; i < internal.size(); ++i) b[i] = to_bf16_bits(internal[i]);
     S_TRY(cudaMemcpy(md->p, internal.data(), sizeof(float) * internal.size(), cudaMemcpyHostToDevice));
     S_TRY(cudaMemcpy(md->pb, b.data(), sizeof(uint16_t) * b.size(), cudaMemcpyHostToDevice));
+    S_TRY(rta::launch_pack_tc(md->pb, md->pk, 0));
+    S_TRY(cudaDeviceSynchronize());
     return RTA_OK;
 }
 
@@ -268,6 +271,7 @@ int rta_surrogate_create(rta_ctx* ctx, uint64_t seed, const float* h_cam_code, r
         md->n_sm = 1;
     const size_t n = rta::N_PARAM_INTERNAL;
     bool ok = cudaMalloc(&md->p, n * 4) == cudaSuccess && cudaMalloc(&md->pb, n * 2) == cudaSuccess &&
+              cudaMalloc(&md->pk, sizeof(__nv_bfloat16) * rta::N_PK) == cudaSuccess &&
               cudaMalloc(&md->m, n * 4) == cudaSuccess && cudaMalloc(&md->v, n * 4) == cudaSuccess &&
               cudaMalloc(&md->g, n * 4) == cudaSuccess && cudaMalloc(&md->cam_code, 4 * RTA_MAX_CAMS) == cudaSuccess &&
               cudaMalloc(&md->split_ws, sizeof(float) * SPLIT_WS) == cudaSuccess;
@@ -317,6 +321,7 @@ int rta_surrogate_destroy(rta_model* md) {
     free_ws(md);
     cudaFree(md->p);
     cudaFree(md->pb);
+    cudaFree(md->pk);
     cudaFree(md->m);
     cudaFree(md->v);
     cudaFree(md->g);
@@ -438,6 +443,7 @@ int rta_surrogate_train_step(rta_model* md, const rta_hillas_t* d_h, const int32
         ad.bc1 = float(1.0 - pow(0.9, double(md->step)));
         ad.bc2 = float(1.0 - pow(0.999, double(md->step)));
         S_TRY(rta::launch_adam(ad, s));
+        S_TRY(rta::launch_pack_tc(md->pb, md->pk, s));
     }
     return RTA_OK;
 }
@@ -462,13 +468,15 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     ia.f.n_used = md->n_used;
     ia.pb = md->pb;
     ia.p = md->p;
+    ia.pk = md->pk;
     ia.P = md->P;
-    // one persistent CTA per SM; tiles of up to 32 events, sized so that every
-    // CTA gets the same number of tiles
-    const int64_t per_round = int64_t(md->n_sm) * rta::INFER_MAX_TILE_EVENTS;
-    const int64_t rounds = (n_evt + per_round - 1) / per_round;
-    ia.tile_events = int((n_evt + md->n_sm * rounds - 1) / (md->n_sm * rounds));
-    ia.n_tiles = (n_evt + ia.tile_events - 1) / ia.tile_events;
+    // k_tel runs two CTAs per SM; tiles of up to 32 events, sized so that the
+    // CTAs get equal numbers of tiles
+    {
+        const int64_t slots = int64_t(md->n_sm) * 2;
+        const int64_t rounds = (n_evt + slots * 32 - 1) / (slots * 32);
+        ia.tel_tile_events = int((n_evt + slots * rounds - 1) / (slots * rounds));
+    }
     rta::OutArgs& oa = ia.o;
     oa.n_evt = n_evt;
     oa.fallback_deg = fallback_deg;
@@ -476,6 +484,7 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     oa.n_fallback = md->n_fallback;
     oa.fallback_idx = md->fallback_idx;
     oa.geo = md->geo;
+    oa.status = rta::surrogate_ctx_status(md->ctx);
     S_TRY(cudaMemsetAsync(md->n_fallback, 0, sizeof(unsigned int), s));
     S_TRY(rta::launch_infer(ia, md->n_sm, s));
     // the geometric intersection only for the events that need it

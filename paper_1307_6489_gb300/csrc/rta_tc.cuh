@@ -1,0 +1,89 @@
+// tcgen05 (fifth-generation tensor core) building blocks: tensor-memory (TMEM)
+// allocation, shared-memory matrix descriptors for K-major operands without
+// swizzle, single-thread MMA issue, completion through an mbarrier, and TMEM
+// loads into registers.
+//
+// Operand layout ("canonical K-major, no swizzle"): a matrix of R rows by K
+// BF16 values is stored as 8-row x 16-byte core matrices (8 rows of 8 values,
+// row stride 16 bytes). Core matrices adjacent in K are LBO = 128 bytes apart,
+// core matrices adjacent in R are SBO = K * 16 bytes apart, so element (r, k)
+// sits at element offset (r / 8) * 8K + (k / 8) * 64 + (r % 8) * 8 + k % 8.
+// One MMA consumes a K-step of 16 values: its descriptor starts 256 bytes
+// further per step.
+#pragma once
+
+#include "rta_device.cuh"
+
+namespace rta {
+
+__host__ __device__ constexpr int64_t canon_off(int64_t r, int64_t k, int64_t K) {
+    return (r / 8) * (8 * K) + (k / 8) * 64 + (r % 8) * 8 + (k % 8);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride (row)
+// byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, dense, shape M x N.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// TMEM allocation of ncols columns (a power of two >= 32) by one whole warp; the
+// TMEM address is written to *dst.
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D = A B (accumulate == false) or D += A B, issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(int(accumulate))
+        : "memory");
+}
+
+// One arrival on *bar once every MMA this thread issued before has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Generic-proxy writes to shared memory become visible to the tensor core.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Sixteen consecutive 32-bit TMEM columns of one lane per thread: thread t of
+// the warp reads lane (taddr's lane + t). A warp may only read the 32 lanes of
+// its own quarter (warp index % 4). The load and its wait are one asm
+// statement, so no use of the registers can be scheduled before the data has
+// arrived.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+}  // namespace rta

@@ -153,9 +153,10 @@ def test_inference_flags_and_geometric_fallback(setup):
         ok = fb & (st["flags"] == 0)
         np.testing.assert_array_equal(ev["dir_x"][ok], st["dir_x"][ok])
         keep = ~fb & ~nodir
-        np.testing.assert_allclose(ev["dir_x"][keep], b[keep, 0] + y[keep, 1], rtol=0, atol=1e-6)
-        np.testing.assert_allclose(ev["log_energy"], y[:, 0], rtol=0, atol=0)
-        np.testing.assert_allclose(ev["gammaness"], 1 / (1 + np.exp(-y[:, 3].astype(np.float64))), atol=1e-6)
+        # the inference kernels sum the event network in the tensor core's own order
+        np.testing.assert_allclose(ev["dir_x"][keep], b[keep, 0] + y[keep, 1], rtol=0, atol=2e-3)
+        assert np.max(np.abs(ev["log_energy"] - y[:, 0]) / (1 + np.abs(y[:, 0]))) <= 2e-3
+        np.testing.assert_allclose(ev["gammaness"], 1 / (1 + np.exp(-y[:, 3].astype(np.float64))), atol=2e-3)
 
 
 def test_trained_network_gains_over_the_geometric_reconstruction():
@@ -223,20 +224,28 @@ def _infer_and_forward(s, a, b, merge=1, break_offsets=False):
 
 
 @pytest.mark.parametrize("case", ["all", "one", "ragged", "hundreds_of_images", "malformed"])
-def test_fused_inference_equals_the_layer_by_layer_forward(setup, case):
-    """The fused kernel keeps every expression and summation order of the
-    training-path kernels, so its outputs equal theirs bit for bit."""
+def test_inference_kernels_agree_with_the_layer_by_layer_forward(setup, case):
+    """The inference kernels (baseline, features, telescope network and pooling
+    with the training path's expressions and orders; event network on tcgen05)
+    against the training-path forward on the same batch: baselines and used
+    counts bit for bit, outputs within FP32 accumulation-order effects. The
+    event network's products are exact and its sums FP32 in both, in a
+    different order; a BF16 rounding of an activation can flip by one unit, so
+    the bound is 2e-3 (1 + |y|)."""
     s = setup
     n = s["wl"].n_evt
     a, b, merge, brk = {"all": (0, n, 1, False), "one": (7, 8, 1, False), "ragged": (5, 5 + 211, 1, False),
                         "hundreds_of_images": (0, n, 25, False), "malformed": (0, 64, 1, True)}[case]
     ev, y, base = _infer_and_forward(s, a, b, merge, brk)
-    np.testing.assert_array_equal(ev["log_energy"].view(np.uint32), y[:, 0].view(np.uint32))
     np.testing.assert_array_equal(ev["base_x"].view(np.uint32), base[:, 0].view(np.uint32))
     np.testing.assert_array_equal(ev["base_y"].view(np.uint32), base[:, 1].view(np.uint32))
-    np.testing.assert_array_equal(ev["dir_x"], base[:, 0] + y[:, 1])
-    np.testing.assert_array_equal(ev["dir_y"], base[:, 1] + y[:, 2])
-    np.testing.assert_allclose(ev["gammaness"], 1 / (1 + np.exp(-y[:, 3].astype(np.float64))), rtol=0, atol=1e-6)
+    tol = 2e-3 * (1 + np.abs(y))
+    dy = np.stack([ev["log_energy"] - y[:, 0], ev["dir_x"] - base[:, 0] - y[:, 1], ev["dir_y"] - base[:, 1] - y[:, 2]],
+                  axis=1)
+    print(case, "max |dy| / (1 + |y|):", np.max(np.abs(dy) / (1 + np.abs(y[:, :3]))))
+    assert (np.abs(dy) <= tol[:, :3]).all()
+    sig = 1 / (1 + np.exp(-y[:, 3].astype(np.float64)))
+    assert np.max(np.abs(ev["gammaness"] - sig)) <= 2e-3
     assert ((ev["flags"] & rta.RTA_EF_FALLBACK) == 0).all()
     np.testing.assert_array_equal((ev["flags"] & rta.RTA_EF_NO_DIRECTION) != 0, ev["n_used"] < 2)
     if case == "malformed":
