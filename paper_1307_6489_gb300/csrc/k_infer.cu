@@ -47,10 +47,14 @@ constexpr size_t TS_LO = TS_BASE + size_t(TE) * 8;               // int [32] fir
 constexpr size_t TS_CNT = TS_LO + size_t(TE) * 4;                // int [32] rows
 constexpr size_t TS_NU = TS_CNT + size_t(TE) * 4;                // int [32] used images (0 if malformed)
 constexpr size_t TS_USED = TS_NU + size_t(TE) * 4;               // u8 [128]
-constexpr size_t TS_BAR = TS_USED + TM;                          // mbarrier, TMEM address, abort flag
+constexpr size_t TS_TCAM = TS_USED + TM;                         // int [1024] camera of each telescope
+constexpr size_t TS_TXY = TS_TCAM + size_t(RTA_MAX_TEL) * 4;     // float2 [1024] telescope positions
+constexpr size_t TS_CODE = TS_TXY + size_t(RTA_MAX_TEL) * 8;     // f32 [16] camera codes
+constexpr size_t TS_BAR = TS_CODE + size_t(RTA_MAX_CAMS) * 4;    // MMA mbarrier, load mbarrier, TMEM address, abort flag
 constexpr size_t TS_TOTAL = TS_BAR + 32;
 static_assert(TS_H % 16 == 0 && TS_X % 16 == 0 && TS_W2 % 16 == 0, "16-byte aligned operand tiles");
-static_assert(TS_BAR % 8 == 0 && TS_ROWB % 8 == 0, "aligned barrier and row table");
+static_assert(TS_BAR % 8 == 0 && TS_ROWB % 8 == 0 && TS_TXY % 8 == 0, "aligned barriers and tables");
+static_assert(TS_W2 == TS_W1 + size_t(PK_W2T - PK_W1T) * 2, "W1^T and W2^T are one contiguous copy");
 static_assert(2 * TS_TOTAL <= 227 * 1024, "two k_tel CTAs per SM");
 
 // k_event shared memory
@@ -59,9 +63,16 @@ constexpr size_t SM_P = SM_V1 + size_t(SUR_G) * SUR_G * 2;       // bf16 pooled 
 constexpr size_t SM_V2 = SM_P + size_t(TM) * SUR_G * 2;          // f32 [256][4]
 constexpr size_t SM_C1 = SM_V2 + size_t(SUR_G) * 4 * 4;          // f32 [256]
 constexpr size_t SM_YP = SM_C1 + size_t(SUR_G) * 4;              // f32 [128][4] second-half partial outputs
-constexpr size_t SM_BAR = SM_YP + size_t(TM) * 4 * 4;            // mbarrier, TMEM address, abort flag
+constexpr size_t SM_BAR = SM_YP + size_t(TM) * 4 * 4;            // MMA mbarrier, load mbarrier, TMEM address, abort flag
 constexpr size_t SM_TOTAL = SM_BAR + 32;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory per CTA");
+
+// One thread: copy `bytes` (a multiple of 16) from global to shared memory with
+// the bulk-copy engine in pieces of at most 32 KB, all completing on bar.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
+    for (uint32_t o = 0; o < bytes; o += 32768u)
+        bulk_g2s(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o, min(32768u, bytes - o), bar, policy);
+}
 
 // Wait for the MMAs committed to bar (phase `phase`); on a timeout flag the
 // status word and the CTA's abort flag. Every thread calls it; returns false
@@ -77,15 +88,18 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase, volatile 
     return true;
 }
 
-// Release the CTA's tensor memory. After an abort, one more bounded wait lets
-// MMAs still in flight finish first.
-__device__ __forceinline__ void tc_teardown(uint64_t* bar, uint32_t phase, volatile int* abort_s, uint32_t tmem,
-                                            uint32_t ncols) {
+// Release the CTA's tensor memory. After an abort, one more bounded wait on
+// each barrier lets MMAs and copies still in flight finish first (mma_parity /
+// ld_parity: the parity of the phase that may be pending; a completed or never
+// started phase returns at once).
+__device__ __forceinline__ void tc_teardown(uint64_t* bar, uint32_t mma_parity, uint64_t* bar_ld, uint32_t ld_parity,
+                                            volatile int* abort_s, uint32_t tmem, uint32_t ncols) {
     tc_fence_before();
     __syncthreads();
     if (*abort_s && threadIdx.x == 0) {
         volatile int none = 0;
-        mbar_wait(bar, phase ^ 1u, &none);
+        mbar_wait(bar, mma_parity, &none);
+        mbar_wait(bar_ld, ld_parity, &none);
     }
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) tc_dealloc(tmem, ncols);
@@ -109,12 +123,17 @@ __global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
     int* cnt_s = reinterpret_cast<int*>(sm + TS_CNT);
     int* nu_s = reinterpret_cast<int*>(sm + TS_NU);
     uint8_t* used_s = sm + TS_USED;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TS_BAR);
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + TS_BAR + 8);
-    volatile int* abort_s = reinterpret_cast<volatile int*>(sm + TS_BAR + 12);
+    int* tcam_s = reinterpret_cast<int*>(sm + TS_TCAM);
+    float2* txy_s = reinterpret_cast<float2*>(sm + TS_TXY);
+    float* code_s = reinterpret_cast<float*>(sm + TS_CODE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TS_BAR);       // MMA completion
+    uint64_t* bar_ld = bar + 1;                                       // weight copy
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + TS_BAR + 16);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(sm + TS_BAR + 20);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const FeatArgs& f = a.f;
     const int64_t n_evt = f.n_evt, n_img = f.n_img;
+    const int n_tel = min(f.n_tel, RTA_MAX_TEL);
 
     if (warp == 0) {
         tc_alloc(tmem_s, 256);               // columns 0-127: layer 1, 128-255: layer 2
@@ -122,20 +141,42 @@ __global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
     }
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(bar_ld, 1);
         fence_mbar_init();
         *abort_s = 0;
+        // W1^T and W2^T (canonical operands) by the bulk-copy engine
+        constexpr uint32_t bytes = uint32_t(PK_V1T - PK_W1T) * 2;
+        mbar_arrive_expect_tx(bar_ld, bytes);
+        bulk_copy(W1s, a.pk + PK_W1T, bytes, bar_ld, l2_policy_evict_last());
     }
     {
-        const uint4* w1 = reinterpret_cast<const uint4*>(a.pk + PK_W1T);
-        const uint4* w2 = reinterpret_cast<const uint4*>(a.pk + PK_W2T);
-        for (int i = tid; i < SUR_H * SUR_XPAD / 8; i += NT) reinterpret_cast<uint4*>(W1s)[i] = w1[i];
-        for (int i = tid; i < SUR_H * SUR_H / 8; i += NT) reinterpret_cast<uint4*>(W2s)[i] = w2[i];
-        for (int i = tid; i < SUR_H; i += NT) {
-            b1s[i] = a.p[OFF_B1 + i];
-            b2s[i] = a.p[OFF_B2 + i];
+        // telescope tables and biases: all loads issued before any store
+        int tc[RTA_MAX_TEL / NT];
+        float2 txy[RTA_MAX_TEL / NT];
+#pragma unroll
+        for (int k = 0; k < RTA_MAX_TEL / NT; ++k) {
+            const int i = tid + k * NT;
+            tc[k] = i < n_tel ? f.tel_cam[i] : 0;
+            txy[k] = i < n_tel ? f.tel_xy[i] : make_float2(0.f, 0.f);
+        }
+        const float code = tid < RTA_MAX_CAMS ? f.cam_code[tid] : 0.f;
+        const float bb1 = tid < SUR_H ? a.p[OFF_B1 + tid] : 0.f, bb2 = tid < SUR_H ? a.p[OFF_B2 + tid] : 0.f;
+#pragma unroll
+        for (int k = 0; k < RTA_MAX_TEL / NT; ++k) {
+            const int i = tid + k * NT;
+            if (i < n_tel) {
+                tcam_s[i] = tc[k];
+                txy_s[i] = txy[k];
+            }
+        }
+        if (tid < RTA_MAX_CAMS) code_s[tid] = code;
+        if (tid < SUR_H) {
+            b1s[tid] = bb1;
+            b2s[tid] = bb2;
         }
     }
-    fence_proxy_async_smem();
+    __syncthreads();
+    bool alive = tc_wait(bar_ld, 0, abort_s, a.o.status);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -146,11 +187,10 @@ __global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
     const uint32_t t_lane = uint32_t(32 * q) << 16;
     const int sub = lane % SUR_EVT_LANES, grp = lane / SUR_EVT_LANES;
     uint32_t phase = 0;
-    bool alive = true;
     const int te = a.tel_tile_events;
     const int64_t n_tiles = (n_evt + te - 1) / te;
 
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (int64_t t = alive ? int64_t(blockIdx.x) : n_tiles; t < n_tiles; t += gridDim.x) {
         const int64_t e0 = t * te;
         const int ne = int(te < n_evt - e0 ? te : n_evt - e0);
         // ---- per-event prologue, eight lanes per event (as k_features)
@@ -211,7 +251,7 @@ __global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
                     const rta_hillas_t h = f.h[img];
                     used = sur_used(h);
                     const float2 b = base_s[lo];
-                    sur_image_features(h, f.img_tel[img], f.tel_cam, f.tel_xy, f.cam_code, f.n_tel, b.x, b.y, x);
+                    sur_image_features(h, f.img_tel[img], tcam_s, txy_s, code_s, n_tel, b.x, b.y, x);
                 } else {
 #pragma unroll
                     for (int j = 0; j < SUR_XPAD / 2; ++j) x[j] = __floats2bfloat162_rn(0.f, 0.f);
@@ -301,16 +341,18 @@ __global__ void __launch_bounds__(NT, 2) k_tel(const InferArgs a) {
             const int el = idx / (SUR_H / 4), c4 = idx % (SUR_H / 4);
             const float4 s = reinterpret_cast<const float4*>(Pacc + el * SUR_H)[c4];
             const float d = fmaxf(1.f, float(nu_s[el]));
-            __nv_bfloat16* pr = a.P + (e0 + el) * SUR_G + 4 * c4;
-            *reinterpret_cast<uint2*>(pr) =
+            const int64_t e = e0 + el, et = e / a.ev_tile_events, er = e % a.ev_tile_events;
+            __nv_bfloat16* blk = a.P + et * (TM * SUR_G);
+            *reinterpret_cast<uint2*>(blk + canon_off(er, 4 * c4, SUR_G)) =
                 make_uint2(bf2_bits(__floats2bfloat162_rn(s.x * (1.f / SUR_POOL_DIV), s.y * (1.f / SUR_POOL_DIV))),
                            bf2_bits(__floats2bfloat162_rn(s.z * (1.f / SUR_POOL_DIV), s.w * (1.f / SUR_POOL_DIV))));
-            *reinterpret_cast<uint2*>(pr + SUR_H) = make_uint2(bf2_bits(__floats2bfloat162_rn(s.x / d, s.y / d)),
-                                                               bf2_bits(__floats2bfloat162_rn(s.z / d, s.w / d)));
+            *reinterpret_cast<uint2*>(blk + canon_off(er, SUR_H + 4 * c4, SUR_G)) =
+                make_uint2(bf2_bits(__floats2bfloat162_rn(s.x / d, s.y / d)),
+                           bf2_bits(__floats2bfloat162_rn(s.z / d, s.w / d)));
         }
         __syncthreads();
     }
-    tc_teardown(bar, phase, abort_s, tmem, 256);
+    tc_teardown(bar, phase ^ 1u, bar_ld, 0u, abort_s, tmem, 256);
 }
 
 // ------------------------------------------------------------------ k_event
@@ -328,11 +370,19 @@ __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
     float* V2f = reinterpret_cast<float*>(sm + SM_V2);
     float* c1s = reinterpret_cast<float*>(sm + SM_C1);
     float* yp = reinterpret_cast<float*>(sm + SM_YP);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM_BAR);
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + SM_BAR + 8);
-    volatile int* abort_s = reinterpret_cast<volatile int*>(sm + SM_BAR + 12);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM_BAR);       // MMA completion
+    uint64_t* bar_ld = bar + 1;                                       // operand copies
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + SM_BAR + 16);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(sm + SM_BAR + 20);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_evt = a.f.n_evt;
+    const int te = a.ev_tile_events;
+    const int64_t n_tiles = (n_evt + te - 1) / te;
+    // bytes of the pooled rows of tile t: whole 8-row core-matrix groups
+    auto tile_bytes = [&](int64_t t) {
+        const int64_t ne = te < n_evt - t * te ? te : n_evt - t * te;
+        return uint32_t((ne + 7) / 8) * uint32_t(8 * SUR_G * 2);
+    };
 
     if (warp == 0) {
         tc_alloc(tmem_s, 256);
@@ -340,16 +390,26 @@ __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
     }
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(bar_ld, 1);
         fence_mbar_init();
         *abort_s = 0;
+        // V1^T and the first tile's pooled rows by the bulk-copy engine
+        const int64_t t0 = blockIdx.x;
+        const uint32_t pbytes = t0 < n_tiles ? tile_bytes(t0) : 0u;
+        mbar_arrive_expect_tx(bar_ld, uint32_t(SUR_G * SUR_G * 2) + pbytes);
+        bulk_copy(V1s, a.pk + PK_V1T, uint32_t(SUR_G * SUR_G * 2), bar_ld, l2_policy_evict_last());
+        if (pbytes) bulk_copy(Pt, a.P + t0 * (TM * SUR_G), pbytes, bar_ld, l2_policy_evict_first());
     }
     {
-        const uint4* src = reinterpret_cast<const uint4*>(a.pk + PK_V1T);
-        uint4* dst = reinterpret_cast<uint4*>(V1s);
-        for (int i = tid; i < SUR_G * SUR_G / 8; i += NT) dst[i] = src[i];
-        for (int i = tid; i < SUR_G * 4; i += NT) V2f[i] = __bfloat162float(a.pb[OFF_V2 + i]);
-        for (int i = tid; i < SUR_G; i += NT) c1s[i] = a.p[OFF_C1 + i];
+        float v2[SUR_G * 4 / NT];
+#pragma unroll
+        for (int k = 0; k < SUR_G * 4 / NT; ++k) v2[k] = __bfloat162float(a.pb[OFF_V2 + tid + k * NT]);
+        const float c1 = a.p[OFF_C1 + tid];
+#pragma unroll
+        for (int k = 0; k < SUR_G * 4 / NT; ++k) V2f[tid + k * NT] = v2[k];
+        c1s[tid] = c1;
     }
+    __syncthreads();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -359,31 +419,27 @@ __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
     const int q = warp & 3, hcol = (warp >> 2) * (SUR_G / 2);
     const int row = 32 * q + lane;
     const float c2[4] = {a.p[OFF_C2 + 0], a.p[OFF_C2 + 1], a.p[OFF_C2 + 2], a.p[OFF_C2 + 3]};
-    uint32_t phase = 0;
-    const int64_t n_tiles = (n_evt + TM - 1) / TM;
+    uint32_t phase = 0, ld_phase = 0;
 
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int64_t e0 = t * TM;
-        const int ne = int(TM < n_evt - e0 ? TM : n_evt - e0);
-        // pooled rows -> canonical K-major tile; eight consecutive threads fill
-        // one 128-byte core-matrix row block
-        for (int idx = tid; idx < TM * (SUR_G / 8); idx += NT) {
-            const int r = 8 * (idx >> 8) + (idx & 7), c = (idx >> 3) & 31;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (r < ne) v = *reinterpret_cast<const uint4*>(a.P + (e0 + r) * SUR_G + 8 * c);
-            *reinterpret_cast<uint4*>(Pt + canon_off(r, 8 * c, SUR_G)) = v;
+        const int64_t e0 = t * te;
+        const int ne = int(te < n_evt - e0 ? te : n_evt - e0);
+        if (t != blockIdx.x && tid == 0) {            // later tiles: pooled rows only
+            const uint32_t pbytes = tile_bytes(t);
+            mbar_arrive_expect_tx(bar_ld, pbytes);
+            bulk_copy(Pt, a.P + t * (TM * SUR_G), pbytes, bar_ld, l2_policy_evict_first());
         }
-        fence_proxy_async_smem();
-        __syncthreads();
+        bool alive = tc_wait(bar_ld, ld_phase, abort_s, a.o.status);
+        ld_phase ^= 1u;
+        if (!alive) break;
         if (tid == 0) {
-            tc_fence_after();
 #pragma unroll 1
             for (int ks = 0; ks < SUR_G / 16; ++ks)
                 tc_mma(tmem, tc_desc(p_addr + 256u * ks, 128u, 16u * SUR_G), tc_desc(v_addr + 256u * ks, 128u, 16u * SUR_G),
                        idesc, ks > 0);
             tc_commit(bar);
         }
-        const bool alive = tc_wait(bar, phase, abort_s, a.o.status);
+        alive = tc_wait(bar, phase, abort_s, a.o.status);
         phase ^= 1u;
         if (!alive) break;
         // this thread's event row, half of the columns
@@ -414,7 +470,7 @@ __global__ void __launch_bounds__(NT, 1) k_event(const InferArgs a) {
             sur_emit_event(a.o, e, yo, a.f.base[e], a.f.n_used[e]);
         }
     }
-    tc_teardown(bar, phase, abort_s, tmem, 256);
+    tc_teardown(bar, phase ^ 1u, bar_ld, ld_phase ^ 1u, abort_s, tmem, 256);
 }
 
 // BF16 twin -> transposed canonical K-major layout of the tensor-core layers.
@@ -450,7 +506,8 @@ cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_event, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SM_TOTAL))) != cudaSuccess)
         return e;
-    const int64_t tiles = (a.f.n_evt + TM - 1) / TM;
+    if (a.ev_tile_events < 1 || a.ev_tile_events > TM) return cudaErrorInvalidValue;
+    const int64_t tiles = (a.f.n_evt + a.ev_tile_events - 1) / a.ev_tile_events;
     k_event<<<int(std::min<int64_t>(tiles, n_sm)), NT, SM_TOTAL, s>>>(a);
     return cudaGetLastError();
 }

@@ -127,8 +127,9 @@ struct InferArgs {
     const __nv_bfloat16* pb;   // BF16 parameter twin (internal layout)
     const float* p;            // FP32 master (biases)
     const __nv_bfloat16* pk;   // tensor-core weight layout (PK_*)
-    __nv_bfloat16* P;          // [n_evt x 256] pooled vectors (workspace)
+    __nv_bfloat16* P;          // pooled vectors, per event tile a canonical 128 x 256 operand block (workspace)
     int tel_tile_events;       // events per k_tel tile, 1..32
+    int ev_tile_events;        // events per k_event tile, 1..128
     OutArgs o;
 };
 
@@ -153,7 +154,8 @@ cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_
                           float* out, cudaStream_t s);
 cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
-// k_tel then k_event (one CTA per SM, n_sm of them at most)
+// k_tel then k_event (one CTA per SM, n_sm of them at most). a.P holds
+// ceil(n_evt / ev_tile_events) * 128 * 256 BF16 values.
 cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s);
 // BF16 twin -> tensor-core weight layout
 cudaError_t launch_pack_tc(const __nv_bfloat16* pb, __nv_bfloat16* pk, cudaStream_t s);

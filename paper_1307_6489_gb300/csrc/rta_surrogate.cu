@@ -59,6 +59,9 @@ struct rta_model {
     unsigned int* n_fallback = nullptr;
     int32_t* fallback_idx = nullptr;
     rta_stereo_t* geo = nullptr;
+    // pooled vectors of the inference kernels, one canonical 128 x 256 block per event tile
+    __nv_bfloat16* Pc = nullptr;
+    int64_t cap_pc = 0;
 };
 
 namespace {
@@ -322,6 +325,7 @@ int rta_surrogate_destroy(rta_model* md) {
     cudaFree(md->p);
     cudaFree(md->pb);
     cudaFree(md->pk);
+    cudaFree(md->Pc);
     cudaFree(md->m);
     cudaFree(md->v);
     cudaFree(md->g);
@@ -469,7 +473,21 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     ia.pb = md->pb;
     ia.p = md->p;
     ia.pk = md->pk;
-    ia.P = md->P;
+    // k_event: one tile per SM, 32..128 events each
+    {
+        const int64_t per_sm = (n_evt + md->n_sm - 1) / md->n_sm;
+        ia.ev_tile_events = int(std::min<int64_t>(128, std::max<int64_t>(32, per_sm)));
+        const int64_t need = (n_evt + ia.ev_tile_events - 1) / ia.ev_tile_events * 128 * SUR_G;
+        if (need > md->cap_pc) {
+            cudaFree(md->Pc);
+            md->Pc = nullptr;
+            md->cap_pc = 0;
+            if (cudaMalloc(&md->Pc, sizeof(__nv_bfloat16) * need) != cudaSuccess)
+                return sfail(RTA_E_NOMEM, "inference workspace allocation failed");
+            md->cap_pc = need;
+        }
+        ia.P = md->Pc;
+    }
     // k_tel runs two CTAs per SM; tiles of up to 32 events, sized so that the
     // CTAs get equal numbers of tiles
     {
