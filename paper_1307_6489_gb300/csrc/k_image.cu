@@ -86,14 +86,9 @@ __device__ __forceinline__ int tree_max(int (&v)[N]) {
 // prefer the smaller start. All window sums are independent of each other (built
 // from pair sums), so the search has no serial dependency chain.
 template <int S, int W>
-__device__ __forceinline__ int best_key_T(const uint16_t* row, int one, int k128) {
+__device__ __forceinline__ int best_key_x(const int (&x)[S], int one, int k128) {
     static_assert(W == 5 || W == 6, "specialised widths");
     constexpr int NK = S - W + 1;
-    uint32_t w[(S + 1) / 2];
-    load_row<S>(row, w);
-    int x[S];
-#pragma unroll
-    for (int k = 0; k < S; ++k) x[k] = sample<S>(w, k);
     int p2[S - 1];
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) p2[k] = x[k] * one + x[k + 1];          // IMAD: FMA pipe
@@ -104,6 +99,48 @@ __device__ __forceinline__ int best_key_T(const uint16_t* row, int one, int k128
         key[k] = sum * k128 + (127 - k);                                     // IMAD: FMA pipe
     }
     return tree_max(key);
+}
+
+template <int S, int W>
+__device__ __forceinline__ int best_key_T(const uint16_t* row, int one, int k128) {
+    uint32_t w[(S + 1) / 2];
+    load_row<S>(row, w);
+    int x[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) x[k] = sample<S>(w, k);
+    return best_key_x<S, W>(x, one, k128);
+}
+
+// Two adjacent pixels of an odd sample count S: their 2S samples are S whole
+// 32-bit words from a 4-byte-aligned address (the pair starts at an even pixel),
+// so every sample sits at a compile-time word and half -- no funnel shifts.
+template <int S, int W>
+__device__ __forceinline__ void best_key_pair(const uint16_t* row0, int one, int k128, int& key0, int& key1) {
+    static_assert(S % 2 == 1, "pairs are for odd sample counts");
+    const uint32_t* v = reinterpret_cast<const uint32_t*>(row0);
+    uint32_t w[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) w[j] = v[j];
+    int x[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) x[k] = (k & 1) ? int(w[k >> 1] >> 16) : int(w[k >> 1] & 0xFFFFu);
+    key0 = best_key_x<S, W>(x, one, k128);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const int m = S + k;
+        x[k] = (m & 1) ? int(w[m >> 1] >> 16) : int(w[m >> 1] & 0xFFFFu);
+    }
+    key1 = best_key_x<S, W>(x, one, k128);
+}
+
+// Bits 0..15 of v spread to the even bit positions.
+__device__ __forceinline__ uint32_t spread_even(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
 }
 
 __device__ __forceinline__ int best_key_generic(const uint16_t* row, int S, int W) {
@@ -117,16 +154,12 @@ __device__ __forceinline__ int best_key_generic(const uint16_t* row, int S, int 
     return key;
 }
 
-// Window start and integer sum of one pixel whose S samples start at `row` (shared memory).
+// Window start and integer sum of one pixel whose S samples start at `row`
+// (shared memory), for the cameras without a specialised search.
 __device__ __forceinline__ void window_sum(const uint16_t* row, int S, const ProcParams& pp, int& sum, int& st) {
     const int W = pp.W;
     if (pp.sliding) {
-        int key;
-        if (S == 40 && W == 6) key = best_key_T<40, 6>(row, pp.one, pp.k128);
-        else if (S == 30 && W == 6) key = best_key_T<30, 6>(row, pp.one, pp.k128);
-        else if (S == 25 && W == 6) key = best_key_T<25, 6>(row, pp.one, pp.k128);
-        else if (S == 16 && W == 5) key = best_key_T<16, 5>(row, pp.one, pp.k128);
-        else key = best_key_generic(row, S, W);
+        const int key = best_key_generic(row, S, W);
         sum = key >> 7;
         st = 127 - (key & 127);
     } else {
@@ -382,8 +415,92 @@ __host__ __device__ __forceinline__ int chunk_pixels(int chunk, int stage_wave_b
     return cp < chunk ? cp : chunk;
 }
 
+// This thread's pixels of one chunk: window search, the calibration multiply,
+// and either the integrate-only outputs or the slot values (q, and t for pixels
+// that can survive cleaning) and the hi/lo bitmap words. S and W are
+// compile-time for the specialised sliding-window cameras (the camera is the
+// same for the whole chunk, so the dispatch happens once per chunk); S == 0 is
+// the generic path with run-time S and W.
+template <int S, int W, int IT, int PPT>
+__device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcParams& pp, const StageHdr& h,
+                                                const unsigned char* buf, const int32_t* cp16, const float* cscale,
+                                                const SlotView& v, int ct, int lane) {
+    const int Sr = S ? S : h.S;
+    const int Wr = W ? W : pp.W;
+    // charge, outputs and thresholds of chunk pixel c with window sum `sum` starting at `wst`
+    auto emit = [&](int c, int sum, int wst, const uint16_t* row, bool& hi, bool& lo) {
+        const int p16 = cp16[c];
+        int num;
+        const float q = charge(sum, Wr, p16, cscale[c], num);
+        const int p = h.base + c;
+        if (a.integrate_only) {
+            a.q_out[h.pix_off + p] = q;
+            if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, Wr, p16, num);
+        } else {
+            v.q[p] = q;
+            hi = q >= pp.t_hi;
+            lo = q >= pp.t_lo;
+            // only pixels that can survive cleaning need their time
+            if (lo) v.t[p] = peak_time(row, wst, Wr, p16, num);
+        }
+    };
+    if constexpr (S != 0 && S % 2 == 1 && PPT == 2) {
+        // adjacent pixel pairs 2ct, 2ct + 1 (P is a multiple of 8 for odd S, so
+        // chunks hold whole pairs); the warp covers 64 consecutive pixels
+        const int c0 = 2 * ct;
+        bool hi0 = false, lo0 = false, hi1 = false, lo1 = false;
+        if (c0 < h.npix) {
+            const uint16_t* row0 = reinterpret_cast<const uint16_t*>(buf) + size_t(c0) * S;
+            int key0, key1;
+            best_key_pair<S, W>(row0, pp.one, pp.k128, key0, key1);
+            emit(c0, key0 >> 7, 127 - (key0 & 127), row0, hi0, lo0);
+            emit(c0 + 1, key1 >> 7, 127 - (key1 & 127), row0 + S, hi1, lo1);
+        }
+        if (!a.integrate_only) {
+            const uint32_t h0 = __ballot_sync(0xffffffffu, hi0), h1 = __ballot_sync(0xffffffffu, hi1);
+            const uint32_t l0 = __ballot_sync(0xffffffffu, lo0), l1 = __ballot_sync(0xffffffffu, lo1);
+            const int word = (h.base + 64 * (ct >> 5)) >> 5;
+            const int nw = (h.base + h.npix + 31) >> 5;      // only the chunk's own words
+            if (lane == 0 && word < nw) {
+                v.hi[word] = spread_even(h0) | (spread_even(h1) << 1);
+                v.lo[word] = spread_even(l0) | (spread_even(l1) << 1);
+            }
+            if (lane == 0 && word + 1 < nw) {
+                v.hi[word + 1] = spread_even(h0 >> 16) | (spread_even(h1 >> 16) << 1);
+                v.lo[word + 1] = spread_even(l0 >> 16) | (spread_even(l1 >> 16) << 1);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int c = ct + k * IT;    // pixel within the chunk
+            bool hi = false, lo = false;
+            if (c < h.npix) {
+                const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * Sr;
+                int sum, wst;
+                if constexpr (S != 0) {
+                    const int key = best_key_T<S, W>(row, pp.one, pp.k128);
+                    sum = key >> 7;
+                    wst = 127 - (key & 127);
+                } else {
+                    window_sum(row, h.S, pp, sum, wst);
+                }
+                emit(c, sum, wst, row, hi, lo);
+            }
+            if (!a.integrate_only) {
+                const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
+                const int word = (h.base + c) >> 5;
+                if (lane == 0 && word < ((h.base + h.npix + 31) >> 5)) {      // only the chunk's own words
+                    v.hi[word] = bh;
+                    v.lo[word] = bl;
+                }
+            }
+        }
+    }
+}
+
 template <int IW, int PPT>
-__global__ void __launch_bounds__(IW * 32 + 64, 1) k_image_chain(const ChainArgs a) {
+__global__ void __launch_bounds__(IW * 32 + 64, 2) k_image_chain(const ChainArgs a) {
     constexpr int IT = IW * 32;          // integrator threads
     constexpr int CHUNK = IT * PPT;      // largest chunk in pixels
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -583,37 +700,16 @@ __global__ void __launch_bounds__(IW * 32 + 64, 1) k_image_chain(const ChainArgs
         const unsigned char* buf = stages + size_t(stage) * stage_bytes;
         const int32_t* cp16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes);
         const float* cscale = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes);
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const int c = ct + k * IT;    // pixel within the chunk
-            bool hi = false, lo = false;
-            if (c < h.npix) {
-                const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * h.S;
-                const int p16 = cp16[c];
-                int sum, wst, num;
-                window_sum(row, h.S, pp, sum, wst);
-                const float q = charge(sum, pp.W, p16, cscale[c], num);
-                const int p = h.base + c;
-                if (a.integrate_only) {
-                    a.q_out[h.pix_off + p] = q;
-                    if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, pp.W, p16, num);
-                } else {
-                    v.q[p] = q;
-                    hi = q >= pp.t_hi;
-                    lo = q >= pp.t_lo;
-                    // only pixels that can survive cleaning need their time
-                    if (lo) v.t[p] = peak_time(row, wst, pp.W, p16, num);
-                }
-            }
-            if (!a.integrate_only) {
-                const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
-                const int word = (h.base + c) >> 5;
-                if (lane == 0 && word < words_of(h.P)) {
-                    v.hi[word] = bh;
-                    v.lo[word] = bl;
-                }
-            }
-        }
+        if (pp.sliding && pp.W == 6 && h.S == 40)
+            integrate_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+        else if (pp.sliding && pp.W == 6 && h.S == 30)
+            integrate_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+        else if (pp.sliding && pp.W == 6 && h.S == 25)
+            integrate_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+        else if (pp.sliding && pp.W == 5 && h.S == 16)
+            integrate_chunk<16, 5, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+        else
+            integrate_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == NST) { stage = 0; phase ^= 1u; }

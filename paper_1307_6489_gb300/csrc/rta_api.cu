@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -55,6 +56,14 @@ struct Slot {  // one half of the host-path double buffer
     size_t img_cap = 0, evt_cap = 0;
     int64_t* h_off = nullptr;   // pinned
     int32_t* h_evt = nullptr;   // pinned
+    // results of the slot's last chunk, staged in pinned memory so that the
+    // device-to-host copies never block the thread that enqueues the next upload
+    rta_hillas_t* h_hres = nullptr;
+    rta_stereo_t* h_sres = nullptr;
+    cudaEvent_t res_done = nullptr;
+    cudaEvent_t up_done = nullptr;     // this slot's last upload has landed
+    bool res_pending = false;
+    int64_t res_i0 = 0, res_ni = 0, res_e0 = 0, res_ne = 0;
 };
 
 }  // namespace
@@ -172,6 +181,21 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
         return fail(RTA_E_INVALID, "tile variant %d has no room for %d samples", k.variant, c->max_S);
     *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P);
     int occ = rta::chain_occupancy(k.variant, *smem);
+    if (k.ctas_per_sm > 0 && occ < k.ctas_per_sm) {
+        // smaller stages (still at least 128 pixels of the longest camera per
+        // chunk) so that the requested number of CTAs fits on an SM
+        for (int s2 = (*swb - 1024) & ~127; s2 >= 4096; s2 -= 1024) {
+            if (rta::chain_chunk_pixels(k.variant, s2, c->max_S) < 128) break;
+            const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P);
+            const int occ2 = rta::chain_occupancy(k.variant, sm2);
+            if (occ2 >= k.ctas_per_sm) {
+                *swb = s2;
+                *smem = sm2;
+                occ = occ2;
+                break;
+            }
+        }
+    }
     if (occ < 1) return fail(RTA_E_INVALID, "image kernel does not fit: %zu bytes of shared memory", *smem);
     if (k.ctas_per_sm > 0) {
         if (occ < k.ctas_per_sm) return fail(RTA_E_INVALID, "%d CTAs/SM do not fit (%d do)", k.ctas_per_sm, occ);
@@ -338,6 +362,9 @@ int rta_destroy(rta_ctx* c) {
         if (s.meta_done) cudaEventDestroy(s.meta_done);
         cudaFree(s.d_wave); cudaFree(s.d_off); cudaFree(s.d_tel); cudaFree(s.d_evt); cudaFree(s.d_h); cudaFree(s.d_s);
         cudaFreeHost(s.h_off); cudaFreeHost(s.h_evt);
+        cudaFreeHost(s.h_hres); cudaFreeHost(s.h_sres);
+        if (s.res_done) cudaEventDestroy(s.res_done);
+        if (s.up_done) cudaEventDestroy(s.up_done);
     }
     cudaFree(c->d_cams); cudaFree(c->d_tel_cam); cudaFree(c->d_tel_xy); cudaFree(c->d_tel_row);
     cudaFree(c->d_p16); cudaFree(c->d_scale); cudaFree(c->d_status); cudaFree(c->d_counters);
@@ -673,7 +700,10 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
         if (!s.stream) {
             CUDA_TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
             CUDA_TRY(cudaEventCreateWithFlags(&s.meta_done, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&s.res_done, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&s.up_done, cudaEventDisableTiming));
         }
+        s.res_pending = false;
         if (s.wave_cap < size_t(cap) * 2) {
             if (c->staged_bytes + size_t(cap) * 2 > c->budget) return fail(RTA_E_NOMEM, "staging exceeds the HBM budget");
             cudaFree(s.d_wave);
@@ -685,6 +715,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
         if (s.img_cap < size_t(max_img) || s.evt_cap < size_t(max_evt) + 1) {
             cudaFree(s.d_off); cudaFree(s.d_tel); cudaFree(s.d_evt); cudaFree(s.d_h); cudaFree(s.d_s);
             cudaFreeHost(s.h_off); cudaFreeHost(s.h_evt);
+            cudaFreeHost(s.h_hres); cudaFreeHost(s.h_sres);
             s.img_cap = size_t(max_img) + 1024;
             s.evt_cap = size_t(max_evt) + 1024;
             CUDA_TRY(cudaMalloc(&s.d_off, sizeof(int64_t) * s.img_cap));
@@ -694,6 +725,8 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
             CUDA_TRY(cudaMalloc(&s.d_s, sizeof(rta_stereo_t) * s.evt_cap));
             CUDA_TRY(cudaMallocHost(&s.h_off, sizeof(int64_t) * s.img_cap));
             CUDA_TRY(cudaMallocHost(&s.h_evt, sizeof(int32_t) * s.evt_cap));
+            CUDA_TRY(cudaMallocHost(&s.h_hres, sizeof(rta_hillas_t) * s.img_cap));
+            CUDA_TRY(cudaMallocHost(&s.h_sres, sizeof(rta_stereo_t) * s.evt_cap));
         }
     }
     rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
@@ -704,9 +737,23 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
         const int64_t ni = i1 - i0, ne = e1 - e0;
         // the pinned metadata of this slot may still feed the copy issued two chunks ago
         CUDA_TRY(cudaEventSynchronize(s.meta_done));
+        // hand the slot's previous results to the caller before they are overwritten
+        auto deliver = [&](Slot& d) -> int {
+            if (!d.res_pending) return RTA_OK;
+            CUDA_TRY(cudaEventSynchronize(d.res_done));
+            memcpy(h_hillas + d.res_i0, d.h_hres, sizeof(rta_hillas_t) * d.res_ni);
+            memcpy(h_stereo + d.res_e0, d.h_sres, sizeof(rta_stereo_t) * d.res_ne);
+            d.res_pending = false;
+            return RTA_OK;
+        };
+        if ((rc = deliver(s))) return rc;
         const int64_t base = ni ? h_wave_off[i0] : 0;
         for (int64_t i = 0; i < ni; ++i) s.h_off[i] = h_wave_off[i0 + i] - base;
         for (int64_t e = 0; e <= ne; ++e) s.h_evt[e] = int32_t(h_evt_off[e0 + e] - i0);
+        // uploads go one at a time, in chunk order: the host link is the bottleneck
+        // and two concurrent uploads share it less well than one after the other;
+        // the kernels of a chunk still overlap the next chunk's upload
+        if (k > 0) CUDA_TRY(cudaStreamWaitEvent(s.stream, c->slot[(k - 1) & 1].up_done, 0));
         if (ni) {
             const size_t bytes = size_t(img_end[i1 - 1] - base) * 2;
             CUDA_TRY(cudaMemcpyAsync(s.d_wave, h_wave + base, bytes, cudaMemcpyHostToDevice, s.stream));
@@ -715,15 +762,29 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
         }
         CUDA_TRY(cudaMemcpyAsync(s.d_evt, s.h_evt, sizeof(int32_t) * (ne + 1), cudaMemcpyHostToDevice, s.stream));
         CUDA_TRY(cudaEventRecord(s.meta_done, s.stream));
+        CUDA_TRY(cudaEventRecord(s.up_done, s.stream));
         if (ni) {
             rc = run_chain(c, s.d_wave, int64_t(s.wave_cap / 2), s.d_off, s.d_tel, nullptr, ni, pp, nullptr, nullptr,
                            0, s.d_h, 0, s.stream, c->d_counters + N_COUNTERS - 1 - (k & 1));
             if (rc) return rc;
-            CUDA_TRY(cudaMemcpyAsync(h_hillas + i0, s.d_h, sizeof(rta_hillas_t) * ni, cudaMemcpyDeviceToHost, s.stream));
+            CUDA_TRY(cudaMemcpyAsync(s.h_hres, s.d_h, sizeof(rta_hillas_t) * ni, cudaMemcpyDeviceToHost, s.stream));
         }
         rc = run_stereo(c, s.d_h, s.d_tel, ni, s.d_evt, ne, s.d_s, s.stream);
         if (rc) return rc;
-        CUDA_TRY(cudaMemcpyAsync(h_stereo + e0, s.d_s, sizeof(rta_stereo_t) * ne, cudaMemcpyDeviceToHost, s.stream));
+        CUDA_TRY(cudaMemcpyAsync(s.h_sres, s.d_s, sizeof(rta_stereo_t) * ne, cudaMemcpyDeviceToHost, s.stream));
+        CUDA_TRY(cudaEventRecord(s.res_done, s.stream));
+        s.res_pending = true;
+        s.res_i0 = i0;
+        s.res_ni = ni;
+        s.res_e0 = e0;
+        s.res_ne = ne;
+    }
+    for (auto& d : c->slot) {
+        if (!d.res_pending) continue;
+        CUDA_TRY(cudaEventSynchronize(d.res_done));
+        memcpy(h_hillas + d.res_i0, d.h_hres, sizeof(rta_hillas_t) * d.res_ni);
+        memcpy(h_stereo + d.res_e0, d.h_sres, sizeof(rta_stereo_t) * d.res_ne);
+        d.res_pending = false;
     }
     CUDA_TRY(cudaStreamSynchronize(c->slot[0].stream));
     CUDA_TRY(cudaStreamSynchronize(c->slot[1].stream));

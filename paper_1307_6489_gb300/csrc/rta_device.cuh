@@ -87,12 +87,28 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// As mbar_try_wait, but a thread whose phase is not complete may sleep in the
+// instruction until the phase completes, at most suspend_ns: waiting warps stop
+// taking issue slots from working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t suspend_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(suspend_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase of `parity` to complete. Gives up after timeout_ns or as
-// soon as *abort becomes non-zero; returns false then.
+// soon as *abort becomes non-zero (both checked between sleeps of at most
+// 100 us); returns false then.
 __device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity, 100000u)) {
         if (*abort) return false;
         if (global_ns() - t0 > timeout_ns) return false;
     }
