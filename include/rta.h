@@ -185,8 +185,10 @@ int rta_set_chain_config(rta_ctx* ctx, int variant, int n_stages, int ctas_per_s
 int rta_get_chain_config(rta_ctx* ctx, int* variant, int* n_stages, int* ctas_per_sm, int* grid,
                          size_t* smem_bytes);
 
-/* Tile shape of a variant (0 .. RTA_CHAIN_VARIANTS-1). */
-#define RTA_CHAIN_VARIANTS 4
+/* Tile shape of a variant (0 .. RTA_CHAIN_VARIANTS-1). Variant 4 has the shape of
+ * variant 0, compiled for at most 68 registers per thread so that three CTAs fit on
+ * an SM (with stages shrunk to fit their shared memory). */
+#define RTA_CHAIN_VARIANTS 5
 int rta_chain_variant_info(int variant, int* integrator_warps, int* pixels_per_thread);
 
 /* One measured configuration of rta_autotune. */

@@ -193,7 +193,7 @@ def rta_check(ctx: int, stream: int = 0) -> int:
     return bits.value
 
 
-RTA_CHAIN_VARIANTS = 4
+RTA_CHAIN_VARIANTS = 5
 
 
 class TuneEntry(ctypes.Structure):

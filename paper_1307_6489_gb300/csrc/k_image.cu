@@ -111,6 +111,60 @@ __device__ __forceinline__ int best_key_T(const uint16_t* row, int one, int k128
     return best_key_x<S, W>(x, one, k128);
 }
 
+// Maximum W = 6 window sum of one pixel when every loaded 16-bit sample is below
+// 4096 (true for 12-bit digitisers; checked here): two samples per 32-bit word,
+// pair sums and window sums formed two lanes at a time with plain 32-bit adds
+// (each lane stays below 2^15, so no carry crosses a lane), then the maximum
+// over both lanes. Rows that start on an odd 16-bit position are read from the
+// word boundary below; the lanes then hold windows k - 1 and k instead of k and
+// k + 1, and the windows that would reach outside the row are masked. Returns
+// false (nothing computed) when a sample is 4096 or more; the window start is
+// not computed here.
+template <int S>
+__device__ __forceinline__ bool max_window6_packed(const uint16_t* row, int& M) {
+    constexpr int NK = S - 6 + 1;                 // window starts 0 .. NK - 1
+    constexpr int JQ = NK / 2 + 1;                // packed window words
+    constexpr int NW = JQ + 3;                    // loaded words
+    const uintptr_t a = reinterpret_cast<uintptr_t>(row);
+    const bool odd = (S % 2 == 1) && (a & 2u);
+    const uint32_t* v = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+    uint32_t u[NW];
+    if constexpr ((2 * S) % 16 == 0) {
+#pragma unroll
+        for (int k = 0; k < NW / 4; ++k) {
+            const uint4 q = reinterpret_cast<const uint4*>(v)[k];
+            u[4 * k] = q.x; u[4 * k + 1] = q.y; u[4 * k + 2] = q.z; u[4 * k + 3] = q.w;
+        }
+#pragma unroll
+        for (int k = 4 * (NW / 4); k < NW; ++k) u[k] = v[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < NW; ++k) u[k] = v[k];
+    }
+    uint32_t any = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) any |= u[k];
+    if (any & 0xF000F000u) return false;
+    // pair sums: lanes (hi(u_j) + lo(u_j+1) : lo(u_j) + hi(u_j))
+    uint32_t P[NW - 1];
+#pragma unroll
+    for (int j = 0; j < NW - 1; ++j) P[j] = u[j] + __byte_perm(u[j], u[j + 1], 0x5432);
+    // every word (its high lane orders it: all values < 2^31) and every word
+    // shifted up by one lane into one three-input max tree
+    int m[2 * JQ];
+#pragma unroll
+    for (int j = 0; j < JQ; ++j) {
+        uint32_t q = P[j] + P[j + 1] + P[j + 2];  // lanes: windows (2j + 1 : 2j), or (2j : 2j - 1) for odd rows
+        const bool lo_ok = odd ? (j >= 1 && 2 * j <= NK) : (2 * j <= NK - 1);
+        const bool hi_ok = odd ? (2 * j <= NK - 1) : (2 * j + 1 <= NK - 1);
+        q &= (hi_ok ? 0xFFFF0000u : 0u) | (lo_ok ? 0xFFFFu : 0u);
+        m[2 * j] = int(q);
+        m[2 * j + 1] = int(q << 16);
+    }
+    M = tree_max(m) >> 16;
+    return true;
+}
+
 // Two adjacent pixels of an odd sample count S: their 2S samples are S whole
 // 32-bit words from a 4-byte-aligned address (the pair starts at an even pixel),
 // so every sample sits at a compile-time word and half -- no funnel shifts.
@@ -478,7 +532,23 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
             if (c < h.npix) {
                 const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * Sr;
                 int sum, wst;
-                if constexpr (S != 0) {
+                if constexpr (S != 0 && W == 6) {
+                    // The charge needs only the maximum; the window start (first
+                    // maximum) only for pixels whose peak time is needed. The packed
+                    // maximum decides; the exact search (one call site) runs for the
+                    // pixels that reach t_lo or whose samples are out of its range.
+                    int m = 0;
+                    bool need = a.integrate_only || !max_window6_packed<S>(row, m);
+                    if (!need) need = __fmul_rn(__int2float_rn(16 * m - W * cp16[c]), cscale[c]) >= pp.t_lo;
+                    if (need) {
+                        const int key = best_key_T<S, W>(row, pp.one, pp.k128);
+                        sum = key >> 7;
+                        wst = 127 - (key & 127);
+                    } else {
+                        sum = m;
+                        wst = 0;       // unused: the pixel is below t_lo
+                    }
+                } else if constexpr (S != 0) {
                     const int key = best_key_T<S, W>(row, pp.one, pp.k128);
                     sum = key >> 7;
                     wst = 127 - (key & 127);
@@ -499,8 +569,8 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
     }
 }
 
-template <int IW, int PPT>
-__global__ void __launch_bounds__(IW * 32 + 64, 2) k_image_chain(const ChainArgs a) {
+template <int IW, int PPT, int MB>
+__global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
     constexpr int IT = IW * 32;          // integrator threads
     constexpr int CHUNK = IT * PPT;      // largest chunk in pixels
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -817,12 +887,13 @@ __global__ void __launch_bounds__(256) k_hillas(const HillasArgs a) {
 // ------------------------------------------------------------------ host-side launchers
 // Tile-shape variants of the fused kernel: (integrator warps, pixels per thread).
 struct ChainVariant {
-    int iw, ppt;
+    int iw, ppt, min_blocks;   // integrator warps, pixels per thread, CTAs per SM the registers are sized for
 };
-static const ChainVariant kVariants[RTA_CHAIN_VARIANTS] = {{8, 1}, {4, 2}, {8, 2}, {4, 1}};
+static const ChainVariant kVariants[RTA_CHAIN_VARIANTS] = {{8, 1, 2}, {4, 2, 2}, {8, 2, 2}, {4, 1, 2}, {8, 1, 3}};
 
 int chain_variant_warps(int v) { return kVariants[v].iw; }
 int chain_variant_ppt(int v) { return kVariants[v].ppt; }
+int chain_variant_min_blocks(int v) { return kVariants[v].min_blocks; }
 int chain_threads(int v) { return kVariants[v].iw * 32 + 64; }
 
 int chain_stage_wave_bytes(int v, int max_S) {
@@ -843,10 +914,10 @@ int chain_chunk_pixels(int v, int stage_wave_bytes, int S) {
     return chunk_pixels(kVariants[v].iw * 32 * kVariants[v].ppt, stage_wave_bytes, S);
 }
 
-template <int IW, int PPT>
+template <int IW, int PPT, int MB>
 static cudaError_t launch_t(const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occupancy_only,
                             int* occ) {
-    auto kern = k_image_chain<IW, PPT>;
+    auto kern = k_image_chain<IW, PPT, MB>;
     // the dynamic shared-memory opt-in is per device; remember the largest size set
     static size_t attr_bytes[64] = {};
     int dev = 0;
@@ -867,10 +938,11 @@ static cudaError_t launch_t(const ChainArgs& a, int grid, size_t smem, cudaStrea
 static cudaError_t dispatch(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
                             int* occ) {
     switch (v) {
-    case 0: return launch_t<8, 1>(a, grid, smem, s, occ_only, occ);
-    case 1: return launch_t<4, 2>(a, grid, smem, s, occ_only, occ);
-    case 2: return launch_t<8, 2>(a, grid, smem, s, occ_only, occ);
-    case 3: return launch_t<4, 1>(a, grid, smem, s, occ_only, occ);
+    case 0: return launch_t<8, 1, 2>(a, grid, smem, s, occ_only, occ);
+    case 1: return launch_t<4, 2, 2>(a, grid, smem, s, occ_only, occ);
+    case 2: return launch_t<8, 2, 2>(a, grid, smem, s, occ_only, occ);
+    case 3: return launch_t<4, 1, 2>(a, grid, smem, s, occ_only, occ);
+    case 4: return launch_t<8, 1, 3>(a, grid, smem, s, occ_only, occ);   // registers for three CTAs per SM
     default: return cudaErrorInvalidValue;
     }
 }

@@ -90,9 +90,9 @@ struct rta_ctx {
     unsigned int* d_counters = nullptr;
     std::atomic<unsigned> next_counter{0};
     // launch configuration of the fused image kernel
-    int variant = 0;      // tile shape, see chain_variant_*
-    int nstage = 3;
-    int ctas_per_sm = 0;  // 0 = as many as fit
+    int variant = 4;      // tile shape, see chain_variant_* (the fastest on GB300 for the array cameras)
+    int nstage = 2;
+    int ctas_per_sm = 0;  // 0 = the variant's target, shrinking the stages to fit, else as many as fit
     int max_P = 0, max_S = 0;
     Slot slot[2];
     std::mutex host_mu;
@@ -181,14 +181,15 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
         return fail(RTA_E_INVALID, "tile variant %d has no room for %d samples", k.variant, c->max_S);
     *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P);
     int occ = rta::chain_occupancy(k.variant, *smem);
-    if (k.ctas_per_sm > 0 && occ < k.ctas_per_sm) {
+    const int want = k.ctas_per_sm > 0 ? k.ctas_per_sm : rta::chain_variant_min_blocks(k.variant);
+    if (occ < want) {
         // smaller stages (still at least 128 pixels of the longest camera per
         // chunk) so that the requested number of CTAs fits on an SM
         for (int s2 = (*swb - 1024) & ~127; s2 >= 4096; s2 -= 1024) {
             if (rta::chain_chunk_pixels(k.variant, s2, c->max_S) < 128) break;
             const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P);
             const int occ2 = rta::chain_occupancy(k.variant, sm2);
-            if (occ2 >= k.ctas_per_sm) {
+            if (occ2 >= want) {
                 *swb = s2;
                 *smem = sm2;
                 occ = occ2;

@@ -73,6 +73,7 @@ int chain_stage_wave_bytes(int v, int max_S);
 size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P);
 int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
 int chain_occupancy(int v, size_t smem);
+int chain_variant_min_blocks(int v);
 int stereo_events_per_block();
 cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_clean(const CleanArgs& a, int grid, cudaStream_t s);

@@ -85,7 +85,7 @@ def test_image_chain_fused(setup):
     assert (g["n_pix"] > 0).mean() > 0.5
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("n_stages,ctas", [(2, 1), (2, 2), (3, 0), (4, 1), (6, 1), (8, 1)])
 def test_image_chain_every_tile_and_pipeline_depth_is_identical(setup, variant, n_stages, ctas):
     name, wl, ref, ctx, dev = setup
