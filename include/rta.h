@@ -350,6 +350,8 @@ int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const in
 /* ---------------------------------------------------------------------- */
 #define RTA_SKY_N 256      /* sky-map bins per axis, 0.02 deg each, [-2.56, 2.56) deg */
 #define RTA_SKY_SLABS 30   /* one-second slabs; a map is the sum of the last 30 */
+#define RTA_SKY_MIN_SLABS 60   /* one-minute slabs: windows up to one hour */
+#define RTA_MAX_DISK_RADIUS 32 /* largest on-region radius of the transient search, in bins */
 
 /* One bundle of events in HOST memory (pinned memory gives full copy speed).
  * Layout as the device calls (offsets from h_wave, CSR from 0). Every buffer
@@ -403,6 +405,52 @@ int rta_skymap_read(rta_stream* stream, int64_t now_ns, uint32_t* h_map);
 int rta_stream_add_events(rta_stream* stream, const rta_event_t* d_events, int64_t n_evt, int64_t arrival_ns,
                           void* cuda_stream);
 int rta_stream_destroy(rta_stream* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Transient search on the sky map (Sec. 2.1 requirement (ii): multiple    */
+/* timescales from seconds to hours, in a source region and elsewhere in   */
+/* the field of view)                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* One timescale: an "on" window of on_s seconds ending at the search time and
+ * the "off" (background) window of off_s seconds just before it, in whole
+ * seconds of bundle arrival: with now_s = now_ns / 1e9 (integer division), on
+ * covers the seconds (now_s - on_s, now_s] and off (now_s - on_s - off_s,
+ * now_s - on_s]. Either on_s + off_s <= RTA_SKY_SLABS (read from the one-second
+ * slabs), or both are multiples of 60 and on_s + off_s <= 60 * RTA_SKY_MIN_SLABS
+ * (read from the one-minute slabs; minute of a second: floor(s / 60)). The
+ * stream fills both rings as it bins events. */
+typedef struct rta_window_t {
+    int32_t on_s, off_s;
+} rta_window_t;
+
+/* One alert: a (window, bin) whose significance reached the threshold. n_on and
+ * n_off are the event counts in the disk of radius_bins around the bin (bins
+ * with (dx^2 + dy^2) <= radius^2, clipped at the map edge) in the on and off
+ * windows; alpha = on_s / off_s; significance = Li & Ma (1983) Eq. 17, signed
+ * (negative for a deficit, n_on < alpha * n_off), computed in FP64. 48 bytes. */
+typedef struct rta_alert_t {
+    int32_t window; /* index into the windows array */
+    int32_t ix, iy; /* bin column and row */
+    int32_t pad;
+    int64_t n_on, n_off;
+    double alpha, significance;
+} rta_alert_t;
+
+/* Transient search over every bin of the sky map for each of n_windows windows:
+ * writes the alerts with significance >= s_min, sorted by (window, iy, ix), to
+ * h_alerts (at most max_alerts; *n_alerts gets the number found, which may be
+ * larger). radius_bins in 0..RTA_MAX_DISK_RADIUS (0: single bins). Errors:
+ * RTA_E_INVALID for a window outside the rules above or a bad radius.
+ * Synchronises the map's stream. */
+int rta_transient_search(rta_stream* stream, int64_t now_ns, const rta_window_t* windows, int n_windows,
+                         int radius_bins, double s_min, rta_alert_t* h_alerts, int max_alerts, int* n_alerts);
+
+/* The full significance map of one window: h_sig (RTA_SKY_N x RTA_SKY_N
+ * doubles, row y then column x) and, when not NULL, the disk counts h_on and
+ * h_off (int64). Same definitions as rta_transient_search. */
+int rta_significance_map(rta_stream* stream, int64_t now_ns, rta_window_t window, int radius_bins, double* h_sig,
+                         int64_t* h_on, int64_t* h_off);
 
 /* ---------------------------------------------------------------------- */
 /* Entry point that allocates nothing                                      */

@@ -12,6 +12,8 @@ calibration multiply); this module only marshals numpy arrays.  Row layouts:
   stereo row (6 doubles):  dir_x, dir_y (deg), core_x, core_y (m), n_valid, flags
 
 ``mlp.py`` holds the FP64 deep-sets network, its backward pass and Adam.
+The sky map (``skymap``) and the transient search on it (``li_ma``,
+``disk_sum``, ``transient_maps``, ``transient_search``) are numpy here.
 """
 from __future__ import annotations
 
@@ -175,3 +177,85 @@ def reconstruct(wl, threads: int | None = None, do_stereo: bool = True, per_pixe
     if st != 0:
         raise RuntimeError("or_reconstruct failed")
     return dict(hillas=hil, stereo=ste, q=q, t=t, mask=mk)
+
+
+SKY_MIN_SLABS = 60
+
+
+def li_ma(n_on, n_off, alpha):
+    """Significance of an on/off count pair (Li & Ma 1983, ApJ 272, 317, Eq. 17),
+    signed: negative when n_on < alpha * n_off. Terms with a zero count are 0
+    (the limit of n ln n). FP64."""
+    n_on = np.asarray(n_on, np.float64)
+    n_off = np.asarray(n_off, np.float64)
+    alpha = np.asarray(alpha, np.float64)
+    tot = n_on + n_off
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1 = np.where(n_on > 0, n_on * np.log((1.0 + alpha) / alpha * (n_on / tot)), 0.0)
+        t2 = np.where(n_off > 0, n_off * np.log((1.0 + alpha) * (n_off / tot)), 0.0)
+    s = np.sqrt(np.maximum(2.0 * (t1 + t2), 0.0))
+    s = np.where(tot > 0, s, 0.0)
+    return np.where(n_on >= alpha * n_off, s, -s)
+
+
+def disk_sum(m, radius):
+    """Sum of m over the disk of bins (dx^2 + dy^2 <= radius^2) around every bin,
+    bins outside the map counting 0."""
+    m = np.asarray(m, np.int64)
+    n = m.shape[0]
+    out = np.zeros_like(m)
+    for dy in range(-radius, radius + 1):
+        for dx in range(-radius, radius + 1):
+            if dx * dx + dy * dy > radius * radius:
+                continue
+            ys = slice(max(0, -dy), min(n, n - dy))
+            yd = slice(max(0, dy), min(n, n + dy))
+            xs = slice(max(0, -dx), min(n, n - dx))
+            xd = slice(max(0, dx), min(n, n + dx))
+            out[ys, xs] += m[yd, xd]
+    return out
+
+
+def _window_ok(on_s, off_s):
+    if on_s < 1 or off_s < 1:
+        return False
+    if on_s + off_s <= SKY_WINDOW_S:
+        return True
+    return on_s % 60 == 0 and off_s % 60 == 0 and on_s + off_s <= 60 * SKY_MIN_SLABS
+
+
+def transient_maps(dir_x, dir_y, has_dir, arrival_s, now_s, window, radius):
+    """(significance, disk on counts, disk off counts, alpha) maps [iy, ix] of one
+    window (on_s, off_s): on = arrival seconds in (now - on, now], off = the
+    off_s seconds before that; seconds, or whole minutes (floor(s / 60)) when the
+    window is longer than the one-second ring."""
+    on_s, off_s = int(window[0]), int(window[1])
+    if not _window_ok(on_s, off_s):
+        raise ValueError("window outside the ring rules")
+    ix, iy = sky_bin(dir_x), sky_bin(dir_y)
+    sec = np.asarray(arrival_s, np.int64)
+    ok = np.asarray(has_dir, bool) & (ix >= 0) & (iy >= 0)
+    if on_s + off_s <= SKY_WINDOW_S:
+        t, now, on, off = sec, int(now_s), on_s, off_s
+    else:
+        t, now, on, off = np.floor_divide(sec, 60), int(now_s) // 60, on_s // 60, off_s // 60
+    sel_on = ok & (t > now - on) & (t <= now)
+    sel_off = ok & (t > now - on - off) & (t <= now - on)
+    m_on = np.zeros((SKY_N, SKY_N), np.int64)
+    m_off = np.zeros((SKY_N, SKY_N), np.int64)
+    np.add.at(m_on, (iy[sel_on], ix[sel_on]), 1)
+    np.add.at(m_off, (iy[sel_off], ix[sel_off]), 1)
+    d_on, d_off = disk_sum(m_on, radius), disk_sum(m_off, radius)
+    alpha = on_s / off_s
+    return li_ma(d_on, d_off, alpha), d_on, d_off, alpha
+
+
+def transient_search(dir_x, dir_y, has_dir, arrival_s, now_s, windows, radius, s_min):
+    """Alerts (window, ix, iy, n_on, n_off, alpha, significance) with significance
+    >= s_min, sorted by (window, iy, ix)."""
+    rows = []
+    for w, win in enumerate(windows):
+        sig, d_on, d_off, alpha = transient_maps(dir_x, dir_y, has_dir, arrival_s, now_s, win, radius)
+        for y, x in zip(*np.nonzero(sig >= s_min)):
+            rows.append((w, int(x), int(y), int(d_on[y, x]), int(d_off[y, x]), alpha, float(sig[y, x])))
+    return rows
