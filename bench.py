@@ -317,10 +317,20 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
                         "offered_gbs": (total / ((arr[-1] - arr[0]) / 1e9) / 1e9) if arr[-1] > arr[0] else None,
                         "sustained_gbs": total / span / 1e9, "p50_ms": float(np.percentile(lat, 50)),
                         "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())})
+        # transient search over the sky map the stream has just filled: 1 s .. 30 min windows
+        windows = [(1, 5), (5, 25), (10, 20), (60, 600), (300, 1800), (600, 3000), (1800, 1800)]
+        now = time.monotonic_ns()
+        rta.rta_transient_search(st, now, windows, 5, 5.0)          # warm (work buffers)
+        t0 = time.perf_counter()
+        for _ in range(10):
+            alerts = rta.rta_transient_search(st, now, windows, 5, 5.0)
+        search_ms = (time.perf_counter() - t0) / 10 * 1e3
     finally:
         rta.rta_stream_destroy(st)
     return out, {"pool_bundles": len(pool), "pool_events": [b["n_evt"] for b in pool],
-                 "pool_gb": sum(b["bytes"] for b in pool) / 1e9}
+                 "pool_gb": sum(b["bytes"] for b in pool) / 1e9,
+                 "transient_search": {"windows": len(windows), "radius_bins": 5, "s_min": 5.0, "ms_per_call": search_ms,
+                                      "alerts": int(len(alerts))}}
 
 
 def run_reference(args, ws, rank):

@@ -106,6 +106,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_skymap_read": ([P, i64, P], i32),
         "rta_stream_add_events": ([P, P, i64, i64, P], i32),
         "rta_stream_destroy": ([P], i32),
+        "rta_transient_search": ([P, i64, P, i32, i32, ctypes.c_double, P, i32, P], i32),
+        "rta_significance_map": ([P, i64, Window, i32, P, P, P], i32),
         "rta_selftest_wait_timeout": ([P, i32, P, P], i32),
         "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
                                      P, P, P], i32),
@@ -373,6 +375,17 @@ RTA_SKY_N = 256
 RTA_SKY_SLABS = 30
 
 
+class Window(ctypes.Structure):
+    """rta_window_t: on window of on_s seconds ending at the search time, off window of off_s seconds before it."""
+    _fields_ = [("on_s", ctypes.c_int32), ("off_s", ctypes.c_int32)]
+
+
+ALERT_DTYPE = np.dtype([("window", np.int32), ("ix", np.int32), ("iy", np.int32), ("pad", np.int32),
+                        ("n_on", np.int64), ("n_off", np.int64), ("alpha", np.float64), ("significance", np.float64)])
+RTA_SKY_MIN_SLABS = 60
+RTA_MAX_DISK_RADIUS = 32
+
+
 class Bundle(ctypes.Structure):
     """rta_bundle_t: one bundle in host memory for the serving stream."""
     _fields_ = [("h_wave", ctypes.c_void_p), ("n_wave", ctypes.c_int64), ("h_wave_off", ctypes.c_void_p),
@@ -420,6 +433,28 @@ def rta_stream_add_events(stream: int, d_events: int, n_evt: int, arrival_ns: in
 
 def rta_stream_destroy(stream: int):
     _check(load().rta_stream_destroy(stream))
+
+
+def rta_transient_search(stream: int, now_ns: int, windows, radius_bins: int, s_min: float,
+                         max_alerts: int = 65536) -> np.ndarray:
+    """Alerts (ALERT_DTYPE rows sorted by window, iy, ix) of the windows [(on_s, off_s), ...]."""
+    w = np.ascontiguousarray(np.asarray(windows, np.int32).reshape(-1, 2))
+    out = np.zeros(max(max_alerts, 1), ALERT_DTYPE)
+    n = ctypes.c_int(0)
+    _check(load().rta_transient_search(stream, now_ns, w.ctypes.data_as(ctypes.c_void_p), len(w), radius_bins,
+                                       float(s_min), out.ctypes.data_as(ctypes.c_void_p), max_alerts, ctypes.byref(n)))
+    return out[: min(n.value, max_alerts)].copy()
+
+
+def rta_significance_map(stream: int, now_ns: int, window, radius_bins: int):
+    """(significance, disk on counts, disk off counts) maps [iy, ix] of one window (on_s, off_s)."""
+    sig = np.zeros((RTA_SKY_N, RTA_SKY_N), np.float64)
+    on = np.zeros((RTA_SKY_N, RTA_SKY_N), np.int64)
+    off = np.zeros((RTA_SKY_N, RTA_SKY_N), np.int64)
+    _check(load().rta_significance_map(stream, now_ns, Window(int(window[0]), int(window[1])), radius_bins,
+                                       sig.ctypes.data_as(ctypes.c_void_p), on.ctypes.data_as(ctypes.c_void_p),
+                                       off.ctypes.data_as(ctypes.c_void_p)))
+    return sig, on, off
 
 
 RTA_NOALLOC_MAX_CAMS = 16

@@ -84,7 +84,26 @@ cudaError_t launch_wait_selftest(unsigned int* status, uint64_t timeout_ns, unsi
 // stores a message for rta_last_error() on the calling thread
 void set_last_error(const char* msg);
 // sky map and geometric event rows (k_skymap.cu)
-cudaError_t launch_skymap_fill(const rta_event_t* ev, int64_t n_evt, unsigned int* slab, cudaStream_t s);
+cudaError_t launch_skymap_fill(const rta_event_t* ev, int64_t n_evt, unsigned int* slab, unsigned int* slab_min,
+                               cudaStream_t s);
+// One window of the transient search (k_skymap.cu): counts from the ring,
+// row prefix sums, disk sums, significance, alerts.
+struct TransientArgs {
+    const unsigned int* slabs;
+    int n_slabs;
+    unsigned long long use_on, use_off;
+    unsigned int *on, *off, *pre_on, *pre_off;   // [256*256], [256*257] work maps
+    const int* hw;                               // [2R + 1] disk half-widths
+    int R;
+    double alpha, s_min;
+    int window;
+    rta_alert_t* alerts;                         // nullable
+    unsigned int* n_alerts;
+    unsigned int cap;
+    double* sig;                                 // nullable
+    int64_t *d_on, *d_off;                       // nullable
+};
+cudaError_t launch_transient(const TransientArgs& t, cudaStream_t s);
 cudaError_t launch_skymap_sum(const unsigned int* slabs, unsigned long long use, unsigned int* out, cudaStream_t s);
 cudaError_t launch_stereo_to_events(const rta_stereo_t* st, int64_t n_evt, rta_event_t* ev, cudaStream_t s);
 // grow a model's workspace ahead of use (rta_surrogate.cu)

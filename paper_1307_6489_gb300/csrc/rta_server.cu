@@ -138,8 +138,17 @@ struct rta_stream {
     std::vector<Slot> slots;
     cudaStream_t s_model = nullptr, s_map = nullptr;
     unsigned int* d_slabs = nullptr;   // RTA_SKY_SLABS x 256 x 256
+    unsigned int* d_slabs_min = nullptr;   // RTA_SKY_MIN_SLABS x 256 x 256
     unsigned int* d_map = nullptr;
     int64_t slab_sec[RTA_SKY_SLABS];
+    int64_t slab_min[RTA_SKY_MIN_SLABS];
+    // transient-search work buffers (grown on demand)
+    unsigned int *d_won = nullptr, *d_woff = nullptr, *d_pre_on = nullptr, *d_pre_off = nullptr, *d_nal = nullptr;
+    int* d_hw = nullptr;
+    rta_alert_t* d_alerts = nullptr;
+    size_t alerts_cap = 0;
+    double* d_sig = nullptr;
+    int64_t *d_son = nullptr, *d_soff = nullptr;
     // requests
     std::mutex mu;
     std::condition_variable cv, done_cv;
@@ -153,6 +162,36 @@ struct rta_stream {
 };
 
 namespace {
+
+int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Count events into the one-second slab of arrival_ns and the one-minute slab of
+// its second, on the map stream, recycling a slab when a newer second (minute)
+// claims it; events of a second (minute) that has left its ring are not counted.
+// Caller holds S->mu.
+cudaError_t fill_slabs(rta_stream* S, const rta_event_t* d_ev, int64_t n_evt, int64_t arrival_ns) {
+    const int64_t sec = arrival_ns / 1000000000ll;
+    const int slab = int(((sec % RTA_SKY_SLABS) + RTA_SKY_SLABS) % RTA_SKY_SLABS);
+    const int64_t mnt = floor_div(sec, 60);
+    const int mslab = int(((mnt % RTA_SKY_MIN_SLABS) + RTA_SKY_MIN_SLABS) % RTA_SKY_MIN_SLABS);
+    const size_t map_bytes = sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N;
+    unsigned int* p_sec = S->d_slabs + size_t(slab) * RTA_SKY_N * RTA_SKY_N;
+    unsigned int* p_min = S->d_slabs_min + size_t(mslab) * RTA_SKY_N * RTA_SKY_N;
+    cudaError_t e = cudaSuccess;
+    if (S->slab_sec[slab] < sec) {
+        e = cudaMemsetAsync(p_sec, 0, map_bytes, S->s_map);
+        S->slab_sec[slab] = sec;
+    }
+    if (e == cudaSuccess && S->slab_min[mslab] < mnt) {
+        e = cudaMemsetAsync(p_min, 0, map_bytes, S->s_map);
+        S->slab_min[mslab] = mnt;
+    }
+    if (e != cudaSuccess || n_evt <= 0) return e;
+    unsigned int* a = S->slab_sec[slab] == sec ? p_sec : nullptr;
+    unsigned int* b = S->slab_min[mslab] == mnt ? p_min : nullptr;
+    if (!a && !b) return cudaSuccess;
+    return rta::launch_skymap_fill(d_ev, n_evt, a, b, S->s_map);
+}
 
 int dispatch(rta_stream* S, Req& r, Slot& sl) {
     const rta_bundle_t& b = r.b;
@@ -189,17 +228,10 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
         if (rc) return rc;
         D_TRY(rta::launch_stereo_to_events(d_st, b.n_evt, d_ev, s));
     }
-    // sky map: the one-second slab of the bundle's arrival
-    const int64_t sec = b.arrival_ns / 1000000000ll;
-    const int slab = int(((sec % RTA_SKY_SLABS) + RTA_SKY_SLABS) % RTA_SKY_SLABS);
+    // sky map: the one-second and one-minute slabs of the bundle's arrival
     D_TRY(cudaEventRecord(sl.e_ev, s));
     D_TRY(cudaStreamWaitEvent(S->s_map, sl.e_ev, 0));
-    unsigned int* slab_ptr = S->d_slabs + size_t(slab) * RTA_SKY_N * RTA_SKY_N;
-    if (S->slab_sec[slab] < sec) {
-        D_TRY(cudaMemsetAsync(slab_ptr, 0, sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N, S->s_map));
-        S->slab_sec[slab] = sec;
-    }
-    if (S->slab_sec[slab] == sec) D_TRY(rta::launch_skymap_fill(d_ev, b.n_evt, slab_ptr, S->s_map));
+    D_TRY(fill_slabs(S, d_ev, b.n_evt, b.arrival_ns));
     D_TRY(cudaEventRecord(sl.e_map, S->s_map));
     D_TRY(cudaStreamWaitEvent(s, sl.e_map, 0));
     D_TRY(cudaMemcpyAsync(b.h_events, d_ev, size_t(b.n_evt) * sizeof(rta_event_t), cudaMemcpyDeviceToHost, s));
@@ -279,6 +311,12 @@ void release_all(rta_stream* S) {
     if (S->s_map) cudaStreamDestroy(S->s_map);
     cudaFree(S->arena.base);
     cudaFree(S->d_slabs);
+    cudaFree(S->d_slabs_min);
+    {
+        void* w[] = {S->d_won, S->d_woff, S->d_pre_on, S->d_pre_off, S->d_nal, S->d_hw, S->d_alerts, S->d_sig,
+                     S->d_son, S->d_soff};
+        for (void* q : w) cudaFree(q);
+    }
     cudaFree(S->d_map);
 }
 
@@ -313,8 +351,11 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
     S->max_img = max_img;
     S->max_evt = max_evt;
     for (auto& x : S->slab_sec) x = -1;
+    for (auto& x : S->slab_min) x = INT64_MIN;
     bool ok = cudaMalloc(&S->arena.base, hbm_budget_bytes) == cudaSuccess &&
               cudaMalloc(&S->d_slabs, sizeof(unsigned int) * RTA_SKY_SLABS * RTA_SKY_N * RTA_SKY_N) == cudaSuccess &&
+              cudaMalloc(&S->d_slabs_min, sizeof(unsigned int) * RTA_SKY_MIN_SLABS * RTA_SKY_N * RTA_SKY_N) ==
+                  cudaSuccess &&
               cudaMalloc(&S->d_map, sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->s_model, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->s_map, cudaStreamNonBlocking) == cudaSuccess;
@@ -332,6 +373,7 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
     S->arena.size = hbm_budget_bytes;
     S->arena.reset();
     cudaMemset(S->d_slabs, 0, sizeof(unsigned int) * RTA_SKY_SLABS * RTA_SKY_N * RTA_SKY_N);
+    cudaMemset(S->d_slabs_min, 0, sizeof(unsigned int) * RTA_SKY_MIN_SLABS * RTA_SKY_N * RTA_SKY_N);
     if (model && (rc = rta::surrogate_reserve(model, max_img, max_evt))) {
         release_all(S);
         delete S;
@@ -413,14 +455,7 @@ int rta_stream_add_events(rta_stream* S, const rta_event_t* d_events, int64_t n_
     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(ev, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_map, ev, 0);
-    const int64_t sec = arrival_ns / 1000000000ll;
-    const int slab = int(((sec % RTA_SKY_SLABS) + RTA_SKY_SLABS) % RTA_SKY_SLABS);
-    unsigned int* slab_ptr = S->d_slabs + size_t(slab) * RTA_SKY_N * RTA_SKY_N;
-    if (e == cudaSuccess && S->slab_sec[slab] < sec) {
-        e = cudaMemsetAsync(slab_ptr, 0, sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N, S->s_map);
-        S->slab_sec[slab] = sec;
-    }
-    if (e == cudaSuccess && S->slab_sec[slab] == sec && n_evt > 0) e = rta::launch_skymap_fill(d_events, n_evt, slab_ptr, S->s_map);
+    if (e == cudaSuccess) e = fill_slabs(S, d_events, n_evt, arrival_ns);
     // the caller's stream must not reuse d_events before the fill has read it
     if (e == cudaSuccess) e = cudaEventRecord(ev, S->s_map);
     if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, ev, 0);
@@ -441,6 +476,172 @@ int rta_stream_destroy(rta_stream* S) {
     cudaDeviceSynchronize();
     release_all(S);
     delete S;
+    return RTA_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================= transient search
+namespace {
+
+bool window_ok(const rta_window_t& w) {
+    if (w.on_s < 1 || w.off_s < 1) return false;
+    if (int64_t(w.on_s) + w.off_s <= RTA_SKY_SLABS) return true;
+    return w.on_s % 60 == 0 && w.off_s % 60 == 0 && int64_t(w.on_s) + w.off_s <= 60 * RTA_SKY_MIN_SLABS;
+}
+
+// Half-widths of the rows of the disk x^2 + y^2 <= R^2: hw[dy + R] = largest w
+// with w^2 + dy^2 <= R^2.
+std::vector<int> disk_half_widths(int R) {
+    std::vector<int> hw(size_t(2 * R + 1));
+    for (int dy = -R; dy <= R; ++dy) {
+        int w = 0;
+        while ((w + 1) * (w + 1) + dy * dy <= R * R) ++w;
+        hw[size_t(dy + R)] = w;
+    }
+    return hw;
+}
+
+// Ring and slab masks of one window at time now_ns (caller holds S->mu).
+void window_masks(const rta_stream* S, int64_t now_ns, const rta_window_t& w, const unsigned int** slabs,
+                  int* n_slabs, unsigned long long* use_on, unsigned long long* use_off) {
+    const int64_t now_s = now_ns / 1000000000ll;
+    *use_on = *use_off = 0;
+    if (int64_t(w.on_s) + w.off_s <= RTA_SKY_SLABS) {
+        *slabs = S->d_slabs;
+        *n_slabs = RTA_SKY_SLABS;
+        for (int k = 0; k < RTA_SKY_SLABS; ++k) {
+            const int64_t t = S->slab_sec[k];
+            if (t > now_s - w.on_s && t <= now_s) *use_on |= 1ull << k;
+            if (t > now_s - w.on_s - w.off_s && t <= now_s - w.on_s) *use_off |= 1ull << k;
+        }
+    } else {
+        const int64_t now_m = floor_div(now_s, 60), on = w.on_s / 60, off = w.off_s / 60;
+        *slabs = S->d_slabs_min;
+        *n_slabs = RTA_SKY_MIN_SLABS;
+        for (int k = 0; k < RTA_SKY_MIN_SLABS; ++k) {
+            const int64_t t = S->slab_min[k];
+            if (t > now_m - on && t <= now_m) *use_on |= 1ull << k;
+            if (t > now_m - on - off && t <= now_m - on) *use_off |= 1ull << k;
+        }
+    }
+}
+
+cudaError_t ensure_work(rta_stream* S, size_t alerts_cap, bool maps) {
+    const size_t nb = size_t(RTA_SKY_N) * RTA_SKY_N, np = size_t(RTA_SKY_N) * (RTA_SKY_N + 1);
+    cudaError_t e = cudaSuccess;
+    if (!S->d_won) {
+        if ((e = cudaMalloc(&S->d_won, nb * 4)) != cudaSuccess || (e = cudaMalloc(&S->d_woff, nb * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&S->d_pre_on, np * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&S->d_pre_off, np * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&S->d_nal, sizeof(unsigned int))) != cudaSuccess ||
+            (e = cudaMalloc(&S->d_hw, sizeof(int) * (2 * RTA_MAX_DISK_RADIUS + 1))) != cudaSuccess)
+            return e;
+    }
+    if (alerts_cap > S->alerts_cap) {
+        cudaFree(S->d_alerts);
+        S->d_alerts = nullptr;
+        S->alerts_cap = 0;
+        if ((e = cudaMalloc(&S->d_alerts, sizeof(rta_alert_t) * alerts_cap)) != cudaSuccess) return e;
+        S->alerts_cap = alerts_cap;
+    }
+    if (maps && !S->d_sig) {
+        if ((e = cudaMalloc(&S->d_sig, nb * 8)) != cudaSuccess || (e = cudaMalloc(&S->d_son, nb * 8)) != cudaSuccess ||
+            (e = cudaMalloc(&S->d_soff, nb * 8)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// Enqueue the search of one window on the map stream (caller holds S->mu).
+cudaError_t enqueue_window(rta_stream* S, int64_t now_ns, const rta_window_t& w, int index, int R, double s_min,
+                           bool alerts, bool maps) {
+    rta::TransientArgs t = {};
+    window_masks(S, now_ns, w, &t.slabs, &t.n_slabs, &t.use_on, &t.use_off);
+    t.on = S->d_won;
+    t.off = S->d_woff;
+    t.pre_on = S->d_pre_on;
+    t.pre_off = S->d_pre_off;
+    t.hw = S->d_hw;
+    t.R = R;
+    t.alpha = double(w.on_s) / double(w.off_s);
+    t.s_min = s_min;
+    t.window = index;
+    t.alerts = alerts ? S->d_alerts : nullptr;
+    t.n_alerts = S->d_nal;
+    t.cap = unsigned(S->alerts_cap);
+    t.sig = maps ? S->d_sig : nullptr;
+    t.d_on = maps ? S->d_son : nullptr;
+    t.d_off = maps ? S->d_soff : nullptr;
+    return rta::launch_transient(t, S->s_map);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rta_transient_search(rta_stream* S, int64_t now_ns, const rta_window_t* windows, int n_windows, int radius_bins,
+                         double s_min, rta_alert_t* h_alerts, int max_alerts, int* n_alerts) {
+    if (!S || !n_alerts || n_windows < 0 || (n_windows > 0 && !windows) || max_alerts < 0 ||
+        (max_alerts > 0 && !h_alerts))
+        return vfail(RTA_E_INVALID, "bad argument");
+    if (radius_bins < 0 || radius_bins > RTA_MAX_DISK_RADIUS)
+        return vfail(RTA_E_INVALID, "radius %d outside 0..%d", radius_bins, RTA_MAX_DISK_RADIUS);
+    for (int i = 0; i < n_windows; ++i)
+        if (!window_ok(windows[i]))
+            return vfail(RTA_E_INVALID, "window %d (%d s on, %d s off) does not fit the slab rings", i, windows[i].on_s,
+                         windows[i].off_s);
+    *n_alerts = 0;
+    if (n_windows == 0) return RTA_OK;
+    cudaSetDevice(S->device);
+    const std::vector<int> hw = disk_half_widths(radius_bins);
+    unsigned int n_dev = 0;
+    std::unique_lock<std::mutex> lock(S->mu);
+    cudaError_t e = ensure_work(S, size_t(n_windows) * RTA_SKY_N * RTA_SKY_N, false);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_hw, hw.data(), sizeof(int) * hw.size(), cudaMemcpyHostToDevice, S->s_map);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_nal, 0, sizeof(unsigned int), S->s_map);
+    for (int i = 0; i < n_windows && e == cudaSuccess; ++i)
+        e = enqueue_window(S, now_ns, windows[i], i, radius_bins, s_min, true, false);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_dev, S->d_nal, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->s_map);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_map);
+    std::vector<rta_alert_t> all(std::min<size_t>(n_dev, S->alerts_cap));
+    if (e == cudaSuccess && !all.empty())
+        e = cudaMemcpy(all.data(), S->d_alerts, sizeof(rta_alert_t) * all.size(), cudaMemcpyDeviceToHost);
+    lock.unlock();
+    if (e != cudaSuccess) return vfail(RTA_E_CUDA, "transient search: %s", cudaGetErrorString(e));
+    std::sort(all.begin(), all.end(), [](const rta_alert_t& a, const rta_alert_t& b) {
+        if (a.window != b.window) return a.window < b.window;
+        if (a.iy != b.iy) return a.iy < b.iy;
+        return a.ix < b.ix;
+    });
+    *n_alerts = int(all.size());
+    const size_t n_out = std::min<size_t>(all.size(), size_t(max_alerts));
+    if (n_out) memcpy(h_alerts, all.data(), sizeof(rta_alert_t) * n_out);
+    return RTA_OK;
+}
+
+int rta_significance_map(rta_stream* S, int64_t now_ns, rta_window_t window, int radius_bins, double* h_sig,
+                         int64_t* h_on, int64_t* h_off) {
+    if (!S || !h_sig) return vfail(RTA_E_INVALID, "bad argument");
+    if (radius_bins < 0 || radius_bins > RTA_MAX_DISK_RADIUS)
+        return vfail(RTA_E_INVALID, "radius %d outside 0..%d", radius_bins, RTA_MAX_DISK_RADIUS);
+    if (!window_ok(window))
+        return vfail(RTA_E_INVALID, "window (%d s on, %d s off) does not fit the slab rings", window.on_s, window.off_s);
+    cudaSetDevice(S->device);
+    const std::vector<int> hw = disk_half_widths(radius_bins);
+    const size_t nb = size_t(RTA_SKY_N) * RTA_SKY_N;
+    std::unique_lock<std::mutex> lock(S->mu);
+    cudaError_t e = ensure_work(S, 0, true);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_hw, hw.data(), sizeof(int) * hw.size(), cudaMemcpyHostToDevice, S->s_map);
+    if (e == cudaSuccess) e = enqueue_window(S, now_ns, window, 0, radius_bins, 0.0, false, true);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_sig, S->d_sig, nb * 8, cudaMemcpyDeviceToHost, S->s_map);
+    if (e == cudaSuccess && h_on) e = cudaMemcpyAsync(h_on, S->d_son, nb * 8, cudaMemcpyDeviceToHost, S->s_map);
+    if (e == cudaSuccess && h_off) e = cudaMemcpyAsync(h_off, S->d_soff, nb * 8, cudaMemcpyDeviceToHost, S->s_map);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_map);
+    lock.unlock();
+    if (e != cudaSuccess) return vfail(RTA_E_CUDA, "significance map: %s", cudaGetErrorString(e));
     return RTA_OK;
 }
 
