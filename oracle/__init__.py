@@ -54,12 +54,12 @@ def _L():
         lib = ctypes.CDLL(_LIB)
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_float
-        lib.or_integrate.argtypes = [P, i32, i32, P, P, i32, i32, i32, P, P, P, P]
+        lib.or_integrate.argtypes = [P, i32, i32, P, P, i32, i32, i32, P, P, P, P, P]
         lib.or_clean.argtypes = [i32, P, P, i32, f32, f32, i32, P]
         lib.or_hillas.argtypes = [i32, P, P, P, P, P]
         lib.or_stereo.argtypes = [i32, P, P, P]
         lib.or_reconstruct.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, i32, f32, f32, i32, P, P, P, P,
-                                       P, i64, P, P, P, i32]
+                                       P, i64, P, P, P, i32, P]
         _lib = lib
     return _lib
 
@@ -71,8 +71,12 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def integrate(wave, p16, scale, sliding: bool, start: int, W: int):
-    """wave (P, S) uint16 -> (q float32, t float64, window start int32, window sum int64)."""
+def integrate(wave, p16, scale, sliding: bool, start: int, W: int, weights=None):
+    """wave (P, S) uint16 -> (q float32, t float64, window start int32, window sum int64).
+
+    weights (W integers, optional): the digital-filter-style charge
+    16 * sum_k c_k s[st + k] - (sum_k c_k) * p16, rounded to FP32 and multiplied by
+    the scale, over the same window (st and the flat sum are unchanged)."""
     wave = np.ascontiguousarray(wave, np.uint16)
     P, Sn = wave.shape
     p16 = np.ascontiguousarray(p16, np.int32)
@@ -81,8 +85,11 @@ def integrate(wave, p16, scale, sliding: bool, start: int, W: int):
     t = np.zeros(P, np.float64)
     ws = np.zeros(P, np.int32)
     wsum = np.zeros(P, np.int64)
-    if _L().or_integrate(_p(wave), P, Sn, _p(p16), _p(scale), int(sliding), int(start), int(W), _p(q), _p(t),
-                         _p(ws), _p(wsum)) != 0:
+    wts = None if weights is None else np.ascontiguousarray(weights, np.int32)
+    if wts is not None and len(wts) != W:
+        raise ValueError("weights must have W entries")
+    if _L().or_integrate(_p(wave), P, Sn, _p(p16), _p(scale), int(sliding), int(start), int(W), _p(wts), _p(q),
+                         _p(t), _p(ws), _p(wsum)) != 0:
         raise ValueError("or_integrate: bad arguments")
     return q, t, ws, wsum
 
@@ -168,12 +175,13 @@ def reconstruct(wl, threads: int | None = None, do_stereo: bool = True, per_pixe
     pr = wl.proc
     threads = threads or os.cpu_count() or 1
     tel_xy = np.ascontiguousarray(wl.tel_xy, np.float32)
+    wts = None if getattr(pr, "weights", None) is None else np.ascontiguousarray(pr.weights, np.int32)
     st = lib.or_reconstruct(n_img, _p(wave), _p(wl.wave_off), _p(wl.img_tel), _p(wl.tel_cam), _p(wl.tel_pix_off),
                             _p(wl.p16), _p(wl.scale), _p(cam_info), ctypes.cast(cam_xy, ctypes.c_void_p),
                             ctypes.cast(cam_nb, ctypes.c_void_p), int(pr.sliding), int(pr.start), int(pr.W),
                             float(pr.t_hi), float(pr.t_lo), int(pr.core_needs_neighbour), _p(hil),
                             _p(wl.pix_off) if per_pixel else None, _p(q), _p(t), _p(mk), n_evt if do_stereo else 0,
-                            _p(wl.evt_off), _p(tel_xy), _p(ste), int(threads))
+                            _p(wl.evt_off), _p(tel_xy), _p(ste), int(threads), _p(wts))
     if st != 0:
         raise RuntimeError("or_reconstruct failed")
     return dict(hillas=hil, stereo=ste, q=q, t=t, mask=mk)

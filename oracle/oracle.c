@@ -64,7 +64,7 @@ enum { OS_DIR_X = 0, OS_DIR_Y, OS_CORE_X, OS_CORE_Y, OS_NVALID, OS_FLAGS, OS_N }
  * when num <= 0. Returns 0, or -1 if an argument is out of range.
  */
 int or_integrate(const uint16_t* wave, int P, int S, const int32_t* p16, const float* scale, int sliding,
-                 int start, int W, float* q, double* t, int32_t* wstart, int64_t* wsum) {
+                 int start, int W, const int32_t* weights, float* q, double* t, int32_t* wstart, int64_t* wsum) {
     if (P < 0 || S <= 0 || W <= 0 || W > S) return -1;
     if (!sliding && (start < 0 || start + W > S)) return -1;
     for (int p = 0; p < P; ++p) {
@@ -82,7 +82,18 @@ int or_integrate(const uint16_t* wave, int P, int S, const int32_t* p16, const f
             for (int k = start; k < start + W; ++k) best += w[k];
         }
         int64_t num = 16 * best - (int64_t)W * p16[p];
-        volatile float fnum = (float)num;
+        /* digital-filter-style extractor: integer weights over the same window,
+           pedestal weighted by their sum; one rounding to FP32, one multiply */
+        int64_t qnum = num;
+        if (weights) {
+            int64_t a = 0, c = 0;
+            for (int k = 0; k < W; ++k) {
+                a += (int64_t)weights[k] * w[best_s + k];
+                c += weights[k];
+            }
+            qnum = 16 * a - c * p16[p];
+        }
+        volatile float fnum = (float)qnum;
         volatile float qq = fnum * scale[p];
         q[p] = qq;
         if (t) {
@@ -286,6 +297,7 @@ typedef struct {
     const float* const* cam_xy;
     const int16_t* const* cam_nb;
     int sliding, start, W, core_nb;
+    const int32_t* weights;   /* NULL: flat window sum */
     float t_hi, t_lo;
     /* outputs */
     double* hillas;                 /* n_img * OH_N */
@@ -316,8 +328,8 @@ static void* bundle_worker(void* arg) {
         int tel = J->img_tel[i], cam = J->tel_cam[tel];
         int P = J->cam_info[3 * cam], S = J->cam_info[3 * cam + 1], K = J->cam_info[3 * cam + 2];
         int64_t row = J->tel_pix_off[tel];
-        if (or_integrate(J->wave + J->wave_off[i], P, S, J->p16 + row, J->scale + row, J->sliding, J->start, J->W, q,
-                         t, NULL, NULL) != 0) {
+        if (or_integrate(J->wave + J->wave_off[i], P, S, J->p16 + row, J->scale + row, J->sliding, J->start, J->W,
+                         J->weights, q, t, NULL, NULL) != 0) {
             J->status = -1;
             continue;
         }
@@ -373,12 +385,13 @@ int or_reconstruct(int64_t n_img, const uint16_t* wave, const int64_t* wave_off,
                    const int32_t* cam_info, const float* const* cam_xy, const int16_t* const* cam_nb, int sliding,
                    int start, int W, float t_hi, float t_lo, int core_nb, double* hillas, const int64_t* pix_off,
                    float* q_out, double* t_out, uint8_t* mask_out, int64_t n_evt, const int32_t* evt_off,
-                   const float* tel_xy, double* stereo, int n_threads) {
+                   const float* tel_xy, double* stereo, int n_threads, const int32_t* weights) {
     bundle_job_t J;
     memset(&J, 0, sizeof J);
     J.n_img = n_img; J.wave = wave; J.wave_off = wave_off; J.img_tel = img_tel; J.tel_cam = tel_cam;
     J.tel_pix_off = tel_pix_off; J.p16 = p16; J.scale = scale; J.cam_info = cam_info; J.cam_xy = cam_xy;
-    J.cam_nb = cam_nb; J.sliding = sliding; J.start = start; J.W = W; J.core_nb = core_nb; J.t_hi = t_hi;
+    J.cam_nb = cam_nb; J.sliding = sliding; J.start = start; J.W = W; J.weights = weights; J.core_nb = core_nb;
+    J.t_hi = t_hi;
     J.t_lo = t_lo; J.hillas = hillas; J.pix_off = pix_off; J.q_out = q_out; J.t_out = t_out;
     J.mask_out = mask_out; J.n_evt = n_evt; J.evt_off = evt_off; J.tel_xy = tel_xy; J.stereo = stereo;
     run_threads(bundle_worker, &J, n_threads);

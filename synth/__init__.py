@@ -139,13 +139,16 @@ def window_fraction(sliding: bool, start: int, W: int) -> float:
 # --------------------------------------------------------------------------
 @dataclass
 class Processing:
-    """Per-workload processing parameters (window and tailcut)."""
+    """Per-workload processing parameters (window and tailcut). weights: integer
+    weights of the digital-filter-style charge over the sliding window (None:
+    the flat window sum)."""
     sliding: bool
     start: int
     W: int
     t_hi: float
     t_lo: float
     core_needs_neighbour: bool
+    weights: tuple = None
 
 
 PRESET_PROCESSING = {

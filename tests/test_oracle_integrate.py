@@ -134,3 +134,47 @@ def test_bad_arguments_rejected():
         oracle.integrate(wave, np.zeros(2, np.int32), np.ones(2, np.float32), True, 0, 9)
     with pytest.raises(ValueError):
         oracle.integrate(wave, np.zeros(2, np.int32), np.ones(2, np.float32), False, 5, 4)
+
+
+# ---------------------------------------------------------------------------- digital-filter-style charge
+def test_filter_with_unit_weights_is_the_window_sum():
+    rng = np.random.default_rng(21)
+    P, S, W = 64, 30, 6
+    wave = rng.integers(300, 3000, size=(P, S)).astype(np.uint16)
+    p16 = rng.integers(16 * 380, 16 * 420, size=P).astype(np.int32)
+    scale = rng.uniform(0.004, 0.01, P).astype(np.float32)
+    q0, t0, s0, _ = oracle.integrate(wave, p16, scale, True, 0, W)
+    q1, t1, s1, _ = oracle.integrate(wave, p16, scale, True, 0, W, weights=[1] * W)
+    np.testing.assert_array_equal(q0.view(np.uint32), q1.view(np.uint32))
+    np.testing.assert_array_equal(t0, t1)
+    np.testing.assert_array_equal(s0, s1)
+
+
+def test_filter_is_linear_in_its_weights_and_blind_to_the_pedestal():
+    """With scale = 1/16 and small integers every charge is exact, so charges of
+    summed weights add exactly; a waveform at the pedestal gives zero for any
+    weights; a single non-zero sample inside the window picks one weight."""
+    rng = np.random.default_rng(22)
+    P, S, W = 40, 25, 6
+    wave = rng.integers(0, 200, size=(P, S)).astype(np.uint16)
+    p16 = (16 * rng.integers(0, 50, size=P)).astype(np.int32)
+    scale = np.full(P, 1.0 / 16.0, np.float32)
+    c1 = np.array([1, 3, 5, 4, 2, 1])
+    c2 = np.array([-1, 0, 2, 7, 0, 3])
+    qa, _, sa, _ = oracle.integrate(wave, p16, scale, True, 0, W, weights=c1)
+    qb, _, sb, _ = oracle.integrate(wave, p16, scale, True, 0, W, weights=c2)
+    qc, _, sc, _ = oracle.integrate(wave, p16, scale, True, 0, W, weights=c1 + c2)
+    assert (sa == sb).all() and (sa == sc).all()                 # the window does not depend on the weights
+    np.testing.assert_array_equal(qc, qa + qb)
+    ped = (p16 // 16).astype(np.uint16)
+    flat = np.repeat(ped[:, None], S, axis=1)
+    qp, _, _, _ = oracle.integrate(flat, p16, scale, True, 0, W, weights=c1)
+    assert (qp == 0).all()
+    for j in range(W):
+        # the only signal at sample j < W: every window with start <= j ties, the
+        # first (start 0) is chosen, so the sample meets weight j
+        one = np.zeros((1, S), np.uint16)
+        one[0, j] = 100
+        q, _, st, _ = oracle.integrate(one, np.zeros(1, np.int32), np.ones(1, np.float32), True, 0, W,
+                                       weights=c1)
+        assert st[0] == 0 and q[0] == 16 * 100 * c1[j]
