@@ -500,6 +500,28 @@ def main():
     rta.rta_graph_destroy(graph)
     ctx.check(sp)
 
+    # ---------------- the digital-filter-style extractor on the same bundle (image kernel alone)
+    # weights summing to W, so that the registered (flat-window) calibration
+    # normalises the filter and the cleaning sees charges of the same scale
+    filt_w = (0, 1, 2, 2, 1, 0)
+    filt_ms = None
+    if proc[2] == len(filt_w) and proc[0] != rta.RTA_WINDOW_FIXED:
+        rta.rta_set_filter_weights(h, filt_w)
+        fproc = (rta.RTA_WINDOW_FILTER,) + tuple(proc[1:])
+        fhil = torch.empty_like(hil)
+        for _ in range(3):
+            rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *fproc,
+                                fhil.data_ptr(), sp)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *fproc,
+                                fhil.data_ptr(), sp)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        filt_ms = f0.elapsed_time(f1) / args.steps
+        ctx.check(sp)
+
     # ---------------- roofline of the dominant kernel (fused image kernel)
     hbm_peak, peak_kind = peaks()
     alg_bytes = wl.wave_bytes + wl.n_img * HILLAS_BYTES
@@ -569,6 +591,9 @@ def main():
             "gbs": wl.wave_bytes * ws / (ms_per_step / 1e3) / 1e9,
             "gbs_vs_hbm_peak": wl.wave_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
             "kernel_ms": {"image_chain": chain_avg, "stereo": statistics.mean(stereo_ms)},
+            "extractors": {"sliding_window_ms": chain_avg, "digital_filter_ms": filt_ms, "filter_weights": list(filt_w),
+                           "digital_filter_hbm_frac": (alg_bytes / (filt_ms / 1e3) / 1e9 / hbm_peak
+                                                       if filt_ms else None)},
             "graph": {"ms_per_step": graph_ms, "events_per_s": events_all / (graph_ms / 1e3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,

@@ -72,6 +72,9 @@ typedef enum {
 /* Window modes of rta_calibrate_integrate / rta_image_chain */
 #define RTA_WINDOW_FIXED 0   /* samples [start, start+W) */
 #define RTA_WINDOW_SLIDING 1 /* the W-window of maximal integer sum, lowest start on ties */
+#define RTA_WINDOW_FILTER 2  /* the sliding window, charge as an integer-weighted sum over it
+                                (digital-filter-style extractor; weights per context, see
+                                rta_set_filter_weights) */
 
 /* Hillas row flags */
 #define RTA_HF_EMPTY 1u     /* no pixel survived cleaning: every field but n_pix is 0 */
@@ -184,6 +187,16 @@ int rta_set_chain_config(rta_ctx* ctx, int variant, int n_stages, int ctas_per_s
  * size and dynamic shared memory per CTA in bytes (NULL outputs are skipped). */
 int rta_get_chain_config(rta_ctx* ctx, int* variant, int* n_stages, int* ctas_per_sm, int* grid,
                          size_t* smem_bytes);
+
+/* Weights of the digital-filter-style extractor (window_mode RTA_WINDOW_FILTER;
+ * a signal-extraction alternative to the flat window sum, Sec. 5): W integer
+ * weights c_k, |c_k| <= 4096, sum > 0. With st the sliding window's start, the
+ * charge is q = fl32(16 * sum_k c_k s[st+k] - (sum_k c_k) * p16) * scale: exact
+ * 64-bit integers, one rounding to FP32, one FP32 multiply (the calibration
+ * scale then normalises the filter); st and the peak time are those of the flat
+ * window. A call in RTA_WINDOW_FILTER mode must pass this W. Copied; W = 0
+ * clears. Not available to rta_image_chain_noalloc. */
+int rta_set_filter_weights(rta_ctx* ctx, const int32_t* weights, int W);
 
 /* Tile shape of a variant (0 .. RTA_CHAIN_VARIANTS-1). Variant 4 has the shape of
  * variant 0, compiled for at most 68 registers per thread so that three CTAs fit on

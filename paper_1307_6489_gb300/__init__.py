@@ -29,6 +29,7 @@ RTA_E_TIMEOUT = -6
 RTA_E_DEVICE = -7
 RTA_WINDOW_FIXED = 0
 RTA_WINDOW_SLIDING = 1
+RTA_WINDOW_FILTER = 2
 RTA_HF_EMPTY = 1
 RTA_HF_NO_TIME = 2
 RTA_HF_BAD_INPUT = 4
@@ -106,6 +107,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_skymap_read": ([P, i64, P], i32),
         "rta_stream_add_events": ([P, P, i64, i64, P], i32),
         "rta_stream_destroy": ([P], i32),
+        "rta_set_filter_weights": ([P, P, i32], i32),
         "rta_transient_search": ([P, i64, P, i32, i32, ctypes.c_double, P, i32, P], i32),
         "rta_significance_map": ([P, i64, Window, i32, P, P, P], i32),
         "rta_selftest_wait_timeout": ([P, i32, P, P], i32),
@@ -208,6 +210,12 @@ def rta_selftest_wait_timeout(ctx: int, timeout_ms: int, stream: int = 0) -> int
     w = ctypes.c_uint64()
     _check(load().rta_selftest_wait_timeout(ctx, timeout_ms, ctypes.byref(w), stream))
     return w.value
+
+
+def rta_set_filter_weights(ctx: int, weights):
+    """Integer weights of the RTA_WINDOW_FILTER extractor (empty: clear)."""
+    w = np.ascontiguousarray(np.asarray(weights, np.int32).reshape(-1))
+    _check(load().rta_set_filter_weights(ctx, w.ctypes.data_as(ctypes.c_void_p) if len(w) else None, len(w)))
 
 
 def rta_set_chain_config(ctx: int, variant: int, n_stages: int, ctas_per_sm: int):

@@ -229,6 +229,17 @@ __device__ __forceinline__ float charge(int sum, int W, int p16, float scale, in
     return __fmul_rn(__int2float_rn(num), scale);
 }
 
+// The digital-filter-style charge over the chosen window: exact 64-bit integer
+// numerator 16 * sum_k c_k s[st+k] - (sum_k c_k) * p16, one rounding to FP32, one
+// FP32 multiply (never fused). The weights come from the kernel parameters.
+__device__ __forceinline__ float filter_charge(const uint16_t* row, int st, int W, const int* wts, int csum, int p16,
+                                               float scale) {
+    int64_t acc = 0;
+    for (int k = 0; k < W; ++k) acc += int64_t(wts[k]) * row[st + k];
+    const int64_t num = 16 * acc - int64_t(csum) * p16;
+    return __fmul_rn(__ll2float_rn(num), scale);
+}
+
 // Pedestal-subtracted sample centroid of the chosen window.
 __device__ __forceinline__ float peak_time(const uint16_t* row, int st, int W, int p16, int num) {
     int sj = 0;
@@ -448,6 +459,7 @@ struct ChainSmem {
     int abort;
     int pad[31];
     float red[8];
+    int wts[RTA_MAX_W];   // weights of the digital-filter-style extractor
 };
 
 struct SlotView {
@@ -478,14 +490,15 @@ __host__ __device__ __forceinline__ int chunk_pixels(int chunk, int stage_wave_b
 template <int S, int W, int IT, int PPT>
 __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcParams& pp, const StageHdr& h,
                                                 const unsigned char* buf, const int32_t* cp16, const float* cscale,
-                                                const SlotView& v, int ct, int lane) {
+                                                const SlotView& v, int ct, int lane, const int* wts) {
     const int Sr = S ? S : h.S;
     const int Wr = W ? W : pp.W;
     // charge, outputs and thresholds of chunk pixel c with window sum `sum` starting at `wst`
     auto emit = [&](int c, int sum, int wst, const uint16_t* row, bool& hi, bool& lo) {
         const int p16 = cp16[c];
         int num;
-        const float q = charge(sum, Wr, p16, cscale[c], num);
+        float q = charge(sum, Wr, p16, cscale[c], num);
+        if (pp.filter) q = filter_charge(row, wst, Wr, wts, pp.csum, p16, cscale[c]);
         const int p = h.base + c;
         if (a.integrate_only) {
             a.q_out[h.pix_off + p] = q;
@@ -538,7 +551,7 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
                     // maximum decides; the exact search (one call site) runs for the
                     // pixels that reach t_lo or whose samples are out of its range.
                     int m = 0;
-                    bool need = a.integrate_only || !max_window6_packed<S>(row, m);
+                    bool need = a.integrate_only || pp.filter || !max_window6_packed<S>(row, m);
                     if (!need) need = __fmul_rn(__int2float_rn(16 * m - W * cp16[c]), cscale[c]) >= pp.t_lo;
                     if (need) {
                         const int key = best_key_T<S, W>(row, pp.one, pp.k128);
@@ -608,6 +621,10 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
         }
         sm.abort = 0;
         fence_mbar_init();
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < RTA_MAX_W; ++k) sm.wts[k] = a.pp.wts[k];   // constant indices: no copy of the parameters
     }
     __syncthreads();
 
@@ -771,15 +788,15 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
         const int32_t* cp16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes);
         const float* cscale = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes);
         if (pp.sliding && pp.W == 6 && h.S == 40)
-            integrate_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+            integrate_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
         else if (pp.sliding && pp.W == 6 && h.S == 30)
-            integrate_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+            integrate_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
         else if (pp.sliding && pp.W == 6 && h.S == 25)
-            integrate_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+            integrate_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
         else if (pp.sliding && pp.W == 5 && h.S == 16)
-            integrate_chunk<16, 5, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+            integrate_chunk<16, 5, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
         else
-            integrate_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane);
+            integrate_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == NST) { stage = 0; phase ^= 1u; }

@@ -90,6 +90,8 @@ struct rta_ctx {
     unsigned int* d_counters = nullptr;
     std::atomic<unsigned> next_counter{0};
     // launch configuration of the fused image kernel
+    int filter_n = 0;     // digital-filter weights (RTA_WINDOW_FILTER), 0 = none
+    int filter_w[RTA_MAX_W] = {};
     int variant = 4;      // tile shape, see chain_variant_* (the fastest on GB300 for the array cameras)
     int nstage = 2;
     int ctas_per_sm = 0;  // 0 = the variant's target, shrinking the stages to fit, else as many as fit
@@ -156,7 +158,10 @@ rta::DevArray dev_array(rta_ctx* c) {
 
 // Window and tailcut rules against every camera the array uses.
 int check_proc(rta_ctx* c, int mode, int start, int W, bool need_clean, float t_hi, float t_lo) {
-    if (mode != RTA_WINDOW_FIXED && mode != RTA_WINDOW_SLIDING) return fail(RTA_E_INVALID, "bad window mode %d", mode);
+    if (mode != RTA_WINDOW_FIXED && mode != RTA_WINDOW_SLIDING && mode != RTA_WINDOW_FILTER)
+        return fail(RTA_E_INVALID, "bad window mode %d", mode);
+    if (mode == RTA_WINDOW_FILTER && c->filter_n != W)
+        return fail(RTA_E_INVALID, "filter mode with W = %d but %d weights set", W, c->filter_n);
     if (W < 1 || W > RTA_MAX_W) return fail(RTA_E_INVALID, "window width %d outside 1..%d", W, RTA_MAX_W);
     for (int t = 0; t < c->n_tel; ++t) {
         const HostCam& h = c->cams[c->tel_cam[t]];
@@ -167,6 +172,27 @@ int check_proc(rta_ctx* c, int mode, int start, int W, bool need_clean, float t_
     if (need_clean && !(t_hi >= t_lo && t_lo > 0.f))
         return fail(RTA_E_INVALID, "tailcut thresholds need t_hi >= t_lo > 0 (got %g, %g)", t_hi, t_lo);
     return RTA_OK;
+}
+
+// Per-call processing parameters of the kernels.
+rta::ProcParams make_pp(const rta_ctx* c, int mode, int start, int W, int core_nb, float t_hi, float t_lo) {
+    rta::ProcParams pp = {};
+    pp.sliding = mode != RTA_WINDOW_FIXED;
+    pp.start = start;
+    pp.W = W;
+    pp.core_nb = core_nb ? 1 : 0;
+    pp.t_hi = t_hi;
+    pp.t_lo = t_lo;
+    pp.one = 1;
+    pp.k128 = 128;
+    if (mode == RTA_WINDOW_FILTER) {
+        pp.filter = 1;
+        for (int k = 0; k < W; ++k) {
+            pp.wts[k] = c->filter_w[k];
+            pp.csum += c->filter_w[k];
+        }
+    }
+    return pp;
 }
 
 struct ChainCfg {
@@ -480,6 +506,21 @@ int rta_set_chain_config(rta_ctx* c, int variant, int n_stages, int ctas_per_sm)
     return RTA_OK;
 }
 
+int rta_set_filter_weights(rta_ctx* c, const int32_t* w, int W) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (W < 0 || W > RTA_MAX_W || (W > 0 && !w)) return fail(RTA_E_INVALID, "filter of %d weights outside 0..%d", W, RTA_MAX_W);
+    int64_t sum = 0;
+    for (int k = 0; k < W; ++k) {
+        if (w[k] < -4096 || w[k] > 4096) return fail(RTA_E_INVALID, "filter weight %d outside -4096..4096", w[k]);
+        sum += w[k];
+    }
+    if (W > 0 && sum <= 0) return fail(RTA_E_INVALID, "filter weights must have a positive sum");
+    c->filter_n = W;
+    for (int k = 0; k < RTA_MAX_W; ++k) c->filter_w[k] = k < W ? w[k] : 0;
+    return RTA_OK;
+}
+
 int rta_get_chain_config(rta_ctx* c, int* variant, int* n_stages, int* ctas_per_sm, int* grid, size_t* smem_bytes) {
     int rc = check_ctx(c);
     if (rc) return rc;
@@ -514,7 +555,7 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
     const ChainCfg saved{c->variant, c->nstage, c->ctas_per_sm};
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -565,7 +606,7 @@ int rta_calibrate_integrate(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, 
     if (n_img == 0) return RTA_OK;
     if (!d_wave || !d_wave_off || !d_img_tel || !d_pix_off || !d_q) return fail(RTA_E_INVALID, "NULL device pointer");
     if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, 0, 0.f, 0.f, 1, 128};
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, 0, 0.f, 0.f);
     if (n_wave < 0 || n_q < 0) return fail(RTA_E_INVALID, "negative buffer length");
     return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, pp, d_q, d_t, n_q, nullptr, 1,
                      (cudaStream_t)stream, nullptr);
@@ -624,7 +665,7 @@ int rta_image_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const in
     if (n_img == 0) return RTA_OK;
     if (!d_wave || !d_wave_off || !d_img_tel || !d_out) return fail(RTA_E_INVALID, "NULL device pointer");
     if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
     if (n_wave < 0) return fail(RTA_E_INVALID, "negative buffer length");
     return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out, 0,
                      (cudaStream_t)stream, nullptr);
@@ -730,7 +771,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
             CUDA_TRY(cudaMallocHost(&s.h_sres, sizeof(rta_stereo_t) * s.evt_cap));
         }
     }
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
     for (size_t k = 0; k < chunks.size(); ++k) {
         Slot& s = c->slot[k & 1];
         const int64_t e0 = chunks[k].e0, e1 = chunks[k].e1;
@@ -836,7 +877,7 @@ int rta_graph_create(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const i
         delete g;
         return fail(RTA_E_CUDA, "stream creation failed");
     }
-    rta::ProcParams pp = {window_mode == RTA_WINDOW_SLIDING, start, W, core_needs_neighbour ? 1 : 0, t_hi, t_lo, 1, 128};
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, max_img, pp, nullptr, nullptr, 0, d_hillas, 0,

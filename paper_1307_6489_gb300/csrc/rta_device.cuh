@@ -45,6 +45,9 @@ struct ProcParams {
     // the compiler cannot see run on the FMA pipe, so part of the window search
     // leaves the integer ALU pipe, which it would otherwise saturate.
     int one, k128;
+    // digital-filter-style extractor: charge from integer weights over the window
+    int filter, csum;
+    int wts[RTA_MAX_W];
 };
 
 // ------------------------------------------------------------------ PTX helpers

@@ -31,6 +31,8 @@ def make_ctx(wl, device=0):
     for c, cam in wl.cams.items():
         ctx.register_camera(c, cam.xy, cam.nb, cam.n_samples)
     ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
+    if getattr(wl.proc, "weights", None) is not None:
+        rta.rta_set_filter_weights(ctx.handle, wl.proc.weights)
     return ctx
 
 
@@ -56,8 +58,11 @@ class Dev:
 
 def proc_args(wl):
     p = wl.proc
-    return (rta.RTA_WINDOW_SLIDING if p.sliding else rta.RTA_WINDOW_FIXED, p.start, p.W, p.t_hi, p.t_lo,
-            p.core_needs_neighbour)
+    if getattr(p, "weights", None) is not None:
+        mode = rta.RTA_WINDOW_FILTER
+    else:
+        mode = rta.RTA_WINDOW_SLIDING if p.sliding else rta.RTA_WINDOW_FIXED
+    return (mode, p.start, p.W, p.t_hi, p.t_lo, p.core_needs_neighbour)
 
 
 def hillas_rows(buf, n):
