@@ -14,6 +14,8 @@ calibration multiply); this module only marshals numpy arrays.  Row layouts:
 ``mlp.py`` holds the FP64 deep-sets network, its backward pass and Adam.
 The sky map (``skymap``) and the transient search on it (``li_ma``,
 ``disk_sum``, ``transient_maps``, ``transient_search``) are numpy here.
+``lut.py`` holds the lookup-table ("calibration matrix") energy and scaled
+width/length reconstruction.
 """
 from __future__ import annotations
 
@@ -267,3 +269,6 @@ def transient_search(dir_x, dir_y, has_dir, arrival_s, now_s, windows, radius, s
         for y, x in zip(*np.nonzero(sig >= s_min)):
             rows.append((w, int(x), int(y), int(d_on[y, x]), int(d_off[y, x]), alpha, float(sig[y, x])))
     return rows
+
+
+from .lut import bin_index, impact_distance, lut_build, lut_reconstruct  # noqa: E402
