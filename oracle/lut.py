@@ -27,6 +27,7 @@ import numpy as np
 
 N_CAMS = 16
 MIN_PIX = 3                 # images the stereo step uses: at least 3 cleaned pixels
+SKIP_FLAGS = 1 | 4          # ... and neither empty nor skipped as bad input
 CELL_FIELDS = ["n", "mean_w", "sigma_w", "mean_l", "sigma_l", "mean_e", "sigma_e"]
 EVENT_FIELDS = ["log_energy", "sigma_log_energy", "mscw", "mscl", "n_used", "flags"]
 LF_GAMMA = 1                # the event passed the scaled-width and scaled-length box
@@ -65,10 +66,11 @@ def lut_build(hrows, img_tel, evt_off, tel_cam, tel_xy, log_energy, core_xy, use
     """The cells from training events with known truth. hrows: Hillas rows
     (n_img, 12) as the oracle lays them out; log_energy (n_evt,) and core_xy
     (n_evt, 2) the events' true log10 E and impact point; use: events to take
-    (gamma showers), None = all. An image enters cell (camera type, size bin,
-    true-impact-distance bin) when it has at least MIN_PIX pixels and both
-    bins exist. Mean and population standard deviation per quantity; cells
-    with fewer than min_count images keep n and get zeros elsewhere (unused).
+    (gamma showers), None = all; events whose image range is not inside
+    [0, n_img] are skipped. An image (the rule of _image_ok) enters cell
+    (camera type, size bin, true-impact-distance bin) when both bins exist.
+    Mean and population standard deviation per quantity; cells with fewer
+    than min_count images keep n and get zeros elsewhere (unused).
     Returns (cells (N_CAMS * n_size * n_dist, 8) float32, n as int64)."""
     from . import H
     se, de = _check_edges(size_edges), _check_edges(dist_edges)
@@ -79,14 +81,16 @@ def lut_build(hrows, img_tel, evt_off, tel_cam, tel_xy, log_energy, core_xy, use
     cnt = np.zeros(n_cells, np.int64)
     s = np.zeros((n_cells, 3))          # sums of width, length, log E
     s2 = np.zeros((n_cells, 3))         # sums of squares
+    n_img, n_tel = len(hrows), len(tel_cam)
     for e in range(len(evt_off) - 1):
-        if use is not None and not use[e]:
+        a, b = int(evt_off[e]), int(evt_off[e + 1])
+        if (use is not None and not use[e]) or a < 0 or b < a or b > n_img:
             continue
-        for i in range(int(evt_off[e]), int(evt_off[e + 1])):
+        for i in range(a, b):
             h = hrows[i]
-            if h[H["n_pix"]] < MIN_PIX:
-                continue
             t = int(img_tel[i])
+            if not _image_ok(h, t, n_tel, H):
+                continue
             cam = int(tel_cam[t])
             iu = bin_index(h[H["size"]], se)
             r = impact_distance(core_xy[e][0], core_xy[e][1], tel_xy[t, 0], tel_xy[t, 1])
@@ -112,6 +116,12 @@ def lut_build(hrows, img_tel, evt_off, tel_cam, tel_xy, log_energy, core_xy, use
     return cells, cnt
 
 
+def _image_ok(h, t, n_tel, H):
+    """An image counts when its telescope id exists, it kept at least MIN_PIX
+    pixels and is neither empty nor skipped as bad input (the stereo rule)."""
+    return 0 <= t < n_tel and h[H["n_pix"]] >= MIN_PIX and not (int(h[H["flags"]]) & SKIP_FLAGS)
+
+
 def _cell_ok(cell):
     return cell[0] >= 1 and cell[2] > 0 and cell[4] > 0 and cell[6] > 0
 
@@ -121,7 +131,8 @@ def lut_reconstruct(hrows, img_tel, evt_off, n_img, tel_cam, tel_xy, srows, cell
     """Energy and scaled parameters of each event from the cells. srows: stereo
     rows (n_evt, 6) as the oracle lays them out, the core taken from there;
     cuts: (mscw_lo, mscw_hi, mscl_lo, mscl_hi), the gamma box (inclusive).
-    Per used image (at least MIN_PIX pixels, both bins exist, the cell filled):
+    Per used image (a known telescope, at least MIN_PIX pixels, neither empty
+    nor bad input, both bins exist, the cell filled):
       scaled width   (w - mean_w) / sigma_w, likewise the length;
       weight         1 / sigma_e^2, estimate mean_e.
     mscw, mscl = the scaled values summed in image order over the images, / n;
@@ -150,9 +161,9 @@ def lut_reconstruct(hrows, img_tel, evt_off, n_img, tel_cam, tel_xy, srows, cell
         n = 0
         for i in range(a, b):
             h = hrows[i]
-            if h[H["n_pix"]] < MIN_PIX:
-                continue
             t = int(img_tel[i])
+            if not _image_ok(h, t, len(tel_cam), H):
+                continue
             iu = bin_index(h[H["size"]], se)
             ir = bin_index(impact_distance(cx, cy, tel_xy[t, 0], tel_xy[t, 1]), de)
             if iu < 0 or ir < 0:

@@ -272,3 +272,22 @@ def test_tables_from_generated_gammas_separate_gammas_and_estimate_energy(shower
     assert eff_g > 0.8 and eff_p < 0.5 * eff_g
     de = out[ok & g, 0] - np.log10(te.truth[ok & g, 0])
     assert abs(np.median(de)) < 0.1 and np.std(de) < 0.35
+
+
+def test_unknown_telescopes_flagged_images_and_malformed_events_are_left_out():
+    tel_cam, tel_xy = _one_telescope_array()
+    cells, se, de = _hand_table()
+    good = hrow(500.0, 0.75, 1.5)
+    bad_flag = hrow(500.0, 0.75, 1.5)
+    bad_flag[H["flags"]] = 4
+    hrows = np.array([good, good, bad_flag, good])
+    img_tel = np.array([0, 7, 0, -1], np.int32)
+    evt_off = np.array([0, 4], np.int32)
+    out = lut.lut_reconstruct(hrows, img_tel, evt_off, 4, tel_cam, tel_xy, np.array([srow(100.0, 250.0)]), cells, se,
+                              de, (-9, 9, -9, 9))
+    assert out[0, 4] == 1 and out[0, 2] == 1.0
+    # the build skips them too, and events whose range leaves [0, n_img]
+    core = np.float32([[100.0, 250.0]] * 3)
+    cl, n = lut.lut_build(hrows, img_tel, np.array([0, 4, 2, 9], np.int32), tel_cam, tel_xy, np.float32([1, 1, 1]),
+                          core, None, se, de, 1)
+    assert n.sum() == 1
