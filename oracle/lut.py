@@ -133,7 +133,8 @@ def lut_reconstruct(hrows, img_tel, evt_off, n_img, tel_cam, tel_xy, srows, cell
     cuts: (mscw_lo, mscw_hi, mscl_lo, mscl_hi), the gamma box (inclusive).
     Per used image (a known telescope, at least MIN_PIX pixels, neither empty
     nor bad input, both bins exist, the cell filled):
-      scaled width   (w - mean_w) / sigma_w, likewise the length;
+      scaled width   (w - mean_w) * (1 / sigma_w), likewise the length (the
+                     reciprocal is a property of the cell, rounded once);
       weight         1 / sigma_e^2, estimate mean_e.
     mscw, mscl = the scaled values summed in image order over the images, / n;
     log_energy = sum(weight * estimate) / sum(weight); sigma = sqrt(1 / sum(weight)).
@@ -172,8 +173,8 @@ def lut_reconstruct(hrows, img_tel, evt_off, n_img, tel_cam, tel_xy, srows, cell
             if not _cell_ok(cell):
                 continue
             w, ln = float(np.float32(h[H["width"]])), float(np.float32(h[H["length"]]))
-            sw += (w - float(cell[1])) / float(cell[2])
-            sl += (ln - float(cell[3])) / float(cell[4])
+            sw += (w - float(cell[1])) * (1.0 / float(cell[2]))
+            sl += (ln - float(cell[3])) * (1.0 / float(cell[4]))
             se2 = float(cell[6]) * float(cell[6])
             wt = 1.0 / se2
             num += float(cell[5]) * wt
