@@ -148,6 +148,12 @@ def cpu_baseline(wl, target_s: float = 10.0):
             "gbs": reps * sub.wave_bytes / total / 1e9}
 
 
+# lookup-table binning: 32 size bins over 10..1e5 photoelectrons, 20 distance bins of 50 m
+LUT_SIZE_EDGES = np.float32(10.0) ** np.linspace(1.0, 5.0, 33, dtype=np.float32)
+LUT_DIST_EDGES = np.linspace(0.0, 1000.0, 21, dtype=np.float32)
+LUT_CUTS = (-2.0, 0.9, -2.0, 2.0)      # gamma box: mscw_lo, mscw_hi, mscl_lo, mscl_hi
+
+
 def cam_codes(wl):
     codes = np.zeros(16, np.float32)
     for c, cam in wl.cams.items():
@@ -180,7 +186,33 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
     t_fit = time.perf_counter()
     losses = tr.fit(h_tr, dtel, tw.evt_off, logE, src, gam, epochs=25, batch_events=1024, lr=2e-3, lr_end=1e-4)
     fit_s = time.perf_counter() - t_fit
-    del dwave, h_tr
+    # lookup tables (calibration matrices) from the same training gammas at their true cores
+    se_d = torch.from_numpy(LUT_SIZE_EDGES).cuda()
+    de_d = torch.from_numpy(LUT_DIST_EDGES).cuda()
+    n_cells = rta.RTA_MAX_CAMS * (len(LUT_SIZE_EDGES) - 1) * (len(LUT_DIST_EDGES) - 1)
+    acc = torch.zeros(n_cells * 8, dtype=torch.float64, device=wave.device)
+    cells = torch.zeros(n_cells * 8, dtype=torch.float32, device=wave.device)
+    core_t = torch.from_numpy(tw.truth[:, 3:5].astype(np.float32).reshape(-1)).cuda()
+    rta.rta_lut_accumulate(ctx.handle, h_tr.data_ptr(), dtel.data_ptr(), tw.n_img, devt.data_ptr(), tw.n_evt,
+                           logE.data_ptr(), core_t.data_ptr(), gam.data_ptr(), se_d.data_ptr(),
+                           len(LUT_SIZE_EDGES) - 1, de_d.data_ptr(), len(LUT_DIST_EDGES) - 1, acc.data_ptr(), sp)
+    rta.rta_lut_finalize(ctx.handle, acc.data_ptr(), n_cells, 10, cells.data_ptr(), sp)
+    lookup = torch.zeros(n_cells * rta.LUT_LOOKUP_BYTES // 4, dtype=torch.float32, device=wave.device)
+    rta.rta_lut_prepare(ctx.handle, cells.data_ptr(), n_cells, lookup.data_ptr(), sp)
+    # protons of the training set stay out of the tables: their pass fraction is out of sample
+    st_tr = torch.zeros(tw.n_evt * 8, dtype=torch.float32, device=wave.device)
+    lev_tr = torch.zeros(tw.n_evt * 8, dtype=torch.float32, device=wave.device)
+    rta.rta_stereo(ctx.handle, h_tr.data_ptr(), dtel.data_ptr(), tw.n_img, devt.data_ptr(), tw.n_evt,
+                   st_tr.data_ptr(), sp)
+    rta.rta_lut_reconstruct(ctx.handle, h_tr.data_ptr(), dtel.data_ptr(), tw.n_img, devt.data_ptr(), tw.n_evt,
+                            st_tr.data_ptr(), lookup.data_ptr(), se_d.data_ptr(), len(LUT_SIZE_EDGES) - 1,
+                            de_d.data_ptr(), len(LUT_DIST_EDGES) - 1, LUT_CUTS, lev_tr.data_ptr(), sp)
+    torch.cuda.synchronize()
+    lt = rta.lut_events_to_numpy(lev_tr.cpu().numpy())
+    ok_tr = (lt["flags"] & (rta.RTA_LF_NO_CORE | rta.RTA_LF_NO_IMAGE | rta.RTA_LF_MALFORMED)) == 0
+    prot = tw.truth[:, 5] != 0
+    proton_pass = float(np.mean((lt["flags"][ok_tr & prot] & rta.RTA_LF_GAMMA) != 0)) if (ok_tr & prot).any() else None
+    del dwave, h_tr, st_tr, lev_tr
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     # timed: image kernel + learned reconstruction on the bundle
@@ -220,6 +252,48 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
 
     infer_nofb_ms = infer_ms(1e30)
     infer_full_ms = infer_ms(0.5)
+
+    # the non-learned path: image kernel + geometric stereo + lookup tables
+    lev = torch.zeros(wl.n_evt * 8, dtype=torch.float32, device=wave.device)
+    lut_args = (lookup.data_ptr(), se_d.data_ptr(), len(LUT_SIZE_EDGES) - 1, de_d.data_ptr(),
+                len(LUT_DIST_EDGES) - 1, LUT_CUTS, lev.data_ptr(), sp)
+
+    def lut_step():
+        rta.rta_image_chain(h, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img,
+                            *proc, hil.data_ptr(), sp)
+        rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), sp)
+        rta.rta_lut_reconstruct(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt,
+                                ste.data_ptr(), *lut_args)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    lut_path_ms = timed(lut_step)
+    lut_ms = timed(lambda: rta.rta_lut_reconstruct(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img,
+                                                   evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), *lut_args))
+    stereo_ms = timed(lambda: rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(),
+                                             wl.n_evt, ste.data_ptr(), sp))
+    ctx.check(sp)
+    le = rta.lut_events_to_numpy(lev.cpu().numpy())
+    ok = (le["flags"] & (rta.RTA_LF_NO_CORE | rta.RTA_LF_NO_IMAGE | rta.RTA_LF_MALFORMED)) == 0
+    g_b = wl.truth[:, 5] == 0
+    d_le = le["log_energy"][ok & g_b] - np.log10(wl.truth[ok & g_b, 0])
+    lut_out = {"ms_per_step": lut_path_ms, "events_per_s": wl.n_evt / (lut_path_ms / 1e3), "lut_ms": lut_ms,
+               "stereo_ms": stereo_ms, "cuts": list(LUT_CUTS), "filled_cells": int((cells.view(torch.int32)[0::8] >= 10).sum()),
+               "accuracy_on_bundle": {"with_energy_frac": float(np.mean(ok[g_b])) if g_b.any() else None,
+                                      "energy_bias": float(np.mean(d_le)) if len(d_le) else None,
+                                      "energy_res": float(np.std(d_le)) if len(d_le) else None,
+                                      "gamma_pass": float(np.mean((le["flags"][ok & g_b] & rta.RTA_LF_GAMMA) != 0))
+                                      if (ok & g_b).any() else None},
+               "proton_pass_train_set": proton_pass}
     # accuracy on the bundle (gamma showers) against the geometric result of the same images
     rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), sp)
     torch.cuda.synchronize()
@@ -227,7 +301,7 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
     out = {"ms_per_step": sur_ms, "events_per_s": wl.n_evt / (sur_ms / 1e3),
            "infer_ms": infer_full_ms, "infer_without_fallback_ms": infer_nofb_ms, "train_events": n_train,
            "train_steps": len(losses), "train_s": fit_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
-           "accuracy_on_bundle": res}
+           "accuracy_on_bundle": res, "lookup_tables": lut_out}
     return out, tr
 
 

@@ -357,6 +357,86 @@ int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const in
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Lookup tables: the calibration matrices of the real-time reconstruction  */
+/* (Sec. 4.1: energy and gamma/hadron separation), a non-learned second     */
+/* path beside the surrogate                                               */
+/* ---------------------------------------------------------------------- */
+/* A table has RTA_MAX_CAMS * n_size * n_dist cells in device memory, cell
+ * (camera id * n_size + size bin) * n_dist + distance bin. Size bin i holds
+ * size_edges[i] <= size < size_edges[i + 1] (photoelectrons); distance bin j
+ * holds dist_edges[j] <= R < dist_edges[j + 1], R the ground distance (m) from
+ * the telescope to the shower core, sqrt(dx * dx + dy * dy) in FP32 with one
+ * rounding per operation. Both decisions are FP32 comparisons. Edge arrays
+ * (n + 1 floats, device memory, 1 <= n <= RTA_LUT_MAX_BINS) must increase
+ * strictly; unsorted edges give unspecified bins but no access outside the
+ * table. An image counts when its telescope id exists, it has >= 3 cleaned
+ * pixels and is neither RTA_HF_EMPTY nor RTA_HF_BAD_INPUT (the stereo rule). */
+#define RTA_MAX_CAMS 16
+#define RTA_LUT_MAX_BINS 64
+typedef struct rta_lut_cell_t {
+    int32_t n;             /* training images that fell in the cell */
+    float mean_w, sigma_w; /* image width (deg): mean and population standard deviation */
+    float mean_l, sigma_l; /* image length (deg) */
+    float mean_e, sigma_e; /* log10(E / TeV) */
+    float reserved;
+} rta_lut_cell_t;          /* a cell is used when n >= 1 and all three sigmas are > 0 */
+
+typedef struct rta_lut_event_t {
+    float log_energy;       /* sum(mean_e / sigma_e^2) / sum(1 / sigma_e^2) over the used images */
+    float sigma_log_energy; /* sqrt(1 / sum(1 / sigma_e^2)) */
+    float mscw, mscl;       /* means over the used images of (width - mean_w) / sigma_w, likewise length */
+    int32_t n_used;         /* images in a used cell (-1: malformed image range) */
+    uint32_t flags;         /* RTA_LF_* */
+    float reserved[2];
+} rta_lut_event_t;
+#define RTA_LF_GAMMA 1u     /* mscw and mscl inside the cut box (inclusive) */
+#define RTA_LF_NO_CORE 2u   /* the stereo row is RTA_SF_INVALID: no impact distances, fields 0 */
+#define RTA_LF_NO_IMAGE 4u  /* no image fell in a used cell: fields 0 */
+#define RTA_LF_MALFORMED 8u /* the image range is outside [0, n_img]; also sets a device status bit */
+
+/* Training sums for the tables. d_acc: RTA_MAX_CAMS * n_size * n_dist rows of
+ * 8 doubles (count, sum w, sum w^2, sum l, sum l^2, sum e, sum e^2, unused),
+ * zeroed by the caller; this call adds to them, so several batches accumulate.
+ * The distance is taken from the TRUE impact point. d_log_energy[n_evt]: true
+ * log10(E / TeV); d_core_xy[2 n_evt]: true impact point (m); d_use[n_evt]:
+ * events to take (gamma showers), NULL = all. Events with a malformed image
+ * range are skipped. FP64 atomic sums: the order of additions varies between
+ * runs, the sums by a few units in their last place. Asynchronous on stream.
+ * Alignment (RTA_E_ALIGN otherwise): d_hillas, d_stereo, d_cells, d_lookup and
+ * d_out on 16 bytes, d_acc on 8. RTA_E_INVALID for NULL pointers or bin counts outside
+ * 1..RTA_LUT_MAX_BINS. */
+int rta_lut_accumulate(rta_ctx* ctx, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                       const int32_t* d_evt_off, int64_t n_evt, const float* d_log_energy, const float* d_core_xy,
+                       const uint8_t* d_use, const float* d_size_edges, int n_size, const float* d_dist_edges,
+                       int n_dist, double* d_acc, void* stream);
+/* Cells from the sums: mean = S / n, sigma = sqrt(max(S2 / n - mean^2, 0)) in
+ * FP64, rounded once to FP32; cells with n < min_count (min_count >= 1) keep n
+ * and are zero elsewhere, i.e. unused. n_cells = RTA_MAX_CAMS * n_size * n_dist. */
+int rta_lut_finalize(rta_ctx* ctx, const double* d_acc, int64_t n_cells, int min_count, rta_lut_cell_t* d_cells,
+                     void* stream);
+/* The lookup form of a table, made once per table: per cell, in FP64 with one
+ * rounding per operation, 1 / sigma_w, 1 / sigma_l, the energy weight
+ * w_e = 1 / (sigma_e * sigma_e) and w_e * mean_e, and the FP32 means; unused
+ * cells get zeros. d_lookup: n_cells * RTA_LUT_LOOKUP_BYTES bytes, 16-byte
+ * aligned, device memory; its layout is private to the library. */
+#define RTA_LUT_LOOKUP_BYTES 64
+int rta_lut_prepare(rta_ctx* ctx, const rta_lut_cell_t* d_cells, int64_t n_cells, void* d_lookup, void* stream);
+/* Energy and scaled width and length of each event from a table in lookup
+ * form and the event's stereo row (the reconstructed core gives the
+ * distances). Per used image: (w - mean_w) * (1 / sigma_w), likewise the
+ * length, the weight w_e and w_e * mean_e, in FP64 with one rounding per
+ * operation; the four are summed in image order and divided once per event
+ * (the order and the roundings are fixed, so results are reproducible bit for
+ * bit). Gamma-like (RTA_LF_GAMMA): mscw_lo <= mscw <= mscw_hi and
+ * mscl_lo <= mscl <= mscl_hi, compared in FP64. d_out: n_evt rows.
+ * Asynchronous on stream. */
+int rta_lut_reconstruct(rta_ctx* ctx, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                        const int32_t* d_evt_off, int64_t n_evt, const rta_stereo_t* d_stereo,
+                        const void* d_lookup, const float* d_size_edges, int n_size,
+                        const float* d_dist_edges, int n_dist, float mscw_lo, float mscw_hi, float mscl_lo,
+                        float mscl_hi, rta_lut_event_t* d_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: a stream of bundles with continuous batching, and the sky map   */
 /* (Sec. 4.2 event-by-event RTA; Sec. 2.1 30 s alert latency and           */
 /* transient search on several timescales)                                 */

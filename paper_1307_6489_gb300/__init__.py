@@ -111,6 +111,10 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_transient_search": ([P, i64, P, i32, i32, ctypes.c_double, P, i32, P], i32),
         "rta_significance_map": ([P, i64, Window, i32, P, P, P], i32),
         "rta_selftest_wait_timeout": ([P, i32, P, P], i32),
+        "rta_lut_accumulate": ([P, P, P, i64, P, i64, P, P, P, P, i32, P, i32, P, P], i32),
+        "rta_lut_finalize": ([P, P, i64, i32, P, P], i32),
+        "rta_lut_prepare": ([P, P, i64, P, P], i32),
+        "rta_lut_reconstruct": ([P, P, P, i64, P, i64, P, P, P, i32, P, i32, f32, f32, f32, f32, P, P], i32),
         "rta_image_chain_noalloc": ([P, i32, P, P, i32, P, P, i64, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32,
                                      P, P, P], i32),
     }
@@ -359,6 +363,70 @@ def events_to_numpy(raw: np.ndarray) -> dict:
     return dict(log_energy=f[:, 0].copy(), dir_x=f[:, 1].copy(), dir_y=f[:, 2].copy(), gammaness=f[:, 3].copy(),
                 n_used=i[:, 4].copy(), flags=i[:, 5].view(np.uint32).copy(), base_x=f[:, 6].copy(),
                 base_y=f[:, 7].copy())
+
+
+RTA_MAX_CAMS = 16
+RTA_LUT_MAX_BINS = 64
+RTA_LF_GAMMA = 1
+RTA_LF_NO_CORE = 2
+RTA_LF_NO_IMAGE = 4
+RTA_LF_MALFORMED = 8
+LUT_CELL_BYTES = 32
+LUT_LOOKUP_BYTES = 64
+LUT_EVENT_BYTES = 32
+LUT_CELL_FIELDS = ["n", "mean_w", "sigma_w", "mean_l", "sigma_l", "mean_e", "sigma_e"]
+
+
+def rta_lut_accumulate(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_log_energy, d_core_xy, d_use,
+                       d_size_edges, n_size, d_dist_edges, n_dist, d_acc, stream=0):
+    _check(load().rta_lut_accumulate(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_log_energy, d_core_xy, d_use,
+                                     d_size_edges, n_size, d_dist_edges, n_dist, d_acc, stream))
+
+
+def rta_lut_finalize(ctx, d_acc, n_cells, min_count, d_cells, stream=0):
+    _check(load().rta_lut_finalize(ctx, d_acc, n_cells, min_count, d_cells, stream))
+
+
+def rta_lut_prepare(ctx, d_cells, n_cells, d_lookup, stream=0):
+    """The lookup form of a table (n_cells * LUT_LOOKUP_BYTES bytes at d_lookup)."""
+    _check(load().rta_lut_prepare(ctx, d_cells, n_cells, d_lookup, stream))
+
+
+def rta_lut_reconstruct(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_stereo, d_lookup, d_size_edges, n_size,
+                        d_dist_edges, n_dist, cuts, d_out, stream=0):
+    """cuts = (mscw_lo, mscw_hi, mscl_lo, mscl_hi); d_lookup from rta_lut_prepare."""
+    c = [float(v) for v in cuts]
+    _check(load().rta_lut_reconstruct(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_stereo, d_lookup,
+                                      d_size_edges, n_size, d_dist_edges, n_dist, c[0], c[1], c[2], c[3], d_out,
+                                      stream))
+
+
+def lut_cells_to_numpy(raw: np.ndarray) -> dict:
+    """Decode rows of rta_lut_cell_t (n*32 bytes)."""
+    raw = np.ascontiguousarray(raw).view(np.uint8).reshape(-1, LUT_CELL_BYTES)
+    f = raw.view(np.float32).reshape(-1, 8)
+    out = {k: f[:, j].copy() for j, k in enumerate(LUT_CELL_FIELDS) if j}
+    out["n"] = raw.view(np.int32).reshape(-1, 8)[:, 0].copy()
+    return out
+
+
+def lut_cells_from_numpy(n, mean_w, sigma_w, mean_l, sigma_l, mean_e, sigma_e) -> np.ndarray:
+    """Pack per-cell columns into rta_lut_cell_t rows (float32 array of n_cells x 8)."""
+    n = np.asarray(n)
+    out = np.zeros((len(n), 8), np.float32)
+    out.view(np.int32)[:, 0] = n.astype(np.int32)
+    for j, v in enumerate([mean_w, sigma_w, mean_l, sigma_l, mean_e, sigma_e]):
+        out[:, 1 + j] = np.asarray(v, np.float32)
+    return out
+
+
+def lut_events_to_numpy(raw: np.ndarray) -> dict:
+    """Decode rows of rta_lut_event_t (n*32 bytes)."""
+    raw = np.ascontiguousarray(raw).view(np.uint8).reshape(-1, LUT_EVENT_BYTES)
+    f = raw.view(np.float32).reshape(-1, 8)
+    i = raw.view(np.int32).reshape(-1, 8)
+    return dict(log_energy=f[:, 0].copy(), sigma_log_energy=f[:, 1].copy(), mscw=f[:, 2].copy(), mscl=f[:, 3].copy(),
+                n_used=i[:, 4].copy(), flags=i[:, 5].view(np.uint32).copy())
 
 
 # packed parameter layout of the surrogate (name, shape), row-major

@@ -917,3 +917,115 @@ int rta_graph_destroy(rta_graph* g) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Lookup tables (k_lut.cu)
+// ---------------------------------------------------------------------------
+namespace {
+
+int check_lut_axes(const float* se, int n_size, const float* de, int n_dist) {
+    if (!se || !de) return fail(RTA_E_INVALID, "NULL edge array");
+    if (n_size < 1 || n_size > RTA_LUT_MAX_BINS || n_dist < 1 || n_dist > RTA_LUT_MAX_BINS)
+        return fail(RTA_E_INVALID, "bins per axis must be 1..%d (got %d, %d)", RTA_LUT_MAX_BINS, n_size, n_dist);
+    return RTA_OK;
+}
+
+rta::LutArgs lut_args(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
+                      const int32_t* d_evt_off, int64_t n_evt, const float* se, int n_size, const float* de,
+                      int n_dist) {
+    rta::LutArgs a{};
+    a.arr = dev_array(c);
+    a.h = d_h;
+    a.img_tel = d_img_tel;
+    a.n_img = n_img;
+    a.evt_off = d_evt_off;
+    a.n_evt = n_evt;
+    a.size_edges = se;
+    a.n_size = n_size;
+    a.dist_edges = de;
+    a.n_dist = n_dist;
+    a.status = c->d_status;
+    return a;
+}
+
+}  // namespace
+
+int rta_lut_accumulate(rta_ctx* c, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                       const int32_t* d_evt_off, int64_t n_evt, const float* d_log_energy, const float* d_core_xy,
+                       const uint8_t* d_use, const float* d_size_edges, int n_size, const float* d_dist_edges,
+                       int n_dist, double* d_acc, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_evt, "n_evt")) || (rc = check_n(n_img, "n_img"))) return rc;
+    if ((rc = check_lut_axes(d_size_edges, n_size, d_dist_edges, n_dist))) return rc;
+    if (n_evt == 0) return RTA_OK;
+    if (!d_evt_off || !d_log_energy || !d_core_xy || !d_acc || (n_img > 0 && (!d_hillas || !d_img_tel)))
+        return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_hillas) || (reinterpret_cast<uintptr_t>(d_acc) & 7u))
+        return fail(RTA_E_ALIGN, "d_hillas must be 16-byte and d_acc 8-byte aligned");
+    rta::LutArgs a = lut_args(c, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_size_edges, n_size, d_dist_edges,
+                              n_dist);
+    a.log_e = d_log_energy;
+    a.core_xy = d_core_xy;
+    a.use = d_use;
+    a.acc = d_acc;
+    const int64_t g = std::min<int64_t>((n_evt + 255) / 256, int64_t(c->n_sm) * 8);
+    CUDA_TRY(rta::launch_lut_accumulate(a, int(g), (cudaStream_t)stream));
+    return RTA_OK;
+}
+
+int rta_lut_finalize(rta_ctx* c, const double* d_acc, int64_t n_cells, int min_count, rta_lut_cell_t* d_cells,
+                     void* stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n_cells < 0 || n_cells > int64_t(RTA_MAX_CAMS) * RTA_LUT_MAX_BINS * RTA_LUT_MAX_BINS)
+        return fail(RTA_E_INVALID, "n_cells = %lld out of range", (long long)n_cells);
+    if (min_count < 1) return fail(RTA_E_INVALID, "min_count must be >= 1");
+    if (n_cells == 0) return RTA_OK;
+    if (!d_acc || !d_cells) return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_cells) || (reinterpret_cast<uintptr_t>(d_acc) & 7u))
+        return fail(RTA_E_ALIGN, "d_cells must be 16-byte and d_acc 8-byte aligned");
+    const int64_t g = std::min<int64_t>((n_cells + 255) / 256, int64_t(c->n_sm) * 8);
+    CUDA_TRY(rta::launch_lut_finalize(d_acc, n_cells, min_count, d_cells, int(g), (cudaStream_t)stream));
+    return RTA_OK;
+}
+
+int rta_lut_prepare(rta_ctx* c, const rta_lut_cell_t* d_cells, int64_t n_cells, void* d_lookup, void* stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n_cells < 0 || n_cells > int64_t(RTA_MAX_CAMS) * RTA_LUT_MAX_BINS * RTA_LUT_MAX_BINS)
+        return fail(RTA_E_INVALID, "n_cells = %lld out of range", (long long)n_cells);
+    if (n_cells == 0) return RTA_OK;
+    if (!d_cells || !d_lookup) return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_cells) || !aligned16(d_lookup)) return fail(RTA_E_ALIGN, "d_cells and d_lookup must be 16-byte aligned");
+    const int64_t g = std::min<int64_t>((n_cells + 255) / 256, int64_t(c->n_sm) * 8);
+    CUDA_TRY(rta::launch_lut_prepare(d_cells, n_cells, d_lookup, int(g), (cudaStream_t)stream));
+    return RTA_OK;
+}
+
+int rta_lut_reconstruct(rta_ctx* c, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
+                        const int32_t* d_evt_off, int64_t n_evt, const rta_stereo_t* d_stereo,
+                        const void* d_lookup, const float* d_size_edges, int n_size,
+                        const float* d_dist_edges, int n_dist, float mscw_lo, float mscw_hi, float mscl_lo,
+                        float mscl_hi, rta_lut_event_t* d_out, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_evt, "n_evt")) || (rc = check_n(n_img, "n_img"))) return rc;
+    if ((rc = check_lut_axes(d_size_edges, n_size, d_dist_edges, n_dist))) return rc;
+    if (n_evt == 0) return RTA_OK;
+    if (!d_evt_off || !d_stereo || !d_lookup || !d_out || (n_img > 0 && (!d_hillas || !d_img_tel)))
+        return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_hillas) || !aligned16(d_stereo) || !aligned16(d_lookup) || !aligned16(d_out))
+        return fail(RTA_E_ALIGN, "d_hillas, d_stereo, d_lookup and d_out must be 16-byte aligned");
+    rta::LutArgs a = lut_args(c, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_size_edges, n_size, d_dist_edges,
+                              n_dist);
+    a.stereo = d_stereo;
+    a.lookup = static_cast<const unsigned char*>(d_lookup);
+    a.cut[0] = mscw_lo;
+    a.cut[1] = mscw_hi;
+    a.cut[2] = mscl_lo;
+    a.cut[3] = mscl_hi;
+    a.out = d_out;
+    a.events_per_block = rta::lut_events_per_block(n_evt, c->n_sm);
+    const int64_t g = std::min<int64_t>((n_evt + a.events_per_block - 1) / a.events_per_block, int64_t(c->n_sm) * 16);
+    CUDA_TRY(rta::launch_lut_reconstruct(a, int(g), (cudaStream_t)stream));
+    return RTA_OK;
+}

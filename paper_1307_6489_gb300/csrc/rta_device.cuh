@@ -9,7 +9,6 @@
 
 #include "rta.h"
 
-#define RTA_MAX_CAMS 16
 #define RTA_MAX_PIX 4096
 #define RTA_MAX_SAMPLES 128
 #define RTA_MAX_W 16

@@ -106,6 +106,35 @@ struct TransientArgs {
 cudaError_t launch_transient(const TransientArgs& t, cudaStream_t s);
 cudaError_t launch_skymap_sum(const unsigned int* slabs, unsigned long long use, unsigned int* out, cudaStream_t s);
 cudaError_t launch_stereo_to_events(const rta_stereo_t* st, int64_t n_evt, rta_event_t* ev, cudaStream_t s);
+// Lookup-table reconstruction and its training sums (k_lut.cu).
+struct LutArgs {
+    DevArray arr;
+    const rta_hillas_t* h;
+    const int32_t* img_tel;
+    int64_t n_img;
+    const int32_t* evt_off;
+    int64_t n_evt;
+    const rta_stereo_t* stereo;     // reconstruction: the cores
+    const float* log_e;             // training: true log10 E per event
+    const float* core_xy;           // training: true impact point per event
+    const uint8_t* use;             // training: events to take (nullable)
+    const float* size_edges;
+    int n_size;
+    const float* dist_edges;
+    int n_dist;
+    const unsigned char* lookup;    // reconstruction: the table in lookup form (RTA_LUT_LOOKUP_BYTES a cell)
+    double* acc;                    // training sums, 8 per cell
+    float cut[4];                   // mscw_lo, mscw_hi, mscl_lo, mscl_hi
+    rta_lut_event_t* out;
+    unsigned int* status;
+    int events_per_block;
+};
+int lut_events_per_block(int64_t n_evt, int n_sm);
+cudaError_t launch_lut_reconstruct(const LutArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_lut_accumulate(const LutArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_lut_finalize(const double* acc, int64_t n_cells, int min_count, rta_lut_cell_t* cells, int grid,
+                                cudaStream_t s);
+cudaError_t launch_lut_prepare(const rta_lut_cell_t* cells, int64_t n_cells, void* lookup, int grid, cudaStream_t s);
 // grow a model's workspace ahead of use (rta_surrogate.cu)
 int surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt);
 // context access for the surrogate (rta_api.cu)
