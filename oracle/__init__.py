@@ -57,11 +57,12 @@ def _L():
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_float
         lib.or_integrate.argtypes = [P, i32, i32, P, P, i32, i32, i32, P, P, P, P, P]
+        lib.or_integrate_nbpeak.argtypes = [P, i32, i32, P, P, P, i32, i32, P, P, P]
         lib.or_clean.argtypes = [i32, P, P, i32, f32, f32, i32, P]
         lib.or_hillas.argtypes = [i32, P, P, P, P, P]
         lib.or_stereo.argtypes = [i32, P, P, P]
         lib.or_reconstruct.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, i32, f32, f32, i32, P, P, P, P,
-                                       P, i64, P, P, P, i32, P]
+                                       P, i64, P, P, P, i32, P, i32]
         _lib = lib
     return _lib
 
@@ -94,6 +95,22 @@ def integrate(wave, p16, scale, sliding: bool, start: int, W: int, weights=None)
                          _p(t), _p(ws), _p(wsum)) != 0:
         raise ValueError("or_integrate: bad arguments")
     return q, t, ws, wsum
+
+
+def integrate_nbpeak(wave, p16, scale, nb, W: int):
+    """Neighbour-peak window: wave (P, S) uint16, nb (P, K) int16 neighbour ids
+    (-1 = none) -> (q float32, t float64, chosen window start int32)."""
+    wave = np.ascontiguousarray(wave, np.uint16)
+    P, Sn = wave.shape
+    nb = np.ascontiguousarray(nb, np.int16).reshape(P, -1)
+    q = np.zeros(P, np.float32)
+    t = np.zeros(P, np.float64)
+    ws = np.zeros(P, np.int32)
+    if _L().or_integrate_nbpeak(_p(wave), P, Sn, _p(np.ascontiguousarray(p16, np.int32)),
+                                _p(np.ascontiguousarray(scale, np.float32)), _p(nb), nb.shape[1], int(W), _p(q),
+                                _p(t), _p(ws)) != 0:
+        raise ValueError("or_integrate_nbpeak: bad arguments")
+    return q, t, ws
 
 
 def clean(q, nb, t_hi: float, t_lo: float, core_needs_neighbour: bool):
@@ -183,7 +200,8 @@ def reconstruct(wl, threads: int | None = None, do_stereo: bool = True, per_pixe
                             ctypes.cast(cam_nb, ctypes.c_void_p), int(pr.sliding), int(pr.start), int(pr.W),
                             float(pr.t_hi), float(pr.t_lo), int(pr.core_needs_neighbour), _p(hil),
                             _p(wl.pix_off) if per_pixel else None, _p(q), _p(t), _p(mk), n_evt if do_stereo else 0,
-                            _p(wl.evt_off), _p(tel_xy), _p(ste), int(threads), _p(wts))
+                            _p(wl.evt_off), _p(tel_xy), _p(ste), int(threads), _p(wts),
+                            int(bool(getattr(pr, "nbpeak", False))))
     if st != 0:
         raise RuntimeError("or_reconstruct failed")
     return dict(hillas=hil, stereo=ste, q=q, t=t, mask=mk)

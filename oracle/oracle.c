@@ -21,6 +21,9 @@
  *              exact integer and the calibration scale is 1/(16 gain f_W). The
  *              one floating-point step is a single FP32 multiply of that
  *              integer by the FP32 scale; it is done in FP32 here on purpose.
+ *   nbpeak     the neighbour-peak window: a pixel integrates its own samples
+ *              in the sliding window of the brightest pixel (largest charge,
+ *              then earliest start) of its closed neighbourhood.
  *   clean      two-threshold tailcut: core pixels q >= t_hi (optionally with a
  *              neighbour also >= t_hi), boundary pixels q >= t_lo next to a core
  *              pixel; one pass.
@@ -104,6 +107,53 @@ int or_integrate(const uint16_t* wave, int P, int S, const int32_t* p16, const f
         if (wstart) wstart[p] = best_s;
         if (wsum) wsum[p] = best;
     }
+    return 0;
+}
+
+/*
+ * Neighbour-peak window (an extractor of the Sec. 5 family; the paper names
+ * the family, not a definition). Step 1: every pixel's own sliding window
+ * (first maximal W-sum) and the charge q0 it gives, with the same FP32
+ * multiply as above. Step 2: pixel p integrates its OWN samples in the window
+ * of the brightest pixel of its closed neighbourhood {p} and nb[p*K + j]: the
+ * largest q0, and among equal q0 the earliest window start. Charge and time
+ * then follow the flat-window rules above at that start. wstart receives the
+ * chosen start.
+ */
+int or_integrate_nbpeak(const uint16_t* wave, int P, int S, const int32_t* p16, const float* scale,
+                        const int16_t* nb, int K, int W, float* q, double* t, int32_t* wstart) {
+    if (P < 0 || S <= 0 || W <= 0 || W > S || K < 0) return -1;
+    float* q0 = (float*)malloc(sizeof(float) * (size_t)(P + 1));
+    int32_t* s0 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P + 1));
+    if (!q0 || !s0) { free(q0); free(s0); return -1; }
+    /* step 1: the sliding window of every pixel */
+    if (or_integrate(wave, P, S, p16, scale, 1, 0, W, NULL, q0, NULL, s0, NULL) != 0) {
+        free(q0); free(s0); return -1;
+    }
+    /* step 2: the window of the brightest pixel in the closed neighbourhood */
+    for (int p = 0; p < P; ++p) {
+        int b = p;
+        for (int j = 0; j < K; ++j) {
+            int n = nb[(size_t)p * K + j];
+            if (n < 0 || n >= P) continue;
+            if (q0[n] > q0[b] || (q0[n] == q0[b] && s0[n] < s0[b])) b = n;
+        }
+        const int st = s0[b];
+        const uint16_t* w = wave + (size_t)p * S;
+        int64_t sum = 0;
+        for (int k = st; k < st + W; ++k) sum += w[k];
+        int64_t num = 16 * sum - (int64_t)W * p16[p];
+        volatile float fnum = (float)num;
+        volatile float qq = fnum * scale[p];
+        q[p] = qq;
+        if (t) {
+            int64_t numt = 0;
+            for (int j = 0; j < W; ++j) numt += (int64_t)j * (16 * (int64_t)w[st + j] - p16[p]);
+            t[p] = num > 0 ? (double)st + (double)numt / (double)num : (double)st + 0.5 * (W - 1);
+        }
+        if (wstart) wstart[p] = st;
+    }
+    free(q0); free(s0);
     return 0;
 }
 
@@ -298,6 +348,7 @@ typedef struct {
     const int16_t* const* cam_nb;
     int sliding, start, W, core_nb;
     const int32_t* weights;   /* NULL: flat window sum */
+    int nbpeak;               /* 1: neighbour-peak window (sliding ignored) */
     float t_hi, t_lo;
     /* outputs */
     double* hillas;                 /* n_img * OH_N */
@@ -328,8 +379,12 @@ static void* bundle_worker(void* arg) {
         int tel = J->img_tel[i], cam = J->tel_cam[tel];
         int P = J->cam_info[3 * cam], S = J->cam_info[3 * cam + 1], K = J->cam_info[3 * cam + 2];
         int64_t row = J->tel_pix_off[tel];
-        if (or_integrate(J->wave + J->wave_off[i], P, S, J->p16 + row, J->scale + row, J->sliding, J->start, J->W,
-                         J->weights, q, t, NULL, NULL) != 0) {
+        const int rc = J->nbpeak
+            ? or_integrate_nbpeak(J->wave + J->wave_off[i], P, S, J->p16 + row, J->scale + row, J->cam_nb[cam], K,
+                                  J->W, q, t, NULL)
+            : or_integrate(J->wave + J->wave_off[i], P, S, J->p16 + row, J->scale + row, J->sliding, J->start, J->W,
+                           J->weights, q, t, NULL, NULL);
+        if (rc != 0) {
             J->status = -1;
             continue;
         }
@@ -385,12 +440,13 @@ int or_reconstruct(int64_t n_img, const uint16_t* wave, const int64_t* wave_off,
                    const int32_t* cam_info, const float* const* cam_xy, const int16_t* const* cam_nb, int sliding,
                    int start, int W, float t_hi, float t_lo, int core_nb, double* hillas, const int64_t* pix_off,
                    float* q_out, double* t_out, uint8_t* mask_out, int64_t n_evt, const int32_t* evt_off,
-                   const float* tel_xy, double* stereo, int n_threads, const int32_t* weights) {
+                   const float* tel_xy, double* stereo, int n_threads, const int32_t* weights, int nbpeak) {
     bundle_job_t J;
     memset(&J, 0, sizeof J);
     J.n_img = n_img; J.wave = wave; J.wave_off = wave_off; J.img_tel = img_tel; J.tel_cam = tel_cam;
     J.tel_pix_off = tel_pix_off; J.p16 = p16; J.scale = scale; J.cam_info = cam_info; J.cam_xy = cam_xy;
     J.cam_nb = cam_nb; J.sliding = sliding; J.start = start; J.W = W; J.weights = weights; J.core_nb = core_nb;
+    J.nbpeak = nbpeak;
     J.t_hi = t_hi;
     J.t_lo = t_lo; J.hillas = hillas; J.pix_off = pix_off; J.q_out = q_out; J.t_out = t_out;
     J.mask_out = mask_out; J.n_evt = n_evt; J.evt_off = evt_off; J.tel_xy = tel_xy; J.stereo = stereo;

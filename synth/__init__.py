@@ -141,7 +141,8 @@ def window_fraction(sliding: bool, start: int, W: int) -> float:
 class Processing:
     """Per-workload processing parameters (window and tailcut). weights: integer
     weights of the digital-filter-style charge over the sliding window (None:
-    the flat window sum)."""
+    the flat window sum). nbpeak: the neighbour-peak window (a pixel takes the
+    window of the brightest pixel of its closed neighbourhood)."""
     sliding: bool
     start: int
     W: int
@@ -149,6 +150,7 @@ class Processing:
     t_lo: float
     core_needs_neighbour: bool
     weights: tuple = None
+    nbpeak: bool = False
 
 
 PRESET_PROCESSING = {
