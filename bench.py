@@ -596,6 +596,25 @@ def main():
         filt_ms = f0.elapsed_time(f1) / args.steps
         ctx.check(sp)
 
+    # ---------------- the neighbour-peak window on the same bundle (image kernel alone; reads each image twice)
+    nbp_ms = None
+    if proc[0] != rta.RTA_WINDOW_FIXED:
+        nproc = (rta.RTA_WINDOW_NEIGHBOUR,) + tuple(proc[1:])
+        nhil = torch.empty_like(hil)
+        for _ in range(3):
+            rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *nproc,
+                                nhil.data_ptr(), sp)
+        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0.record(stream)
+        for _ in range(args.steps):
+            rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *nproc,
+                                nhil.data_ptr(), sp)
+        n1.record(stream)
+        torch.cuda.synchronize(dev)
+        nbp_ms = n0.elapsed_time(n1) / args.steps
+        ctx.check(sp)
+        del nhil
+
     # ---------------- roofline of the dominant kernel (fused image kernel)
     hbm_peak, peak_kind = peaks()
     alg_bytes = wl.wave_bytes + wl.n_img * HILLAS_BYTES
@@ -667,7 +686,10 @@ def main():
             "kernel_ms": {"image_chain": chain_avg, "stereo": statistics.mean(stereo_ms)},
             "extractors": {"sliding_window_ms": chain_avg, "digital_filter_ms": filt_ms, "filter_weights": list(filt_w),
                            "digital_filter_hbm_frac": (alg_bytes / (filt_ms / 1e3) / 1e9 / hbm_peak
-                                                       if filt_ms else None)},
+                                                       if filt_ms else None),
+                           "neighbour_peak_ms": nbp_ms,
+                           "neighbour_peak_hbm_frac": (alg_bytes / (nbp_ms / 1e3) / 1e9 / hbm_peak
+                                                       if nbp_ms else None)},
             "graph": {"ms_per_step": graph_ms, "events_per_s": events_all / (graph_ms / 1e3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,

@@ -75,6 +75,11 @@ typedef enum {
 #define RTA_WINDOW_FILTER 2  /* the sliding window, charge as an integer-weighted sum over it
                                 (digital-filter-style extractor; weights per context, see
                                 rta_set_filter_weights) */
+#define RTA_WINDOW_NEIGHBOUR 3 /* neighbour-peak window: every pixel's sliding window and its
+                                  charge first; then a pixel integrates its own samples in the
+                                  window of the brightest pixel (largest charge, then earliest
+                                  start) of itself and its registered neighbours. The image is
+                                  read twice (the second time from L2); `start` is ignored. */
 
 /* Hillas row flags */
 #define RTA_HF_EMPTY 1u     /* no pixel survived cleaning: every field but n_pix is 0 */

@@ -30,6 +30,7 @@ RTA_E_DEVICE = -7
 RTA_WINDOW_FIXED = 0
 RTA_WINDOW_SLIDING = 1
 RTA_WINDOW_FILTER = 2
+RTA_WINDOW_NEIGHBOUR = 3
 RTA_HF_EMPTY = 1
 RTA_HF_NO_TIME = 2
 RTA_HF_BAD_INPUT = 4

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -158,7 +159,8 @@ rta::DevArray dev_array(rta_ctx* c) {
 
 // Window and tailcut rules against every camera the array uses.
 int check_proc(rta_ctx* c, int mode, int start, int W, bool need_clean, float t_hi, float t_lo) {
-    if (mode != RTA_WINDOW_FIXED && mode != RTA_WINDOW_SLIDING && mode != RTA_WINDOW_FILTER)
+    if (mode != RTA_WINDOW_FIXED && mode != RTA_WINDOW_SLIDING && mode != RTA_WINDOW_FILTER &&
+        mode != RTA_WINDOW_NEIGHBOUR)
         return fail(RTA_E_INVALID, "bad window mode %d", mode);
     if (mode == RTA_WINDOW_FILTER && c->filter_n != W)
         return fail(RTA_E_INVALID, "filter mode with W = %d but %d weights set", W, c->filter_n);
@@ -185,6 +187,7 @@ rta::ProcParams make_pp(const rta_ctx* c, int mode, int start, int W, int core_n
     pp.t_lo = t_lo;
     pp.one = 1;
     pp.k128 = 128;
+    pp.nbpeak = mode == RTA_WINDOW_NEIGHBOUR ? 1 : 0;
     if (mode == RTA_WINDOW_FILTER) {
         pp.filter = 1;
         for (int k = 0; k < W; ++k) {
@@ -199,22 +202,22 @@ struct ChainCfg {
     int variant, nstage, ctas_per_sm;
 };
 
-int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_t* smem, int* swb) {
+int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_t* smem, int* swb, int nb = 0) {
     if (k.variant < 0 || k.variant >= RTA_CHAIN_VARIANTS) return fail(RTA_E_INVALID, "variant %d", k.variant);
     const int nst = std::max(2, std::min(k.nstage, 8));
     *swb = rta::chain_stage_wave_bytes(k.variant, c->max_S);
     if (rta::chain_chunk_pixels(k.variant, *swb, c->max_S) < 32)
         return fail(RTA_E_INVALID, "tile variant %d has no room for %d samples", k.variant, c->max_S);
-    *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P);
-    int occ = rta::chain_occupancy(k.variant, *smem);
+    *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P, nb);
+    int occ = rta::chain_occupancy(k.variant, *smem, nb);
     const int want = k.ctas_per_sm > 0 ? k.ctas_per_sm : rta::chain_variant_min_blocks(k.variant);
     if (occ < want) {
         // smaller stages (still at least 128 pixels of the longest camera per
         // chunk) so that the requested number of CTAs fits on an SM
         for (int s2 = (*swb - 1024) & ~127; s2 >= 4096; s2 -= 1024) {
             if (rta::chain_chunk_pixels(k.variant, s2, c->max_S) < 128) break;
-            const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P);
-            const int occ2 = rta::chain_occupancy(k.variant, sm2);
+            const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P, nb);
+            const int occ2 = rta::chain_occupancy(k.variant, sm2, nb);
             if (occ2 >= want) {
                 *swb = s2;
                 *smem = sm2;
@@ -234,8 +237,8 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
     return RTA_OK;
 }
 
-int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int* swb) {
-    return config_launch(c, ChainCfg{c->variant, c->nstage, c->ctas_per_sm}, n_img, grid, smem, swb);
+int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int* swb, int nb = 0) {
+    return config_launch(c, ChainCfg{c->variant, c->nstage, c->ctas_per_sm}, n_img, grid, smem, swb, nb);
 }
 
 int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
@@ -244,7 +247,7 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
               const int64_t* d_n_img = nullptr) {
     int grid, swb;
     size_t smem;
-    int rc = chain_launch_config(c, n_img, &grid, &smem, &swb);
+    int rc = chain_launch_config(c, n_img, &grid, &smem, &swb, pp.nbpeak);
     if (rc) return rc;
     rta::ChainArgs a;
     a.arr = dev_array(c);
@@ -439,6 +442,15 @@ int rta_register_array(rta_ctx* c, int n_tel, const int32_t* h_tel_cam, const fl
     if (rc) return rc;
     if (n_tel < 1 || n_tel > RTA_MAX_TEL) return fail(RTA_E_INVALID, "n_tel %d outside 1..%d", n_tel, RTA_MAX_TEL);
     if (!h_tel_cam || !h_tel_xy || !h_p16 || !h_scale) return fail(RTA_E_INVALID, "array table is NULL");
+    {
+        int64_t n_rows = 0;
+        for (int t = 0; t < n_tel; ++t) {
+            const int cam = h_tel_cam[t];
+            if (cam >= 0 && cam < RTA_MAX_CAMS && c->cams[cam].valid) n_rows += c->cams[cam].P;
+        }
+        for (int64_t r = 0; r < n_rows; ++r)
+            if (!std::isfinite(h_scale[r])) return fail(RTA_E_INVALID, "calibration scale %lld is not finite", (long long)r);
+    }
     std::vector<int64_t> row(n_tel);
     int64_t rows = 0, src_rows = 0;
     for (int t = 0; t < n_tel; ++t) {
@@ -567,7 +579,7 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
             for (int cps = 1; cps <= 4; ++cps) {
                 int g, swb;
                 size_t sm;
-                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb) != RTA_OK) continue;
+                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb, pp.nbpeak) != RTA_OK) continue;
                 c->variant = v;
                 c->nstage = nst;
                 c->ctas_per_sm = cps;

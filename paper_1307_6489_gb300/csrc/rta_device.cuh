@@ -47,6 +47,8 @@ struct ProcParams {
     // digital-filter-style extractor: charge from integer weights over the window
     int filter, csum;
     int wts[RTA_MAX_W];
+    // neighbour-peak window: two sweeps over every image (keys, then charges)
+    int nbpeak;
 };
 
 // ------------------------------------------------------------------ PTX helpers

@@ -70,9 +70,12 @@ int chain_variant_warps(int v);
 int chain_variant_ppt(int v);
 int chain_threads(int v);
 int chain_stage_wave_bytes(int v, int max_S);
-size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P);
+size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys = 0);
 int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
-int chain_occupancy(int v, size_t smem);
+int chain_occupancy(int v, size_t smem, int nb = 0);
+// the neighbour-peak instantiations (k_image_nb.cu)
+cudaError_t dispatch_image_chain_nb(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
+                                    int* occ);
 int chain_variant_min_blocks(int v);
 int stereo_events_per_block();
 cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s);

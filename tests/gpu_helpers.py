@@ -58,7 +58,9 @@ class Dev:
 
 def proc_args(wl):
     p = wl.proc
-    if getattr(p, "weights", None) is not None:
+    if getattr(p, "nbpeak", False):
+        mode = rta.RTA_WINDOW_NEIGHBOUR
+    elif getattr(p, "weights", None) is not None:
         mode = rta.RTA_WINDOW_FILTER
     else:
         mode = rta.RTA_WINDOW_SLIDING if p.sliding else rta.RTA_WINDOW_FIXED
