@@ -163,8 +163,9 @@ int rta_register_camera(rta_ctx* ctx, int cam, int n_pix, int n_samples, const f
  * and the calibration table (Sec. 4.1 "calibration matrices"): per row the
  * pedestal in 1/16 ADC fixed point h_p16[row] and the FP32 factor
  * h_scale[row] = 1 / (16 * gain * window containment) that converts the
- * 1/16-ADC window numerator into photoelectrons. Rows of telescope t start at
- * sum of n_pix of telescopes < t. Host arrays are copied. */
+ * 1/16-ADC window numerator into photoelectrons (finite and > 0, else
+ * RTA_E_INVALID). Rows of telescope t start at sum of n_pix of telescopes < t.
+ * Host arrays are copied. */
 int rta_register_array(rta_ctx* ctx, int n_tel, const int32_t* h_tel_cam, const float* h_tel_xy,
                        const int32_t* h_p16, const float* h_scale);
 

@@ -113,7 +113,7 @@ size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int 
     const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
     const size_t words = (max_P + 31) / 32;
     const size_t chunk = size_t(kVariants[v].iw) * 32 * kVariants[v].ppt;
-    const size_t keys = nb_keys ? 8 * size_t(max_P) + 16 : 0;
+    const size_t keys = nb_keys ? 10 * size_t(max_P) + 16 : 0;   // 64-bit keys, 16-bit candidate ids
     return head + size_t(nstage) * (stage_wave_bytes + 2 * chunk * 4) + NSLOT * slot_bytes(max_P) + 8 * words + 16 +
            keys;
 }

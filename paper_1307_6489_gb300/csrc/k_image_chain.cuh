@@ -27,7 +27,7 @@ constexpr int NCW = 8;             // warps of the block-wide (unfused) kernels
 constexpr int NCT = NCW * 32;
 constexpr int MAX_STAGES = 8;
 
-enum { HDR_LAST = 1, HDR_BAD = 2, HDR_END = 4, HDR_SWEEP0 = 8 };
+enum { HDR_LAST = 1, HDR_BAD = 2, HDR_END = 4 };
 
 struct StageHdr {
     int img;
@@ -36,6 +36,8 @@ struct StageHdr {
     int flags;     // HDR_*
     int P, S, cam, pad;
     int64_t pix_off;
+    int64_t woff;  // first sample of the image in the waveform buffer
+    int64_t row;   // first calibration row of the image's telescope
     int64_t pad2;
 };
 
@@ -460,8 +462,9 @@ struct ChainSmem {
     SlotHdr shdr[NSLOT];
     uint64_t nb_ready;    // neighbour-peak window: every warp has written this image's keys
     uint64_t nb_free;     // ... and has read them (the next image may overwrite)
+    int nb_cnt[2];        // candidates of the current and the next image
     int abort;
-    int pad[27];
+    int pad[25];
     float red[8];
     int wts[RTA_MAX_W];   // weights of the digital-filter-style extractor
 };
@@ -485,98 +488,119 @@ __host__ __device__ __forceinline__ int chunk_pixels(int chunk, int stage_wave_b
     return cp < chunk ? cp : chunk;
 }
 
-// Neighbour-peak window, sweep 0: every pixel's own sliding window and the
-// charge it gives, as one 64-bit key ordered by charge, then by earliest start
-// (the charge's IEEE bits mapped to an unsigned order; never NaN, the
-// calibration table holds finite values).
+// Neighbour-peak window. Per chunk, every pixel's own sliding window and the
+// charge q0 it gives go into a 64-bit key ordered by charge, then by earliest
+// start (the charge's IEEE bits mapped to an unsigned order; never NaN, the
+// calibration scales are finite and positive). After the image's last chunk,
+// a candidate pass gives every pixel that needs a charge the start of the
+// largest key of its closed neighbourhood and integrates its own samples there,
+// re-read from L2 (the image streamed in a moment earlier with an evict-last
+// hint).
+//
+// A pixel's charge in any window is at most q0 (the scales are positive), so a
+// pixel with q0 < t_lo cannot pass cleaning whatever its window, and it never
+// outranks a neighbour that can: the image chain needs exact starts and final
+// charges only where q0 >= t_lo. Those pixels are the candidates; the packed
+// maximum gives q0 for the rest, whose stored start is never used. The
+// integrate-only outputs need every pixel's charge, so there every start is
+// exact and every pixel goes through the candidate pass.
 __device__ __forceinline__ uint64_t nb_key(float q, int st) {
     const uint32_t b = __float_as_uint(__fadd_rn(q, 0.0f));          // -0 -> +0
     const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
     return (uint64_t(o) << 32) | uint32_t(0xFFFFFFFFu - uint32_t(st));
 }
 
+struct NbShared {
+    uint64_t* key;        // [max_P] this image's keys
+    int16_t* cand;        // [max_P] candidate pixels (image chain)
+    int* n_cand;          // candidates so far in this image
+};
+
 template <int S, int W, int IT, int PPT>
-__device__ __forceinline__ void nb_keys_chunk(const ProcParams& pp, const StageHdr& h, const unsigned char* buf,
-                                              const int32_t* cp16, const float* cscale, uint64_t* nbk, int ct) {
+__device__ __forceinline__ void nb_keys_chunk(const ChainArgs& a, const ProcParams& pp, const StageHdr& h,
+                                              const unsigned char* buf, const int32_t* cp16, const float* cscale,
+                                              const NbShared& nb, const SlotView& v, int ct, int lane) {
     const int Sr = S ? S : h.S;
     const int Wr = W ? W : pp.W;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int c = ct + k * IT;
+        bool cand = false;
         if (c < h.npix) {
             const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * Sr;
-            int key;
-            if constexpr (S != 0) key = best_key_T<S, W>(row, pp.one, pp.k128);
-            else key = best_key_generic(row, Sr, Wr);
             int num;
-            const float q0 = charge(key >> 7, Wr, cp16[c], cscale[c], num);
-            nbk[h.base + c] = nb_key(q0, 127 - (key & 127));
+            float q0 = 0.f;
+            int st = 0;
+            bool exact = true;
+            if constexpr (S != 0 && W == 6) {
+                int m = 0;
+                if (!a.integrate_only && max_window6_packed<S>(row, m)) {
+                    q0 = charge(m, Wr, cp16[c], cscale[c], num);
+                    exact = q0 >= pp.t_lo;
+                }
+            }
+            if (exact) {
+                int key;
+                if constexpr (S != 0) key = best_key_T<S, W>(row, pp.one, pp.k128);
+                else key = best_key_generic(row, Sr, Wr);
+                q0 = charge(key >> 7, Wr, cp16[c], cscale[c], num);
+                st = 127 - (key & 127);
+            }
+            nb.key[h.base + c] = nb_key(q0, st);
+            cand = !a.integrate_only && q0 >= pp.t_lo;
+        }
+        if (!a.integrate_only) {
+            // append the candidates (one atomic per warp); the chunk's bitmap words
+            // start empty and the candidate pass sets their bits
+            const uint32_t bc = __ballot_sync(0xffffffffu, cand);
+            int base = 0;
+            if (lane == 0 && bc) base = atomicAdd(nb.n_cand, __popc(bc));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (cand) nb.cand[base + __popc(bc & ((1u << lane) - 1u))] = int16_t(h.base + c);
+            const int word = (h.base + c) >> 5;
+            if (lane == 0 && word < ((h.base + h.npix + 31) >> 5)) {      // only the chunk's own words
+                v.hi[word] = 0u;
+                v.lo[word] = 0u;
+            }
         }
     }
 }
 
-// The calibrated charge, time and bitmap bits of chunk pixel c with window sum
-// `sum` starting at `wst` (shared by every window mode).
-__device__ __forceinline__ void emit_pixel(const ChainArgs& a, const ProcParams& pp, const StageHdr& h, int c, int sum,
-                                           int wst, int Wr, const uint16_t* row, const int32_t* cp16,
-                                           const float* cscale, const SlotView& v, const int* wts, bool& hi,
-                                           bool& lo) {
-    const int p16 = cp16[c];
+// The candidate pass of one image: pixel p takes the start of the largest key
+// among itself and its registered neighbours, then its own flat sum there, the
+// calibration multiply and the peak time; in the image chain q, t and the
+// bitmap bits go to the slot.
+__device__ __forceinline__ void nb_pixel(const ChainArgs& a, const ProcParams& pp, const StageHdr& h, const DevCam& C,
+                                         const uint64_t* key, int p, const SlotView& v) {
+    uint64_t best = key[p];
+    const int4 nbr = C.nb[p];
+    const int16_t* ids = reinterpret_cast<const int16_t*>(&nbr);
+#pragma unroll
+    for (int j = 0; j < RTA_NB_PAD; ++j) {
+        const int id = ids[j];
+        if (j < C.K && id >= 0 && id < h.P) {
+            const uint64_t kn = key[id];
+            best = kn > best ? kn : best;
+        }
+    }
+    const int wst = int(0xFFFFFFFFu - uint32_t(best));
+    const int Wr = pp.W;
+    const uint16_t* row = a.wave + h.woff + size_t(p) * h.S;       // global memory (L2)
+    int sum = 0;
+    for (int j = 0; j < Wr; ++j) sum += __ldg(row + wst + j);
+    const int p16 = __ldg(a.arr.p16 + h.row + p);
     int num;
-    float q = charge(sum, Wr, p16, cscale[c], num);
-    if (pp.filter) q = filter_charge(row, wst, Wr, wts, pp.csum, p16, cscale[c]);
-    const int p = h.base + c;
+    const float q = charge(sum, Wr, p16, __ldg(a.arr.scale + h.row + p), num);
     if (a.integrate_only) {
         a.q_out[h.pix_off + p] = q;
         if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, Wr, p16, num);
     } else {
         v.q[p] = q;
-        hi = q >= pp.t_hi;
-        lo = q >= pp.t_lo;
-        // only pixels that can survive cleaning need their time
-        if (lo) v.t[p] = peak_time(row, wst, Wr, p16, num);
-    }
-}
-
-// Neighbour-peak window, sweep 1: the start of the largest key among the pixel
-// and its registered neighbours, the pixel's own flat sum there, then the
-// common outputs.
-template <int IT, int PPT>
-__device__ __forceinline__ void nb_emit_chunk(const ChainArgs& a, const ProcParams& pp, const StageHdr& h,
-                                              const unsigned char* buf, const int32_t* cp16, const float* cscale,
-                                              const uint64_t* nbk, const SlotView& v, int ct, int lane) {
-    const DevCam C = a.arr.cams[h.cam];
-    const int Sr = h.S, Wr = pp.W;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int c = ct + k * IT;
-        bool hi = false, lo = false;
-        if (c < h.npix) {
-            const int p = h.base + c;
-            uint64_t best = nbk[p];
-            const int4 nbr = C.nb[p];
-            const int16_t* ids = reinterpret_cast<const int16_t*>(&nbr);
-#pragma unroll
-            for (int j = 0; j < RTA_NB_PAD; ++j) {
-                const int id = ids[j];
-                if (j < C.K && id >= 0 && id < h.P) {
-                    const uint64_t kn = nbk[id];
-                    best = kn > best ? kn : best;
-                }
-            }
-            const int wst = int(0xFFFFFFFFu - uint32_t(best));
-            const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * Sr;
-            int sum = 0;
-            for (int j = 0; j < Wr; ++j) sum += row[wst + j];
-            emit_pixel(a, pp, h, c, sum, wst, Wr, row, cp16, cscale, v, nullptr, hi, lo);
-        }
-        if (!a.integrate_only) {
-            const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
-            const int word = (h.base + c) >> 5;
-            if (lane == 0 && word < ((h.base + h.npix + 31) >> 5)) {      // only the chunk's own words
-                v.hi[word] = bh;
-                v.lo[word] = bl;
-            }
+        const uint32_t bit = 1u << (p & 31);
+        if (q >= pp.t_hi) atomicOr(&v.hi[p >> 5], bit);
+        if (q >= pp.t_lo) {
+            atomicOr(&v.lo[p >> 5], bit);
+            v.t[p] = peak_time(row, wst, Wr, p16, num);
         }
     }
 }
@@ -682,9 +706,9 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
     }
 }
 
-// NB: the neighbour-peak window (two sweeps per image, keys in shared memory);
-// a separate instantiation, so that the other window modes run the same code
-// as without it.
+// NB: the neighbour-peak window (keys and candidates in shared memory, a
+// candidate pass after each image); a separate instantiation, so that the other
+// window modes run the same code as without it.
 template <int IW, int PPT, int MB, bool NB>
 __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
     constexpr int IT = IW * 32;          // integrator threads
@@ -710,8 +734,9 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
     };
     uint32_t* core = reinterpret_cast<uint32_t*>(slots + NSLOT * slot_bytes(maxP));
     uint32_t* maskb = core + maxw;
-    // neighbour-peak keys of the image being integrated (8-byte aligned)
+    // neighbour-peak keys and candidates of the image being integrated
     uint64_t* nbk = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(maskb + maxw) + 15) & ~uintptr_t(15));
+    int16_t* nbc = reinterpret_cast<int16_t*>(nbk + maxP);
     volatile int* abort_flag = &sm.abort;
 
     const int tid = threadIdx.x;
@@ -727,6 +752,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
         if (NB) {
             mbar_init(&sm.nb_ready, IW);
             mbar_init(&sm.nb_free, IW);
+            sm.nb_cnt[0] = sm.nb_cnt[1] = 0;
         }
         sm.abort = 0;
         fence_mbar_init();
@@ -793,9 +819,6 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             const int P = C.P, S = C.S, CP = chunk_pixels(CHUNK, a.stage_wave_bytes, S);
             const int64_t row = a.arr.tel_row[tel];
             const uint16_t* src = a.wave + woff;
-            // the neighbour-peak window reads the image twice: sweep 0 keeps it in L2
-            // for sweep 1, which is its last use
-            for (int sweep = NB ? 0 : 1; sweep < 2 && ok; ++sweep)
             for (int base = 0; base < P; base += CP) {
                 if (!acquire(stage, phase)) { ok = false; break; }
                 const int npix = min(CP, P - base);
@@ -803,19 +826,23 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 h.img = int(img);
                 h.base = base;
                 h.npix = npix;
-                h.flags = sweep == 0 ? HDR_SWEEP0 : (base + CP >= P) ? HDR_LAST : 0;
+                h.flags = (base + CP >= P) ? HDR_LAST : 0;
                 h.P = P;
                 h.S = S;
                 h.cam = cam;
                 h.pad = 0;
                 h.pix_off = poff;
+                h.woff = woff;
+                h.row = row;
                 h.pad2 = 0;
                 sm.hdr[stage] = h;
                 const uint32_t wbytes = uint32_t(npix) * uint32_t(S) * 2u;     // multiple of 16 (P*S % 8 == 0)
                 const uint32_t cbytes = (uint32_t(npix) * 4u + 15u) & ~15u;
                 unsigned char* buf = stages + size_t(stage) * stage_bytes;
                 mbar_arrive_expect_tx(&sm.full[stage], wbytes + 2u * cbytes);
-                bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], sweep == 0 ? pol_keep : pol_stream);
+                // the neighbour-peak window reads its candidates' samples once more right
+                // after the image: keep the image in L2 until then
+                bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], NB ? pol_keep : pol_stream);
                 bulk_g2s(buf + a.stage_wave_bytes, a.arr.p16 + row + base, cbytes, &sm.full[stage], pol_keep);
                 bulk_g2s(buf + a.stage_wave_bytes + calib_bytes, a.arr.scale + row + base, cbytes, &sm.full[stage],
                          pol_keep);
@@ -871,7 +898,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
     int stage = 0, slot = 0;
     uint32_t phase = 0, sphase = 0;
     uint32_t nb_rph = 0, nb_fph = 0;  // neighbour-peak barrier phases
-    bool nb_first = true;
+    int nb_img = 0;                   // neighbour-peak images done by this CTA
     SlotView v = slot_view(0);
     for (;;) {
         if (!mbar_wait(&sm.full[stage], phase, abort_flag)) { give_up(); break; }
@@ -894,60 +921,67 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             if (++stage == NST) { stage = 0; phase ^= 1u; }
             continue;
         }
-        const unsigned char* buf = stages + size_t(stage) * stage_bytes;
-        const int32_t* cp16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes);
-        const float* cscale = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes);
-        if constexpr (NB) {
-            if (h.flags & HDR_SWEEP0) {
-                // neighbour-peak window, sweep 0: this image's keys; the previous
-                // image's keys must have been read by every warp first
-                if (h.base == 0) {
-                    if (!nb_first) {
-                        if (!mbar_wait(&sm.nb_free, nb_fph, abort_flag)) { give_up(); break; }
-                        nb_fph ^= 1u;
-                    }
-                    nb_first = false;
-                }
-                if (pp.W == 6 && h.S == 40)
-                    nb_keys_chunk<40, 6, IT, PPT>(pp, h, buf, cp16, cscale, nbk, ct);
-                else if (pp.W == 6 && h.S == 30)
-                    nb_keys_chunk<30, 6, IT, PPT>(pp, h, buf, cp16, cscale, nbk, ct);
-                else if (pp.W == 6 && h.S == 25)
-                    nb_keys_chunk<25, 6, IT, PPT>(pp, h, buf, cp16, cscale, nbk, ct);
-                else
-                    nb_keys_chunk<0, 0, IT, PPT>(pp, h, buf, cp16, cscale, nbk, ct);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.empty[stage]);
-                if (h.base + h.npix >= h.P && lane == 0) mbar_arrive(&sm.nb_ready);
-                if (++stage == NST) { stage = 0; phase ^= 1u; }
-                continue;
-            }
-        }
-        if (NB && h.base == 0) {
-            // sweep 1 reads the keys of the whole image
-            if (!mbar_wait(&sm.nb_ready, nb_rph, abort_flag)) { give_up(); break; }
-            nb_rph ^= 1u;
+        if (NB && h.base == 0 && nb_img > 0) {
+            // this image's keys and candidates overwrite the previous image's:
+            // every warp must be done with those
+            if (!mbar_wait(&sm.nb_free, nb_fph, abort_flag)) { give_up(); break; }
+            nb_fph ^= 1u;
         }
         if (h.base == 0 && !a.integrate_only) {
             // the slot must be free: the tail warp is done with the image two back
             if (!mbar_wait(&sm.slot_free[slot], sphase ^ 1u, abort_flag)) { give_up(); break; }
         }
-        if constexpr (NB)
-            nb_emit_chunk<IT, PPT>(a, pp, h, buf, cp16, cscale, nbk, v, ct, lane);
-        else if (pp.sliding && pp.W == 6 && h.S == 40)
-            integrate_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
-        else if (pp.sliding && pp.W == 6 && h.S == 30)
-            integrate_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
-        else if (pp.sliding && pp.W == 6 && h.S == 25)
-            integrate_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
-        else if (pp.sliding && pp.W == 5 && h.S == 16)
-            integrate_chunk<16, 5, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
-        else
-            integrate_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.empty[stage]);
-        if (++stage == NST) { stage = 0; phase ^= 1u; }
-        if (NB && (h.flags & HDR_LAST) && lane == 0) mbar_arrive(&sm.nb_free);
+        const unsigned char* buf = stages + size_t(stage) * stage_bytes;
+        const int32_t* cp16 = reinterpret_cast<const int32_t*>(buf + a.stage_wave_bytes);
+        const float* cscale = reinterpret_cast<const float*>(buf + a.stage_wave_bytes + calib_bytes);
+        if constexpr (NB) {
+            // per image two counters in turn: the one of the image before is reset
+            // during this image's candidate pass, after every warp has passed nb_free
+            const NbShared nb = {nbk, nbc, &sm.nb_cnt[nb_img & 1]};
+            if (pp.W == 6 && h.S == 40)
+                nb_keys_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+            else if (pp.W == 6 && h.S == 30)
+                nb_keys_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+            else if (pp.W == 6 && h.S == 25)
+                nb_keys_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+            else
+                nb_keys_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            if (++stage == NST) { stage = 0; phase ^= 1u; }
+            if (h.flags & HDR_LAST) {
+                // every key, candidate and bitmap word of the image is written...
+                if (lane == 0) mbar_arrive(&sm.nb_ready);
+                if (!mbar_wait(&sm.nb_ready, nb_rph, abort_flag)) { give_up(); break; }
+                nb_rph ^= 1u;
+                // ...so the candidate pass can look at any pixel's neighbours
+                const DevCam C = a.arr.cams[h.cam];
+                if (a.integrate_only) {
+                    for (int p = ct; p < h.P; p += IT) nb_pixel(a, pp, h, C, nbk, p, v);
+                } else {
+                    const int n = *nb.n_cand;
+                    for (int j = ct; j < n; j += IT) nb_pixel(a, pp, h, C, nbk, nbc[j], v);
+                }
+                if (ct == 0) sm.nb_cnt[(nb_img + 1) & 1] = 0;
+                ++nb_img;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.nb_free);
+            }
+        } else {
+            if (pp.sliding && pp.W == 6 && h.S == 40)
+                integrate_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+            else if (pp.sliding && pp.W == 6 && h.S == 30)
+                integrate_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+            else if (pp.sliding && pp.W == 6 && h.S == 25)
+                integrate_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+            else if (pp.sliding && pp.W == 5 && h.S == 16)
+                integrate_chunk<16, 5, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+            else
+                integrate_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            if (++stage == NST) { stage = 0; phase ^= 1u; }
+        }
         if ((h.flags & HDR_LAST) && !a.integrate_only) {
             if (ct == 0) {
                 SlotHdr sh;

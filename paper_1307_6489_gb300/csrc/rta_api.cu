@@ -449,7 +449,8 @@ int rta_register_array(rta_ctx* c, int n_tel, const int32_t* h_tel_cam, const fl
             if (cam >= 0 && cam < RTA_MAX_CAMS && c->cams[cam].valid) n_rows += c->cams[cam].P;
         }
         for (int64_t r = 0; r < n_rows; ++r)
-            if (!std::isfinite(h_scale[r])) return fail(RTA_E_INVALID, "calibration scale %lld is not finite", (long long)r);
+            if (!std::isfinite(h_scale[r]) || !(h_scale[r] > 0.f))
+                return fail(RTA_E_INVALID, "calibration scale %lld is not finite and positive", (long long)r);
     }
     std::vector<int64_t> row(n_tel);
     int64_t rows = 0, src_rows = 0;

@@ -119,3 +119,21 @@ def test_nbpeak_full_size_bundle():
     imgs = np.concatenate([np.arange(wl.evt_off[e], wl.evt_off[e + 1]) for e in ev])
     compare_hillas({k: v[imgs] for k, v in g.items()}, ref["hillas"][imgs], "nbpeak full bundle")
     ctx.close()
+
+
+def test_calibration_scales_must_be_finite_and_positive():
+    """The neighbour-peak shortcut (a pixel's charge in any window is at most
+    its sliding-window charge) needs positive scales; registration refuses
+    others."""
+    wl = synth.make_workload(0, 4)
+    ctx = rta.Context(0)
+    for c, cam in wl.cams.items():
+        ctx.register_camera(c, cam.xy, cam.nb, cam.n_samples)
+    for bad in (0.0, -1.0, np.nan, np.inf):
+        scale = wl.scale.copy()
+        scale[3] = bad
+        with pytest.raises(rta.RtaError) as e:
+            ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, scale)
+        assert e.value.code == rta.RTA_E_INVALID
+    ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
+    ctx.close()
