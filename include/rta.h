@@ -92,6 +92,7 @@ typedef enum {
 /* Device status word bits (rta_check) */
 #define RTA_DEV_BAD_IMAGE 1u
 #define RTA_DEV_TIMEOUT 2u
+#define RTA_DEV_BAD_STREAM 4u   /* rta_ingest met a malformed byte stream (see its counts) */
 
 /* One image's parameters, 64 bytes. Angles in radians, positions in degrees of
  * the flat camera (nominal) frame, time in samples (ns at 1 GS/s). */
@@ -361,6 +362,89 @@ int rta_surrogate_train_step(rta_model* model, const rta_hillas_t* d_hillas, con
  * events only) and RTA_EF_FALLBACK. */
 int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* DL0 byte-stream ingest (Sec. 5: the telescope data as a stream of bytes  */
+/* formatted like satellite telemetry)                                     */
+/* ---------------------------------------------------------------------- */
+/* The paper names the standard (CCSDS space packets with a PUS telemetry
+ * secondary header), not the packet contents; this is the layout librta reads.
+ * A packet carries a pixel range (segment) of one image. Packets start on
+ * 16-byte boundaries and follow one another with no gap; header fields are
+ * big-endian, samples little-endian.
+ *   bytes   field
+ *   0-1     version 0 (3 bits) | type 0 = telemetry (1) | secondary header 1 (1)
+ *           | APID = telescope id (11)
+ *   2-3     sequence flags (2 bits: 3 = the whole image, 1 = first, 0 =
+ *           continuation, 2 = last segment) | sequence count (14, not checked)
+ *   4-5     packet data length = packet bytes - 7
+ *   6       0x10: PUS version 1 in the high nibble
+ *   7       service type 200 (camera data)
+ *   8       service subtype 1 (waveform segment)
+ *   9       destination id (not checked)
+ *   10-13   event time, seconds (CUC coarse time)
+ *   14-15   event time, 1/65536 s (CUC fine time)
+ *   16-23   event number
+ *   24-25   first pixel of the segment
+ *   26-27   pixels in the segment, n (n x samples a multiple of 8)
+ *   28-29   pixels of the image (must equal the camera's)
+ *   30-31   samples per pixel (must equal the camera's)
+ *   32 ...  n x samples uint16 samples, pixel-major (the DL0 bundle layout)
+ *   +14     zero padding
+ *   +2      packet error control: CRC-16-CCITT (polynomial 0x1021, initial
+ *           value 0xFFFF, no reflection, no final XOR) of every byte before it
+ * A packet is 48 + 2 n S bytes, at most 65536. The segments of an image follow
+ * one another in pixel order, starting at pixel 0 and ending at the image's last
+ * pixel; an event is a run of images with the same event number. */
+#define RTA_PKT_HEADER_BYTES 32
+#define RTA_PKT_TRAILER_BYTES 16
+#define RTA_PKT_MAX_BYTES 65536
+#define RTA_PKT_SERVICE 200
+#define RTA_PKT_SUBSERVICE 1
+
+/* One segment of the stream directory: where its samples are and which pixels. */
+typedef struct rta_segment_t {
+    int64_t offset;      /* byte offset of the first sample in the stream */
+    int32_t first_pixel; /* first pixel of the image it carries */
+    int32_t n_pixels;    /* pixels it carries */
+} rta_segment_t;
+
+/* Why rta_ingest stopped (d_counts[4]); the byte offset of the packet is d_counts[5]. */
+#define RTA_STREAM_OK 0
+#define RTA_STREAM_FRAMING 1   /* no valid packet where the previous one ends, or bytes left over */
+#define RTA_STREAM_HEADER 2    /* a fixed header field is wrong */
+#define RTA_STREAM_CAMERA 3    /* unknown telescope, or pixels/samples differ from its camera */
+#define RTA_STREAM_SEGMENT 4   /* segments out of order, overlapping or incomplete */
+#define RTA_STREAM_CRC 5       /* packet error control mismatch (verify_crc) */
+#define RTA_STREAM_CAPACITY 6  /* more segments, images or events than the capacities */
+
+/* Decode a device-resident byte stream into a directory: segments (in stream
+ * order), images (d_img_seg[i] = first segment of image i, n_img + 1 entries;
+ * d_img_tel[i]) and events (d_evt_off: n_evt + 1 image offsets; event number
+ * and event time in ns = seconds * 1e9 + floor(fine * 1e9 / 65536)). Nothing is
+ * copied: rta_reconstruct_stream reads the samples where they are. Packets are
+ * found in parallel: the stream is cut into 1 MiB pieces, each piece looks for
+ * its first valid packet (a header whose fixed fields hold and whose successor
+ * also starts a valid header) and walks from there; the walks must join up.
+ * verify_crc != 0 also checks every packet's CRC (reads every byte once).
+ * d_counts (6 int64, device): n_segments, n_img, n_evt, n_samples, error code
+ * (RTA_STREAM_*), byte offset of the first bad packet (-1). On an error the
+ * directory is incomplete and RTA_DEV_BAD_STREAM is set in the status word.
+ * The stream must be 16-byte aligned. Asynchronous on stream; grows the
+ * context's workspace (an allocation) when a stream is larger than any before. */
+int rta_ingest(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, int verify_crc, rta_segment_t* d_seg,
+               int64_t seg_cap, int32_t* d_img_seg, int32_t* d_img_tel, int64_t img_cap, int32_t* d_evt_off,
+               uint64_t* d_evt_number, int64_t* d_evt_time_ns, int64_t evt_cap, int64_t* d_counts, void* stream);
+
+/* rta_reconstruct over an ingested stream, zero copy: the image kernel's bulk
+ * copies read each chunk of pixels from the segment(s) that hold it. Counts are
+ * read on the device (d_counts from rta_ingest: [1] images, [2] events), at
+ * most max_img and max_evt. Stream-ordered, no host sync. */
+int rta_reconstruct_stream(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, const rta_segment_t* d_seg,
+                           const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
+                           const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_counts, int window_mode,
+                           int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                           rta_hillas_t* d_hillas, rta_stereo_t* d_stereo, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Lookup tables: the calibration matrices of the real-time reconstruction  */

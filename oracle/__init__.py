@@ -15,7 +15,7 @@ calibration multiply); this module only marshals numpy arrays.  Row layouts:
 The sky map (``skymap``) and the transient search on it (``li_ma``,
 ``disk_sum``, ``transient_maps``, ``transient_search``) are numpy here.
 ``lut.py`` holds the lookup-table ("calibration matrix") energy and scaled
-width/length reconstruction.
+width/length reconstruction; ``ingest.py`` the DL0 byte-stream decoder.
 """
 from __future__ import annotations
 
@@ -290,3 +290,4 @@ def transient_search(dir_x, dir_y, has_dir, arrival_s, now_s, windows, radius, s
 
 
 from .lut import bin_index, impact_distance, lut_build, lut_reconstruct  # noqa: E402
+from . import ingest  # noqa: E402,F401

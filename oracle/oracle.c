@@ -454,3 +454,24 @@ int or_reconstruct(int64_t n_img, const uint16_t* wave, const int64_t* wave_off,
     if (stereo && n_evt > 0) run_threads(stereo_worker, &J, n_threads);
     return J.status;
 }
+
+/* ------------------------------------------------------------------ */
+/* CRC of the DL0 packets (Sec. 5: telemetry-formatted byte stream)     */
+/* ------------------------------------------------------------------ */
+/*
+ * CRC-16-CCITT by its definition: the message bits, most significant bit of
+ * each byte first, are divided by x^16 + x^12 + x^5 + 1 with the register
+ * preset to 0xFFFF; no reflection, no final XOR. One bit at a time.
+ */
+uint32_t or_crc16(const uint8_t* p, int64_t n) {
+    uint32_t r = 0xFFFFu;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int b = 7; b >= 0; --b) {
+            const uint32_t in = (p[i] >> b) & 1u;
+            const uint32_t top = (r >> 15) & 1u;
+            r = (r << 1) & 0xFFFFu;
+            if (top ^ in) r ^= 0x1021u;
+        }
+    }
+    return r;
+}

@@ -66,6 +66,9 @@ def _L():
         lib.synth_test_normals.argtypes = [u64, i32, P]
         lib.synth_test_poisson.argtypes = [u64, f64, i32, P]
         lib.synth_philox_block.argtypes = [P, P, P]
+        lib.synth_crc16.argtypes = [P, i64]
+        lib.synth_crc16.restype = ctypes.c_uint16
+        lib.synth_write_stream.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, i32]
         _lib = lib
     return _lib
 
@@ -342,3 +345,80 @@ def subset(wl: Workload, events) -> Workload:
     return Workload(wl.preset, wl.seed, wl.proc, wl.cams, wl.tel_cam, wl.tel_xy, wl.tel_pix_off, wl.ped, wl.gain,
                     wl.p16, wl.scale, evt_off, img_tel, np.repeat(np.arange(len(events), dtype=np.int32), counts),
                     wave_off, pix_off, wl.ell[imgs].copy(), wl.n_ell[imgs].copy(), wl.truth[events].copy(), wave)
+
+
+# ----------------------------------------------------------------------------- DL0 byte stream
+PKT_MAX_BYTES = 65536
+
+
+def max_segment_pixels(S: int) -> int:
+    """Largest pixel count of one packet for S samples: 48 + 2 n S <= 65536 and
+    n S a multiple of 8."""
+    n = (PKT_MAX_BYTES - 48) // (2 * S)
+    while (n * S) % 8:
+        n -= 1
+    return n
+
+
+def stream_plan(wl: Workload, seg_pixels=None):
+    """Packets of a workload in stream order (events in order, images of an event
+    in order, segments of an image in pixel order): arrays img, first, n, flags
+    (3 whole, 1 first, 0 continuation, 2 last), count (per telescope, mod 2^14) and
+    the byte offset of each packet. seg_pixels: {camera id: pixels per segment}
+    (default: the largest that fits)."""
+    img, first, npx, flags = [], [], [], []
+    for i in range(wl.n_img):
+        cam = wl.image_cam(i)
+        P, S = cam.n_pix, cam.n_samples
+        seg = (seg_pixels or {}).get(int(wl.tel_cam[wl.img_tel[i]]), max_segment_pixels(S))
+        assert (seg * S) % 8 == 0 and 48 + 2 * seg * S <= PKT_MAX_BYTES
+        starts = list(range(0, P, seg))
+        for j, f in enumerate(starts):
+            n = min(seg, P - f)
+            img.append(i)
+            first.append(f)
+            npx.append(n)
+            whole, last = len(starts) == 1, j == len(starts) - 1
+            flags.append(3 if whole else (1 if j == 0 else (2 if last else 0)))
+    img = np.array(img, np.int32)
+    first = np.array(first, np.int32)
+    npx = np.array(npx, np.int32)
+    flags = np.array(flags, np.int32)
+    S_of = np.array([wl.image_cam(i).n_samples for i in range(wl.n_img)], np.int32)
+    size = 48 + 2 * npx.astype(np.int64) * S_of[img]
+    off = np.concatenate([[0], np.cumsum(size)[:-1]]).astype(np.int64)
+    tel = wl.img_tel[img]
+    count = np.zeros(len(img), np.int32)
+    seen = {}
+    for k, t in enumerate(tel):
+        c = seen.get(int(t), 0)
+        count[k] = c % 16384
+        seen[int(t)] = c + 1
+    return dict(img=img, first=first, n=npx, flags=flags, count=count, off=off, size=size,
+                n_bytes=int(size.sum()))
+
+
+def encode_stream(wl: Workload, event_numbers=None, times_ns=None, seg_pixels=None, threads: int | None = None,
+                  out: np.ndarray | None = None):
+    """The workload as a DL0 byte stream (the layout of include/rta.h). Returns
+    (uint8 array, plan). event_numbers / times_ns: per event (defaults 1000 + e
+    and 1 ms apart from 1.7e18 ns)."""
+    plan = stream_plan(wl, seg_pixels)
+    n_evt = wl.n_evt
+    evnum = np.asarray(event_numbers if event_numbers is not None else 1000 + np.arange(n_evt), np.uint64)
+    t_ns = np.asarray(times_ns if times_ns is not None else 1_700_000_000_000_000_000 + 1_000_000 * np.arange(n_evt),
+                      np.int64)
+    evt_of_img = np.repeat(np.arange(n_evt), np.diff(wl.evt_off))
+    img_evnum = np.ascontiguousarray(evnum[evt_of_img])
+    img_time = np.ascontiguousarray(t_ns[evt_of_img])
+    img_P = np.array([wl.image_cam(i).n_pix for i in range(wl.n_img)], np.int32)
+    img_S = np.array([wl.image_cam(i).n_samples for i in range(wl.n_img)], np.int32)
+    buf = out if out is not None else np.empty(plan["n_bytes"], np.uint8)
+    assert buf.size >= plan["n_bytes"]
+    _L().synth_write_stream(len(plan["img"]), _p(plan["img"]), _p(plan["first"]), _p(plan["n"]), _p(plan["flags"]),
+                            _p(plan["count"]), _p(plan["off"]), _p(np.ascontiguousarray(wl.wave)),
+                            _p(np.ascontiguousarray(wl.wave_off)), _p(np.ascontiguousarray(wl.img_tel)), _p(img_P),
+                            _p(img_S), _p(img_evnum), _p(img_time), _p(buf), int(threads or os.cpu_count() or 1))
+    plan["event_numbers"] = evnum
+    plan["times_ns"] = t_ns
+    return buf[: plan["n_bytes"]], plan

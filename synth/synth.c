@@ -601,3 +601,95 @@ int synth_render(uint64_t seed, int64_t n_img, const int32_t* img_evt, const int
     for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* DL0 byte stream (the event builder's output; layout in include/rta.h) */
+/* ------------------------------------------------------------------ */
+static uint16_t crc16_table[256];
+static pthread_once_t crc16_once = PTHREAD_ONCE_INIT;
+
+static void crc16_init(void) {
+    for (int b = 0; b < 256; ++b) {
+        uint16_t r = (uint16_t)(b << 8);
+        for (int k = 0; k < 8; ++k) r = (r & 0x8000u) ? (uint16_t)((r << 1) ^ 0x1021u) : (uint16_t)(r << 1);
+        crc16_table[b] = r;
+    }
+}
+
+/* CRC-16-CCITT, polynomial 0x1021, initial value 0xFFFF, no reflection. */
+uint16_t synth_crc16(const uint8_t* p, int64_t n) {
+    pthread_once(&crc16_once, crc16_init);
+    uint16_t r = 0xFFFFu;
+    for (int64_t i = 0; i < n; ++i) r = (uint16_t)((r << 8) ^ crc16_table[((r >> 8) ^ p[i]) & 0xFF]);
+    return r;
+}
+
+static void put16(uint8_t* p, uint32_t v) { p[0] = (uint8_t)(v >> 8); p[1] = (uint8_t)v; }
+static void put32(uint8_t* p, uint32_t v) { put16(p, v >> 16); put16(p + 2, v); }
+
+typedef struct {
+    int64_t n_pk;
+    const int32_t *pk_img, *pk_first, *pk_n, *pk_flags, *pk_count;
+    const int64_t* pk_off;
+    const uint16_t* wave;
+    const int64_t* wave_off;
+    const int32_t *img_tel, *img_P, *img_S;
+    const uint64_t* img_evnum;
+    const int64_t* img_time_ns;
+    uint8_t* out;
+    int64_t next;
+} stream_job_t;
+
+static void* stream_worker(void* arg) {
+    stream_job_t* J = (stream_job_t*)arg;
+    for (;;) {
+        int64_t k = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (k >= J->n_pk) break;
+        const int i = J->pk_img[k], P = J->img_P[i], S = J->img_S[i];
+        const int first = J->pk_first[k], n = J->pk_n[k];
+        const int64_t nbytes = (int64_t)n * S * 2, total = 48 + nbytes;
+        uint8_t* p = J->out + J->pk_off[k];
+        put16(p, (0u << 13) | (0u << 12) | (1u << 11) | ((uint32_t)J->img_tel[i] & 0x7FFu));
+        put16(p + 2, ((uint32_t)J->pk_flags[k] << 14) | ((uint32_t)J->pk_count[k] & 0x3FFFu));
+        put16(p + 4, (uint32_t)(total - 7));
+        p[6] = 0x10; p[7] = 200; p[8] = 1; p[9] = 0;
+        const int64_t t = J->img_time_ns[i];
+        const int64_t sec = t / 1000000000, ns = t % 1000000000;
+        put32(p + 10, (uint32_t)sec);
+        put16(p + 14, (uint32_t)((ns * 65536) / 1000000000));
+        put32(p + 16, (uint32_t)(J->img_evnum[i] >> 32));
+        put32(p + 20, (uint32_t)J->img_evnum[i]);
+        put16(p + 24, (uint32_t)first);
+        put16(p + 26, (uint32_t)n);
+        put16(p + 28, (uint32_t)P);
+        put16(p + 30, (uint32_t)S);
+        const uint16_t* src = J->wave + J->wave_off[i] + (int64_t)first * S;
+        for (int64_t j = 0; j < (int64_t)n * S; ++j) {      /* little-endian samples */
+            p[32 + 2 * j] = (uint8_t)src[j];
+            p[33 + 2 * j] = (uint8_t)(src[j] >> 8);
+        }
+        memset(p + 32 + nbytes, 0, 14);
+        put16(p + 46 + nbytes, synth_crc16(p, 46 + nbytes));
+    }
+    return NULL;
+}
+
+/* Write n_pk packets (plan in stream order: image, first pixel, pixel count,
+ * sequence flags and count, byte offset) from a bundle into out. */
+int synth_write_stream(int64_t n_pk, const int32_t* pk_img, const int32_t* pk_first, const int32_t* pk_n,
+                       const int32_t* pk_flags, const int32_t* pk_count, const int64_t* pk_off, const uint16_t* wave,
+                       const int64_t* wave_off, const int32_t* img_tel, const int32_t* img_P, const int32_t* img_S,
+                       const uint64_t* img_evnum, const int64_t* img_time_ns, uint8_t* out, int n_threads) {
+    stream_job_t J = {n_pk, pk_img, pk_first, pk_n, pk_flags, pk_count, pk_off, wave, wave_off, img_tel, img_P,
+                      img_S, img_evnum, img_time_ns, out, 0};
+    pthread_once(&crc16_once, crc16_init);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int i = 1; i < n_threads; ++i)
+        if (pthread_create(&th[started], NULL, stream_worker, &J) == 0) ++started;
+    stream_worker(&J);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
