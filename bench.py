@@ -154,6 +154,113 @@ LUT_DIST_EDGES = np.linspace(0.0, 1000.0, 21, dtype=np.float32)
 LUT_CUTS = (-2.0, 0.9, -2.0, 2.0)      # gamma box: mscw_lo, mscw_hi, mscl_lo, mscl_hi
 
 
+def stream_leg(ctx, wl, proc, stream, steps, e2e_steps, hil, ste):
+    """The bundle as a DL0 byte stream (the packet layout of include/rta.h),
+    written by the generator into pinned host memory: rta_ingest alone (with and
+    without the CRC check), the zero-copy rta_reconstruct_stream, and end to end
+    per step: host-to-device copy of the stream, ingest with CRC, reconstruction,
+    device-to-host copy of the Hillas and stereo rows."""
+    import torch
+    import paper_1307_6489_gb300 as rta
+    import synth
+    sp = stream.cuda_stream
+    plan = synth.stream_plan(wl)
+    n_bytes = plan["n_bytes"]
+    host = torch.empty(n_bytes, dtype=torch.uint8, pin_memory=True)
+    buf, plan = synth.encode_stream(wl, out=host.numpy())
+    n_pk = len(plan["img"])
+    d_stream = torch.empty((n_bytes + 31) // 16 * 16, dtype=torch.uint8, device="cuda")
+    d_seg = torch.empty(n_pk * 2, dtype=torch.int64, device="cuda")
+    d_img_seg = torch.empty(wl.n_img + 1, dtype=torch.int32, device="cuda")
+    d_img_tel = torch.empty(wl.n_img, dtype=torch.int32, device="cuda")
+    d_evt_off = torch.empty(wl.n_evt + 1, dtype=torch.int32, device="cuda")
+    d_evn = torch.empty(wl.n_evt, dtype=torch.int64, device="cuda")
+    d_evt = torch.empty(wl.n_evt, dtype=torch.int64, device="cuda")
+    d_cnt = torch.zeros(6, dtype=torch.int64, device="cuda")
+    h2 = torch.empty_like(hil)
+    s2 = torch.empty_like(ste)
+    h = ctx.handle
+    d_stream[:n_bytes].copy_(host, non_blocking=True)
+    torch.cuda.synchronize()
+
+    def ingest(crc):
+        rta.rta_ingest(h, d_stream.data_ptr(), n_bytes, crc, d_seg.data_ptr(), n_pk, d_img_seg.data_ptr(),
+                       d_img_tel.data_ptr(), wl.n_img, d_evt_off.data_ptr(), d_evn.data_ptr(), d_evt.data_ptr(),
+                       wl.n_evt, d_cnt.data_ptr(), sp)
+
+    def recon():
+        rta.rta_reconstruct_stream(h, d_stream.data_ptr(), n_bytes, d_seg.data_ptr(), n_pk, d_img_seg.data_ptr(),
+                                   d_img_tel.data_ptr(), wl.n_img, d_evt_off.data_ptr(), wl.n_evt, d_cnt.data_ptr(),
+                                   *proc, h2.data_ptr(), s2.data_ptr(), sp)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ingest_ms = timed(lambda: ingest(0))
+    ingest_crc_ms = timed(lambda: ingest(1))
+    cnt = d_cnt.cpu().numpy()
+    assert cnt[4] == 0 and cnt[0] == n_pk and cnt[1] == wl.n_img and cnt[2] == wl.n_evt, cnt
+    recon_ms = timed(recon)
+    ctx.check(sp)
+    assert torch.equal(h2, hil) and torch.equal(s2, ste), "zero-copy rows differ from the bundle path"
+    # end to end from the pinned host stream: two device copies of the stream, so
+    # that the next bundle's upload (copy stream) overlaps this bundle's ingest,
+    # reconstruction and read-back (compute stream)
+    hh = torch.empty(hil.numel(), dtype=torch.float32, pin_memory=True)
+    hs = torch.empty(ste.numel(), dtype=torch.float32, pin_memory=True)
+    bufs = [d_stream, torch.empty_like(d_stream)]
+    cs = torch.cuda.Stream()
+    up = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    for ev in done:
+        ev.record(stream)
+
+    def e2e_step(k):
+        nonlocal d_stream
+        b = k & 1
+        cs.wait_event(done[b])
+        with torch.cuda.stream(cs):
+            bufs[b][:n_bytes].copy_(host, non_blocking=True)
+        up[b].record(cs)
+        stream.wait_event(up[b])
+        d_stream = bufs[b]
+        ingest(1)
+        recon()
+        with torch.cuda.stream(stream):
+            hh.copy_(h2, non_blocking=True)
+            hs.copy_(s2, non_blocking=True)
+        done[b].record(stream)
+
+    e2e_step(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    ctx.check(sp)
+    assert torch.equal(hh, hil.cpu()), "end-to-end stream rows differ"
+    hbm_peak, _ = peaks()
+    return {"stream_bytes": n_bytes, "packets": n_pk, "ingest_ms": ingest_ms, "ingest_crc_ms": ingest_crc_ms,
+            "ingest_crc_gbs": n_bytes / (ingest_crc_ms / 1e3) / 1e9,
+            "ingest_crc_hbm_frac": n_bytes / (ingest_crc_ms / 1e3) / 1e9 / hbm_peak,
+            "reconstruct_stream_ms": recon_ms,
+            "e2e": {"value": wl.n_evt / e2e_s, "unit": "events/s", "h2d_bytes_per_step": n_bytes,
+                    "d2h_bytes_per_step": (hil.numel() + ste.numel()) * 4, "gbs": n_bytes / e2e_s / 1e9,
+                    "call": "H2D stream + rta_ingest (CRC) + rta_reconstruct_stream + D2H rows, "
+                            "next upload overlapped"}}
+
+
 def cam_codes(wl):
     codes = np.zeros(16, np.float32)
     for c, cam in wl.cams.items():
@@ -451,6 +558,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--train-events", type=int, default=24000)
     ap.add_argument("--serve-rates", default="0.5,2,8,inf", help="aggregate arrival rates, GB/s (inf: a burst)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -652,6 +760,11 @@ def main():
     h2d = wl.wave_bytes + wl.n_img * 12 + (wl.n_evt + 1) * 4
     d2h = wl.n_img * HILLAS_BYTES + wl.n_evt * STEREO_BYTES
 
+    # ---------------- the DL0 byte stream: ingest and the zero-copy reconstruction
+    stream_out = None
+    if not args.no_stream:
+        stream_out = stream_leg(ctx, wl, proc, stream, args.steps, e2e_steps, hil, ste)
+
     # ---------------- the learned path (setup: training) and the serving loop
     sur, trainer, serving, pool_info = None, None, None, None
     if not args.no_surrogate:
@@ -699,6 +812,7 @@ def main():
                     "call": "rta_reconstruct_host (pinned host bundle)"},
             "paths": {"geometric": {"ms_per_step": ms_per_step, "events_per_s": wl.n_evt / (ms_per_step / 1e3)},
                       "surrogate": sur},
+            "dl0_stream": stream_out,
             "serving": {"rates": serving, "pool": pool_info, "budget_gb": 24 * 1.073741824, "slots": 4,
                         "model": "surrogate" if trainer else "geometric"} if serving else None,
             "p99_bundle_latency_ms": next((r["p99_ms"] for r in serving if r["rate_gbs"] == 8.0), None)

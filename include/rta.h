@@ -427,6 +427,8 @@ typedef struct rta_segment_t {
  * its first valid packet (a header whose fixed fields hold and whose successor
  * also starts a valid header) and walks from there; the walks must join up.
  * verify_crc != 0 also checks every packet's CRC (reads every byte once).
+ * Capacities: d_seg seg_cap entries, d_img_seg img_cap + 1, d_img_tel img_cap,
+ * d_evt_off evt_cap + 1, d_evt_number and d_evt_time_ns (may be NULL) evt_cap.
  * d_counts (6 int64, device): n_segments, n_img, n_evt, n_samples, error code
  * (RTA_STREAM_*), byte offset of the first bad packet (-1). On an error the
  * directory is incomplete and RTA_DEV_BAD_STREAM is set in the status word.
@@ -439,9 +441,13 @@ int rta_ingest(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, int verif
 /* rta_reconstruct over an ingested stream, zero copy: the image kernel's bulk
  * copies read each chunk of pixels from the segment(s) that hold it. Counts are
  * read on the device (d_counts from rta_ingest: [1] images, [2] events), at
- * most max_img and max_evt. Stream-ordered, no host sync. */
+ * most max_img and max_evt; d_seg holds max_seg entries, d_img_seg max_img + 1.
+ * An image whose segments do not tile its pixels with 16-byte-aligned runs
+ * inside the stream is skipped (RTA_HF_BAD_INPUT). Stream-ordered, no host sync.
+ * d_hillas: max_img rows, d_stereo: max_evt rows. Grows the context's
+ * per-image workspace (an allocation) when max_img is larger than any before. */
 int rta_reconstruct_stream(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, const rta_segment_t* d_seg,
-                           const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
+                           int64_t max_seg, const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
                            const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_counts, int window_mode,
                            int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
                            rta_hillas_t* d_hillas, rta_stereo_t* d_stereo, void* stream);

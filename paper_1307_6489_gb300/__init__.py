@@ -112,6 +112,9 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_transient_search": ([P, i64, P, i32, i32, ctypes.c_double, P, i32, P], i32),
         "rta_significance_map": ([P, i64, Window, i32, P, P, P], i32),
         "rta_selftest_wait_timeout": ([P, i32, P, P], i32),
+        "rta_ingest": ([P, P, i64, i32, P, i64, P, P, i64, P, P, P, i64, P, P], i32),
+        "rta_reconstruct_stream": ([P, P, i64, P, i64, P, P, i64, P, i64, P, i32, i32, i32, f32, f32, i32, P, P, P],
+                                   i32),
         "rta_lut_accumulate": ([P, P, P, i64, P, i64, P, P, P, P, i32, P, i32, P, P], i32),
         "rta_lut_finalize": ([P, P, i64, i32, P, P], i32),
         "rta_lut_prepare": ([P, P, i64, P, P], i32),
@@ -364,6 +367,28 @@ def events_to_numpy(raw: np.ndarray) -> dict:
     return dict(log_energy=f[:, 0].copy(), dir_x=f[:, 1].copy(), dir_y=f[:, 2].copy(), gammaness=f[:, 3].copy(),
                 n_used=i[:, 4].copy(), flags=i[:, 5].view(np.uint32).copy(), base_x=f[:, 6].copy(),
                 base_y=f[:, 7].copy())
+
+
+RTA_DEV_BAD_STREAM = 4
+RTA_STREAM_OK, RTA_STREAM_FRAMING, RTA_STREAM_HEADER, RTA_STREAM_CAMERA, RTA_STREAM_SEGMENT, RTA_STREAM_CRC, \
+    RTA_STREAM_CAPACITY = range(7)
+SEGMENT_DTYPE = np.dtype([("offset", "<i8"), ("first_pixel", "<i4"), ("n_pixels", "<i4")])
+
+
+def rta_ingest(ctx, d_stream, n_bytes, verify_crc, d_seg, seg_cap, d_img_seg, d_img_tel, img_cap, d_evt_off,
+               d_evt_number, d_evt_time_ns, evt_cap, d_counts, stream=0):
+    """Directory of a device-resident DL0 byte stream (see include/rta.h); d_counts
+    (6 int64) receives n_segments, n_img, n_evt, n_samples, error, error offset."""
+    _check(load().rta_ingest(ctx, d_stream, n_bytes, int(verify_crc), d_seg, seg_cap, d_img_seg, d_img_tel, img_cap,
+                             d_evt_off, d_evt_number, d_evt_time_ns, evt_cap, d_counts, stream))
+
+
+def rta_reconstruct_stream(ctx, d_stream, n_bytes, d_seg, max_seg, d_img_seg, d_img_tel, max_img, d_evt_off, max_evt,
+                           d_counts, window_mode, start, W, t_hi, t_lo, core_needs_neighbour, d_hillas, d_stereo,
+                           stream=0):
+    _check(load().rta_reconstruct_stream(ctx, d_stream, n_bytes, d_seg, max_seg, d_img_seg, d_img_tel, max_img,
+                                         d_evt_off, max_evt, d_counts, window_mode, start, W, t_hi, t_lo,
+                                         int(core_needs_neighbour), d_hillas, d_stereo, stream))
 
 
 RTA_MAX_CAMS = 16

@@ -1,7 +1,7 @@
 // The unfused image-stage kernels (k_clean, k_hillas) and the host-side
 // launchers of the fused image kernel; the kernels themselves live in
-// k_image_chain.cuh, whose neighbour-peak instantiations are compiled in
-// k_image_nb.cu.
+// k_image_chain.cuh, whose neighbour-peak and byte-stream instantiations are
+// compiled in k_image_nb.cu and k_image_stream.cu.
 #include "k_image_chain.cuh"
 
 namespace rta {
@@ -157,14 +157,16 @@ static cudaError_t dispatch(int v, const ChainArgs& a, int grid, size_t smem, cu
 
 cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s) {
     if (a.pp.nbpeak) return dispatch_image_chain_nb(v, a, grid, smem, s, false, nullptr);
+    if (a.smeta) return dispatch_image_chain_stream(v, a, grid, smem, s, false, nullptr);
     return dispatch(v, a, grid, smem, s, false, nullptr);
 }
 
-int chain_occupancy(int v, size_t smem, int nb) {
+int chain_occupancy(int v, size_t smem, int kind) {
     int n = 0;
     ChainArgs dummy = {};
-    const cudaError_t e = nb ? dispatch_image_chain_nb(v, dummy, 0, smem, nullptr, true, &n)
-                             : dispatch(v, dummy, 0, smem, nullptr, true, &n);
+    const cudaError_t e = kind == CHAIN_NB       ? dispatch_image_chain_nb(v, dummy, 0, smem, nullptr, true, &n)
+                          : kind == CHAIN_STREAM ? dispatch_image_chain_stream(v, dummy, 0, smem, nullptr, true, &n)
+                                                 : dispatch(v, dummy, 0, smem, nullptr, true, &n);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;

@@ -34,11 +34,11 @@ struct StageHdr {
     int base;      // first pixel of the chunk
     int npix;      // pixels in the chunk
     int flags;     // HDR_*
-    int P, S, cam, pad;
+    int P, S, cam, seg0;  // seg0, seg1: the image's segments of a byte stream
     int64_t pix_off;
     int64_t woff;  // first sample of the image in the waveform buffer
     int64_t row;   // first calibration row of the image's telescope
-    int64_t pad2;
+    int seg1, pad;
 };
 
 
@@ -585,7 +585,14 @@ __device__ __forceinline__ void nb_pixel(const ChainArgs& a, const ProcParams& p
     }
     const int wst = int(0xFFFFFFFFu - uint32_t(best));
     const int Wr = pp.W;
-    const uint16_t* row = a.wave + h.woff + size_t(p) * h.S;       // global memory (L2)
+    const uint16_t* row;                                           // global memory (L2)
+    if (a.seg) {
+        int k = h.seg0;
+        while (k + 1 < h.seg1 && p >= a.seg[k].first_pixel + a.seg[k].n_pixels) ++k;
+        row = a.wave + a.seg[k].offset / 2 + size_t(p - a.seg[k].first_pixel) * h.S;
+    } else {
+        row = a.wave + h.woff + size_t(p) * h.S;
+    }
     int sum = 0;
     for (int j = 0; j < Wr; ++j) sum += __ldg(row + wst + j);
     const int p16 = __ldg(a.arr.p16 + h.row + p);
@@ -706,10 +713,46 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
     }
 }
 
+// The chunk's pixels [base, base + npix) of a byte-stream image from the
+// segment(s) that hold them (segment and chunk boundaries are multiples of 8
+// samples: 16-byte copies); seg is the segment to start looking at, returned
+// for the next chunk.
+static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, const StreamImg* m, int seg, int base,
+                                                     int npix, int S, unsigned char* buf, uint64_t* bar,
+                                                     uint64_t pol) {
+    int done = 0;
+    while (done < npix) {
+        int first, n;
+        long long off;
+        if (seg < STREAM_INLINE_SEGS) {
+            first = m->first[seg];
+            n = m->n[seg];
+            off = m->off[seg];
+        } else {
+            const rta_segment_t sg = a.seg[m->seg0 + seg];
+            first = sg.first_pixel;
+            n = sg.n_pixels;
+            off = sg.offset;
+        }
+        const int p0 = base + done;
+        if (p0 >= first + n) {
+            ++seg;
+            continue;
+        }
+        const int take = min(npix - done, first + n - p0);
+        bulk_g2s(buf + size_t(done) * S * 2, a.wave + off / 2 + size_t(p0 - first) * S,
+                 uint32_t(take) * uint32_t(S) * 2u, bar, pol);
+        done += take;
+    }
+    return seg;
+}
+
 // NB: the neighbour-peak window (keys and candidates in shared memory, a
-// candidate pass after each image); a separate instantiation, so that the other
-// window modes run the same code as without it.
-template <int IW, int PPT, int MB, bool NB>
+// candidate pass after each image). STREAM: a byte-stream bundle (per-image
+// records from k_stream_meta, chunks copied from the stream's segments). Each is
+// a separate instantiation, so that the contiguous path runs the same code as
+// without them.
+template <int IW, int PPT, int MB, bool NB, bool STREAM = false>
 __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
     constexpr int IT = IW * 32;          // integrator threads
     constexpr int CHUNK = IT * PPT;      // largest chunk in pixels
@@ -780,9 +823,34 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             pending &= ~(1u << s);
             return true;
         };
+        // the next image is taken, and its table entries loaded, while the current
+        // image's chunks are issued: neither the work counter's atomic nor those
+        // loads wait at an image boundary
+        constexpr bool stream_mode = STREAM;
+        int64_t next = atomicAdd(a.counter, 1u);
+        int next_tel = -1;
+        int64_t next_woff = 0;
+        int4 next_m0 = make_int4(0, 0, 0, 0), next_m1 = next_m0;     // a byte-stream image's record head
+        auto fetch_next = [&]() {
+            if (next >= n_img) return;
+            if (stream_mode) {
+                next_m0 = __ldg(reinterpret_cast<const int4*>(a.smeta + next));
+                next_m1 = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 1);
+            } else {
+                next_tel = a.img_tel[next];
+                next_woff = a.wave_off[next];
+            }
+        };
+        fetch_next();
         for (;;) {
-            const unsigned int img_u = atomicAdd(a.counter, 1u);
-            const int64_t img = img_u;
+            const int64_t img = next;
+            const int tel = next_tel;
+            const int64_t woff = next_woff;
+            const int4 m0 = next_m0, m1 = next_m1;
+            if (img < n_img) {
+                next = atomicAdd(a.counter, 1u);
+                fetch_next();
+            }
             if (img >= n_img) {
                 if (!acquire(stage, phase)) { ok = false; break; }
                 StageHdr h = {};
@@ -792,18 +860,37 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 mbar_arrive(&sm.full[stage]);
                 break;
             }
-            const int tel = a.img_tel[img];
-            const int64_t woff = a.wave_off[img];
-            bool bad = tel < 0 || tel >= a.arr.n_tel || woff < 0 || (woff & 7) != 0;
-            DevCam C = {};
+            bool bad;
+            int P, S, cam;
+            int64_t row;
             int64_t poff = 0;
-            if (!bad) {
-                C = a.arr.cams[a.arr.tel_cam[tel]];
-                bad = woff + int64_t(C.P) * C.S > a.n_wave;       // never read past the waveform buffer
-                if (a.integrate_only) {
-                    poff = a.pix_off[img];
-                    bad = bad || poff < 0 || poff + C.P > a.n_q;    // never write past q / t
+            int seg0 = 0, seg1 = 0;
+            if (stream_mode) {
+                // ok, cam, segments | calibration row, P, S (checked by k_stream_meta)
+                bad = m0.x == 0;
+                cam = m0.y;
+                seg0 = m0.w;
+                seg1 = m0.w + m0.z;
+                row = int64_t(uint32_t(m1.x)) | (int64_t(m1.y) << 32);
+                P = m1.z;
+                S = m1.w;
+            } else {
+                bad = tel < 0 || tel >= a.arr.n_tel || woff < 0 || (woff & 7) != 0;
+                cam = 0;
+                P = S = 0;
+                row = 0;
+                if (!bad) {
+                    cam = a.arr.tel_cam[tel];
+                    const DevCam C = a.arr.cams[cam];
+                    P = C.P;
+                    S = C.S;
+                    row = a.arr.tel_row[tel];
+                    bad = woff + int64_t(P) * S > a.n_wave;   // never read past the waveform buffer
                 }
+            }
+            if (!bad && a.integrate_only) {
+                poff = a.pix_off[img];
+                bad = poff < 0 || poff + P > a.n_q;            // never write past q / t
             }
             if (bad) {
                 if (!acquire(stage, phase)) { ok = false; break; }
@@ -815,10 +902,9 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 if (++stage == NST) { stage = 0; phase ^= 1u; }
                 continue;
             }
-            const int cam = a.arr.tel_cam[tel];
-            const int P = C.P, S = C.S, CP = chunk_pixels(CHUNK, a.stage_wave_bytes, S);
-            const int64_t row = a.arr.tel_row[tel];
+            const int CP = chunk_pixels(CHUNK, a.stage_wave_bytes, S);
             const uint16_t* src = a.wave + woff;
+            int cur_seg = 0;
             for (int base = 0; base < P; base += CP) {
                 if (!acquire(stage, phase)) { ok = false; break; }
                 const int npix = min(CP, P - base);
@@ -830,11 +916,12 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 h.P = P;
                 h.S = S;
                 h.cam = cam;
+                h.seg0 = seg0;
+                h.seg1 = seg1;
                 h.pad = 0;
                 h.pix_off = poff;
                 h.woff = woff;
                 h.row = row;
-                h.pad2 = 0;
                 sm.hdr[stage] = h;
                 const uint32_t wbytes = uint32_t(npix) * uint32_t(S) * 2u;     // multiple of 16 (P*S % 8 == 0)
                 const uint32_t cbytes = (uint32_t(npix) * 4u + 15u) & ~15u;
@@ -842,7 +929,12 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 mbar_arrive_expect_tx(&sm.full[stage], wbytes + 2u * cbytes);
                 // the neighbour-peak window reads its candidates' samples once more right
                 // after the image: keep the image in L2 until then
-                bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], NB ? pol_keep : pol_stream);
+                const uint64_t pol = NB ? pol_keep : pol_stream;
+                if (stream_mode) {
+                    cur_seg = stream_chunk_copy(a, a.smeta + img, cur_seg, base, npix, S, buf, &sm.full[stage], pol);
+                } else {
+                    bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], pol);
+                }
                 bulk_g2s(buf + a.stage_wave_bytes, a.arr.p16 + row + base, cbytes, &sm.full[stage], pol_keep);
                 bulk_g2s(buf + a.stage_wave_bytes + calib_bytes, a.arr.scale + row + base, cbytes, &sm.full[stage],
                          pol_keep);

@@ -1,14 +1,15 @@
 // The neighbour-peak instantiations of the fused image kernel (k_image_chain
-// with NB = true, k_image_chain.cuh), compiled apart from the other window
-// modes' instantiations so that the two build in parallel.
+// with NB = true, k_image_chain.cuh), for contiguous bundles and byte streams,
+// compiled apart from the other instantiations so that the builds run in
+// parallel.
 #include "k_image_chain.cuh"
 
 namespace rta {
 
-template <int IW, int PPT, int MB>
+template <int IW, int PPT, int MB, bool STREAM>
 static cudaError_t launch_nb(const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occupancy_only,
                              int* occ) {
-    auto kern = k_image_chain<IW, PPT, MB, true>;
+    auto kern = k_image_chain<IW, PPT, MB, true, STREAM>;
     // the dynamic shared-memory opt-in is per device; remember the largest size set
     static size_t attr_bytes[64] = {};
     int dev = 0;
@@ -29,12 +30,22 @@ static cudaError_t launch_nb(const ChainArgs& a, int grid, size_t smem, cudaStre
 // The same tile variants as the other window modes (kVariants in k_image.cu).
 cudaError_t dispatch_image_chain_nb(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
                                     int* occ) {
+    if (a.smeta) {          // a byte-stream bundle
+        switch (v) {
+        case 0: return launch_nb<8, 1, 2, true>(a, grid, smem, s, occ_only, occ);
+        case 1: return launch_nb<4, 2, 2, true>(a, grid, smem, s, occ_only, occ);
+        case 2: return launch_nb<8, 2, 2, true>(a, grid, smem, s, occ_only, occ);
+        case 3: return launch_nb<4, 1, 2, true>(a, grid, smem, s, occ_only, occ);
+        case 4: return launch_nb<8, 1, 3, true>(a, grid, smem, s, occ_only, occ);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (v) {
-    case 0: return launch_nb<8, 1, 2>(a, grid, smem, s, occ_only, occ);
-    case 1: return launch_nb<4, 2, 2>(a, grid, smem, s, occ_only, occ);
-    case 2: return launch_nb<8, 2, 2>(a, grid, smem, s, occ_only, occ);
-    case 3: return launch_nb<4, 1, 2>(a, grid, smem, s, occ_only, occ);
-    case 4: return launch_nb<8, 1, 3>(a, grid, smem, s, occ_only, occ);
+    case 0: return launch_nb<8, 1, 2, false>(a, grid, smem, s, occ_only, occ);
+    case 1: return launch_nb<4, 2, 2, false>(a, grid, smem, s, occ_only, occ);
+    case 2: return launch_nb<8, 2, 2, false>(a, grid, smem, s, occ_only, occ);
+    case 3: return launch_nb<4, 1, 2, false>(a, grid, smem, s, occ_only, occ);
+    case 4: return launch_nb<8, 1, 3, false>(a, grid, smem, s, occ_only, occ);
     default: return cudaErrorInvalidValue;
     }
 }

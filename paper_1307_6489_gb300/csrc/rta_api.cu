@@ -98,6 +98,12 @@ struct rta_ctx {
     int ctas_per_sm = 0;  // 0 = the variant's target, shrinking the stages to fit, else as many as fit
     int max_P = 0, max_S = 0;
     Slot slot[2];
+    // workspace of rta_ingest (pieces, packet list), grown on demand
+    void* d_ingest = nullptr;
+    size_t ingest_bytes = 0;
+    // per-image records of rta_reconstruct_stream, grown on demand
+    void* d_smeta = nullptr;
+    size_t smeta_bytes = 0;
     std::mutex host_mu;
 };
 
@@ -202,14 +208,17 @@ struct ChainCfg {
     int variant, nstage, ctas_per_sm;
 };
 
-int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_t* smem, int* swb, int nb = 0) {
+// kind: which instantiation (rta::CHAIN_*); the neighbour-peak one also needs its keys in shared memory
+int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_t* smem, int* swb,
+                  int kind = rta::CHAIN_PLAIN) {
+    const int nb = kind == rta::CHAIN_NB;
     if (k.variant < 0 || k.variant >= RTA_CHAIN_VARIANTS) return fail(RTA_E_INVALID, "variant %d", k.variant);
     const int nst = std::max(2, std::min(k.nstage, 8));
     *swb = rta::chain_stage_wave_bytes(k.variant, c->max_S);
     if (rta::chain_chunk_pixels(k.variant, *swb, c->max_S) < 32)
         return fail(RTA_E_INVALID, "tile variant %d has no room for %d samples", k.variant, c->max_S);
     *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P, nb);
-    int occ = rta::chain_occupancy(k.variant, *smem, nb);
+    int occ = rta::chain_occupancy(k.variant, *smem, kind);
     const int want = k.ctas_per_sm > 0 ? k.ctas_per_sm : rta::chain_variant_min_blocks(k.variant);
     if (occ < want) {
         // smaller stages (still at least 128 pixels of the longest camera per
@@ -217,7 +226,7 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
         for (int s2 = (*swb - 1024) & ~127; s2 >= 4096; s2 -= 1024) {
             if (rta::chain_chunk_pixels(k.variant, s2, c->max_S) < 128) break;
             const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P, nb);
-            const int occ2 = rta::chain_occupancy(k.variant, sm2, nb);
+            const int occ2 = rta::chain_occupancy(k.variant, sm2, kind);
             if (occ2 >= want) {
                 *swb = s2;
                 *smem = sm2;
@@ -237,19 +246,21 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
     return RTA_OK;
 }
 
-int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int* swb, int nb = 0) {
-    return config_launch(c, ChainCfg{c->variant, c->nstage, c->ctas_per_sm}, n_img, grid, smem, swb, nb);
+int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int* swb, int kind = rta::CHAIN_PLAIN) {
+    return config_launch(c, ChainCfg{c->variant, c->nstage, c->ctas_per_sm}, n_img, grid, smem, swb, kind);
 }
 
 int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
               const int64_t* d_pix_off, int64_t n_img, const rta::ProcParams& pp, float* d_q, float* d_t,
               int64_t n_q, rta_hillas_t* d_out, int integrate_only, cudaStream_t s, unsigned int* counter,
-              const int64_t* d_n_img = nullptr) {
+              const int64_t* d_n_img = nullptr, const rta_segment_t* d_seg = nullptr,
+              const int32_t* d_img_seg = nullptr, int64_t n_seg = 0, rta::StreamImg* d_smeta = nullptr) {
     int grid, swb;
     size_t smem;
-    int rc = chain_launch_config(c, n_img, &grid, &smem, &swb, pp.nbpeak);
+    const int kind = pp.nbpeak ? rta::CHAIN_NB : d_smeta ? rta::CHAIN_STREAM : rta::CHAIN_PLAIN;
+    int rc = chain_launch_config(c, n_img, &grid, &smem, &swb, kind);
     if (rc) return rc;
-    rta::ChainArgs a;
+    rta::ChainArgs a{};
     a.arr = dev_array(c);
     a.pp = pp;
     a.wave = d_wave;
@@ -269,6 +280,11 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.nstage = std::max(2, std::min(c->nstage, 8));
     a.integrate_only = integrate_only;
     a.n_img_dev = d_n_img;
+    a.seg = d_seg;
+    a.img_seg = d_img_seg;
+    a.n_seg = n_seg;
+    a.smeta = d_smeta;
+    if (d_smeta) CUDA_TRY(rta::launch_stream_meta(a, d_smeta, n_img, c->n_sm, s));
     CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
     CUDA_TRY(rta::launch_image_chain(c->variant, a, grid, smem, s));
     return RTA_OK;
@@ -398,6 +414,8 @@ int rta_destroy(rta_ctx* c) {
     }
     cudaFree(c->d_cams); cudaFree(c->d_tel_cam); cudaFree(c->d_tel_xy); cudaFree(c->d_tel_row);
     cudaFree(c->d_p16); cudaFree(c->d_scale); cudaFree(c->d_status); cudaFree(c->d_counters);
+    cudaFree(c->d_ingest);
+    cudaFree(c->d_smeta);
     delete c;
     return RTA_OK;
 }
@@ -580,7 +598,9 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
             for (int cps = 1; cps <= 4; ++cps) {
                 int g, swb;
                 size_t sm;
-                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb, pp.nbpeak) != RTA_OK) continue;
+                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb,
+                                  pp.nbpeak ? rta::CHAIN_NB : rta::CHAIN_PLAIN) != RTA_OK)
+                    continue;
                 c->variant = v;
                 c->nstage = nst;
                 c->ctas_per_sm = cps;
@@ -1041,4 +1061,106 @@ int rta_lut_reconstruct(rta_ctx* c, const rta_hillas_t* d_hillas, const int32_t*
     const int64_t g = std::min<int64_t>((n_evt + a.events_per_block - 1) / a.events_per_block, int64_t(c->n_sm) * 16);
     CUDA_TRY(rta::launch_lut_reconstruct(a, int(g), (cudaStream_t)stream));
     return RTA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DL0 byte-stream ingest (k_ingest.cu) and the zero-copy reconstruction
+// ---------------------------------------------------------------------------
+int rta_ingest(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes, int verify_crc, rta_segment_t* d_seg,
+               int64_t seg_cap, int32_t* d_img_seg, int32_t* d_img_tel, int64_t img_cap, int32_t* d_evt_off,
+               uint64_t* d_evt_number, int64_t* d_evt_time_ns, int64_t evt_cap, int64_t* d_counts, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c))) return rc;
+    if (n_bytes < 0 || seg_cap < 0 || img_cap < 0 || evt_cap < 0 || seg_cap > (int64_t(1) << 31) - 2 ||
+        img_cap > (int64_t(1) << 31) - 2 || evt_cap > (int64_t(1) << 31) - 2)
+        return fail(RTA_E_INVALID, "negative size or capacity above 2^31 - 2");
+    if (!d_counts || !d_seg || !d_img_seg || !d_img_tel || !d_evt_off || !d_evt_number || (n_bytes > 0 && !d_stream))
+        return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_stream) || !aligned16(d_seg)) return fail(RTA_E_ALIGN, "d_stream and d_seg must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_bytes == 0) {
+        // an empty stream is an empty directory
+        CUDA_TRY(cudaMemsetAsync(d_counts, 0, 6 * sizeof(int64_t), s));
+        const int64_t minus1 = -1;
+        CUDA_TRY(cudaMemcpyAsync(d_counts + 5, &minus1, sizeof minus1, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemsetAsync(d_img_seg, 0, sizeof(int32_t), s));
+        CUDA_TRY(cudaMemsetAsync(d_evt_off, 0, sizeof(int32_t), s));
+        return RTA_OK;
+    }
+    const int64_t nc = rta::ingest_chunks(n_bytes);
+    const int64_t max_pk = seg_cap + 1;
+    const int64_t n_blk = (max_pk + 1023) / 1024;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t b_chunks = up(sizeof(rta::IngChunk) * size_t(nc));
+    const size_t b_hdr = up(sizeof(rta::IngHdr));
+    const size_t b_off = up(sizeof(int64_t) * size_t(max_pk));
+    const size_t b_err = up(sizeof(int) * size_t(max_pk));
+    const size_t b_scan = up(sizeof(unsigned long long) * size_t(max_pk));
+    const size_t b_blk = up(sizeof(unsigned long long) * size_t(n_blk));
+    const size_t need = b_chunks + b_hdr + b_off + b_err + b_scan + b_blk;
+    if (need > c->ingest_bytes) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(c->d_ingest);
+        c->d_ingest = nullptr;
+        c->ingest_bytes = 0;
+        CUDA_TRY(cudaMalloc(&c->d_ingest, need));
+        c->ingest_bytes = need;
+    }
+    unsigned char* w = static_cast<unsigned char*>(c->d_ingest);
+    rta::IngestArgs a{};
+    a.arr = dev_array(c);
+    a.stream = d_stream;
+    a.n_bytes = n_bytes;
+    a.n_chunks = nc;
+    a.chunks = reinterpret_cast<rta::IngChunk*>(w);
+    a.hdr = reinterpret_cast<rta::IngHdr*>(w + b_chunks);
+    a.pk_off = reinterpret_cast<int64_t*>(w + b_chunks + b_hdr);
+    a.pk_err = reinterpret_cast<int*>(w + b_chunks + b_hdr + b_off);
+    a.pk_scan = reinterpret_cast<unsigned long long*>(w + b_chunks + b_hdr + b_off + b_err);
+    a.blk_sum = reinterpret_cast<unsigned long long*>(w + b_chunks + b_hdr + b_off + b_err + b_scan);
+    a.seg = d_seg;
+    a.seg_cap = seg_cap;
+    a.img_seg = d_img_seg;
+    a.img_tel = d_img_tel;
+    a.img_cap = img_cap;
+    a.evt_off = d_evt_off;
+    a.evt_number = d_evt_number;
+    a.evt_time = d_evt_time_ns;
+    a.evt_cap = evt_cap;
+    a.counts = d_counts;
+    a.status = c->d_status;
+    CUDA_TRY(rta::launch_ingest(a, verify_crc, c->n_sm, s));
+    return RTA_OK;
+}
+
+int rta_reconstruct_stream(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes, const rta_segment_t* d_seg,
+                           int64_t max_seg, const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
+                           const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_counts, int window_mode,
+                           int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                           rta_hillas_t* d_hillas, rta_stereo_t* d_stereo, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(max_img, "max_img")) || (rc = check_n(max_evt, "max_evt")))
+        return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (max_img == 0) return RTA_OK;
+    if (!d_stream || !d_seg || !d_img_seg || !d_img_tel || !d_counts || !d_hillas || (max_evt > 0 && (!d_evt_off || !d_stereo)))
+        return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_stream)) return fail(RTA_E_ALIGN, "d_stream is not 16-byte aligned");
+    if (n_bytes < 0 || max_seg < 1) return fail(RTA_E_INVALID, "bad stream size or segment capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
+    const size_t need = sizeof(rta::StreamImg) * size_t(max_img);
+    if (need > c->smeta_bytes) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(c->d_smeta);
+        c->d_smeta = nullptr;
+        c->smeta_bytes = 0;
+        CUDA_TRY(cudaMalloc(&c->d_smeta, need));
+        c->smeta_bytes = need;
+    }
+    rc = run_chain(c, reinterpret_cast<const uint16_t*>(d_stream), n_bytes / 2, nullptr, d_img_tel, nullptr, max_img,
+                   pp, nullptr, nullptr, 0, d_hillas, 0, s, nullptr, d_counts + 1, d_seg, d_img_seg, max_seg,
+                   static_cast<rta::StreamImg*>(c->d_smeta));
+    if (rc || max_evt == 0) return rc;
+    return run_stereo(c, d_hillas, d_img_tel, max_img, d_evt_off, max_evt, d_stereo, s, d_counts + 1, d_counts + 2);
 }

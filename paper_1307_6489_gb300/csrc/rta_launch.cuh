@@ -24,7 +24,28 @@ struct ChainArgs {
     int stage_wave_bytes;    // multiple of 128
     int nstage;
     int integrate_only;
+    // a byte-stream bundle (rta_ingest's directory): wave is the stream, wave_off unused;
+    // smeta: one prepared record per image (k_stream_meta)
+    const rta_segment_t* seg;
+    const int32_t* img_seg;
+    int64_t n_seg;
+    const struct StreamImg* smeta;
 };
+
+// One image of a byte stream as the image kernel's producer needs it: checked
+// once (its segments tile the camera's pixels with 16-byte-aligned runs inside
+// the stream) and read with two 16-byte loads at the image boundary; the first
+// STREAM_INLINE_SEGS segments inline, the rest from the directory.
+constexpr int STREAM_INLINE_SEGS = 4;
+struct StreamImg {
+    int ok, cam, nseg, seg0;
+    long long row;               // first calibration row of the telescope
+    int P, S;
+    int first[STREAM_INLINE_SEGS];
+    int n[STREAM_INLINE_SEGS];
+    long long off[STREAM_INLINE_SEGS];
+};
+cudaError_t launch_stream_meta(const ChainArgs& a, StreamImg* out, int64_t max_img, int n_sm, cudaStream_t s);
 
 struct CleanArgs {
     DevArray arr;
@@ -72,10 +93,14 @@ int chain_threads(int v);
 int chain_stage_wave_bytes(int v, int max_S);
 size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys = 0);
 int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
-int chain_occupancy(int v, size_t smem, int nb = 0);
-// the neighbour-peak instantiations (k_image_nb.cu)
+// which instantiation of the fused kernel a launch uses
+enum { CHAIN_PLAIN = 0, CHAIN_NB = 1, CHAIN_STREAM = 2 };
+int chain_occupancy(int v, size_t smem, int kind = CHAIN_PLAIN);
+// the neighbour-peak instantiations (k_image_nb.cu) and the byte-stream ones (k_image_stream.cu)
 cudaError_t dispatch_image_chain_nb(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
                                     int* occ);
+cudaError_t dispatch_image_chain_stream(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s,
+                                        bool occ_only, int* occ);
 int chain_variant_min_blocks(int v);
 int stereo_events_per_block();
 cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s);
@@ -109,6 +134,48 @@ struct TransientArgs {
 cudaError_t launch_transient(const TransientArgs& t, cudaStream_t s);
 cudaError_t launch_skymap_sum(const unsigned int* slabs, unsigned long long use, unsigned int* out, cudaStream_t s);
 cudaError_t launch_stereo_to_events(const rta_stereo_t* st, int64_t n_evt, rta_event_t* ev, cudaStream_t s);
+// DL0 byte-stream ingest (k_ingest.cu).
+struct IngChunk {            // one 1 MiB piece of the stream
+    long long first;         // its first packet (-1: none found)
+    long long end;           // where its walk stopped (>= the piece's end, or a fault)
+    long long base;          // packets in the pieces before it
+    long long err_pos;
+    int count;               // packets that start in it
+    int err;
+};
+struct IngHdr {
+    long long n_pk;          // packets on the chain (before a framing fault)
+    long long first_bad_pk;  // earliest packet with a fault
+    long long walk_err_pos;
+    int walk_err;
+    int error;
+};
+struct IngestArgs {
+    DevArray arr;
+    const uint8_t* stream;
+    int64_t n_bytes;
+    int64_t n_chunks;
+    IngChunk* chunks;
+    IngHdr* hdr;
+    int64_t* pk_off;             // seg_cap + 1
+    int* pk_err;
+    unsigned long long* pk_scan;
+    unsigned long long* blk_sum;
+    rta_segment_t* seg;
+    int64_t seg_cap;
+    int32_t* img_seg;
+    int32_t* img_tel;
+    int64_t img_cap;
+    int32_t* evt_off;
+    uint64_t* evt_number;
+    int64_t* evt_time;
+    int64_t evt_cap;
+    int64_t* counts;
+    unsigned int* status;
+};
+int64_t ingest_chunks(int64_t n_bytes);
+cudaError_t launch_ingest(const IngestArgs& a, int verify_crc, int n_sm, cudaStream_t s);
+
 // Lookup-table reconstruction and its training sums (k_lut.cu).
 struct LutArgs {
     DevArray arr;

@@ -156,7 +156,7 @@ extern "C" int rta_image_chain_noalloc(const rta_camera_desc_t* h_cams, int n_ca
     NA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     int64_t grid = int64_t(n_sm) * occ;
     if (grid > n_img) grid = n_img;
-    rta::ChainArgs a;
+    rta::ChainArgs a{};
     memset(&a, 0, sizeof a);
     a.arr.cams = reinterpret_cast<const rta::DevCam*>(scratch + kCamWord);
     a.arr.tel_cam = reinterpret_cast<const int32_t*>(scratch + kTelCamWord);
