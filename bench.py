@@ -760,11 +760,6 @@ def main():
     h2d = wl.wave_bytes + wl.n_img * 12 + (wl.n_evt + 1) * 4
     d2h = wl.n_img * HILLAS_BYTES + wl.n_evt * STEREO_BYTES
 
-    # ---------------- the DL0 byte stream: ingest and the zero-copy reconstruction
-    stream_out = None
-    if not args.no_stream:
-        stream_out = stream_leg(ctx, wl, proc, stream, args.steps, e2e_steps, hil, ste)
-
     # ---------------- the learned path (setup: training) and the serving loop
     sur, trainer, serving, pool_info = None, None, None, None
     if not args.no_surrogate:
@@ -776,6 +771,13 @@ def main():
                                          args.serve_seconds)
     if trainer:
         trainer.close()
+
+    # ---------------- the DL0 byte stream: ingest and the zero-copy reconstruction (last:
+    # its pinned and device copies of the stream stay out of the serving measurement)
+    stream_out = None
+    if not args.no_stream:
+        stream_out = stream_leg(ctx, wl, proc, stream, args.steps, e2e_steps, hil, ste)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
