@@ -107,6 +107,30 @@ def dist_setup():
     return ws, rank, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank reconstructs its own bundle: the generator's seed of rank r."""
+    import synth
+    return synth.BASE_SEED + 2 + 1000 * rank
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest value over all ranks (a step time, so that the slowest rank
+    sets the job's time); x itself when there is one rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank has its own bundle of the same size)."""
+    return units_per_rank * ws / seconds
+
+
 def make_bundle(n_events: int, seed: int, pinned: bool):
     import synth
     import torch
@@ -579,8 +603,7 @@ def main():
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    seed = synth.BASE_SEED + 2 + 1000 * rank
-    wl, host = make_bundle(args.events, seed, pinned=True)
+    wl, host = make_bundle(args.events, rank_seed(rank), pinned=True)
     wave_h = host.numpy().view(np.uint16)
 
     ctx = rta.Context(local, hbm_budget_bytes=8 << 30)
@@ -655,13 +678,10 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     chain_ms = [a.elapsed_time(b) for a, b, _ in ev]
     stereo_ms = [b.elapsed_time(c) for _, b, c in ev]
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, dev)
     ms_per_step = total_ms / args.steps
     events_all = wl.n_evt * ws
-    value = events_all / (ms_per_step / 1e3)
+    value = job_rate(wl.n_evt, ws, ms_per_step / 1e3)
 
     # ---------------- the same step launched as one CUDA graph (captured at capacity)
     n_img_d = torch.tensor([wl.n_img], dtype=torch.int64, device=dev)
@@ -751,11 +771,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.reconstruct_host(wave_h, woff, itel, eoff, *proc, hh, hs)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws, dev)
     assert np.array_equal(hh.view(np.uint32), hil.cpu().numpy().view(np.uint32)), "host path differs"
     h2d = wl.wave_bytes + wl.n_img * 12 + (wl.n_evt + 1) * 4
     d2h = wl.n_img * HILLAS_BYTES + wl.n_evt * STEREO_BYTES
