@@ -237,8 +237,11 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
     }
     if (occ < 1) return fail(RTA_E_INVALID, "image kernel does not fit: %zu bytes of shared memory", *smem);
     if (k.ctas_per_sm > 0) {
-        if (occ < k.ctas_per_sm) return fail(RTA_E_INVALID, "%d CTAs/SM do not fit (%d do)", k.ctas_per_sm, occ);
-        occ = k.ctas_per_sm;
+        // a count set (or tuned) for the plain kernel is a ceiling for the other
+        // instantiations, whose shared memory or registers may allow fewer
+        if (occ < k.ctas_per_sm && kind == rta::CHAIN_PLAIN)
+            return fail(RTA_E_INVALID, "%d CTAs/SM do not fit (%d do)", k.ctas_per_sm, occ);
+        occ = std::min(occ, k.ctas_per_sm);
     }
     int64_t g = int64_t(c->n_sm) * occ;
     g = std::min<int64_t>(g, std::max<int64_t>(n_img, 1));

@@ -137,3 +137,21 @@ def test_calibration_scales_must_be_finite_and_positive():
         assert e.value.code == rta.RTA_E_INVALID
     ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
     ctx.close()
+
+
+def test_a_cta_count_tuned_for_the_plain_kernel_does_not_block_the_neighbour_peak_window(nset):
+    """The autotuner may pin 3 CTAs per SM for the plain kernel; the
+    neighbour-peak kernel (more shared memory) runs with as many as fit."""
+    name, wl, ref, ctx, dev = nset
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    default = ctx.chain_config()
+    base = dev.hillas_buf()
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, base)
+    out = dev.hillas_buf()
+    try:
+        ctx.set_chain_config(4, 2, 3)
+        ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, out)
+        assert ctx.check() == 0
+    finally:
+        ctx.set_chain_config(default["variant"], default["n_stages"], 0)
+    assert torch.equal(out, base)
