@@ -153,19 +153,24 @@ __device__ __forceinline__ bool max_window6_packed(const uint16_t* row, int& M) 
     uint32_t P[NW - 1];
 #pragma unroll
     for (int j = 0; j < NW - 1; ++j) P[j] = u[j] + __byte_perm(u[j], u[j + 1], 0x5432);
-    // every word (its high lane orders it: all values < 2^31) and every word
-    // shifted up by one lane into one three-input max tree
-    int m[2 * JQ];
+    // the window words, reduced lane by lane with the three-input 16x2 maximum
+    // (both lanes at once; masked lanes are 0 and every sum is >= 0), then the
+    // larger of the two lanes
+    uint32_t m[JQ];
 #pragma unroll
     for (int j = 0; j < JQ; ++j) {
         uint32_t q = P[j] + P[j + 1] + P[j + 2];  // lanes: windows (2j + 1 : 2j), or (2j : 2j - 1) for odd rows
         const bool lo_ok = odd ? (j >= 1 && 2 * j <= NK) : (2 * j <= NK - 1);
         const bool hi_ok = odd ? (2 * j <= NK - 1) : (2 * j + 1 <= NK - 1);
         q &= (hi_ok ? 0xFFFF0000u : 0u) | (lo_ok ? 0xFFFFu : 0u);
-        m[2 * j] = int(q);
-        m[2 * j + 1] = int(q << 16);
+        m[j] = q;
     }
-    M = tree_max(m) >> 16;
+#pragma unroll
+    for (int step = 1; step < JQ; step *= 3)
+#pragma unroll
+        for (int i = 0; i + step < JQ; i += 3 * step)
+            m[i] = __vimax3_u16x2(m[i], m[i + step], i + 2 * step < JQ ? m[i + 2 * step] : 0u);
+    M = int(max(m[0] >> 16, m[0] & 0xFFFFu));
     return true;
 }
 
