@@ -290,90 +290,106 @@ __device__ __forceinline__ uint32_t gf_pow(uint32_t b, int e) {
     return r;
 }
 
-constexpr int CRC_CHAINS = 4;                     // independent chains per lane
 constexpr int CRC_X16 = RTA_PKT_MAX_BYTES / 16 + 1;
+constexpr int CRC_THREADS = 1024;                 // one CTA per SM (the lane tables fill most of its shared memory)
+constexpr int CRC_STRIDE_WORDS = 32;             // a lane's 16-byte words are this far apart
+constexpr size_t CRC_LANE_TABLE_BYTES = size_t(6) * 256 * 32 * 4;
+constexpr size_t CRC_SMEM_BYTES =
+    CRC_LANE_TABLE_BYTES + 2 * (size_t(6) * 256 + CRC_X16 + 64 + CRC_X16 / 64 + 1);
+static_assert(CRC_SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 
 }  // namespace
 
 // One warp per packet. For a correct packet, running the CRC register over all
 // L bytes -- the CRC field included, most significant byte first -- ends at 0
 // (the register after the message equals the field, and two bytes equal to the
-// register clear it), so every piece boundary is a multiple of 16 bytes. Each
-// lane takes 4 consecutive pieces of the packet, one CRC chain each (register
-// starting at 0, four bytes a step through four lookup tables); a chain's value
-// is carried to the packet's end by x^(8 k) modulo the generator, k the bytes
-// after the piece, taken from a table over multiples of 16 bytes; the preset
-// register 0xFFFF is carried likewise; the XOR of all of it must be 0.
-__global__ void __launch_bounds__(256) k_pkt_crc(const IngestArgs a) {
-    __shared__ uint16_t T[4][256];
-    __shared__ uint16_t X16[CRC_X16];      // x^(128 k) mod G
-    __shared__ uint16_t A[64], B[CRC_X16 / 64 + 1];
+// register clear it). The register is linear in the message, so the packet's
+// 16-byte words can be taken in any grouping: lane l takes words l, l + 32, ...
+// (the warp reads 512 contiguous bytes a step), forms each word's CRC from a zero
+// register (four bytes a step through four lookup tables) and folds it into its
+// own register, which is carried over the 512-byte stride between its words by
+// two more tables (multiplication by x^4096 modulo the generator). At the end
+// each lane's register is carried to the packet's end by x^(8 k), k the bytes
+// after its last word, from a table over multiples of 16 bytes; the preset
+// register 0xFFFF is carried likewise; the XOR of all of it must be 0. Every
+// lane has its own copy of the tables in shared memory, so a warp's lookups hit
+// 32 different banks.
+__global__ void __launch_bounds__(CRC_THREADS, 1) k_pkt_crc(const IngestArgs a) {
+    extern __shared__ __align__(16) unsigned char crc_smem[];
+    uint32_t* Tl = reinterpret_cast<uint32_t*>(crc_smem);                       // [6][256][32]
+    uint16_t* T = reinterpret_cast<uint16_t*>(crc_smem + CRC_LANE_TABLE_BYTES); // [6][256]
+    uint16_t* X16 = T + 6 * 256;                                                // x^(128 k) mod G
+    uint16_t* A = X16 + CRC_X16;
+    uint16_t* B = A + 64;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         uint32_t r = uint32_t(i) << 8;
         for (int k = 0; k < 8; ++k) r = (r & 0x8000u) ? ((r << 1) ^ 0x1021u) : (r << 1);
-        T[0][i] = uint16_t(r);
+        T[i] = uint16_t(r);
     }
     const uint32_t x128 = gf_pow(2u, 128);          // x^128 = 16 zero bytes
     if (threadIdx.x < 64) A[threadIdx.x] = uint16_t(gf_pow(x128, threadIdx.x));
     if (threadIdx.x < CRC_X16 / 64 + 1) B[threadIdx.x] = uint16_t(gf_pow(gf_pow(x128, 64), threadIdx.x));
     __syncthreads();
+    const uint32_t K = gf_pow(2u, 8 * 16 * CRC_STRIDE_WORDS);     // one lane's stride: 32 words
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         // T[k][x]: byte x followed by k zero bytes, register starting at zero
-        uint32_t r = T[0][i];
+        uint32_t r = T[i];
         for (int k = 1; k < 4; ++k) {
-            r = ((r << 8) & 0xFFFFu) ^ T[0][(r >> 8) & 0xFFu];
-            T[k][i] = uint16_t(r);
+            r = ((r << 8) & 0xFFFFu) ^ T[(r >> 8) & 0xFFu];
+            T[k * 256 + i] = uint16_t(r);
         }
+        // register (x : 0) and (0 : x) carried over one lane stride of zero bytes
+        T[4 * 256 + i] = uint16_t(gf_mulmod(uint32_t(i) << 8, K));
+        T[5 * 256 + i] = uint16_t(gf_mulmod(uint32_t(i), K));
     }
     for (int k = threadIdx.x; k < CRC_X16; k += blockDim.x) X16[k] = uint16_t(gf_mulmod(A[k & 63], B[k >> 6]));
     __syncthreads();
+    // one copy of the six tables per lane, entry (k, x) of lane l in word
+    // (256 k + x) * 32 + l: every lookup of a warp hits 32 different banks
+    for (int w = threadIdx.x; w < 6 * 256 * 32; w += blockDim.x) Tl[w] = T[w >> 5];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
+    const uint32_t* L0 = Tl + lane;
+    const uint32_t* L1 = L0 + 256 * 32;
+    const uint32_t* L2 = L0 + 512 * 32;
+    const uint32_t* L3 = L0 + 768 * 32;
+    const uint32_t* ZH = L0 + 1024 * 32;
+    const uint32_t* ZL = L0 + 1280 * 32;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     const int64_t n = a.hdr->n_pk < a.seg_cap + 1 ? a.hdr->n_pk : a.seg_cap + 1;
     for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps) {
         const int64_t pos = a.pk_off[k];
-        const uint8_t* p = a.stream + pos;
+        const uint4* p = reinterpret_cast<const uint4*>(a.stream + pos);
         PktFields f;
         pkt_check(a.stream, pos, a.n_bytes, a.arr, f);
         const int L = f.length;                           // multiple of 16
         const int words = L >> 4;
-        const int per = (words + 32 * CRC_CHAINS - 1) / (32 * CRC_CHAINS);   // 16-byte words per chain
-        uint32_t r[CRC_CHAINS];
-        int s0[CRC_CHAINS], s1[CRC_CHAINS];
+        // lane l takes words l, l + 32, ...: one coalesced 512-byte load per warp and
+        // step, issued one step ahead. Its register r covers its words with zeros
+        // between them: r <- r x^(8 * 512) + CRC_0(word), the word's own CRC from a
+        // zero register.
+        uint32_t r = 0;
+        int w = lane;
+        uint4 qn = w < words ? __ldg(p + w) : make_uint4(0, 0, 0, 0);
+        int last = -1;
+        for (; w < words; w += CRC_STRIDE_WORDS) {
+            const uint4 q = qn;
+            if (w + CRC_STRIDE_WORDS < words) qn = __ldg(p + w + CRC_STRIDE_WORDS);
+            const uint32_t ws[4] = {q.x, q.y, q.z, q.w};
+            uint32_t c = 0;
 #pragma unroll
-        for (int c = 0; c < CRC_CHAINS; ++c) {
-            r[c] = 0;
-            const int w0 = (lane * CRC_CHAINS + c) * per;
-            s0[c] = min(words, w0) * 16;
-            s1[c] = min(words, w0 + per) * 16;
-        }
-        for (int i = 0; i < per * 16; i += 16) {
-            // one 16-byte load per chain and step (the lanes' pieces are far apart,
-            // so narrower loads would fetch every sector several times)
-            uint4 q[CRC_CHAINS];
-#pragma unroll
-            for (int c = 0; c < CRC_CHAINS; ++c)
-                q[c] = s0[c] + i < s1[c] ? __ldg(reinterpret_cast<const uint4*>(p + s0[c] + i))
-                                         : make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int c = 0; c < CRC_CHAINS; ++c) {
-                if (s0[c] + i < s1[c]) {
-                    const uint32_t ws[4] = {q[c].x, q[c].y, q[c].z, q[c].w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t w = ws[j];
-                        const uint32_t b0 = w & 0xFF, b1 = (w >> 8) & 0xFF, b2 = (w >> 16) & 0xFF, b3 = w >> 24;
-                        const uint32_t u = r[c] ^ ((b0 << 8) | b1);
-                        r[c] = uint32_t(T[3][u >> 8]) ^ T[2][u & 0xFF] ^ T[1][b2] ^ T[0][b3];
-                    }
-                }
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = ws[j];
+                const uint32_t b0 = x & 0xFF, b1 = (x >> 8) & 0xFF, b2 = (x >> 16) & 0xFF, b3 = x >> 24;
+                const uint32_t u = c ^ ((b0 << 8) | b1);
+                c = L3[(u >> 8) << 5] ^ L2[(u & 0xFF) << 5] ^ L1[b2 << 5] ^ L0[b3 << 5];
             }
+            r = ZH[(r >> 8) << 5] ^ ZL[(r & 0xFF) << 5] ^ c;
+            last = w;
         }
-        uint32_t v = 0;
-#pragma unroll
-        for (int c = 0; c < CRC_CHAINS; ++c)
-            if (s1[c] > s0[c]) v ^= gf_mulmod(r[c], X16[(L - s1[c]) >> 4]);
-        if (lane == 0) v ^= gf_mulmod(0xFFFFu, X16[L >> 4]);       // the preset register
+        // carried to the packet's end; the preset register 0xFFFF likewise
+        uint32_t v = last >= 0 ? gf_mulmod(r, X16[words - 1 - last]) : 0u;
+        if (lane == 0) v ^= gf_mulmod(0xFFFFu, X16[words]);
         for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0 && v != 0 && a.pk_err[k] == 0) a.pk_err[k] = RTA_STREAM_CRC;
     }
@@ -577,7 +593,20 @@ cudaError_t launch_ingest(const IngestArgs& a, int verify_crc, int n_sm, cudaStr
     k_frame_list<<<unsigned(nc), 32, 0, s>>>(a);
     const int g = int(std::min<int64_t>((max_pk + 255) / 256, int64_t(n_sm) * 8));
     k_pkt_check<<<g, 256, 0, s>>>(a);
-    if (verify_crc) k_pkt_crc<<<int(std::min<int64_t>((max_pk + 7) / 8, int64_t(n_sm) * 4)), 256, 0, s>>>(a);
+    if (verify_crc) {
+        // the dynamic shared-memory opt-in is per device
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+            if ((e = cudaFuncSetAttribute(k_pkt_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(CRC_SMEM_BYTES))) !=
+                cudaSuccess)
+                return e;
+            if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        }
+        const int64_t wpb = CRC_THREADS / 32;
+        k_pkt_crc<<<int(std::min<int64_t>((max_pk + wpb - 1) / wpb, int64_t(n_sm))), CRC_THREADS, CRC_SMEM_BYTES, s>>>(a);
+    }
     k_pkt_scan_local<<<unsigned(n_blk), 1024, 0, s>>>(a);
     k_pkt_scan_blocks<<<1, 1024, 0, s>>>(a, n_blk);
     k_pkt_final<<<unsigned(n_blk), 1024, 0, s>>>(a);
