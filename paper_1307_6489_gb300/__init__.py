@@ -538,14 +538,16 @@ def rta_stream_destroy(stream: int):
 
 
 def rta_transient_search(stream: int, now_ns: int, windows, radius_bins: int, s_min: float,
-                         max_alerts: int = 65536) -> np.ndarray:
-    """Alerts (ALERT_DTYPE rows sorted by window, iy, ix) of the windows [(on_s, off_s), ...]."""
+                         max_alerts: int = 65536, with_total: bool = False):
+    """Alerts (ALERT_DTYPE rows sorted by window, iy, ix) of the windows [(on_s, off_s), ...]; the
+    first max_alerts of them, and with with_total=True also the number found (which may be larger)."""
     w = np.ascontiguousarray(np.asarray(windows, np.int32).reshape(-1, 2))
     out = np.zeros(max(max_alerts, 1), ALERT_DTYPE)
     n = ctypes.c_int(0)
     _check(load().rta_transient_search(stream, now_ns, w.ctypes.data_as(ctypes.c_void_p), len(w), radius_bins,
                                        float(s_min), out.ctypes.data_as(ctypes.c_void_p), max_alerts, ctypes.byref(n)))
-    return out[: min(n.value, max_alerts)].copy()
+    rows = out[: min(n.value, max_alerts)].copy()
+    return (rows, int(n.value)) if with_total else rows
 
 
 def rta_significance_map(stream: int, now_ns: int, window, radius_bins: int):

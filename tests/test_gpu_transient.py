@@ -96,6 +96,10 @@ def test_alerts_match_the_oracle_and_find_the_flares(sky):
     # a cap on the number returned keeps the first ones in order
     few = rta.rta_transient_search(st, NOW_S * 1_000_000_000 + 999, WINDOWS, RADIUS, S_MIN, max_alerts=3)
     assert len(few) == min(3, len(got)) and (few == got[: len(few)]).all()
+    # ... and the number found is still the full count
+    few, n_found = rta.rta_transient_search(st, NOW_S * 1_000_000_000 + 999, WINDOWS, RADIUS, S_MIN, max_alerts=3,
+                                            with_total=True)
+    assert n_found == len(got) and len(few) == min(3, len(got))
 
 
 def test_windows_outside_the_rings_are_refused(sky):
