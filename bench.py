@@ -482,17 +482,31 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
     out = []
     try:
         for rate in rates:
-            sched, total, t = [], 0, time.monotonic_ns() + 50_000_000
+            sched, total, t_start = [], 0, time.monotonic_ns() + 50_000_000
             if rate == float("inf"):      # capacity: a burst of 24 bundles arriving together
                 for _ in range(24):
                     b = pool[int(rng.integers(len(pool)))]
-                    sched.append((t, b))
+                    sched.append((t_start, b))
                     total += b["bytes"]
-            while rate != float("inf") and total < rate * 1e9 * duration_s:
-                b = pool[int(rng.integers(len(pool)))]
-                t += int(rng.exponential(b["bytes"] / (rate * 1e9)) * 1e9)
-                sched.append((t, b))
-                total += b["bytes"]
+            else:
+                # Poisson arrivals (exponential gaps, each with the mean its bundle's bytes
+                # give at this rate), the gaps then scaled by one factor so that the
+                # schedule offers exactly `rate`: its bytes over the time from the start
+                # to the last arrival
+                picks, gaps = [], []
+                # at least 8 arrivals, so that the low rates' percentiles are not those of one or two
+                mean_b = sum(b["bytes"] for b in pool) / len(pool)
+                dur = max(duration_s, 8 * mean_b / (rate * 1e9))
+                while total < rate * 1e9 * dur:
+                    b = pool[int(rng.integers(len(pool)))]
+                    gaps.append(rng.exponential(b["bytes"] / (rate * 1e9)))
+                    picks.append(b)
+                    total += b["bytes"]
+                scale = (total / (rate * 1e9)) / sum(gaps)
+                t = float(t_start)
+                for b, g in zip(picks, gaps):
+                    t += g * scale * 1e9
+                    sched.append((int(t), b))
             ev_all = torch.empty(sum(b["n_evt"] for _, b in sched) * 32, dtype=torch.uint8, pin_memory=True)
             ev_np = ev_all.numpy()
             pos, structs, tickets, arr = 0, [], [], []
@@ -516,10 +530,10 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
                             done[j] = d
                 time.sleep(0.0002)
             lat = np.array([(done[j] - arr[j]) / 1e6 for j in range(len(sched))])
-            span = (max(done.values()) - arr[0]) / 1e9
+            span = (max(done.values()) - t_start) / 1e9
             out.append({"rate_gbs": rate if rate != float("inf") else "burst", "bundles": len(sched),
                         "bytes": int(total),
-                        "offered_gbs": (total / ((arr[-1] - arr[0]) / 1e9) / 1e9) if arr[-1] > arr[0] else None,
+                        "offered_gbs": (total / ((arr[-1] - t_start) / 1e9) / 1e9) if arr[-1] > t_start else None,
                         "sustained_gbs": total / span / 1e9, "p50_ms": float(np.percentile(lat, 50)),
                         "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())})
         # transient search over the sky map the stream has just filled: 1 s .. 30 min windows
@@ -729,11 +743,15 @@ def main():
         filt_ms = f0.elapsed_time(f1) / args.steps
         ctx.check(sp)
 
-    # ---------------- the neighbour-peak window on the same bundle (image kernel alone; reads each image twice)
+    # ---------------- the neighbour-peak window on the same bundle (image kernel alone; its own
+    # launch configuration, tuned by the autotuner in this mode outside the timed region)
     nbp_ms = None
     if proc[0] != rta.RTA_WINDOW_FIXED:
         nproc = (rta.RTA_WINDOW_NEIGHBOUR,) + tuple(proc[1:])
         nhil = torch.empty_like(hil)
+        if not args.no_autotune and not args.chain:
+            rta.rta_autotune(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *nproc,
+                             nhil.data_ptr(), reps=2, stream=sp)
         for _ in range(3):
             rta.rta_image_chain(h, wave.data_ptr(), nw, wave_off.data_ptr(), img_tel.data_ptr(), wl.n_img, *nproc,
                                 nhil.data_ptr(), sp)

@@ -186,12 +186,15 @@ int rta_selftest_wait_timeout(rta_ctx* ctx, int timeout_ms, uint64_t* waited_ns,
  * calls built on it). variant selects the tile shape (rta_chain_variant_info:
  * integrator warps per CTA and pixels per thread), n_stages the shared-memory
  * pipeline depth (2..8), ctas_per_sm the resident CTAs per SM (0 = as many as
- * fit). Returns RTA_E_INVALID if the combination does not fit in shared memory
- * for the registered cameras. Results do not depend on the configuration. */
+ * fit). Sets the configuration of every window mode, the neighbour-peak
+ * window's included (whose kernel runs with as many of the CTAs as fit).
+ * Returns RTA_E_INVALID if the combination does not fit in shared memory for
+ * the registered cameras. Results do not depend on the configuration. */
 int rta_set_chain_config(rta_ctx* ctx, int variant, int n_stages, int ctas_per_sm);
 
-/* The configuration a launch would use now: variant, stages, CTAs per SM, grid
- * size and dynamic shared memory per CTA in bytes (NULL outputs are skipped). */
+/* The configuration a launch outside the neighbour-peak mode would use now:
+ * variant, stages, CTAs per SM, grid size and dynamic shared memory per CTA in
+ * bytes (NULL outputs are skipped). */
 int rta_get_chain_config(rta_ctx* ctx, int* variant, int* n_stages, int* ctas_per_sm, int* grid,
                          size_t* smem_bytes);
 
@@ -221,8 +224,11 @@ typedef struct rta_tune_entry_t {
  * every configuration that fits (variant x 2..6 stages x 1..4 CTAs/SM), `reps`
  * timed launches each (CUDA events on `stream`), keeps the fastest in the
  * context and reports every measurement in h_entries (up to max_entries;
- * *n_entries = number measured). d_out receives the (configuration-independent)
- * Hillas rows. Synchronises `stream`. */
+ * *n_entries = number measured). The neighbour-peak window
+ * (RTA_WINDOW_NEIGHBOUR) has a configuration of its own, which a call in that
+ * mode tunes; a call in any other mode tunes the configuration all other modes
+ * share. d_out receives the (configuration-independent) Hillas rows.
+ * Synchronises `stream`. */
 int rta_autotune(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
                  const int32_t* d_img_tel, int64_t n_img, int window_mode, int start, int W, float t_hi,
                  float t_lo, int core_needs_neighbour, rta_hillas_t* d_out, int reps, rta_tune_entry_t* h_entries,

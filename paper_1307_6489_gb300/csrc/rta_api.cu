@@ -96,6 +96,11 @@ struct rta_ctx {
     int variant = 4;      // tile shape, see chain_variant_* (the fastest on GB300 for the array cameras)
     int nstage = 2;
     int ctas_per_sm = 0;  // 0 = the variant's target, shrinking the stages to fit, else as many as fit
+    // the neighbour-peak kernel's own configuration (more shared memory per CTA,
+    // a per-image barrier: its fastest shape differs)
+    int nb_variant = 0;
+    int nb_nstage = 3;
+    int nb_ctas_per_sm = 0;
     int max_P = 0, max_S = 0;
     Slot slot[2];
     // workspace of rta_ingest (pieces, packet list), grown on demand
@@ -249,8 +254,15 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
     return RTA_OK;
 }
 
+// The configuration the kernel of `kind` runs with: the neighbour-peak kernel has
+// its own, the others share the plain kernel's.
+ChainCfg cfg_of(const rta_ctx* c, int kind) {
+    if (kind == rta::CHAIN_NB) return ChainCfg{c->nb_variant, c->nb_nstage, c->nb_ctas_per_sm};
+    return ChainCfg{c->variant, c->nstage, c->ctas_per_sm};
+}
+
 int chain_launch_config(rta_ctx* c, int64_t n_img, int* grid, size_t* smem, int* swb, int kind = rta::CHAIN_PLAIN) {
-    return config_launch(c, ChainCfg{c->variant, c->nstage, c->ctas_per_sm}, n_img, grid, smem, swb, kind);
+    return config_launch(c, cfg_of(c, kind), n_img, grid, smem, swb, kind);
 }
 
 int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
@@ -280,7 +292,8 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.counter = counter ? counter : take_counter(c);
     a.status = c->d_status;
     a.stage_wave_bytes = swb;
-    a.nstage = std::max(2, std::min(c->nstage, 8));
+    const ChainCfg cfg = cfg_of(c, kind);
+    a.nstage = std::max(2, std::min(cfg.nstage, 8));
     a.integrate_only = integrate_only;
     a.n_img_dev = d_n_img;
     a.seg = d_seg;
@@ -289,7 +302,7 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.smeta = d_smeta;
     if (d_smeta) CUDA_TRY(rta::launch_stream_meta(a, d_smeta, n_img, c->n_sm, s));
     CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
-    CUDA_TRY(rta::launch_image_chain(c->variant, a, grid, smem, s));
+    CUDA_TRY(rta::launch_image_chain(cfg.variant, a, grid, smem, s));
     return RTA_OK;
 }
 
@@ -534,9 +547,9 @@ int rta_set_chain_config(rta_ctx* c, int variant, int n_stages, int ctas_per_sm)
     int g, swb;
     size_t sm;
     if ((rc = config_launch(c, ChainCfg{variant, n_stages, ctas_per_sm}, int64_t(1) << 30, &g, &sm, &swb))) return rc;
-    c->variant = variant;
-    c->nstage = n_stages;
-    c->ctas_per_sm = ctas_per_sm;
+    c->variant = c->nb_variant = variant;
+    c->nstage = c->nb_nstage = n_stages;
+    c->ctas_per_sm = c->nb_ctas_per_sm = ctas_per_sm;
     return RTA_OK;
 }
 
@@ -588,8 +601,12 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
     if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
-    const ChainCfg saved{c->variant, c->nstage, c->ctas_per_sm};
     const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
+    // the neighbour-peak window tunes its own configuration, the other modes the plain kernel's
+    int* cv = pp.nbpeak ? &c->nb_variant : &c->variant;
+    int* cn = pp.nbpeak ? &c->nb_nstage : &c->nstage;
+    int* cc = pp.nbpeak ? &c->nb_ctas_per_sm : &c->ctas_per_sm;
+    const ChainCfg saved{*cv, *cn, *cc};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -604,9 +621,9 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
                 if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb,
                                   pp.nbpeak ? rta::CHAIN_NB : rta::CHAIN_PLAIN) != RTA_OK)
                     continue;
-                c->variant = v;
-                c->nstage = nst;
-                c->ctas_per_sm = cps;
+                *cv = v;
+                *cn = nst;
+                *cc = cps;
                 rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out,
                                0, s, nullptr);
                 if (rc) break;
@@ -626,9 +643,9 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->variant = rc ? saved.variant : best.variant;
-    c->nstage = rc ? saved.nstage : best.nstage;
-    c->ctas_per_sm = rc ? saved.ctas_per_sm : best.ctas_per_sm;
+    *cv = rc ? saved.variant : best.variant;
+    *cn = rc ? saved.nstage : best.nstage;
+    *cc = rc ? saved.ctas_per_sm : best.ctas_per_sm;
     if (n_entries) *n_entries = n;
     return rc;
 }

@@ -115,6 +115,29 @@ def test_every_planted_fault_is_reported_like_the_oracle(sset):
     compare_dirs(d.ingest(ctx, dev_bytes(buf), len(buf)), ingest.decode_stream(buf, wl.tel_cam, cams_of(wl)))
 
 
+def test_short_packets_crc_like_the_oracle():
+    """Segments of 8 pixels: packets of 18-43 16-byte words, so some warps have
+    lanes without a word (fewer words than lanes) and some exactly one more than
+    the lanes; the clean stream and a flipped bit in a short packet and in a
+    long one are judged like the oracle."""
+    wl = synth.make_workload(2, 6)
+    ctx = make_ctx(wl)
+    buf, plan = synth.encode_stream(wl, seg_pixels={1: 8, 2: 8, 3: 8})
+    words = plan["size"] // 16
+    assert words.min() < 32 and words.max() > 32 and (words == 33).any()
+    d = GpuDir(len(plan["img"]) + 5, wl.n_img + 3, wl.n_evt + 1)
+    r = ingest.decode_stream(buf, wl.tel_cam, cams_of(wl), verify_crc=True)
+    assert r["error"] == 0
+    compare_dirs(d.ingest(ctx, dev_bytes(buf), len(buf), True), r)
+    for k in (int(np.argmin(words)), int(np.nonzero(words == 33)[0][0]), int(np.argmax(words))):
+        b = buf.copy()
+        b[plan["off"][k] + plan["size"][k] - 20] ^= 0x01          # a sample bit near the packet's end
+        r = ingest.decode_stream(b, wl.tel_cam, cams_of(wl), verify_crc=True)
+        assert (r["error"], r["error_offset"]) == (ingest.CRC, plan["off"][k])
+        compare_dirs(d.ingest(ctx, dev_bytes(b), len(b), True), r)
+    ctx.close()
+
+
 def test_capacities_like_the_oracle(sset):
     wl, ctx = sset
     buf, plan = synth.encode_stream(wl)
