@@ -575,7 +575,10 @@ typedef struct rta_stream rta_stream;
  * geometric fallback) or, with model = NULL, rta_stereo (geometric direction,
  * no energy or gammaness), the sky-map fill of the one-second slab of its
  * arrival, and the copy of its event list out. max_img / max_evt bound one
- * bundle. A scheduler thread owned by the stream does the device work. */
+ * bundle. A scheduler thread owned by the stream does the device work. Each
+ * slot keeps a pinned host staging buffer of max(12 max_img + 4 (max_evt + 1),
+ * 32 max_evt) bytes for the bundle's tables and its event list, so that only
+ * h_wave needs to be pinned for the copies to run asynchronously. */
 int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, int max_inflight, int64_t max_img,
                       int64_t max_evt, int window_mode, int start, int W, float t_hi, float t_lo,
                       int core_needs_neighbour, float fallback_deg, rta_stream** out);

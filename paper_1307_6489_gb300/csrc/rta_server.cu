@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -123,6 +124,10 @@ struct Slot {
     cudaEvent_t e_img = nullptr, e_model = nullptr, e_ev = nullptr, e_map = nullptr, e_done = nullptr;
     uint64_t ticket = 0;
     bool busy = false;
+    // pinned staging of the bundle's tables (in) and event list (out): copies from
+    // and to pageable memory would block the scheduler thread (and with it every
+    // other slot) until this slot's stream reached them
+    char* h_stage = nullptr;
 };
 
 }  // namespace
@@ -209,10 +214,16 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
         cudaError_t e_ = (call);                                                                    \
         if (e_ != cudaSuccess) return vfail(RTA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
+    // the tables through the slot's pinned staging (the slot's previous bundle, the
+    // last user of it, has completed), in the order of the device layout
+    const size_t tb_off = size_t(b.n_img) * 8, tb_tel = size_t(b.n_img) * 4, tb_evt = size_t(b.n_evt + 1) * 4;
+    std::memcpy(sl.h_stage, b.h_wave_off, tb_off);
+    std::memcpy(sl.h_stage + tb_off, b.h_img_tel, tb_tel);
+    std::memcpy(sl.h_stage + tb_off + tb_tel, b.h_evt_off, tb_evt);
     D_TRY(cudaMemcpyAsync(d_wave, b.h_wave, size_t(b.n_wave) * 2, cudaMemcpyHostToDevice, s));
-    D_TRY(cudaMemcpyAsync(d_off, b.h_wave_off, size_t(b.n_img) * 8, cudaMemcpyHostToDevice, s));
-    D_TRY(cudaMemcpyAsync(d_tel, b.h_img_tel, size_t(b.n_img) * 4, cudaMemcpyHostToDevice, s));
-    D_TRY(cudaMemcpyAsync(d_evt, b.h_evt_off, size_t(b.n_evt + 1) * 4, cudaMemcpyHostToDevice, s));
+    D_TRY(cudaMemcpyAsync(d_off, sl.h_stage, tb_off, cudaMemcpyHostToDevice, s));
+    D_TRY(cudaMemcpyAsync(d_tel, sl.h_stage + tb_off, tb_tel, cudaMemcpyHostToDevice, s));
+    D_TRY(cudaMemcpyAsync(d_evt, sl.h_stage + tb_off + tb_tel, tb_evt, cudaMemcpyHostToDevice, s));
     int rc = rta_image_chain(S->ctx, d_wave, b.n_wave, d_off, d_tel, b.n_img, S->window_mode, S->start, S->W,
                              S->t_hi, S->t_lo, S->core_nb, d_h, s);
     if (rc) return rc;
@@ -234,7 +245,7 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     D_TRY(fill_slabs(S, d_ev, b.n_evt, b.arrival_ns));
     D_TRY(cudaEventRecord(sl.e_map, S->s_map));
     D_TRY(cudaStreamWaitEvent(s, sl.e_map, 0));
-    D_TRY(cudaMemcpyAsync(b.h_events, d_ev, size_t(b.n_evt) * sizeof(rta_event_t), cudaMemcpyDeviceToHost, s));
+    D_TRY(cudaMemcpyAsync(sl.h_stage, d_ev, size_t(b.n_evt) * sizeof(rta_event_t), cudaMemcpyDeviceToHost, s));
     D_TRY(cudaEventRecord(sl.e_done, s));
 #undef D_TRY
     return RTA_OK;
@@ -251,6 +262,8 @@ void worker_loop(rta_stream* S) {
             const cudaError_t q = cudaEventQuery(sl.e_done);
             if (q == cudaErrorNotReady) continue;
             Req& r = S->reqs[sl.ticket];
+            if (q == cudaSuccess)       // the event list, from the slot's staging
+                std::memcpy(r.b.h_events, sl.h_stage, size_t(r.b.n_evt) * sizeof(rta_event_t));
             r.done_ns = now_ns();
             r.state = q == cudaSuccess ? REQ_DONE : REQ_FAILED;
             if (q != cudaSuccess) r.rc = RTA_E_CUDA;
@@ -303,6 +316,7 @@ void worker_loop(rta_stream* S) {
 void release_all(rta_stream* S) {
     for (auto& sl : S->slots) {
         if (sl.s) cudaStreamDestroy(sl.s);
+        if (sl.h_stage) cudaFreeHost(sl.h_stage);
         cudaEvent_t ev[] = {sl.e_img, sl.e_model, sl.e_ev, sl.e_map, sl.e_done};
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
@@ -360,8 +374,12 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
               cudaStreamCreateWithFlags(&S->s_model, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->s_map, cudaStreamNonBlocking) == cudaSuccess;
     S->slots.resize(max_inflight);
+    // staging per slot: the tables in, or the event list out, of the largest bundle
+    const size_t stage_bytes = std::max(size_t(max_img) * 12 + size_t(max_evt + 1) * 4,
+                                        size_t(max_evt) * sizeof(rta_event_t));
     for (auto& sl : S->slots) {
         ok = ok && cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaHostAlloc(reinterpret_cast<void**>(&sl.h_stage), stage_bytes, cudaHostAllocDefault) == cudaSuccess;
         cudaEvent_t* ev[] = {&sl.e_img, &sl.e_model, &sl.e_ev, &sl.e_map, &sl.e_done};
         for (auto e : ev) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     }
