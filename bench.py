@@ -883,7 +883,7 @@ def _kernel_hash():
     import hashlib
     h = hashlib.sha1()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_1307_6489_gb300", "csrc"))):
-        if f in ("k_image.cu", "k_image_chain.cuh", "rta_device.cuh"):
+        if f in ("k_image.cu", "k_image_lean.cu", "k_image_chain.cuh", "rta_device.cuh"):
             h.update(open(os.path.join(ROOT, "paper_1307_6489_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 

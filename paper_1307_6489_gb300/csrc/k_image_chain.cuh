@@ -623,20 +623,24 @@ __device__ __forceinline__ void nb_pixel(const ChainArgs& a, const ProcParams& p
 // compile-time for the specialised sliding-window cameras (the camera is the
 // same for the whole chunk, so the dispatch happens once per chunk); S == 0 is
 // the generic path with run-time S and W.
-template <int S, int W, int IT, int PPT>
+template <int S, int W, int IT, int PPT, bool NO_INTEG, bool NO_FILTER>
 __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcParams& pp, const StageHdr& h,
                                                 const unsigned char* buf, const int32_t* cp16, const float* cscale,
                                                 const SlotView& v, int ct, int lane, const int* wts) {
     const int Sr = S ? S : h.S;
     const int Wr = W ? W : pp.W;
+    // NO_INTEG / NO_FILTER: instantiations that never see the integrate-only call
+    // or the digital filter leave those branches out of their code
+    const bool integ = !NO_INTEG && a.integrate_only;
+    const bool filt = !NO_FILTER && pp.filter;
     // charge, outputs and thresholds of chunk pixel c with window sum `sum` starting at `wst`
     auto emit = [&](int c, int sum, int wst, const uint16_t* row, bool& hi, bool& lo) {
         const int p16 = cp16[c];
         int num;
         float q = charge(sum, Wr, p16, cscale[c], num);
-        if (pp.filter) q = filter_charge(row, wst, Wr, wts, pp.csum, p16, cscale[c]);
+        if (filt) q = filter_charge(row, wst, Wr, wts, pp.csum, p16, cscale[c]);
         const int p = h.base + c;
-        if (a.integrate_only) {
+        if (integ) {
             a.q_out[h.pix_off + p] = q;
             if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, Wr, p16, num);
         } else {
@@ -659,7 +663,7 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
             emit(c0, key0 >> 7, 127 - (key0 & 127), row0, hi0, lo0);
             emit(c0 + 1, key1 >> 7, 127 - (key1 & 127), row0 + S, hi1, lo1);
         }
-        if (!a.integrate_only) {
+        if (!integ) {
             const uint32_t h0 = __ballot_sync(0xffffffffu, hi0), h1 = __ballot_sync(0xffffffffu, hi1);
             const uint32_t l0 = __ballot_sync(0xffffffffu, lo0), l1 = __ballot_sync(0xffffffffu, lo1);
             const int word = (h.base + 64 * (ct >> 5)) >> 5;
@@ -687,7 +691,7 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
                     // maximum decides; the exact search (one call site) runs for the
                     // pixels that reach t_lo or whose samples are out of its range.
                     int m = 0;
-                    bool need = a.integrate_only || pp.filter || !max_window6_packed<S>(row, m);
+                    bool need = integ || filt || !max_window6_packed<S>(row, m);
                     if (!need) need = __fmul_rn(__int2float_rn(16 * m - W * cp16[c]), cscale[c]) >= pp.t_lo;
                     if (need) {
                         const int key = best_key_T<S, W>(row, pp.one, pp.k128);
@@ -706,7 +710,7 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
                 }
                 emit(c, sum, wst, row, hi, lo);
             }
-            if (!a.integrate_only) {
+            if (!integ) {
                 const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
                 const int word = (h.base + c) >> 5;
                 if (lane == 0 && word < ((h.base + h.npix + 31) >> 5)) {      // only the chunk's own words
@@ -757,8 +761,12 @@ static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, cons
 // records from k_stream_meta, chunks copied from the stream's segments). Each is
 // a separate instantiation, so that the contiguous path runs the same code as
 // without them.
-template <int IW, int PPT, int MB, bool NB, bool STREAM = false>
+template <int IW, int PPT, int MB, bool NB, bool STREAM = false, bool LEAN = false>
 __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
+    static_assert(!(LEAN && (NB || STREAM)), "the lean form is of the contiguous flat-window kernel");
+    // LEAN: the image chain with the flat window only; STREAM: never integrate-only
+    constexpr bool NO_INTEG = LEAN || STREAM;
+    const bool integ = !NO_INTEG && a.integrate_only;
     constexpr int IT = IW * 32;          // integrator threads
     constexpr int CHUNK = IT * PPT;      // largest chunk in pixels
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -893,7 +901,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                     bad = woff + int64_t(P) * S > a.n_wave;   // never read past the waveform buffer
                 }
             }
-            if (!bad && a.integrate_only) {
+            if (!bad && integ) {
                 poff = a.pix_off[img];
                 bad = poff < 0 || poff + P > a.n_q;            // never write past q / t
             }
@@ -1013,7 +1021,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             if (lane == 0) mbar_arrive(&sm.empty[stage]);
             if (ct == 0) {
                 atomicOr(a.status, RTA_DEV_BAD_IMAGE);
-                if (!a.integrate_only) write_bad_row(a.out + h.img);
+                if (!integ) write_bad_row(a.out + h.img);
             }
             if (++stage == NST) { stage = 0; phase ^= 1u; }
             continue;
@@ -1024,7 +1032,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             if (!mbar_wait(&sm.nb_free, nb_fph, abort_flag)) { give_up(); break; }
             nb_fph ^= 1u;
         }
-        if (h.base == 0 && !a.integrate_only) {
+        if (h.base == 0 && !integ) {
             // the slot must be free: the tail warp is done with the image two back
             if (!mbar_wait(&sm.slot_free[slot], sphase ^ 1u, abort_flag)) { give_up(); break; }
         }
@@ -1053,7 +1061,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 nb_rph ^= 1u;
                 // ...so the candidate pass can look at any pixel's neighbours
                 const DevCam C = a.arr.cams[h.cam];
-                if (a.integrate_only) {
+                if (integ) {
                     for (int p = ct; p < h.P; p += IT) nb_pixel(a, pp, h, C, nbk, p, v);
                 } else {
                     const int n = *nb.n_cand;
@@ -1066,20 +1074,20 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             }
         } else {
             if (pp.sliding && pp.W == 6 && h.S == 40)
-                integrate_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+                integrate_chunk<40, 6, IT, PPT, NO_INTEG, LEAN>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
             else if (pp.sliding && pp.W == 6 && h.S == 30)
-                integrate_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+                integrate_chunk<30, 6, IT, PPT, NO_INTEG, LEAN>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
             else if (pp.sliding && pp.W == 6 && h.S == 25)
-                integrate_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+                integrate_chunk<25, 6, IT, PPT, NO_INTEG, LEAN>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
             else if (pp.sliding && pp.W == 5 && h.S == 16)
-                integrate_chunk<16, 5, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+                integrate_chunk<16, 5, IT, PPT, NO_INTEG, LEAN>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
             else
-                integrate_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
+                integrate_chunk<0, 0, IT, PPT, NO_INTEG, LEAN>(a, pp, h, buf, cp16, cscale, v, ct, lane, sm.wts);
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[stage]);
             if (++stage == NST) { stage = 0; phase ^= 1u; }
         }
-        if ((h.flags & HDR_LAST) && !a.integrate_only) {
+        if ((h.flags & HDR_LAST) && !integ) {
             if (ct == 0) {
                 SlotHdr sh;
                 sh.img = h.img;

@@ -1,0 +1,44 @@
+// The lean instantiations of the fused image kernel (k_image_chain with LEAN =
+// true, k_image_chain.cuh): the image chain with the flat window, without the
+// integrate-only outputs and the digital filter, so that neither branch is
+// compiled into the kernel the reconstruction runs. Compiled apart from the
+// other instantiations so that the builds run in parallel.
+#include "k_image_chain.cuh"
+
+namespace rta {
+
+template <int IW, int PPT, int MB>
+static cudaError_t launch_lean(const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occupancy_only,
+                               int* occ) {
+    auto kern = k_image_chain<IW, PPT, MB, false, false, true>;
+    // the dynamic shared-memory opt-in is per device; remember the largest size set
+    static size_t attr_bytes[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || attr_bytes[dev] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_bytes[dev] = smem;
+    }
+    if (occupancy_only) {
+        *occ = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, IW * 32 + 64, smem);
+    }
+    kern<<<grid, IW * 32 + 64, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The same tile variants as the other window modes (kVariants in k_image.cu).
+cudaError_t dispatch_image_chain_lean(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s,
+                                      bool occ_only, int* occ) {
+    switch (v) {
+    case 0: return launch_lean<8, 1, 2>(a, grid, smem, s, occ_only, occ);
+    case 1: return launch_lean<4, 2, 2>(a, grid, smem, s, occ_only, occ);
+    case 2: return launch_lean<8, 2, 2>(a, grid, smem, s, occ_only, occ);
+    case 3: return launch_lean<4, 1, 2>(a, grid, smem, s, occ_only, occ);
+    case 4: return launch_lean<8, 1, 3>(a, grid, smem, s, occ_only, occ);   // registers for three CTAs per SM
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rta

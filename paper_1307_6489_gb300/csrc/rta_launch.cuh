@@ -96,9 +96,12 @@ int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
 // which instantiation of the fused kernel a launch uses
 enum { CHAIN_PLAIN = 0, CHAIN_NB = 1, CHAIN_STREAM = 2 };
 int chain_occupancy(int v, size_t smem, int kind = CHAIN_PLAIN);
-// the neighbour-peak instantiations (k_image_nb.cu) and the byte-stream ones (k_image_stream.cu)
+// the neighbour-peak instantiations (k_image_nb.cu), the lean ones of the image chain with the
+// flat window (k_image_lean.cu) and the byte-stream ones (k_image_stream.cu)
 cudaError_t dispatch_image_chain_nb(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
                                     int* occ);
+cudaError_t dispatch_image_chain_lean(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s,
+                                      bool occ_only, int* occ);
 cudaError_t dispatch_image_chain_stream(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s,
                                         bool occ_only, int* occ);
 int chain_variant_min_blocks(int v);

@@ -82,6 +82,27 @@ void free_ws(rta_model* md) {
     md->cap_img = md->cap_evt = 0;
 }
 
+// Events per k_event tile: one tile per SM, 32..128 events each.
+int event_tile(const rta_model* md, int64_t n_evt) {
+    const int64_t per_sm = (n_evt + md->n_sm - 1) / md->n_sm;
+    return int(std::min<int64_t>(128, std::max<int64_t>(32, per_sm)));
+}
+
+// Grow the inference's pooled-vector workspace to n_tiles tiles of 128 x SUR_G.
+// (A growth frees and allocates, which synchronises the device: the serving
+// engine reserves its largest batch up front.)
+int reserve_pooled(rta_model* md, int64_t n_tiles) {
+    const int64_t need = n_tiles * 128 * SUR_G;
+    if (need <= md->cap_pc) return RTA_OK;
+    cudaFree(md->Pc);
+    md->Pc = nullptr;
+    md->cap_pc = 0;
+    if (cudaMalloc(&md->Pc, sizeof(__nv_bfloat16) * need) != cudaSuccess)
+        return sfail(RTA_E_NOMEM, "inference workspace allocation failed");
+    md->cap_pc = need;
+    return RTA_OK;
+}
+
 // Grow the activation workspace to hold n_img images and n_evt events.
 int reserve(rta_model* md, int64_t n_img, int64_t n_evt) {
     if (n_img <= md->cap_img && n_evt <= md->cap_evt) return RTA_OK;
@@ -254,7 +275,10 @@ int upload_params(rta_model* md, const std::vector<float>& internal) {
 int rta::surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt) {
     if (!md) return sfail(RTA_E_INVALID, "model is NULL");
     S_TRY(cudaSetDevice(md->device));
-    return reserve(md, n_img, n_evt);
+    const int rc = reserve(md, n_img, n_evt);
+    // the inference's pooled tiles for any batch of up to n_evt events: at most one
+    // tile per SM while the tiles hold up to 128 events, else n_evt / 128
+    return rc ? rc : reserve_pooled(md, std::max<int64_t>(md->n_sm, (n_evt + 127) / 128));
 }
 
 extern "C" {
@@ -475,17 +499,8 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     ia.pk = md->pk;
     // k_event: one tile per SM, 32..128 events each
     {
-        const int64_t per_sm = (n_evt + md->n_sm - 1) / md->n_sm;
-        ia.ev_tile_events = int(std::min<int64_t>(128, std::max<int64_t>(32, per_sm)));
-        const int64_t need = (n_evt + ia.ev_tile_events - 1) / ia.ev_tile_events * 128 * SUR_G;
-        if (need > md->cap_pc) {
-            cudaFree(md->Pc);
-            md->Pc = nullptr;
-            md->cap_pc = 0;
-            if (cudaMalloc(&md->Pc, sizeof(__nv_bfloat16) * need) != cudaSuccess)
-                return sfail(RTA_E_NOMEM, "inference workspace allocation failed");
-            md->cap_pc = need;
-        }
+        ia.ev_tile_events = event_tile(md, n_evt);
+        if ((rc = reserve_pooled(md, (n_evt + ia.ev_tile_events - 1) / ia.ev_tile_events))) return rc;
         ia.P = md->Pc;
     }
     // k_tel runs two CTAs per SM; tiles of up to 32 events, sized so that the
