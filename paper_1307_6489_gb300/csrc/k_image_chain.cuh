@@ -521,12 +521,13 @@ struct NbShared {
     int* n_cand;          // candidates so far in this image
 };
 
-template <int S, int W, int IT, int PPT>
+template <int S, int W, int IT, int PPT, bool NO_INTEG>
 __device__ __forceinline__ void nb_keys_chunk(const ChainArgs& a, const ProcParams& pp, const StageHdr& h,
                                               const unsigned char* buf, const int32_t* cp16, const float* cscale,
                                               const NbShared& nb, const SlotView& v, int ct, int lane) {
     const int Sr = S ? S : h.S;
     const int Wr = W ? W : pp.W;
+    const bool integ = !NO_INTEG && a.integrate_only;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int c = ct + k * IT;
@@ -539,7 +540,7 @@ __device__ __forceinline__ void nb_keys_chunk(const ChainArgs& a, const ProcPara
             bool exact = true;
             if constexpr (S != 0 && W == 6) {
                 int m = 0;
-                if (!a.integrate_only && max_window6_packed<S>(row, m)) {
+                if (!integ && max_window6_packed<S>(row, m)) {
                     q0 = charge(m, Wr, cp16[c], cscale[c], num);
                     exact = q0 >= pp.t_lo;
                 }
@@ -552,9 +553,9 @@ __device__ __forceinline__ void nb_keys_chunk(const ChainArgs& a, const ProcPara
                 st = 127 - (key & 127);
             }
             nb.key[h.base + c] = nb_key(q0, st);
-            cand = !a.integrate_only && q0 >= pp.t_lo;
+            cand = !integ && q0 >= pp.t_lo;
         }
-        if (!a.integrate_only) {
+        if (!integ) {
             // append the candidates (one atomic per warp); the chunk's bitmap words
             // start empty and the candidate pass sets their bits
             const uint32_t bc = __ballot_sync(0xffffffffu, cand);
@@ -575,6 +576,7 @@ __device__ __forceinline__ void nb_keys_chunk(const ChainArgs& a, const ProcPara
 // among itself and its registered neighbours, then its own flat sum there, the
 // calibration multiply and the peak time; in the image chain q, t and the
 // bitmap bits go to the slot.
+template <bool NO_INTEG>
 __device__ __forceinline__ void nb_pixel(const ChainArgs& a, const ProcParams& pp, const StageHdr& h, const DevCam& C,
                                          const uint64_t* key, int p, const SlotView& v) {
     uint64_t best = key[p];
@@ -603,7 +605,7 @@ __device__ __forceinline__ void nb_pixel(const ChainArgs& a, const ProcParams& p
     const int p16 = __ldg(a.arr.p16 + h.row + p);
     int num;
     const float q = charge(sum, Wr, p16, __ldg(a.arr.scale + h.row + p), num);
-    if (a.integrate_only) {
+    if (!NO_INTEG && a.integrate_only) {
         a.q_out[h.pix_off + p] = q;
         if (a.t_out) a.t_out[h.pix_off + p] = peak_time(row, wst, Wr, p16, num);
     } else {
@@ -763,8 +765,9 @@ static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, cons
 // without them.
 template <int IW, int PPT, int MB, bool NB, bool STREAM = false, bool LEAN = false>
 __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
-    static_assert(!(LEAN && (NB || STREAM)), "the lean form is of the contiguous flat-window kernel");
-    // LEAN: the image chain with the flat window only; STREAM: never integrate-only
+    static_assert(!(LEAN && STREAM), "the lean forms are of the contiguous kernels");
+    // LEAN: the image chain only (and, outside NB, the flat window only); STREAM:
+    // never integrate-only
     constexpr bool NO_INTEG = LEAN || STREAM;
     const bool integ = !NO_INTEG && a.integrate_only;
     constexpr int IT = IW * 32;          // integrator threads
@@ -1044,13 +1047,13 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             // during this image's candidate pass, after every warp has passed nb_free
             const NbShared nb = {nbk, nbc, &sm.nb_cnt[nb_img & 1]};
             if (pp.W == 6 && h.S == 40)
-                nb_keys_chunk<40, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+                nb_keys_chunk<40, 6, IT, PPT, NO_INTEG>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
             else if (pp.W == 6 && h.S == 30)
-                nb_keys_chunk<30, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+                nb_keys_chunk<30, 6, IT, PPT, NO_INTEG>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
             else if (pp.W == 6 && h.S == 25)
-                nb_keys_chunk<25, 6, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+                nb_keys_chunk<25, 6, IT, PPT, NO_INTEG>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
             else
-                nb_keys_chunk<0, 0, IT, PPT>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
+                nb_keys_chunk<0, 0, IT, PPT, NO_INTEG>(a, pp, h, buf, cp16, cscale, nb, v, ct, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[stage]);
             if (++stage == NST) { stage = 0; phase ^= 1u; }
@@ -1062,10 +1065,10 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 // ...so the candidate pass can look at any pixel's neighbours
                 const DevCam C = a.arr.cams[h.cam];
                 if (integ) {
-                    for (int p = ct; p < h.P; p += IT) nb_pixel(a, pp, h, C, nbk, p, v);
+                    for (int p = ct; p < h.P; p += IT) nb_pixel<NO_INTEG>(a, pp, h, C, nbk, p, v);
                 } else {
                     const int n = *nb.n_cand;
-                    for (int j = ct; j < n; j += IT) nb_pixel(a, pp, h, C, nbk, nbc[j], v);
+                    for (int j = ct; j < n; j += IT) nb_pixel<NO_INTEG>(a, pp, h, C, nbk, nbc[j], v);
                 }
                 if (ct == 0) sm.nb_cnt[(nb_img + 1) & 1] = 0;
                 ++nb_img;
