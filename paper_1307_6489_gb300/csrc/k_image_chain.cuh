@@ -765,9 +765,8 @@ static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, cons
 // without them.
 template <int IW, int PPT, int MB, bool NB, bool STREAM = false, bool LEAN = false>
 __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
-    static_assert(!(LEAN && STREAM), "the lean forms are of the contiguous kernels");
-    // LEAN: the image chain only (and, outside NB, the flat window only); STREAM:
-    // never integrate-only
+    // LEAN: the image chain only, without the digital filter; STREAM: never
+    // integrate-only
     constexpr bool NO_INTEG = LEAN || STREAM;
     const bool integ = !NO_INTEG && a.integrate_only;
     constexpr int IT = IW * 32;          // integrator threads

@@ -56,6 +56,7 @@ struct Slot {  // one half of the host-path double buffer
     rta_stereo_t* d_s = nullptr;
     size_t img_cap = 0, evt_cap = 0;
     int64_t* h_off = nullptr;   // pinned
+    int32_t* h_tel = nullptr;   // pinned (a copy from the caller's pageable table would block the enqueueing thread)
     int32_t* h_evt = nullptr;   // pinned
     // results of the slot's last chunk, staged in pinned memory so that the
     // device-to-host copies never block the thread that enqueues the next upload
@@ -423,7 +424,7 @@ int rta_destroy(rta_ctx* c) {
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.meta_done) cudaEventDestroy(s.meta_done);
         cudaFree(s.d_wave); cudaFree(s.d_off); cudaFree(s.d_tel); cudaFree(s.d_evt); cudaFree(s.d_h); cudaFree(s.d_s);
-        cudaFreeHost(s.h_off); cudaFreeHost(s.h_evt);
+        cudaFreeHost(s.h_off); cudaFreeHost(s.h_tel); cudaFreeHost(s.h_evt);
         cudaFreeHost(s.h_hres); cudaFreeHost(s.h_sres);
         if (s.res_done) cudaEventDestroy(s.res_done);
         if (s.up_done) cudaEventDestroy(s.up_done);
@@ -809,7 +810,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
         }
         if (s.img_cap < size_t(max_img) || s.evt_cap < size_t(max_evt) + 1) {
             cudaFree(s.d_off); cudaFree(s.d_tel); cudaFree(s.d_evt); cudaFree(s.d_h); cudaFree(s.d_s);
-            cudaFreeHost(s.h_off); cudaFreeHost(s.h_evt);
+            cudaFreeHost(s.h_off); cudaFreeHost(s.h_tel); cudaFreeHost(s.h_evt);
             cudaFreeHost(s.h_hres); cudaFreeHost(s.h_sres);
             s.img_cap = size_t(max_img) + 1024;
             s.evt_cap = size_t(max_evt) + 1024;
@@ -819,6 +820,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
             CUDA_TRY(cudaMalloc(&s.d_h, sizeof(rta_hillas_t) * s.img_cap));
             CUDA_TRY(cudaMalloc(&s.d_s, sizeof(rta_stereo_t) * s.evt_cap));
             CUDA_TRY(cudaMallocHost(&s.h_off, sizeof(int64_t) * s.img_cap));
+            CUDA_TRY(cudaMallocHost(&s.h_tel, sizeof(int32_t) * s.img_cap));
             CUDA_TRY(cudaMallocHost(&s.h_evt, sizeof(int32_t) * s.evt_cap));
             CUDA_TRY(cudaMallocHost(&s.h_hres, sizeof(rta_hillas_t) * s.img_cap));
             CUDA_TRY(cudaMallocHost(&s.h_sres, sizeof(rta_stereo_t) * s.evt_cap));
@@ -844,6 +846,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
         if ((rc = deliver(s))) return rc;
         const int64_t base = ni ? h_wave_off[i0] : 0;
         for (int64_t i = 0; i < ni; ++i) s.h_off[i] = h_wave_off[i0 + i] - base;
+        if (ni) memcpy(s.h_tel, h_img_tel + i0, sizeof(int32_t) * ni);
         for (int64_t e = 0; e <= ne; ++e) s.h_evt[e] = int32_t(h_evt_off[e0 + e] - i0);
         // uploads go one at a time, in chunk order: the host link is the bottleneck
         // and two concurrent uploads share it less well than one after the other;
@@ -853,7 +856,7 @@ int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, con
             const size_t bytes = size_t(img_end[i1 - 1] - base) * 2;
             CUDA_TRY(cudaMemcpyAsync(s.d_wave, h_wave + base, bytes, cudaMemcpyHostToDevice, s.stream));
             CUDA_TRY(cudaMemcpyAsync(s.d_off, s.h_off, sizeof(int64_t) * ni, cudaMemcpyHostToDevice, s.stream));
-            CUDA_TRY(cudaMemcpyAsync(s.d_tel, h_img_tel + i0, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s.stream));
+            CUDA_TRY(cudaMemcpyAsync(s.d_tel, s.h_tel, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s.stream));
         }
         CUDA_TRY(cudaMemcpyAsync(s.d_evt, s.h_evt, sizeof(int32_t) * (ne + 1), cudaMemcpyHostToDevice, s.stream));
         CUDA_TRY(cudaEventRecord(s.meta_done, s.stream));
