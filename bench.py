@@ -468,6 +468,31 @@ def build_serving_pool(wl, wave_h, n_bundles, rng, max_events):
     return pool
 
 
+def arrival_schedule(pool_bytes, rate, duration_s, rng, min_arrivals=8, burst=24):
+    """Arrivals [(ns after the start, pool index)] of bundles drawn from a pool at
+    an aggregate rate (GB/s). rate = inf: a burst of `burst` bundles at the start.
+    Otherwise Poisson arrivals -- exponential gaps, each with the mean its bundle's
+    bytes give at this rate -- for at least duration_s and at least min_arrivals
+    bundles (so that the low rates' percentiles are not those of one or two), the
+    gaps then scaled by one factor so that the schedule offers exactly `rate`: its
+    bytes over the time from the start to the last arrival."""
+    n = len(pool_bytes)
+    if rate == float("inf"):
+        return [(0, int(rng.integers(n))) for _ in range(burst)]
+    picks, gaps, total = [], [], 0
+    while total < rate * 1e9 * duration_s or len(picks) < min_arrivals:
+        i = int(rng.integers(n))
+        gaps.append(rng.exponential(pool_bytes[i] / (rate * 1e9)))
+        picks.append(i)
+        total += pool_bytes[i]
+    scale = (total / (rate * 1e9)) / sum(gaps)
+    out, t = [], 0.0
+    for i, g in zip(picks, gaps):
+        t += g * scale * 1e9
+        out.append((int(t), i))
+    return out
+
+
 def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894):
     """Poisson arrivals of sub-array bundles at fixed aggregate rates through the
     serving stream (continuous batching under an HBM budget); per rate the
@@ -482,31 +507,10 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
     out = []
     try:
         for rate in rates:
-            sched, total, t_start = [], 0, time.monotonic_ns() + 50_000_000
-            if rate == float("inf"):      # capacity: a burst of 24 bundles arriving together
-                for _ in range(24):
-                    b = pool[int(rng.integers(len(pool)))]
-                    sched.append((t_start, b))
-                    total += b["bytes"]
-            else:
-                # Poisson arrivals (exponential gaps, each with the mean its bundle's bytes
-                # give at this rate), the gaps then scaled by one factor so that the
-                # schedule offers exactly `rate`: its bytes over the time from the start
-                # to the last arrival
-                picks, gaps = [], []
-                # at least 8 arrivals, so that the low rates' percentiles are not those of one or two
-                mean_b = sum(b["bytes"] for b in pool) / len(pool)
-                dur = max(duration_s, 8 * mean_b / (rate * 1e9))
-                while total < rate * 1e9 * dur:
-                    b = pool[int(rng.integers(len(pool)))]
-                    gaps.append(rng.exponential(b["bytes"] / (rate * 1e9)))
-                    picks.append(b)
-                    total += b["bytes"]
-                scale = (total / (rate * 1e9)) / sum(gaps)
-                t = float(t_start)
-                for b, g in zip(picks, gaps):
-                    t += g * scale * 1e9
-                    sched.append((int(t), b))
+            t_start = time.monotonic_ns() + 50_000_000
+            sched = [(t_start + dt, pool[i]) for dt, i in arrival_schedule([b["bytes"] for b in pool], rate,
+                                                                           duration_s, rng)]
+            total = sum(b["bytes"] for _, b in sched)
             ev_all = torch.empty(sum(b["n_evt"] for _, b in sched) * 32, dtype=torch.uint8, pin_memory=True)
             ev_np = ev_all.numpy()
             pos, structs, tickets, arr = 0, [], [], []
