@@ -156,10 +156,9 @@ static cudaError_t dispatch(int v, const ChainArgs& a, int grid, size_t smem, cu
 }
 
 cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s) {
-    // the image chain on a contiguous bundle (flat window, or neighbour-peak window)
-    // runs a lean instantiation
-    if (!a.smeta && !a.integrate_only && !a.pp.filter)
-        return dispatch_image_chain_lean(v, a, grid, smem, s, false, nullptr);
+    // the image chain on a contiguous bundle (flat window, neighbour-peak window or
+    // digital filter) runs a lean instantiation
+    if (!a.smeta && !a.integrate_only) return dispatch_image_chain_lean(v, a, grid, smem, s, false, nullptr);
     if (a.pp.nbpeak) return dispatch_image_chain_nb(v, a, grid, smem, s, false, nullptr);
     if (a.smeta) return dispatch_image_chain_stream(v, a, grid, smem, s, false, nullptr);
     return dispatch(v, a, grid, smem, s, false, nullptr);

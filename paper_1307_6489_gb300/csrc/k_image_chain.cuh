@@ -760,14 +760,16 @@ static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, cons
 
 // NB: the neighbour-peak window (keys and candidates in shared memory, a
 // candidate pass after each image). STREAM: a byte-stream bundle (per-image
-// records from k_stream_meta, chunks copied from the stream's segments). Each is
-// a separate instantiation, so that the contiguous path runs the same code as
-// without them.
-template <int IW, int PPT, int MB, bool NB, bool STREAM = false, bool LEAN = false>
+// records from k_stream_meta, chunks copied from the stream's segments). LEAN:
+// the image chain only, without the integrate-only outputs and the digital
+// filter; FILT: the image chain with the digital filter, without the
+// integrate-only outputs. Each combination is a separate instantiation, so that
+// every kernel carries only the code of the calls it serves (branches left in,
+// even untaken, cost the hot loop instruction-cache misses and scheduling).
+template <int IW, int PPT, int MB, bool NB, bool STREAM = false, bool LEAN = false, bool FILT = false>
 __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArgs a) {
-    // LEAN: the image chain only, without the digital filter; STREAM: never
-    // integrate-only
-    constexpr bool NO_INTEG = LEAN || STREAM;
+    static_assert(!(LEAN && FILT) && !(NB && FILT), "the filter form is of the flat-window chain");
+    constexpr bool NO_INTEG = LEAN || STREAM || FILT;     // STREAM: never integrate-only
     const bool integ = !NO_INTEG && a.integrate_only;
     constexpr int IT = IW * 32;          // integrator threads
     constexpr int CHUNK = IT * PPT;      // largest chunk in pixels
