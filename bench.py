@@ -477,6 +477,8 @@ def arrival_schedule(pool_bytes, rate, duration_s, rng, min_arrivals=8, burst=24
     gaps then scaled by one factor so that the schedule offers exactly `rate`: its
     bytes over the time from the start to the last arrival."""
     n = len(pool_bytes)
+    if not rate > 0:
+        raise ValueError(f"arrival rate {rate} GB/s must be positive")
     if rate == float("inf"):
         return [(0, int(rng.integers(n))) for _ in range(burst)]
     picks, gaps, total = [], [], 0

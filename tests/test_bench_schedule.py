@@ -43,3 +43,9 @@ def test_burst():
     s = bench.arrival_schedule(POOL, float("inf"), 5.0, np.random.default_rng(6))
     assert len(s) == 24 and all(dt == 0 for dt, _ in s)
     assert all(0 <= i < len(POOL) for _, i in s)
+
+
+def test_rates_must_be_positive():
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(ValueError):
+            bench.arrival_schedule(POOL, bad, 5.0, np.random.default_rng(7))
