@@ -316,7 +316,6 @@ static_assert(CRC_SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 // 32 different banks.
 __global__ void __launch_bounds__(CRC_THREADS, 1) k_pkt_crc(const IngestArgs a) {
     extern __shared__ __align__(16) unsigned char crc_smem[];
-    uint32_t* Tl = reinterpret_cast<uint32_t*>(crc_smem);                       // [6][256][32]
     uint16_t* T = reinterpret_cast<uint16_t*>(crc_smem + CRC_LANE_TABLE_BYTES); // [6][256]
     uint16_t* X16 = T + 6 * 256;                                                // x^(128 k) mod G
     uint16_t* A = X16 + CRC_X16;
@@ -344,17 +343,23 @@ __global__ void __launch_bounds__(CRC_THREADS, 1) k_pkt_crc(const IngestArgs a) 
     }
     for (int k = threadIdx.x; k < CRC_X16; k += blockDim.x) X16[k] = uint16_t(gf_mulmod(A[k & 63], B[k >> 6]));
     __syncthreads();
-    // one copy of the six tables per lane, entry (k, x) of lane l in word
-    // (256 k + x) * 32 + l: every lookup of a warp hits 32 different banks
-    for (int w = threadIdx.x; w < 6 * 256 * 32; w += blockDim.x) Tl[w] = T[w >> 5];
+    // one copy of the six tables per lane: entry (k, x) of lane l at byte
+    // 65536 (k >> 1) + 256 x + 128 (k & 1) + 4 l, so that every lookup of a warp hits
+    // 32 different banks and a lookup's offset is one byte permute of the index
+    // byte and 4 l (the table's constant part goes into the load's immediate)
+    for (int w = threadIdx.x; w < 6 * 256 * 32; w += blockDim.x) {
+        const int k = w >> 13, x = (w >> 5) & 255, l = w & 31;
+        *reinterpret_cast<uint32_t*>(crc_smem + 65536 * (k >> 1) + 256 * x + 128 * (k & 1) + 4 * l) = T[k * 256 + x];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint32_t* L0 = Tl + lane;
-    const uint32_t* L1 = L0 + 256 * 32;
-    const uint32_t* L2 = L0 + 512 * 32;
-    const uint32_t* L3 = L0 + 768 * 32;
-    const uint32_t* ZH = L0 + 1024 * 32;
-    const uint32_t* ZL = L0 + 1280 * 32;
+    const uint32_t l4 = uint32_t(lane) * 4u;
+    // entry of table k at the index in byte j of v (byte permute: l4 in byte 0, the
+    // index byte in byte 1, zeros above)
+    auto look = [&](int k, uint32_t v, int j) {
+        const uint32_t off = __byte_perm(v, l4, 0x7604u | (uint32_t(j) << 4));
+        return *reinterpret_cast<const uint32_t*>(crc_smem + off + 65536 * (k >> 1) + 128 * (k & 1));
+    };
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     const int64_t n = a.hdr->n_pk < a.seg_cap + 1 ? a.hdr->n_pk : a.seg_cap + 1;
     for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps) {
@@ -380,11 +385,10 @@ __global__ void __launch_bounds__(CRC_THREADS, 1) k_pkt_crc(const IngestArgs a) 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint32_t x = ws[j];
-                const uint32_t b0 = x & 0xFF, b1 = (x >> 8) & 0xFF, b2 = (x >> 16) & 0xFF, b3 = x >> 24;
-                const uint32_t u = c ^ ((b0 << 8) | b1);
-                c = L3[(u >> 8) << 5] ^ L2[(u & 0xFF) << 5] ^ L1[b2 << 5] ^ L0[b3 << 5];
+                const uint32_t u = c ^ __byte_perm(x, 0u, 0x4401u);     // register ^ (b0 : b1)
+                c = look(3, u, 1) ^ look(2, u, 0) ^ look(1, x, 2) ^ look(0, x, 3);
             }
-            r = ZH[(r >> 8) << 5] ^ ZL[(r & 0xFF) << 5] ^ c;
+            r = look(4, r, 1) ^ look(5, r, 0) ^ c;
             last = w;
         }
         // carried to the packet's end; the preset register 0xFFFF likewise
