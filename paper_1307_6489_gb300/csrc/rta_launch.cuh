@@ -93,11 +93,14 @@ int chain_threads(int v);
 int chain_stage_wave_bytes(int v, int max_S);
 size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys = 0);
 int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
-// which instantiation of the fused kernel a launch uses
+// which instantiation family of the fused kernel a launch uses (the occupancy of
+// a family's general instantiation stands for its lean ones: same launch bounds,
+// same shared memory)
 enum { CHAIN_PLAIN = 0, CHAIN_NB = 1, CHAIN_STREAM = 2 };
 int chain_occupancy(int v, size_t smem, int kind = CHAIN_PLAIN);
-// the neighbour-peak instantiations (k_image_nb.cu), the lean ones of the image chain with the
-// flat window (k_image_lean.cu) and the byte-stream ones (k_image_stream.cu)
+// the neighbour-peak instantiations (k_image_nb.cu), the lean ones of the image chain on
+// contiguous bundles -- flat window, neighbour-peak window, digital filter -- (k_image_lean.cu)
+// and the byte-stream ones (k_image_stream.cu)
 cudaError_t dispatch_image_chain_nb(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s, bool occ_only,
                                     int* occ);
 cudaError_t dispatch_image_chain_lean(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s,
