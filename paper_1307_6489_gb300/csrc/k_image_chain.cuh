@@ -686,22 +686,27 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
             bool hi = false, lo = false;
             if (c < h.npix) {
                 const uint16_t* row = reinterpret_cast<const uint16_t*>(buf) + size_t(c) * Sr;
-                int sum, wst;
+                int sum = 0, wst = 0;
+                bool done = false;
                 if constexpr (S != 0 && W == 6) {
                     // The charge needs only the maximum; the window start (first
                     // maximum) only for pixels whose peak time is needed. The packed
-                    // maximum decides; the exact search (one call site) runs for the
-                    // pixels that reach t_lo or whose samples are out of its range.
+                    // maximum decides: below t_lo its charge is the pixel's whole
+                    // result (no time, no bits); the exact search (one call site)
+                    // runs for the pixels that reach t_lo or whose samples are out of
+                    // its range.
                     int m = 0;
-                    bool need = integ || filt || !max_window6_packed<S>(row, m);
-                    if (!need) need = __fmul_rn(__int2float_rn(16 * m - W * cp16[c]), cscale[c]) >= pp.t_lo;
-                    if (need) {
+                    if (!integ && !filt && max_window6_packed<S>(row, m)) {
+                        const float q0 = __fmul_rn(__int2float_rn(16 * m - W * cp16[c]), cscale[c]);
+                        if (q0 < pp.t_lo) {
+                            v.q[h.base + c] = q0;
+                            done = true;
+                        }
+                    }
+                    if (!done) {
                         const int key = best_key_T<S, W>(row, pp.one, pp.k128);
                         sum = key >> 7;
                         wst = 127 - (key & 127);
-                    } else {
-                        sum = m;
-                        wst = 0;       // unused: the pixel is below t_lo
                     }
                 } else if constexpr (S != 0) {
                     const int key = best_key_T<S, W>(row, pp.one, pp.k128);
@@ -710,7 +715,7 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
                 } else {
                     window_sum(row, h.S, pp, sum, wst);
                 }
-                emit(c, sum, wst, row, hi, lo);
+                if (!done) emit(c, sum, wst, row, hi, lo);
             }
             if (!integ) {
                 const uint32_t bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
