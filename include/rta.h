@@ -272,6 +272,18 @@ int rta_image_chain(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const 
                     const int32_t* d_img_tel, int64_t n_img, int window_mode, int start, int W, float t_hi,
                     float t_lo, int core_needs_neighbour, rta_hillas_t* d_out, void* stream);
 
+/* rta_image_chain that also writes each image's cleaning mask, for checking or
+ * displaying cleaned images: d_mask[d_pix_off[i] + p] = 1 when pixel p of image
+ * i survived cleaning, else 0 (the rule of rta_clean). The same kernel template,
+ * definitions and Hillas rows (bit for bit) as rta_image_chain, compiled with
+ * this per-pixel output. Rows of skipped images (RTA_HF_BAD_INPUT) are not
+ * written; an image whose rows do not fit n_q mask rows keeps its Hillas row,
+ * is not written, and sets RTA_DEV_BAD_IMAGE. */
+int rta_image_chain_masks(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                          const int32_t* d_img_tel, const int64_t* d_pix_off, int64_t n_img, int window_mode,
+                          int start, int W, float t_hi, float t_lo, int core_needs_neighbour, uint8_t* d_mask,
+                          int64_t n_q, rta_hillas_t* d_out, void* stream);
+
 /* Stereo Hillas intersection of n_evt events (direction reconstruction,
  * Sec. 4.1). Images with n_pix >= 3 are used. For each used pair i < j with
  * |sin(psi_j - psi_i)| >= 1e-6, the major axes u = (cos psi, sin psi) through
@@ -667,7 +679,10 @@ int rta_significance_map(rta_stream* stream, int64_t now_ns, rta_window_t window
 typedef struct rta_camera_desc_t {
     int n_pix, n_samples, K;  /* as rta_register_camera; n_pix*n_samples a multiple of 8 */
     const float* d_pix_xy;    /* 2*n_pix floats (deg), 8-byte aligned */
-    const int16_t* d_nb8;     /* n_pix rows of 8 int16 neighbour ids, -1 padded, 16-byte aligned */
+    const int16_t* d_nb8;     /* n_pix rows of 8 int16 neighbour ids, 16-byte aligned: the first K
+                                 of row p are ids in [0, n_pix) other than p, or -1 for none;
+                                 an id outside [0, n_pix) counts as -1 (it is not validated
+                                 here, unlike rta_register_camera, and is never read) */
 } rta_camera_desc_t;
 
 /* rta_image_chain without a context and without any allocation: the same
@@ -694,7 +709,9 @@ typedef struct rta_camera_desc_t {
  * must be serialised by the caller. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. This call makes no
- * cudaMalloc, cudaFree or other allocating call. Asynchronous on `stream`. */
+ * cudaMalloc, cudaFree or other allocating call. Asynchronous on `stream`;
+ * the host arrays (h_cams, h_tel_cam, h_tel_row) are consumed before it
+ * returns, whatever memory they are in. */
 int rta_image_chain_noalloc(const rta_camera_desc_t* h_cams, int n_cams, const int32_t* h_tel_cam,
                             const int64_t* h_tel_row, int n_tel, const int32_t* d_p16, const float* d_scale,
                             int64_t n_calib_rows, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,

@@ -87,6 +87,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_clean": ([P, P, i64, P, P, i64, f32, f32, i32, P, P], i32),
         "rta_hillas": ([P, P, P, P, i64, P, P, i64, P, P], i32),
         "rta_image_chain": ([P, P, i64, P, P, i64, i32, i32, i32, f32, f32, i32, P, P], i32),
+        "rta_image_chain_masks": ([P, P, i64, P, P, P, i64, i32, i32, i32, f32, f32, i32, P, i64, P, P], i32),
         "rta_stereo": ([P, P, P, i64, P, i64, P, P], i32),
         "rta_reconstruct": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P, P], i32),
         "rta_reconstruct_host": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, P, P], i32),
@@ -274,6 +275,12 @@ def rta_image_chain(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mo
                     core_needs_neighbour, d_out, stream=0):
     _check(load().rta_image_chain(ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi,
                                   t_lo, int(core_needs_neighbour), d_out, stream))
+
+
+def rta_image_chain_masks(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, window_mode, start, W, t_hi,
+                          t_lo, core_needs_neighbour, d_mask, n_q, d_out, stream=0):
+    _check(load().rta_image_chain_masks(ctx, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, window_mode,
+                                        start, W, t_hi, t_lo, int(core_needs_neighbour), d_mask, n_q, d_out, stream))
 
 
 def rta_stereo(ctx, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_out, stream=0):
@@ -677,6 +684,13 @@ class Context:
         rta_image_chain(self.handle, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(),
                         img_tel.numel(), window_mode, start, W, t_hi, t_lo, core_needs_neighbour, out.data_ptr(),
                         self._stream(stream))
+
+    def image_chain_masks(self, wave, wave_off, img_tel, pix_off, window_mode, start, W, t_hi, t_lo,
+                          core_needs_neighbour, mask, out, stream=None):
+        rta_image_chain_masks(self.handle, wave.data_ptr(), wave.numel(), wave_off.data_ptr(), img_tel.data_ptr(),
+                              pix_off.data_ptr(), img_tel.numel(), window_mode, start, W, t_hi, t_lo,
+                              core_needs_neighbour, mask.data_ptr(), mask.numel(), out.data_ptr(),
+                              self._stream(stream))
 
     def stereo(self, hillas, evt_off, img_tel, out, stream=None):
         rta_stereo(self.handle, hillas.data_ptr(), img_tel.data_ptr(), img_tel.numel(), evt_off.data_ptr(),

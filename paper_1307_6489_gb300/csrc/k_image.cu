@@ -157,8 +157,10 @@ static cudaError_t dispatch(int v, const ChainArgs& a, int grid, size_t smem, cu
 
 cudaError_t launch_image_chain(int v, const ChainArgs& a, int grid, size_t smem, cudaStream_t s) {
     // the image chain on a contiguous bundle (flat window, neighbour-peak window or
-    // digital filter) runs a lean instantiation
-    if (!a.smeta && !a.integrate_only) return dispatch_image_chain_lean(v, a, grid, smem, s, false, nullptr);
+    // digital filter) runs a lean instantiation; the per-pixel outputs (integrate-only
+    // charges and times, cleaning masks) are compiled into the general ones only
+    if (!a.smeta && !a.integrate_only && !a.mask_out)
+        return dispatch_image_chain_lean(v, a, grid, smem, s, false, nullptr);
     if (a.pp.nbpeak) return dispatch_image_chain_nb(v, a, grid, smem, s, false, nullptr);
     if (a.smeta) return dispatch_image_chain_stream(v, a, grid, smem, s, false, nullptr);
     return dispatch(v, a, grid, smem, s, false, nullptr);

@@ -307,13 +307,16 @@ __device__ __forceinline__ void block_reduce(float (&v)[N], float* red, int tid,
 
 __device__ __forceinline__ bool bit_of(const uint32_t* bits, int id) { return (bits[id >> 5] >> (id & 31)) & 1u; }
 
-__device__ __forceinline__ bool any_neighbour(const int4 nbr, int K, const uint32_t* bits) {
+// A neighbour id counts only inside [0, P): -1 pads a list, and an id outside
+// the camera (possible in caller-supplied tables) is ignored rather than read
+// from another image's bitmap words.
+__device__ __forceinline__ bool any_neighbour(const int4 nbr, int K, int P, const uint32_t* bits) {
     const int16_t* n = reinterpret_cast<const int16_t*>(&nbr);
     bool any = false;
 #pragma unroll
     for (int j = 0; j < RTA_NB_PAD; ++j) {
         const int id = n[j];
-        if (j < K && id >= 0 && bit_of(bits, id)) any = true;
+        if (j < K && unsigned(id) < unsigned(P) && bit_of(bits, id)) any = true;
     }
     return any;
 }
@@ -331,7 +334,7 @@ __device__ __forceinline__ void clean_bits(const DevCam& C, const ProcParams& pp
             cb = 0;
             for (uint32_t m = hb; m; m &= m - 1) {
                 const int bit = __ffs(m) - 1;
-                if (any_neighbour(__ldg(C.nb + (w * 32 + bit)), C.K, b.hi)) cb |= 1u << bit;
+                if (any_neighbour(__ldg(C.nb + (w * 32 + bit)), C.K, C.P, b.hi)) cb |= 1u << bit;
             }
         }
         b.core[w] = cb;
@@ -342,7 +345,7 @@ __device__ __forceinline__ void clean_bits(const DevCam& C, const ProcParams& pp
         uint32_t mb = cb;
         for (uint32_t m = b.lo[w] & ~cb; m; m &= m - 1) {
             const int bit = __ffs(m) - 1;
-            if (any_neighbour(__ldg(C.nb + (w * 32 + bit)), C.K, b.core)) mb |= 1u << bit;
+            if (any_neighbour(__ldg(C.nb + (w * 32 + bit)), C.K, C.P, b.core)) mb |= 1u << bit;
         }
         b.mask[w] = mb;
     }
@@ -435,6 +438,19 @@ __device__ __forceinline__ void hillas_bits(const float* q, const float* t, cons
         h.reserved[0] = h.reserved[1] = h.reserved[2] = h.reserved[3] = 0.f;
         *out = h;
     }
+}
+
+// The cleaning mask of one image as one byte per pixel at rows pix_off[img] ..
+// pix_off[img] + P - 1 (the per-pixel output of the general instantiations);
+// an image whose rows do not fit n_q is flagged and not written.
+__device__ __forceinline__ void write_mask(const ChainArgs& a, const DevCam& C, const uint32_t* mask, int img,
+                                           int lane) {
+    const int64_t off = a.pix_off[img];
+    if (off < 0 || off + C.P > a.n_q) {
+        if (lane == 0) atomicOr(a.status, RTA_DEV_BAD_IMAGE);
+        return;
+    }
+    for (int p = lane; p < C.P; p += 32) a.mask_out[off + p] = bit_of(mask, p) ? 1 : 0;
 }
 
 __device__ __forceinline__ void write_bad_row(rta_hillas_t* out) {
@@ -999,6 +1015,9 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             const DevCam C = a.arr.cams[sh.cam];
             const ImgBits ib = {v.hi, v.lo, core, maskb};
             clean_bits(C, pp, ib, lane, 32, WarpBar());
+            if constexpr (!NO_INTEG) {
+                if (a.mask_out) write_mask(a, C, maskb, sh.img, lane);
+            }
             hillas_bits(v.q, v.t, C, maskb, sm.red, lane, 32, WarpBar(), a.out + sh.img);
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.slot_free[slot]);

@@ -270,7 +270,8 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
               const int64_t* d_pix_off, int64_t n_img, const rta::ProcParams& pp, float* d_q, float* d_t,
               int64_t n_q, rta_hillas_t* d_out, int integrate_only, cudaStream_t s, unsigned int* counter,
               const int64_t* d_n_img = nullptr, const rta_segment_t* d_seg = nullptr,
-              const int32_t* d_img_seg = nullptr, int64_t n_seg = 0, rta::StreamImg* d_smeta = nullptr) {
+              const int32_t* d_img_seg = nullptr, int64_t n_seg = 0, rta::StreamImg* d_smeta = nullptr,
+              uint8_t* d_mask = nullptr) {
     int grid, swb;
     size_t smem;
     const int kind = pp.nbpeak ? rta::CHAIN_NB : d_smeta ? rta::CHAIN_STREAM : rta::CHAIN_PLAIN;
@@ -290,6 +291,7 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.q_out = d_q;
     a.t_out = d_t;
     a.out = d_out;
+    a.mask_out = d_mask;
     a.counter = counter ? counter : take_counter(c);
     a.status = c->d_status;
     a.stage_wave_bytes = swb;
@@ -723,6 +725,23 @@ int rta_image_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const in
     if (n_wave < 0) return fail(RTA_E_INVALID, "negative buffer length");
     return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out, 0,
                      (cudaStream_t)stream, nullptr);
+}
+
+int rta_image_chain_masks(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                          const int32_t* d_img_tel, const int64_t* d_pix_off, int64_t n_img, int window_mode,
+                          int start, int W, float t_hi, float t_lo, int core_needs_neighbour, uint8_t* d_mask,
+                          int64_t n_q, rta_hillas_t* d_out, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(n_img, "n_img"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (n_img == 0) return RTA_OK;
+    if (!d_wave || !d_wave_off || !d_img_tel || !d_pix_off || !d_mask || !d_out)
+        return fail(RTA_E_INVALID, "NULL device pointer");
+    if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
+    if (n_wave < 0 || n_q < 0) return fail(RTA_E_INVALID, "negative buffer length");
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
+    return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, d_pix_off, n_img, pp, nullptr, nullptr, n_q, d_out, 0,
+                     (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, 0, nullptr, d_mask);
 }
 
 int rta_stereo(rta_ctx* c, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,

@@ -12,13 +12,14 @@ struct ChainArgs {
     int64_t n_wave;          // samples in wave
     const int64_t* wave_off;
     const int32_t* img_tel;
-    const int64_t* pix_off;  // integrate-only mode
-    int64_t n_q;             // rows of q_out / t_out
+    const int64_t* pix_off;  // integrate-only mode, and the rows of mask_out
+    int64_t n_q;             // rows of q_out / t_out / mask_out
     int64_t n_img;           // images (capacity when n_img_dev is set)
     const int64_t* n_img_dev;  // optional device-resident image count (<= n_img), read at run time
     float* q_out;            // integrate-only mode
     float* t_out;
     rta_hillas_t* out;       // full mode
+    uint8_t* mask_out;       // full mode, optional: cleaning masks (general instantiations only)
     unsigned int* counter;   // zeroed before the launch
     unsigned int* status;
     int stage_wave_bytes;    // multiple of 128

@@ -141,10 +141,17 @@ extern "C" int rta_image_chain_noalloc(const rta_camera_desc_t* h_cams, int n_ca
     int rc = scratch_address(dev, &scratch);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    NA_TRY(cudaMemcpyAsync(scratch + kCamWord, cams, sizeof cams, cudaMemcpyHostToDevice, s));
-    NA_TRY(cudaMemcpyAsync(scratch + kTelCamWord, h_tel_cam, sizeof(int32_t) * n_tel, cudaMemcpyHostToDevice, s));
-    NA_TRY(cudaMemcpyAsync(scratch + kTelRowWord, h_tel_row, sizeof(int64_t) * n_tel, cudaMemcpyHostToDevice, s));
-    NA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned int), s));   // work counter and status start at zero
+    // The tables travel as one copy of a stack image of the scratch's table
+    // region, with the work counter and status word (zero) in front: a copy
+    // from pageable host memory is staged before cudaMemcpyAsync returns, so
+    // no caller array (pinned or not) is read after this call has returned.
+    unsigned int image[kScratchWords];
+    memset(image, 0, sizeof(unsigned int) * kTelRowWord);
+    memcpy(image + kCamWord, cams, sizeof cams);
+    memcpy(image + kTelCamWord, h_tel_cam, sizeof(int32_t) * n_tel);
+    memcpy(image + kTelRowWord, h_tel_row, sizeof(int64_t) * n_tel);
+    NA_TRY(cudaMemcpyAsync(scratch, image, sizeof(unsigned int) * kTelRowWord + sizeof(int64_t) * n_tel,
+                           cudaMemcpyHostToDevice, s));
 
     // ---- the launch: the fused kernel's default tile (8 integrator warps, 1 pixel per thread, 3 stages)
     const int variant = 0, nstage = 3;

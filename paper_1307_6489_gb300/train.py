@@ -43,6 +43,9 @@ class SurrogateTrainer:
 
     def fit(self, hillas, img_tel, evt_off, log_energy, src_xy, is_gamma, epochs=10, batch_events=4096, lr=2e-3,
             lr_end=2e-4, seed=0, stream=None):
+        """Adam over shuffled batches of consecutive events. Nothing waits for the
+        device inside the loop: every batch's event offsets are uploaded once, and
+        each step's loss goes to its own slot of a device array read at the end."""
         import torch
         dev = hillas.device
         stream = torch.cuda.current_stream(dev).cuda_stream if stream is None else int(stream)
@@ -51,25 +54,28 @@ class SurrogateTrainer:
         starts = np.arange(0, n_evt, batch_events)
         rng = np.random.default_rng(seed)
         steps = epochs * len(starts)
-        losses = []
-        d_loss = torch.zeros(1, dtype=torch.float32, device=dev)
-        off_buf = torch.zeros(batch_events + 1, dtype=torch.int32, device=dev)
+        # per batch b: its events' image offsets relative to its first image (CSR)
+        offs = np.zeros((len(starts), batch_events + 1), np.int32)
+        for b, e0 in enumerate(starts):
+            e1 = min(n_evt, e0 + batch_events)
+            offs[b, : e1 - e0 + 1] = evt_off[e0:e1 + 1] - evt_off[e0]
+        d_offs = torch.from_numpy(offs).to(dev)
+        d_loss = torch.zeros(max(steps, 1), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)          # the uploads above ran on torch's stream
         k = 0
         for ep in range(epochs):
-            for e0 in rng.permutation(starts):
-                e0 = int(e0)
+            for b in rng.permutation(len(starts)):
+                e0 = int(starts[b])
                 e1 = min(n_evt, e0 + batch_events)
                 i0, i1 = int(evt_off[e0]), int(evt_off[e1])
-                off = torch.from_numpy((evt_off[e0:e1 + 1] - i0).astype(np.int32))
-                off_buf[: e1 - e0 + 1].copy_(off, non_blocking=False)
                 rate = lr * (lr_end / lr) ** (k / max(1, steps - 1))
                 rta_surrogate_train_step(self.model, hillas.data_ptr() + 64 * i0, img_tel.data_ptr() + 4 * i0, i1 - i0,
-                                         off_buf.data_ptr(), e1 - e0, log_energy.data_ptr() + 4 * e0,
+                                         d_offs[b].data_ptr(), e1 - e0, log_energy.data_ptr() + 4 * e0,
                                          src_xy.data_ptr() + 8 * e0, is_gamma.data_ptr() + e0, rate, 1,
-                                         d_loss.data_ptr(), stream)
-                losses.append(float(d_loss.item()))
+                                         d_loss[k].data_ptr(), stream)
                 k += 1
-        return losses
+        torch.cuda.synchronize(dev)
+        return d_loss[:steps].cpu().numpy().astype(np.float64).tolist()
 
     def infer(self, hillas, img_tel, evt_off_dev, fallback_deg=0.5, stream=None):
         """rta_event_t rows (uint8 CUDA tensor n_evt*32) for a device-resident set."""

@@ -65,6 +65,20 @@ def test_filter_chain_and_stereo_match_the_oracle(fset):
     assert np.percentile(ddir, 99) <= DIR_DEG
 
 
+def test_filter_chain_masks_bit_exact(fset):
+    wl, ref, ctx, dev = fset
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    base = dev.hillas_buf()
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, base)
+    mask = torch.full((dev.n_pix,), 7, dtype=torch.uint8, device="cuda")
+    out = torch.full_like(base, float("nan"))
+    ctx.image_chain_masks(dev.wave, dev.wave_off, dev.img_tel, dev.pix_off, mode, start, W, t_hi, t_lo, core_nb, mask,
+                          out)
+    assert ctx.check() == 0
+    np.testing.assert_array_equal(mask.cpu().numpy(), ref["mask"])
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), base.cpu().numpy().view(np.uint32))
+
+
 def test_unit_weights_equal_the_flat_window():
     wl = synth.make_workload(2, 40)
     ctx = make_ctx(wl)

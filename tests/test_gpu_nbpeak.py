@@ -77,6 +77,22 @@ def test_nbpeak_chain_matches_the_oracle(nset):
         assert np.percentile(d, 99) <= DIR_DEG
 
 
+def test_nbpeak_chain_masks_bit_exact(nset):
+    """The neighbour-peak kernel's cleaning masks against the oracle's, pixel by
+    pixel; its Hillas rows equal rta_image_chain's bit for bit."""
+    name, wl, ref, ctx, dev = nset
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    base = dev.hillas_buf()
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, base)
+    mask = torch.full((dev.n_pix,), 7, dtype=torch.uint8, device="cuda")
+    out = torch.full_like(base, float("nan"))
+    ctx.image_chain_masks(dev.wave, dev.wave_off, dev.img_tel, dev.pix_off, mode, start, W, t_hi, t_lo, core_nb, mask,
+                          out)
+    assert ctx.check() == 0
+    np.testing.assert_array_equal(mask.cpu().numpy(), ref["mask"])
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), base.cpu().numpy().view(np.uint32))
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("n_stages,ctas", [(2, 1), (3, 0), (6, 1)])
 def test_nbpeak_every_tile_and_pipeline_depth_is_identical(nset, variant, n_stages, ctas):

@@ -85,6 +85,23 @@ def test_image_chain_fused(setup):
     assert (g["n_pix"] > 0).mean() > 0.5
 
 
+def test_image_chain_masks_bit_exact(setup):
+    """The fused kernel's own cleaning masks, pixel by pixel, against the oracle's,
+    and its Hillas rows against rta_image_chain's (the lean instantiation), bit for bit."""
+    name, wl, ref, ctx, dev = setup
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    base = dev.hillas_buf()
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, mode, start, W, t_hi, t_lo, core_nb, base)
+    mask = torch.full((dev.n_pix,), 7, dtype=torch.uint8, device="cuda")
+    out = torch.full_like(base, float("nan"))
+    ctx.image_chain_masks(dev.wave, dev.wave_off, dev.img_tel, dev.pix_off, mode, start, W, t_hi, t_lo, core_nb, mask,
+                          out)
+    assert ctx.check() == 0
+    np.testing.assert_array_equal(mask.cpu().numpy(), ref["mask"])
+    assert ref["mask"].sum() > 0
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), base.cpu().numpy().view(np.uint32))
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("n_stages,ctas", [(2, 1), (2, 2), (3, 0), (4, 1), (6, 1), (8, 1)])
 def test_image_chain_every_tile_and_pipeline_depth_is_identical(setup, variant, n_stages, ctas):
@@ -137,7 +154,10 @@ def test_stereo_stage_isolated(setup):
     np.testing.assert_array_equal(g["flags"], exp[:, S["flags"]].astype(np.uint32))
     np.testing.assert_array_equal(g["n_valid"], exp[:, S["n_valid"]].astype(np.int32))
     ok = exp[:, S["flags"]] == 0
-    assert ok.sum() > 0.3 * wl.n_evt
+    # not a vacuous comparison: 142 of these 300 seeded events (47 %) have a usable
+    # pair; the rest keep fewer than two images of >= 3 pixels after the 8/4 pe
+    # cleaning with the core-neighbour test (the trigger asks only >= 30 pe per image)
+    assert ok.sum() > 0.4 * wl.n_evt
     ddir = np.hypot(g["dir_x"][ok] - exp[ok, S["dir_x"]], g["dir_y"][ok] - exp[ok, S["dir_y"]])
     dcore = np.hypot(g["core_x"][ok] - exp[ok, S["core_x"]], g["core_y"][ok] - exp[ok, S["core_y"]])
     print("stereo max |ddir| deg", ddir.max(), "max |dcore| m", dcore.max())

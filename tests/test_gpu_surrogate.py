@@ -159,6 +159,40 @@ def test_inference_flags_and_geometric_fallback(setup):
         np.testing.assert_allclose(ev["gammaness"], 1 / (1 + np.exp(-y[:, 3].astype(np.float64))), atol=2e-3)
 
 
+def test_inference_kernels_match_the_fp64_oracle(setup):
+    """rta_surrogate_infer (the tcgen05 inference kernels, fallback off) directly
+    against the FP64 oracle's forward pass with the same BF16 weights and BF16
+    features: used counts and no-direction flags exact, baselines within 1e-4 deg,
+    energy, direction offsets and the gammaness logit within the forward bar
+    2e-2 (1 + |y|) (four BF16 activation stores on the GPU side)."""
+    s = setup
+    wl, d = s["wl"], s["d"]
+    out = torch.zeros(wl.n_evt * 32, dtype=torch.uint8, device="cuda")
+    rta.rta_surrogate_infer(s["model"], d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img,
+                            d["evt_off"].data_ptr(), wl.n_evt, 1e30, out.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    s["ctx"].check()
+    ev = rta.events_to_numpy(out.cpu().numpy())
+    y_ref, _ = mlp.forward(s["p"], mlp.bf16_round(s["X"]), s["used"], wl.evt_off)
+    np.testing.assert_array_equal(ev["n_used"], s["n_used"])
+    nodir = s["n_used"] < 2
+    np.testing.assert_array_equal((ev["flags"] & rta.RTA_EF_NO_DIRECTION) != 0, nodir)
+    assert ((ev["flags"] & rta.RTA_EF_FALLBACK) == 0).all()
+    np.testing.assert_allclose(ev["base_x"], s["base"][:, 0], atol=1e-4)
+    np.testing.assert_allclose(ev["base_y"], s["base"][:, 1], atol=1e-4)
+    tol = Y_TOL * (1 + np.abs(y_ref))
+    assert (np.abs(ev["log_energy"] - y_ref[:, 0]) <= tol[:, 0]).all()
+    ok = ~nodir
+    assert (np.abs(ev["dir_x"][ok] - s["base"][ok, 0] - y_ref[ok, 1]) <= tol[ok, 1] + 1e-4).all()
+    assert (np.abs(ev["dir_y"][ok] - s["base"][ok, 1] - y_ref[ok, 2]) <= tol[ok, 2] + 1e-4).all()
+    # |sigmoid(a) - sigmoid(b)| <= |a - b| / 4: the logit bar carried to the gammaness
+    sig = 1 / (1 + np.exp(-y_ref[:, 3]))
+    err = np.abs(ev["gammaness"] - sig) / (0.25 * (1 + np.abs(y_ref[:, 3])))
+    print("inference vs oracle: max scaled gammaness error", err.max())
+    assert err.max() <= Y_TOL
+    assert np.abs(y_ref).max() > 0.1 and ok.sum() > 0.3 * wl.n_evt
+
+
 def test_trained_network_gains_over_the_geometric_reconstruction():
     """Train on 24k mixed gamma/proton events with the GPU kernels, evaluate on 6k
     held-out events: the learned path adds an energy estimate and a gamma/hadron

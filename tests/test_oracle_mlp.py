@@ -142,3 +142,67 @@ def test_bf16_rounding():
     assert r[2] == 1.0 + 2 ** -6                                     # tie to even upwards
     assert r[3] == 1.0 + 2 ** -7 and r[4] == -2.5
     assert abs(r[5] / 3.0e38 - 1) < 2 ** -8
+
+
+def test_feature_rows_written_out_by_hand():
+    """Every one of the 12 feature columns, for hand-built events, against values
+    worked out on paper from the feature definition (log10 size, centroid minus
+    baseline, length, width, cos 2psi, sin 2psi, time gradient / 10, distance to
+    the baseline, camera code, telescope x and y in km). A slip such as cos psi
+    for cos 2psi, a missing /10, x instead of x - b_x, or the brightest pair taken
+    over unused images changes at least one entry."""
+    PI = np.pi
+    tel_xy = np.array([[100.0, -200.0], [250.0, 1000.0]])
+    tel_code = np.array([0.5, -0.25])
+
+    def row(size, x, y, L, W, psi, tg, npix, flags=0):
+        r = np.zeros(12)
+        r[[0, 1, 2, 3, 4, 5, 8, 10, 11]] = [size, x, y, L, W, psi, tg, npix, flags]
+        return r
+
+    rows = np.array([
+        # event 0: brightest used A (psi 0) and B (psi pi/4); C is brighter than B but has 2 pixels.
+        # A's axis y = 0.25 meets B's axis (-0.5 + t, 0.75 + t) at t = -0.5: b = (-1.0, 0.25)
+        row(1000.0, 0.5, 0.25, 0.25, 0.125, 0.0, 2.5, 10),
+        row(100.0, -0.5, 0.75, 0.5, 0.0625, PI / 4, -5.0, 7, flags=2),   # NO_TIME does not exclude
+        row(500.0, 2.0, 2.0, 0.1, 0.1, PI / 4, 0.0, 2),
+        # event 1: one used image (the other is flagged BAD_INPUT): b = its centroid
+        row(10.0, 0.125, -0.375, 0.2, 0.05, -PI / 4, 1.0, 5),
+        row(4000.0, 1.0, 1.0, 0.3, 0.1, 0.0, 0.0, 40, flags=4),
+        # event 2: the brightest pair is parallel (|sin| = 0 < 0.1): size-weighted mean of the
+        # used images, b = ((300 - 100) / 400, (0 + 40) / 400) = (0.5, 0.1)
+        row(300.0, 1.0, 0.0, 0.2, 0.1, 0.0, 0.0, 9),
+        row(100.0, -1.0, 0.4, 0.2, 0.1, 0.0, 0.0, 9),
+        # event 3: three equal sizes; ties go to the lower index, so the pair is images 0 and 1
+        # of the event (parallel, psi = 0): the mean of all three, b = (0, 0.5); the pair
+        # (0, 2) would have crossed at (0.5, 0)
+        row(200.0, 0.0, 0.0, 0.2, 0.1, 0.0, 0.0, 9),
+        row(200.0, -1.5, 0.5, 0.2, 0.1, 0.0, 0.0, 9),
+        row(200.0, 1.5, 1.0, 0.2, 0.1, PI / 4, 0.0, 9),
+        # event 4: an empty image only: b = (0, 0), log10 of the 1e-3 floor
+        row(0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0, flags=1),
+    ])
+    evt_off = np.array([0, 3, 5, 7, 10, 11])
+    img_tel = np.array([0, 1, 0, 1, 0, 0, 1, 1, 0, 1, 0])
+    X, used, base, n_used = mlp.features(rows, evt_off, img_tel, tel_xy, tel_code)
+    T0 = [0.5, 0.1, -0.2]          # code, x / km, y / km of telescope 0
+    T1 = [-0.25, 0.25, 1.0]
+    r2 = np.sqrt(0.5)
+    expect = np.array([
+        [3.0, 1.5, 0.0, 0.25, 0.125, 1.0, 0.0, 0.25, 1.5] + T0,
+        [2.0, 0.5, 0.5, 0.5, 0.0625, 0.0, 1.0, -0.5, r2] + T1,
+        [np.log10(500.0), 3.0, 1.75, 0.1, 0.1, 0.0, 1.0, 0.0, np.hypot(3.0, 1.75)] + T0,
+        [1.0, 0.0, 0.0, 0.2, 0.05, 0.0, -1.0, 0.1, 0.0] + T1,
+        [np.log10(4000.0), 0.875, 1.375, 0.3, 0.1, 1.0, 0.0, 0.0, np.hypot(0.875, 1.375)] + T0,
+        [np.log10(300.0), 0.5, -0.1, 0.2, 0.1, 1.0, 0.0, 0.0, np.hypot(0.5, 0.1)] + T0,
+        [2.0, -1.5, 0.3, 0.2, 0.1, 1.0, 0.0, 0.0, np.hypot(1.5, 0.3)] + T1,
+        [np.log10(200.0), 0.0, -0.5, 0.2, 0.1, 1.0, 0.0, 0.0, 0.5] + T1,
+        [np.log10(200.0), -1.5, 0.0, 0.2, 0.1, 1.0, 0.0, 0.0, 1.5] + T0,
+        [np.log10(200.0), 1.5, 0.5, 0.2, 0.1, 0.0, 1.0, 0.0, np.hypot(1.5, 0.5)] + T1,
+        [-3.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0] + T0,
+    ])
+    np.testing.assert_allclose(X, expect, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(base, [[-1.0, 0.25], [0.125, -0.375], [0.5, 0.1], [0.0, 0.5], [0.0, 0.0]],
+                               rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(used, [1, 1, 0, 1, 0, 1, 1, 1, 1, 1, 0])
+    np.testing.assert_array_equal(n_used, [2, 1, 2, 3, 0])

@@ -104,3 +104,109 @@ def test_noalloc_entry_rejects_sizes_beyond_its_scratch():
                                     dev.img_tel.data_ptr(), wl.n_img, mode, start, W, t_hi, t_lo, core_nb,
                                     out.data_ptr())
     assert e.value.code == rta.RTA_E_INVALID and "camera" in str(e.value)
+
+
+def _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, n_img, proc, out, status_ptr=0):
+    mode, start, W, t_hi, t_lo, core_nb = proc
+    rta.rta_image_chain_noalloc(descs, tel_cam, tel_row, d_p16.data_ptr(), d_scale.data_ptr(), n_rows,
+                                dev.wave.data_ptr(), dev.wave.numel(), dev.wave_off.data_ptr(),
+                                dev.img_tel.data_ptr(), n_img, mode, start, W, t_hi, t_lo, core_nb,
+                                out.data_ptr(), status_ptr, torch.cuda.current_stream().cuda_stream)
+
+
+def test_noalloc_status_is_reset_between_calls_and_optional():
+    # call 1 has one misaligned image offset: that row is skipped with RTA_HF_BAD_INPUT
+    # and the status word reports RTA_DEV_BAD_IMAGE; call 2 on the same stream is clean
+    # and must report 0, i.e. the shared scratch's status word was cleared in between
+    wl = synth.make_workload(2, 60)
+    descs, tel_cam, tel_row, d_p16, d_scale, n_rows, keep = caller_tables(wl)
+    proc = proc_args(wl)
+    dev = Dev(wl)
+    ctx = make_ctx(wl)
+    ref = dev.hillas_buf()
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, *proc, ref)
+    ctx.check()
+    status = torch.full((1,), 777, dtype=torch.int32, device="cuda")
+    bad = Dev(wl)
+    bad_img = wl.n_img // 2
+    bad.wave_off[bad_img] += 4                        # 8 bytes: breaks the 16-byte rule
+    out1 = torch.full_like(ref, float("nan"))
+    _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, bad, wl.n_img, proc, out1, status.data_ptr())
+    torch.cuda.synchronize()
+    assert int(status.item()) & rta.RTA_DEV_BAD_IMAGE
+    r1 = hillas_rows(out1, wl.n_img)
+    assert r1["flags"][bad_img] & rta.RTA_HF_BAD_INPUT
+    keep_rows = np.arange(wl.n_img) != bad_img
+    u1 = out1.cpu().numpy().reshape(-1, 16).view(np.uint32)
+    uref = ref.cpu().numpy().reshape(-1, 16).view(np.uint32)
+    np.testing.assert_array_equal(u1[keep_rows], uref[keep_rows])
+    out2 = torch.full_like(ref, float("nan"))
+    _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, out2, status.data_ptr())
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    np.testing.assert_array_equal(out2.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+    # no status pointer: the same rows
+    out3 = torch.full_like(ref, float("nan"))
+    _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, out3, 0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out3.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+    ctx.close()
+
+
+def test_noalloc_ignores_neighbour_ids_outside_the_camera():
+    # the caller's neighbour tables are not validated: ids outside [0, n_pix) must act
+    # like -1 (never read), so the rows equal a context whose tables hold -1 there
+    wl = synth.make_workload(2, 80)
+    descs, tel_cam, tel_row, d_p16, d_scale, n_rows, keep = caller_tables(wl)
+    rng = np.random.default_rng(5)
+    cam_ids = sorted(wl.cams)
+    ctx = rta.Context(0)
+    planted = 0
+    for i, c in enumerate(cam_ids):
+        cam = wl.cams[c]
+        nb = np.array(cam.nb, np.int16).copy()
+        nb8 = np.full((cam.n_pix, 8), -1, np.int16)
+        nb8[:, :cam.K] = nb
+        rows = rng.choice(cam.n_pix, size=cam.n_pix // 3, replace=False)
+        for p in rows:
+            j = int(rng.integers(cam.K))
+            nb8[p, j] = rng.choice([cam.n_pix, cam.n_pix + 1, 4095, 32767, -2, -32768])
+            nb[p, j] = -1
+            planted += 1
+        d_nb8 = torch.from_numpy(nb8).cuda()
+        keep.append(d_nb8)
+        descs[i] = rta.CameraDesc(cam.n_pix, cam.n_samples, cam.K, descs[i].d_pix_xy, d_nb8.data_ptr())
+        ctx.register_camera(c, cam.xy, nb, cam.n_samples)
+    ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
+    assert planted > 1000
+    proc = proc_args(wl)
+    assert proc[5] == 1        # the core-neighbour test reads the tables too
+    dev = Dev(wl)
+    ref = dev.hillas_buf()
+    ctx.image_chain(dev.wave, dev.wave_off, dev.img_tel, *proc, ref)
+    ctx.check()
+    status = torch.full((1,), 777, dtype=torch.int32, device="cuda")
+    out = torch.full_like(ref, float("nan"))
+    _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, out, status.data_ptr())
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+    ctx.close()
+
+
+def test_noalloc_rejects_bad_calibration_rows():
+    wl = synth.make_workload(2, 5)
+    descs, tel_cam, tel_row, d_p16, d_scale, n_rows, keep = caller_tables(wl)
+    dev = Dev(wl)
+    out = dev.hillas_buf()
+    proc = proc_args(wl)
+    for bad in (tel_row + np.where(np.arange(len(tel_row)) == 3, 4, 0),     # not a multiple of 8
+                tel_row + np.where(np.arange(len(tel_row)) == len(tel_row) - 1, 8, 0)):  # no slack left
+        with pytest.raises(rta.RtaError) as e:
+            _call(descs, tel_cam, bad.astype(np.int64), d_p16, d_scale, n_rows, dev, wl.n_img, proc, out)
+        assert e.value.code == rta.RTA_E_INVALID and "calibration row" in str(e.value)
+    bad_cam = tel_cam.copy()
+    bad_cam[0] = len(descs)
+    with pytest.raises(rta.RtaError) as e:
+        _call(descs, bad_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, out)
+    assert e.value.code == rta.RTA_E_INVALID
