@@ -10,7 +10,9 @@ Tolerances (floating point; integer and byte outputs are compared bit-exact):
   psi                  1e-4 rad modulo pi, where (length - width) / length > 1e-2
   time gradient        |d| <= 1e-3 + 1e-4 |ref| where n_pix >= 5 and elongated as above,
                        with the sign taken along the GPU's psi orientation
-  stereo direction     1e-3 deg; core 0.05 m (stage-isolated: both sides get the same FP32 rows)
+  stereo direction     1e-3 deg; core 0.05 m + 2e-6 |core| (stage-isolated: both sides get the
+                       same FP32 rows; the relative term is FP32 rounding of the core itself,
+                       which for events with nearly parallel axes lies hundreds of km away)
 """
 import numpy as np
 import torch
@@ -24,6 +26,12 @@ T_ABS = 1e-3
 TG_ABS, TG_REL = 1e-3, 1e-4
 DIR_DEG = 1e-3
 CORE_M = 0.05
+CORE_REL = 2e-6
+
+
+def core_ok(gx, gy, rx, ry):
+    """Stage-isolated core parity: |d| <= CORE_M + CORE_REL |ref| per event."""
+    return np.hypot(gx - rx, gy - ry) <= CORE_M + CORE_REL * np.hypot(rx, ry)
 
 
 def make_ctx(wl, device=0):

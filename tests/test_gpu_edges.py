@@ -11,8 +11,8 @@ import oracle
 import synth
 import paper_1307_6489_gb300 as rta
 
-from gpu_helpers import (CORE_M, DIR_DEG, T_ABS, Dev, compare_hillas, hillas_rows, hillas_rows_as_f32, make_ctx, proc_args,
-                         stereo_rows, f32_rows_as_oracle)
+from gpu_helpers import (DIR_DEG, T_ABS, Dev, compare_hillas, core_ok, hillas_rows, hillas_rows_as_f32, make_ctx,
+                         proc_args, stereo_rows, f32_rows_as_oracle)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -264,7 +264,7 @@ def test_full_size_bundle_every_event():
     np.testing.assert_array_equal(g["n_valid"], exp[:, S["n_valid"]].astype(np.int32))
     ok = exp[:, S["flags"]] == 0
     assert np.max(np.hypot(g["dir_x"][ok] - exp[ok, S["dir_x"]], g["dir_y"][ok] - exp[ok, S["dir_y"]])) <= DIR_DEG
-    assert np.max(np.hypot(g["core_x"][ok] - exp[ok, S["core_x"]], g["core_y"][ok] - exp[ok, S["core_y"]])) <= CORE_M
+    assert core_ok(g["core_x"][ok], g["core_y"][ok], exp[ok, S["core_x"]], exp[ok, S["core_y"]]).all()
     ctx.close()
 
 

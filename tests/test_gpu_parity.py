@@ -12,7 +12,7 @@ import pytest
 import oracle
 import synth
 
-from gpu_helpers import (CORE_M, DIR_DEG, T_ABS, Dev, compare_hillas, f32_rows_as_oracle, hillas_rows,
+from gpu_helpers import (CORE_M, DIR_DEG, core_ok, T_ABS, Dev, compare_hillas, f32_rows_as_oracle, hillas_rows,
                          hillas_rows_as_f32, make_ctx, proc_args, stereo_rows)
 
 torch = pytest.importorskip("torch")
@@ -162,7 +162,7 @@ def test_stereo_stage_isolated(setup):
     dcore = np.hypot(g["core_x"][ok] - exp[ok, S["core_x"]], g["core_y"][ok] - exp[ok, S["core_y"]])
     print("stereo max |ddir| deg", ddir.max(), "max |dcore| m", dcore.max())
     assert ddir.max() <= DIR_DEG
-    assert dcore.max() <= CORE_M
+    assert core_ok(g["core_x"][ok], g["core_y"][ok], exp[ok, S["core_x"]], exp[ok, S["core_y"]]).all()
 
 
 def test_reconstruct_end_to_end(setup):
