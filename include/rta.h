@@ -353,8 +353,8 @@ int rta_reconstruct_host(rta_ctx* ctx, const uint16_t* h_wave, int64_t n_wave, c
  * Packed parameter order (rta_surrogate_num_params() floats, row-major):
  * W1[12x128], b1[128], W2[128x128], b2[128], V1[256x256], c1[256], V2[256x4], c2[4].
  * The model borrows the context's telescope tables and must not outlive it.
- * Calls that need a larger batch than any before grow the model's device
- * workspace (an allocation). */
+ * Forward and training calls that need a larger batch than any before grow the
+ * model's device workspace (an allocation); inference needs none. */
 typedef struct rta_model rta_model;
 int rta_surrogate_num_params(void);
 /* h_cam_code: RTA_MAX_CAMS floats, the type code of each camera id (NULL = zeros). */
@@ -377,7 +377,9 @@ int rta_surrogate_train_step(rta_model* model, const rta_hillas_t* d_hillas, con
  * with fewer than 2 used images get RTA_EF_NO_DIRECTION (the geometric method
  * is undefined too); events whose learned offset from the baseline exceeds
  * fallback_deg get the geometric intersection of rta_stereo (computed for those
- * events only) and RTA_EF_FALLBACK. */
+ * events only, the same bits as rta_stereo gives them) and RTA_EF_FALLBACK, or
+ * RTA_EF_NO_DIRECTION when that intersection is invalid. One kernel launch, no
+ * model workspace and no allocation: calls on different streams may overlap. */
 int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream);
 

@@ -15,7 +15,7 @@
 namespace rta {
 
 // ------------------------------------------------------------------ features
-// Eight lanes per event (four events per warp); also the first stage of inference.
+// SUR_EVT_LANES lanes per event; the inference kernel forms baselines and features the same way.
 __global__ void __launch_bounds__(256) k_features(const FeatArgs a) {
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int sub = lane % SUR_EVT_LANES;
@@ -185,6 +185,7 @@ __global__ void k_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t
 
 // ------------------------------------------------------------------ pooling
 // P[e] = [sum_used h2 / 40, sum_used h2 / max(1, n_used)] (BF16). One block per event, 128 threads (one per channel).
+// The mean multiplies by the event's reciprocal count (RN(1 / n)), as the inference kernel does.
 __global__ void __launch_bounds__(SUR_H) k_pool(const PoolArgs a) {
     const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
     const int ch = threadIdx.x;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(SUR_H) k_pool(const PoolArgs a) {
                     ++cnt;
                 }
         a.P[e * 2 * SUR_H + ch] = __float2bfloat16(s * (1.f / SUR_POOL_DIV));
-        a.P[e * 2 * SUR_H + SUR_H + ch] = __float2bfloat16(s / fmaxf(1.f, float(cnt)));
+        a.P[e * 2 * SUR_H + SUR_H + ch] = __float2bfloat16(s * (1.f / fmaxf(1.f, float(cnt))));
     }
 }
 
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(SUR_H) k_pool_bwd(const PoolArgs a) {
         if (a.n_used[e] >= 0)
             for (int i = i0; i < i1; ++i) cnt += a.used[i] ? 1 : 0;
         const float g = __bfloat162float(a.dP[e * 2 * SUR_H + ch]) * (1.f / SUR_POOL_DIV) +
-                        __bfloat162float(a.dP[e * 2 * SUR_H + SUR_H + ch]) / fmaxf(1.f, float(cnt));
+                        __bfloat162float(a.dP[e * 2 * SUR_H + SUR_H + ch]) * (1.f / fmaxf(1.f, float(cnt)));
         if (a.n_used[e] < 0) continue;
         for (int i = i0; i < i1; ++i) {
             const float h = __bfloat162float(a.H2[int64_t(i) * SUR_H + ch]);
@@ -338,32 +339,6 @@ __global__ void k_head_bwd_dv2(const HeadArgs a) {
     }
 }
 
-// Inference outputs: direction = baseline + offsets; fallback list for the geometric pass.
-__global__ void k_outputs(const OutArgs a) {
-    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n_evt; e += int64_t(gridDim.x) * blockDim.x) {
-        const float y[4] = {a.Y[e * 4 + 0], a.Y[e * 4 + 1], a.Y[e * 4 + 2], a.Y[e * 4 + 3]};
-        sur_emit_event(a, e, y, a.base[e], a.n_used[e]);
-    }
-}
-
-// Geometric direction for the events on the fallback list (after k_stereo_list).
-__global__ void k_apply_fallback(const OutArgs a) {
-    const unsigned n = *a.n_fallback;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int e = a.fallback_idx[i];
-        const rta_stereo_t s = a.geo[i];
-        rta_event_t r = a.out[e];
-        if (!(s.flags & RTA_SF_INVALID)) {
-            r.dir_x = s.dir_x;
-            r.dir_y = s.dir_y;
-        } else {
-            r.flags |= RTA_EF_NO_DIRECTION;
-        }
-        a.out[e] = r;
-    }
-}
-
 // ------------------------------------------------------------------ Adam
 // FP32 master weights; BF16 copies of the GEMM operands refreshed in the same pass.
 __global__ void k_adam(const AdamArgs a) {
@@ -416,11 +391,6 @@ cudaError_t launch_head_bwd(const HeadArgs& a, int grid, cudaStream_t s) {
 cudaError_t launch_loss(const LossArgs& a, int grid, float* d_loss, cudaStream_t s) {
     k_loss<<<grid, 256, 0, s>>>(a);
     if (d_loss) k_loss_sum<<<1, 256, 0, s>>>(a.lterm, a.n_evt, a.n_evt_dev, d_loss);
-    return cudaGetLastError();
-}
-cudaError_t launch_outputs(const OutArgs& a, int grid, bool apply_fallback, cudaStream_t s) {
-    if (apply_fallback) k_apply_fallback<<<grid, 256, 0, s>>>(a);
-    else k_outputs<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t* rows_dev, int64_t rows, int cols,

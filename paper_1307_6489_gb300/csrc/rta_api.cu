@@ -321,8 +321,6 @@ int run_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     a.n_evt = n_evt;
     a.n_img_dev = d_n_img;
     a.n_evt_dev = d_n_evt;
-    a.evt_idx = nullptr;
-    a.n_list_dev = nullptr;
     a.out = d_out;
     a.status = c->d_status;
     const int epb = rta::stereo_events_per_block();
@@ -353,28 +351,6 @@ int rta::surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2*
 }
 
 unsigned int* rta::surrogate_ctx_status(rta_ctx* c) { return c ? c->d_status : nullptr; }
-
-int rta::surrogate_stereo_list(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
-                               const int32_t* d_evt_off, int64_t n_evt, const int32_t* d_idx, const unsigned int* d_n,
-                               rta_stereo_t* d_out, cudaStream_t s) {
-    rta::StereoArgs a;
-    a.arr = dev_array(c);
-    a.h = d_h;
-    a.img_tel = d_img_tel;
-    a.n_img = n_img;
-    a.evt_off = d_evt_off;
-    a.n_evt = n_evt;
-    a.n_img_dev = nullptr;
-    a.n_evt_dev = nullptr;
-    a.evt_idx = d_idx;
-    a.n_list_dev = d_n;
-    a.out = d_out;
-    a.status = c->d_status;
-    const int epb = rta::stereo_events_per_block();
-    int64_t g = std::min<int64_t>((n_evt + epb - 1) / epb, int64_t(c->n_sm) * 16);
-    CUDA_TRY(rta::launch_stereo(a, int(std::max<int64_t>(g, 1)), s));
-    return RTA_OK;
-}
 
 // ======================================================================= C ABI
 extern "C" {

@@ -52,6 +52,13 @@ struct ProcParams {
 };
 
 // ------------------------------------------------------------------ PTX helpers
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while the kernel before it on the
+// stream is finishing; this wait (a no-op otherwise) returns once that kernel
+// has completed and its memory is visible. Nothing an earlier kernel writes may
+// be read before it.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -82,8 +82,6 @@ struct StereoArgs {
     int64_t n_evt;             // events (capacity when n_evt_dev is set)
     const int64_t* n_img_dev;  // optional device-resident counts, read at run time
     const int64_t* n_evt_dev;
-    const int32_t* evt_idx;    // optional list of events: output e is event evt_idx[e]
-    const unsigned int* n_list_dev;  // length of that list (device), <= n_evt
     rta_stereo_t* out;
     unsigned int* status;
 };
@@ -218,8 +216,4 @@ int surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt);
 int surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2** tel_xy, int* n_tel, int* device);
 // the context's device status word
 unsigned int* surrogate_ctx_status(rta_ctx* c);
-int surrogate_stereo_list(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
-                          const int32_t* d_evt_off, int64_t n_evt, const int32_t* d_idx, const unsigned int* d_n,
-                          rta_stereo_t* d_out, cudaStream_t s);
-
 }  // namespace rta

@@ -15,6 +15,10 @@
 
 namespace rta {
 
+// Lanes per event of the per-event prologue (used images, baseline): a pair, so
+// that 256 threads take 128 events at once (half of the events have 2-3 images).
+constexpr int SUR_EVT_LANES = 2;
+
 // internal parameter layout (FP32 master copy and its BF16 twin), element offsets
 constexpr int64_t OFF_W1 = 0;                                // [16 x 128], rows 12..15 zero
 constexpr int64_t OFF_B1 = OFF_W1 + SUR_XPAD * SUR_H;
@@ -106,30 +110,19 @@ struct LossArgs {
 };
 
 struct OutArgs {
-    int64_t n_evt;
-    const int64_t* n_evt_dev;
-    const float* Y;
-    const float2* base;
-    const int32_t* n_used;
-    float fallback_deg;
-    rta_event_t* out;
-    unsigned int* n_fallback;
-    int32_t* fallback_idx;
-    const rta_stereo_t* geo;
+    float fallback_deg;        // learned offsets beyond this take the geometric direction
+    rta_event_t* out;          // [n_evt]
     unsigned int* status;      // device status word (RTA_DEV_*)
 };
 
-// Inference: f carries the inputs and tables, and receives the baselines and
-// used counts (its X/used are not touched); the output block's Y/base are not
-// read.
+// Inference: f carries the inputs and tables (its X/used/base/n_used are not
+// touched).
 struct InferArgs {
     FeatArgs f;
     const __nv_bfloat16* pb;   // BF16 parameter twin (internal layout)
     const float* p;            // FP32 master (biases)
     const __nv_bfloat16* pk;   // tensor-core weight layout (PK_*)
-    __nv_bfloat16* P;          // pooled vectors, per event tile a canonical 128 x 256 operand block (workspace)
-    int tel_tile_events;       // events per k_tel tile, 1..32
-    int ev_tile_events;        // events per k_event tile, 1..128
+    int rows_aligned;          // f.h is 16-byte aligned: a tile's rows may arrive by bulk copy
     OutArgs o;
 };
 
@@ -149,13 +142,13 @@ cudaError_t launch_pool(const PoolArgs& a, int grid, bool bwd, cudaStream_t s);
 cudaError_t launch_head(const HeadArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_head_bwd(const HeadArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_loss(const LossArgs& a, int grid, float* d_loss, cudaStream_t s);
-cudaError_t launch_outputs(const OutArgs& a, int grid, bool apply_fallback, cudaStream_t s);
 cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t* rows_dev, int64_t rows, int cols,
                           float* out, cudaStream_t s);
 cudaError_t launch_reduce_splits(const float* ws, int splits, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
-// k_tel then k_event (one CTA per SM, n_sm of them at most). a.P holds
-// ceil(n_evt / ev_tile_events) * 128 * 256 BF16 values.
+// The whole inference in one persistent launch (one CTA per SM, n_sm of them at
+// most, each with an equal share of the image rows; programmatic dependent
+// launch), geometric fallback included.
 cudaError_t launch_infer(const InferArgs& a, int n_sm, cudaStream_t s);
 // BF16 twin -> tensor-core weight layout
 cudaError_t launch_pack_tc(const __nv_bfloat16* pb, __nv_bfloat16* pk, cudaStream_t s);

@@ -36,9 +36,6 @@ __device__ __forceinline__ bool sur_used(const rta_hillas_t& h) {
     return h.n_pix >= 3 && !(h.flags & (RTA_HF_EMPTY | RTA_HF_BAD_INPUT));
 }
 
-// Lanes per event in the feature kernel: most events have fewer than eight images.
-constexpr int SUR_EVT_LANES = 8;
-
 // Per-event prologue by a group of SUR_EVT_LANES lanes (sub = lane within the
 // group) over images [i0, i1) (n = i1 - i0, 0 for a malformed event): number of
 // used images, and the baseline direction -- the intersection of the axes of
@@ -46,7 +43,9 @@ constexpr int SUR_EVT_LANES = 8;
 // size-weighted centroid when they are nearly parallel or only one image is
 // used. Every lane of the warp must call it (the group reductions shuffle
 // across the full warp); all lanes of a group return the same values.
-// used_out (nullable) receives the per-image flags.
+// used_out (nullable) receives the per-image flags. Its quotients and angle
+// functions are the fast forms (absolute errors below 1e-6 on these arguments,
+// |angle| < pi), which the training and inference paths share.
 __device__ __forceinline__ void sur_event_baseline(const rta_hillas_t* __restrict__ hrows, int i0, int n, int sub,
                                                    uint8_t* used_out, float& bx, float& by, int& n_used) {
     // Sizes are positive, so their bit patterns order like the values; the low
@@ -90,20 +89,20 @@ __device__ __forceinline__ void sur_event_baseline(const rta_hillas_t* __restric
     bool done = false;
     if (cnt >= 2 && idx1 >= 0 && idx2 >= 0) {
         const rta_hillas_t A = hrows[i0 + idx1], B = hrows[i0 + idx2];
-        const float s = sinf(B.psi - A.psi);
+        const float s = __sinf(B.psi - A.psi);
         if (fabsf(s) >= SUR_BASE_MIN_SIN) {
             float sa, ca, sb, cb2;
-            sincosf(A.psi, &sa, &ca);
-            sincosf(B.psi, &sb, &cb2);
-            const float k = ((B.x - A.x) * sb - (B.y - A.y) * cb2) / s;
+            __sincosf(A.psi, &sa, &ca);
+            __sincosf(B.psi, &sb, &cb2);
+            const float k = __fdividef((B.x - A.x) * sb - (B.y - A.y) * cb2, s);
             bx = A.x + k * ca;
             by = A.y + k * sa;
             done = true;
         }
     }
     if (!done && cnt >= 1) {
-        bx = swx / sw;
-        by = swy / sw;
+        bx = __fdividef(swx, sw);
+        by = __fdividef(swy, sw);
     }
     n_used = cnt;
 }
@@ -120,34 +119,12 @@ __device__ __forceinline__ void sur_image_features(const rta_hillas_t& h, int te
     const float code = tel_ok ? cam_code[tel_cam[tel]] : 0.f;
     const float dx = h.x - bx, dy = h.y - by;
     float s2, c2;
-    sincosf(2.f * h.psi, &s2, &c2);
-    const float f[SUR_XPAD] = {log10f(fmaxf(h.size, 1e-3f)), dx, dy, h.length, h.width, c2, s2,
+    __sincosf(2.f * h.psi, &s2, &c2);      // fast forms: their errors (~1e-6) are far below the BF16 rounding
+    const float f[SUR_XPAD] = {__log10f(fmaxf(h.size, 1e-3f)), dx, dy, h.length, h.width, c2, s2,
                                h.time_grad * 0.1f, sqrtf(dx * dx + dy * dy), code, txy.x * 1e-3f,
                                txy.y * 1e-3f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < SUR_XPAD / 2; ++j) out[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-}
-
-// One event's inference output from the network outputs y and the baseline:
-// direction = baseline + offset; events whose offset exceeds the fallback bound
-// go on the list for the geometric intersection.
-__device__ __forceinline__ void sur_emit_event(const OutArgs& a, int64_t e, const float (&y)[4], float2 b, int n_used) {
-    rta_event_t r = {};
-    r.log_energy = y[0];
-    r.dir_x = b.x + y[1];
-    r.dir_y = b.y + y[2];
-    r.gammaness = 1.f / (1.f + expf(-y[3]));
-    r.n_used = n_used;
-    r.base_x = b.x;
-    r.base_y = b.y;
-    if (n_used < 2) {
-        r.flags |= RTA_EF_NO_DIRECTION;        // the geometric method is undefined as well
-    } else if (sqrtf(y[1] * y[1] + y[2] * y[2]) > a.fallback_deg) {
-        r.flags |= RTA_EF_FALLBACK;
-        const unsigned slot = atomicAdd(a.n_fallback, 1u);
-        a.fallback_idx[slot] = int(e);
-    }
-    a.out[e] = r;
 }
 
 }  // namespace rta

@@ -56,19 +56,13 @@ struct rta_model {
     int32_t* n_used = nullptr;
     __nv_bfloat16 *P = nullptr, *G = nullptr, *dG = nullptr, *dP = nullptr;
     float *Y = nullptr, *dY = nullptr, *lterm = nullptr;
-    unsigned int* n_fallback = nullptr;
-    int32_t* fallback_idx = nullptr;
-    rta_stereo_t* geo = nullptr;
-    // pooled vectors of the inference kernels, one canonical 128 x 256 block per event tile
-    __nv_bfloat16* Pc = nullptr;
-    int64_t cap_pc = 0;
 };
 
 namespace {
 
 void free_ws(rta_model* md) {
     void* ptrs[] = {md->X, md->H1, md->H2, md->dZ1, md->dZ2, md->used, md->base, md->n_used, md->P, md->G, md->dG,
-                    md->dP, md->Y, md->dY, md->lterm, md->n_fallback, md->fallback_idx, md->geo};
+                    md->dP, md->Y, md->dY, md->lterm};
     for (void* q : ptrs) cudaFree(q);
     md->X = md->H1 = md->H2 = md->dZ1 = md->dZ2 = nullptr;
     md->used = nullptr;
@@ -76,31 +70,7 @@ void free_ws(rta_model* md) {
     md->n_used = nullptr;
     md->P = md->G = md->dG = md->dP = nullptr;
     md->Y = md->dY = md->lterm = nullptr;
-    md->n_fallback = nullptr;
-    md->fallback_idx = nullptr;
-    md->geo = nullptr;
     md->cap_img = md->cap_evt = 0;
-}
-
-// Events per k_event tile: one tile per SM, 32..128 events each.
-int event_tile(const rta_model* md, int64_t n_evt) {
-    const int64_t per_sm = (n_evt + md->n_sm - 1) / md->n_sm;
-    return int(std::min<int64_t>(128, std::max<int64_t>(32, per_sm)));
-}
-
-// Grow the inference's pooled-vector workspace to n_tiles tiles of 128 x SUR_G.
-// (A growth frees and allocates, which synchronises the device: the serving
-// engine reserves its largest batch up front.)
-int reserve_pooled(rta_model* md, int64_t n_tiles) {
-    const int64_t need = n_tiles * 128 * SUR_G;
-    if (need <= md->cap_pc) return RTA_OK;
-    cudaFree(md->Pc);
-    md->Pc = nullptr;
-    md->cap_pc = 0;
-    if (cudaMalloc(&md->Pc, sizeof(__nv_bfloat16) * need) != cudaSuccess)
-        return sfail(RTA_E_NOMEM, "inference workspace allocation failed");
-    md->cap_pc = need;
-    return RTA_OK;
 }
 
 // Grow the activation workspace to hold n_img images and n_evt events.
@@ -119,9 +89,7 @@ int reserve(rta_model* md, int64_t n_img, int64_t n_evt) {
               al((void**)&md->G, sizeof(__nv_bfloat16) * ce * SUR_G) &&
               al((void**)&md->dG, sizeof(__nv_bfloat16) * ce * SUR_G) &&
               al((void**)&md->dP, sizeof(__nv_bfloat16) * ce * SUR_G) && al((void**)&md->Y, sizeof(float) * ce * 4) &&
-              al((void**)&md->dY, sizeof(float) * ce * 4) && al((void**)&md->lterm, sizeof(float) * ce) &&
-              al((void**)&md->n_fallback, sizeof(unsigned int)) &&
-              al((void**)&md->fallback_idx, sizeof(int32_t) * ce) && al((void**)&md->geo, sizeof(rta_stereo_t) * ce);
+              al((void**)&md->dY, sizeof(float) * ce * 4) && al((void**)&md->lterm, sizeof(float) * ce);
     if (!ok) {
         free_ws(md);
         return sfail(RTA_E_NOMEM, "surrogate workspace allocation failed");
@@ -171,14 +139,17 @@ int weight_grad(rta_model* md, const __nv_bfloat16* A, int64_t lda, const __nv_b
     return RTA_OK;
 }
 
+// Argument checks of a batch; with_workspace: also grow the layer-by-layer
+// workspace to the batch (the training path and the raw forward pass need it,
+// the fused inference kernel does not).
 int check_batch(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
-                const int32_t* d_evt_off, int64_t n_evt) {
+                const int32_t* d_evt_off, int64_t n_evt, bool with_workspace = true) {
     if (!md) return sfail(RTA_E_INVALID, "model is NULL");
     if (cudaSetDevice(md->device) != cudaSuccess) return sfail(RTA_E_CUDA, "cudaSetDevice failed");
     if (n_img < 0 || n_evt < 0 || n_img > (int64_t(1) << 30) || n_evt > (int64_t(1) << 30))
         return sfail(RTA_E_INVALID, "batch size out of range");
     if (n_evt > 0 && (!d_evt_off || (n_img > 0 && (!d_h || !d_img_tel)))) return sfail(RTA_E_INVALID, "NULL pointer");
-    return reserve(md, std::max<int64_t>(n_img, 1), std::max<int64_t>(n_evt, 1));
+    return with_workspace ? reserve(md, std::max<int64_t>(n_img, 1), std::max<int64_t>(n_evt, 1)) : RTA_OK;
 }
 
 int forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off,
@@ -199,7 +170,7 @@ int forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     f.base = md->base;
     f.n_used = md->n_used;
     if (n_img > 0) S_TRY(cudaMemsetAsync(md->X, 0, sizeof(__nv_bfloat16) * n_img * SUR_XPAD, s));
-    S_TRY(rta::launch_features(f, blocks_for(n_evt, 32), s));
+    S_TRY(rta::launch_features(f, blocks_for(n_evt, 256 / rta::SUR_EVT_LANES), s));
     const __nv_bfloat16* pb = md->pb;
     if (n_img > 0) {
         if ((rc = gemm(md->X, SUR_XPAD, false, pb + rta::OFF_W1, SUR_H, false, n_img, SUR_H, SUR_XPAD,
@@ -275,10 +246,7 @@ int upload_params(rta_model* md, const std::vector<float>& internal) {
 int rta::surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt) {
     if (!md) return sfail(RTA_E_INVALID, "model is NULL");
     S_TRY(cudaSetDevice(md->device));
-    const int rc = reserve(md, n_img, n_evt);
-    // the inference's pooled tiles for any batch of up to n_evt events: at most one
-    // tile per SM while the tiles hold up to 128 events, else n_evt / 128
-    return rc ? rc : reserve_pooled(md, std::max<int64_t>(md->n_sm, (n_evt + 127) / 128));
+    return reserve(md, n_img, n_evt);
 }
 
 extern "C" {
@@ -349,7 +317,6 @@ int rta_surrogate_destroy(rta_model* md) {
     cudaFree(md->p);
     cudaFree(md->pb);
     cudaFree(md->pk);
-    cudaFree(md->Pc);
     cudaFree(md->m);
     cudaFree(md->v);
     cudaFree(md->g);
@@ -478,7 +445,7 @@ int rta_surrogate_train_step(rta_model* md, const rta_hillas_t* d_h, const int32
 
 int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream) {
-    int rc = check_batch(md, d_h, d_img_tel, n_img, d_evt_off, n_evt);
+    int rc = check_batch(md, d_h, d_img_tel, n_img, d_evt_off, n_evt, false);
     if (rc) return rc;
     if (n_evt == 0) return RTA_OK;
     if (!d_out) return sfail(RTA_E_INVALID, "NULL output");
@@ -492,39 +459,14 @@ int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d
     ia.f.n_evt = n_evt;
     if ((rc = rta::surrogate_ctx_tables(md->ctx, &ia.f.tel_cam, &ia.f.tel_xy, &ia.f.n_tel, nullptr))) return rc;
     ia.f.cam_code = md->cam_code;
-    ia.f.base = md->base;
-    ia.f.n_used = md->n_used;
     ia.pb = md->pb;
     ia.p = md->p;
     ia.pk = md->pk;
-    // k_event: one tile per SM, 32..128 events each
-    {
-        ia.ev_tile_events = event_tile(md, n_evt);
-        if ((rc = reserve_pooled(md, (n_evt + ia.ev_tile_events - 1) / ia.ev_tile_events))) return rc;
-        ia.P = md->Pc;
-    }
-    // k_tel runs two CTAs per SM; tiles of up to 32 events, sized so that the
-    // CTAs get equal numbers of tiles
-    {
-        const int64_t slots = int64_t(md->n_sm) * 2;
-        const int64_t rounds = (n_evt + slots * 32 - 1) / (slots * 32);
-        ia.tel_tile_events = int((n_evt + slots * rounds - 1) / (slots * rounds));
-    }
-    rta::OutArgs& oa = ia.o;
-    oa.n_evt = n_evt;
-    oa.fallback_deg = fallback_deg;
-    oa.out = d_out;
-    oa.n_fallback = md->n_fallback;
-    oa.fallback_idx = md->fallback_idx;
-    oa.geo = md->geo;
-    oa.status = rta::surrogate_ctx_status(md->ctx);
-    S_TRY(cudaMemsetAsync(md->n_fallback, 0, sizeof(unsigned int), s));
+    ia.rows_aligned = (reinterpret_cast<uintptr_t>(d_h) & 15u) == 0;
+    ia.o.fallback_deg = fallback_deg;
+    ia.o.out = d_out;
+    ia.o.status = rta::surrogate_ctx_status(md->ctx);
     S_TRY(rta::launch_infer(ia, md->n_sm, s));
-    // the geometric intersection only for the events that need it
-    if ((rc = rta::surrogate_stereo_list(md->ctx, d_h, d_img_tel, n_img, d_evt_off, n_evt, md->fallback_idx,
-                                         md->n_fallback, md->geo, s)))
-        return rc;
-    S_TRY(rta::launch_outputs(oa, blocks_for(n_evt, 256), true, s));
     return RTA_OK;
 }
 
