@@ -890,6 +890,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 fetch_next();
             }
             if (img >= n_img) {
+                grid_dependents_launch();    // no image left to take: the next kernel may be scheduled
                 if (!acquire(stage, phase)) { ok = false; break; }
                 StageHdr h = {};
                 h.img = -1;

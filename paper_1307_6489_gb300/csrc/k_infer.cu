@@ -1,39 +1,44 @@
 // Inference of the deep-sets surrogate (energy, direction offset and
 // gamma/hadron score next to the geometric direction, Sec. 4.1) in ONE
-// persistent kernel on the fifth-generation tensor cores: a CTA per SM takes a
-// tile of up to 128 consecutive events and carries it from the Hillas rows to
-// the event rows, geometric fallback included:
+// persistent kernel on the fifth-generation tensor cores: a CTA of 512 threads
+// per SM takes an equal share of the bundle's image rows (a range of whole
+// events) and carries it from the Hillas rows to the event rows, geometric
+// fallback included, in tiles of at most 128 events:
 //
-//   1. per event (a pair of lanes): used images and the two-image baseline;
-//   2. per 128 image rows: the features, the per-telescope network
-//      16 -> 128 -> 128 (ReLU; BF16 activations re-staged as the next layer's
-//      operand) and the sum over each event's used images (image order);
+//   1. the tile's Hillas rows arrive by one bulk copy; per event (a pair of
+//      lanes) the used images and the two-image baseline;
+//   2. the features of up to 512 rows at once, then per 128 image rows the
+//      per-telescope network 16 -> 128 -> 128 (ReLU; BF16 activations re-staged
+//      as the next layer's operand) and the sum over each event's used images
+//      (image order, channel by channel);
 //   3. the pooled vectors [sum / 40, mean] as the A operand of the event
-//      network 256 -> 256 (ReLU), then the 256 -> 4 output layer in FP32 from
-//      the BF16-rounded activations;
+//      network 256 -> 256 (ReLU), whose BF16-rounded activations are the A
+//      operand of the 256 -> 4 output layer (N padded to 16);
 //   4. the events whose learned offset exceeds the fallback bound get the
-//      stereo intersection of their images, computed by the CTA's warps with
-//      the stereo kernel's own pieces (rta_stereo_dev.cuh), so their direction
-//      equals rta_stereo's bit for bit.
+//      stereo intersection of their images, computed with the stereo kernel's
+//      own pieces and grouping (rta_stereo_dev.cuh), so their direction equals
+//      rta_stereo's bit for bit.
 //
 // tcgen05 usage: operands in shared memory as canonical K-major core matrices
 // (rta_tc.cuh), FP32 accumulators in tensor memory (256 columns: the two
-// per-telescope layers, later the event network), one thread issuing the MMAs
-// and committing them to an mbarrier that the CTA waits on with a time limit.
-// Weights arrive by bulk copies; the event network's 128 KB V1^T shares its
-// shared memory with the per-telescope stage (its tail is copied at the start,
-// its head once the per-telescope stage is done).
+// per-telescope layers, later the event network and the output layer), one
+// thread issuing the MMAs and committing them to an mbarrier that the CTA waits
+// on with a time limit; four warps share each TMEM lane quarter, each taking a
+// slice of the columns. Weights arrive by bulk copies; the event network's
+// 128 KB V1^T shares its shared memory with the per-telescope stage (its tail,
+// over the staged rows, follows the last feature pass; its head the last
+// pooling).
 //
 // The kernel is launched with programmatic dependent launch: everything before
 // griddepcontrol.wait (tensor-memory allocation, barriers, the registered
 // telescope tables) overlaps the end of the kernel before it on the stream;
 // nothing that earlier stream work may write is read before the wait.
 //
-// The features and the eight-lane event reductions are the training path's own
+// The features and the per-event reductions are the training path's own
 // expressions (rta_mlp_dev.cuh), so baselines and used counts equal those of
-// k_features bit for bit (the same lanes per event); the layers sum their exact BF16 products in FP32 in
-// the tensor core's order, so the outputs agree with the training-path forward
-// to accumulation-order effects.
+// k_features bit for bit (the same lanes per event); the layers sum their exact
+// BF16 products in FP32 in the tensor core's order, so the outputs agree with
+// the training-path forward to accumulation-order effects.
 #include <algorithm>
 
 #include "rta_mlp_dev.cuh"
@@ -43,8 +48,10 @@
 namespace rta {
 namespace {
 
-constexpr int NT = 256;             // threads per CTA (eight warps)
+constexpr int NT = 512;             // threads per CTA (sixteen warps: four per TMEM lane quarter)
 constexpr int NW = NT / 32;
+constexpr int NSLICE = NW / 4;      // column slices of a TMEM row (warps sharing a lane quarter)
+constexpr int ST_NTC = 256;         // threads of the CTA-wide stereo (as in the stereo kernel)
 constexpr int TM = 128;             // MMA M: image rows per block, events per tile at most
 constexpr int LDH = SUR_H + 8;      // row stride of the row-major hidden tile used for pooling
 
@@ -70,9 +77,9 @@ constexpr size_t S_CODE = S_TXY + size_t(RTA_MAX_TEL) * 8;        // f32 [16] ca
 constexpr size_t S_B1 = S_CODE + size_t(RTA_MAX_CAMS) * 4;        // f32 [128]
 constexpr size_t S_B2 = S_B1 + SUR_H * 4;                         // f32 [128]
 constexpr size_t S_C1 = S_B2 + SUR_H * 4;                         // f32 [256]
-constexpr size_t S_V2 = S_C1 + SUR_G * 4;                         // f32 [256][4]
-constexpr size_t S_YP = S_V2 + size_t(SUR_G) * 4 * 4;             // f32 [128][4] second-half partial outputs
-constexpr size_t S_ROWB = S_YP + size_t(TM) * 4 * 4;              // int64 [129] first row of each event
+constexpr int NHEAD = 16;           // the output layer's MMA N: its 4 outputs and 12 zero columns
+constexpr size_t S_V2 = S_C1 + SUR_G * 4;                         // bf16 V2^T canonical [16][256] (rows 4.. zero)
+constexpr size_t S_ROWB = S_V2 + size_t(NHEAD) * SUR_G * 2;       // int64 [129] first row of each event
 constexpr size_t S_BASE = S_ROWB + size_t(TM + 1) * 8;            // float2 [128]
 constexpr size_t S_EOFF = S_BASE + size_t(TM) * 8;                // int [129 + pad] the tile's event offsets
 constexpr size_t S_LO = S_EOFF + size_t(TM + 4) * 4;              // int [128] first image
@@ -82,7 +89,7 @@ constexpr size_t S_INV = S_NU + size_t(TM) * 4;                   // f32 [128] 1
 constexpr size_t S_FB = S_INV + size_t(TM) * 4;                   // int [128] fallback list; [128] its count
 constexpr size_t S_FBB = S_FB + size_t(TM + 4) * 4;               // int [128] fallback events for the CTA; [128] count
 constexpr size_t S_RED = S_FBB + size_t(TM + 4) * 4;              // DW [8][5], int [8][2]: CTA-wide stereo sums
-constexpr size_t S_TEL = S_RED + size_t(NW) * 5 * sizeof(DW) + size_t(NW) * 2 * 4;    // int [672] staged rows' telescopes
+constexpr size_t S_TEL = S_RED + size_t(ST_NTC / 32) * (5 * sizeof(DW) + 2 * 4);    // int [672] staged rows' telescopes
 constexpr size_t S_USED = S_TEL + size_t(MAX_STAGED_ROWS) * 4;    // u8 [SB]
 constexpr size_t S_BAR = S_USED + SB;                             // 6 mbarriers, TMEM address, abort flag
 constexpr size_t S_TOTAL = S_BAR + 64;
@@ -124,22 +131,26 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase, volatile 
 // max() rule still gives every event to some CTA. scratch: 2 ints of shared memory.
 __device__ __forceinline__ void event_range(const int32_t* evt_off, int64_t n_evt, int* scratch, int64_t& begin,
                                             int64_t& end) {
-    const int tid = threadIdx.x, half = tid >> 7, k = tid & 127;
+    const int tid = threadIdx.x, half = (tid >> 7) & 1, k = tid & 127;
+    const bool act = tid < 256;                         // threads past 256 only join the barriers
     const int64_t G = gridDim.x, b = blockIdx.x;
-    const int64_t first = evt_off[0], total = max(int64_t(0), int64_t(evt_off[n_evt]) - first);
+    const int32_t first = evt_off[0], last = evt_off[n_evt];
     const int64_t j = b + half;                         // bound B_b (half 0) and B_b+1 (half 1)
-    const int64_t target = first + (total * j) / G;
     int64_t lo = 0, hi = n_evt;                         // the bound lies in [lo, hi]
-    if (j == 0) hi = 0;
+    if (j == 0 || !act) hi = 0;
     if (j == G) lo = n_evt;
     for (;;) {
-        const bool open = lo < hi;
+        const bool open = act && lo < hi;
         if (!__syncthreads_or(open)) break;
-        if (k == 0) scratch[half] = 128;
+        if (act && k == 0) scratch[half] = 128;
         __syncthreads();
         const int64_t step = open ? max(int64_t(1), (hi - lo + 127) / 128) : 1;
         const int64_t pk = lo + k * step;
-        if (open && pk < hi && int64_t(evt_off[pk]) >= target) atomicMin(&scratch[half], k);
+        const int64_t v = open && pk < hi ? int64_t(evt_off[pk]) : 0;
+        // the target after the sample's load: the first round's loads overlap
+        const int64_t total = max(int64_t(0), int64_t(last) - first);
+        const int64_t target = first + (total * j) / G;
+        if (open && pk < hi && v >= target) atomicMin(&scratch[half], k);
         __syncthreads();
         if (open) {
             const int kk = scratch[half];
@@ -152,7 +163,7 @@ __device__ __forceinline__ void event_range(const int32_t* evt_off, int64_t n_ev
             }
         }
     }
-    if (k == 0) scratch[half] = int(lo);
+    if (act && k == 0) scratch[half] = int(lo);
     __syncthreads();
     begin = scratch[0];
     end = max(begin, int64_t(scratch[1]));
@@ -176,8 +187,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
     float* b1s = reinterpret_cast<float*>(sm + S_B1);
     float* b2s = reinterpret_cast<float*>(sm + S_B2);
     float* c1s = reinterpret_cast<float*>(sm + S_C1);
-    float* V2f = reinterpret_cast<float*>(sm + S_V2);
-    float* yp = reinterpret_cast<float*>(sm + S_YP);
+    __nv_bfloat16* V2s = reinterpret_cast<__nv_bfloat16*>(sm + S_V2);
     int64_t* rowb = reinterpret_cast<int64_t*>(sm + S_ROWB);
     float2* base_s = reinterpret_cast<float2*>(sm + S_BASE);
     int* eoff_s = reinterpret_cast<int*>(sm + S_EOFF);
@@ -190,7 +200,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
     int* fbb_s = reinterpret_cast<int*>(sm + S_FBB);
     int* fbb_n = fbb_s + TM;
     DW* red_s = reinterpret_cast<DW*>(sm + S_RED);
-    int* redi_s = reinterpret_cast<int*>(sm + S_RED + size_t(NW) * 5 * sizeof(DW));
+    int* redi_s = reinterpret_cast<int*>(sm + S_RED + size_t(ST_NTC / 32) * 5 * sizeof(DW));
     int* tel_s = reinterpret_cast<int*>(sm + S_TEL);
     uint8_t* used_s = sm + S_USED;
     uint64_t* bar_mma = reinterpret_cast<uint64_t*>(sm + S_BAR);    // MMA completion
@@ -246,28 +256,16 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
         mbar_arrive_expect_tx(bar_w, uint32_t(W_BYTES));
         bulk_copy(Ws, a.pk + PK_W1T, uint32_t(W_BYTES), bar_w, l2_policy_evict_last());
     }
-    {
-        const float bb1 = tid < SUR_H ? a.p[OFF_B1 + tid] : 0.f, bb2 = tid < SUR_H ? a.p[OFF_B2 + tid] : 0.f;
-        const float c1 = a.p[OFF_C1 + tid];
-        float v2[SUR_G * 4 / NT];
-#pragma unroll
-        for (int k = 0; k < SUR_G * 4 / NT; ++k) v2[k] = __bfloat162float(a.pb[OFF_V2 + tid + k * NT]);
-        if (tid < SUR_H) {
-            b1s[tid] = bb1;
-            b2s[tid] = bb2;
-        }
-        c1s[tid] = c1;
-#pragma unroll
-        for (int k = 0; k < SUR_G * 4 / NT; ++k) V2f[tid + k * NT] = v2[k];
-    }
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_s;
-    const uint32_t idesc_h = tc_idesc_bf16(TM, SUR_H), idesc_g = tc_idesc_bf16(TM, SUR_G);
+    const uint32_t idesc_h = tc_idesc_bf16(TM, SUR_H), idesc_g = tc_idesc_bf16(TM, SUR_G),
+                   idesc_o = tc_idesc_bf16(TM, NHEAD);
+    const uint32_t v2_addr = smem_addr(V2s);
     const uint32_t x_addr = smem_addr(Xs), h_addr = smem_addr(Hs), w1_addr = smem_addr(Ws),
                    w2_addr = smem_addr(Ws + SUR_H * SUR_XPAD), p_addr = smem_addr(Ps), v_addr = smem_addr(sm);
-    const int q = warp & 3, row = 32 * q + lane;
-    const int c_half = (warp >> 2) * (SUR_H / 2), g_half = (warp >> 2) * (SUR_G / 2);
+    const int q = warp & 3, row = 32 * q + lane, slice = warp >> 2;
+    const int c_half = slice * (SUR_H / NSLICE), g_half = slice * (SUR_G / NSLICE);
     const uint32_t t_lane = uint32_t(32 * q) << 16;
     const int sub = lane % SUR_EVT_LANES, grp = lane / SUR_EVT_LANES;
     const float c2[4] = {a.p[OFF_C2 + 0], a.p[OFF_C2 + 1], a.p[OFF_C2 + 2], a.p[OFF_C2 + 3]};
@@ -285,16 +283,42 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
             bulk_copy(Ws, a.pk + PK_W1T, uint32_t(W_BYTES), bar_w, l2_policy_evict_last());
             w_fly = true;
         }
-        // ---- the tile's event offsets; pooling sums start at zero
-        if (tid <= ne) eoff_s[tid] = f.evt_off[e0 + tid];
+        // ---- the tile's event offsets (and, with the first tile, the biases and the output
+        // layer's weights, whose loads overlap); pooling sums start at zero
+        const int eo = tid <= ne ? f.evt_off[e0 + tid] : 0;
+        if (e0 == ev_begin) {
+            const float bb1 = tid < SUR_H ? a.p[OFF_B1 + tid] : 0.f, bb2 = tid < SUR_H ? a.p[OFF_B2 + tid] : 0.f;
+            const float c1 = tid < SUR_G ? a.p[OFF_C1 + tid] : 0.f;
+            // V2^T as the output layer's B operand: row n < 4 is output n, the rest zero
+            __nv_bfloat16 v2[NHEAD * SUR_G / NT];
+#pragma unroll
+            for (int k = 0; k < NHEAD * SUR_G / NT; ++k) {
+                const int i = tid + k * NT, n = i / SUR_G, kk = i % SUR_G;
+                v2[k] = n < 4 ? a.pb[OFF_V2 + kk * 4 + n] : __float2bfloat16(0.f);
+            }
+            if (tid < SUR_H) {
+                b1s[tid] = bb1;
+                b2s[tid] = bb2;
+            }
+            if (tid < SUR_G) c1s[tid] = c1;
+#pragma unroll
+            for (int k = 0; k < NHEAD * SUR_G / NT; ++k) {
+                const int i = tid + k * NT;
+                V2s[canon_off(i / SUR_G, i % SUR_G, SUR_G)] = v2[k];
+            }
+            fence_proxy_async_smem();
+        }
+        if (tid <= ne) eoff_s[tid] = eo;
         for (int i = tid; i < TM * PSTRIDE; i += NT) Pacc[i] = 0.f;
         if (tid == 0) *fb_n = *fbb_n = 0;
         __syncthreads();
         // ---- the tile's Hillas rows in shared memory when its offsets are well formed
         // (ascending, inside [0, n_img]) and they fit; else every row is read from global memory
         const bool ordered = tid >= ne || (eoff_s[tid] <= eoff_s[tid + 1] && eoff_s[tid] >= 0 && eoff_s[tid + 1] <= n_img);
-        const bool staged = __syncthreads_and(ordered) && a.rows_aligned &&
-                            eoff_s[ne] - eoff_s[0] <= MAX_STAGED_ROWS && eoff_s[ne] > eoff_s[0];
+        const bool wellformed = __syncthreads_and(ordered);
+        const bool staged = wellformed && a.rows_aligned && eoff_s[ne] - eoff_s[0] <= MAX_STAGED_ROWS &&
+                            eoff_s[ne] > eoff_s[0];
+        if (wellformed && tid <= ne) rowb[tid] = int64_t(eoff_s[tid]) - eoff_s[0];   // the tile's rows in order
         const int row_first = staged ? eoff_s[0] : 0;
         const rta_hillas_t* hrows = staged ? rows_s : f.h;
         if (staged) {
@@ -341,8 +365,9 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            // first row of each event in the tile: a scan of the row counts, four per lane
+        if (!wellformed && warp == 0) {
+            // first row of each event in the tile: a scan of the row counts (0 for a
+            // malformed event), four per lane
             int64_t v[4], run = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -430,7 +455,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
             mma_fly = false;
             // ReLU(D1 + b1) in BF16 -> canonical operand of layer 2 (this thread: one row, 64 columns)
 #pragma unroll 1
-            for (int cb = 0; cb < SUR_H / 2; cb += 32) {
+            for (int cb = 0; cb < SUR_H / NSLICE; cb += 32) {
                 const int c0 = c_half + cb;
                 uint32_t v[32];
                 tc_ld32(tmem + t_lane + uint32_t(c0), v);
@@ -466,7 +491,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
             // ReLU(D2 + b2) in BF16, +0 rows for unused images -> row-major tile for pooling
             const bool urow = used_s[xb * TM + row];
 #pragma unroll 1
-            for (int cb = 0; cb < SUR_H / 2; cb += 32) {
+            for (int cb = 0; cb < SUR_H / NSLICE; cb += 32) {
                 const int c0 = c_half + cb;
                 uint32_t v[32];
                 tc_ld32(tmem + SUR_H + t_lane + uint32_t(c0), v);
@@ -486,9 +511,10 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
             }
             tc_fence_before();
             __syncthreads();
-            // ---- pooling: thread = (channel pair, event group of four); each channel's
-            // sum runs over the event's rows in image order
+            // ---- pooling: thread = (channel pair, event group); each channel's sum runs
+            // over the event's rows in image order
             {
+                constexpr int NG = NT / 64;
                 const int cp = tid & 63, g4 = tid >> 6;
                 const int64_t rend = min(R, rb + TM);
                 int ev = 0, hi = ne - 1;                 // first event with a row in [rb, rend)
@@ -497,7 +523,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
                     if (rowb[mid + 1] <= rb) ev = mid + 1;
                     else hi = mid;
                 }
-                for (int el = ev + g4; el < ne && rowb[el] < rend; el += 4) {
+                for (int el = ev + g4; el < ne && rowb[el] < rend; el += NG) {
                     const int64_t lo = max(rowb[el], rb), up = min(rowb[el + 1], rend);
                     if (lo >= up) continue;
                     float2 s2 = reinterpret_cast<const float2*>(Pacc + el * PSTRIDE)[cp];
@@ -538,9 +564,10 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
         // Item i of this thread: event 8 (k / 128) + k % 8 and channels 8 ((k / 8) % 16) .. + 7,
         // k = tid + 256 i; every sum is read before any operand is written.
         {
-            float sv[8][8];
+            constexpr int NIT = TM * (SUR_H / 8) / NT;       // items per thread
+            float sv[NIT][8];
 #pragma unroll
-            for (int it = 0; it < 8; ++it) {
+            for (int it = 0; it < NIT; ++it) {
                 const int k = tid + NT * it;
                 const int el = 8 * (k >> 7) + (k & 7), ch = 8 * ((k >> 3) & 15);
                 const float4 u0 = *reinterpret_cast<const float4*>(Pacc + el * PSTRIDE + ch);
@@ -550,7 +577,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
             }
             __syncthreads();
 #pragma unroll
-            for (int it = 0; it < 8; ++it) {
+            for (int it = 0; it < NIT; ++it) {
                 const int k = tid + NT * it;
                 const int el = 8 * (k >> 7) + (k & 7), ch = 8 * ((k >> 3) & 15);
                 const bool live = el < ne;
@@ -591,113 +618,131 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
         if (!alive) break;
         ph_mma ^= 1u;
         mma_fly = false;
-        // ---- output layer: this thread's event row, half of the columns
-        float y[4] = {0.f, 0.f, 0.f, 0.f};
+        // ---- output layer on the tensor core: G = BF16(ReLU(acc + c1)) (this thread: one row,
+        // its slice of the columns) as the A operand in place of P, then y = G V2 (N = 16,
+        // outputs in TMEM columns 0-3, over the event network's consumed accumulators)
 #pragma unroll 1
-        for (int cb = 0; cb < SUR_G / 2; cb += 32) {
+        for (int cb = 0; cb < SUR_G / NSLICE; cb += 32) {
+            const int c0 = g_half + cb;
             uint32_t rr[32];
-            tc_ld32(tmem + t_lane + uint32_t(g_half + cb), rr);
+            tc_ld32(tmem + t_lane + uint32_t(c0), rr);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int col = g_half + cb + i;
-                const float g = __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(rr[i]) + c1s[col], 0.f)));
-                const float4 v2 = reinterpret_cast<const float4*>(V2f)[col];
-                y[0] = fmaf(g, v2.x, y[0]);
-                y[1] = fmaf(g, v2.y, y[1]);
-                y[2] = fmaf(g, v2.z, y[2]);
-                y[3] = fmaf(g, v2.w, y[3]);
+            for (int q8 = 0; q8 < 4; ++q8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = 8 * q8 + 2 * i;
+                    w[i] = bf2_bits(__floats2bfloat162_rn(fmaxf(__uint_as_float(rr[k]) + c1s[c0 + k], 0.f),
+                                                          fmaxf(__uint_as_float(rr[k + 1]) + c1s[c0 + k + 1], 0.f)));
+                }
+                *reinterpret_cast<uint4*>(Ps + canon_off(row, c0 + 8 * q8, SUR_G)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        if (g_half != 0) {
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int ks = 0; ks < SUR_G / 16; ++ks)
+                tc_mma(tmem, tc_desc(p_addr + 256u * ks, 128u, 16u * SUR_G), tc_desc(v2_addr + 256u * ks, 128u, 16u * SUR_G),
+                       idesc_o, ks > 0);
+            tc_commit(bar_mma);
+            mma_fly = true;
+        }
+        alive = tc_wait(bar_mma, ph_mma, abort_s, a.o.status);
+        if (!alive) break;
+        ph_mma ^= 1u;
+        mma_fly = false;
+        if (slice == 0) {
+            uint32_t rr[16];
+            tc_ld16(tmem + t_lane, rr);
+            if (row < ne) {
+                float yo[4];
 #pragma unroll
-            for (int o = 0; o < 4; ++o) yp[row * 4 + o] = y[o];
+                for (int o = 0; o < 4; ++o) yo[o] = __uint_as_float(rr[o]) + c2[o];
+                const int64_t e = e0 + row;
+                const float2 b = base_s[row];
+                const int nu = nu_s[row];
+                rta_event_t r = {};
+                r.log_energy = yo[0];
+                r.dir_x = b.x + yo[1];
+                r.dir_y = b.y + yo[2];
+                r.gammaness = 1.f / (1.f + expf(-yo[3]));
+                r.n_used = nu;
+                r.base_x = b.x;
+                r.base_y = b.y;
+                if (nu < 2) {
+                    r.flags |= RTA_EF_NO_DIRECTION;        // the geometric method is undefined as well
+                } else if (sqrtf(yo[1] * yo[1] + yo[2] * yo[2]) > a.o.fallback_deg) {
+                    r.flags |= RTA_EF_FALLBACK;
+                    if (cnt_s[row] > STEREO_WARP_M) fbb_s[atomicAdd(fbb_n, 1)] = row;   // for the CTA-wide pass
+                    else fb_s[atomicAdd(fb_n, 1)] = row;
+                }
+                a.o.out[e] = r;
+            }
         }
         tc_fence_before();
         __syncthreads();
-        if (g_half == 0 && row < ne) {
-            float yo[4];
-#pragma unroll
-            for (int o = 0; o < 4; ++o) yo[o] = (y[o] + yp[row * 4 + o]) + c2[o];
-            const int64_t e = e0 + row;
-            const float2 b = base_s[row];
-            const int nu = nu_s[row];
-            rta_event_t r = {};
-            r.log_energy = yo[0];
-            r.dir_x = b.x + yo[1];
-            r.dir_y = b.y + yo[2];
-            r.gammaness = 1.f / (1.f + expf(-yo[3]));
-            r.n_used = nu;
-            r.base_x = b.x;
-            r.base_y = b.y;
-            if (nu < 2) {
-                r.flags |= RTA_EF_NO_DIRECTION;        // the geometric method is undefined as well
-            } else if (sqrtf(yo[1] * yo[1] + yo[2] * yo[2]) > a.o.fallback_deg) {
-                r.flags |= RTA_EF_FALLBACK;
-                fb_s[atomicAdd(fb_n, 1)] = row;
-            }
-            a.o.out[e] = r;
-        }
-        __syncthreads();
         // ---- geometric fallback with the stereo kernel's grouping: up to STEREO_SMALL_M
         // images eight lanes, up to STEREO_WARP_M a warp (one event per warp at a time),
-        // larger events the whole CTA, one after another
+        // larger events ST_NTC threads (warps 0-7, one event after another) while the
+        // other warps take the smaller ones
         {
-            StereoImg* im = reinterpret_cast<StereoImg*>(sm) + warp * RTA_STEREO_MAX_M;
-            const int nfb = *fb_n;
-            for (int j = warp; j < nfb; j += NW) {
-                const int el = fb_s[j];
-                const int i0 = lo_s[el], m = min(cnt_s[el], RTA_STEREO_MAX_M);
-                if (m > STEREO_WARP_M) {
-                    if (lane == 0) fbb_s[atomicAdd(fbb_n, 1)] = el;
-                    continue;
-                }
-                int nvalid = 0;
-                for (int k = lane; k < m; k += 32)
-                    nvalid += stereo_stage(f.h[i0 + k], f.img_tel[i0 + k], n_tel, f.tel_xy, a.o.status, im + k);
-                __syncwarp();
-                rta_stereo_t sr;
-                if (m <= STEREO_SMALL_M) {
-                    // lanes 0-7 hold the event (eight-lane group 0); the other groups are empty
+            const int nsmall = *fb_n, nbig = *fbb_n;
+            if (nbig > 0 && warp < ST_NTC / 32) {
+                StereoImg* imc = reinterpret_cast<StereoImg*>(sm);
+                for (int j = 0; j < nbig; ++j) {
+                    const int el = fbb_s[j];
+                    const int i0 = lo_s[el], m = min(cnt_s[el], RTA_STEREO_MAX_M);
+                    int nvalid = 0;
+                    if (tid < m)
+                        nvalid = stereo_stage(f.h[i0 + tid], f.img_tel[i0 + tid], n_tel, f.tel_xy, a.o.status, imc + tid);
+                    stereo_bar<ST_NTC>();
                     CSum acc[5];
-                    const int npair = pair_sums<8>(im, lane < 8 ? m : 0, lane & 7, acc);
-                    sr = group_result<8>(acc, npair, nvalid);
-                } else {
-                    CSum acc[5];
-                    const int npair = pair_sums<32>(im, m, lane, acc);
-                    sr = group_result<32>(acc, npair, nvalid);
-                }
-                if (lane == 0) {
-                    rta_event_t* o = a.o.out + e0 + el;
-                    if (!(sr.flags & RTA_SF_INVALID)) {
-                        o->dir_x = sr.dir_x;
-                        o->dir_y = sr.dir_y;
-                    } else {
-                        o->flags |= RTA_EF_NO_DIRECTION;
+                    const int npair = pair_sums<ST_NTC>(imc, m, tid, acc);
+                    const rta_stereo_t sr = cta_result<ST_NTC>(acc, npair, nvalid, red_s, redi_s);
+                    if (tid == 0) {
+                        rta_event_t* o = a.o.out + e0 + el;
+                        if (!(sr.flags & RTA_SF_INVALID)) {
+                            o->dir_x = sr.dir_x;
+                            o->dir_y = sr.dir_y;
+                        } else {
+                            o->flags |= RTA_EF_NO_DIRECTION;
+                        }
                     }
                 }
-                __syncwarp();
-            }
-            __syncthreads();
-            StereoImg* imc = reinterpret_cast<StereoImg*>(sm);
-            const int nbig = *fbb_n;
-            for (int j = 0; j < nbig; ++j) {
-                const int el = fbb_s[j];
-                const int i0 = lo_s[el], m = min(cnt_s[el], RTA_STEREO_MAX_M);
-                int nvalid = 0;
-                if (tid < m) nvalid = stereo_stage(f.h[i0 + tid], f.img_tel[i0 + tid], n_tel, f.tel_xy, a.o.status,
-                                                   imc + tid);
-                __syncthreads();
-                CSum acc[5];
-                const int npair = pair_sums<NT>(imc, m, tid, acc);
-                const rta_stereo_t sr = cta_result<NT>(acc, npair, nvalid, red_s, redi_s);
-                if (tid == 0) {
-                    rta_event_t* o = a.o.out + e0 + el;
-                    if (!(sr.flags & RTA_SF_INVALID)) {
-                        o->dir_x = sr.dir_x;
-                        o->dir_y = sr.dir_y;
+            } else {
+                const int w0 = nbig > 0 ? ST_NTC / 32 : 0;
+                StereoImg* im = reinterpret_cast<StereoImg*>(sm) + warp * RTA_STEREO_MAX_M;
+                for (int j = warp - w0; j < nsmall; j += NW - w0) {
+                    const int el = fb_s[j];
+                    const int i0 = lo_s[el], m = min(cnt_s[el], RTA_STEREO_MAX_M);
+                    int nvalid = 0;
+                    for (int k = lane; k < m; k += 32)
+                        nvalid += stereo_stage(f.h[i0 + k], f.img_tel[i0 + k], n_tel, f.tel_xy, a.o.status, im + k);
+                    __syncwarp();
+                    rta_stereo_t sr;
+                    if (m <= STEREO_SMALL_M) {
+                        // lanes 0-7 hold the event (eight-lane group 0); the other groups are empty
+                        CSum acc[5];
+                        const int npair = pair_sums<8>(im, lane < 8 ? m : 0, lane & 7, acc);
+                        sr = group_result<8>(acc, npair, nvalid);
                     } else {
-                        o->flags |= RTA_EF_NO_DIRECTION;
+                        CSum acc[5];
+                        const int npair = pair_sums<32>(im, m, lane, acc);
+                        sr = group_result<32>(acc, npair, nvalid);
                     }
+                    if (lane == 0) {
+                        rta_event_t* o = a.o.out + e0 + el;
+                        if (!(sr.flags & RTA_SF_INVALID)) {
+                            o->dir_x = sr.dir_x;
+                            o->dir_y = sr.dir_y;
+                        } else {
+                            o->flags |= RTA_EF_NO_DIRECTION;
+                        }
+                    }
+                    __syncwarp();
                 }
             }
         }

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(ST_NT) k_stereo(const StereoArgs a) {
             const int bm = big_m[b];
             int nvalid = 0;
             if (threadIdx.x < bm) nvalid = stage_image(a, int64_t(big_i0[b]) + threadIdx.x, sh[0] + threadIdx.x);
-            __syncthreads();
+            stereo_bar<ST_NT>();
             CSum acc[5];
             const int npair = pair_sums<ST_NT>(sh[0], bm, threadIdx.x, acc);
             const rta_stereo_t r = cta_result<ST_NT>(acc, npair, nvalid, red, redi);

@@ -59,6 +59,13 @@ struct ProcParams {
 // be read before it.
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The kernel after this one on the stream, when launched as a programmatic
+// dependent, may be scheduled once every CTA of this kernel has signalled (or
+// exited): a CTA signals when it has taken its last work item, so that the next
+// kernel's set-up runs on SMs freed by the tail of this one. Its wait still
+// sees all of this kernel's writes.
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -74,13 +74,16 @@ __device__ __forceinline__ DW dw_warp_sum(DW v) {
     return v;
 }
 
-// (a.hi + a.lo) / (b.hi + b.lo) rounded to FP32 (one correction step).
+// (a.hi + a.lo) / (b.hi + b.lo) in FP32: a first quotient from the correctly
+// rounded reciprocal of b.hi, then one correction step with the exact residual
+// of that quotient (within about one unit in the last place of the result).
 __device__ __forceinline__ float dw_div(DW a, DW b) {
-    const float q = __fdiv_rn(a.hi, b.hi);
+    const float rb = __frcp_rn(b.hi);
+    const float q = __fmul_rn(a.hi, rb);
     const float p = __fmul_rn(q, b.hi);
     const float pe = __fmaf_rn(q, b.hi, -p);            // q * b.hi = p + pe exactly
     const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo), __fmul_rn(q, b.lo));
-    return __fadd_rn(q, __fdiv_rn(r, b.hi));
+    return __fmaf_rn(r, rb, q);
 }
 
 // One image staged for the pair loop from its Hillas row and telescope id: its
@@ -229,10 +232,17 @@ __device__ __forceinline__ rta_stereo_t group_result(CSum (&acc)[5], int npair, 
 constexpr int STEREO_SMALL_M = 8;
 constexpr int STEREO_WARP_M = 24;
 
-// Combine the sums of all NT threads of the CTA in a fixed order (a shuffle tree
-// per warp, then the warps in index order) and form the event's row; every
-// thread returns it. red: NT / 32 * 5 double words and redi: NT / 32 * 2 ints of
-// shared memory. Every thread of the CTA must call it.
+// Barrier of the first NT threads of the CTA (named barrier 1), so that a
+// larger CTA can run the CTA-wide stereo on a subset of its warps.
+template <int NT>
+__device__ __forceinline__ void stereo_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+// Combine the sums of threads 0 .. NT-1 in a fixed order (a shuffle tree per
+// warp, then the warps in index order) and form the event's row; every one of
+// them returns it. red: NT / 32 * 5 double words and redi: NT / 32 * 2 ints of
+// shared memory. Threads 0 .. NT-1 must all call it, and no other thread.
 template <int NT>
 __device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, int nvalid, DW* red, int* redi) {
     constexpr int NWC = NT / 32;
@@ -251,7 +261,7 @@ __device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, in
         redi[warp * 2] = npair;
         redi[warp * 2 + 1] = nvalid;
     }
-    __syncthreads();
+    stereo_bar<NT>();
     DW tot[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -263,7 +273,7 @@ __device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, in
         np += redi[w * 2];
         nv += redi[w * 2 + 1];
     }
-    __syncthreads();                                   // red and redi may be reused
+    stereo_bar<NT>();                                  // red and redi may be reused
     return stereo_row(tot, np, nv);
 }
 
