@@ -285,6 +285,114 @@ def stream_leg(ctx, wl, proc, stream, steps, e2e_steps, hil, ste):
                             "next upload overlapped"}}
 
 
+def config1_leg(n_events, hbm_peak, steps, device, cpu_events=20000, sample_events=300):
+    """The single large camera streamed from host memory: n_events events of the
+    1855-pixel hexagonal camera (40 samples, sliding 6-sample window, tailcut 8/4
+    with the neighbour test), about 30 GB at 200,000 events, in a pinned host
+    buffer. Reported: the image kernel's GB/s on one HBM-resident chunk (roofline
+    fraction), the end-to-end rate of rta_reconstruct_host over the whole stream
+    (its chunked, double-buffered host-to-device copies included), the oracle on
+    the first cpu_events events (all host cores), and a sampled parity check of
+    the streamed rows against the oracle."""
+    import torch
+    import oracle
+    import paper_1307_6489_gb300 as rta
+    import synth
+    t_setup = time.perf_counter()
+    wl = synth.make_workload(1, n_events, render=False)
+    host = torch.empty(wl.n_samples_total, dtype=torch.int16, pin_memory=True)
+    wave_h = host.numpy().view(np.uint16)
+    synth.render_waves(wl, wave_out=wave_h)
+    gen_s = time.perf_counter() - t_setup
+    ctx = rta.Context(device, hbm_budget_bytes=8 << 30)
+    for c, cam in wl.cams.items():
+        ctx.register_camera(c, cam.xy, cam.nb, cam.n_samples)
+    ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
+    p = wl.proc
+    proc = (rta.RTA_WINDOW_SLIDING if p.sliding else rta.RTA_WINDOW_FIXED, p.start, p.W, p.t_hi, p.t_lo,
+            p.core_needs_neighbour)
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    # the image kernel on one HBM-resident chunk of up to 20,000 events (~3 GB, larger than L2)
+    n_c = min(wl.n_evt, 20000)
+    i_c = int(wl.evt_off[n_c])
+    s_c = int(wl.wave_off[i_c]) if i_c < wl.n_img else wl.n_samples_total
+    wave_c = host[:s_c].to(dev)
+    off_c = torch.from_numpy(np.ascontiguousarray(wl.wave_off[:i_c])).to(dev)
+    tel_c = torch.from_numpy(np.ascontiguousarray(wl.img_tel[:i_c])).to(dev)
+    hil_c = torch.zeros(i_c * 16, dtype=torch.float32, device=dev)
+    h = ctx.handle
+
+    def chain():
+        rta.rta_image_chain(h, wave_c.data_ptr(), wave_c.numel(), off_c.data_ptr(), tel_c.data_ptr(), i_c, *proc,
+                            hil_c.data_ptr(), sp)
+
+    for _ in range(3):
+        chain()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        chain()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    chain_ms = e0.elapsed_time(e1) / steps
+    ctx.check(sp)
+    alg = 2 * s_c + 64 * i_c
+    kernel_gbs = alg / (chain_ms / 1e3) / 1e9
+    del wave_c
+    torch.cuda.empty_cache()
+    # end to end: the whole host stream through rta_reconstruct_host
+    hh = np.zeros(wl.n_img * 16, np.float32)
+    hs = np.zeros(wl.n_evt * 8, np.float32)
+    woff = np.ascontiguousarray(wl.wave_off)
+    itel = np.ascontiguousarray(wl.img_tel)
+    eoff = np.ascontiguousarray(wl.evt_off)
+    ctx.reconstruct_host(wave_h, woff, itel, eoff, *proc, hh, hs)      # warm (staging buffers)
+    passes = 2
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        ctx.reconstruct_host(wave_h, woff, itel, eoff, *proc, hh, hs)
+    e2e_s = (time.perf_counter() - t0) / passes
+    # the HBM-resident chunk and the streamed pass give the same rows
+    assert np.array_equal(hh[: i_c * 16].view(np.uint32), hil_c.cpu().numpy().view(np.uint32)), "streamed rows differ"
+    # sampled parity of the streamed rows against the oracle, over the whole stream
+    rng = np.random.default_rng(5)
+    ev = np.sort(rng.choice(wl.n_evt, min(sample_events, wl.n_evt), replace=False))
+    sub = synth.subset(wl, ev)
+    ref = oracle.reconstruct(sub, do_stereo=False)
+    g = rta.hillas_to_numpy(hh.reshape(-1, 16)[ev].reshape(-1))
+    H = oracle.H
+    nmatch = int(np.sum(g["n_pix"] == ref["hillas"][:, H["n_pix"]].astype(np.int32)))
+    ok = ref["hillas"][:, H["n_pix"]] > 0
+    rel = np.abs(g["size"][ok] - ref["hillas"][ok, H["size"]]) / ref["hillas"][ok, H["size"]]
+    parity = {"events": int(len(ev)), "n_pix_equal": nmatch, "max_size_rel_err": float(rel.max()) if ok.any() else 0.0,
+              "pass": bool(nmatch == len(ev) and (not ok.any() or rel.max() <= 1e-4))}
+    # the oracle on the first cpu_events events, all host cores
+    cores = os.cpu_count() or 1
+    n_o = min(cpu_events, wl.n_evt)
+    sub_o = synth.subset(wl, np.arange(n_o))
+    t0 = time.perf_counter()
+    oracle.reconstruct(sub_o, do_stereo=False, threads=cores)
+    cpu_s = time.perf_counter() - t0
+    out = {"workload": f"1855-pixel hexagonal camera, {wl.n_evt} events x 40 samples, {wl.wave_bytes / 1e9:.2f} GB "
+                       "in pinned host memory", "events": wl.n_evt, "bytes": wl.wave_bytes, "generate_s": gen_s,
+           "kernel": {"events_on_device": n_c, "ms": chain_ms, "gbs": kernel_gbs, "hbm_frac": kernel_gbs / hbm_peak,
+                      "events_per_s": n_c / (chain_ms / 1e3)},
+           "e2e": {"value": wl.n_evt / e2e_s, "unit": "events/s", "gbs": wl.wave_bytes / e2e_s / 1e9,
+                   "h2d_bytes_per_pass": wl.wave_bytes + wl.n_img * 12 + (wl.n_evt + 1) * 4,
+                   "d2h_bytes_per_pass": wl.n_img * 64 + wl.n_evt * 32, "passes": passes,
+                   "call": "rta_reconstruct_host (pinned host stream, chunked and double-buffered)"},
+           "cpu_baseline": {"value": n_o / cpu_s, "unit": "events/s", "cores": cores, "kind": "oracle",
+                            "sample": f"the first {n_o} events, {cpu_s:.1f} s on {cores} threads",
+                            "gbs": sub_o.wave_bytes / cpu_s / 1e9},
+           "parity_sampled": parity}
+    ctx.close()
+    del host
+    return out
+
+
 def cam_codes(wl):
     codes = np.zeros(16, np.float32)
     for c, cam in wl.cams.items():
@@ -408,6 +516,12 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
         return e0.elapsed_time(e1) / steps
 
     lut_path_ms = timed(lut_step)
+    # the geometric step timed exactly like the learned one (the same loop, no events between the kernels)
+    geo_loop_ms = timed(lambda: (rta.rta_image_chain(h, wave.data_ptr(), wave.numel(), wave_off.data_ptr(),
+                                                     img_tel.data_ptr(), wl.n_img, *proc, hil.data_ptr(), sp),
+                                 rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(),
+                                                wl.n_evt, ste.data_ptr(), sp)))
+    sur_ms = timed(sur_step)                       # again, next to it
     lut_ms = timed(lambda: rta.rta_lut_reconstruct(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img,
                                                    evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), *lut_args))
     stereo_ms = timed(lambda: rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(),
@@ -430,6 +544,8 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
     torch.cuda.synchronize()
     res = train.evaluate(rta.events_to_numpy(ev.cpu().numpy()), rta.stereo_to_numpy(ste.cpu().numpy()), wl.truth)
     out = {"ms_per_step": sur_ms, "events_per_s": wl.n_evt / (sur_ms / 1e3),
+           "geometric_same_loop_ms_per_step": geo_loop_ms,
+           "learned_vs_geometric_events_per_s": geo_loop_ms / sur_ms,
            "infer_ms": infer_full_ms, "infer_without_fallback_ms": infer_nofb_ms, "train_events": n_train,
            "train_steps": len(losses), "train_s": fit_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
            "accuracy_on_bundle": res, "lookup_tables": lut_out}
@@ -612,6 +728,8 @@ def main():
     ap.add_argument("--serve-rates", default="0.5,2,8,inf", help="aggregate arrival rates, GB/s (inf: a burst)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--chain", default="", help="fixed image-kernel config 'variant,stages,ctas_per_sm'")
+    ap.add_argument("--config1-events", type=int, default=200000,
+                    help="events of the single-camera stream leg (1855 px x 40 samples; 0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -828,6 +946,13 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
 
+    # ---------------- the single large camera streamed from host memory (last: ~30 GB pinned)
+    cfg1 = None
+    if args.config1_events > 0:
+        del host, wave_h
+        torch.cuda.empty_cache()
+        cfg1 = config1_leg(args.config1_events, hbm_peak, args.steps, local)
+
     if rank == 0:
         cfg = ctx.chain_config()
         line = {
@@ -860,6 +985,7 @@ def main():
             "paths": {"geometric": {"ms_per_step": ms_per_step, "events_per_s": wl.n_evt / (ms_per_step / 1e3)},
                       "surrogate": sur},
             "dl0_stream": stream_out,
+            "single_camera_stream": cfg1,
             "serving": {"rates": serving, "pool": pool_info, "budget_gb": 24 * 1.073741824, "slots": 4,
                         "model": "surrogate" if trainer else "geometric"} if serving else None,
             "p99_bundle_latency_ms": next((r["p99_ms"] for r in serving if r["rate_gbs"] == 8.0), None)
