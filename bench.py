@@ -400,58 +400,124 @@ def cam_codes(wl):
     return codes
 
 
-def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
-    """Train the deep-sets surrogate with the library's kernels on mixed gamma/proton
-    events (setup), then time the learned path on the benchmark bundle
-    (image kernel + surrogate with geometric fallback) against the geometric
-    path, and compare both with the generated truth."""
+def hillas_sets(ctx, calib_seed, proc, n_events, chunk=20000, seed0=1307064893):
+    """Hillas rows of n_events events of the learned-surrogate preset (the array,
+    gamma and proton showers) made the way a deployment makes them: waveforms
+    rendered chunk by chunk into device memory (the generator's GPU renderer:
+    same showers and noise as the host renderer, in FP32) and reconstructed by
+    the image kernel; only the 64-byte rows stay (device). Returns rows,
+    telescopes, event offsets, truth and camera codes."""
+    import torch
+    import synth
+    plans = []
+    k = 0
+    while sum(p.n_evt for p in plans) < n_events:
+        n = min(chunk, n_events - sum(p.n_evt for p in plans))
+        plans.append(synth.make_workload(3, n, seed=seed0 + 7919 * k, render=False, calib_seed=calib_seed))
+        k += 1
+    n_img = sum(p.n_img for p in plans)
+    rows = torch.zeros(n_img * 16, dtype=torch.float32, device="cuda")
+    tel = torch.from_numpy(np.concatenate([p.img_tel for p in plans]).astype(np.int32)).cuda()
+    dwave = torch.empty(max(p.n_samples_total for p in plans), dtype=torch.int16, device="cuda")
+    i0 = 0
+    for p in plans:
+        keep = synth.render_waves_gpu(p, dwave, torch.cuda.current_stream().cuda_stream)
+        off = torch.from_numpy(np.ascontiguousarray(p.wave_off)).cuda()
+        ctx.image_chain(dwave[: p.n_samples_total], off, tel[i0:i0 + p.n_img], *proc,
+                        rows[i0 * 16:(i0 + p.n_img) * 16])
+        torch.cuda.synchronize()
+        del keep
+        i0 += p.n_img
+    ctx.check()
+    offs, base = [0], 0
+    for p in plans:
+        offs.extend((p.evt_off[1:] + base).tolist())
+        base += p.n_img
+    truth = np.concatenate([p.truth for p in plans])
+    del dwave
+    torch.cuda.empty_cache()
+    return rows, tel, np.asarray(offs, np.int64), truth, cam_codes(plans[0])
+
+
+def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
+    """Train the deep-sets surrogate with the library's kernels on n_train mixed
+    gamma/proton events and judge it, next to the geometric reconstruction and
+    the lookup tables built from the same training events, on n_eval held-out
+    events (setup, outside any timed region); then time the learned path on the
+    benchmark bundle (image kernel + surrogate with geometric fallback) against
+    the geometric path."""
     import torch
     import paper_1307_6489_gb300 as rta
-    import synth
     from paper_1307_6489_gb300 import train
     wave, wave_off, img_tel, evt_off, hil, ste = dev_b
     sp = stream.cuda_stream
     t_setup = time.perf_counter()
-    tw = synth.make_workload(3, n_train, calib_seed=wl.seed)      # same array, same calibration
-    dwave = torch.from_numpy(tw.wave.view(np.int16)).cuda()
-    doff = torch.from_numpy(tw.wave_off).cuda()
-    dtel = torch.from_numpy(tw.img_tel).cuda()
-    devt = torch.from_numpy(tw.evt_off).cuda()
-    h_tr = train.reconstruct_images(ctx, dwave, doff, dtel, devt, proc)
-    logE = torch.from_numpy(np.log10(tw.truth[:, 0]).astype(np.float32)).cuda()
-    src = torch.from_numpy(tw.truth[:, 1:3].astype(np.float32).reshape(-1)).cuda()
-    gam = torch.from_numpy((tw.truth[:, 5] == 0).astype(np.uint8)).cuda()
-    tr = train.SurrogateTrainer(ctx, seed=1, cam_code=cam_codes(tw))
+    rows, tel, offs, truth, codes = hillas_sets(ctx, wl.seed, proc, n_train + n_eval)
+    gen_s = time.perf_counter() - t_setup
+    i_tr = int(offs[n_train])
+    h_tr, tel_tr, off_tr = rows[: i_tr * 16], tel[:i_tr], offs[: n_train + 1]
+    h_ev, tel_ev = rows[i_tr * 16:].contiguous(), tel[i_tr:].contiguous()
+    off_ev = (offs[n_train:] - i_tr).astype(np.int32)
+    tr_truth, ev_truth = truth[:n_train], truth[n_train:]
+    dev = wave.device
+    logE = torch.from_numpy(np.log10(tr_truth[:, 0]).astype(np.float32)).to(dev)
+    src = torch.from_numpy(tr_truth[:, 1:3].astype(np.float32).reshape(-1)).to(dev)
+    gam = torch.from_numpy((tr_truth[:, 5] == 0).astype(np.uint8)).to(dev)
+    tr = train.SurrogateTrainer(ctx, seed=1, cam_code=codes)
     t_fit = time.perf_counter()
-    losses = tr.fit(h_tr, dtel, tw.evt_off, logE, src, gam, epochs=25, batch_events=1024, lr=2e-3, lr_end=1e-4)
+    # about 6,000 Adam steps of 2,048 events whatever the training-set size (at least 3 epochs)
+    epochs = max(3, int(round(6000 * 2048 / n_train)))
+    losses = tr.fit(h_tr, tel_tr, off_tr, logE, src, gam, epochs=epochs, batch_events=2048, lr=2e-3, lr_end=5e-5)
     fit_s = time.perf_counter() - t_fit
     # lookup tables (calibration matrices) from the same training gammas at their true cores
-    se_d = torch.from_numpy(LUT_SIZE_EDGES).cuda()
-    de_d = torch.from_numpy(LUT_DIST_EDGES).cuda()
+    se_d = torch.from_numpy(LUT_SIZE_EDGES).to(dev)
+    de_d = torch.from_numpy(LUT_DIST_EDGES).to(dev)
     n_cells = rta.RTA_MAX_CAMS * (len(LUT_SIZE_EDGES) - 1) * (len(LUT_DIST_EDGES) - 1)
-    acc = torch.zeros(n_cells * 8, dtype=torch.float64, device=wave.device)
-    cells = torch.zeros(n_cells * 8, dtype=torch.float32, device=wave.device)
-    core_t = torch.from_numpy(tw.truth[:, 3:5].astype(np.float32).reshape(-1)).cuda()
-    rta.rta_lut_accumulate(ctx.handle, h_tr.data_ptr(), dtel.data_ptr(), tw.n_img, devt.data_ptr(), tw.n_evt,
+    acc = torch.zeros(n_cells * 8, dtype=torch.float64, device=dev)
+    cells = torch.zeros(n_cells * 8, dtype=torch.float32, device=dev)
+    core_t = torch.from_numpy(tr_truth[:, 3:5].astype(np.float32).reshape(-1)).to(dev)
+    devt_tr = torch.from_numpy(off_tr.astype(np.int32)).to(dev)
+    rta.rta_lut_accumulate(ctx.handle, h_tr.data_ptr(), tel_tr.data_ptr(), i_tr, devt_tr.data_ptr(), n_train,
                            logE.data_ptr(), core_t.data_ptr(), gam.data_ptr(), se_d.data_ptr(),
                            len(LUT_SIZE_EDGES) - 1, de_d.data_ptr(), len(LUT_DIST_EDGES) - 1, acc.data_ptr(), sp)
     rta.rta_lut_finalize(ctx.handle, acc.data_ptr(), n_cells, 10, cells.data_ptr(), sp)
-    lookup = torch.zeros(n_cells * rta.LUT_LOOKUP_BYTES // 4, dtype=torch.float32, device=wave.device)
+    lookup = torch.zeros(n_cells * rta.LUT_LOOKUP_BYTES // 4, dtype=torch.float32, device=dev)
     rta.rta_lut_prepare(ctx.handle, cells.data_ptr(), n_cells, lookup.data_ptr(), sp)
-    # protons of the training set stay out of the tables: their pass fraction is out of sample
-    st_tr = torch.zeros(tw.n_evt * 8, dtype=torch.float32, device=wave.device)
-    lev_tr = torch.zeros(tw.n_evt * 8, dtype=torch.float32, device=wave.device)
-    rta.rta_stereo(ctx.handle, h_tr.data_ptr(), dtel.data_ptr(), tw.n_img, devt.data_ptr(), tw.n_evt,
-                   st_tr.data_ptr(), sp)
-    rta.rta_lut_reconstruct(ctx.handle, h_tr.data_ptr(), dtel.data_ptr(), tw.n_img, devt.data_ptr(), tw.n_evt,
-                            st_tr.data_ptr(), lookup.data_ptr(), se_d.data_ptr(), len(LUT_SIZE_EDGES) - 1,
-                            de_d.data_ptr(), len(LUT_DIST_EDGES) - 1, LUT_CUTS, lev_tr.data_ptr(), sp)
+    # the held-out events: learned path, geometric path and lookup tables on the same rows
+    n_ev_img = h_ev.numel() // 16
+    devt_ev = torch.from_numpy(off_ev).to(dev)
+    st_ev = torch.zeros(n_eval * 8, dtype=torch.float32, device=dev)
+    lev_ev = torch.zeros(n_eval * 8, dtype=torch.float32, device=dev)
+    sev = torch.zeros(n_eval * 32, dtype=torch.uint8, device=dev)
+    rta.rta_stereo(ctx.handle, h_ev.data_ptr(), tel_ev.data_ptr(), n_ev_img, devt_ev.data_ptr(), n_eval,
+                   st_ev.data_ptr(), sp)
+    rta.rta_surrogate_infer(tr.model, h_ev.data_ptr(), tel_ev.data_ptr(), n_ev_img, devt_ev.data_ptr(), n_eval, 0.5,
+                            sev.data_ptr(), sp)
+    rta.rta_lut_reconstruct(ctx.handle, h_ev.data_ptr(), tel_ev.data_ptr(), n_ev_img, devt_ev.data_ptr(), n_eval,
+                            st_ev.data_ptr(), lookup.data_ptr(), se_d.data_ptr(), len(LUT_SIZE_EDGES) - 1,
+                            de_d.data_ptr(), len(LUT_DIST_EDGES) - 1, LUT_CUTS, lev_ev.data_ptr(), sp)
     torch.cuda.synchronize()
-    lt = rta.lut_events_to_numpy(lev_tr.cpu().numpy())
-    ok_tr = (lt["flags"] & (rta.RTA_LF_NO_CORE | rta.RTA_LF_NO_IMAGE | rta.RTA_LF_MALFORMED)) == 0
-    prot = tw.truth[:, 5] != 0
-    proton_pass = float(np.mean((lt["flags"][ok_tr & prot] & rta.RTA_LF_GAMMA) != 0)) if (ok_tr & prot).any() else None
-    del dwave, h_tr, st_tr, lev_tr
+    ctx.check(sp)
+    sev_np = rta.events_to_numpy(sev.cpu().numpy())
+    held_out = train.evaluate(sev_np, rta.stereo_to_numpy(st_ev.cpu().numpy()), ev_truth)
+    lt = rta.lut_events_to_numpy(lev_ev.cpu().numpy())
+    ok_l = (lt["flags"] & (rta.RTA_LF_NO_CORE | rta.RTA_LF_NO_IMAGE | rta.RTA_LF_MALFORMED)) == 0
+    g_ev = ev_truth[:, 5] == 0
+    # the learned energy on exactly the gammas the tables give an energy for
+    sub = ok_l & g_ev & ((sev_np["flags"] & rta.RTA_EF_NO_DIRECTION) == 0)
+    d_s = sev_np["log_energy"][sub] - np.log10(ev_truth[sub, 0])
+    held_out["energy_res_on_table_events"] = float(np.std(d_s)) if sub.any() else None
+    held_out["energy_bias_on_table_events"] = float(np.mean(d_s)) if sub.any() else None
+    d_le = lt["log_energy"][ok_l & g_ev] - np.log10(ev_truth[ok_l & g_ev, 0])
+    lut_held_out = {"with_energy_frac": float(np.mean(ok_l[g_ev])) if g_ev.any() else None,
+                    "energy_bias": float(np.mean(d_le)) if len(d_le) else None,
+                    "energy_res": float(np.std(d_le)) if len(d_le) else None,
+                    "gamma_pass": float(np.mean((lt["flags"][ok_l & g_ev] & rta.RTA_LF_GAMMA) != 0))
+                    if (ok_l & g_ev).any() else None,
+                    "proton_pass": float(np.mean((lt["flags"][ok_l & ~g_ev] & rta.RTA_LF_GAMMA) != 0))
+                    if (ok_l & ~g_ev).any() else None}
+    proton_pass = lut_held_out["proton_pass"]
+    del rows, h_tr, h_ev, st_ev, lev_ev, sev
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     # timed: image kernel + learned reconstruction on the bundle
@@ -538,7 +604,7 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
                                       "energy_res": float(np.std(d_le)) if len(d_le) else None,
                                       "gamma_pass": float(np.mean((le["flags"][ok & g_b] & rta.RTA_LF_GAMMA) != 0))
                                       if (ok & g_b).any() else None},
-               "proton_pass_train_set": proton_pass}
+               "proton_pass_held_out": proton_pass}
     # accuracy on the bundle (gamma showers) against the geometric result of the same images
     rta.rta_stereo(h, hil.data_ptr(), img_tel.data_ptr(), wl.n_img, evt_off.data_ptr(), wl.n_evt, ste.data_ptr(), sp)
     torch.cuda.synchronize()
@@ -547,7 +613,9 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train):
            "geometric_same_loop_ms_per_step": geo_loop_ms,
            "learned_vs_geometric_events_per_s": geo_loop_ms / sur_ms,
            "infer_ms": infer_full_ms, "infer_without_fallback_ms": infer_nofb_ms, "train_events": n_train,
-           "train_steps": len(losses), "train_s": fit_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
+           "held_out_events": n_eval, "train_epochs": epochs, "train_steps": len(losses), "train_s": fit_s,
+           "generate_and_reconstruct_s": gen_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
+           "held_out": held_out, "held_out_lookup_tables": lut_held_out,
            "accuracy_on_bundle": res, "lookup_tables": lut_out}
     return out, tr
 
@@ -724,7 +792,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
-    ap.add_argument("--train-events", type=int, default=24000)
+    ap.add_argument("--train-events", type=int, default=2000000)
+    ap.add_argument("--eval-events", type=int, default=1000000)
     ap.add_argument("--serve-rates", default="0.5,2,8,inf", help="aggregate arrival rates, GB/s (inf: a burst)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--chain", default="", help="fixed image-kernel config 'variant,stages,ctas_per_sm'")
@@ -927,7 +996,7 @@ def main():
     sur, trainer, serving, pool_info = None, None, None, None
     if not args.no_surrogate:
         sur, trainer = surrogate_leg(ctx, wl, (wave, wave_off, img_tel, evt_off, hil, ste), proc, stream, args.steps,
-                                     args.train_events)
+                                     args.train_events, args.eval_events)
     if not args.no_serving:
         rates = [float(r) for r in args.serve_rates.split(",")]
         serving, pool_info = serving_leg(ctx, trainer.model if trainer else None, wl, wave_h, proc, rates,

@@ -73,6 +73,77 @@ def _L():
     return _lib
 
 
+_GPU_SRC = os.path.join(_HERE, "synth_gpu.cu")
+_GPU_LIB = os.path.join(_HERE, "libsynth_gpu.so")
+_gpu_lib = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile libsynth_gpu.so in-tree (nvcc, sm_103a): the GPU renderer for bulk inputs."""
+    if force or not os.path.exists(_GPU_LIB) or os.path.getmtime(_GPU_LIB) < os.path.getmtime(_GPU_SRC):
+        tmp = _GPU_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([os.environ.get("NVCC", "nvcc"), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                               "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, _GPU_SRC])
+        os.replace(tmp, _GPU_LIB)
+    return _GPU_LIB
+
+
+class _RenderGpuArgs(ctypes.Structure):
+    P = ctypes.c_void_p
+    _fields_ = [("seed", ctypes.c_uint64), ("n_img", ctypes.c_int64), ("img_evt", P), ("img_tel", P),
+                ("tel_cam", P), ("tel_pix_off", P), ("ped", P), ("gain", P), ("ell", P), ("n_ell", P),
+                ("cam_xy", P * 16), ("cam_pix", ctypes.c_int * 16), ("cam_samp", ctypes.c_int * 16),
+                ("cam_area", ctypes.c_float * 16), ("wave_off", P), ("wave", P), ("inv_norm", ctypes.c_float)]
+
+
+def _GL():
+    global _gpu_lib
+    if _gpu_lib is None:
+        build_gpu()
+        lib = ctypes.CDLL(_GPU_LIB)
+        lib.synth_render_gpu.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        if lib.synth_render_gpu_args_size() != ctypes.sizeof(_RenderGpuArgs):
+            raise RuntimeError("libsynth_gpu argument block does not match")
+        _gpu_lib = lib
+    return _gpu_lib
+
+
+def render_waves_gpu(wl: "Workload", d_wave, stream: int = 0):
+    """Render the workload's waveforms on the GPU into the device buffer d_wave (a
+    torch CUDA tensor of at least n_samples_total 16-bit values), asynchronously on
+    `stream`. The same model and random streams as render_waves, in FP32: the
+    samples follow the same distributions but are not equal to the host
+    renderer's bit for bit (bulk training and evaluation sets only; parity tests
+    use render_waves). Returns the tensors the kernel reads, which must stay alive
+    until it has run."""
+    import torch
+    dev = d_wave.device
+    assert d_wave.numel() >= wl.n_samples_total and d_wave.element_size() == 2
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev, non_blocking=False)
+    keep = [t(wl.img_evt, np.int32), t(wl.img_tel, np.int32), t(wl.tel_cam, np.int32), t(wl.tel_pix_off, np.int64),
+            t(wl.ped, np.float32), t(wl.gain, np.float32), t(wl.ell.reshape(len(wl.img_tel), -1), np.float32),
+            t(wl.n_ell, np.int32), t(wl.wave_off, np.int64)]
+    a = _RenderGpuArgs()
+    a.seed = wl.seed
+    a.n_img = wl.n_img
+    a.img_evt, a.img_tel, a.tel_cam, a.tel_pix_off, a.ped, a.gain, a.ell, a.n_ell, a.wave_off = \
+        [k.data_ptr() for k in keep]
+    for c, cam in wl.cams.items():
+        xy = t(cam.xy, np.float32)
+        keep.append(xy)
+        a.cam_xy[c] = xy.data_ptr()
+        a.cam_pix[c] = cam.n_pix
+        a.cam_samp[c] = cam.n_samples
+        a.cam_area[c] = cam.pix_area
+    a.wave = d_wave.data_ptr()
+    k = np.arange(-60, 61, dtype=np.float64)
+    a.inv_norm = float(1.0 / np.exp(-k * k / (2 * 1.5 * 1.5)).sum())
+    rc = _GL().synth_render_gpu(ctypes.byref(a), int(min(wl.n_img, 1 << 20)), stream)
+    if rc != 0:
+        raise RuntimeError(f"synth_render_gpu failed: CUDA error {rc}")
+    return keep
+
+
 def _p(a: np.ndarray):
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.c_void_p)

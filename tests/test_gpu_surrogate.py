@@ -222,7 +222,7 @@ def test_trained_network_gains_over_the_geometric_reconstruction():
     print("surrogate vs geometric:", res)
     assert res["energy_res"] < 0.3 and abs(res["energy_bias"]) < 0.1
     assert res["auc_gamma_hadron"] > 0.75
-    assert res["r68_ratio"] < 1.5
+    assert res["r68_ratio"] < 1.1            # the bound on the learned direction: at most 1.1x geometric
     tr.close()
     ctx.close()
 
