@@ -439,6 +439,37 @@ def hillas_sets(ctx, calib_seed, proc, n_events, chunk=20000, seed0=1307064893):
     return rows, tel, np.asarray(offs, np.int64), truth, cam_codes(plans[0])
 
 
+def oracle_forward_baseline(tr, h_dev, tel_dev, evt_off, codes, n_evt):
+    """The oracle's learned reconstruction (features and FP64 forward pass, numpy)
+    on the first n_evt held-out events with the trained weights, timed on the
+    host: the CPU baseline of the learned path."""
+    import oracle
+    import paper_1307_6489_gb300 as rta
+    from oracle import mlp
+    import synth
+    n_img = int(evt_off[n_evt])
+    g = rta.hillas_to_numpy(h_dev[: n_img * 16].cpu().numpy())
+    H = oracle.H
+    rows = np.zeros((n_img, 12))
+    for k in rta.HILLAS_FIELDS:
+        rows[:, H[k]] = g[k]
+    rows[:, H["n_pix"]] = g["n_pix"]
+    rows[:, H["flags"]] = g["flags"]
+    tel = tel_dev[:n_img].cpu().numpy()
+    tel_cam, tel_xy = np.zeros(69, np.int32), np.zeros(138, np.float32)
+    synth._L().synth_array(synth._p(tel_cam), synth._p(tel_xy))
+    params = rta.unpack_params(rta.rta_surrogate_get_params(tr.model, 0))
+    params = {k: mlp.bf16_round(v) for k, v in params.items()}
+    off = np.asarray(evt_off[: n_evt + 1], np.int64)
+    t0 = time.perf_counter()
+    X, used, base, n_used = mlp.features(rows, off, tel, tel_xy.reshape(-1, 2).astype(np.float64), codes[tel_cam])
+    y, _ = mlp.forward(params, mlp.bf16_round(X), used, off)
+    dt = time.perf_counter() - t0
+    return {"value": n_evt / dt, "unit": "events/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"features and FP64 forward pass of the first {n_evt} held-out events ({n_img} images), "
+                      f"{dt:.1f} s (numpy; the matrix products may use the host's threads)"}
+
+
 def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
     """Train the deep-sets surrogate with the library's kernels on n_train mixed
     gamma/proton events and judge it, next to the geometric reconstruction and
@@ -517,6 +548,7 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
                     "proton_pass": float(np.mean((lt["flags"][ok_l & ~g_ev] & rta.RTA_LF_GAMMA) != 0))
                     if (ok_l & ~g_ev).any() else None}
     proton_pass = lut_held_out["proton_pass"]
+    cpu_fwd = oracle_forward_baseline(tr, h_ev, tel_ev, off_ev, codes, min(100000, n_eval))
     del rows, h_tr, h_ev, st_ev, lev_ev, sev
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
@@ -615,7 +647,7 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
            "infer_ms": infer_full_ms, "infer_without_fallback_ms": infer_nofb_ms, "train_events": n_train,
            "held_out_events": n_eval, "train_epochs": epochs, "train_steps": len(losses), "train_s": fit_s,
            "generate_and_reconstruct_s": gen_s, "setup_s": setup_s, "final_loss": float(np.mean(losses[-20:])),
-           "held_out": held_out, "held_out_lookup_tables": lut_held_out,
+           "held_out": held_out, "held_out_lookup_tables": lut_held_out, "cpu_baseline_forward": cpu_fwd,
            "accuracy_on_bundle": res, "lookup_tables": lut_out}
     return out, tr
 
