@@ -652,36 +652,70 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
     return out, tr
 
 
-def build_serving_pool(wl, wave_h, n_bundles, rng, max_events):
-    """Bundles of sub-array events cut from the benchmark bundle into their own
-    pinned host buffers: each takes a random event range and a random subset of
-    20-69 telescopes and keeps the events with at least two images left."""
+def serving_feed(wl, n_events, rng, seg_events=5000, seed0=1307064895):
+    """The telescope feed of the serving leg: n_events array events in one pinned
+    host buffer, made of segments of seg_events events, each triggered on its own
+    random sub-array of 20-69 telescopes (same array and calibration as wl),
+    rendered on the GPU (the generator's GPU renderer) and copied out. A bundle
+    is any contiguous event range of it, so bundles of 1k-50k events mix
+    sub-arrays without copies of their own."""
     import torch
-    pool = []
-    P = np.array([wl.cams[int(c)].n_pix * wl.cams[int(c)].n_samples for c in wl.tel_cam], np.int64)
+    import synth
+    plans, k = [], 0
+    while sum(p.n_evt for p in plans) < n_events:
+        sub = rng.choice(len(wl.tel_cam), size=int(rng.integers(20, len(wl.tel_cam) + 1)), replace=False)
+        plans.append(synth.make_workload(2, min(seg_events, n_events - sum(p.n_evt for p in plans)),
+                                         seed=seed0 + 7919 * k, render=False, telescopes=sub, calib_seed=wl.seed))
+        k += 1
+    feed = feed_layout(plans)
+    host = torch.empty(feed["n_samples"], dtype=torch.int16, pin_memory=True)
+    dwave = torch.empty(max(p.n_samples_total for p in plans), dtype=torch.int16, device="cuda")
+    for p, b0 in zip(plans, feed["seg_base"]):
+        keep = synth.render_waves_gpu(p, dwave, torch.cuda.current_stream().cuda_stream)
+        host[int(b0):int(b0) + p.n_samples_total].copy_(dwave[:p.n_samples_total])
+        torch.cuda.synchronize()
+        del keep
+    del dwave
+    torch.cuda.empty_cache()
+    feed.update(host=host, wave=host.numpy().view(np.uint16))
+    return feed
+
+
+def feed_layout(plans):
+    """The feed's tables: the segments' images one after another (sample offsets
+    from the feed's start, telescopes, event CSR over all of them)."""
+    sizes = np.array([p.n_samples_total for p in plans], np.int64)
+    base = np.concatenate([[0], np.cumsum(sizes)])
+    img_base = np.concatenate([[0], np.cumsum([p.n_img for p in plans])])
+    evt_off = [0]
+    for p, i0 in zip(plans, img_base[:-1]):
+        evt_off.extend((p.evt_off[1:].astype(np.int64) + i0).tolist())
+    wave_off = np.concatenate([p.wave_off + b0 for p, b0 in zip(plans, base[:-1])]).astype(np.int64)
+    return dict(seg_base=base[:-1], n_samples=int(base[-1]), wave_off=wave_off,
+                wave_end=np.append(wave_off[1:], base[-1]),
+                img_tel=np.concatenate([p.img_tel for p in plans]).astype(np.int32),
+                evt_off=np.asarray(evt_off, np.int64), n_evt=len(evt_off) - 1, segments=len(plans),
+                bytes=int(2 * base[-1]))
+
+
+def feed_bundles(feed, n_bundles, rng, lo=1000, hi=50000):
+    """n_bundles contiguous event ranges of the feed, their event counts
+    log-uniform in [lo, hi], with the tables a bundle carries (wave offsets from
+    its first sample, telescopes, event CSR from 0)."""
+    out = []
+    hi = min(hi, feed["n_evt"])
     for _ in range(n_bundles):
-        n = int(rng.integers(1000, min(max_events, wl.n_evt) + 1))
-        e0 = int(rng.integers(0, wl.n_evt - n + 1))
-        keep_tel = np.zeros(len(wl.tel_cam), bool)
-        keep_tel[rng.choice(len(wl.tel_cam), size=int(rng.integers(20, len(wl.tel_cam) + 1)), replace=False)] = True
-        imgs, evt_off = [], [0]
-        for e in range(e0, e0 + n):
-            ii = [i for i in range(wl.evt_off[e], wl.evt_off[e + 1]) if keep_tel[wl.img_tel[i]]]
-            if len(ii) >= 2:
-                imgs += ii
-                evt_off.append(len(imgs))
-        imgs = np.asarray(imgs, np.int64)
-        sizes = P[wl.img_tel[imgs]]
-        off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
-        total = int(sizes.sum())
-        t_wave = torch.empty(total, dtype=torch.int16, pin_memory=True)
-        w = t_wave.numpy().view(np.uint16)
-        for k, i in enumerate(imgs):
-            w[off[k]:off[k] + sizes[k]] = wave_h[wl.wave_off[i]:wl.wave_off[i] + sizes[k]]
-        pool.append(dict(t_wave=t_wave, wave=w, off=off, tel=wl.img_tel[imgs].astype(np.int32),
-                         evt=np.asarray(evt_off, np.int32), n_img=len(imgs), n_evt=len(evt_off) - 1,
-                         bytes=2 * total))
-    return pool
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi + 1))))
+        n = max(lo, min(hi, n))
+        e0 = int(rng.integers(0, feed["n_evt"] - n + 1))
+        i0, i1 = int(feed["evt_off"][e0]), int(feed["evt_off"][e0 + n])
+        w0, w1 = int(feed["wave_off"][i0]), int(feed["wave_end"][i1 - 1])
+        out.append(dict(ptr=feed["wave"][w0:].ctypes.data, n_wave=w1 - w0,
+                        off=np.ascontiguousarray(feed["wave_off"][i0:i1] - w0),
+                        tel=np.ascontiguousarray(feed["img_tel"][i0:i1]),
+                        evt=np.ascontiguousarray(feed["evt_off"][e0:e0 + n + 1] - i0, dtype=np.int32),
+                        n_img=i1 - i0, n_evt=n, bytes=2 * (w1 - w0)))
+    return out
 
 
 def arrival_schedule(pool_bytes, rate, duration_s, rng, min_arrivals=8, burst=24):
@@ -711,29 +745,99 @@ def arrival_schedule(pool_bytes, rate, duration_s, rng, min_arrivals=8, burst=24
     return out
 
 
-def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894):
-    """Poisson arrivals of sub-array bundles at fixed aggregate rates through the
+def hour_of_sky(st, now_s, rate_hz, rng, flare_xy=(0.31, -0.47), flare_s=20, flare_hz=30):
+    """An hour of sky-map history before now_s, second by second, counted in
+    through rta_stream_add_events: rate_hz background events a second, uniform
+    in a 2.5 deg disk (3 % without a direction), and the last flare_s seconds
+    flare_hz more a second in a 0.03 deg Gaussian at flare_xy."""
+    import torch
+    import paper_1307_6489_gb300 as rta
+    cs = torch.cuda.current_stream().cuda_stream
+    keep = []
+    for t in range(now_s - 3599, now_s + 1):
+        n = int(rng.poisson(rate_hz))
+        r = 2.5 * np.sqrt(rng.uniform(size=n))
+        a = rng.uniform(0, 2 * np.pi, n)
+        x, y = r * np.cos(a), r * np.sin(a)
+        if t > now_s - flare_s:
+            k = int(rng.poisson(flare_hz))
+            x = np.concatenate([x, flare_xy[0] + rng.normal(0, 0.03, k)])
+            y = np.concatenate([y, flare_xy[1] + rng.normal(0, 0.03, k)])
+        rows = np.zeros((len(x), 8), np.float32)
+        rows[:, 1], rows[:, 2] = x, y
+        rows.view(np.uint32)[:, 5] = np.where(rng.uniform(size=len(x)) < 0.97, 0, rta.RTA_EF_NO_DIRECTION)
+        d = torch.from_numpy(rows.reshape(-1)).cuda(non_blocking=False)
+        rta.rta_stream_add_events(st, d.data_ptr(), len(x), t * 1_000_000_000 + 250_000_000, cs)
+        keep.append(d)
+        if len(keep) > 64:
+            torch.cuda.synchronize()
+            keep.clear()
+    torch.cuda.synchronize()
+
+
+def transient_leg(ctx, proc, rate_hz=10000, seed=1307064896):
+    """Transient search over an hour of history (its own stream): the time of one
+    call for 1 s .. 30 min windows, and what it finds: the planted flare and any
+    other alert."""
+    import paper_1307_6489_gb300 as rta
+    rng = np.random.default_rng(seed)
+    windows = [(1, 5), (5, 25), (10, 20), (60, 600), (300, 1800), (600, 3000), (1800, 1800)]
+    now_s = 2_000_000 * 60 + 23
+    fx, fy = 0.31, -0.47
+    st = rta.rta_stream_create(ctx.handle, 0, 64 << 20, 1, 1000, 1000, *proc, 0.5)
+    try:
+        t0 = time.perf_counter()
+        hour_of_sky(st, now_s, rate_hz, rng, (fx, fy))
+        fill_s = time.perf_counter() - t0
+        now = now_s * 1_000_000_000 + 999_000_000
+        rta.rta_transient_search(st, now, windows, 5, 5.0)          # warm (work buffers)
+        t0 = time.perf_counter()
+        for _ in range(10):
+            alerts, n_found = rta.rta_transient_search(st, now, windows, 5, 5.0, with_total=True)
+        search_ms = (time.perf_counter() - t0) / 10 * 1e3
+    finally:
+        rta.rta_stream_destroy(st)
+    cx = (alerts["ix"] + 0.5) * 0.02 - 2.56
+    cy = (alerts["iy"] + 0.5) * 0.02 - 2.56
+    near = np.hypot(cx - fx, cy - fy) <= 0.15
+    return {"history": f"3600 one-second slabs, Poisson {rate_hz} events/s uniform in a 2.5 deg disk, 3 % without "
+                       f"direction; a 20 s flare of 30 events/s (0.03 deg Gaussian) at ({fx}, {fy}) deg",
+            "fill_s": fill_s, "windows": len(windows), "radius_bins": 5, "s_min": 5.0, "ms_per_call": search_ms,
+            "alerts": int(n_found), "flare_alerts": int(near.sum()),
+            "flare_windows": sorted({windows[int(w)][0] for w in alerts["window"][near]}),
+            "other_alerts": int((~near).sum()),
+            "max_significance": float(alerts["significance"].max()) if len(alerts) else None}
+
+
+def serving_leg(ctx, model, wl, proc, rates, duration_s, feed_events=60000, seed=1307064894):
+    """Poisson arrivals of telescope bundles (1k-50k events, contiguous ranges of
+    a GPU-rendered feed of mixed sub-arrays) at fixed aggregate rates through the
     serving stream (continuous batching under an HBM budget); per rate the
-    sustained GB/s and the arrival-to-event-list latency percentiles."""
+    sustained GB/s, the arrival-to-event-list latency percentiles and where each
+    bundle's time went (queue wait before a slot and memory free up, copies in,
+    device work, copy out)."""
     import torch
     import paper_1307_6489_gb300 as rta
     rng = np.random.default_rng(seed)
-    pool = build_serving_pool(wl, wave_h, 6, rng, 10000)
+    feed = serving_feed(wl, feed_events, rng)
+    pool = feed_bundles(feed, 64, rng)
     max_img = max(b["n_img"] for b in pool)
     max_evt = max(b["n_evt"] for b in pool)
-    st = rta.rta_stream_create(ctx.handle, model or 0, 24 << 30, 4, max_img, max_evt, *proc, 0.5)
+    budget = 48 << 30
+    st = rta.rta_stream_create(ctx.handle, model or 0, budget, 4, max_img, max_evt, *proc, 0.5)
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     out = []
     try:
         for rate in rates:
             t_start = time.monotonic_ns() + 50_000_000
             sched = [(t_start + dt, pool[i]) for dt, i in arrival_schedule([b["bytes"] for b in pool], rate,
-                                                                           duration_s, rng)]
+                                                                           duration_s, rng, min_arrivals=6)]
             total = sum(b["bytes"] for _, b in sched)
             ev_all = torch.empty(sum(b["n_evt"] for _, b in sched) * 32, dtype=torch.uint8, pin_memory=True)
             ev_np = ev_all.numpy()
             pos, structs, tickets, arr = 0, [], [], []
             for t_arr, b in sched:
-                bs = rta.Bundle(b["wave"].ctypes.data, b["wave"].size, b["off"].ctypes.data, b["tel"].ctypes.data,
+                bs = rta.Bundle(b["ptr"], b["n_wave"], b["off"].ctypes.data, b["tel"].ctypes.data,
                                 b["n_img"], b["evt"].ctypes.data, b["n_evt"], t_arr, ev_np[pos:].ctypes.data)
                 pos += b["n_evt"] * 32
                 structs.append(bs)
@@ -747,36 +851,42 @@ def serving_leg(ctx, model, wl, wave_h, proc, rates, duration_s, seed=1307064894
                     k += 1
                 for j, tk in enumerate(tickets):
                     if j not in done:
-                        d = rta.rta_stream_poll(st, tk)
+                        d = rta.rta_stream_poll_times(st, tk)
                         if d is not None:
                             done[j] = d
                 time.sleep(0.0002)
-            lat = np.array([(done[j] - arr[j]) / 1e6 for j in range(len(sched))])
-            span = (max(done.values()) - t_start) / 1e9
+            T = [done[j] for j in range(len(sched))]
+            lat = np.array([(t.done_ns - t.arrival_ns) / 1e6 for t in T])
+            qwait = np.array([(t.admit_ns - t.arrival_ns) / 1e6 for t in T])
+            h2d = np.array([t.h2d_ms for t in T])
+            comp = np.array([t.compute_ms for t in T])
+            d2h = np.array([t.d2h_ms for t in T])
+            nbytes = np.array([b["bytes"] for _, b in sched], np.float64)
+            span = (max(t.done_ns for t in T) - t_start) / 1e9
+            slowest = int(np.argmax(lat))
             out.append({"rate_gbs": rate if rate != float("inf") else "burst", "bundles": len(sched),
-                        "bytes": int(total),
+                        "bytes": int(total), "events": int(sum(b["n_evt"] for _, b in sched)),
                         "offered_gbs": (total / ((arr[-1] - t_start) / 1e9) / 1e9) if arr[-1] > t_start else None,
-                        "sustained_gbs": total / span / 1e9, "p50_ms": float(np.percentile(lat, 50)),
-                        "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())})
-        # transient search over the sky map the stream has just filled: 1 s .. 30 min windows
-        windows = [(1, 5), (5, 25), (10, 20), (60, 600), (300, 1800), (600, 3000), (1800, 1800)]
-        now = time.monotonic_ns()
-        rta.rta_transient_search(st, now, windows, 5, 5.0)          # warm (work buffers)
-        t0 = time.perf_counter()
-        for _ in range(10):
-            alerts, n_found = rta.rta_transient_search(st, now, windows, 5, 5.0, with_total=True)
-        search_ms = (time.perf_counter() - t0) / 10 * 1e3
-        per_window = np.bincount(alerts["window"], minlength=len(windows)).tolist() if n_found == len(alerts) else None
+                        "sustained_gbs": total / span / 1e9, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                        "max_ms": float(lat.max()),
+                        "queue_wait_ms": {"p50": pct(qwait, 50), "p99": pct(qwait, 99), "max": float(qwait.max())},
+                        "h2d_ms": {"p50": pct(h2d, 50), "p99": pct(h2d, 99), "max": float(h2d.max()),
+                                   "gbs_median": float(np.median(nbytes / (h2d * 1e6)))},
+                        "device_ms": {"p50": pct(comp, 50), "p99": pct(comp, 99), "max": float(comp.max()),
+                                      "gbs_median": float(np.median(nbytes / (comp * 1e6)))},
+                        "d2h_ms": {"p50": pct(d2h, 50), "max": float(d2h.max())},
+                        "slowest": {"events": int(sched[slowest][1]["n_evt"]), "gb": float(nbytes[slowest] / 1e9),
+                                    "latency_ms": float(lat[slowest]), "queue_wait_ms": float(qwait[slowest]),
+                                    "h2d_ms": float(h2d[slowest]), "device_ms": float(comp[slowest])}})
+            del ev_all
     finally:
         rta.rta_stream_destroy(st)
-    return out, {"pool_bundles": len(pool), "pool_events": [b["n_evt"] for b in pool],
-                 "pool_gb": sum(b["bytes"] for b in pool) / 1e9,
-                 "transient_search": {"windows": len(windows), "radius_bins": 5, "s_min": 5.0, "ms_per_call": search_ms,
-                                      "alerts_found": n_found, "alerts_returned": int(len(alerts)),
-                                 "alerts_per_window": per_window,
-                                 "note": "the map holds only the last seconds of arrivals, so every off window "
-                                         "that reaches before them is nearly empty and bins with on counts are "
-                                         "excesses"}}
+    info = {"feed_events": feed["n_evt"], "feed_gb": feed["bytes"] / 1e9, "feed_segments": feed["segments"],
+            "bundle_events": {"min": min(b["n_evt"] for b in pool), "median": int(np.median([b["n_evt"] for b in pool])),
+                              "max": max(b["n_evt"] for b in pool)},
+            "bundle_gb_max": max(b["bytes"] for b in pool) / 1e9, "hbm_budget_gb": budget / 2**30, "slots": 4}
+    del feed
+    return out, info
 
 
 def run_reference(args, ws, rank):
@@ -827,7 +937,7 @@ def main():
     ap.add_argument("--train-events", type=int, default=2000000)
     ap.add_argument("--eval-events", type=int, default=1000000)
     ap.add_argument("--serve-rates", default="0.5,2,8,inf", help="aggregate arrival rates, GB/s (inf: a burst)")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--chain", default="", help="fixed image-kernel config 'variant,stages,ctas_per_sm'")
     ap.add_argument("--config1-events", type=int, default=200000,
                     help="events of the single-camera stream leg (1855 px x 40 samples; 0: skip)")
@@ -1031,8 +1141,9 @@ def main():
                                      args.train_events, args.eval_events)
     if not args.no_serving:
         rates = [float(r) for r in args.serve_rates.split(",")]
-        serving, pool_info = serving_leg(ctx, trainer.model if trainer else None, wl, wave_h, proc, rates,
+        serving, pool_info = serving_leg(ctx, trainer.model if trainer else None, wl, proc, rates,
                                          args.serve_seconds)
+        pool_info["transient_search"] = transient_leg(ctx, proc)
     if trainer:
         trainer.close()
 
@@ -1087,7 +1198,7 @@ def main():
                       "surrogate": sur},
             "dl0_stream": stream_out,
             "single_camera_stream": cfg1,
-            "serving": {"rates": serving, "pool": pool_info, "budget_gb": 24 * 1.073741824, "slots": 4,
+            "serving": {"rates": serving, "feed": pool_info,
                         "model": "surrogate" if trainer else "geometric"} if serving else None,
             "p99_bundle_latency_ms": next((r["p99_ms"] for r in serving if r["rate_gbs"] == 8.0), None)
             if serving else None,

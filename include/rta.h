@@ -584,9 +584,10 @@ typedef struct rta_stream rta_stream;
  * sub-allocated per bundle (its waveforms, tables, Hillas rows and event
  * list): a bundle is admitted when one of max_inflight slots (CUDA streams) is
  * free and the budget has room, in arrival order; bundles of several slots run
- * concurrently. Each bundle: copies in, rta_image_chain, then
- * rta_surrogate_infer with the given model (events with a learned direction,
- * geometric fallback) or, with model = NULL, rta_stereo (geometric direction,
+ * concurrently. Each bundle, on its slot's stream: copies in, rta_image_chain,
+ * then rta_surrogate_infer with the given model (events with a learned direction,
+ * geometric fallback; the learned stages of concurrent bundles overlap) or,
+ * with model = NULL, rta_stereo (geometric direction,
  * no energy or gammaness), the sky-map fill of the one-second slab of its
  * arrival, and the copy of its event list out. max_img / max_evt bound one
  * bundle. A scheduler thread owned by the stream does the device work. Each
@@ -603,6 +604,19 @@ int rta_stream_submit(rta_stream* stream, const rta_bundle_t* bundle, uint64_t* 
  * completion time in *done_ns, same clock as arrival_ns; the ticket is then
  * released), RTA_E_BUSY while it is queued or running. */
 int rta_stream_poll(rta_stream* stream, uint64_t ticket, int64_t* done_ns);
+/* Where a bundle's time went: host steady-clock instants (ns, the clock of
+ * arrival_ns) of its arrival, submission, admission to a slot and completion,
+ * and device durations measured by timing events on its slot's stream: the
+ * copies in (waveforms and tables), the device work (image kernel and learned
+ * or geometric reconstruction) and the copy of the event list out (which waits
+ * for the sky-map fill). The queue wait is admit_ns - arrival_ns. */
+typedef struct rta_bundle_times_t {
+    int64_t arrival_ns, submit_ns, admit_ns, done_ns;
+    float h2d_ms, compute_ms, d2h_ms;
+    int32_t slot;
+} rta_bundle_times_t;
+/* rta_stream_poll that also returns the bundle's times (times may be NULL). */
+int rta_stream_poll_times(rta_stream* stream, uint64_t ticket, int64_t* done_ns, rta_bundle_times_t* times);
 /* Wait until every submitted bundle has finished (RTA_E_TIMEOUT after timeout_ms). */
 int rta_stream_drain(rta_stream* stream, int timeout_ms);
 /* The sky-count map at time now_ns: per bin (row y, column x, RTA_SKY_N each)

@@ -105,6 +105,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_stream_create": ([P, P, sz, i32, i64, i64, i32, i32, i32, f32, f32, i32, f32, P], i32),
         "rta_stream_submit": ([P, P, P], i32),
         "rta_stream_poll": ([P, ctypes.c_uint64, P], i32),
+        "rta_stream_poll_times": ([P, ctypes.c_uint64, P, P], i32),
         "rta_stream_drain": ([P, i32], i32),
         "rta_skymap_read": ([P, i64, P], i32),
         "rta_stream_add_events": ([P, P, i64, i64, P], i32),
@@ -524,6 +525,28 @@ def rta_stream_poll(stream: int, ticket: int):
         return None
     _check(rc)
     return done.value
+
+
+class BundleTimes(ctypes.Structure):
+    """rta_bundle_times_t: host instants (ns) of a bundle's arrival, submission, admission and completion,
+    and the device durations (ms) of its copies in, device work and copy out."""
+    _fields_ = [("arrival_ns", ctypes.c_int64), ("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64), ("h2d_ms", ctypes.c_float), ("compute_ms", ctypes.c_float),
+                ("d2h_ms", ctypes.c_float), ("slot", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def rta_stream_poll_times(stream: int, ticket: int):
+    """The bundle's BundleTimes once done, else None."""
+    done = ctypes.c_int64()
+    t = BundleTimes()
+    rc = load().rta_stream_poll_times(stream, ticket, ctypes.byref(done), ctypes.byref(t))
+    if rc == RTA_E_BUSY:
+        return None
+    _check(rc)
+    return t
 
 
 def rta_stream_drain(stream: int, timeout_ms: int = 60000):

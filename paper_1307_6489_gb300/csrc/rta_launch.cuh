@@ -210,8 +210,6 @@ cudaError_t launch_lut_accumulate(const LutArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_lut_finalize(const double* acc, int64_t n_cells, int min_count, rta_lut_cell_t* cells, int grid,
                                 cudaStream_t s);
 cudaError_t launch_lut_prepare(const rta_lut_cell_t* cells, int64_t n_cells, void* lookup, int grid, cudaStream_t s);
-// grow a model's workspace ahead of use (rta_surrogate.cu)
-int surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt);
 // context access for the surrogate (rta_api.cu)
 int surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2** tel_xy, int* n_tel, int* device);
 // the context's device status word

@@ -8,10 +8,12 @@
 // are on the GPU starts as soon as memory and a slot free up, and the copies
 // and kernels of different bundles overlap on the device. Per bundle, on its
 // slot stream: host-to-device copies, the fused image kernel, then the learned
-// reconstruction on the model stream (serialised: one model workspace) or the
-// geometric intersection, the sky-map fill on the map stream, and the copy of
-// the event list back to the caller's host buffer. Completion is detected by
-// polling a CUDA event; the bundle's arena range is freed only then.
+// reconstruction (one kernel with no model workspace, so the learned stages of
+// concurrent bundles overlap as well) or the geometric intersection, the
+// sky-map fill on the map stream, and the copy of the event list back to the
+// caller's host buffer. Completion is detected by polling a CUDA event; the
+// bundle's arena range is freed only then. Timing events on the slot stream
+// split each bundle's time into queue wait, copies in, device work and copy out.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -117,11 +119,13 @@ struct Req {
     int state = REQ_PENDING;
     int rc = RTA_OK;
     int64_t done_ns = 0;
+    rta_bundle_times_t times{};
 };
 
 struct Slot {
     cudaStream_t s = nullptr;
-    cudaEvent_t e_img = nullptr, e_model = nullptr, e_ev = nullptr, e_map = nullptr, e_done = nullptr;
+    cudaEvent_t e_ev = nullptr, e_map = nullptr, e_done = nullptr;
+    cudaEvent_t t_in = nullptr, t_copied = nullptr, t_computed = nullptr, t_out = nullptr;   // timing
     uint64_t ticket = 0;
     bool busy = false;
     // pinned staging of the bundle's tables (in) and event list (out): copies from
@@ -141,7 +145,7 @@ struct rta_stream {
     int64_t max_img = 0, max_evt = 0;
     Arena arena;
     std::vector<Slot> slots;
-    cudaStream_t s_model = nullptr, s_map = nullptr;
+    cudaStream_t s_map = nullptr;
     unsigned int* d_slabs = nullptr;   // RTA_SKY_SLABS x 256 x 256
     unsigned int* d_slabs_min = nullptr;   // RTA_SKY_MIN_SLABS x 256 x 256
     unsigned int* d_map = nullptr;
@@ -209,6 +213,8 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     rta_event_t* d_ev = reinterpret_cast<rta_event_t*>(base + r.L.events);
     rta_stereo_t* d_st = reinterpret_cast<rta_stereo_t*>(base + r.L.stereo);
     cudaStream_t s = sl.s;
+    r.times.admit_ns = now_ns();
+    r.times.slot = int(&sl - &S->slots[0]);
 #define D_TRY(call)                                                                                 \
     do {                                                                                            \
         cudaError_t e_ = (call);                                                                    \
@@ -220,25 +226,24 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     std::memcpy(sl.h_stage, b.h_wave_off, tb_off);
     std::memcpy(sl.h_stage + tb_off, b.h_img_tel, tb_tel);
     std::memcpy(sl.h_stage + tb_off + tb_tel, b.h_evt_off, tb_evt);
+    D_TRY(cudaEventRecord(sl.t_in, s));
     D_TRY(cudaMemcpyAsync(d_wave, b.h_wave, size_t(b.n_wave) * 2, cudaMemcpyHostToDevice, s));
     D_TRY(cudaMemcpyAsync(d_off, sl.h_stage, tb_off, cudaMemcpyHostToDevice, s));
     D_TRY(cudaMemcpyAsync(d_tel, sl.h_stage + tb_off, tb_tel, cudaMemcpyHostToDevice, s));
     D_TRY(cudaMemcpyAsync(d_evt, sl.h_stage + tb_off + tb_tel, tb_evt, cudaMemcpyHostToDevice, s));
+    D_TRY(cudaEventRecord(sl.t_copied, s));
     int rc = rta_image_chain(S->ctx, d_wave, b.n_wave, d_off, d_tel, b.n_img, S->window_mode, S->start, S->W,
                              S->t_hi, S->t_lo, S->core_nb, d_h, s);
     if (rc) return rc;
     if (S->model) {
-        D_TRY(cudaEventRecord(sl.e_img, s));
-        D_TRY(cudaStreamWaitEvent(S->s_model, sl.e_img, 0));
-        rc = rta_surrogate_infer(S->model, d_h, d_tel, b.n_img, d_evt, b.n_evt, S->fallback_deg, d_ev, S->s_model);
+        rc = rta_surrogate_infer(S->model, d_h, d_tel, b.n_img, d_evt, b.n_evt, S->fallback_deg, d_ev, s);
         if (rc) return rc;
-        D_TRY(cudaEventRecord(sl.e_model, S->s_model));
-        D_TRY(cudaStreamWaitEvent(s, sl.e_model, 0));
     } else {
         rc = rta_stereo(S->ctx, d_h, d_tel, b.n_img, d_evt, b.n_evt, d_st, s);
         if (rc) return rc;
         D_TRY(rta::launch_stereo_to_events(d_st, b.n_evt, d_ev, s));
     }
+    D_TRY(cudaEventRecord(sl.t_computed, s));
     // sky map: the one-second and one-minute slabs of the bundle's arrival
     D_TRY(cudaEventRecord(sl.e_ev, s));
     D_TRY(cudaStreamWaitEvent(S->s_map, sl.e_ev, 0));
@@ -246,6 +251,7 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     D_TRY(cudaEventRecord(sl.e_map, S->s_map));
     D_TRY(cudaStreamWaitEvent(s, sl.e_map, 0));
     D_TRY(cudaMemcpyAsync(sl.h_stage, d_ev, size_t(b.n_evt) * sizeof(rta_event_t), cudaMemcpyDeviceToHost, s));
+    D_TRY(cudaEventRecord(sl.t_out, s));
     D_TRY(cudaEventRecord(sl.e_done, s));
 #undef D_TRY
     return RTA_OK;
@@ -262,9 +268,14 @@ void worker_loop(rta_stream* S) {
             const cudaError_t q = cudaEventQuery(sl.e_done);
             if (q == cudaErrorNotReady) continue;
             Req& r = S->reqs[sl.ticket];
-            if (q == cudaSuccess)       // the event list, from the slot's staging
+            if (q == cudaSuccess) {     // the event list, from the slot's staging; the bundle's times
                 std::memcpy(r.b.h_events, sl.h_stage, size_t(r.b.n_evt) * sizeof(rta_event_t));
+                cudaEventElapsedTime(&r.times.h2d_ms, sl.t_in, sl.t_copied);
+                cudaEventElapsedTime(&r.times.compute_ms, sl.t_copied, sl.t_computed);
+                cudaEventElapsedTime(&r.times.d2h_ms, sl.t_computed, sl.t_out);
+            }
             r.done_ns = now_ns();
+            r.times.done_ns = r.done_ns;
             r.state = q == cudaSuccess ? REQ_DONE : REQ_FAILED;
             if (q != cudaSuccess) r.rc = RTA_E_CUDA;
             S->arena.release(r.off, r.L.total);
@@ -291,7 +302,6 @@ void worker_loop(rta_stream* S) {
             const int rc = dispatch(S, r, *fs);
             if (rc) {   // nothing more is enqueued for it; let what was enqueued finish
                 cudaStreamSynchronize(fs->s);
-                cudaStreamSynchronize(S->s_model);
                 cudaStreamSynchronize(S->s_map);
                 S->arena.release(r.off, r.L.total);
                 fs->busy = false;
@@ -317,11 +327,10 @@ void release_all(rta_stream* S) {
     for (auto& sl : S->slots) {
         if (sl.s) cudaStreamDestroy(sl.s);
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
-        cudaEvent_t ev[] = {sl.e_img, sl.e_model, sl.e_ev, sl.e_map, sl.e_done};
+        cudaEvent_t ev[] = {sl.e_ev, sl.e_map, sl.e_done, sl.t_in, sl.t_copied, sl.t_computed, sl.t_out};
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
     }
-    if (S->s_model) cudaStreamDestroy(S->s_model);
     if (S->s_map) cudaStreamDestroy(S->s_map);
     cudaFree(S->arena.base);
     cudaFree(S->d_slabs);
@@ -371,7 +380,6 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
               cudaMalloc(&S->d_slabs_min, sizeof(unsigned int) * RTA_SKY_MIN_SLABS * RTA_SKY_N * RTA_SKY_N) ==
                   cudaSuccess &&
               cudaMalloc(&S->d_map, sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&S->s_model, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->s_map, cudaStreamNonBlocking) == cudaSuccess;
     S->slots.resize(max_inflight);
     // staging per slot: the tables in, or the event list out, of the largest bundle
@@ -380,8 +388,10 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
     for (auto& sl : S->slots) {
         ok = ok && cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaHostAlloc(reinterpret_cast<void**>(&sl.h_stage), stage_bytes, cudaHostAllocDefault) == cudaSuccess;
-        cudaEvent_t* ev[] = {&sl.e_img, &sl.e_model, &sl.e_ev, &sl.e_map, &sl.e_done};
+        cudaEvent_t* ev[] = {&sl.e_ev, &sl.e_map, &sl.e_done};
         for (auto e : ev) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        cudaEvent_t* tv[] = {&sl.t_in, &sl.t_copied, &sl.t_computed, &sl.t_out};
+        for (auto e : tv) ok = ok && cudaEventCreate(e) == cudaSuccess;
     }
     if (!ok) {
         release_all(S);
@@ -392,11 +402,6 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
     S->arena.reset();
     cudaMemset(S->d_slabs, 0, sizeof(unsigned int) * RTA_SKY_SLABS * RTA_SKY_N * RTA_SKY_N);
     cudaMemset(S->d_slabs_min, 0, sizeof(unsigned int) * RTA_SKY_MIN_SLABS * RTA_SKY_N * RTA_SKY_N);
-    if (model && (rc = rta::surrogate_reserve(model, max_img, max_evt))) {
-        release_all(S);
-        delete S;
-        return rc;
-    }
     cudaDeviceSynchronize();
     S->worker = std::thread(worker_loop, S);
     *out = S;
@@ -413,6 +418,8 @@ int rta_stream_submit(rta_stream* S, const rta_bundle_t* b, uint64_t* ticket) {
         return vfail(RTA_E_INVALID, "evt_off must run from 0 to n_img");
     Req r;
     r.b = *b;
+    r.times.arrival_ns = b->arrival_ns;
+    r.times.submit_ns = now_ns();
     r.L = layout_of(*b, S->model == nullptr);
     if (r.L.total > S->arena.size) return vfail(RTA_E_NOMEM, "bundle needs %zu bytes, budget is %zu", r.L.total, S->arena.size);
     std::lock_guard<std::mutex> lock(S->mu);
@@ -426,6 +433,10 @@ int rta_stream_submit(rta_stream* S, const rta_bundle_t* b, uint64_t* ticket) {
 }
 
 int rta_stream_poll(rta_stream* S, uint64_t ticket, int64_t* done_ns) {
+    return rta_stream_poll_times(S, ticket, done_ns, nullptr);
+}
+
+int rta_stream_poll_times(rta_stream* S, uint64_t ticket, int64_t* done_ns, rta_bundle_times_t* times) {
     if (!S) return vfail(RTA_E_INVALID, "NULL stream");
     std::lock_guard<std::mutex> lock(S->mu);
     auto it = S->reqs.find(ticket);
@@ -433,6 +444,7 @@ int rta_stream_poll(rta_stream* S, uint64_t ticket, int64_t* done_ns) {
     const Req& r = it->second;
     if (r.state == REQ_PENDING || r.state == REQ_RUNNING) return RTA_E_BUSY;
     if (done_ns) *done_ns = r.done_ns;
+    if (times) *times = r.times;
     const int rc = r.state == REQ_DONE ? RTA_OK : r.rc;
     S->reqs.erase(it);
     if (rc) return vfail(rc, "bundle %llu failed", (unsigned long long)ticket);

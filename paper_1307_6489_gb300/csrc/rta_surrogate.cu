@@ -243,12 +243,6 @@ int upload_params(rta_model* md, const std::vector<float>& internal) {
 
 }  // namespace
 
-int rta::surrogate_reserve(rta_model* md, int64_t n_img, int64_t n_evt) {
-    if (!md) return sfail(RTA_E_INVALID, "model is NULL");
-    S_TRY(cudaSetDevice(md->device));
-    return reserve(md, n_img, n_evt);
-}
-
 extern "C" {
 
 int rta_surrogate_num_params(void) { return int(rta::N_PARAM_PACKED); }

@@ -49,3 +49,34 @@ def test_rates_must_be_positive():
     for bad in (0.0, -1.0, float("nan")):
         with pytest.raises(ValueError):
             bench.arrival_schedule(POOL, bad, 5.0, np.random.default_rng(7))
+
+
+def test_feed_bundles_are_contiguous_event_ranges_of_the_feed():
+    """A serving bundle cut from the feed carries exactly its events' images and
+    waveforms: tables rebased to its first sample and image, samples equal to the
+    segments' own renderings."""
+    import synth
+    rng = np.random.default_rng(11)
+    plans = [synth.make_workload(2, 12, seed=100 + k, telescopes=rng.choice(69, 25 + 10 * k, replace=False))
+             for k in range(3)]
+    feed = bench.feed_layout(plans)
+    wave = np.concatenate([p.wave for p in plans])
+    assert wave.size == feed["n_samples"]
+    feed["wave"] = wave
+    imgs = [(p, i) for p in plans for i in range(p.n_img)]
+    evts = [(p, e) for p in plans for e in range(p.n_evt)]
+    for b in bench.feed_bundles(feed, 20, rng, lo=3, hi=30):
+        assert 3 <= b["n_evt"] <= 30 and b["evt"][0] == 0 and b["evt"][-1] == b["n_img"]
+        w0 = (b["ptr"] - wave.ctypes.data) // 2
+        e0 = int(np.searchsorted(feed["evt_off"], feed["wave_off"].searchsorted(w0), side="left"))
+        i0 = int(feed["evt_off"][e0])
+        assert b["off"][0] == 0 and b["n_wave"] == sum(
+            imgs[i0 + k][0].image_wave(imgs[i0 + k][1]).size for k in range(b["n_img"]))
+        for k in range(b["n_img"]):
+            p, i = imgs[i0 + k]
+            assert b["tel"][k] == p.img_tel[i]
+            seg = p.image_wave(i).reshape(-1)
+            np.testing.assert_array_equal(wave[w0 + b["off"][k]: w0 + b["off"][k] + seg.size], seg)
+        for j in range(b["n_evt"]):
+            p, e = evts[e0 + j]
+            assert b["evt"][j + 1] - b["evt"][j] == p.evt_off[e + 1] - p.evt_off[e]

@@ -48,18 +48,22 @@ def make_bundles(wl, sizes):
     return out
 
 
-def serve(stream, bundles, arrival_ns, concurrent=True):
+def serve(stream, bundles, arrival_ns, concurrent=True, times=None):
     hbs = [HostBundle(b, arrival_ns) for b in bundles]
     if concurrent:
         tickets = [rta.rta_stream_submit(stream, h.b) for h in hbs]
         rta.rta_stream_drain(stream, 120000)
-        for t in tickets:
-            assert rta.rta_stream_poll(stream, t) is not None
     else:
+        tickets = []
         for h in hbs:
-            t = rta.rta_stream_submit(stream, h.b)
+            tickets.append(rta.rta_stream_submit(stream, h.b))
             rta.rta_stream_drain(stream, 120000)
+    for t in tickets:           # a ticket is reported once
+        if times is None:
             assert rta.rta_stream_poll(stream, t) is not None
+        else:
+            times.append(rta.rta_stream_poll_times(stream, t))
+            assert times[-1] is not None
     return [h.events.copy() for h in hbs]
 
 
@@ -117,8 +121,9 @@ def test_admission_waits_for_the_budget(env):
     # room for one bundle at a time: the others are admitted as memory frees up
     st = rta.rta_stream_create(ctx.handle, 0, int(need * 1.3) + (8 << 20), 4, 20000, 3000, mode, start, W, t_hi,
                                t_lo, core_nb, 0.5)
+    times = []
     try:
-        res = serve(st, bundles, time.monotonic_ns())
+        res = serve(st, bundles, time.monotonic_ns(), times=times)
         big = synth.subset(wl, np.arange(0, 2400))
         with pytest.raises(rta.RtaError) as e:
             rta.rta_stream_submit(st, HostBundle(big, time.monotonic_ns()).b)
@@ -132,6 +137,12 @@ def test_admission_waits_for_the_budget(env):
         rta.rta_stream_destroy(st2)
     for a, b in zip(res, ref):
         np.testing.assert_array_equal(a, b)
+    # each bundle's times are ordered and its device durations positive; with room
+    # for one bundle at a time, a later bundle is admitted only after an earlier one is done
+    for t in times:
+        assert t.arrival_ns <= t.submit_ns <= t.admit_ns <= t.done_ns
+        assert t.h2d_ms > 0 and t.compute_ms > 0 and t.d2h_ms > 0 and 0 <= t.slot < 4
+    assert max(t.admit_ns for t in times) >= min(t.done_ns for t in times)
 
 
 def test_sky_map_matches_the_oracle():
