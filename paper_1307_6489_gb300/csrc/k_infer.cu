@@ -765,10 +765,11 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
     if (warp == 0) tc_dealloc(tmem, 256);
 }
 
-// BF16 twin -> transposed canonical K-major layout of the tensor-core layers.
+// BF16 twin -> transposed canonical K-major layout of the inference kernel's
+// tensor-core layers, and the padded output layer of the training path.
 __global__ void k_pack_tc(const __nv_bfloat16* __restrict__ pb, __nv_bfloat16* __restrict__ pk) {
-    const int64_t n1 = SUR_H * SUR_XPAD, n2 = SUR_H * SUR_H, n3 = SUR_G * SUR_G;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n1 + n2 + n3;
+    const int64_t n1 = SUR_H * SUR_XPAD, n2 = SUR_H * SUR_H, n3 = SUR_G * SUR_G, n4 = SUR_G * 16;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n1 + n2 + n3 + n4;
          i += int64_t(gridDim.x) * blockDim.x) {
         if (i < n1) {                                 // W1 [16 k][128 n] -> [128 n][16 k]
             const int64_t k = i / SUR_H, n = i % SUR_H;
@@ -776,9 +777,12 @@ __global__ void k_pack_tc(const __nv_bfloat16* __restrict__ pb, __nv_bfloat16* _
         } else if (i < n1 + n2) {                     // W2 [128 k][128 n]
             const int64_t j = i - n1, k = j / SUR_H, n = j % SUR_H;
             pk[PK_W2T + canon_off(n, k, SUR_H)] = pb[OFF_W2 + j];
-        } else {                                      // V1 [256 k][256 n]
+        } else if (i < n1 + n2 + n3) {                // V1 [256 k][256 n]
             const int64_t j = i - n1 - n2, k = j / SUR_G, n = j % SUR_G;
             pk[PK_V1T + canon_off(n, k, SUR_G)] = pb[OFF_V1 + j];
+        } else {                                      // V2 [256 k][4 n] -> [256 k][16 n], zero columns 4..15
+            const int64_t j = i - n1 - n2 - n3, k = j / 16, n = j % 16;
+            pk[PK_V2P + j] = n < 4 ? pb[OFF_V2 + k * 4 + n] : __float2bfloat16(0.f);
         }
     }
 }

@@ -3,13 +3,12 @@
 // gamma/hadron separation next to the direction).
 //
 //   k_features   per event: used images, baseline (two brightest axes), 12 features per image
-//   k_gemm       C = op(A) op(B) on BF16 operands with FP32 accumulation on the
-//                tensor cores (mma.sync m16n8k16), fused epilogues
-//   k_pool / k_pool_bwd, k_head / k_head_bwd, k_loss, k_adam, k_colsum, k_reduce_splits
+//   k_pool / k_pool_bwd, k_head_bwd, k_loss, k_adam, k_colsum, k_reduce_splits
+// (the dense layers, forward and backward, are tensor-core GEMMs: k_gemm_tc.cu)
 //
 // Row-major matrices throughout. Activations are stored in BF16 (the operand
-// type of the next GEMM); biases, the 4-wide output layer and every gradient
-// reduction are FP32.
+// type of the next GEMM); biases, the output layer's backward pass and every
+// gradient reduction are FP32.
 #include "rta_mlp_dev.cuh"
 
 namespace rta {
@@ -50,109 +49,6 @@ __global__ void __launch_bounds__(256) k_features(const FeatArgs a) {
             xr[1] = make_uint4(bf2_bits(x[4]), bf2_bits(x[5]), bf2_bits(x[6]), bf2_bits(x[7]));
         }
     }
-}
-
-// ------------------------------------------------------------------ tensor-core GEMM
-// C[M x N] = op(A)[M x K] op(B)[K x N]; A is [M x K] (TA = false) or stored as
-// [K x M] (TA = true); B is [K x N] (TB = false) or stored as [N x K] (TB = true).
-// Tile 64 x 64 x 32, 4 warps of 32 x 32, mma.sync.m16n8k16 BF16 -> FP32.
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
-
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
-    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];   // n-major: k pairs adjacent
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    const int64_t M = g.M_dev ? min(*g.M_dev, g.M) : g.M;
-    const int64_t K = g.K_dev ? min(*g.K_dev, g.K) : g.K;
-    if (m0 >= M) return;
-    // split-K range
-    const int64_t kchunk = ((K + gridDim.z - 1) / gridDim.z + GBK - 1) / GBK * GBK;
-    const int64_t kbeg = int64_t(blockIdx.z) * kchunk, kend = min(K, kbeg + kchunk);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gq = lane >> 2, tq = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
-        for (int e = tid; e < GBM * GBK; e += 128) {
-            int m, k;
-            if (TA) { m = e % GBM; k = e / GBM; }     // consecutive threads along the stored row (m)
-            else { k = e % GBK; m = e / GBK; }
-            const int64_t gm = m0 + m, gk = k0 + k;
-            __nv_bfloat16 v = zero;
-            if (gm < M && gk < kend) v = TA ? g.A[gk * g.lda + gm] : g.A[gm * g.lda + gk];
-            As[m][k] = v;
-        }
-        for (int e = tid; e < GBN * GBK; e += 128) {
-            int n, k;
-            if (TB) { k = e % GBK; n = e / GBK; }
-            else { n = e % GBN; k = e / GBN; }
-            const int64_t gn = n0 + n, gk = k0 + k;
-            __nv_bfloat16 v = zero;
-            if (gn < g.N && gk < kend) v = TB ? g.B[gn * g.ldb + gk] : g.B[gk * g.ldb + gn];
-            Bs[n][k] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GBK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + 16 * i + gq, c = kk + 2 * tq;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][c]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][c]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][c + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][c + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = wn + 8 * j + gq, c = kk + 2 * tq;
-                bf[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][c]);
-                bf[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][c + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
-    }
-    // epilogue
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int64_t m = m0 + wm + 16 * i + gq + (r >= 2 ? 8 : 0);
-                const int64_t n = n0 + wn + 8 * j + 2 * tq + (r & 1);
-                if (m >= M || n >= g.N) continue;
-                float v = acc[i][j][r];
-                const int64_t o = m * g.ldc + n;
-                switch (g.epi) {
-                case EPI_BIAS_RELU_BF16:
-                    v = fmaxf(v + g.bias[n], 0.f);
-                    g.Cb[o] = __float2bfloat16(v);
-                    break;
-                case EPI_MASK_BF16:
-                    v = __bfloat162float(g.mask[m * g.ldmask + n]) > 0.f ? v : 0.f;
-                    g.Cb[o] = __float2bfloat16(v);
-                    break;
-                case EPI_BF16:
-                    g.Cb[o] = __float2bfloat16(v);
-                    break;
-                default:   // EPI_F32_SPLIT: partial sums of split z
-                    g.Cf[int64_t(blockIdx.z) * M * g.ldc + o] = v;
-                    break;
-                }
-            }
 }
 
 // Sum of the split-K partials in a fixed order.
@@ -224,41 +120,6 @@ __global__ void __launch_bounds__(SUR_H) k_pool_bwd(const PoolArgs a) {
 }
 
 // ------------------------------------------------------------------ output layer, loss, outputs
-// y[e] = G[e] . V2 + c2 (4 outputs) on the tensor cores: one warp per 16
-// events, 16 k-steps in ascending order, V2 widened to 8 zero-padded columns.
-__global__ void __launch_bounds__(256) k_head(const HeadArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int gq = lane >> 2, tq = lane & 3;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
-    for (int64_t r0 = int64_t(warp) * 16; r0 < n_evt; r0 += nwarps * 16) {
-        const int64_t ra = r0 + gq, rb = r0 + gq + 8;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-        for (int ks = 0; ks < SUR_G / 16; ++ks) {
-            const int k = 16 * ks + 2 * tq;
-            uint32_t af[4], bf[2];
-            af[0] = ra < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + ra * SUR_G + k) : 0u;
-            af[1] = rb < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + rb * SUR_G + k) : 0u;
-            af[2] = ra < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + ra * SUR_G + k + 8) : 0u;
-            af[3] = rb < n_evt ? *reinterpret_cast<const uint32_t*>(a.G + rb * SUR_G + k + 8) : 0u;
-            head_b_fragment(a.V2b, ks, gq, tq, bf);
-            mma_bf16(acc, af, bf);
-        }
-        if (tq < 2) {
-            const int c = 2 * tq;
-            if (ra < n_evt) {
-                a.Y[ra * 4 + c] = acc[0] + a.c2[c];
-                a.Y[ra * 4 + c + 1] = acc[1] + a.c2[c + 1];
-            }
-            if (rb < n_evt) {
-                a.Y[rb * 4 + c] = acc[2] + a.c2[c];
-                a.Y[rb * 4 + c + 1] = acc[3] + a.c2[c + 1];
-            }
-        }
-    }
-}
-
 // Per-event loss terms and dL/dy (mean over n_evt events).
 __global__ void k_loss(const LossArgs a) {
     const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
@@ -356,20 +217,6 @@ __global__ void k_adam(const AdamArgs a) {
 }
 
 // ------------------------------------------------------------------ launchers
-template <bool TA, bool TB>
-static cudaError_t gemm_t(const GemmArgs& g, int splits, cudaStream_t s) {
-    dim3 grid(unsigned((g.N + GBN - 1) / GBN), unsigned((g.M + GBM - 1) / GBM), unsigned(splits));
-    k_gemm<TA, TB><<<grid, 128, 0, s>>>(g);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gemm(const GemmArgs& g, bool ta, bool tb, int splits, cudaStream_t s) {
-    if (ta && tb) return gemm_t<true, true>(g, splits, s);
-    if (ta) return gemm_t<true, false>(g, splits, s);
-    if (tb) return gemm_t<false, true>(g, splits, s);
-    return gemm_t<false, false>(g, splits, s);
-}
-
 cudaError_t launch_features(const FeatArgs& a, int grid, cudaStream_t s) {
     k_features<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -377,10 +224,6 @@ cudaError_t launch_features(const FeatArgs& a, int grid, cudaStream_t s) {
 cudaError_t launch_pool(const PoolArgs& a, int grid, bool bwd, cudaStream_t s) {
     if (bwd) k_pool_bwd<<<grid, SUR_H, 0, s>>>(a);
     else k_pool<<<grid, SUR_H, 0, s>>>(a);
-    return cudaGetLastError();
-}
-cudaError_t launch_head(const HeadArgs& a, int grid, cudaStream_t s) {
-    k_head<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_head_bwd(const HeadArgs& a, int grid, cudaStream_t s) {

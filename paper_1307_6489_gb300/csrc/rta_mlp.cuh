@@ -31,12 +31,15 @@ constexpr int64_t OFF_C2 = OFF_V2 + SUR_G * 4;
 constexpr int64_t N_PARAM_INTERNAL = OFF_C2 + 4;
 // Weights of the inference kernels' tensor-core layers, transposed to N x K and
 // laid out as canonical K-major core matrices (see rta_tc.cuh): W1 (128 x 16),
-// W2 (128 x 128), V1 (256 x 256). Refreshed from the BF16 twin after every
-// parameter change.
+// W2 (128 x 128), V1 (256 x 256); then the padded output layer. Refreshed from
+// the BF16 twin after every parameter change.
 constexpr int64_t PK_W1T = 0;
 constexpr int64_t PK_W2T = PK_W1T + SUR_H * SUR_XPAD;
 constexpr int64_t PK_V1T = PK_W2T + SUR_H * SUR_H;
-constexpr int64_t N_PK = PK_V1T + SUR_G * SUR_G;
+// V2 widened to 16 zero-padded columns, row-major [256 x 16]: the B operand of
+// the training path's output layer.
+constexpr int64_t PK_V2P = PK_V1T + SUR_G * SUR_G;
+constexpr int64_t N_PK = PK_V2P + SUR_G * 16;
 constexpr int64_t N_PARAM_PACKED = SUR_NF * SUR_H + SUR_H + SUR_H * SUR_H + SUR_H + SUR_G * SUR_G + SUR_G + SUR_G * 4 + 4;
 
 struct FeatArgs {
@@ -56,20 +59,27 @@ struct FeatArgs {
     int32_t* n_used;         // [n_evt], -1 = malformed event
 };
 
-enum { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32_SPLIT = 2, EPI_BF16 = 3 };
+// Epilogues: ReLU(D + bias) as BF16; D where mask > 0 (the ReLU derivative) as
+// BF16; D as BF16; D as the FP32 partial sum of a split reduction; the first
+// n_store columns of D + bias as FP32.
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32_SPLIT = 2, EPI_BF16 = 3, EPI_F32_BIAS = 4 };
 
+// D[M x N] = op(A) op(B): A stored [M x K] (K-major) or [K x M] (MN-major), B
+// stored [N x K] (K-major) or [K x N] (MN-major); 16 <= N <= 256, N % 16 == 0;
+// MN-major row counts and K-major K are multiples of 8; leading dimensions
+// and bases 16-byte aligned.
 struct GemmArgs {
     const __nv_bfloat16* A;
     const __nv_bfloat16* B;
     int64_t lda, ldb, ldc, ldmask;
     int64_t M, N, K;
-    const int64_t* M_dev;    // optional run-time row count (<= M)
-    const int64_t* K_dev;    // optional run-time reduction length (<= K)
     int epi;
+    int n_store;             // EPI_F32_BIAS: columns written
     const float* bias;
     const __nv_bfloat16* mask;
     __nv_bfloat16* Cb;
     float* Cf;
+    unsigned int* status;    // device status word (RTA_DEV_TIMEOUT)
 };
 
 struct PoolArgs {
@@ -137,9 +147,12 @@ struct AdamArgs {
 };
 
 cudaError_t launch_features(const FeatArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_gemm(const GemmArgs& g, bool ta, bool tb, int splits, cudaStream_t s);
+// Tensor-core GEMM (tcgen05): a_mn / b_mn give the operands' storage order;
+// splits > 1 divides K (EPI_F32_SPLIT; gemm_tc_splits gives the number of
+// partial sums actually written).
+cudaError_t launch_gemm(const GemmArgs& g, bool a_mn, bool b_mn, int splits, int n_sm, cudaStream_t s);
+int gemm_tc_splits(int64_t K, int splits);
 cudaError_t launch_pool(const PoolArgs& a, int grid, bool bwd, cudaStream_t s);
-cudaError_t launch_head(const HeadArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_head_bwd(const HeadArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_loss(const LossArgs& a, int grid, float* d_loss, cudaStream_t s);
 cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, const int64_t* rows_dev, int64_t rows, int cols,

@@ -101,9 +101,10 @@ int reserve(rta_model* md, int64_t n_img, int64_t n_evt) {
 
 int blocks_for(int64_t n, int per) { return int(std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 65535))); }
 
-int gemm(const __nv_bfloat16* A, int64_t lda, bool ta, const __nv_bfloat16* B, int64_t ldb, bool tb, int64_t M, int64_t N,
-         int64_t K, int epi, const float* bias, const __nv_bfloat16* mask, int64_t ldmask, __nv_bfloat16* Cb, float* Cf,
-         int64_t ldc, int splits, cudaStream_t s) {
+// D = op(A) op(B) on the tensor cores. ta: A stored [K x M]; tb: B stored [N x K].
+int gemm(rta_model* md, const __nv_bfloat16* A, int64_t lda, bool ta, const __nv_bfloat16* B, int64_t ldb, bool tb,
+         int64_t M, int64_t N, int64_t K, int epi, const float* bias, const __nv_bfloat16* mask, int64_t ldmask,
+         __nv_bfloat16* Cb, float* Cf, int64_t ldc, int splits, cudaStream_t s, int n_store = 0) {
     rta::GemmArgs g;
     g.A = A;
     g.B = B;
@@ -114,28 +115,30 @@ int gemm(const __nv_bfloat16* A, int64_t lda, bool ta, const __nv_bfloat16* B, i
     g.M = M;
     g.N = N;
     g.K = K;
-    g.M_dev = nullptr;
-    g.K_dev = nullptr;
     g.epi = epi;
+    g.n_store = n_store;
     g.bias = bias;
     g.mask = mask;
     g.Cb = Cb;
     g.Cf = Cf;
-    S_TRY(rta::launch_gemm(g, ta, tb, splits, s));
+    g.status = rta::surrogate_ctx_status(md->ctx);
+    S_TRY(rta::launch_gemm(g, ta, !tb, splits, md->n_sm, s));
     return RTA_OK;
 }
 
-// Weight gradient [M x N] = A^T B with the reduction split over `splits` blocks
-// and summed in a fixed order.
+// Weight gradient [M x N] = A^T B with the reduction split into K-ranges whose
+// partial sums are added in a fixed order.
 int weight_grad(rta_model* md, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M,
                 int64_t N, int64_t K, float* out, cudaStream_t s) {
-    const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
-    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(256 / tiles, (K + 127) / 128));
+    const int64_t tiles = (M + 127) / 128;
+    // about one work item per SM, each at least 8 chunks (512 rows) of the reduction
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(md->n_sm / tiles, (K + 511) / 512));
     splits = std::min<int64_t>(splits, SPLIT_WS / (M * N));
-    int rc = gemm(A, lda, true, B, ldb, false, M, N, K, rta::EPI_F32_SPLIT, nullptr, nullptr, 0, nullptr, md->split_ws,
-                  N, int(splits), s);
+    const int used = rta::gemm_tc_splits(K, int(splits));
+    int rc = gemm(md, A, lda, true, B, ldb, false, M, N, K, rta::EPI_F32_SPLIT, nullptr, nullptr, 0, nullptr,
+                  md->split_ws, N, int(splits), s);
     if (rc) return rc;
-    S_TRY(rta::launch_reduce_splits(md->split_ws, int(splits), M * N, out, s));
+    S_TRY(rta::launch_reduce_splits(md->split_ws, used, M * N, out, s));
     return RTA_OK;
 }
 
@@ -173,10 +176,10 @@ int forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     S_TRY(rta::launch_features(f, blocks_for(n_evt, 256 / rta::SUR_EVT_LANES), s));
     const __nv_bfloat16* pb = md->pb;
     if (n_img > 0) {
-        if ((rc = gemm(md->X, SUR_XPAD, false, pb + rta::OFF_W1, SUR_H, false, n_img, SUR_H, SUR_XPAD,
+        if ((rc = gemm(md, md->X, SUR_XPAD, false, pb + rta::OFF_W1, SUR_H, false, n_img, SUR_H, SUR_XPAD,
                        rta::EPI_BIAS_RELU_BF16, md->p + rta::OFF_B1, nullptr, 0, md->H1, nullptr, SUR_H, 1, s)))
             return rc;
-        if ((rc = gemm(md->H1, SUR_H, false, pb + rta::OFF_W2, SUR_H, false, n_img, SUR_H, SUR_H,
+        if ((rc = gemm(md, md->H1, SUR_H, false, pb + rta::OFF_W2, SUR_H, false, n_img, SUR_H, SUR_H,
                        rta::EPI_BIAS_RELU_BF16, md->p + rta::OFF_B2, nullptr, 0, md->H2, nullptr, SUR_H, 1, s)))
             return rc;
     }
@@ -188,16 +191,13 @@ int forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, in
     pa.H2 = md->H2;
     pa.P = md->P;
     S_TRY(rta::launch_pool(pa, blocks_for(n_evt, 1), false, s));
-    if ((rc = gemm(md->P, SUR_G, false, pb + rta::OFF_V1, SUR_G, false, n_evt, SUR_G, SUR_G, rta::EPI_BIAS_RELU_BF16,
+    if ((rc = gemm(md, md->P, SUR_G, false, pb + rta::OFF_V1, SUR_G, false, n_evt, SUR_G, SUR_G, rta::EPI_BIAS_RELU_BF16,
                    md->p + rta::OFF_C1, nullptr, 0, md->G, nullptr, SUR_G, 1, s)))
         return rc;
-    rta::HeadArgs ha = {};
-    ha.n_evt = n_evt;
-    ha.G = md->G;
-    ha.V2b = pb + rta::OFF_V2;
-    ha.c2 = md->p + rta::OFF_C2;
-    ha.Y = md->Y;
-    S_TRY(rta::launch_head(ha, blocks_for(n_evt, 128), s));
+    // output layer: Y = G V2 + c2 (V2 widened to 16 zero columns; 4 stored)
+    if ((rc = gemm(md, md->G, SUR_G, false, md->pk + rta::PK_V2P, 16, false, n_evt, 16, SUR_G, rta::EPI_F32_BIAS,
+                   md->p + rta::OFF_C2, nullptr, 0, nullptr, md->Y, 4, 1, s, 4)))
+        return rc;
     return RTA_OK;
 }
 
@@ -388,7 +388,7 @@ int rta_surrogate_train_step(rta_model* md, const rta_hillas_t* d_h, const int32
     // event network
     if ((rc = weight_grad(md, md->P, SUR_G, md->dG, SUR_G, SUR_G, SUR_G, n_evt, md->g + rta::OFF_V1, s))) return rc;
     S_TRY(rta::launch_colsum(md->dG, nullptr, nullptr, n_evt, SUR_G, md->g + rta::OFF_C1, s));
-    if ((rc = gemm(md->dG, SUR_G, false, md->pb + rta::OFF_V1, SUR_G, true, n_evt, SUR_G, SUR_G, rta::EPI_BF16, nullptr,
+    if ((rc = gemm(md, md->dG, SUR_G, false, md->pb + rta::OFF_V1, SUR_G, true, n_evt, SUR_G, SUR_G, rta::EPI_BF16, nullptr,
                    nullptr, 0, md->dP, nullptr, SUR_G, 1, s)))
         return rc;
     // pooling
@@ -407,7 +407,7 @@ int rta_surrogate_train_step(rta_model* md, const rta_hillas_t* d_h, const int32
         if ((rc = weight_grad(md, md->H1, SUR_H, md->dZ2, SUR_H, SUR_H, SUR_H, n_img, md->g + rta::OFF_W2, s)))
             return rc;
         S_TRY(rta::launch_colsum(md->dZ2, nullptr, nullptr, n_img, SUR_H, md->g + rta::OFF_B2, s));
-        if ((rc = gemm(md->dZ2, SUR_H, false, md->pb + rta::OFF_W2, SUR_H, true, n_img, SUR_H, SUR_H,
+        if ((rc = gemm(md, md->dZ2, SUR_H, false, md->pb + rta::OFF_W2, SUR_H, true, n_img, SUR_H, SUR_H,
                        rta::EPI_MASK_BF16, nullptr, md->H1, SUR_H, md->dZ1, nullptr, SUR_H, 1, s)))
             return rc;
         if ((rc = weight_grad(md, md->X, SUR_XPAD, md->dZ1, SUR_H, SUR_XPAD, SUR_H, n_img, md->g + rta::OFF_W1, s)))

@@ -34,9 +34,8 @@ def cam_codes(wl):
     return codes
 
 
-@pytest.fixture(scope="module")
-def setup():
-    wl = synth.make_workload(3, 300)
+def make_setup(n_events):
+    wl = synth.make_workload(3, n_events)
     ref = oracle.reconstruct(wl, do_stereo=False)
     rows32 = hillas_rows_as_f32(ref["hillas"])
     same = f32_rows_as_oracle(rows32)
@@ -52,10 +51,29 @@ def setup():
              logE=torch.from_numpy(np.log10(wl.truth[:, 0]).astype(np.float32)).cuda(),
              src=torch.from_numpy(wl.truth[:, 1:3].astype(np.float32).reshape(-1)).cuda(),
              gam=torch.from_numpy((wl.truth[:, 5] == 0).astype(np.uint8)).cuda())
-    yield dict(wl=wl, ctx=ctx, model=model, p=p, same=same, X=X, used=used, base=base, n_used=n_used, d=d,
-               rows32=rows32)
-    rta.rta_surrogate_destroy(model)
-    ctx.close()
+    return dict(wl=wl, ctx=ctx, model=model, p=p, same=same, X=X, used=used, base=base, n_used=n_used, d=d,
+                rows32=rows32)
+
+
+def close_setup(s):
+    rta.rta_surrogate_destroy(s["model"])
+    s["ctx"].close()
+
+
+@pytest.fixture(scope="module")
+def setup():
+    s = make_setup(300)
+    yield s
+    close_setup(s)
+
+
+@pytest.fixture(scope="module")
+def big():
+    """A training-sized batch: about 100 tiles of 128 image rows with a ragged
+    last one, and weight gradients reduced over several K-ranges."""
+    s = make_setup(3000)
+    yield s
+    close_setup(s)
 
 
 def gpu_forward(s):
@@ -68,8 +86,9 @@ def gpu_forward(s):
     return y.cpu().numpy().reshape(-1, 4), b.cpu().numpy().reshape(-1, 2)
 
 
-def test_forward_and_baseline_match_the_oracle(setup):
-    s = setup
+@pytest.mark.parametrize("which", ["setup", "big"])
+def test_forward_and_baseline_match_the_oracle(which, request):
+    s = request.getfixturevalue(which)
     y, b = gpu_forward(s)
     np.testing.assert_allclose(b, s["base"], atol=1e-4)
     y_ref, _ = mlp.forward(s["p"], mlp.bf16_round(s["X"]), s["used"], s["wl"].evt_off)
@@ -79,8 +98,9 @@ def test_forward_and_baseline_match_the_oracle(setup):
     assert np.abs(y_ref).max() > 0.1                      # a non-trivial network
 
 
-def test_gradients_match_the_oracle(setup):
-    s = setup
+@pytest.mark.parametrize("which", ["setup", "big"])
+def test_gradients_match_the_oracle(which, request):
+    s = request.getfixturevalue(which)
     wl, d = s["wl"], s["d"]
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     rta.rta_surrogate_train_step(s["model"], d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img,
@@ -259,9 +279,10 @@ def _infer_and_forward(s, a, b, merge=1, break_offsets=False):
 
 @pytest.mark.parametrize("case", ["all", "one", "ragged", "hundreds_of_images", "malformed"])
 def test_inference_kernels_agree_with_the_layer_by_layer_forward(setup, case):
-    """The inference kernels (baseline, features, telescope network and pooling
-    with the training path's expressions and orders; event network on tcgen05)
-    against the training-path forward on the same batch: baselines and used
+    """The fused inference kernel (baseline, features, telescope network and
+    pooling with the training path's expressions and orders) against the
+    training-path forward (its tensor-core GEMM kernels) on the same batch:
+    baselines and used
     counts bit for bit, outputs within FP32 accumulation-order effects. The
     event network's products are exact and its sums FP32 in both, in a
     different order; a BF16 rounding of an activation can flip by one unit, so
