@@ -298,7 +298,11 @@ int rta_stereo(rta_ctx* ctx, const rta_hillas_t* d_hillas, const int32_t* d_img_
 
 /* One pass of the whole path over a device-resident bundle:
  * rta_image_chain followed by rta_stereo, stream-ordered, no host sync and no
- * allocation (capturable in a CUDA graph). d_hillas must hold n_img rows. */
+ * allocation (capturable in a CUDA graph). d_hillas must hold n_img rows.
+ * Because the kernel before the stereo kernel is then the image kernel, the
+ * stereo kernel reads the event offsets while the image kernel is finishing:
+ * d_evt_off must not change between the call and the end of its work on the
+ * stream. The same rows as the two calls made one after the other. */
 int rta_reconstruct(rta_ctx* ctx, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
                     const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off, int64_t n_evt, int window_mode,
                     int start, int W, float t_hi, float t_lo, int core_needs_neighbour, rta_hillas_t* d_hillas,
@@ -382,6 +386,23 @@ int rta_surrogate_train_step(rta_model* model, const rta_hillas_t* d_hillas, con
  * model workspace and no allocation: calls on different streams may overlap. */
 int rta_surrogate_infer(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream);
+
+/* The learned reconstruction of a bundle (Sec. 4.1) in one call: rta_image_chain on the
+ * waveforms (Hillas rows into d_hillas, as that call) followed, on the same
+ * stream, by rta_surrogate_infer on those rows (event rows into d_events, as
+ * that call), with the model's context and camera set-up. Because the kernel
+ * before the inference kernel is then known to be the image kernel, the
+ * inference kernel reads the event offsets, telescope ids and weights while
+ * the image kernel is still finishing, and waits only for the Hillas rows:
+ * d_evt_off, d_img_tel and the model's weights must not change between the
+ * call and the end of its work on the stream (no training step of the model on
+ * another stream meanwhile). Errors as the
+ * two calls; nothing is allocated. The same events and rows as the two calls
+ * made one after the other, bit for bit. */
+int rta_reconstruct_learned(rta_model* model, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                            const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off, int64_t n_evt,
+                            int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                            float fallback_deg, rta_hillas_t* d_hillas, rta_event_t* d_events, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* DL0 byte-stream ingest (Sec. 5: the telescope data as a stream of bytes  */

@@ -102,6 +102,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_surrogate_forward": ([P, P, P, i64, P, i64, P, P, P], i32),
         "rta_surrogate_train_step": ([P, P, P, i64, P, i64, P, P, P, f32, i32, P, P], i32),
         "rta_surrogate_infer": ([P, P, P, i64, P, i64, f32, P, P], i32),
+        "rta_reconstruct_learned": ([P, P, i64, P, P, i64, P, i64, i32, i32, i32, f32, f32, i32, f32, P, P, P], i32),
         "rta_stream_create": ([P, P, sz, i32, i64, i64, i32, i32, i32, f32, f32, i32, f32, P], i32),
         "rta_stream_submit": ([P, P, P], i32),
         "rta_stream_poll": ([P, ctypes.c_uint64, P], i32),
@@ -365,6 +366,13 @@ def rta_surrogate_train_step(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt
 
 def rta_surrogate_infer(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, fallback_deg, d_out, stream=0):
     _check(load().rta_surrogate_infer(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, fallback_deg, d_out, stream))
+
+
+def rta_reconstruct_learned(model, d_wave, n_wave, d_wave_off, d_img_tel, n_img, d_evt_off, n_evt, window_mode, start,
+                            W, t_hi, t_lo, core_needs_neighbour, fallback_deg, d_hillas, d_events, stream=0):
+    _check(load().rta_reconstruct_learned(model, d_wave, n_wave, d_wave_off, d_img_tel, n_img, d_evt_off, n_evt,
+                                          window_mode, start, W, t_hi, t_lo, core_needs_neighbour, fallback_deg,
+                                          d_hillas, d_events, stream))
 
 
 def events_to_numpy(raw: np.ndarray) -> dict:

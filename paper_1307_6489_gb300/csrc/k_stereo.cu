@@ -46,11 +46,23 @@ __global__ void __launch_bounds__(ST_NT) k_stereo(const StereoArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / ST_GL, sub = lane % ST_GL;
     StereoImg* im = sh[warp];
-    grid_dependency_wait();          // launched as a programmatic dependent of the image kernel
+    // Launched as a programmatic dependent of the image kernel. When the caller declared the
+    // event offsets and counts settled (written before the image kernel started), they are
+    // read before the dependency wait: the counts and the first round's offsets.
+    if (!a.settled) grid_dependency_wait();
     // a graph captured at capacity reads the bundle's counts at run time
     const int64_t n_evt = a.n_evt_dev ? min(*a.n_evt_dev, a.n_evt) : a.n_evt;
     const int64_t n_img = a.n_img_dev ? min(*a.n_img_dev, a.n_img) : a.n_img;
     const int64_t n_tiles = (n_evt + ST_EPW - 1) / ST_EPW;
+    int pre0 = 0, pre1 = 0;                                // the first round's offsets of this group
+    {
+        const int64_t e = (int64_t(blockIdx.x) * ST_WARPS + warp) * ST_EPW + g;
+        if (e < n_evt) {
+            pre0 = a.evt_off[e];
+            pre1 = a.evt_off[e + 1];
+        }
+    }
+    if (a.settled) grid_dependency_wait();
     for (int64_t r0 = int64_t(blockIdx.x) * ST_WARPS; r0 < n_tiles; r0 += int64_t(gridDim.x) * ST_WARPS) {
         __syncthreads();                                   // the previous round's list is read
         if (threadIdx.x == 0) n_big = 0;
@@ -61,7 +73,8 @@ __global__ void __launch_bounds__(ST_NT) k_stereo(const StereoArgs a) {
             int i0 = 0, m = 0;
             bool valid = false;
             if (e < n_evt) {
-                const int b0 = a.evt_off[e], b1 = a.evt_off[e + 1];
+                const bool first = r0 == int64_t(blockIdx.x) * ST_WARPS;
+                const int b0 = first ? pre0 : a.evt_off[e], b1 = first ? pre1 : a.evt_off[e + 1];
                 if (b0 < 0 || b1 < b0 || b1 > n_img) {         // malformed CSR: flag, never index
                     if (sub == 0) {
                         atomicOr(a.status, RTA_DEV_BAD_IMAGE);

@@ -309,10 +309,13 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     return RTA_OK;
 }
 
+// settled: the kernel before the stereo kernel on the stream is the image kernel, and the event
+// offsets and counts were written before it started (read before the dependency wait).
 int run_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off,
                int64_t n_evt, rta_stereo_t* d_out, cudaStream_t s, const int64_t* d_n_img = nullptr,
-               const int64_t* d_n_evt = nullptr) {
-    rta::StereoArgs a;
+               const int64_t* d_n_evt = nullptr, bool settled = false) {
+    rta::StereoArgs a = {};
+    a.settled = settled ? 1 : 0;
     a.arr = dev_array(c);
     a.h = d_h;
     a.img_tel = d_img_tel;
@@ -736,7 +739,13 @@ int rta_reconstruct(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const in
     int rc = rta_image_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
                              core_needs_neighbour, d_hillas, stream);
     if (rc) return rc;
-    return rta_stereo(c, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_stereo, stream);
+    if ((rc = check_n(n_evt, "n_evt"))) return rc;
+    if (n_evt == 0) return RTA_OK;
+    if (!d_evt_off || !d_stereo) return fail(RTA_E_INVALID, "NULL device pointer");
+    // the kernel before the stereo kernel is the image kernel (launched when n_img > 0), which
+    // started after the event offsets were written: they are read before the dependency wait
+    return run_stereo(c, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_stereo, (cudaStream_t)stream, nullptr,
+                      nullptr, n_img > 0);
 }
 
 int rta_reconstruct_host(rta_ctx* c, const uint16_t* h_wave, int64_t n_wave, const int64_t* h_wave_off,

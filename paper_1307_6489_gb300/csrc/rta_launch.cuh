@@ -84,6 +84,8 @@ struct StereoArgs {
     const int64_t* n_evt_dev;
     rta_stereo_t* out;
     unsigned int* status;
+    int settled;               // event offsets and counts were written before the kernel this one follows
+                               // on the stream started: they are read before the dependency wait
 };
 
 int chain_variant_warps(int v);

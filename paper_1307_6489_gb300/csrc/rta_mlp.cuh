@@ -15,9 +15,10 @@
 
 namespace rta {
 
-// Lanes per event of the per-event prologue (used images, baseline): a pair, so
-// that 256 threads take 128 events at once (half of the events have 2-3 images).
-constexpr int SUR_EVT_LANES = 2;
+// Lanes per event of the per-event prologue (used images, baseline): four, so
+// that 512 threads take a tile of 128 events at once and an event of 40 images
+// takes ten steps per lane.
+constexpr int SUR_EVT_LANES = 4;
 
 // internal parameter layout (FP32 master copy and its BF16 twin), element offsets
 constexpr int64_t OFF_W1 = 0;                                // [16 x 128], rows 12..15 zero
@@ -133,6 +134,9 @@ struct InferArgs {
     const float* p;            // FP32 master (biases)
     const __nv_bfloat16* pk;   // tensor-core weight layout (PK_*)
     int rows_aligned;          // f.h is 16-byte aligned: a tile's rows may arrive by bulk copy
+    int settled;               // the event offsets, telescope ids and weights were written before the
+                               // kernel this one follows on the stream started: they are read before
+                               // the dependency wait (only the Hillas rows are the preceding kernel's)
     OutArgs o;
 };
 

@@ -243,6 +243,35 @@ int upload_params(rta_model* md, const std::vector<float>& internal) {
 
 }  // namespace
 
+// The inference launch; settled: the kernel before it on the stream is the image kernel, so
+// the event offsets, telescope ids and weights may be read before its dependency wait.
+static int infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off,
+          int64_t n_evt, float fallback_deg, rta_event_t* d_out, cudaStream_t s, bool settled) {
+    int rc = check_batch(md, d_h, d_img_tel, n_img, d_evt_off, n_evt, false);
+    if (rc) return rc;
+    if (n_evt == 0) return RTA_OK;
+    if (!d_out) return sfail(RTA_E_INVALID, "NULL output");
+    if (!(fallback_deg > 0.f)) return sfail(RTA_E_INVALID, "fallback bound must be > 0");
+    rta::InferArgs ia = {};
+    ia.f.h = d_h;
+    ia.f.img_tel = d_img_tel;
+    ia.f.evt_off = d_evt_off;
+    ia.f.n_img = n_img;
+    ia.f.n_evt = n_evt;
+    if ((rc = rta::surrogate_ctx_tables(md->ctx, &ia.f.tel_cam, &ia.f.tel_xy, &ia.f.n_tel, nullptr))) return rc;
+    ia.f.cam_code = md->cam_code;
+    ia.pb = md->pb;
+    ia.p = md->p;
+    ia.pk = md->pk;
+    ia.rows_aligned = (reinterpret_cast<uintptr_t>(d_h) & 15u) == 0;
+    ia.settled = settled ? 1 : 0;
+    ia.o.fallback_deg = fallback_deg;
+    ia.o.out = d_out;
+    ia.o.status = rta::surrogate_ctx_status(md->ctx);
+    S_TRY(rta::launch_infer(ia, md->n_sm, s));
+    return RTA_OK;
+}
+
 extern "C" {
 
 int rta_surrogate_num_params(void) { return int(rta::N_PARAM_PACKED); }
@@ -439,29 +468,24 @@ int rta_surrogate_train_step(rta_model* md, const rta_hillas_t* d_h, const int32
 
 int rta_surrogate_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
                         const int32_t* d_evt_off, int64_t n_evt, float fallback_deg, rta_event_t* d_out, void* stream) {
-    int rc = check_batch(md, d_h, d_img_tel, n_img, d_evt_off, n_evt, false);
+    return infer(md, d_h, d_img_tel, n_img, d_evt_off, n_evt, fallback_deg, d_out, (cudaStream_t)stream, false);
+}
+
+int rta_reconstruct_learned(rta_model* md, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                            const int32_t* d_img_tel, int64_t n_img, const int32_t* d_evt_off, int64_t n_evt,
+                            int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
+                            float fallback_deg, rta_hillas_t* d_hillas, rta_event_t* d_events, void* stream) {
+    int rc = check_batch(md, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, false);
     if (rc) return rc;
-    if (n_evt == 0) return RTA_OK;
-    if (!d_out) return sfail(RTA_E_INVALID, "NULL output");
+    if (n_evt > 0 && !d_events) return sfail(RTA_E_INVALID, "NULL output");
     if (!(fallback_deg > 0.f)) return sfail(RTA_E_INVALID, "fallback bound must be > 0");
-    cudaStream_t s = (cudaStream_t)stream;
-    rta::InferArgs ia = {};
-    ia.f.h = d_h;
-    ia.f.img_tel = d_img_tel;
-    ia.f.evt_off = d_evt_off;
-    ia.f.n_img = n_img;
-    ia.f.n_evt = n_evt;
-    if ((rc = rta::surrogate_ctx_tables(md->ctx, &ia.f.tel_cam, &ia.f.tel_xy, &ia.f.n_tel, nullptr))) return rc;
-    ia.f.cam_code = md->cam_code;
-    ia.pb = md->pb;
-    ia.p = md->p;
-    ia.pk = md->pk;
-    ia.rows_aligned = (reinterpret_cast<uintptr_t>(d_h) & 15u) == 0;
-    ia.o.fallback_deg = fallback_deg;
-    ia.o.out = d_out;
-    ia.o.status = rta::surrogate_ctx_status(md->ctx);
-    S_TRY(rta::launch_infer(ia, md->n_sm, s));
-    return RTA_OK;
+    rc = rta_image_chain(md->ctx, d_wave, n_wave, d_wave_off, d_img_tel, n_img, window_mode, start, W, t_hi, t_lo,
+                         core_needs_neighbour, d_hillas, stream);
+    if (rc) return rc;
+    // with no image the image kernel is not launched, and the kernel before the inference is
+    // unknown: the inputs are then read after the dependency wait
+    return infer(md, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, fallback_deg, d_events, (cudaStream_t)stream,
+                 n_img > 0);
 }
 
 }  // extern "C"

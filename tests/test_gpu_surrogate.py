@@ -309,3 +309,36 @@ def test_inference_kernels_agree_with_the_layer_by_layer_forward(setup, case):
         np.testing.assert_array_equal(ev["n_used"], s["n_used"][a:b])
     else:
         assert ev["n_used"].max() > 64
+
+
+@pytest.mark.parametrize("bound", [1e3, 0.05])
+def test_fused_learned_call_equals_the_two_calls(setup, bound):
+    """rta_reconstruct_learned runs the image kernel and then the inference kernel,
+    which reads the event offsets, telescope ids and weights before its dependency
+    wait: its Hillas rows and event rows equal those of rta_image_chain followed
+    by rta_surrogate_infer bit for bit, with (bound 0.05 deg) and without
+    geometric fallbacks, on three calls in a row."""
+    s = setup
+    wl, ctx = s["wl"], s["ctx"]
+    dv = Dev(wl)
+    proc = proc_args(wl)
+    stream = torch.cuda.current_stream().cuda_stream
+    h_ref, ev_ref = dv.hillas_buf(), torch.zeros(wl.n_evt * 32, dtype=torch.uint8, device="cuda")
+    rta.rta_image_chain(ctx.handle, dv.wave.data_ptr(), dv.wave.numel(), dv.wave_off.data_ptr(), dv.img_tel.data_ptr(),
+                        wl.n_img, *proc, h_ref.data_ptr(), stream)
+    rta.rta_surrogate_infer(s["model"], h_ref.data_ptr(), dv.img_tel.data_ptr(), wl.n_img, dv.evt_off.data_ptr(),
+                            wl.n_evt, bound, ev_ref.data_ptr(), stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ev0 = rta.events_to_numpy(ev_ref.cpu().numpy())
+    if bound < 1:
+        assert ((ev0["flags"] & rta.RTA_EF_FALLBACK) != 0).sum() > 5
+    for _ in range(3):
+        h, ev = dv.hillas_buf(), torch.zeros(wl.n_evt * 32, dtype=torch.uint8, device="cuda")
+        rta.rta_reconstruct_learned(s["model"], dv.wave.data_ptr(), dv.wave.numel(), dv.wave_off.data_ptr(),
+                                    dv.img_tel.data_ptr(), wl.n_img, dv.evt_off.data_ptr(), wl.n_evt, *proc, bound,
+                                    h.data_ptr(), ev.data_ptr(), stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        assert torch.equal(h.view(torch.int32), h_ref.view(torch.int32))
+        assert torch.equal(ev, ev_ref)
