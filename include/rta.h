@@ -602,39 +602,52 @@ typedef struct rta_bundle_t {
 typedef struct rta_stream rta_stream;
 
 /* Create the serving engine. hbm_budget_bytes is allocated once and
- * sub-allocated per bundle (its waveforms, tables, Hillas rows and event
- * list): a bundle is admitted when one of max_inflight slots (CUDA streams) is
- * free and the budget has room, in arrival order; bundles of several slots run
- * concurrently. Each bundle, on its slot's stream: copies in, rta_image_chain,
- * then rta_surrogate_infer with the given model (events with a learned direction,
- * geometric fallback; the learned stages of concurrent bundles overlap) or,
- * with model = NULL, rta_stereo (geometric direction,
- * no energy or gammaness), the sky-map fill of the one-second slab of its
- * arrival, and the copy of its event list out. max_img / max_evt bound one
- * bundle. A scheduler thread owned by the stream does the device work. Each
- * slot keeps a pinned host staging buffer of max(12 max_img + 4 (max_evt + 1),
- * 32 max_evt) bytes for the bundle's tables and its event list, so that only
- * h_wave needs to be pinned for the copies to run asynchronously. */
+ * sub-allocated per bundle (its waveforms and tables): a bundle is admitted,
+ * in arrival order, when one of max_inflight copy slots (CUDA streams) is free
+ * and the budget has room; its slot's stream copies it in and then publishes
+ * its descriptor into a queue held in device memory. Reconstruction runs as
+ * passes on one compute stream, each of which takes on the device every bundle
+ * published and not yet taken (up to twice max_img images and twice max_evt
+ * events), and runs once over all of them: rta_image_chain, then
+ * rta_surrogate_infer with the given model (events with a learned direction,
+ * geometric fallback) or, with model = NULL, rta_stereo (geometric direction,
+ * no energy or gammaness); each bundle's event rows go straight into its
+ * slot's mapped host staging, and its events into the sky-map slabs of its
+ * arrival (slab ownership is kept on the device). Bundles published while a
+ * pass runs are taken by the next one: copies of arriving bundles overlap the
+ * reconstruction of earlier ones. max_img / max_evt bound one bundle (at most
+ * 2^29). A scheduler thread owned by the stream issues the copies and the
+ * passes. Each slot keeps a pinned, mapped host staging buffer of
+ * max(12 max_img + 4 (max_evt + 1), 32 max_evt) bytes for the bundle's tables
+ * and its event list, so that only h_wave needs to be pinned for the copies to
+ * run asynchronously. A bundle's event rows do not depend on the bundles that
+ * share its pass. */
 int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, int max_inflight, int64_t max_img,
                       int64_t max_evt, int window_mode, int start, int W, float t_hi, float t_lo,
                       int core_needs_neighbour, float fallback_deg, rta_stream** out);
 /* Queue a bundle; returns at once with its ticket. RTA_E_NOMEM if it can never
- * fit the budget, RTA_E_BUSY if 4096 bundles are already waiting. */
+ * fit the budget, RTA_E_BUSY if 4096 bundles are already waiting, RTA_E_INVALID
+ * or RTA_E_ALIGN if an image lies outside h_wave, has an offset that is not a
+ * multiple of 8 samples, or names an unregistered telescope. */
 int rta_stream_submit(rta_stream* stream, const rta_bundle_t* bundle, uint64_t* ticket);
 /* Non-blocking: RTA_OK once the bundle's event list is in host memory (its
  * completion time in *done_ns, same clock as arrival_ns; the ticket is then
  * released), RTA_E_BUSY while it is queued or running. */
 int rta_stream_poll(rta_stream* stream, uint64_t ticket, int64_t* done_ns);
 /* Where a bundle's time went: host steady-clock instants (ns, the clock of
- * arrival_ns) of its arrival, submission, admission to a slot and completion,
- * and device durations measured by timing events on its slot's stream: the
- * copies in (waveforms and tables), the device work (image kernel and learned
- * or geometric reconstruction) and the copy of the event list out (which waits
- * for the sky-map fill). The queue wait is admit_ns - arrival_ns. */
+ * arrival_ns) of its arrival, submission, admission to a copy slot and
+ * completion; device durations from timing events: the copies in (waveforms
+ * and tables, on its slot's stream), the wait of its published data for the
+ * pass that took it, that pass's device work (image kernel and learned or
+ * geometric reconstruction over the whole batch) and the pass's output (event
+ * rows to host memory and the sky-map fill); and the number of bundles in its
+ * pass. The host queue wait is admit_ns - arrival_ns. */
 typedef struct rta_bundle_times_t {
     int64_t arrival_ns, submit_ns, admit_ns, done_ns;
     float h2d_ms, compute_ms, d2h_ms;
     int32_t slot;
+    float ready_wait_ms;
+    int32_t batch_bundles;
 } rta_bundle_times_t;
 /* rta_stream_poll that also returns the bundle's times (times may be NULL). */
 int rta_stream_poll_times(rta_stream* stream, uint64_t ticket, int64_t* done_ns, rta_bundle_times_t* times);

@@ -537,10 +537,12 @@ def rta_stream_poll(stream: int, ticket: int):
 
 class BundleTimes(ctypes.Structure):
     """rta_bundle_times_t: host instants (ns) of a bundle's arrival, submission, admission and completion,
-    and the device durations (ms) of its copies in, device work and copy out."""
+    the device durations (ms) of its copies in, its pass's device work and output, the wait of its
+    published data for that pass, and the number of bundles in the pass."""
     _fields_ = [("arrival_ns", ctypes.c_int64), ("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64),
                 ("done_ns", ctypes.c_int64), ("h2d_ms", ctypes.c_float), ("compute_ms", ctypes.c_float),
-                ("d2h_ms", ctypes.c_float), ("slot", ctypes.c_int32)]
+                ("d2h_ms", ctypes.c_float), ("slot", ctypes.c_int32), ("ready_wait_ms", ctypes.c_float),
+                ("batch_bundles", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -287,7 +287,6 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
     volatile int* abort_s = reinterpret_cast<volatile int*>(sm + S_BAR + 52);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const FeatArgs& f = a.f;
-    const int64_t n_evt = f.n_evt, n_img = f.n_img;
     const int n_tel = min(f.n_tel, RTA_MAX_TEL);
     const bool settled = a.settled != 0;
 
@@ -319,6 +318,9 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
     }
     const float code = tid < RTA_MAX_CAMS ? f.cam_code[tid] : 0.f;
     if (!settled) grid_dependency_wait();
+    // a batch gathered on the device gives its counts at run time (capacities in f)
+    const int64_t n_evt = f.n_evt_dev ? min(*f.n_evt_dev, f.n_evt) : f.n_evt;
+    const int64_t n_img = f.n_img_dev ? min(*f.n_img_dev, f.n_img) : f.n_img;
     if (tid == 0) {
         mbar_arrive_expect_tx(bar_w, uint32_t(W_BYTES));
         bulk_copy(Ws, a.pk + PK_W1T, uint32_t(W_BYTES), bar_w, l2_policy_evict_last());

@@ -17,12 +17,6 @@
 
 namespace rta {
 
-__device__ __forceinline__ int sky_bin(float v) {
-    const float u = __fmul_rn(__fadd_rn(v, 2.56f), 50.0f);
-    if (!(u >= 0.f) || !(u < float(RTA_SKY_N))) return -1;   // also rejects NaN
-    return int(floorf(u));
-}
-
 __global__ void k_skymap_fill(const rta_event_t* ev, int64_t n_evt, unsigned int* slab, unsigned int* slab_min) {
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n_evt; e += int64_t(gridDim.x) * blockDim.x) {
         const rta_event_t r = ev[e];
@@ -142,15 +136,7 @@ __global__ void k_skymap_sum(const unsigned int* slabs, unsigned long long use, 
 // Event rows from geometric stereo rows (used when no learned model is attached).
 __global__ void k_stereo_to_events(const rta_stereo_t* st, int64_t n_evt, rta_event_t* ev) {
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n_evt; e += int64_t(gridDim.x) * blockDim.x) {
-        const rta_stereo_t s = st[e];
-        rta_event_t r = {};
-        r.log_energy = __int_as_float(0x7fc00000);   // no energy estimate
-        r.gammaness = __int_as_float(0x7fc00000);
-        r.dir_x = s.dir_x;
-        r.dir_y = s.dir_y;
-        r.n_used = s.n_valid;
-        r.flags = (s.flags & RTA_SF_INVALID) ? RTA_EF_NO_DIRECTION : 0u;
-        ev[e] = r;
+        ev[e] = stereo_event_row(st[e]);
     }
 }
 

@@ -343,6 +343,46 @@ int check_n(int64_t n, const char* what) {
 }  // namespace
 
 // Context tables the surrogate needs, and the stereo pass over a device list of events.
+int rta::serve_image_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                           const int32_t* d_img_tel, const int64_t* d_n_img, int64_t max_img, int window_mode,
+                           int start, int W, float t_hi, float t_lo, int core_nb, rta_hillas_t* d_out, cudaStream_t s) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(max_img, "max_img"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (!d_wave || !d_wave_off || !d_img_tel || !d_n_img || !d_out || max_img < 1)
+        return fail(RTA_E_INVALID, "NULL pointer or empty capacity");
+    if (!aligned16(d_wave)) return fail(RTA_E_ALIGN, "d_wave is not 16-byte aligned");
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_nb, t_hi, t_lo);
+    return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, max_img, pp, nullptr, nullptr, 0, d_out, 0, s,
+                     nullptr, d_n_img);
+}
+
+int rta::serve_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t max_img,
+                      const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_n_img, const int64_t* d_n_evt,
+                      rta_stereo_t* d_out, cudaStream_t s) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c))) return rc;
+    if (!d_h || !d_img_tel || !d_evt_off || !d_n_img || !d_n_evt || !d_out || max_img < 1 || max_evt < 1)
+        return fail(RTA_E_INVALID, "NULL pointer or empty capacity");
+    // the counts and offsets were written before the image kernel before it started
+    return run_stereo(c, d_h, d_img_tel, max_img, d_evt_off, max_evt, d_out, s, d_n_img, d_n_evt, true);
+}
+
+int rta::check_bundle_images(rta_ctx* c, const int64_t* h_wave_off, const int32_t* h_img_tel, int64_t n_img,
+                             int64_t n_wave) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c))) return rc;
+    for (int64_t i = 0; i < n_img; ++i) {
+        const int tel = h_img_tel[i];
+        if (tel < 0 || tel >= c->n_tel) return fail(RTA_E_INVALID, "image %lld has telescope id %d", (long long)i, tel);
+        const HostCam& h = c->cams[c->tel_cam[tel]];
+        if (h_wave_off[i] < 0 || (h_wave_off[i] & 7))
+            return fail(RTA_E_ALIGN, "image %lld offset not a non-negative multiple of 8", (long long)i);
+        if (h_wave_off[i] + int64_t(h.P) * h.S > n_wave) return fail(RTA_E_INVALID, "image %lld ends past n_wave", (long long)i);
+    }
+    return RTA_OK;
+}
+
 int rta::surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2** tel_xy, int* n_tel, int* device) {
     int rc = check_ctx(c);
     if (rc || (rc = check_array(c))) return rc;

@@ -212,8 +212,46 @@ cudaError_t launch_lut_accumulate(const LutArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_lut_finalize(const double* acc, int64_t n_cells, int min_count, rta_lut_cell_t* cells, int grid,
                                 cudaStream_t s);
 cudaError_t launch_lut_prepare(const rta_lut_cell_t* cells, int64_t n_cells, void* lookup, int grid, cudaStream_t s);
+// Sky-map bin of a direction coordinate: floor((v + 2.56) * 50) in FP32 with
+// round-to-nearest and no contraction, -1 outside [0, RTA_SKY_N) (and for NaN).
+__device__ __forceinline__ int sky_bin(float v) {
+    const float u = __fmul_rn(__fadd_rn(v, 2.56f), 50.0f);
+    if (!(u >= 0.f) || !(u < float(RTA_SKY_N))) return -1;
+    return int(floorf(u));
+}
+
+// The event row of a geometric reconstruction: its direction, no energy or
+// gamma/hadron score (NaN), no direction when the intersection is invalid.
+__device__ __forceinline__ rta_event_t stereo_event_row(const rta_stereo_t& s) {
+    rta_event_t r = {};
+    r.log_energy = __int_as_float(0x7fc00000);
+    r.gammaness = __int_as_float(0x7fc00000);
+    r.dir_x = s.dir_x;
+    r.dir_y = s.dir_y;
+    r.n_used = s.n_valid;
+    r.flags = (s.flags & RTA_SF_INVALID) ? RTA_EF_NO_DIRECTION : 0u;
+    return r;
+}
+
 // context access for the surrogate (rta_api.cu)
 int surrogate_ctx_tables(rta_ctx* c, const int32_t** tel_cam, const float2** tel_xy, int* n_tel, int* device);
 // the context's device status word
 unsigned int* surrogate_ctx_status(rta_ctx* c);
+// The serving loop's passes over a batch gathered on the device (capacities and device
+// counts; the counts and tables were written before the image kernel started):
+// rta_server.cu calls them, rta_api.cu and rta_surrogate.cu define them.
+int serve_image_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
+                      const int32_t* d_img_tel, const int64_t* d_n_img, int64_t max_img, int window_mode, int start,
+                      int W, float t_hi, float t_lo, int core_nb, rta_hillas_t* d_out, cudaStream_t s);
+int serve_stereo(rta_ctx* c, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t max_img,
+                 const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_n_img, const int64_t* d_n_evt,
+                 rta_stereo_t* d_out, cudaStream_t s);
+int serve_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t max_img,
+                const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_n_img, const int64_t* d_n_evt,
+                float fallback_deg, rta_event_t* d_out, cudaStream_t s);
+// Host-side check of a bundle's image table against the registered cameras: every
+// offset non-negative, a multiple of 8 samples, the image inside n_wave samples; every
+// telescope registered. RTA_OK or RTA_E_INVALID / RTA_E_ALIGN with the message set.
+int check_bundle_images(rta_ctx* c, const int64_t* h_wave_off, const int32_t* h_img_tel, int64_t n_img,
+                        int64_t n_wave);
 }  // namespace rta

@@ -1,22 +1,31 @@
 // The serving engine: a stream of telescope bundles processed with continuous
 // batching under an HBM budget (the RTA processes the event builder's output
-// as it arrives, Sec. 4.2, within the 30 s alert latency of Sec. 2.1).
+// as it arrives, Sec. 4.2, within the 30 s alert latency of Sec. 2.1), with
+// the queue of bundles ready for reconstruction held in device memory.
 //
-// One scheduler thread owns the device side. Submitted bundles wait in a FIFO;
-// the head is admitted as soon as a slot (a CUDA stream) is free and the
-// budget arena has room for its buffers, so a bundle that arrives while others
-// are on the GPU starts as soon as memory and a slot free up, and the copies
-// and kernels of different bundles overlap on the device. Per bundle, on its
-// slot stream: host-to-device copies, the fused image kernel, then the learned
-// reconstruction (one kernel with no model workspace, so the learned stages of
-// concurrent bundles overlap as well) or the geometric intersection, the
-// sky-map fill on the map stream, and the copy of the event list back to the
-// caller's host buffer. Completion is detected by polling a CUDA event; the
-// bundle's arena range is freed only then. Timing events on the slot stream
-// split each bundle's time into queue wait, copies in, device work and copy out.
+// Admission (host): submitted bundles wait in arrival order until one of the
+// copy slots is free and the budget arena has room for their waveforms and
+// tables; the slot's stream then copies them in and, stream-ordered after the
+// copies, a one-thread kernel publishes the bundle's descriptor into a ring in
+// device memory (claim an index, write the descriptor, then its ready flag).
+//
+// Reconstruction (device-resident loop): passes on one compute stream, each
+// of which takes at run time, on the device, every bundle published and not yet
+// taken (in claim order, up to the batch capacity), gathers their image and
+// event tables into one batch (image offsets rebased to the arena, event
+// offsets to the batch), runs the fused image kernel and the learned (or the
+// geometric) reconstruction once over the whole batch, writes each bundle's
+// event rows straight into its slot's mapped host staging, and counts the
+// events into the sky-map slabs of their bundles' arrival seconds (slab
+// ownership is kept on the device). Bundles that arrive while a pass runs are
+// taken by the next one, so copies of new bundles overlap the reconstruction
+// of earlier ones and several bundles share one launch of each kernel. The
+// host only launches passes while published bundles are outstanding and
+// reads, after each pass, which tickets it took.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -90,25 +99,223 @@ struct Arena {
     }
 };
 
+
 struct Layout {   // byte offsets of one bundle's buffers inside its arena range
-    size_t wave, wave_off, img_tel, evt_off, hillas, events, stereo, total;
+    size_t wave, wave_off, img_tel, evt_off, total;
 };
 
-Layout layout_of(const rta_bundle_t& b, bool need_stereo) {
+Layout layout_of(const rta_bundle_t& b) {
     Layout L;
     size_t o = 0;
     L.wave = o; o = up(o + size_t(b.n_wave) * 2);
     L.wave_off = o; o = up(o + size_t(b.n_img) * 8);
     L.img_tel = o; o = up(o + size_t(b.n_img) * 4);
     L.evt_off = o; o = up(o + size_t(b.n_evt + 1) * 4);
-    L.hillas = o; o = up(o + size_t(b.n_img) * sizeof(rta_hillas_t));
-    L.events = o; o = up(o + size_t(b.n_evt) * sizeof(rta_event_t));
-    L.stereo = o; if (need_stereo) o = up(o + size_t(b.n_evt) * sizeof(rta_stereo_t));
     L.total = o;
     return L;
 }
 
-enum { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_FAILED = 3 };
+// ------------------------------------------------------------------ device-side queue
+constexpr int RING = 32;           // published descriptors; never more in flight than copy slots (<= 16)
+
+struct BundleDesc {                // a bundle whose waveforms and tables are in the arena
+    unsigned long long ticket;
+    int64_t wave_base;             // its waveforms, in samples from the arena base
+    const int64_t* wave_off;       // its tables in the arena
+    const int32_t* img_tel;
+    const int32_t* evt_off;
+    int64_t n_img, n_evt, arrival_ns;
+    rta_event_t* out;              // device view of its slot's mapped host staging
+};
+static_assert(sizeof(BundleDesc) % 8 == 0, "copied as 8-byte words");
+struct RingSlot {
+    BundleDesc d;
+    int ready;                     // 1 from publication until taken
+    int pad;
+};
+struct QueueCtl {
+    unsigned long long claimed;    // descriptors claimed by publishers
+    unsigned long long head;       // descriptors taken by passes
+};
+struct BatchEntry {                // a bundle in a pass: its descriptor and its first image and event
+    BundleDesc d;
+    int64_t img_base, evt_base;
+};
+struct BatchHead {                 // n_img and n_evt first: the kernels read them as device counts
+    int64_t n_img, n_evt;
+    int n;
+    int pad;
+    unsigned long long reset_sec, reset_min;   // sky-map slabs the pass's bundles claimed
+};
+struct SkyOwn {                    // the second (minute) each sky-map slab holds
+    int64_t sec[RTA_SKY_SLABS];
+    int64_t mnt[RTA_SKY_MIN_SLABS];
+};
+
+__host__ __device__ int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__host__ __device__ int mod_ring(int64_t a, int n) { return int(((a % n) + n) % n); }
+
+// Publish one bundle (one thread, on its slot's stream after its copies).
+__global__ void k_publish(RingSlot* ring, QueueCtl* ctl, BundleDesc d) {
+    const unsigned long long i = atomicAdd(&ctl->claimed, 1ull);
+    RingSlot* r = ring + (i % RING);
+    r->d = d;
+    __threadfence();
+    atomicExch(&r->ready, 1);
+}
+
+// Slab ownership for the bundles batch[0..n), in order: a bundle of a newer
+// second (minute) claims its slab, which is then cleared; one of an older one
+// leaves it alone and its events are not counted there.
+__device__ void claim_slabs(const BatchEntry* batch, int n, SkyOwn* own, BatchHead* head) {
+    unsigned long long rs = 0, rm = 0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t sec = floor_div(batch[k].d.arrival_ns, 1000000000ll), mnt = floor_div(sec, 60);
+        const int s = mod_ring(sec, RTA_SKY_SLABS), m = mod_ring(mnt, RTA_SKY_MIN_SLABS);
+        if (own->sec[s] < sec) {
+            own->sec[s] = sec;
+            rs |= 1ull << s;
+        }
+        if (own->mnt[m] < mnt) {
+            own->mnt[m] = mnt;
+            rm |= 1ull << m;
+        }
+    }
+    head->reset_sec = rs;
+    head->reset_min = rm;
+}
+
+// Take, in claim order, the published bundles that fit the batch capacity (the
+// first always does: every bundle fits the capacity); one thread.
+__global__ void k_take(RingSlot* ring, QueueCtl* ctl, int64_t cap_img, int64_t cap_evt, BatchEntry* batch,
+                       BatchHead* head, SkyOwn* own) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long h = ctl->head;
+    int n = 0;
+    int64_t ni = 0, ne = 0;
+    while (n < RING) {
+        RingSlot* r = ring + ((h + n) % RING);
+        if (atomicAdd(&r->ready, 0) == 0) break;      // claimed in order: the next one is not published yet
+        __threadfence();
+        BundleDesc d;
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&r->d);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&d);
+        for (int w = 0; w < int(sizeof(BundleDesc) / 8); ++w) dst[w] = __ldcg(src + w);   // past L1: another
+                                                                                       // kernel wrote it
+        if (n > 0 && (ni + d.n_img > cap_img || ne + d.n_evt > cap_evt)) break;
+        batch[n].d = d;
+        batch[n].img_base = ni;
+        batch[n].evt_base = ne;
+        ni += d.n_img;
+        ne += d.n_evt;
+        atomicExch(&r->ready, 0);
+        ++n;
+    }
+    ctl->head = h + n;
+    head->n = n;
+    head->n_img = ni;
+    head->n_evt = ne;
+    claim_slabs(batch, n, own, head);
+}
+
+// Slab ownership of one list of events with one arrival time (events added from
+// outside the loop); one thread.
+__global__ void k_claim_one(BatchEntry e, BatchEntry* batch, BatchHead* head, SkyOwn* own) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    batch[0] = e;
+    head->n = 1;
+    head->n_img = 0;
+    head->n_evt = e.d.n_evt;
+    claim_slabs(batch, 1, own, head);
+}
+
+// Clear the slabs the pass claimed: blockIdx.y = slab (the one-second ring, then
+// the one-minute ring), blockIdx.x = a 4096-word chunk of it.
+__global__ void k_slab_reset(const BatchHead* head, unsigned int* slabs, unsigned int* slabs_min) {
+    const int k = blockIdx.y;
+    const bool sec = k < RTA_SKY_SLABS;
+    const unsigned long long mask = sec ? head->reset_sec : head->reset_min;
+    const int s = sec ? k : k - RTA_SKY_SLABS;
+    if (!((mask >> s) & 1ull)) return;
+    unsigned int* p = (sec ? slabs : slabs_min) + size_t(s) * RTA_SKY_N * RTA_SKY_N + size_t(blockIdx.x) * 4096;
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) p[i] = 0u;
+}
+
+// The pass's bundle holding item i, items counted by img_base or evt_base.
+__device__ __forceinline__ int bundle_of(const BatchEntry* batch, int n, int64_t i, bool by_event) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_event ? batch[mid].evt_base : batch[mid].img_base) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The batch's tables: image offsets rebased to the arena, telescopes, event
+// offsets rebased to the batch (an offset outside its bundle becomes -1, which
+// the kernels report as malformed).
+__global__ void k_gather(const BatchEntry* batch, const BatchHead* head, int64_t* off_m, int32_t* tel_m,
+                         int32_t* evt_m) {
+    const int n = head->n;
+    const int64_t ni = head->n_img, ne = head->n_evt;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < ni; i += stride) {
+        const BatchEntry& b = batch[bundle_of(batch, n, i, false)];
+        const int64_t k = i - b.img_base;
+        off_m[i] = b.d.wave_base + b.d.wave_off[k];
+        tel_m[i] = b.d.img_tel[k];
+    }
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e <= ne; e += stride) {
+        if (e == ne) {
+            evt_m[e] = int32_t(ni);
+            continue;
+        }
+        const BatchEntry& b = batch[bundle_of(batch, n, e, true)];
+        const int32_t v = b.d.evt_off[e - b.evt_base];
+        evt_m[e] = (v < 0 || v > b.d.n_img) ? -1 : int32_t(b.img_base + v);
+    }
+}
+
+// Each bundle's event rows into its slot's mapped host staging (geometric mode:
+// formed from the stereo rows first, and kept in ev for the sky map too).
+__global__ void k_batch_out(rta_event_t* ev, const rta_stereo_t* st, const BatchEntry* batch, const BatchHead* head) {
+    const int n = head->n;
+    const int64_t ne = head->n_evt;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < ne; e += int64_t(gridDim.x) * blockDim.x) {
+        rta_event_t r;
+        if (st) {
+            r = rta::stereo_event_row(st[e]);
+            ev[e] = r;
+        } else {
+            r = ev[e];
+        }
+        const BatchEntry& b = batch[bundle_of(batch, n, e, true)];
+        b.d.out[e - b.evt_base] = r;
+    }
+}
+
+// Sky-map counts of the batch's events, each in the slabs of its bundle's
+// arrival second and minute when the slab still holds them.
+__global__ void k_sky_fill(const rta_event_t* ev, const BatchEntry* batch, const BatchHead* head, const SkyOwn* own,
+                           unsigned int* slabs, unsigned int* slabs_min) {
+    const int n = head->n;
+    const int64_t ne = head->n_evt;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < ne; e += int64_t(gridDim.x) * blockDim.x) {
+        const rta_event_t r = ev[e];
+        if (r.flags & RTA_EF_NO_DIRECTION) continue;
+        const int ix = rta::sky_bin(r.dir_x), iy = rta::sky_bin(r.dir_y);
+        if (ix < 0 || iy < 0) continue;
+        const BatchEntry& b = batch[bundle_of(batch, n, e, true)];
+        const int64_t sec = floor_div(b.d.arrival_ns, 1000000000ll), mnt = floor_div(sec, 60);
+        const int s = mod_ring(sec, RTA_SKY_SLABS), m = mod_ring(mnt, RTA_SKY_MIN_SLABS);
+        const size_t bin = size_t(iy) * RTA_SKY_N + ix;
+        if (own->sec[s] == sec) atomicAdd(slabs + size_t(s) * RTA_SKY_N * RTA_SKY_N + bin, 1u);
+        if (own->mnt[m] == mnt) atomicAdd(slabs_min + size_t(m) * RTA_SKY_N * RTA_SKY_N + bin, 1u);
+    }
+}
+
+enum { REQ_PENDING = 0, REQ_COPYING = 1, REQ_PUBLISHED = 2, REQ_DONE = 3, REQ_FAILED = 4 };
 
 struct Req {
     uint64_t ticket = 0;
@@ -122,16 +329,22 @@ struct Req {
     rta_bundle_times_t times{};
 };
 
-struct Slot {
+struct Slot {                      // a copy slot: its stream, staging and the bundle it carries
     cudaStream_t s = nullptr;
-    cudaEvent_t e_ev = nullptr, e_map = nullptr, e_done = nullptr;
-    cudaEvent_t t_in = nullptr, t_copied = nullptr, t_computed = nullptr, t_out = nullptr;   // timing
+    cudaEvent_t e_pub = nullptr;   // the bundle is published
+    cudaEvent_t t_in = nullptr, t_copied = nullptr;   // timing
     uint64_t ticket = 0;
     bool busy = false;
-    // pinned staging of the bundle's tables (in) and event list (out): copies from
-    // and to pageable memory would block the scheduler thread (and with it every
-    // other slot) until this slot's stream reached them
+    // pinned, mapped staging: the bundle's tables on the way in (copies from pageable
+    // memory would block the scheduler thread until the slot's stream reached them),
+    // its event rows, written by the device, on the way out
     char* h_stage = nullptr;
+    rta_event_t* d_stage = nullptr;   // device view of h_stage
+};
+
+struct Pass {                      // a reconstruction pass in flight on the compute stream
+    cudaEvent_t t_begin = nullptr, t_computed = nullptr, t_end = nullptr;
+    char* h_tab = nullptr;         // pinned: the pass's BatchHead and BatchEntry table, copied back
 };
 
 }  // namespace
@@ -142,15 +355,30 @@ struct rta_stream {
     int device = 0;
     int window_mode = 0, start = 0, W = 0, core_nb = 0;
     float t_hi = 0.f, t_lo = 0.f, fallback_deg = 0.5f;
-    int64_t max_img = 0, max_evt = 0;
+    int64_t max_img = 0, max_evt = 0, cap_img = 0, cap_evt = 0;
     Arena arena;
     std::vector<Slot> slots;
-    cudaStream_t s_map = nullptr;
-    unsigned int* d_slabs = nullptr;   // RTA_SKY_SLABS x 256 x 256
+    cudaStream_t s_cmp = nullptr;  // the reconstruction passes, the sky map and its searches
+    // device-side queue and the batch of the current pass
+    RingSlot* d_ring = nullptr;
+    QueueCtl* d_ctl = nullptr;
+    BatchEntry* d_batch = nullptr;
+    BatchHead* d_head = nullptr;
+    int64_t* d_off_m = nullptr;
+    int32_t* d_tel_m = nullptr;
+    int32_t* d_evt_m = nullptr;
+    rta_hillas_t* d_hil = nullptr;
+    rta_event_t* d_ev = nullptr;
+    rta_stereo_t* d_st = nullptr;
+    std::vector<Pass> pass_pool;
+    std::deque<int> passes;        // passes in flight, oldest first (indices into pass_pool)
+    bool need_pass = false;
+    // sky map
+    SkyOwn* d_own = nullptr;
+    SkyOwn own{};                  // host copy, read before a map or a search is formed
+    unsigned int* d_slabs = nullptr;       // RTA_SKY_SLABS x 256 x 256
     unsigned int* d_slabs_min = nullptr;   // RTA_SKY_MIN_SLABS x 256 x 256
     unsigned int* d_map = nullptr;
-    int64_t slab_sec[RTA_SKY_SLABS];
-    int64_t slab_min[RTA_SKY_MIN_SLABS];
     // transient-search work buffers (grown on demand)
     unsigned int *d_won = nullptr, *d_woff = nullptr, *d_pre_on = nullptr, *d_pre_off = nullptr, *d_nal = nullptr;
     int* d_hw = nullptr;
@@ -172,36 +400,22 @@ struct rta_stream {
 
 namespace {
 
-int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+constexpr size_t TAB_BYTES = sizeof(BatchHead) + sizeof(BatchEntry) * RING;
 
-// Count events into the one-second slab of arrival_ns and the one-minute slab of
-// its second, on the map stream, recycling a slab when a newer second (minute)
-// claims it; events of a second (minute) that has left its ring are not counted.
-// Caller holds S->mu.
-cudaError_t fill_slabs(rta_stream* S, const rta_event_t* d_ev, int64_t n_evt, int64_t arrival_ns) {
-    const int64_t sec = arrival_ns / 1000000000ll;
-    const int slab = int(((sec % RTA_SKY_SLABS) + RTA_SKY_SLABS) % RTA_SKY_SLABS);
-    const int64_t mnt = floor_div(sec, 60);
-    const int mslab = int(((mnt % RTA_SKY_MIN_SLABS) + RTA_SKY_MIN_SLABS) % RTA_SKY_MIN_SLABS);
-    const size_t map_bytes = sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N;
-    unsigned int* p_sec = S->d_slabs + size_t(slab) * RTA_SKY_N * RTA_SKY_N;
-    unsigned int* p_min = S->d_slabs_min + size_t(mslab) * RTA_SKY_N * RTA_SKY_N;
-    cudaError_t e = cudaSuccess;
-    if (S->slab_sec[slab] < sec) {
-        e = cudaMemsetAsync(p_sec, 0, map_bytes, S->s_map);
-        S->slab_sec[slab] = sec;
-    }
-    if (e == cudaSuccess && S->slab_min[mslab] < mnt) {
-        e = cudaMemsetAsync(p_min, 0, map_bytes, S->s_map);
-        S->slab_min[mslab] = mnt;
-    }
-    if (e != cudaSuccess || n_evt <= 0) return e;
-    unsigned int* a = S->slab_sec[slab] == sec ? p_sec : nullptr;
-    unsigned int* b = S->slab_min[mslab] == mnt ? p_min : nullptr;
-    if (!a && !b) return cudaSuccess;
-    return rta::launch_skymap_fill(d_ev, n_evt, a, b, S->s_map);
+// The slabs' owners on the host, after every pass enqueued so far (caller holds S->mu).
+cudaError_t read_own(rta_stream* S) {
+    cudaError_t e = cudaMemcpyAsync(&S->own, S->d_own, sizeof(SkyOwn), cudaMemcpyDeviceToHost, S->s_cmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_cmp);
+    return e;
 }
 
+#define D_TRY(call)                                                                                 \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return vfail(RTA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+// Admit one bundle: copies in on the slot's stream, then its publication.
 int dispatch(rta_stream* S, Req& r, Slot& sl) {
     const rta_bundle_t& b = r.b;
     char* base = S->arena.base + r.off;
@@ -209,19 +423,10 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     int64_t* d_off = reinterpret_cast<int64_t*>(base + r.L.wave_off);
     int32_t* d_tel = reinterpret_cast<int32_t*>(base + r.L.img_tel);
     int32_t* d_evt = reinterpret_cast<int32_t*>(base + r.L.evt_off);
-    rta_hillas_t* d_h = reinterpret_cast<rta_hillas_t*>(base + r.L.hillas);
-    rta_event_t* d_ev = reinterpret_cast<rta_event_t*>(base + r.L.events);
-    rta_stereo_t* d_st = reinterpret_cast<rta_stereo_t*>(base + r.L.stereo);
     cudaStream_t s = sl.s;
     r.times.admit_ns = now_ns();
     r.times.slot = int(&sl - &S->slots[0]);
-#define D_TRY(call)                                                                                 \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess) return vfail(RTA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
-    } while (0)
-    // the tables through the slot's pinned staging (the slot's previous bundle, the
-    // last user of it, has completed), in the order of the device layout
+    // the tables through the slot's pinned staging (free: its previous bundle is done)
     const size_t tb_off = size_t(b.n_img) * 8, tb_tel = size_t(b.n_img) * 4, tb_evt = size_t(b.n_evt + 1) * 4;
     std::memcpy(sl.h_stage, b.h_wave_off, tb_off);
     std::memcpy(sl.h_stage + tb_off, b.h_img_tel, tb_tel);
@@ -232,29 +437,107 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     D_TRY(cudaMemcpyAsync(d_tel, sl.h_stage + tb_off, tb_tel, cudaMemcpyHostToDevice, s));
     D_TRY(cudaMemcpyAsync(d_evt, sl.h_stage + tb_off + tb_tel, tb_evt, cudaMemcpyHostToDevice, s));
     D_TRY(cudaEventRecord(sl.t_copied, s));
-    int rc = rta_image_chain(S->ctx, d_wave, b.n_wave, d_off, d_tel, b.n_img, S->window_mode, S->start, S->W,
-                             S->t_hi, S->t_lo, S->core_nb, d_h, s);
-    if (rc) return rc;
-    if (S->model) {
-        rc = rta_surrogate_infer(S->model, d_h, d_tel, b.n_img, d_evt, b.n_evt, S->fallback_deg, d_ev, s);
-        if (rc) return rc;
-    } else {
-        rc = rta_stereo(S->ctx, d_h, d_tel, b.n_img, d_evt, b.n_evt, d_st, s);
-        if (rc) return rc;
-        D_TRY(rta::launch_stereo_to_events(d_st, b.n_evt, d_ev, s));
-    }
-    D_TRY(cudaEventRecord(sl.t_computed, s));
-    // sky map: the one-second and one-minute slabs of the bundle's arrival
-    D_TRY(cudaEventRecord(sl.e_ev, s));
-    D_TRY(cudaStreamWaitEvent(S->s_map, sl.e_ev, 0));
-    D_TRY(fill_slabs(S, d_ev, b.n_evt, b.arrival_ns));
-    D_TRY(cudaEventRecord(sl.e_map, S->s_map));
-    D_TRY(cudaStreamWaitEvent(s, sl.e_map, 0));
-    D_TRY(cudaMemcpyAsync(sl.h_stage, d_ev, size_t(b.n_evt) * sizeof(rta_event_t), cudaMemcpyDeviceToHost, s));
-    D_TRY(cudaEventRecord(sl.t_out, s));
-    D_TRY(cudaEventRecord(sl.e_done, s));
-#undef D_TRY
+    BundleDesc d = {};
+    d.ticket = r.ticket;
+    d.wave_base = int64_t((r.off + r.L.wave) / 2);
+    d.wave_off = d_off;
+    d.img_tel = d_tel;
+    d.evt_off = d_evt;
+    d.n_img = b.n_img;
+    d.n_evt = b.n_evt;
+    d.arrival_ns = b.arrival_ns;
+    d.out = sl.d_stage;
+    k_publish<<<1, 1, 0, s>>>(S->d_ring, S->d_ctl, d);
+    D_TRY(cudaGetLastError());
+    D_TRY(cudaEventRecord(sl.e_pub, s));
     return RTA_OK;
+}
+
+// One reconstruction pass on the compute stream over whatever is published when it runs.
+int launch_pass(rta_stream* S, Pass& p) {
+    cudaStream_t s = S->s_cmp;
+    D_TRY(cudaEventRecord(p.t_begin, s));
+    k_take<<<1, 32, 0, s>>>(S->d_ring, S->d_ctl, S->cap_img, S->cap_evt, S->d_batch, S->d_head, S->d_own);
+    D_TRY(cudaGetLastError());
+    k_slab_reset<<<dim3(RTA_SKY_N * RTA_SKY_N / 4096, RTA_SKY_SLABS + RTA_SKY_MIN_SLABS), 256, 0, s>>>(
+        S->d_head, S->d_slabs, S->d_slabs_min);
+    D_TRY(cudaGetLastError());
+    const int g_img = int(std::min<int64_t>((S->cap_img + 255) / 256, 2048));
+    k_gather<<<g_img, 256, 0, s>>>(S->d_batch, S->d_head, S->d_off_m, S->d_tel_m, S->d_evt_m);
+    D_TRY(cudaGetLastError());
+    const int64_t* d_ni = reinterpret_cast<const int64_t*>(reinterpret_cast<const char*>(S->d_head) +
+                                                          offsetof(BatchHead, n_img));
+    const int64_t* d_ne = reinterpret_cast<const int64_t*>(reinterpret_cast<const char*>(S->d_head) +
+                                                          offsetof(BatchHead, n_evt));
+    int rc = rta::serve_image_chain(S->ctx, reinterpret_cast<const uint16_t*>(S->arena.base),
+                                    int64_t(S->arena.size / 2), S->d_off_m, S->d_tel_m, d_ni, S->cap_img,
+                                    S->window_mode, S->start, S->W, S->t_hi, S->t_lo, S->core_nb, S->d_hil, s);
+    if (rc) return rc;
+    if (S->model)
+        rc = rta::serve_infer(S->model, S->d_hil, S->d_tel_m, S->cap_img, S->d_evt_m, S->cap_evt, d_ni, d_ne,
+                              S->fallback_deg, S->d_ev, s);
+    else
+        rc = rta::serve_stereo(S->ctx, S->d_hil, S->d_tel_m, S->cap_img, S->d_evt_m, S->cap_evt, d_ni, d_ne, S->d_st, s);
+    if (rc) return rc;
+    D_TRY(cudaEventRecord(p.t_computed, s));
+    const int g_evt = int(std::min<int64_t>((S->cap_evt + 255) / 256, 2048));
+    k_batch_out<<<g_evt, 256, 0, s>>>(S->d_ev, S->model ? nullptr : S->d_st, S->d_batch, S->d_head);
+    D_TRY(cudaGetLastError());
+    k_sky_fill<<<g_evt, 256, 0, s>>>(S->d_ev, S->d_batch, S->d_head, S->d_own, S->d_slabs, S->d_slabs_min);
+    D_TRY(cudaGetLastError());
+    D_TRY(cudaMemcpyAsync(p.h_tab, S->d_head, sizeof(BatchHead), cudaMemcpyDeviceToHost, s));
+    D_TRY(cudaMemcpyAsync(p.h_tab + sizeof(BatchHead), S->d_batch, sizeof(BatchEntry) * RING, cudaMemcpyDeviceToHost, s));
+    D_TRY(cudaEventRecord(p.t_end, s));
+    return RTA_OK;
+}
+
+// A pass has completed: every bundle it took is done (caller holds S->mu).
+void finish_pass(rta_stream* S, Pass& p) {
+    const BatchHead* hd = reinterpret_cast<const BatchHead*>(p.h_tab);
+    const BatchEntry* tab = reinterpret_cast<const BatchEntry*>(p.h_tab + sizeof(BatchHead));
+    float dev_ms = 0.f, out_ms = 0.f;
+    cudaEventElapsedTime(&dev_ms, p.t_begin, p.t_computed);
+    cudaEventElapsedTime(&out_ms, p.t_computed, p.t_end);
+    const int64_t t_done = now_ns();
+    for (int k = 0; k < hd->n && k < RING; ++k) {
+        auto it = S->reqs.find(tab[k].d.ticket);
+        if (it == S->reqs.end()) continue;
+        Req& r = it->second;
+        Slot& sl = S->slots[r.slot];
+        // the event rows, written into the slot's staging by the pass
+        std::memcpy(r.b.h_events, sl.h_stage, size_t(r.b.n_evt) * sizeof(rta_event_t));
+        cudaEventElapsedTime(&r.times.h2d_ms, sl.t_in, sl.t_copied);
+        float wait_ms = 0.f;
+        cudaEventElapsedTime(&wait_ms, sl.t_copied, p.t_begin);
+        r.times.ready_wait_ms = std::max(0.f, wait_ms);
+        r.times.compute_ms = dev_ms;
+        r.times.d2h_ms = out_ms;
+        r.times.batch_bundles = hd->n;
+        r.done_ns = t_done;
+        r.times.done_ns = t_done;
+        r.state = REQ_DONE;
+        S->arena.release(r.off, r.L.total);
+        sl.busy = false;
+        --S->running;
+        ++S->n_done;
+        S->bytes_done += r.b.n_wave * 2;
+    }
+}
+
+// Every admitted bundle fails (a pass could not be enqueued; caller holds S->mu).
+void fail_admitted(rta_stream* S, int rc) {
+    cudaStreamSynchronize(S->s_cmp);
+    for (auto& sl : S->slots) {
+        if (!sl.busy) continue;
+        cudaStreamSynchronize(sl.s);
+        Req& r = S->reqs[sl.ticket];
+        S->arena.release(r.off, r.L.total);
+        sl.busy = false;
+        --S->running;
+        r.state = REQ_FAILED;
+        r.rc = rc;
+        r.done_ns = now_ns();
+    }
 }
 
 void worker_loop(rta_stream* S) {
@@ -262,27 +545,35 @@ void worker_loop(rta_stream* S) {
     std::unique_lock<std::mutex> lock(S->mu);
     while (!S->stop) {
         bool progress = false;
-        // completions
+        // bundles whose publication has run: a pass must take them
         for (auto& sl : S->slots) {
             if (!sl.busy) continue;
-            const cudaError_t q = cudaEventQuery(sl.e_done);
-            if (q == cudaErrorNotReady) continue;
             Req& r = S->reqs[sl.ticket];
-            if (q == cudaSuccess) {     // the event list, from the slot's staging; the bundle's times
-                std::memcpy(r.b.h_events, sl.h_stage, size_t(r.b.n_evt) * sizeof(rta_event_t));
-                cudaEventElapsedTime(&r.times.h2d_ms, sl.t_in, sl.t_copied);
-                cudaEventElapsedTime(&r.times.compute_ms, sl.t_copied, sl.t_computed);
-                cudaEventElapsedTime(&r.times.d2h_ms, sl.t_computed, sl.t_out);
+            if (r.state != REQ_COPYING) continue;
+            const cudaError_t q = cudaEventQuery(sl.e_pub);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                fail_admitted(S, RTA_E_CUDA);
+                progress = true;
+                break;
             }
-            r.done_ns = now_ns();
-            r.times.done_ns = r.done_ns;
-            r.state = q == cudaSuccess ? REQ_DONE : REQ_FAILED;
-            if (q != cudaSuccess) r.rc = RTA_E_CUDA;
-            S->arena.release(r.off, r.L.total);
-            sl.busy = false;
-            --S->running;
-            ++S->n_done;
-            S->bytes_done += r.b.n_wave * 2;
+            r.state = REQ_PUBLISHED;
+            S->need_pass = true;
+        }
+        // completed passes, oldest first
+        while (!S->passes.empty()) {
+            Pass& p = S->pass_pool[S->passes.front()];
+            const cudaError_t q = cudaEventQuery(p.t_end);
+            if (q == cudaErrorNotReady) break;
+            S->passes.pop_front();
+            if (q != cudaSuccess) {
+                fail_admitted(S, RTA_E_CUDA);
+            } else {
+                finish_pass(S, p);
+            }
+            // bundles published but not taken (batch capacity) need another pass
+            for (auto& sl : S->slots)
+                if (sl.busy && S->reqs[sl.ticket].state == REQ_PUBLISHED) S->need_pass = true;
             progress = true;
         }
         // admissions, in arrival order
@@ -295,20 +586,33 @@ void worker_loop(rta_stream* S) {
             S->pending.pop_front();
             r.off = off;
             r.slot = int(fs - S->slots.begin());
-            r.state = REQ_RUNNING;
+            r.state = REQ_COPYING;
             fs->busy = true;
             fs->ticket = r.ticket;
             ++S->running;
             const int rc = dispatch(S, r, *fs);
             if (rc) {   // nothing more is enqueued for it; let what was enqueued finish
                 cudaStreamSynchronize(fs->s);
-                cudaStreamSynchronize(S->s_map);
                 S->arena.release(r.off, r.L.total);
                 fs->busy = false;
                 --S->running;
                 r.state = REQ_FAILED;
                 r.rc = rc;
                 r.done_ns = now_ns();
+            }
+            progress = true;
+        }
+        // a pass over what is published, at most two queued on the compute stream
+        if (S->need_pass && S->passes.size() < 2) {
+            int idx = -1;
+            for (int k = 0; k < int(S->pass_pool.size()); ++k)
+                if (std::find(S->passes.begin(), S->passes.end(), k) == S->passes.end()) idx = k;
+            const int rc = launch_pass(S, S->pass_pool[idx]);
+            if (rc) {
+                fail_admitted(S, rc);
+            } else {
+                S->passes.push_back(idx);
+                S->need_pass = false;
             }
             progress = true;
         }
@@ -327,21 +631,24 @@ void release_all(rta_stream* S) {
     for (auto& sl : S->slots) {
         if (sl.s) cudaStreamDestroy(sl.s);
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
-        cudaEvent_t ev[] = {sl.e_ev, sl.e_map, sl.e_done, sl.t_in, sl.t_copied, sl.t_computed, sl.t_out};
+        cudaEvent_t ev[] = {sl.e_pub, sl.t_in, sl.t_copied};
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
     }
-    if (S->s_map) cudaStreamDestroy(S->s_map);
-    cudaFree(S->arena.base);
-    cudaFree(S->d_slabs);
-    cudaFree(S->d_slabs_min);
-    {
-        void* w[] = {S->d_won, S->d_woff, S->d_pre_on, S->d_pre_off, S->d_nal, S->d_hw, S->d_alerts, S->d_sig,
-                     S->d_son, S->d_soff};
-        for (void* q : w) cudaFree(q);
+    for (auto& p : S->pass_pool) {
+        cudaEvent_t ev[] = {p.t_begin, p.t_computed, p.t_end};
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        if (p.h_tab) cudaFreeHost(p.h_tab);
     }
-    cudaFree(S->d_map);
+    if (S->s_cmp) cudaStreamDestroy(S->s_cmp);
+    void* d[] = {S->arena.base, S->d_ring, S->d_ctl, S->d_batch, S->d_head, S->d_off_m, S->d_tel_m, S->d_evt_m,
+                 S->d_hil, S->d_ev, S->d_st, S->d_own, S->d_slabs, S->d_slabs_min, S->d_map, S->d_won, S->d_woff,
+                 S->d_pre_on, S->d_pre_off, S->d_nal, S->d_hw, S->d_alerts, S->d_sig, S->d_son, S->d_soff};
+    for (void* q : d) cudaFree(q);
 }
+
+#undef D_TRY
 
 }  // namespace
 
@@ -352,7 +659,7 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
                       int core_needs_neighbour, float fallback_deg, rta_stream** out) {
     if (!ctx || !out) return vfail(RTA_E_INVALID, "NULL argument");
     if (max_inflight < 1 || max_inflight > 16) return vfail(RTA_E_INVALID, "max_inflight %d outside 1..16", max_inflight);
-    if (max_img < 1 || max_evt < 1 || max_img > (int64_t(1) << 30) || max_evt > (int64_t(1) << 30))
+    if (max_img < 1 || max_evt < 1 || max_img > (int64_t(1) << 29) || max_evt > (int64_t(1) << 29))
         return vfail(RTA_E_INVALID, "bad bundle capacity");
     if (hbm_budget_bytes < (size_t(1) << 20)) return vfail(RTA_E_INVALID, "HBM budget below 1 MiB");
     if (model && !(fallback_deg > 0.f)) return vfail(RTA_E_INVALID, "fallback bound must be > 0");
@@ -373,25 +680,44 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
     S->fallback_deg = fallback_deg;
     S->max_img = max_img;
     S->max_evt = max_evt;
-    for (auto& x : S->slab_sec) x = -1;
-    for (auto& x : S->slab_min) x = INT64_MIN;
+    // a pass takes up to two of the largest bundles (and any number of smaller ones up to that)
+    S->cap_img = 2 * max_img;
+    S->cap_evt = 2 * max_evt;
+    for (auto& x : S->own.sec) x = -1;
+    for (auto& x : S->own.mnt) x = INT64_MIN;
+    const size_t slab_bytes = sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N;
     bool ok = cudaMalloc(&S->arena.base, hbm_budget_bytes) == cudaSuccess &&
-              cudaMalloc(&S->d_slabs, sizeof(unsigned int) * RTA_SKY_SLABS * RTA_SKY_N * RTA_SKY_N) == cudaSuccess &&
-              cudaMalloc(&S->d_slabs_min, sizeof(unsigned int) * RTA_SKY_MIN_SLABS * RTA_SKY_N * RTA_SKY_N) ==
-                  cudaSuccess &&
-              cudaMalloc(&S->d_map, sizeof(unsigned int) * RTA_SKY_N * RTA_SKY_N) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&S->s_map, cudaStreamNonBlocking) == cudaSuccess;
+              cudaMalloc(&S->d_slabs, slab_bytes * RTA_SKY_SLABS) == cudaSuccess &&
+              cudaMalloc(&S->d_slabs_min, slab_bytes * RTA_SKY_MIN_SLABS) == cudaSuccess &&
+              cudaMalloc(&S->d_map, slab_bytes) == cudaSuccess &&
+              cudaMalloc(&S->d_ring, sizeof(RingSlot) * RING) == cudaSuccess &&
+              cudaMalloc(&S->d_ctl, sizeof(QueueCtl)) == cudaSuccess &&
+              cudaMalloc(&S->d_batch, sizeof(BatchEntry) * RING) == cudaSuccess &&
+              cudaMalloc(&S->d_head, sizeof(BatchHead)) == cudaSuccess &&
+              cudaMalloc(&S->d_own, sizeof(SkyOwn)) == cudaSuccess &&
+              cudaMalloc(&S->d_off_m, sizeof(int64_t) * S->cap_img) == cudaSuccess &&
+              cudaMalloc(&S->d_tel_m, sizeof(int32_t) * S->cap_img) == cudaSuccess &&
+              cudaMalloc(&S->d_evt_m, sizeof(int32_t) * (S->cap_evt + 1)) == cudaSuccess &&
+              cudaMalloc(&S->d_hil, sizeof(rta_hillas_t) * S->cap_img) == cudaSuccess &&
+              cudaMalloc(&S->d_ev, sizeof(rta_event_t) * S->cap_evt) == cudaSuccess &&
+              (model || cudaMalloc(&S->d_st, sizeof(rta_stereo_t) * S->cap_evt) == cudaSuccess) &&
+              cudaStreamCreateWithFlags(&S->s_cmp, cudaStreamNonBlocking) == cudaSuccess;
     S->slots.resize(max_inflight);
     // staging per slot: the tables in, or the event list out, of the largest bundle
     const size_t stage_bytes = std::max(size_t(max_img) * 12 + size_t(max_evt + 1) * 4,
                                         size_t(max_evt) * sizeof(rta_event_t));
     for (auto& sl : S->slots) {
         ok = ok && cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess;
-        ok = ok && cudaHostAlloc(reinterpret_cast<void**>(&sl.h_stage), stage_bytes, cudaHostAllocDefault) == cudaSuccess;
-        cudaEvent_t* ev[] = {&sl.e_ev, &sl.e_map, &sl.e_done};
-        for (auto e : ev) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-        cudaEvent_t* tv[] = {&sl.t_in, &sl.t_copied, &sl.t_computed, &sl.t_out};
-        for (auto e : tv) ok = ok && cudaEventCreate(e) == cudaSuccess;
+        ok = ok && cudaHostAlloc(reinterpret_cast<void**>(&sl.h_stage), stage_bytes, cudaHostAllocMapped) == cudaSuccess;
+        ok = ok && cudaHostGetDevicePointer(reinterpret_cast<void**>(&sl.d_stage), sl.h_stage, 0) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&sl.e_pub, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreate(&sl.t_in) == cudaSuccess && cudaEventCreate(&sl.t_copied) == cudaSuccess;
+    }
+    S->pass_pool.resize(2);
+    for (auto& p : S->pass_pool) {
+        ok = ok && cudaEventCreate(&p.t_begin) == cudaSuccess && cudaEventCreate(&p.t_computed) == cudaSuccess &&
+             cudaEventCreate(&p.t_end) == cudaSuccess;
+        ok = ok && cudaHostAlloc(reinterpret_cast<void**>(&p.h_tab), TAB_BYTES, cudaHostAllocDefault) == cudaSuccess;
     }
     if (!ok) {
         release_all(S);
@@ -400,9 +726,18 @@ int rta_stream_create(rta_ctx* ctx, rta_model* model, size_t hbm_budget_bytes, i
     }
     S->arena.size = hbm_budget_bytes;
     S->arena.reset();
-    cudaMemset(S->d_slabs, 0, sizeof(unsigned int) * RTA_SKY_SLABS * RTA_SKY_N * RTA_SKY_N);
-    cudaMemset(S->d_slabs_min, 0, sizeof(unsigned int) * RTA_SKY_MIN_SLABS * RTA_SKY_N * RTA_SKY_N);
-    cudaDeviceSynchronize();
+    bool zok = cudaMemset(S->d_slabs, 0, slab_bytes * RTA_SKY_SLABS) == cudaSuccess &&
+               cudaMemset(S->d_slabs_min, 0, slab_bytes * RTA_SKY_MIN_SLABS) == cudaSuccess &&
+               cudaMemset(S->d_ring, 0, sizeof(RingSlot) * RING) == cudaSuccess &&
+               cudaMemset(S->d_ctl, 0, sizeof(QueueCtl)) == cudaSuccess &&
+               cudaMemset(S->d_head, 0, sizeof(BatchHead)) == cudaSuccess &&
+               cudaMemcpy(S->d_own, &S->own, sizeof(SkyOwn), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaDeviceSynchronize() == cudaSuccess;
+    if (!zok) {
+        release_all(S);
+        delete S;
+        return vfail(RTA_E_CUDA, "stream set-up failed");
+    }
     S->worker = std::thread(worker_loop, S);
     *out = S;
     return RTA_OK;
@@ -416,11 +751,15 @@ int rta_stream_submit(rta_stream* S, const rta_bundle_t* b, uint64_t* ticket) {
         return vfail(RTA_E_INVALID, "NULL host buffer");
     if (b->h_evt_off[0] != 0 || b->h_evt_off[b->n_evt] != b->n_img)
         return vfail(RTA_E_INVALID, "evt_off must run from 0 to n_img");
+    // every image inside the bundle's own waveforms: in the batch the image kernel
+    // addresses the whole arena
+    int rc = rta::check_bundle_images(S->ctx, b->h_wave_off, b->h_img_tel, b->n_img, b->n_wave);
+    if (rc) return rc;
     Req r;
     r.b = *b;
     r.times.arrival_ns = b->arrival_ns;
     r.times.submit_ns = now_ns();
-    r.L = layout_of(*b, S->model == nullptr);
+    r.L = layout_of(*b);
     if (r.L.total > S->arena.size) return vfail(RTA_E_NOMEM, "bundle needs %zu bytes, budget is %zu", r.L.total, S->arena.size);
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->pending.size() >= 4096) return vfail(RTA_E_BUSY, "submission queue full");
@@ -442,7 +781,7 @@ int rta_stream_poll_times(rta_stream* S, uint64_t ticket, int64_t* done_ns, rta_
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return vfail(RTA_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
     const Req& r = it->second;
-    if (r.state == REQ_PENDING || r.state == REQ_RUNNING) return RTA_E_BUSY;
+    if (r.state != REQ_DONE && r.state != REQ_FAILED) return RTA_E_BUSY;
     if (done_ns) *done_ns = r.done_ns;
     if (times) *times = r.times;
     const int rc = r.state == REQ_DONE ? RTA_OK : r.rc;
@@ -463,15 +802,16 @@ int rta_skymap_read(rta_stream* S, int64_t now, uint32_t* h_map) {
     if (!S || !h_map) return vfail(RTA_E_INVALID, "NULL argument");
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lock(S->mu);
+    cudaError_t e = read_own(S);
     const int64_t sec = now / 1000000000ll;
     unsigned long long use = 0;
     for (int k = 0; k < RTA_SKY_SLABS; ++k)
-        if (S->slab_sec[k] > sec - RTA_SKY_SLABS && S->slab_sec[k] <= sec) use |= 1ull << k;
-    cudaError_t e = rta::launch_skymap_sum(S->d_slabs, use, S->d_map, S->s_map);
+        if (S->own.sec[k] > sec - RTA_SKY_SLABS && S->own.sec[k] <= sec) use |= 1ull << k;
+    if (e == cudaSuccess) e = rta::launch_skymap_sum(S->d_slabs, use, S->d_map, S->s_cmp);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h_map, S->d_map, sizeof(uint32_t) * RTA_SKY_N * RTA_SKY_N, cudaMemcpyDeviceToHost, S->s_map);
+        e = cudaMemcpyAsync(h_map, S->d_map, sizeof(uint32_t) * RTA_SKY_N * RTA_SKY_N, cudaMemcpyDeviceToHost, S->s_cmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_cmp);
     lock.unlock();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_map);
     if (e != cudaSuccess) return vfail(RTA_E_CUDA, "sky map read: %s", cudaGetErrorString(e));
     return RTA_OK;
 }
@@ -484,10 +824,21 @@ int rta_stream_add_events(rta_stream* S, const rta_event_t* d_events, int64_t n_
     cudaEvent_t ev = nullptr;
     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(ev, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_map, ev, 0);
-    if (e == cudaSuccess) e = fill_slabs(S, d_events, n_evt, arrival_ns);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_cmp, ev, 0);
+    if (e == cudaSuccess) {
+        BatchEntry be = {};
+        be.d.n_evt = n_evt;
+        be.d.arrival_ns = arrival_ns;
+        k_claim_one<<<1, 1, 0, S->s_cmp>>>(be, S->d_batch, S->d_head, S->d_own);
+        k_slab_reset<<<dim3(RTA_SKY_N * RTA_SKY_N / 4096, RTA_SKY_SLABS + RTA_SKY_MIN_SLABS), 256, 0, S->s_cmp>>>(
+            S->d_head, S->d_slabs, S->d_slabs_min);
+        if (n_evt > 0)
+            k_sky_fill<<<int(std::min<int64_t>((n_evt + 255) / 256, 2048)), 256, 0, S->s_cmp>>>(
+                d_events, S->d_batch, S->d_head, S->d_own, S->d_slabs, S->d_slabs_min);
+        e = cudaGetLastError();
+    }
     // the caller's stream must not reuse d_events before the fill has read it
-    if (e == cudaSuccess) e = cudaEventRecord(ev, S->s_map);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, S->s_cmp);
     if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, ev, 0);
     if (ev) cudaEventDestroy(ev);
     if (e != cudaSuccess) return vfail(RTA_E_CUDA, "sky map fill: %s", cudaGetErrorString(e));
@@ -541,7 +892,7 @@ void window_masks(const rta_stream* S, int64_t now_ns, const rta_window_t& w, co
         *slabs = S->d_slabs;
         *n_slabs = RTA_SKY_SLABS;
         for (int k = 0; k < RTA_SKY_SLABS; ++k) {
-            const int64_t t = S->slab_sec[k];
+            const int64_t t = S->own.sec[k];
             if (t > now_s - w.on_s && t <= now_s) *use_on |= 1ull << k;
             if (t > now_s - w.on_s - w.off_s && t <= now_s - w.on_s) *use_off |= 1ull << k;
         }
@@ -550,7 +901,7 @@ void window_masks(const rta_stream* S, int64_t now_ns, const rta_window_t& w, co
         *slabs = S->d_slabs_min;
         *n_slabs = RTA_SKY_MIN_SLABS;
         for (int k = 0; k < RTA_SKY_MIN_SLABS; ++k) {
-            const int64_t t = S->slab_min[k];
+            const int64_t t = S->own.mnt[k];
             if (t > now_m - on && t <= now_m) *use_on |= 1ull << k;
             if (t > now_m - on - off && t <= now_m - on) *use_off |= 1ull << k;
         }
@@ -603,7 +954,7 @@ cudaError_t enqueue_window(rta_stream* S, int64_t now_ns, const rta_window_t& w,
     t.sig = maps ? S->d_sig : nullptr;
     t.d_on = maps ? S->d_son : nullptr;
     t.d_off = maps ? S->d_soff : nullptr;
-    return rta::launch_transient(t, S->s_map);
+    return rta::launch_transient(t, S->s_cmp);
 }
 
 }  // namespace
@@ -627,14 +978,15 @@ int rta_transient_search(rta_stream* S, int64_t now_ns, const rta_window_t* wind
     const std::vector<int> hw = disk_half_widths(radius_bins);
     unsigned int n_dev = 0;
     std::unique_lock<std::mutex> lock(S->mu);
-    cudaError_t e = ensure_work(S, size_t(n_windows) * RTA_SKY_N * RTA_SKY_N, false);
+    cudaError_t e = read_own(S);
+    if (e == cudaSuccess) e = ensure_work(S, size_t(n_windows) * RTA_SKY_N * RTA_SKY_N, false);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->d_hw, hw.data(), sizeof(int) * hw.size(), cudaMemcpyHostToDevice, S->s_map);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_nal, 0, sizeof(unsigned int), S->s_map);
+        e = cudaMemcpyAsync(S->d_hw, hw.data(), sizeof(int) * hw.size(), cudaMemcpyHostToDevice, S->s_cmp);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_nal, 0, sizeof(unsigned int), S->s_cmp);
     for (int i = 0; i < n_windows && e == cudaSuccess; ++i)
         e = enqueue_window(S, now_ns, windows[i], i, radius_bins, s_min, true, false);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_dev, S->d_nal, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->s_map);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_map);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_dev, S->d_nal, sizeof(unsigned int), cudaMemcpyDeviceToHost, S->s_cmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_cmp);
     std::vector<rta_alert_t> all(std::min<size_t>(n_dev, S->alerts_cap));
     if (e == cudaSuccess && !all.empty())
         e = cudaMemcpy(all.data(), S->d_alerts, sizeof(rta_alert_t) * all.size(), cudaMemcpyDeviceToHost);
@@ -662,14 +1014,15 @@ int rta_significance_map(rta_stream* S, int64_t now_ns, rta_window_t window, int
     const std::vector<int> hw = disk_half_widths(radius_bins);
     const size_t nb = size_t(RTA_SKY_N) * RTA_SKY_N;
     std::unique_lock<std::mutex> lock(S->mu);
-    cudaError_t e = ensure_work(S, 0, true);
+    cudaError_t e = read_own(S);
+    if (e == cudaSuccess) e = ensure_work(S, 0, true);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->d_hw, hw.data(), sizeof(int) * hw.size(), cudaMemcpyHostToDevice, S->s_map);
+        e = cudaMemcpyAsync(S->d_hw, hw.data(), sizeof(int) * hw.size(), cudaMemcpyHostToDevice, S->s_cmp);
     if (e == cudaSuccess) e = enqueue_window(S, now_ns, window, 0, radius_bins, 0.0, false, true);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_sig, S->d_sig, nb * 8, cudaMemcpyDeviceToHost, S->s_map);
-    if (e == cudaSuccess && h_on) e = cudaMemcpyAsync(h_on, S->d_son, nb * 8, cudaMemcpyDeviceToHost, S->s_map);
-    if (e == cudaSuccess && h_off) e = cudaMemcpyAsync(h_off, S->d_soff, nb * 8, cudaMemcpyDeviceToHost, S->s_map);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_map);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_sig, S->d_sig, nb * 8, cudaMemcpyDeviceToHost, S->s_cmp);
+    if (e == cudaSuccess && h_on) e = cudaMemcpyAsync(h_on, S->d_son, nb * 8, cudaMemcpyDeviceToHost, S->s_cmp);
+    if (e == cudaSuccess && h_off) e = cudaMemcpyAsync(h_off, S->d_soff, nb * 8, cudaMemcpyDeviceToHost, S->s_cmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_cmp);
     lock.unlock();
     if (e != cudaSuccess) return vfail(RTA_E_CUDA, "significance map: %s", cudaGetErrorString(e));
     return RTA_OK;

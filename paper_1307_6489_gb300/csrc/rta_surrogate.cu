@@ -272,6 +272,36 @@ static int infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_te
     return RTA_OK;
 }
 
+// The serving loop's inference on a batch gathered on the device: capacities max_img and
+// max_evt, actual counts in *d_n_img and *d_n_evt; the counts and tables were written before
+// the image kernel that precedes this launch started (read before the dependency wait).
+int rta::serve_infer(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t max_img,
+                     const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_n_img, const int64_t* d_n_evt,
+                     float fallback_deg, rta_event_t* d_out, cudaStream_t s) {
+    if (!md || !d_n_img || !d_n_evt || !d_out || max_img < 1 || max_evt < 1) return sfail(RTA_E_INVALID, "bad batch");
+    rta::InferArgs ia = {};
+    ia.f.h = d_h;
+    ia.f.img_tel = d_img_tel;
+    ia.f.evt_off = d_evt_off;
+    ia.f.n_img = max_img;
+    ia.f.n_evt = max_evt;
+    ia.f.n_img_dev = d_n_img;
+    ia.f.n_evt_dev = d_n_evt;
+    int rc = rta::surrogate_ctx_tables(md->ctx, &ia.f.tel_cam, &ia.f.tel_xy, &ia.f.n_tel, nullptr);
+    if (rc) return rc;
+    ia.f.cam_code = md->cam_code;
+    ia.pb = md->pb;
+    ia.p = md->p;
+    ia.pk = md->pk;
+    ia.rows_aligned = (reinterpret_cast<uintptr_t>(d_h) & 15u) == 0;
+    ia.settled = 1;
+    ia.o.fallback_deg = fallback_deg;
+    ia.o.out = d_out;
+    ia.o.status = rta::surrogate_ctx_status(md->ctx);
+    S_TRY(rta::launch_infer(ia, md->n_sm, s));
+    return RTA_OK;
+}
+
 extern "C" {
 
 int rta_surrogate_num_params(void) { return int(rta::N_PARAM_PACKED); }

@@ -84,12 +84,17 @@ def test_results_are_the_same_alone_and_in_a_mix_and_equal_the_device_path(env, 
     bundles = make_bundles(wl, [700, 90, 400, 1, 650, 300, 259])
     st = rta.rta_stream_create(ctx.handle, model if use_model else 0, 3 << 30, 3, 20000, 2000, mode, start, W,
                                t_hi, t_lo, core_nb, 0.5)
+    tm = []
     try:
         now = time.monotonic_ns()
-        mixed = serve(st, bundles, now, concurrent=True)
+        mixed = serve(st, bundles, now, concurrent=True, times=tm)
         alone = serve(st, bundles[:3], now, concurrent=False)
     finally:
         rta.rta_stream_destroy(st)
+    # submitted together, bundles share passes: the device queue handed several to one pass
+    print("bundles per pass:", [t.batch_bundles for t in tm])
+    assert max(t.batch_bundles for t in tm) >= 2
+    assert all(1 <= t.batch_bundles <= len(bundles) and t.ready_wait_ms >= 0 for t in tm)
     for a, m in zip(alone, mixed[:3]):
         np.testing.assert_array_equal(a, m)
     # the same rows as the device-resident calls
