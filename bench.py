@@ -285,6 +285,71 @@ def stream_leg(ctx, wl, proc, stream, steps, e2e_steps, hil, ste):
                             "next upload overlapped"}}
 
 
+def config0_leg(steps, device, n_events=2000):
+    """The small single camera: 2,000 events of the 16 x 16 square camera (16
+    samples, fixed 5-sample window, tailcut 10/5): 16.4 MB, resident in L2, so
+    its rate is not an HBM measurement. Reported: the image kernel's events/s,
+    every event's image compared with the oracle (n_pix exact, size within 1e-4),
+    and the oracle on all events (all host cores)."""
+    import torch
+    import oracle
+    import paper_1307_6489_gb300 as rta
+    import synth
+    wl = synth.make_workload(0, n_events)
+    ctx = rta.Context(device, hbm_budget_bytes=1 << 30)
+    for c, cam in wl.cams.items():
+        ctx.register_camera(c, cam.xy, cam.nb, cam.n_samples)
+    ctx.register_array(wl.tel_cam, wl.tel_xy, wl.p16, wl.scale)
+    p = wl.proc
+    proc = (rta.RTA_WINDOW_SLIDING if p.sliding else rta.RTA_WINDOW_FIXED, p.start, p.W, p.t_hi, p.t_lo,
+            p.core_needs_neighbour)
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    wave = torch.from_numpy(wl.wave.view(np.int16)).to(dev)
+    off = torch.from_numpy(np.ascontiguousarray(wl.wave_off)).to(dev)
+    tel = torch.from_numpy(np.ascontiguousarray(wl.img_tel)).to(dev)
+    hil = torch.zeros(wl.n_img * 16, dtype=torch.float32, device=dev)
+
+    def chain():
+        rta.rta_image_chain(ctx.handle, wave.data_ptr(), wave.numel(), off.data_ptr(), tel.data_ptr(), wl.n_img, *proc,
+                            hil.data_ptr(), sp)
+
+    for _ in range(3):
+        chain()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        chain()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    ctx.check(sp)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    passes = 0
+    while passes == 0 or time.perf_counter() - t0 < 2.0:      # whole passes, about 2 s of work
+        ref = oracle.reconstruct(wl, do_stereo=False, threads=cores)
+        passes += 1
+    cpu_s = (time.perf_counter() - t0) / passes
+    g = rta.hillas_to_numpy(hil.cpu().numpy())
+    H = oracle.H
+    nmatch = int(np.sum(g["n_pix"] == ref["hillas"][:, H["n_pix"]].astype(np.int32)))
+    ok = ref["hillas"][:, H["n_pix"]] > 0
+    rel = np.abs(g["size"][ok] - ref["hillas"][ok, H["size"]]) / ref["hillas"][ok, H["size"]]
+    ctx.close()
+    return {"workload": f"16x16 square camera, {wl.n_evt} events x 16 samples, {wl.wave_bytes / 1e6:.1f} MB "
+                        "(L2-resident: not an HBM measurement)",
+            "kernel": {"ms": ms, "events_per_s": wl.n_evt / (ms / 1e3)},
+            "parity_all_events": {"events": wl.n_evt, "n_pix_equal": nmatch,
+                                  "max_size_rel_err": float(rel.max()) if ok.any() else 0.0,
+                                  "pass": bool(nmatch == wl.n_evt and (not ok.any() or rel.max() <= 1e-4))},
+            "cpu_baseline": {"value": wl.n_evt / cpu_s, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{passes} passes over all {wl.n_evt} events, {cpu_s * 1e3:.1f} ms each on "
+                                       f"{cores} threads"}}
+
+
 def config1_leg(n_events, hbm_peak, steps, device, cpu_events=20000, sample_events=300):
     """The single large camera streamed from host memory: n_events events of the
     1855-pixel hexagonal camera (40 samples, sliding 6-sample window, tailcut 8/4
@@ -470,7 +535,7 @@ def oracle_forward_baseline(tr, h_dev, tel_dev, evt_off, codes, n_evt):
                       f"{dt:.1f} s (numpy; the matrix products may use the host's threads)"}
 
 
-def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
+def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval, train_epochs=0):
     """Train the deep-sets surrogate with the library's kernels on n_train mixed
     gamma/proton events and judge it, next to the geometric reconstruction and
     the lookup tables built from the same training events, on n_eval held-out
@@ -497,7 +562,7 @@ def surrogate_leg(ctx, wl, dev_b, proc, stream, steps, n_train, n_eval):
     tr = train.SurrogateTrainer(ctx, seed=1, cam_code=codes)
     t_fit = time.perf_counter()
     # about 6,000 Adam steps of 2,048 events whatever the training-set size (at least 3 epochs)
-    epochs = max(3, int(round(6000 * 2048 / n_train)))
+    epochs = train_epochs or max(3, int(round(6000 * 2048 / n_train)))
     losses = tr.fit(h_tr, tel_tr, off_tr, logE, src, gam, epochs=epochs, batch_events=2048, lr=2e-3, lr_end=5e-5)
     fit_s = time.perf_counter() - t_fit
     # lookup tables (calibration matrices) from the same training gammas at their true cores
@@ -950,6 +1015,8 @@ def main():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--train-events", type=int, default=2000000)
     ap.add_argument("--eval-events", type=int, default=1000000)
+    ap.add_argument("--train-epochs", type=int, default=0,
+                    help="epochs of the surrogate's training (default: about 6,000 Adam steps)")
     ap.add_argument("--serve-rates", default="0.5,2,8,inf", help="aggregate arrival rates, GB/s (inf: a burst)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--chain", default="", help="fixed image-kernel config 'variant,stages,ctas_per_sm'")
@@ -1158,7 +1225,7 @@ def main():
     sur, trainer, serving, pool_info = None, None, None, None
     if not args.no_surrogate:
         sur, trainer = surrogate_leg(ctx, wl, (wave, wave_off, img_tel, evt_off, hil, ste), proc, stream, args.steps,
-                                     args.train_events, args.eval_events)
+                                     args.train_events, args.eval_events, args.train_epochs)
     if not args.no_serving:
         rates = [float(r) for r in args.serve_rates.split(",")]
         serving, pool_info = serving_leg(ctx, trainer.model if trainer else None, wl, proc, rates,
@@ -1184,6 +1251,7 @@ def main():
         del host, wave_h
         torch.cuda.empty_cache()
         cfg1 = config1_leg(args.config1_events, hbm_peak, args.steps, local)
+    cfg0 = config0_leg(args.steps, local)
 
     if rank == 0:
         cfg = ctx.chain_config()
@@ -1218,6 +1286,7 @@ def main():
                       "surrogate": sur},
             "dl0_stream": stream_out,
             "single_camera_stream": cfg1,
+            "single_camera_small": cfg0,
             "serving": {"rates": serving, "feed": pool_info,
                         "model": "surrogate" if trainer else "geometric"} if serving else None,
             "p99_bundle_latency_ms": next((r["p99_ms"] for r in serving if r["rate_gbs"] == 8.0), None)
