@@ -762,6 +762,8 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
         }
         const rta_hillas_t* fr_s = reinterpret_cast<const rta_hillas_t*>(sm + U_FBROWS);
         auto frow = [&](int64_t img) -> const rta_hillas_t& { return staged ? fr_s[img - row_first] : f.h[img]; };
+        // the telescope of an image and the positions: the shared-memory copies
+        auto ftel = [&](int64_t img) { return staged ? tel_s[img - row_first] : f.img_tel[img]; };
         // ---- geometric fallback with the stereo kernel's grouping: up to STEREO_SMALL_M
         // images eight lanes, up to STEREO_WARP_M a warp (one event per warp at a time),
         // larger events ST_NTC threads (warps 0-7, one event after another) while the
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
                     const int i0 = lo_s[el], m = min(cnt_s[el], RTA_STEREO_MAX_M);
                     int nvalid = 0;
                     if (tid < m)
-                        nvalid = stereo_stage(frow(int64_t(i0) + tid), f.img_tel[i0 + tid], n_tel, f.tel_xy, a.o.status, imc + tid);
+                        nvalid = stereo_stage(frow(int64_t(i0) + tid), ftel(int64_t(i0) + tid), n_tel, txy_s, a.o.status, imc + tid);
                     stereo_bar<ST_NTC>();
                     CSum acc[5];
                     const int npair = pair_sums<ST_NTC>(imc, m, tid, acc);
@@ -798,7 +800,7 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
                     const int i0 = lo_s[el], m = min(cnt_s[el], RTA_STEREO_MAX_M);
                     int nvalid = 0;
                     for (int k = lane; k < m; k += 32)
-                        nvalid += stereo_stage(frow(int64_t(i0) + k), f.img_tel[i0 + k], n_tel, f.tel_xy, a.o.status, im + k);
+                        nvalid += stereo_stage(frow(int64_t(i0) + k), ftel(int64_t(i0) + k), n_tel, txy_s, a.o.status, im + k);
                     __syncwarp();
                     rta_stereo_t sr;
                     if (m <= STEREO_SMALL_M) {

@@ -232,21 +232,25 @@ __device__ __forceinline__ rta_stereo_t group_result(CSum (&acc)[5], int npair, 
 constexpr int STEREO_SMALL_M = 8;
 constexpr int STEREO_WARP_M = 24;
 
-// Barrier of the first NT threads of the CTA (named barrier 1), so that a
-// larger CTA can run the CTA-wide stereo on a subset of its warps.
-template <int NT>
+// Barrier of the NT threads of a group of warps (named barrier BAR), so that a
+// larger CTA can run the CTA-wide stereo on a subset of its warps (or on two
+// subsets at once, with different barriers).
+template <int NT, int BAR = 1>
 __device__ __forceinline__ void stereo_bar() {
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
 }
 
-// Combine the sums of threads 0 .. NT-1 in a fixed order (a shuffle tree per
+// Combine the sums of the NT threads of a group (warps gw .. gw + NT/32 - 1 of
+// the CTA; by default the first NT threads) in a fixed order (a shuffle tree per
 // warp, then the warps in index order) and form the event's row; every one of
 // them returns it. red: NT / 32 * 5 double words and redi: NT / 32 * 2 ints of
-// shared memory. Threads 0 .. NT-1 must all call it, and no other thread.
-template <int NT>
-__device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, int nvalid, DW* red, int* redi) {
+// shared memory of the group. The group's threads must all call it, and no other
+// thread; BAR is the group's named barrier.
+template <int NT, int BAR = 1>
+__device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, int nvalid, DW* red, int* redi,
+                                                   int gw = 0) {
     constexpr int NWC = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - gw;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const DW v = dw_warp_sum(two_sum(acc[k].s, acc[k].c));
@@ -261,7 +265,7 @@ __device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, in
         redi[warp * 2] = npair;
         redi[warp * 2 + 1] = nvalid;
     }
-    stereo_bar<NT>();
+    stereo_bar<NT, BAR>();
     DW tot[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -273,7 +277,7 @@ __device__ __forceinline__ rta_stereo_t cta_result(CSum (&acc)[5], int npair, in
         np += redi[w * 2];
         nv += redi[w * 2 + 1];
     }
-    stereo_bar<NT>();                                  // red and redi may be reused
+    stereo_bar<NT, BAR>();                             // red and redi may be reused
     return stereo_row(tot, np, nv);
 }
 

@@ -342,3 +342,37 @@ def test_fused_learned_call_equals_the_two_calls(setup, bound):
         ctx.check()
         assert torch.equal(h.view(torch.int32), h_ref.view(torch.int32))
         assert torch.equal(ev, ev_ref)
+
+
+@pytest.mark.parametrize("merge", [6, 25])
+def test_fallback_of_large_events_equals_the_stereo_kernel(setup, merge):
+    """Every event falls back (bound 1e-4 deg) and events are joined into events of
+    about 28 or 115 images, so a CTA holds several events of more than 24 images:
+    two groups of eight warps take them two at a time. Their directions equal
+    rta_stereo's bit for bit, and invalid intersections give no direction."""
+    s = setup
+    wl, d, ctx = s["wl"], s["d"], s["ctx"]
+    off = wl.evt_off[::merge].astype(np.int64)
+    if off[-1] != wl.evt_off[-1]:
+        off = np.append(off, wl.evt_off[-1])
+    off = off.astype(np.int32)
+    n_evt = len(off) - 1
+    doff = torch.from_numpy(off).cuda()
+    out = torch.zeros(n_evt * 32, dtype=torch.uint8, device="cuda")
+    rta.rta_surrogate_infer(s["model"], d["h"].data_ptr(), d["img_tel"].data_ptr(), wl.n_img, doff.data_ptr(), n_evt,
+                            1e-4, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    geo = torch.zeros(n_evt * 8, dtype=torch.float32, device="cuda")
+    ctx.stereo(d["h"], doff, d["img_tel"], geo)
+    torch.cuda.synchronize()
+    ctx.check()
+    ev = rta.events_to_numpy(out.cpu().numpy())
+    st = stereo_rows(geo, n_evt)
+    big = np.diff(off) > 24
+    assert big.sum() >= 4
+    fb = (ev["flags"] & rta.RTA_EF_FALLBACK) != 0
+    ok = fb & (st["flags"] == 0)
+    assert ok[big].sum() >= 4
+    np.testing.assert_array_equal(ev["dir_x"][ok].view(np.uint32), st["dir_x"][ok].view(np.uint32))
+    np.testing.assert_array_equal(ev["dir_y"][ok].view(np.uint32), st["dir_y"][ok].view(np.uint32))
+    nodir = (ev["flags"] & rta.RTA_EF_NO_DIRECTION) != 0
+    np.testing.assert_array_equal(nodir[fb], st["flags"][fb] != 0)
