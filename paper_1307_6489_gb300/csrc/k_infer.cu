@@ -212,17 +212,37 @@ __device__ __forceinline__ void relu_bf16_32(uint32_t taddr, const float* __rest
                                                    : 0.f));
 }
 
+// Shared-memory accesses by 32-bit shared-window address.
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t a, float2 v) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+// A BF16 pair (low half first) as two floats: exact.
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t v) {
+    return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xFFFF0000u));
+}
+
 // Sums of the second-layer tile's rows [lo, up) (relative to the block) of one
-// event, channel pair cp, added in row order to that event's running sums.
-__device__ __forceinline__ void pool_rows(const __nv_bfloat162* __restrict__ h2, float2* __restrict__ acc, int lo,
-                                          int up) {
-    float2 s = *acc;
+// event, channel pair cp (h2: the pair's shared address in row 0; acc: the
+// event's running sums of the pair), added in row order.
+__device__ __forceinline__ void pool_rows(uint32_t h2, uint32_t acc, int lo, int up) {
+    constexpr uint32_t RS = LDH * 2;         // bytes per row
+    float2 s = lds_f2(acc);
     int r = lo;
     for (; r + 4 <= up; r += 4) {
-        const float2 a0 = __bfloat1622float2(h2[(r + 0) * (LDH / 2)]);
-        const float2 a1 = __bfloat1622float2(h2[(r + 1) * (LDH / 2)]);
-        const float2 a2 = __bfloat1622float2(h2[(r + 2) * (LDH / 2)]);
-        const float2 a3 = __bfloat1622float2(h2[(r + 3) * (LDH / 2)]);
+        const uint32_t base = h2 + uint32_t(r) * RS;
+        const uint32_t v0 = lds_u32(base), v1 = lds_u32(base + RS), v2 = lds_u32(base + 2 * RS),
+                       v3 = lds_u32(base + 3 * RS);
+        const float2 a0 = bf2_to_f2(v0), a1 = bf2_to_f2(v1), a2 = bf2_to_f2(v2), a3 = bf2_to_f2(v3);
         s.x += a0.x;
         s.y += a0.y;
         s.x += a1.x;
@@ -233,11 +253,11 @@ __device__ __forceinline__ void pool_rows(const __nv_bfloat162* __restrict__ h2,
         s.y += a3.y;
     }
     for (; r < up; ++r) {
-        const float2 a0 = __bfloat1622float2(h2[r * (LDH / 2)]);
+        const float2 a0 = bf2_to_f2(lds_u32(h2 + uint32_t(r) * RS));
         s.x += a0.x;
         s.y += a0.y;
     }
-    *acc = s;
+    sts_f2(acc, s);
 }
 
 }  // namespace
@@ -593,10 +613,10 @@ __global__ void __launch_bounds__(NT, 1) k_deepsets_infer(const InferArgs a) {
                     const int nr = int(min(int64_t(TM), R - r0));
                     const int e_first = evr_s[j * TM], e_last = evr_s[j * TM + nr - 1];
                     const int cp = tid & 63, g8 = tid >> 6;
-                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(H2s) + cp;
+                    const uint32_t h2a = smem_addr(H2s) + uint32_t(cp) * 4u, pacc_a = smem_addr(Pacc);
                     for (int el = e_first + g8; el <= e_last; el += NPOOL / 64) {
                         const int lo = int(max(rowb[el], r0) - r0), up = int(min(rowb[el + 1], r0 + nr) - r0);
-                        if (lo < up) pool_rows(h2, reinterpret_cast<float2*>(Pacc + el * PSTRIDE) + cp, lo, up);
+                        if (lo < up) pool_rows(h2a, pacc_a + uint32_t(el * PSTRIDE * 4 + cp * 8), lo, up);
                     }
                 }
                 fence_proxy_async_smem();               // the V1^T tail copy may overwrite the tile next
