@@ -181,3 +181,30 @@ def test_sky_map_matches_the_oracle():
     finally:
         rta.rta_stream_destroy(st)
         ctx.close()
+
+
+def test_submission_rejects_images_outside_the_bundle(env):
+    """In a pass the image kernel addresses the whole arena, so each image must lie
+    inside its own bundle's waveforms: rejected at submission otherwise."""
+    wl, ctx, model = env
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    b = make_bundles(wl, [50])[0]
+    st = rta.rta_stream_create(ctx.handle, 0, 1 << 30, 2, 20000, 2000, mode, start, W, t_hi, t_lo, core_nb, 0.5)
+    try:
+        for change, code in [("past_end", rta.RTA_E_INVALID), ("misaligned", rta.RTA_E_ALIGN),
+                             ("negative", rta.RTA_E_ALIGN)]:
+            hb = HostBundle(b, time.monotonic_ns())
+            if change == "past_end":
+                hb.off[-1] = b.wave.size - 8          # the last image runs past the waveforms
+            elif change == "misaligned":
+                hb.off[1] += 4
+            else:
+                hb.off[0] = -8
+            with pytest.raises(rta.RtaError) as e:
+                rta.rta_stream_submit(st, hb.b)
+            assert e.value.code == code, change
+        # the stream still serves a good bundle afterwards
+        res = serve(st, [b], time.monotonic_ns())
+        assert len(res) == 1
+    finally:
+        rta.rta_stream_destroy(st)

@@ -376,3 +376,32 @@ def test_fallback_of_large_events_equals_the_stereo_kernel(setup, merge):
     np.testing.assert_array_equal(ev["dir_y"][ok].view(np.uint32), st["dir_y"][ok].view(np.uint32))
     nodir = (ev["flags"] & rta.RTA_EF_NO_DIRECTION) != 0
     np.testing.assert_array_equal(nodir[fb], st["flags"][fb] != 0)
+
+
+def test_fused_learned_call_with_empty_events_and_no_images(setup):
+    """Events without images (the call then launches no image kernel, and the
+    inference reads its inputs after the dependency wait) get no direction and
+    zero used images; an empty event list is accepted and writes nothing."""
+    s = setup
+    wl, ctx = s["wl"], s["ctx"]
+    dv = Dev(wl)
+    proc = proc_args(wl)
+    stream = torch.cuda.current_stream().cuda_stream
+    n_evt = 5
+    off = torch.zeros(n_evt + 1, dtype=torch.int32, device="cuda")
+    h = dv.hillas_buf()
+    ev = torch.full((n_evt * 32,), 255, dtype=torch.uint8, device="cuda")
+    rta.rta_reconstruct_learned(s["model"], dv.wave.data_ptr(), dv.wave.numel(), dv.wave_off.data_ptr(),
+                                dv.img_tel.data_ptr(), 0, off.data_ptr(), n_evt, *proc, 0.5, h.data_ptr(),
+                                ev.data_ptr(), stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    e = rta.events_to_numpy(ev.cpu().numpy())
+    assert (e["n_used"] == 0).all()
+    assert ((e["flags"] & rta.RTA_EF_NO_DIRECTION) != 0).all()
+    before = ev.clone()
+    rta.rta_reconstruct_learned(s["model"], dv.wave.data_ptr(), dv.wave.numel(), dv.wave_off.data_ptr(),
+                                dv.img_tel.data_ptr(), 0, off.data_ptr(), 0, *proc, 0.5, h.data_ptr(),
+                                ev.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.equal(ev, before)
