@@ -900,10 +900,16 @@ def serving_leg(ctx, model, wl, proc, rates, duration_s, feed_events=60000, seed
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     out = []
     try:
-        for rate in rates:
+        # the offered rates, then a burst of 48 small bundles (1k-2k events) submitted at once,
+        # where copies finish close together and the device queue hands several to one pass
+        small = feed_bundles(feed, 48, rng, lo=1000, hi=2000)
+        for rate in list(rates) + ["small_burst"]:
             t_start = time.monotonic_ns() + 50_000_000
-            sched = [(t_start + dt, pool[i]) for dt, i in arrival_schedule([b["bytes"] for b in pool], rate,
-                                                                           duration_s, rng, min_arrivals=6)]
+            if rate == "small_burst":
+                sched = [(t_start, b) for b in small]
+            else:
+                sched = [(t_start + dt, pool[i]) for dt, i in arrival_schedule([b["bytes"] for b in pool], rate,
+                                                                               duration_s, rng, min_arrivals=6)]
             total = sum(b["bytes"] for _, b in sched)
             ev_all = torch.empty(sum(b["n_evt"] for _, b in sched) * 32, dtype=torch.uint8, pin_memory=True)
             ev_np = ev_all.numpy()
