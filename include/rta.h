@@ -367,6 +367,17 @@ int rta_surrogate_destroy(rta_model* model);
 int rta_surrogate_set_params(rta_model* model, const float* h_params);
 /* which: 0 parameters, 1 last gradients, 2 Adam first moments, 3 second moments. Synchronises. */
 int rta_surrogate_get_params(rta_model* model, int which, float* h_out);
+/* Checkpoint and resume of training: the FP32 parameters, Adam's first and
+ * second moments (each rta_surrogate_num_params() floats in the packed order of
+ * rta_surrogate_set_params) and the number of Adam steps taken, which sets the
+ * bias corrections of the next step. get_state synchronises the device and
+ * fills the non-NULL arrays; set_state replaces the whole state (the BF16 copy
+ * and the tensor-core layout of the weights are rebuilt), so that training
+ * resumed from a saved state takes the same steps as training that never
+ * stopped. Synchronous. */
+int rta_surrogate_get_state(rta_model* model, float* h_params, float* h_m, float* h_v, int64_t* step);
+int rta_surrogate_set_state(rta_model* model, const float* h_params, const float* h_m, const float* h_v,
+                            int64_t step);
 /* Raw network outputs d_y[n_evt*4] and baselines d_base[n_evt*2] (either may be NULL). */
 int rta_surrogate_forward(rta_model* model, const rta_hillas_t* d_hillas, const int32_t* d_img_tel, int64_t n_img,
                           const int32_t* d_evt_off, int64_t n_evt, float* d_y, float* d_base, void* stream);

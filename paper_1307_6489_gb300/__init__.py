@@ -99,6 +99,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_surrogate_destroy": ([P], i32),
         "rta_surrogate_set_params": ([P, P], i32),
         "rta_surrogate_get_params": ([P, i32, P], i32),
+        "rta_surrogate_get_state": ([P, P, P, P, P], i32),
+        "rta_surrogate_set_state": ([P, P, P, P, i64], i32),
         "rta_surrogate_forward": ([P, P, P, i64, P, i64, P, P, P], i32),
         "rta_surrogate_train_step": ([P, P, P, i64, P, i64, P, P, P, f32, i32, P, P], i32),
         "rta_surrogate_infer": ([P, P, P, i64, P, i64, f32, P, P], i32),
@@ -352,6 +354,23 @@ def rta_surrogate_get_params(model: int, which: int = 0) -> np.ndarray:
     out = np.zeros(rta_surrogate_num_params(), np.float32)
     _check(load().rta_surrogate_get_params(model, which, out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+def rta_surrogate_get_state(model: int):
+    """(parameters, first moments, second moments, Adam steps taken) as float32 arrays and an int."""
+    n = rta_surrogate_num_params()
+    p, m, v = (np.zeros(n, np.float32) for _ in range(3))
+    step = ctypes.c_int64(0)
+    _check(load().rta_surrogate_get_state(model, p.ctypes.data, m.ctypes.data, v.ctypes.data, ctypes.byref(step)))
+    return p, m, v, int(step.value)
+
+
+def rta_surrogate_set_state(model: int, params, m, v, step: int):
+    n = rta_surrogate_num_params()
+    p, m, v = (np.ascontiguousarray(x, np.float32).reshape(-1) for x in (params, m, v))
+    if not (p.size == m.size == v.size == n):
+        raise ValueError(f"state arrays must hold {n} floats each")
+    _check(load().rta_surrogate_set_state(model, p.ctypes.data, m.ctypes.data, v.ctypes.data, int(step)))
 
 
 def rta_surrogate_forward(model, d_hillas, d_img_tel, n_img, d_evt_off, n_evt, d_y, d_base, stream=0):

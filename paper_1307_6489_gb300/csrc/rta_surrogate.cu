@@ -402,6 +402,33 @@ int rta_surrogate_get_params(rta_model* md, int which, float* h_out) {
     return RTA_OK;
 }
 
+int rta_surrogate_get_state(rta_model* md, float* h_params, float* h_m, float* h_v, int64_t* step) {
+    if (!md || !step) return sfail(RTA_E_INVALID, "NULL argument");
+    int rc;
+    if (h_params && (rc = rta_surrogate_get_params(md, 0, h_params))) return rc;
+    if (h_m && (rc = rta_surrogate_get_params(md, 2, h_m))) return rc;
+    if (h_v && (rc = rta_surrogate_get_params(md, 3, h_v))) return rc;
+    *step = md->step;
+    return RTA_OK;
+}
+
+int rta_surrogate_set_state(rta_model* md, const float* h_params, const float* h_m, const float* h_v, int64_t step) {
+    if (!md || !h_params || !h_m || !h_v || step < 0) return sfail(RTA_E_INVALID, "bad argument");
+    int rc = rta_surrogate_set_params(md, h_params);
+    if (rc) return rc;
+    std::vector<float> m(rta::N_PARAM_INTERNAL, 0.f), v(rta::N_PARAM_INTERNAL, 0.f);
+    for (const Seg& sg : segments())
+        for (int64_t r = 0; r < sg.rows; ++r)
+            for (int64_t c = 0; c < sg.cols; ++c) {
+                m[sg.off_int + r * sg.cols + c] = h_m[sg.off_pack + r * sg.cols + c];
+                v[sg.off_int + r * sg.cols + c] = h_v[sg.off_pack + r * sg.cols + c];
+            }
+    S_TRY(cudaMemcpy(md->m, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice));
+    S_TRY(cudaMemcpy(md->v, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
+    md->step = step;
+    return RTA_OK;
+}
+
 int rta_surrogate_forward(rta_model* md, const rta_hillas_t* d_h, const int32_t* d_img_tel, int64_t n_img,
                           const int32_t* d_evt_off, int64_t n_evt, float* d_y, float* d_base, void* stream) {
     int rc = check_batch(md, d_h, d_img_tel, n_img, d_evt_off, n_evt);

@@ -9,6 +9,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (RTA_WINDOW_FIXED, RTA_WINDOW_SLIDING, Context, rta_surrogate_create, rta_surrogate_destroy,
+               rta_surrogate_get_state, rta_surrogate_set_state,
                rta_surrogate_infer, rta_surrogate_train_step, events_to_numpy, hillas_to_numpy, stereo_to_numpy)
 
 
@@ -33,8 +34,22 @@ class SurrogateTrainer:
 
     def __init__(self, ctx: Context, seed: int = 0, cam_code=None, model: int | None = None):
         self.ctx = ctx
+        self.cam_code = np.zeros(16, np.float32) if cam_code is None else np.asarray(cam_code, np.float32)
         self.model = model if model is not None else rta_surrogate_create(ctx.handle, seed, cam_code)
         self.own = model is None
+
+    def save(self, path: str):
+        """Checkpoint: parameters, Adam moments, steps taken and camera codes."""
+        p, m, v, step = rta_surrogate_get_state(self.model)
+        write_checkpoint(path, p, m, v, step, self.cam_code)
+
+    @classmethod
+    def resume(cls, ctx: Context, path: str) -> "SurrogateTrainer":
+        """A trainer whose model continues from a checkpoint exactly where it stopped."""
+        p, m, v, step, codes = read_checkpoint(path)
+        tr = cls(ctx, seed=0, cam_code=codes)
+        rta_surrogate_set_state(tr.model, p, m, v, step)
+        return tr
 
     def close(self):
         if self.own and self.model:
@@ -128,3 +143,46 @@ def evaluate(events: dict, stereo: dict, truth: np.ndarray):
                auc_gamma_hadron=roc_auc(events["gammaness"][gam & ok_s], events["gammaness"][~gam & ok_s]))
     out["r68_ratio"] = out["r68_surrogate_deg"] / out["r68_geometric_deg"]
     return out
+
+
+# Checkpoint file: the magic bytes, then little-endian uint32 version, uint32 parameter
+# count n, int64 Adam steps taken, 16 float32 camera codes, and the float32 parameters,
+# first moments and second moments (n each, the packed order of rta_surrogate_set_params).
+CHECKPOINT_MAGIC = b"RTASURR1"
+CHECKPOINT_VERSION = 1
+
+
+def write_checkpoint(path: str, params, m, v, step: int, cam_code):
+    p, m, v = (np.ascontiguousarray(x, "<f4").reshape(-1) for x in (params, m, v))
+    codes = np.zeros(16, "<f4")
+    c = np.asarray(cam_code, "<f4").reshape(-1)[:16]
+    codes[: len(c)] = c
+    if not (p.size == m.size == v.size):
+        raise ValueError("parameters and moments differ in size")
+    with open(path, "wb") as f:
+        f.write(CHECKPOINT_MAGIC)
+        f.write(np.array([CHECKPOINT_VERSION, p.size], "<u4").tobytes())
+        f.write(np.array([step], "<i8").tobytes())
+        f.write(codes.tobytes())
+        for x in (p, m, v):
+            f.write(x.tobytes())
+
+
+def read_checkpoint(path: str):
+    """(parameters, first moments, second moments, steps, camera codes); ValueError on a
+    file of another kind or a truncated one."""
+    with open(path, "rb") as f:
+        raw = f.read()
+    head = len(CHECKPOINT_MAGIC) + 8 + 8 + 64
+    if len(raw) < head or raw[: len(CHECKPOINT_MAGIC)] != CHECKPOINT_MAGIC:
+        raise ValueError(f"{path}: not a surrogate checkpoint")
+    o = len(CHECKPOINT_MAGIC)
+    version, n = np.frombuffer(raw, "<u4", 2, o)
+    if version != CHECKPOINT_VERSION:
+        raise ValueError(f"{path}: checkpoint version {version}, expected {CHECKPOINT_VERSION}")
+    step = int(np.frombuffer(raw, "<i8", 1, o + 8)[0])
+    codes = np.frombuffer(raw, "<f4", 16, o + 16).copy()
+    if len(raw) != head + 12 * int(n):
+        raise ValueError(f"{path}: truncated or padded checkpoint")
+    arrs = [np.frombuffer(raw, "<f4", int(n), head + 4 * int(n) * k).copy() for k in range(3)]
+    return arrs[0], arrs[1], arrs[2], step, codes

@@ -405,3 +405,30 @@ def test_fused_learned_call_with_empty_events_and_no_images(setup):
                                 ev.data_ptr(), stream)
     torch.cuda.synchronize()
     assert torch.equal(ev, before)
+
+
+def test_training_resumed_from_a_checkpoint_takes_the_same_steps(setup, tmp_path):
+    """Train 4 Adam steps, save, train 3 more; a new trainer resumed from the file
+    trains the same 3 steps: parameters, moments and step count bit for bit."""
+    from paper_1307_6489_gb300 import train
+    s = setup
+    wl, d, ctx = s["wl"], s["d"], s["ctx"]
+    args = (d["h"], d["img_tel"], wl.evt_off, d["logE"], d["src"], d["gam"])
+    a = train.SurrogateTrainer(ctx, seed=21, cam_code=cam_codes(wl))
+    b = None
+    try:
+        a.fit(*args, epochs=2, batch_events=150, lr=1e-3, lr_end=1e-3, seed=0)
+        f = str(tmp_path / "ck.bin")
+        a.save(f)
+        a.fit(*args, epochs=1, batch_events=100, lr=1e-3, lr_end=1e-3, seed=1)
+        b = train.SurrogateTrainer.resume(ctx, f)
+        b.fit(*args, epochs=1, batch_events=100, lr=1e-3, lr_end=1e-3, seed=1)
+        pa, ma, va, sa = rta.rta_surrogate_get_state(a.model)
+        pb, mb, vb, sb = rta.rta_surrogate_get_state(b.model)
+        assert sa == sb == 7
+        for x, y in [(pa, pb), (ma, mb), (va, vb)]:
+            np.testing.assert_array_equal(x.view(np.uint32), y.view(np.uint32))
+    finally:
+        a.close()
+        if b is not None:
+            b.close()
