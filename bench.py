@@ -1034,6 +1034,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
+    if ws > 1:
+        # several ranks measure the step's scaling: the single-GPU legs (learned path with its
+        # training, serving, DL0 stream, the single-camera configurations) run only at N = 1
+        args.no_surrogate = args.no_serving = args.no_stream = True
+        args.config1_events = 0
 
     import torch
     import torch.distributed as dist
@@ -1257,7 +1262,7 @@ def main():
         del host, wave_h
         torch.cuda.empty_cache()
         cfg1 = config1_leg(args.config1_events, hbm_peak, args.steps, local)
-    cfg0 = config0_leg(args.steps, local)
+    cfg0 = config0_leg(args.steps, local) if ws == 1 else None
 
     if rank == 0:
         cfg = ctx.chain_config()
