@@ -768,8 +768,11 @@ typedef struct rta_camera_desc_t {
  * last call's contents (each call resets what must start at zero), so calls
  * whose work overlaps on the GPU (other streams, other host threads) race and
  * must be serialised by the caller. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. This call makes no
+ * array's device address (cudaGetSymbolAddress) with that device current.
+ * Not capturable: the tables travel by a copy from a stack buffer of this call,
+ * so no call (the first or a later one) may be made while `stream` is being
+ * captured into a graph (such a call returns RTA_E_INVALID and leaves the
+ * capture as it was). This call makes no
  * cudaMalloc, cudaFree or other allocating call. Asynchronous on `stream`;
  * the host arrays (h_cams, h_tel_cam, h_tel_row) are consumed before it
  * returns, whatever memory they are in. */

@@ -135,12 +135,15 @@ extern "C" int rta_image_chain_noalloc(const rta_camera_desc_t* h_cams, int n_ca
         return nfail(RTA_E_ALIGN, "d_wave, d_p16 and d_scale must be 16-byte aligned");
 
     // ---- set-up: the scratch's device address on this device
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NA_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return nfail(RTA_E_INVALID, "the stream is being captured");
     int dev = 0;
     NA_TRY(cudaGetDevice(&dev));
     unsigned int* scratch = nullptr;
     int rc = scratch_address(dev, &scratch);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     // The tables travel as one copy of a stack image of the scratch's table
     // region, with the work counter and status word (zero) in front: a copy
     // from pageable host memory is staged before cudaMemcpyAsync returns, so

@@ -210,3 +210,34 @@ def test_noalloc_rejects_bad_calibration_rows():
     with pytest.raises(rta.RtaError) as e:
         _call(descs, bad_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, out)
     assert e.value.code == rta.RTA_E_INVALID
+
+
+def test_noalloc_refuses_a_stream_under_capture_and_leaves_the_capture_intact():
+    # the tables are copied from a stack buffer of the call, which a graph could not
+    # replay: under capture the call must refuse before it enqueues anything, and the
+    # capture must still complete and replay the work captured around it
+    wl = synth.make_workload(2, 40)
+    descs, tel_cam, tel_row, d_p16, d_scale, n_rows, keep = caller_tables(wl)
+    dev = Dev(wl)
+    proc = proc_args(wl)
+    ref = dev.hillas_buf()
+    _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, ref)
+    torch.cuda.synchronize()
+    x = torch.zeros(4, device="cuda")
+    spare = dev.hillas_buf()
+    g = torch.cuda.CUDAGraph()
+    refused = None
+    with torch.cuda.graph(g):
+        x.add_(1.0)
+        try:
+            _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, spare)
+        except rta.RtaError as e:
+            refused = e
+    assert refused is not None and refused.code == rta.RTA_E_INVALID and "captured" in str(refused)
+    g.replay()
+    torch.cuda.synchronize()
+    assert x.tolist() == [1.0] * 4
+    out = torch.full_like(ref, float("nan"))
+    _call(descs, tel_cam, tel_row, d_p16, d_scale, n_rows, dev, wl.n_img, proc, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
