@@ -187,12 +187,14 @@ int rta_selftest_wait_timeout(rta_ctx* ctx, int timeout_ms, uint64_t* waited_ns,
  * integrator warps per CTA and pixels per thread), n_stages the shared-memory
  * pipeline depth (2..8), ctas_per_sm the resident CTAs per SM (0 = as many as
  * fit). Sets the configuration of every window mode, the neighbour-peak
- * window's included (whose kernel runs with as many of the CTAs as fit).
- * Returns RTA_E_INVALID if the combination does not fit in shared memory for
+ * window's included (whose kernel runs with as many of the CTAs as fit), and
+ * of the byte-stream path (rta_reconstruct_stream), undoing what
+ * rta_autotune_stream tuned. Returns RTA_E_INVALID if the combination does not fit in shared memory for
  * the registered cameras. Results do not depend on the configuration. */
 int rta_set_chain_config(rta_ctx* ctx, int variant, int n_stages, int ctas_per_sm);
 
-/* The configuration a launch outside the neighbour-peak mode would use now:
+/* The configuration a launch outside the neighbour-peak mode would use now (the
+ * byte-stream path too, unless rta_autotune_stream has tuned its own):
  * variant, stages, CTAs per SM, grid size and dynamic shared memory per CTA in
  * bytes (NULL outputs are skipped). */
 int rta_get_chain_config(rta_ctx* ctx, int* variant, int* n_stages, int* ctas_per_sm, int* grid,
@@ -503,6 +505,25 @@ int rta_reconstruct_stream(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_byte
                            const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_counts, int window_mode,
                            int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
                            rta_hillas_t* d_hillas, rta_stereo_t* d_stereo, void* stream);
+
+/* The autotuner of the byte-stream path: runs the image kernel of
+ * rta_reconstruct_stream (the per-image records included; no stereo) on an
+ * ingested stream for every configuration that fits (variant x 2..6 stages x
+ * 1..4 CTAs/SM), `reps` timed launches each, and keeps the fastest as the
+ * stream path's own configuration (its producer copies chunks from packet
+ * segments, so its best pipeline depth can differ from the contiguous
+ * bundle's). Arguments as rta_reconstruct_stream; d_hillas (max_img rows)
+ * receives the configuration-independent rows. Every measurement goes to
+ * h_entries (up to max_entries; *n_entries = number measured). The
+ * neighbour-peak window is tuned for bundles and streams alike by rta_autotune:
+ * RTA_WINDOW_NEIGHBOUR returns RTA_E_INVALID here. On a failed launch the
+ * previous configuration stays. Synchronises `stream`; may grow the context's
+ * per-image workspace (an allocation). */
+int rta_autotune_stream(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, const rta_segment_t* d_seg,
+                        int64_t max_seg, const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
+                        const int64_t* d_counts, int window_mode, int start, int W, float t_hi, float t_lo,
+                        int core_needs_neighbour, rta_hillas_t* d_hillas, int reps, rta_tune_entry_t* h_entries,
+                        int max_entries, int* n_entries, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Lookup tables: the calibration matrices of the real-time reconstruction  */

@@ -118,6 +118,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "rta_significance_map": ([P, i64, Window, i32, P, P, P], i32),
         "rta_selftest_wait_timeout": ([P, i32, P, P], i32),
         "rta_ingest": ([P, P, i64, i32, P, i64, P, P, i64, P, P, P, i64, P, P], i32),
+        "rta_autotune_stream": ([P, P, i64, P, i64, P, P, i64, P, i32, i32, i32, f32, f32, i32, P, i32, P, i32, P, P],
+                                i32),
         "rta_reconstruct_stream": ([P, P, i64, P, i64, P, P, i64, P, i64, P, i32, i32, i32, f32, f32, i32, P, P, P],
                                    i32),
         "rta_lut_accumulate": ([P, P, P, i64, P, i64, P, P, P, P, i32, P, i32, P, P], i32),
@@ -424,6 +426,19 @@ def rta_reconstruct_stream(ctx, d_stream, n_bytes, d_seg, max_seg, d_img_seg, d_
     _check(load().rta_reconstruct_stream(ctx, d_stream, n_bytes, d_seg, max_seg, d_img_seg, d_img_tel, max_img,
                                          d_evt_off, max_evt, d_counts, window_mode, start, W, t_hi, t_lo,
                                          int(core_needs_neighbour), d_hillas, d_stereo, stream))
+
+
+def rta_autotune_stream(ctx, d_stream, n_bytes, d_seg, max_seg, d_img_seg, d_img_tel, max_img, d_counts, window_mode,
+                        start, W, t_hi, t_lo, core_needs_neighbour, d_hillas, reps=3, stream=0):
+    """Sweep the byte-stream image kernel's launch configurations; keeps the fastest. Returns all measurements."""
+    cap = 256
+    entries = (TuneEntry * cap)()
+    n = ctypes.c_int()
+    _check(load().rta_autotune_stream(ctx, d_stream, n_bytes, d_seg, max_seg, d_img_seg, d_img_tel, max_img, d_counts,
+                                      window_mode, start, W, t_hi, t_lo, int(core_needs_neighbour), d_hillas, reps,
+                                      entries, cap, ctypes.byref(n), stream))
+    return [dict(variant=e.variant, n_stages=e.n_stages, ctas_per_sm=e.ctas_per_sm, grid=e.grid, ms=e.ms)
+            for e in entries[: min(n.value, cap)]]
 
 
 RTA_MAX_CAMS = 16

@@ -102,6 +102,11 @@ struct rta_ctx {
     int nb_variant = 0;
     int nb_nstage = 3;
     int nb_ctas_per_sm = 0;
+    // the byte-stream kernel's configuration once rta_autotune_stream has tuned it
+    // (st_variant < 0: the plain kernel's)
+    int st_variant = -1;
+    int st_nstage = 2;
+    int st_ctas_per_sm = 0;
     int max_P = 0, max_S = 0;
     Slot slot[2];
     // workspace of rta_ingest (pieces, packet list), grown on demand
@@ -259,6 +264,7 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
 // its own, the others share the plain kernel's.
 ChainCfg cfg_of(const rta_ctx* c, int kind) {
     if (kind == rta::CHAIN_NB) return ChainCfg{c->nb_variant, c->nb_nstage, c->nb_ctas_per_sm};
+    if (kind == rta::CHAIN_STREAM && c->st_variant >= 0) return ChainCfg{c->st_variant, c->st_nstage, c->st_ctas_per_sm};
     return ChainCfg{c->variant, c->nstage, c->ctas_per_sm};
 }
 
@@ -572,6 +578,7 @@ int rta_set_chain_config(rta_ctx* c, int variant, int n_stages, int ctas_per_sm)
     c->variant = c->nb_variant = variant;
     c->nstage = c->nb_nstage = n_stages;
     c->ctas_per_sm = c->nb_ctas_per_sm = ctas_per_sm;
+    c->st_variant = -1;
     return RTA_OK;
 }
 
@@ -612,6 +619,76 @@ int rta_chain_variant_info(int variant, int* integrator_warps, int* pixels_per_t
     return RTA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Every configuration that fits (variant x 2..6 stages x 1..4 CTAs/SM) of the kernel of `kind`:
+// *cv, *cn, *cc (the context's fields for that kind) are set to it, `run` launches the kernel once
+// (one warm-up, then `reps` timed launches between CUDA events); the fastest is kept, or the
+// previous configuration if a launch failed.
+template <class Run>
+int tune_sweep(rta_ctx* c, int kind, int64_t n_img, int reps, cudaStream_t s, int* cv, int* cn, int* cc, Run run,
+               rta_tune_entry_t* h_entries, int max_entries, int* n_entries) {
+    const ChainCfg saved{*cv, *cn, *cc};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(RTA_E_CUDA, "cudaEventCreate failed");
+    }
+    ChainCfg best = saved;
+    float best_ms = 1e30f;
+    int n = 0, rc = RTA_OK;
+    for (int v = 0; v < RTA_CHAIN_VARIANTS && !rc; ++v)
+        for (int nst = 2; nst <= 6 && !rc; ++nst)
+            for (int cps = 1; cps <= 4; ++cps) {
+                int g, swb;
+                size_t sm;
+                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb, kind) != RTA_OK) continue;
+                *cv = v;
+                *cn = nst;
+                *cc = cps;
+                if ((rc = run())) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && !rc; ++r) rc = run();
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(RTA_E_CUDA, "autotune run failed"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                if (h_entries && n < max_entries) h_entries[n] = rta_tune_entry_t{v, nst, cps, g, ms};
+                ++n;
+                if (ms < best_ms) { best_ms = ms; best = ChainCfg{v, nst, cps}; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const ChainCfg keep = rc ? saved : best;
+    *cv = keep.variant;
+    *cn = keep.nstage;
+    *cc = keep.ctas_per_sm;
+    if (n_entries) *n_entries = n;
+    return rc;
+}
+
+// The per-image records of the stream path, grown to max_img images.
+int ensure_smeta(rta_ctx* c, int64_t max_img, cudaStream_t s) {
+    const size_t need = sizeof(rta::StreamImg) * size_t(max_img);
+    if (need <= c->smeta_bytes) return RTA_OK;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(c->d_smeta);
+    c->d_smeta = nullptr;
+    c->smeta_bytes = 0;
+    CUDA_TRY(cudaMalloc(&c->d_smeta, need));
+    c->smeta_bytes = need;
+    return RTA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off, const int32_t* d_img_tel,
                  int64_t n_img, int window_mode, int start, int W, float t_hi, float t_lo, int core_needs_neighbour,
                  rta_hillas_t* d_out, int reps, rta_tune_entry_t* h_entries, int max_entries, int* n_entries,
@@ -625,51 +702,48 @@ int rta_autotune(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64
     cudaStream_t s = (cudaStream_t)stream;
     const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
     // the neighbour-peak window tunes its own configuration, the other modes the plain kernel's
+    const int kind = pp.nbpeak ? rta::CHAIN_NB : rta::CHAIN_PLAIN;
     int* cv = pp.nbpeak ? &c->nb_variant : &c->variant;
     int* cn = pp.nbpeak ? &c->nb_nstage : &c->nstage;
     int* cc = pp.nbpeak ? &c->nb_ctas_per_sm : &c->ctas_per_sm;
-    const ChainCfg saved{*cv, *cn, *cc};
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
-    ChainCfg best = saved;
-    float best_ms = 1e30f;
-    int n = 0;
-    for (int v = 0; v < RTA_CHAIN_VARIANTS; ++v)
-        for (int nst = 2; nst <= 6; ++nst)
-            for (int cps = 1; cps <= 4; ++cps) {
-                int g, swb;
-                size_t sm;
-                if (config_launch(c, ChainCfg{v, nst, cps}, n_img, &g, &sm, &swb,
-                                  pp.nbpeak ? rta::CHAIN_NB : rta::CHAIN_PLAIN) != RTA_OK)
-                    continue;
-                *cv = v;
-                *cn = nst;
-                *cc = cps;
-                rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out,
-                               0, s, nullptr);
-                if (rc) break;
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < reps && !rc; ++r)
-                    rc = run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0,
-                                   d_out, 0, s, nullptr);
-                cudaEventRecord(e1, s);
-                if (rc) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(RTA_E_CUDA, "autotune run failed"); break; }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= reps;
-                if (h_entries && n < max_entries) h_entries[n] = rta_tune_entry_t{v, nst, cps, g, ms};
-                ++n;
-                if (ms < best_ms) { best_ms = ms; best = ChainCfg{v, nst, cps}; }
-            }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    *cv = rc ? saved.variant : best.variant;
-    *cn = rc ? saved.nstage : best.nstage;
-    *cc = rc ? saved.ctas_per_sm : best.ctas_per_sm;
-    if (n_entries) *n_entries = n;
-    return rc;
+    auto run = [&]() {
+        return run_chain(c, d_wave, n_wave, d_wave_off, d_img_tel, nullptr, n_img, pp, nullptr, nullptr, 0, d_out, 0, s,
+                         nullptr);
+    };
+    return tune_sweep(c, kind, n_img, reps, s, cv, cn, cc, run, h_entries, max_entries, n_entries);
+}
+
+int rta_autotune_stream(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes, const rta_segment_t* d_seg,
+                        int64_t max_seg, const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
+                        const int64_t* d_counts, int window_mode, int start, int W, float t_hi, float t_lo,
+                        int core_needs_neighbour, rta_hillas_t* d_hillas, int reps, rta_tune_entry_t* h_entries,
+                        int max_entries, int* n_entries, void* stream) {
+    int rc = check_ctx(c);
+    if (rc || (rc = check_array(c)) || (rc = check_n(max_img, "max_img"))) return rc;
+    if ((rc = check_proc(c, window_mode, start, W, true, t_hi, t_lo))) return rc;
+    if (window_mode == RTA_WINDOW_NEIGHBOUR)
+        return fail(RTA_E_INVALID, "the neighbour-peak window has one configuration for bundles and streams: rta_autotune");
+    if (max_img == 0 || !d_stream || !d_seg || !d_img_seg || !d_img_tel || !d_counts || !d_hillas)
+        return fail(RTA_E_INVALID, "empty stream or NULL device pointer");
+    if (!aligned16(d_stream)) return fail(RTA_E_ALIGN, "d_stream is not 16-byte aligned");
+    if (n_bytes < 0 || max_seg < 1) return fail(RTA_E_INVALID, "bad stream size or segment capacity");
+    if (reps < 1) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
+    if ((rc = ensure_smeta(c, max_img, s))) return rc;
+    // until tuned, the stream kernel follows the plain kernel's configuration: start from it
+    if (c->st_variant < 0) {
+        c->st_variant = c->variant;
+        c->st_nstage = c->nstage;
+        c->st_ctas_per_sm = c->ctas_per_sm;
+    }
+    auto run = [&]() {
+        return run_chain(c, reinterpret_cast<const uint16_t*>(d_stream), n_bytes / 2, nullptr, d_img_tel, nullptr,
+                         max_img, pp, nullptr, nullptr, 0, d_hillas, 0, s, nullptr, d_counts + 1, d_seg, d_img_seg,
+                         max_seg, static_cast<rta::StreamImg*>(c->d_smeta));
+    };
+    return tune_sweep(c, rta::CHAIN_STREAM, max_img, reps, s, &c->st_variant, &c->st_nstage, &c->st_ctas_per_sm, run,
+                      h_entries, max_entries, n_entries);
 }
 
 int rta_calibrate_integrate(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
@@ -1216,15 +1290,7 @@ int rta_reconstruct_stream(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes,
     if (n_bytes < 0 || max_seg < 1) return fail(RTA_E_INVALID, "bad stream size or segment capacity");
     cudaStream_t s = (cudaStream_t)stream;
     const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
-    const size_t need = sizeof(rta::StreamImg) * size_t(max_img);
-    if (need > c->smeta_bytes) {
-        CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(c->d_smeta);
-        c->d_smeta = nullptr;
-        c->smeta_bytes = 0;
-        CUDA_TRY(cudaMalloc(&c->d_smeta, need));
-        c->smeta_bytes = need;
-    }
+    if ((rc = ensure_smeta(c, max_img, s))) return rc;
     rc = run_chain(c, reinterpret_cast<const uint16_t*>(d_stream), n_bytes / 2, nullptr, d_img_tel, nullptr, max_img,
                    pp, nullptr, nullptr, 0, d_hillas, 0, s, nullptr, d_counts + 1, d_seg, d_img_seg, max_seg,
                    static_cast<rta::StreamImg*>(c->d_smeta));

@@ -244,3 +244,44 @@ def test_full_size_stream():
     d = GpuDir(len(plan["img"]), wl.n_img, wl.n_evt)
     compare_dirs(d.ingest(ctx, dev_bytes(buf), len(buf), True), r)
     ctx.close()
+
+
+def test_stream_autotune_keeps_the_rows_and_tunes_only_the_stream_path():
+    """rta_autotune_stream measures every configuration that fits on the stream,
+    keeps one for the stream path alone (the contiguous bundle's stays), and the
+    zero-copy rows under it are still those of the contiguous bundle; the
+    neighbour-peak window is refused (it is tuned by rta_autotune)."""
+    wl = synth.make_workload(2, 120)
+    ctx = make_ctx(wl)
+    plain = rta.rta_get_chain_config(ctx.handle)
+    h0, s0, h1, s1, buf, plan = reconstruct_both(wl, ctx, {1: 200, 2: 256, 3: 520})
+    assert torch.equal(h0, h1)
+    mode, start, W, t_hi, t_lo, core_nb = proc_args(wl)
+    db = dev_bytes(buf)
+    d = GpuDir(len(plan["img"]), wl.n_img, wl.n_evt)
+    assert d.ingest(ctx, db, len(buf), False)["error"] == 0
+    ht = torch.full_like(h0, np.nan)
+    entries = rta.rta_autotune_stream(ctx.handle, db.data_ptr(), len(buf), d.seg.data_ptr(), d.seg_cap,
+                                      d.img_seg.data_ptr(), d.img_tel.data_ptr(), wl.n_img, d.counts.data_ptr(), mode,
+                                      start, W, t_hi, t_lo, core_nb, ht.data_ptr(), reps=1)
+    torch.cuda.synchronize()
+    assert ctx.check() == 0
+    assert len(entries) >= 10 and all(e["ms"] > 0 for e in entries)
+    assert len({(e["variant"], e["n_stages"], e["ctas_per_sm"]) for e in entries}) == len(entries)
+    assert torch.equal(ht, h0)
+    assert rta.rta_get_chain_config(ctx.handle) == plain
+    # the stream path under the tuned configuration: the same rows and stereo results
+    h2 = torch.full_like(h0, np.nan)
+    s2 = torch.full_like(s0, np.nan)
+    rta.rta_reconstruct_stream(ctx.handle, db.data_ptr(), len(buf), d.seg.data_ptr(), d.seg_cap, d.img_seg.data_ptr(),
+                               d.img_tel.data_ptr(), wl.n_img, d.evt_off.data_ptr(), wl.n_evt, d.counts.data_ptr(),
+                               mode, start, W, t_hi, t_lo, core_nb, h2.data_ptr(), s2.data_ptr())
+    torch.cuda.synchronize()
+    assert ctx.check() == 0
+    assert torch.equal(h2, h0) and torch.equal(s2, s0)
+    with pytest.raises(rta.RtaError) as e:
+        rta.rta_autotune_stream(ctx.handle, db.data_ptr(), len(buf), d.seg.data_ptr(), d.seg_cap,
+                                d.img_seg.data_ptr(), d.img_tel.data_ptr(), wl.n_img, d.counts.data_ptr(),
+                                rta.RTA_WINDOW_NEIGHBOUR, start, W, t_hi, t_lo, core_nb, ht.data_ptr(), reps=1)
+    assert e.value.code == rta.RTA_E_INVALID
+    ctx.close()
