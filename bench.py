@@ -246,6 +246,8 @@ def stream_leg(ctx, wl, proc, stream, steps, e2e_steps, hil, ste, tune=True):
                                           d_img_seg.data_ptr(), d_img_tel.data_ptr(), wl.n_img, d_cnt.data_ptr(),
                                           *proc, h2.data_ptr(), reps=2, stream=sp)
         best = min(entries, key=lambda e: e["ms"])
+        for e in sorted(entries, key=lambda e: e["ms"])[:6]:
+            print("autotune_stream", json.dumps(e), file=sys.stderr)
         stream_cfg = {"variant": best["variant"], "n_stages": best["n_stages"], "ctas_per_sm": best["ctas_per_sm"],
                       "grid": best["grid"], "configs_measured": len(entries)}
         h2.zero_()
