@@ -498,11 +498,8 @@ int rta_ingest(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, int verif
  * most max_img and max_evt; d_seg holds max_seg entries, d_img_seg max_img + 1.
  * An image whose segments do not tile its pixels with 16-byte-aligned runs
  * inside the stream is skipped (RTA_HF_BAD_INPUT). Stream-ordered, no host sync.
- * d_hillas: max_img rows, d_stereo: max_evt rows. As in rta_reconstruct, the
- * stereo kernel reads the event offsets and the counts while the image kernel
- * is finishing: d_evt_off and d_counts must not change between the call and the
- * end of its work on the stream. Grows the context's per-image workspace (an
- * allocation) when max_img is larger than any before. */
+ * d_hillas: max_img rows, d_stereo: max_evt rows. Grows the context's
+ * per-image workspace (an allocation) when max_img is larger than any before. */
 int rta_reconstruct_stream(rta_ctx* ctx, const uint8_t* d_stream, int64_t n_bytes, const rta_segment_t* d_seg,
                            int64_t max_seg, const int32_t* d_img_seg, const int32_t* d_img_tel, int64_t max_img,
                            const int32_t* d_evt_off, int64_t max_evt, const int64_t* d_counts, int window_mode,

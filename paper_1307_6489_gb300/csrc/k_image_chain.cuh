@@ -19,7 +19,6 @@
 // copies in flight before it returns.
 #pragma once
 
-#include <cstddef>
 #include "rta_launch.cuh"
 
 namespace rta {
@@ -475,18 +474,6 @@ struct SlotHdr {
     int img, cam, flags, pad;
 };
 
-// The inline segments of a byte-stream image's record (first pixels, pixel
-// counts, byte offsets): loaded by the producer one image ahead and kept in
-// shared memory while the image's chunks are issued, so that no chunk waits for
-// a load of its segment.
-struct SegInline {
-    int4 first, n, off01, off23;
-};
-static_assert(STREAM_INLINE_SEGS == 4, "SegInline holds four segments");
-static_assert(offsetof(StreamImg, first) == 32 && offsetof(StreamImg, n) == 48 && offsetof(StreamImg, off) == 64 &&
-                  sizeof(StreamImg) == 96,
-              "the producer loads a record as six 16-byte words");
-
 struct ChainSmem {
     uint64_t full[MAX_STAGES];
     uint64_t empty[MAX_STAGES];
@@ -501,7 +488,6 @@ struct ChainSmem {
     int pad[25];
     float red[8];
     int wts[RTA_MAX_W];   // weights of the digital-filter-style extractor
-    SegInline si;         // the byte-stream image whose chunks the producer issues
 };
 
 struct SlotView {
@@ -759,27 +745,23 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
     }
 }
 
-static __device__ __forceinline__ int pick4(int4 v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
-
 // The chunk's pixels [base, base + npix) of a byte-stream image from the
 // segment(s) that hold them (segment and chunk boundaries are multiples of 8
 // samples: 16-byte copies); seg is the segment to start looking at, returned
-// for the next chunk. Segments past the inline ones come from the directory.
-static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, const SegInline& si, int seg0, int seg,
-                                                     int base, int npix, int S, unsigned char* buf, uint64_t* bar,
+// for the next chunk.
+static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, const StreamImg* m, int seg, int base,
+                                                     int npix, int S, unsigned char* buf, uint64_t* bar,
                                                      uint64_t pol) {
     int done = 0;
     while (done < npix) {
         int first, n;
         long long off;
         if (seg < STREAM_INLINE_SEGS) {
-            first = pick4(si.first, seg);
-            n = pick4(si.n, seg);
-            const int4 o = seg < 2 ? si.off01 : si.off23;
-            off = (seg & 1) ? (long long)((uint64_t(uint32_t(o.w)) << 32) | uint32_t(o.z))
-                            : (long long)((uint64_t(uint32_t(o.y)) << 32) | uint32_t(o.x));
+            first = m->first[seg];
+            n = m->n[seg];
+            off = m->off[seg];
         } else {
-            const rta_segment_t sg = a.seg[seg0 + seg];
+            const rta_segment_t sg = a.seg[m->seg0 + seg];
             first = sg.first_pixel;
             n = sg.n_pixels;
             off = sg.offset;
@@ -887,16 +869,11 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
         int next_tel = -1;
         int64_t next_woff = 0;
         int4 next_m0 = make_int4(0, 0, 0, 0), next_m1 = next_m0;     // a byte-stream image's record head
-        SegInline next_si = {next_m0, next_m0, next_m0, next_m0};     // ... and its inline segments
         auto fetch_next = [&]() {
             if (next >= n_img) return;
             if (stream_mode) {
                 next_m0 = __ldg(reinterpret_cast<const int4*>(a.smeta + next));
                 next_m1 = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 1);
-                next_si.first = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 2);
-                next_si.n = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 3);
-                next_si.off01 = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 4);
-                next_si.off23 = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 5);
             } else {
                 next_tel = a.img_tel[next];
                 next_woff = a.wave_off[next];
@@ -908,7 +885,6 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             const int tel = next_tel;
             const int64_t woff = next_woff;
             const int4 m0 = next_m0, m1 = next_m1;
-            if (stream_mode) sm.si = next_si;
             if (img < n_img) {
                 next = atomicAdd(a.counter, 1u);
                 fetch_next();
@@ -994,7 +970,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 // after the image: keep the image in L2 until then
                 const uint64_t pol = NB ? pol_keep : pol_stream;
                 if (stream_mode) {
-                    cur_seg = stream_chunk_copy(a, sm.si, seg0, cur_seg, base, npix, S, buf, &sm.full[stage], pol);
+                    cur_seg = stream_chunk_copy(a, a.smeta + img, cur_seg, base, npix, S, buf, &sm.full[stage], pol);
                 } else {
                     bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], pol);
                 }

@@ -540,10 +540,8 @@ __global__ void __launch_bounds__(256) k_pkt_emit(const IngestArgs a) {
 // ---------------------------------------------------------------- the image kernel's per-image records
 // One thread per image of an ingested stream: the directory checked once (a
 // known telescope; segments that tile the camera's pixels in order, 16-byte
-// aligned, inside the stream) and packed for the producer. It also zeroes the
-// image kernel's work counter, which is launched right after it.
+// aligned, inside the stream) and packed for the producer.
 __global__ void __launch_bounds__(256) k_stream_meta(const ChainArgs a, StreamImg* out, int64_t max_img) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0u;
     const int64_t n = a.n_img_dev ? (*a.n_img_dev < max_img ? *a.n_img_dev : max_img) : max_img;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         StreamImg m = {};

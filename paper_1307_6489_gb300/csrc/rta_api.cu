@@ -309,8 +309,8 @@ int run_chain(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t*
     a.img_seg = d_img_seg;
     a.n_seg = n_seg;
     a.smeta = d_smeta;
-    if (d_smeta) CUDA_TRY(rta::launch_stream_meta(a, d_smeta, n_img, c->n_sm, s));   // zeroes the counter too
-    else CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
+    if (d_smeta) CUDA_TRY(rta::launch_stream_meta(a, d_smeta, n_img, c->n_sm, s));
+    CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s));
     CUDA_TRY(rta::launch_image_chain(cfg.variant, a, grid, smem, s));
     return RTA_OK;
 }
@@ -1295,8 +1295,5 @@ int rta_reconstruct_stream(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes,
                    pp, nullptr, nullptr, 0, d_hillas, 0, s, nullptr, d_counts + 1, d_seg, d_img_seg, max_seg,
                    static_cast<rta::StreamImg*>(c->d_smeta));
     if (rc || max_evt == 0) return rc;
-    // the kernel before the stereo kernel is the image kernel: the event offsets and counts
-    // (the directory) are read while it finishes
-    return run_stereo(c, d_hillas, d_img_tel, max_img, d_evt_off, max_evt, d_stereo, s, d_counts + 1, d_counts + 2,
-                      true);
+    return run_stereo(c, d_hillas, d_img_tel, max_img, d_evt_off, max_evt, d_stereo, s, d_counts + 1, d_counts + 2);
 }
