@@ -109,13 +109,14 @@ int chain_stage_wave_bytes(int v, int max_S) {
     return swb < cap ? swb : cap;
 }
 
-size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys) {
+size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys, int stream_recs) {
     const size_t head = (sizeof(ChainSmem) + 127) & ~size_t(127);
     const size_t words = (max_P + 31) / 32;
     const size_t chunk = size_t(kVariants[v].iw) * 32 * kVariants[v].ppt;
     const size_t keys = nb_keys ? 10 * size_t(max_P) + 16 : 0;   // 64-bit keys, 16-bit candidate ids
+    const size_t recs = stream_recs ? 2 * sizeof(StreamImg) + 16 : 0;   // the producer's two stream records
     return head + size_t(nstage) * (stage_wave_bytes + 2 * chunk * 4) + NSLOT * slot_bytes(max_P) + 8 * words + 16 +
-           keys;
+           keys + recs;
 }
 
 int chain_chunk_pixels(int v, int stage_wave_bytes, int S) {

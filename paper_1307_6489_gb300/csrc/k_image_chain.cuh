@@ -748,7 +748,7 @@ __device__ __forceinline__ void integrate_chunk(const ChainArgs& a, const ProcPa
 // The chunk's pixels [base, base + npix) of a byte-stream image from the
 // segment(s) that hold them (segment and chunk boundaries are multiples of 8
 // samples: 16-byte copies); seg is the segment to start looking at, returned
-// for the next chunk.
+// for the next chunk. m: the image's record in shared memory.
 static __device__ __forceinline__ int stream_chunk_copy(const ChainArgs& a, const StreamImg* m, int seg, int base,
                                                      int npix, int S, unsigned char* buf, uint64_t* bar,
                                                      uint64_t pol) {
@@ -818,6 +818,11 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
     // neighbour-peak keys and candidates of the image being integrated
     uint64_t* nbk = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(maskb + maxw) + 15) & ~uintptr_t(15));
     int16_t* nbc = reinterpret_cast<int16_t*>(nbk + maxP);
+    // byte stream: the records of the image whose chunks the producer issues and of
+    // the next one, copied in by cp.async one image ahead (after the keys, if any)
+    StreamImg* srec = reinterpret_cast<StreamImg*>(
+        (reinterpret_cast<uintptr_t>(NB ? static_cast<void*>(nbc + maxP) : static_cast<void*>(nbk)) + 15) &
+        ~uintptr_t(15));
     volatile int* abort_flag = &sm.abort;
 
     const int tid = threadIdx.x;
@@ -868,12 +873,15 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
         int64_t next = atomicAdd(a.counter, 1u);
         int next_tel = -1;
         int64_t next_woff = 0;
-        int4 next_m0 = make_int4(0, 0, 0, 0), next_m1 = next_m0;     // a byte-stream image's record head
+        int rec_next = 0;              // byte stream: the record buffer the next image's record goes to
+        static_assert(sizeof(StreamImg) % 16 == 0, "records copy in 16-byte pieces");
         auto fetch_next = [&]() {
             if (next >= n_img) return;
             if (stream_mode) {
-                next_m0 = __ldg(reinterpret_cast<const int4*>(a.smeta + next));
-                next_m1 = __ldg(reinterpret_cast<const int4*>(a.smeta + next) + 1);
+                const int4* src = reinterpret_cast<const int4*>(a.smeta + next);
+                int4* dst = reinterpret_cast<int4*>(srec + rec_next);
+#pragma unroll
+                for (int k = 0; k < int(sizeof(StreamImg) / 16); ++k) cp_async16(dst + k, src + k);
             } else {
                 next_tel = a.img_tel[next];
                 next_woff = a.wave_off[next];
@@ -884,7 +892,12 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             const int64_t img = next;
             const int tel = next_tel;
             const int64_t woff = next_woff;
-            const int4 m0 = next_m0, m1 = next_m1;
+            const StreamImg* rec = nullptr;
+            if (stream_mode) {
+                cp_async_wait_all();       // this image's record (copied one image ago) has landed
+                rec = srec + rec_next;
+                rec_next ^= 1;
+            }
             if (img < n_img) {
                 next = atomicAdd(a.counter, 1u);
                 fetch_next();
@@ -905,14 +918,14 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
             int64_t poff = 0;
             int seg0 = 0, seg1 = 0;
             if (stream_mode) {
-                // ok, cam, segments | calibration row, P, S (checked by k_stream_meta)
-                bad = m0.x == 0;
-                cam = m0.y;
-                seg0 = m0.w;
-                seg1 = m0.w + m0.z;
-                row = int64_t(uint32_t(m1.x)) | (int64_t(m1.y) << 32);
-                P = m1.z;
-                S = m1.w;
+                // checked by k_stream_meta
+                bad = rec->ok == 0;
+                cam = rec->cam;
+                seg0 = rec->seg0;
+                seg1 = rec->seg0 + rec->nseg;
+                row = rec->row;
+                P = rec->P;
+                S = rec->S;
             } else {
                 bad = tel < 0 || tel >= a.arr.n_tel || woff < 0 || (woff & 7) != 0;
                 cam = 0;
@@ -970,7 +983,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                 // after the image: keep the image in L2 until then
                 const uint64_t pol = NB ? pol_keep : pol_stream;
                 if (stream_mode) {
-                    cur_seg = stream_chunk_copy(a, a.smeta + img, cur_seg, base, npix, S, buf, &sm.full[stage], pol);
+                    cur_seg = stream_chunk_copy(a, rec, cur_seg, base, npix, S, buf, &sm.full[stage], pol);
                 } else {
                     bulk_g2s(buf, src + size_t(base) * S, wbytes, &sm.full[stage], pol);
                 }

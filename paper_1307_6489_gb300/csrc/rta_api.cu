@@ -223,12 +223,14 @@ struct ChainCfg {
 int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_t* smem, int* swb,
                   int kind = rta::CHAIN_PLAIN) {
     const int nb = kind == rta::CHAIN_NB;
+    // the stream kernel keeps two per-image records (the neighbour-peak one too: it may run on a stream)
+    const int st = kind == rta::CHAIN_STREAM || kind == rta::CHAIN_NB;
     if (k.variant < 0 || k.variant >= RTA_CHAIN_VARIANTS) return fail(RTA_E_INVALID, "variant %d", k.variant);
     const int nst = std::max(2, std::min(k.nstage, 8));
     *swb = rta::chain_stage_wave_bytes(k.variant, c->max_S);
     if (rta::chain_chunk_pixels(k.variant, *swb, c->max_S) < 32)
         return fail(RTA_E_INVALID, "tile variant %d has no room for %d samples", k.variant, c->max_S);
-    *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P, nb);
+    *smem = rta::chain_smem_bytes(k.variant, nst, *swb, c->max_P, nb, st);
     int occ = rta::chain_occupancy(k.variant, *smem, kind);
     const int want = k.ctas_per_sm > 0 ? k.ctas_per_sm : rta::chain_variant_min_blocks(k.variant);
     if (occ < want) {
@@ -236,7 +238,7 @@ int config_launch(rta_ctx* c, const ChainCfg& k, int64_t n_img, int* grid, size_
         // chunk) so that the requested number of CTAs fits on an SM
         for (int s2 = (*swb - 1024) & ~127; s2 >= 4096; s2 -= 1024) {
             if (rta::chain_chunk_pixels(k.variant, s2, c->max_S) < 128) break;
-            const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P, nb);
+            const size_t sm2 = rta::chain_smem_bytes(k.variant, nst, s2, c->max_P, nb, st);
             const int occ2 = rta::chain_occupancy(k.variant, sm2, kind);
             if (occ2 >= want) {
                 *swb = s2;

@@ -137,6 +137,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     return mbar_wait_ns(bar, parity, abort, RTA_WAIT_TIMEOUT_NS);
 }
 
+// 16 bytes global -> shared by the calling thread without holding registers
+// (cp.async); complete for this thread after cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // One bulk copy global -> shared through the TMA engine, completing `bytes` of
 // transaction count on `bar`. dst, src 16-byte aligned; bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,

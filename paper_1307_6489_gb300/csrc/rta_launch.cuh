@@ -92,7 +92,7 @@ int chain_variant_warps(int v);
 int chain_variant_ppt(int v);
 int chain_threads(int v);
 int chain_stage_wave_bytes(int v, int max_S);
-size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys = 0);
+size_t chain_smem_bytes(int v, int nstage, int stage_wave_bytes, int max_P, int nb_keys = 0, int stream_recs = 0);
 int chain_chunk_pixels(int v, int stage_wave_bytes, int S);
 // which instantiation family of the fused kernel a launch uses (the occupancy of
 // a family's general instantiation stands for its lean ones: same launch bounds,
