@@ -734,6 +734,8 @@ int rta_autotune_stream(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes, co
     const rta::ProcParams pp = make_pp(c, window_mode, start, W, core_needs_neighbour, t_hi, t_lo);
     if ((rc = ensure_smeta(c, max_img, s))) return rc;
     // until tuned, the stream kernel follows the plain kernel's configuration: start from it
+    // (and follow it again if the sweep fails)
+    const int st_before = c->st_variant;
     if (c->st_variant < 0) {
         c->st_variant = c->variant;
         c->st_nstage = c->nstage;
@@ -744,8 +746,10 @@ int rta_autotune_stream(rta_ctx* c, const uint8_t* d_stream, int64_t n_bytes, co
                          max_img, pp, nullptr, nullptr, 0, d_hillas, 0, s, nullptr, d_counts + 1, d_seg, d_img_seg,
                          max_seg, static_cast<rta::StreamImg*>(c->d_smeta));
     };
-    return tune_sweep(c, rta::CHAIN_STREAM, max_img, reps, s, &c->st_variant, &c->st_nstage, &c->st_ctas_per_sm, run,
-                      h_entries, max_entries, n_entries);
+    rc = tune_sweep(c, rta::CHAIN_STREAM, max_img, reps, s, &c->st_variant, &c->st_nstage, &c->st_ctas_per_sm, run,
+                    h_entries, max_entries, n_entries);
+    if (rc && st_before < 0) c->st_variant = -1;
+    return rc;
 }
 
 int rta_calibrate_integrate(rta_ctx* c, const uint16_t* d_wave, int64_t n_wave, const int64_t* d_wave_off,
