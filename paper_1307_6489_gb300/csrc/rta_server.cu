@@ -415,8 +415,10 @@ cudaError_t read_own(rta_stream* S) {
         if (e_ != cudaSuccess) return vfail(RTA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
 
-// Admit one bundle: copies in on the slot's stream, then its publication.
-int dispatch(rta_stream* S, Req& r, Slot& sl) {
+// Admit one bundle: copies in on the slot's stream, then its publication (*pub: its
+// publication may be on the stream, so a failure after it must empty the device queue).
+int dispatch(rta_stream* S, Req& r, Slot& sl, bool* pub) {
+    *pub = false;
     const rta_bundle_t& b = r.b;
     char* base = S->arena.base + r.off;
     uint16_t* d_wave = reinterpret_cast<uint16_t*>(base + r.L.wave);
@@ -447,6 +449,7 @@ int dispatch(rta_stream* S, Req& r, Slot& sl) {
     d.n_evt = b.n_evt;
     d.arrival_ns = b.arrival_ns;
     d.out = sl.d_stage;
+    *pub = true;
     k_publish<<<1, 1, 0, s>>>(S->d_ring, S->d_ctl, d);
     D_TRY(cudaGetLastError());
     D_TRY(cudaEventRecord(sl.e_pub, s));
@@ -503,6 +506,7 @@ void finish_pass(rta_stream* S, Pass& p) {
         auto it = S->reqs.find(tab[k].d.ticket);
         if (it == S->reqs.end()) continue;
         Req& r = it->second;
+        if (r.state != REQ_COPYING && r.state != REQ_PUBLISHED) continue;   // failed meanwhile: released
         Slot& sl = S->slots[r.slot];
         // the event rows, written into the slot's staging by the pass
         std::memcpy(r.b.h_events, sl.h_stage, size_t(r.b.n_evt) * sizeof(rta_event_t));
@@ -524,12 +528,16 @@ void finish_pass(rta_stream* S, Pass& p) {
     }
 }
 
-// Every admitted bundle fails (a pass could not be enqueued; caller holds S->mu).
+// Every admitted bundle fails (a pass or a publication could not be enqueued, or a
+// CUDA call failed; caller holds S->mu). Once nothing of the stream's is in flight, the
+// passes still listed (their bundles are among the failed) are dropped and the device
+// queue is emptied, so that no later pass takes a descriptor of a released bundle.
 void fail_admitted(rta_stream* S, int rc) {
     cudaStreamSynchronize(S->s_cmp);
+    for (auto& sl : S->slots)
+        if (sl.s) cudaStreamSynchronize(sl.s);
     for (auto& sl : S->slots) {
         if (!sl.busy) continue;
-        cudaStreamSynchronize(sl.s);
         Req& r = S->reqs[sl.ticket];
         S->arena.release(r.off, r.L.total);
         sl.busy = false;
@@ -538,6 +546,11 @@ void fail_admitted(rta_stream* S, int rc) {
         r.rc = rc;
         r.done_ns = now_ns();
     }
+    S->passes.clear();
+    S->need_pass = false;
+    if (cudaMemsetAsync(S->d_ring, 0, sizeof(RingSlot) * RING, S->s_cmp) == cudaSuccess &&
+        cudaMemsetAsync(S->d_ctl, 0, sizeof(QueueCtl), S->s_cmp) == cudaSuccess)
+        cudaStreamSynchronize(S->s_cmp);
 }
 
 void worker_loop(rta_stream* S) {
@@ -590,8 +603,11 @@ void worker_loop(rta_stream* S) {
             fs->busy = true;
             fs->ticket = r.ticket;
             ++S->running;
-            const int rc = dispatch(S, r, *fs);
-            if (rc) {   // nothing more is enqueued for it; let what was enqueued finish
+            bool pub = false;
+            const int rc = dispatch(S, r, *fs, &pub);
+            if (rc && pub) {
+                fail_admitted(S, rc);        // its descriptor may be in the device queue
+            } else if (rc) {   // nothing more is enqueued for it; let what was enqueued finish
                 cudaStreamSynchronize(fs->s);
                 S->arena.release(r.off, r.L.total);
                 fs->busy = false;
