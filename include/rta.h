@@ -366,6 +366,8 @@ int rta_surrogate_num_params(void);
 /* h_cam_code: RTA_MAX_CAMS floats, the type code of each camera id (NULL = zeros). */
 int rta_surrogate_create(rta_ctx* ctx, uint64_t seed, const float* h_cam_code, rta_model** out);
 int rta_surrogate_destroy(rta_model* model);
+/* Replaces the FP32 parameters (packed order) and rebuilds the BF16 copy and the
+ * tensor-core layout; waits for all work on the device first. Synchronous. */
 int rta_surrogate_set_params(rta_model* model, const float* h_params);
 /* which: 0 parameters, 1 last gradients, 2 Adam first moments, 3 second moments. Synchronises. */
 int rta_surrogate_get_params(rta_model* model, int which, float* h_out);
@@ -373,7 +375,8 @@ int rta_surrogate_get_params(rta_model* model, int which, float* h_out);
  * second moments (each rta_surrogate_num_params() floats in the packed order of
  * rta_surrogate_set_params) and the number of Adam steps taken, which sets the
  * bias corrections of the next step. get_state synchronises the device and
- * fills the non-NULL arrays; set_state replaces the whole state (the BF16 copy
+ * fills the non-NULL arrays; set_state waits for all work on the device, then
+ * replaces the whole state (the BF16 copy
  * and the tensor-core layout of the weights are rebuilt), so that training
  * resumed from a saved state takes the same steps as training that never
  * stopped. Synchronous. */

@@ -232,6 +232,9 @@ uint16_t to_bf16_bits(float f) {
 }
 
 int upload_params(rta_model* md, const std::vector<float>& internal) {
+    // work of the model still running on any stream (a training step, an inference)
+    // finishes before its weights are replaced
+    S_TRY(cudaDeviceSynchronize());
     std::vector<uint16_t> b(internal.size());
     for (size_t i = 0; i < internal.size(); ++i) b[i] = to_bf16_bits(internal[i]);
     S_TRY(cudaMemcpy(md->p, internal.data(), sizeof(float) * internal.size(), cudaMemcpyHostToDevice));
