@@ -1007,6 +1007,7 @@ __global__ void __launch_bounds__(IW * 32 + 64, MB) k_image_chain(const ChainArg
                         if (global_ns() - t0 > RTA_WAIT_TIMEOUT_NS) break;
                 }
         }
+        if constexpr (STREAM) cp_async_wait_all();   // a record copy after an abort lands first too
         return;
     }
 
