@@ -297,6 +297,7 @@ def stream_leg(ctx, wl, proc, stream, steps, e2e_steps, hil, ste, tune=True):
             "ingest_crc_gbs": n_bytes / (ingest_crc_ms / 1e3) / 1e9,
             "ingest_crc_hbm_frac": n_bytes / (ingest_crc_ms / 1e3) / 1e9 / hbm_peak,
             "reconstruct_stream_ms": recon_ms,
+            "reconstruct_stream_hbm_frac": n_bytes / (recon_ms / 1e3) / 1e9 / hbm_peak,
             "reconstruct_stream_ms_bundle_config": recon_bundle_cfg_ms,
             "stream_config": stream_cfg,
             "e2e": {"value": wl.n_evt / e2e_s, "unit": "events/s", "h2d_bytes_per_step": n_bytes,
